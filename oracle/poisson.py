@@ -1,0 +1,200 @@
+"""Pressure Poisson equation, multigrid and projection (Section 2.4, Algorithm 1).
+
+  b        = -(1/dt) (D_x * L_x * BC_x(u*) + D_y * ... + D_z * ...)   (Eq. pc_residual)
+  A p      = -Laplacian_h p with one ghost layer (Eq. neg_lap_discretize
+             and the printed 3x3x3 kernel)
+  smoother   p <- p + w_J D^{-1} (b - A p), D = sum_d 2 / h_d^2 scalar
+             (Eq. jacobi_pc; weighted)
+  RES        mean of the 2x2x2 children (Eq. restriction)
+  PROL       cell-centred trilinear interpolation, 3/4 parent + 1/4
+             neighbour per axis, neighbour index clamped to the grid
+             (Eq. prolongation)
+  V-cycle    pre-smooth, restrict the residual, recurse, prolong and
+             correct, post-smooth; exact dense solve on the coarsest level
+  projection u = u* - dt G p, G the cell-centred gradient L * D * BC(p)
+
+Solid cells hold zero pressure and are excluded from every norm.
+"""
+import numpy as np
+
+from .geometry import U, V, W, FK_SOLID, D_op, L_op, pressure_face_states
+
+
+# ------------------------------------------------------------------ level 0
+def poisson_rhs(geo, u, v, w, dt):
+    """b = -div(u*) / dt with face velocities L * BC(u*) (Algorithm 1 lines on b)."""
+    div = np.zeros(geo.shape)
+    for axis, (phi, f) in enumerate(((u, U), (v, V), (w, W))):
+        if geo.shape[axis] == 1:
+            continue
+        L, R, kind = geo.face_states(phi, f, axis)
+        uf = 0.5 * (L + R)
+        uf[kind == FK_SOLID] = 0.0
+        div += D_op(uf, axis, geo.h[axis])
+    b = -div / dt
+    b[geo.solid] = 0.0
+    return b
+
+
+def pressure_gradient(lev, p):
+    """Cell-centred gradient L_j * D_j * BC_j(p) with the pressure ghosts."""
+    g = []
+    for axis in range(3):
+        if lev.shape[axis] == 1:
+            g.append(np.zeros(lev.shape))
+            continue
+        L, R = pressure_face_states(p, lev, axis)
+        g.append(L_op((R - L) / lev.h[axis], axis))
+    return g
+
+
+def project(geo, lev0, u, v, w, p, dt):
+    """u = u* - dt grad p on fluid cells (projection step of Section 2.4)."""
+    g = pressure_gradient(lev0, p)
+    out = []
+    for phi, gg in zip((u, v, w), g):
+        out.append(np.where(geo.fluid, phi - dt * gg, phi))
+    return out
+
+
+def face_divergence(geo, lev0, u, v, w, p, dt):
+    """Divergence of the face fluxes u*_f - dt (p_R - p_L)/h: equals dt (A p - b)."""
+    div = np.zeros(geo.shape)
+    for axis, (phi, f) in enumerate(((u, U), (v, V), (w, W))):
+        if geo.shape[axis] == 1:
+            continue
+        L, R, kind = geo.face_states(phi, f, axis)
+        pL, pR = pressure_face_states(p, lev0, axis)
+        uf = 0.5 * (L + R) - dt * (pR - pL) / geo.h[axis]
+        uf[kind == FK_SOLID] = 0.0
+        div += D_op(uf, axis, geo.h[axis])
+    div[geo.solid] = 0.0
+    return div
+
+
+# ------------------------------------------------------------------ operators
+def apply_A(lev, p):
+    """A p = -sum_d D_d * (D_d * BC_d(p)) on fluid cells."""
+    out = np.zeros(lev.shape)
+    for axis in range(3):
+        if lev.shape[axis] == 1:
+            continue
+        L, R = pressure_face_states(p, lev, axis)
+        out -= D_op((R - L) / lev.h[axis], axis, lev.h[axis])
+    out[lev.solid] = 0.0
+    return out
+
+
+def residual(lev, p, b):
+    r = b - apply_A(lev, p)
+    r[lev.solid] = 0.0
+    return r
+
+
+def jacobi_weight(lev, spec):
+    if spec.jacobi_weight > 0:
+        return spec.jacobi_weight
+    return 6.0 / 7.0 if all(lev.active) else 4.0 / 5.0
+
+
+def smooth(lev, p, b, sweeps, wJ):
+    """Weighted Jacobi: p <- p + w_J (b - A p) / D (Eq. jacobi_pc)."""
+    D = lev.diag()
+    for _ in range(sweeps):
+        p = np.where(lev.fluid, p + wJ * residual(lev, p, b) / D, 0.0)
+    return p
+
+
+def restrict(lev, r):
+    """RES: mean of the children (2 per active axis)."""
+    f = tuple(2 if a else 1 for a in lev.active)
+    c = tuple(n // ff for n, ff in zip(lev.shape, f))
+    return r.reshape(c[0], f[0], c[1], f[1], c[2], f[2]).mean(axis=(1, 3, 5))
+
+
+def prolong(coarse, fine_shape):
+    """PROL: per active axis, fine cell = 3/4 parent + 1/4 neighbour on the
+    fine cell's side (neighbour index clamped into the coarse grid)."""
+    e = coarse
+    for axis in range(3):
+        nc = e.shape[axis]
+        nf = fine_shape[axis]
+        if nf == nc:
+            continue
+        i_f = np.arange(nf)
+        parent = i_f // 2
+        nb = np.clip(parent + np.where(i_f % 2 == 0, -1, 1), 0, nc - 1)
+        e = 0.75 * np.take(e, parent, axis=axis) + 0.25 * np.take(e, nb, axis=axis)
+    return e
+
+
+def dense_operator(lev):
+    """The matrix of A on a level, built column by column from unit vectors.
+    Rows and columns of solid cells are the identity."""
+    n = int(np.prod(lev.shape))
+    M = np.zeros((n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        M[:, c] = apply_A(lev, e.reshape(lev.shape)).ravel()
+    solid = lev.solid.ravel()
+    M[solid, :] = 0.0
+    M[:, solid] = 0.0
+    M[solid, solid] = 1.0
+    return M
+
+
+def direct_solve(lev, b):
+    """Exact discrete solution of A p = b (dense LU through numpy)."""
+    M = dense_operator(lev)
+    rhs = np.where(lev.solid, 0.0, b).ravel()
+    return np.linalg.solve(M, rhs).reshape(lev.shape)
+
+
+# ------------------------------------------------------------------ V-cycle
+class Multigrid:
+    def __init__(self, geo, n_levels):
+        self.spec = geo.spec
+        self.levels = geo.levels(n_levels)
+        self._coarse_M = dense_operator(self.levels[-1])
+
+    def coarse_solve(self, b):
+        lev = self.levels[-1]
+        rhs = np.where(lev.solid, 0.0, b).ravel()
+        return np.linalg.solve(self._coarse_M, rhs).reshape(lev.shape)
+
+    def vcycle(self, p, b, l=0):
+        lev = self.levels[l]
+        if l == len(self.levels) - 1:
+            return self.coarse_solve(b)
+        wJ = jacobi_weight(lev, self.spec)
+        p = smooth(lev, p, b, self.spec.pre_sweeps, wJ)
+        bc = restrict(lev, residual(lev, p, b))
+        ec = self.vcycle(np.zeros(self.levels[l + 1].shape), bc, l + 1)
+        p = np.where(lev.fluid, p + prolong(ec, lev.shape), 0.0)
+        p = smooth(lev, p, b, self.spec.post_sweeps, wJ)
+        return p
+
+    def rel_residual(self, p, b):
+        lev = self.levels[0]
+        nb = np.linalg.norm(b[lev.fluid])
+        if nb == 0.0:
+            return 0.0
+        return float(np.linalg.norm(residual(lev, p, b)[lev.fluid]) / nb)
+
+    def solve(self, p, b):
+        """V-cycles from warm start p: exactly fixed_vcycles of them if set,
+        else until the relative residual is <= mg_rel_tol or max_vcycles ran.
+        Returns (p, cycles, final relative residual)."""
+        s = self.spec
+        if s.fixed_vcycles > 0:
+            for _ in range(s.fixed_vcycles):
+                p = self.vcycle(p, b)
+            return p, s.fixed_vcycles, self.rel_residual(p, b)
+        n = 0
+        rel = self.rel_residual(p, b)
+        while rel > s.mg_rel_tol and n < s.max_vcycles:
+            p = self.vcycle(p, b)
+            n += 1
+            rel = self.rel_residual(p, b)
+        return p, n, rel

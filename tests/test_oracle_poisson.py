@@ -1,0 +1,207 @@
+"""Pins of the oracle's Poisson operator, multigrid and projection
+(Section 2.4, Algorithm 1) against the printed kernel, polynomial
+exactness, brute-force dense solves and a manufactured solution."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import poisson
+from oracle.geometry import Geometry
+from oracle.poisson import Multigrid, apply_A, direct_solve, prolong, restrict
+from oracle.step import OracleCase
+from paper_2603_21869_gb300 import cases
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _spec(nx, ny, nz, L=(1.0, 1.0, 1.0), outlet_faces=(1,), boxes=(), levels=2, **kw):
+    faces = [cases.Patch(cases.WALL) for _ in range(6)]
+    for f in outlet_faces:
+        faces[f] = cases.Patch(cases.OUTLET)
+    if nz == 1:
+        faces[4] = cases.Patch(cases.EMPTY)
+        faces[5] = cases.Patch(cases.EMPTY)
+    return cases.CaseSpec(nx=nx, ny=ny, nz=nz, Lx=L[0], Ly=L[1], Lz=L[2], faces=faces,
+                          boxes=list(boxes), mg_levels=levels, **kw)
+
+
+def test_printed_laplacian_kernel():
+    """A applied to a unit impulse reproduces the printed 3x3x3 kernel (x -1/dx^2)."""
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "laplacian_kernel.txt"))
+            if l.strip() and not l.startswith("#")]
+    K = np.array(rows).reshape(3, 3, 3)          # [k][j][i]
+    h = 0.125
+    geo = Geometry(_spec(8, 8, 8))
+    lev = geo.level0
+    e = np.zeros(lev.shape)
+    e[4, 4, 4] = 1.0
+    Ae = apply_A(lev, e)
+    # A = -(1/h^2) K * BC(p): the response at cell c to an impulse at (4,4,4) is
+    # -(1/h^2) K[offset], and K is symmetric so orientation does not matter
+    got = Ae[3:6, 3:6, 3:6].transpose(2, 1, 0)
+    assert np.allclose(got, -K / h ** 2, rtol=1e-14, atol=0)
+    assert np.count_nonzero(Ae) == 7
+
+
+def test_jacobi_diagonal_is_six_over_dx2():
+    """Eq. jacobi_pc: D replaced by the scalar 6/dx^2 (isotropic 3D)."""
+    geo = Geometry(_spec(8, 8, 8))
+    assert geo.level0.diag() == pytest.approx(6.0 / 0.125 ** 2, rel=1e-15)
+    geo2 = Geometry(_spec(8, 4, 1, L=(1.0, 0.5, 0.125)))
+    assert geo2.level0.diag() == pytest.approx(4.0 / 0.125 ** 2, rel=1e-15)
+
+
+def test_A_exact_on_quadratic():
+    """-Laplacian_h of x^2 + 3 y^2 - z^2 is exactly -(2 + 6 - 2) = -6 in the interior."""
+    geo = Geometry(_spec(8, 8, 8))
+    x = (np.arange(8) + 0.5) / 8
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    Ap = apply_A(geo.level0, X ** 2 + 3 * Y ** 2 - Z ** 2)
+    assert np.allclose(Ap[1:-1, 1:-1, 1:-1], -6.0, rtol=0, atol=1e-10)
+
+
+def test_neumann_and_dirichlet_ghosts():
+    """Zero-gradient faces: A(const) = 0 next to walls; an outlet face adds
+    2/h^2 (ghost = -p puts p = 0 on the face)."""
+    geo = Geometry(_spec(8, 8, 8, outlet_faces=(1,)))
+    Ap = apply_A(geo.level0, np.ones((8, 8, 8)))
+    assert np.allclose(Ap[:-1], 0.0, atol=1e-10)
+    assert np.allclose(Ap[-1], 2.0 / 0.125 ** 2, rtol=1e-14)
+
+
+def test_restrict_prolong_properties():
+    lev = Geometry(_spec(8, 8, 8)).level0
+    c = np.random.default_rng(0).normal(size=(4, 4, 4))
+    # RES is the mean of children: constant in, constant out; sums scale by 1/8
+    r = np.random.default_rng(1).normal(size=(8, 8, 8))
+    assert np.allclose(restrict(lev, np.full((8, 8, 8), 3.5)), 3.5)
+    assert restrict(lev, r).sum() == pytest.approx(r.sum() / 8, rel=1e-13)
+    # PROL reproduces constants everywhere and linear functions away from the clamped edge
+    assert np.allclose(prolong(np.full((4, 4, 4), 2.0), (8, 8, 8)), 2.0)
+    xc = (np.arange(4) + 0.5) * 2.0
+    xf = np.arange(8) + 0.5
+    lin_c = xc[:, None, None] + 0 * c
+    lin_f = prolong(lin_c, (8, 8, 8))
+    assert np.allclose(lin_f[1:-1, :, :], xf[1:-1, None, None], atol=1e-13)
+    # weights (27, 9, 9, 3, 9, 3, 3, 1)/64 around an interior fine cell
+    imp = np.zeros((4, 4, 4))
+    imp[1, 1, 1] = 64.0
+    pf = prolong(imp, (8, 8, 8))
+    assert pf[2, 2, 2] == pytest.approx(27) and pf[3, 3, 3] == pytest.approx(27)
+    assert pf[1, 2, 2] == pytest.approx(9) and pf[1, 1, 2] == pytest.approx(3)
+    assert pf[1, 1, 1] == pytest.approx(1) and pf[4, 4, 4] == pytest.approx(1)
+
+
+@pytest.mark.parametrize("shape,boxes,levels", [
+    ((16, 8, 8), (), 3),
+    ((16, 8, 8), (cases.Box(4, 8, 2, 6, 0, 4),), 3),
+    ((16, 8, 1), (), 3),
+    ((32, 16, 1), (cases.Box(12, 16, 0, 8, 0, 1),), 4),
+])
+def test_vcycles_converge_to_dense_solution(shape, boxes, levels):
+    """Brute force: the V-cycle iterates converge to the dense LU solution
+    (isotropic cells; point Jacobi with full coarsening is not a smoother
+    for stretched cells)."""
+    nx, ny, nz = shape
+    spec = _spec(nx, ny, nz, L=(2.0, 1.0, 1.0 if nz > 1 else 1.0 / ny), boxes=boxes,
+                 levels=levels, outlet_faces=(1,), pre_sweeps=3, post_sweeps=3)
+    geo = Geometry(spec)
+    lev = geo.level0
+    b = np.random.default_rng(7).normal(size=lev.shape)
+    b[lev.solid] = 0.0
+    p_direct = direct_solve(lev, b)
+    mg = Multigrid(geo, levels)
+    p = np.zeros(lev.shape)
+    rels = []
+    for _ in range(40):
+        p = mg.vcycle(p, b)
+        rels.append(mg.rel_residual(p, b))
+        if rels[-1] < 1e-13:
+            break
+    assert np.max(np.abs(p - p_direct)) <= 1e-10 * np.max(np.abs(p_direct))
+    assert np.all(p[lev.solid] == 0.0)
+
+
+@pytest.mark.parametrize("levels,sweeps,bound", [(2, 2, 0.3), (4, 3, 0.3)])
+def test_vcycle_contraction_factor(levels, sweeps, bound):
+    """Sanity bound on the asymptotic residual contraction per cycle: the
+    two-grid V(2,2) and the 4-level V(3,3) with weighted Jacobi, child-mean
+    restriction and trilinear prolongation contract by better than 0.3."""
+    spec = _spec(32, 32, 32, levels=levels, outlet_faces=(1,), pre_sweeps=sweeps, post_sweeps=sweeps)
+    geo = Geometry(spec)
+    mg = Multigrid(geo, levels)
+    b = np.random.default_rng(2).normal(size=geo.shape)
+    p = np.zeros(geo.shape)
+    rs = [mg.rel_residual(p, b)]
+    for _ in range(8):
+        p = mg.vcycle(p, b)
+        rs.append(mg.rel_residual(p, b))
+    rho = (rs[-1] / rs[4]) ** (1 / 4)
+    assert rho < bound
+
+
+def _manufactured_error(n):
+    Lx, Ly, Lz = 2.0, 1.0, 1.0
+    spec = _spec(2 * n, n, n, L=(Lx, Ly, Lz), outlet_faces=(1,), levels=3)
+    geo = Geometry(spec)
+    hx, hy, hz = geo.h
+    x = (np.arange(2 * n) + 0.5) * hx
+    y = (np.arange(n) + 0.5) * hy
+    z = (np.arange(n) + 0.5) * hz
+    X, Y, Z = np.meshgrid(x, y, z, indexing="ij")
+    # dp/dn = 0 on x = 0 and on the y, z walls; p = 0 on the outlet face x = Lx
+    p_ex = np.cos(np.pi * X / (2 * Lx)) * np.cos(np.pi * Y / Ly) * np.cos(np.pi * Z / Lz)
+    lam = np.pi ** 2 * (1 / (4 * Lx ** 2) + 1 / Ly ** 2 + 1 / Lz ** 2)
+    b = lam * p_ex
+    mg = Multigrid(geo, 3)
+    p = np.zeros(geo.shape)
+    for _ in range(60):
+        p = mg.vcycle(p, b)
+        if mg.rel_residual(p, b) < 1e-12:
+            break
+    return np.max(np.abs(p - p_ex))
+
+
+def test_manufactured_solution_second_order():
+    e1 = _manufactured_error(8)
+    e2 = _manufactured_error(16)
+    assert 3.3 < e1 / e2 < 4.7
+    assert e2 < 5e-3
+
+
+def test_projection_with_direct_solve_is_divergence_free():
+    """With the exact discrete pressure the corrected face fluxes have zero
+    divergence: div = dt (A p - b)."""
+    spec = cases.heated_channel_3d(16, 8, 8, mg_levels=2, init_perturb=0.05,
+                                   boxes=[cases.Box(5, 8, 2, 5, 0, 3)])
+    c = OracleCase(spec)
+    c.destruction_half()
+    c.explicit()
+    c.destruction_half()
+    c.rhs()
+    lev = c.mg.levels[0]
+    p = direct_solve(lev, c.b)
+    u, v, w = c.state[:3]
+    div = poisson.face_divergence(c.geo, lev, u, v, w, p, c.dt)
+    scale = np.max(np.abs(c.b)) * c.dt
+    assert scale > 1e-6
+    assert np.max(np.abs(div)) < 1e-11 * scale
+    # and for an arbitrary p the identity div = dt (A p - b) holds exactly
+    q = np.random.default_rng(4).normal(size=lev.shape)
+    q[lev.solid] = 0.0
+    div_q = poisson.face_divergence(c.geo, lev, u, v, w, q, c.dt)
+    ident = c.dt * (apply_A(lev, q) - c.b)
+    assert np.allclose(div_q[lev.fluid], ident[lev.fluid], rtol=0, atol=1e-12 * scale * 1e3)
+
+
+def test_rhs_zero_for_uniform_through_flow():
+    """Uniform u with matching inlet speed and zero-gradient outlet is
+    discretely divergence free: b = 0."""
+    spec = cases.heated_channel_3d(16, 8, 8, mg_levels=2)
+    faces = list(spec.faces)
+    faces[2] = faces[3] = faces[4] = faces[5] = cases.Patch(cases.OUTLET)
+    spec = spec.replace(faces=faces, init_perturb=0.0)
+    c = OracleCase(spec)
+    c.rhs()
+    assert np.max(np.abs(c.b)) == 0.0
