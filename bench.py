@@ -1,0 +1,290 @@
+"""Benchmark: k-omega RANS finite-volume time steps on one GB300 (or N replicas).
+
+Default workload: the 3D heated channel, 256 x 64 x 64 cells (1 cm cells on
+the paper's 2.56 x 0.64 x 0.64 m verification channel), inlet 2 m/s, 6-level
+V-cycles to a 1e-8 relative residual, seeded +-1 % initial perturbation,
+FP32 storage with the FP64 defect-correction pressure solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64]
+                    [--impl ours|reference]
+
+Prints one JSON line.  value = cell-steps/s over all ranks (each rank steps
+its own replica; no collective on the data path, weak scaling).  Timing: W
+untimed steps, then K steps each bracketed by CUDA events on the case's
+stream, with a 256 MB buffer written between steps so the step starts with
+a cold L2 (the state is ~30 MB, below the 129 MB L2).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_21869_gb300 import cases  # noqa: E402
+
+PREC = {"f32": cases.FP32, "f64": cases.FP64, "bf16": cases.BF16_MIXED}
+
+
+def workload(name, precision):
+    if name == "channel":
+        return cases.heated_channel_3d(256, 64, 64, mg_levels=6, precision=precision,
+                                       mg_rel_tol=1e-8, max_vcycles=60), \
+            "heated_channel_3d 256x64x64, 6-level V(3,3), rel tol 1e-8"
+    if name == "room":
+        return cases.room_3d(512, 256, 128, seed=0, mg_levels=7, precision=precision,
+                             mg_rel_tol=1e-8, max_vcycles=60), \
+            "room_3d 512x256x128 (16.8M cells), seeded vents/boxes, buoyancy"
+    if name == "channel2d":
+        return cases.channel_2d(), "channel_2d 128x32"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, ws, local, dist
+
+
+def run_reference(args, spec, label, rank, ws):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    from oracle.step import OracleCase
+    c = OracleCase(spec.replace(precision=cases.FP64))
+    for _ in range(args.warmup):
+        c.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c.step()
+    el = time.perf_counter() - t0
+    v = spec.cells * args.steps / el
+    line = {"impl": "reference", "metric": "cell-steps/s", "value": v, "unit": "cell-steps/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": label, "cells": spec.cells},
+            "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.warmup} untimed + {args.steps} timed steps of the full workload "
+                                       "(numpy float64, one thread)"},
+            "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec, budget_s=25.0):
+    """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload."""
+    from oracle.step import OracleCase
+    t0 = time.perf_counter()
+    c = OracleCase(spec.replace(precision=cases.FP64))
+    n = 0
+    ts = time.perf_counter()
+    while n < 1 or (time.perf_counter() - t0 < budget_s and n < 3):
+        c.step()
+        n += 1
+    el = time.perf_counter() - ts
+    return {"value": spec.cells * n / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} step(s) of the full {spec.nx}x{spec.ny}x{spec.nz} workload, numpy float64 on one "
+                      f"host thread ({os.cpu_count()} cores present)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=list(PREC))
+    ap.add_argument("--workload", default="channel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    spec, label = workload(args.workload, PREC[args.precision])
+    rank, ws, local, dist = dist_setup()
+    if args.impl == "reference":
+        args.steps = min(args.steps, 2)
+        args.warmup = min(args.warmup, 0)
+        run_reference(args, spec, label, rank, ws)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_2603_21869_gb300 import binding, build
+    build.ensure_built()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    case = binding.Case(spec, stream=stream.cuda_stream)
+    N = spec.cells
+    vcycles = 0
+    for _ in range(args.warmup):
+        vcycles += case.step(1, allow_not_converged=True)["vcycles_last"]
+    torch.cuda.synchronize()
+    launches0 = case.info()["kernel_launches"]
+    clocks = Clocks(local)
+    clocks.start()
+    case.profile(True)
+    times = []
+    vc = []
+    rels = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = case.step(1, allow_not_converged=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        vc.append(st["vcycles_last"])
+        rels.append(st["rel_residual"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = case.profile_read()
+    case.profile(False)
+    clk = clocks.stop()
+    launches = case.info()["kernel_launches"] - launches0
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * N * args.steps / (total_ms / 1e3)
+
+    # dominant kernel class and its roofline (algorithmic bytes / mean launch time)
+    flush_ms = 0.0
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    peak, peak_src = peaks()
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    mg_names = [k for k in prof if any(k.startswith(p) for p in ("smooth", "resid", "prolong", "coarse", "norm"))]
+    mg_bytes = sum(prof[k]["bytes"] for k in mg_names)
+    mg_ms = sum(prof[k]["ms"] for k in mg_names)
+    kernel_ms = sum(v["ms"] for v in prof.values())
+
+    # end to end through the C-ABI with host buffers: write state, one step, read state
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(7 * N, dtype=torch.float64, pin_memory=True).numpy()
+        snap = case.read(out=host)
+        vals = {k: v.copy() for k, v in snap.items()}
+        te = 0.0
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            case.write(vals)
+            case.step(1, allow_not_converged=True)
+            got = case.read(out=host)
+            te += time.perf_counter() - t0
+            vals = {k: v.copy() for k, v in got.items()}
+        e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
+               "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = ws * N * args.e2e_steps / float(t.item())
+
+    line = None
+    if rank == 0:
+        line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": label, "cells_per_gpu": N, "precision": args.precision,
+                           "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps"},
+                "vcycles_per_step": statistics.mean(vc), "rel_residual_max": max(rels),
+                "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                             "bytes_per_launch": d["bytes"] / d["launches"],
+                             "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"]},
+                "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
+                           "frac": (mg_bytes / (mg_ms / 1e3) / 1e9) / peak if mg_ms else None,
+                           "ms_per_step": mg_ms / args.steps},
+                "kernel_ms_per_step": kernel_ms / args.steps,
+                "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                                "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
+                            for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+    case.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * fvm.h -- C-ABI of the GB300 k-omega RANS finite-volume step library.
+ *
+ * The library advances cell-centred fields u, v, w, p, T, k, omega on a
+ * uniform structured grid by the time step of "NeuralFVM: Neural-physics-
+ * based Finite Volume Method for Turbulent Flows Using the k-omega Model":
+ *
+ *   1. dt/2 of the semi-implicit destruction of k and omega
+ *      (Section 2.4, Eqs. k_des_step and o_des_step, Algorithm 4);
+ *   2. one forward-Euler step of convection (first-order upwind, Eq.
+ *      upwind_x, Algorithm 2), diffusion (Eq. divergence_theorem) and
+ *      production (Eqs. k_gen, o_gen) for u, v, w, T, k, omega
+ *      (Eqs. ko_mom - ko_temp, Algorithm 3 and Section A.4);
+ *   3. dt/2 of the destruction again (Strang splitting, Section 2.6);
+ *   4. the pressure right-hand side b = -div(u*)/dt (Eq. pc_residual);
+ *   5. multigrid V-cycles on A p = b, A = -Laplacian (Eq. neg_lap_discretize,
+ *      Eq. jacobi_pc, Eqs. restriction / prolongation, Algorithm 1);
+ *   6. the projection u = u* - dt grad p (Section 2.4).
+ * Boundary conditions use one ghost layer (Section 2.5, Eqs. bc_x - bc) and
+ * masks for solid boxes; walls use omega = 6 nu / (beta_i d^2) in the
+ * adjacent cells (Section 2.5); inlet k and omega follow Section 3.2.4.
+ *
+ * Conventions
+ *   - Grid: nx * ny * nz cells, spacing Lx/nx, Ly/ny, Lz/nz; an axis with
+ *     n = 1 is degenerate (2D) and both its faces must be FVM_EMPTY.
+ *   - Field layout everywhere (device and host buffers): one array per
+ *     field, x fastest: index (k * ny + j) * nx + i.
+ *   - Field ids (bit i of a field mask): u 0, v 1, w 2, p 3, T 4, k 5,
+ *     omega 6.
+ *   - Boundary faces: 0..5 = x-, x+, y-, y+, z-, z+.  A vent covers the
+ *     boundary cells [a0, a1) x [b0, b1) of one face, a and b being the
+ *     face's tangential axes in increasing order (x faces: y, z; y faces:
+ *     x, z; z faces: x, y).
+ *   - The library owns all device memory of a case (cudaMalloc at create,
+ *     cudaFree at destroy).  The caller owns every host buffer it passes.
+ *   - Every call returns an fvm_status; on error nothing is written to the
+ *     caller's outputs and fvm_last_error() describes the failure.  No call
+ *     aborts, traps or hangs on bad input; CUDA errors map to FVM_ERR_CUDA.
+ *   - Work is issued on the case's stream (desc.stream, or a stream the
+ *     library creates).  Calls that return data to the host synchronise it.
+ *   - A case is not thread safe; different cases may be used from
+ *     different threads.
+ */
+#ifndef FVM_H
+#define FVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fvm_case fvm_case;          /* opaque, library-owned */
+
+typedef enum {
+    FVM_OK = 0,
+    FVM_ERR_INVALID = -1,        /* bad descriptor or argument */
+    FVM_ERR_OOM = -2,            /* device allocation failed */
+    FVM_ERR_BUDGET = -3,         /* case bytes exceed the caller's budget */
+    FVM_ERR_NOT_CONVERGED = -4,  /* V-cycle cap reached above the tolerance */
+    FVM_ERR_DIVERGED = -5,       /* non-finite residual or time step */
+    FVM_ERR_CUDA = -6            /* a CUDA runtime error */
+} fvm_status;
+
+enum { FVM_WALL = 0, FVM_INLET = 1, FVM_OUTLET = 2, FVM_EMPTY = 3 };
+enum { FVM_ADIABATIC = 0, FVM_FIXED_T = 1, FVM_HEAT_FLUX = 2 };
+enum { FVM_FP64 = 0, FVM_FP32 = 1, FVM_BF16_MIXED = 2 };
+enum { FVM_U = 0, FVM_V = 1, FVM_W = 2, FVM_P = 3, FVM_T = 4, FVM_K = 5, FVM_OMEGA = 6 };
+
+/* Boundary condition of a face or vent (Section 2.5). */
+typedef struct {
+    int32_t kind;            /* FVM_WALL / FVM_INLET / FVM_OUTLET / FVM_EMPTY */
+    int32_t thermal;         /* walls: FVM_ADIABATIC / FVM_FIXED_T / FVM_HEAT_FLUX */
+    double  T_value;         /* wall temperature, or heat flux into the fluid in W/m^2 */
+    double  u_normal;        /* inlet: speed into the domain, m/s */
+    double  intensity;       /* inlet: turbulence intensity I0 (k0 = 1.5 (I0 u0)^2) */
+    double  length_scale;    /* inlet: l0 (omega0 = k0^0.5 / (C_mu l0)) */
+    double  T_in;            /* inlet temperature */
+    double  k_value;         /* inlet: k used instead of the I0 formula when > 0 */
+    double  omega_value;     /* inlet: omega used instead of the l0 formula when > 0 */
+} fvm_patch;
+
+typedef struct {
+    int32_t face, a0, a1, b0, b1, reserved;
+    fvm_patch bc;
+} fvm_vent;
+
+/* Solid box [i0,i1) x [j0,j1) x [k0,k1) with a thermal wall condition. */
+typedef struct {
+    int32_t i0, i1, j0, j1, k0, k1, thermal, reserved;
+    double  T_value;
+} fvm_box;
+
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t precision;               /* FVM_FP64 / FVM_FP32 / FVM_BF16_MIXED */
+    double  Lx, Ly, Lz;              /* m */
+    double  nu, Pr, Prt;             /* kinematic viscosity, Prandtl, turbulent Prandtl */
+    double  sigma_k, sigma_w;        /* turbulent Prandtl numbers of k and omega */
+    double  rho, cp;                 /* for heat-flux walls */
+    double  gravity[3], beta_T, T_ref;
+    int32_t buoyancy;                /* 1: Boussinesq force -g beta_T (T - T_ref) */
+    int32_t dt_adapt;                /* 1: cap dt each step by the explicit stability limit */
+    double  dt;                      /* > 0: fixed dt0; else dt0 = cfl min h / max inlet speed */
+    double  cfl;
+    fvm_patch faces[6];
+    const fvm_vent* vents;  int32_t n_vents;  int32_t reserved0;
+    const fvm_box*  boxes;  int32_t n_boxes;  int32_t reserved1;
+    int32_t mg_levels;               /* 2..12; active axes = 2^(levels-1) * m, m >= 2 */
+    int32_t pre_sweeps, post_sweeps; /* weighted-Jacobi sweeps, each >= 1 */
+    int32_t max_vcycles;             /* cap per solve */
+    int32_t fixed_vcycles;           /* > 0: exactly this many per solve, no test */
+    int32_t reserved2;
+    double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
+    double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
+    uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
+    double  init_perturb;            /* fields start at base * (1 + eps xi), xi in [-1, 1) */
+    double  init_vel[3], init_T;
+    double  init_k, init_omega;      /* <= 0: the first inlet's k0 / omega0 */
+    void*   stream;                  /* cudaStream_t to use, or NULL */
+} fvm_case_desc;
+
+typedef struct {
+    int32_t steps;                   /* steps run by this call */
+    int32_t vcycles_total;           /* V-cycles over those steps */
+    int32_t vcycles_last;            /* V-cycles of the last step */
+    int32_t reserved;
+    double  rel_residual;            /* ||b - A p|| / ||b|| after the last solve */
+    double  dt_last;                 /* dt of the last step */
+    double  sim_time;                /* simulated time since creation */
+} fvm_step_stats;
+
+typedef struct {
+    int64_t cells;
+    int32_t levels, precision;
+    double  dt0, dt;                 /* base and current time step */
+    double  sim_time;
+    int64_t device_bytes;            /* device memory held by the case */
+    int64_t steps;
+    int64_t kernel_launches;         /* kernels launched on the case since creation */
+} fvm_case_info;
+
+/* Per-kernel-class statistics of the profiling hook. */
+typedef struct {
+    char    name[32];                /* kernel class, e.g. "explicit", "smooth_L0" */
+    int64_t launches;
+    double  ms;                      /* summed device time between the bracketing events */
+    double  bytes;                   /* summed algorithmic bytes (each array read or written once) */
+} fvm_kernel_stat;
+
+/* Stages of one step, for fvm_run_stage (in step order). */
+enum {
+    FVM_STAGE_DT = 0,            /* dt = min(dt0, cfl / max rate) (or dt0) */
+    FVM_STAGE_DESTRUCTION = 1,   /* dt/2 of Eqs. k_des_step, o_des_step */
+    FVM_STAGE_EXPLICIT = 2,      /* forward Euler of the remaining terms */
+    FVM_STAGE_RHS = 3,           /* b = -div(u*) / dt */
+    FVM_STAGE_SOLVE = 4,         /* V-cycles on A p = b */
+    FVM_STAGE_PROJECT = 5        /* u = u* - dt grad p */
+};
+
+/* Device bytes a case with this descriptor would allocate (0 if invalid).
+   Used for admission against a memory budget. */
+size_t fvm_case_bytes(const fvm_case_desc* desc);
+
+/* Validate desc, allocate the case's device memory, build boundary tables,
+   multigrid levels and the coarsest-level inverse, and set the seeded
+   initial state (p = 0).  *out is set only on FVM_OK. */
+fvm_status fvm_create_case(const fvm_case_desc* desc, fvm_case** out);
+
+/* Free everything the case holds (after finishing its queued work). */
+void fvm_destroy_case(fvm_case* c);
+
+/* Advance nsteps time steps.  Synchronises the case's stream; out (may be
+   NULL) receives statistics.  Returns FVM_ERR_NOT_CONVERGED if a solve hit
+   max_vcycles above mg_rel_tol (the step is still taken), FVM_ERR_DIVERGED
+   on a non-finite residual or time step. */
+fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out);
+
+/* Run one stage of the step (FVM_STAGE_*), for verification. */
+fvm_status fvm_run_stage(fvm_case* c, int stage);
+
+/* Run ncycles V-cycles on the case's current b and p (no convergence test);
+   *rel_residual (may be NULL) gets ||b - A p|| / ||b|| afterwards. */
+fvm_status fvm_vcycle(fvm_case* c, int ncycles, double* rel_residual);
+
+/* Copy the fields in field_mask, converted to double, into host_out: the
+   selected fields in id order, each nx*ny*nz values.  n = capacity of
+   host_out in doubles.  Synchronises. */
+fvm_status fvm_read_fields(fvm_case* c, unsigned field_mask, double* host_out, size_t n);
+
+/* Overwrite the fields in field_mask from host_in (same layout as
+   fvm_read_fields); values are rounded to the case's storage precision.
+   Synchronises. */
+fvm_status fvm_write_fields(fvm_case* c, unsigned field_mask, const double* host_in, size_t n);
+
+/* Set the Poisson right-hand side b (nx*ny*nz doubles, host). */
+fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n);
+
+/* Read b (nx*ny*nz doubles) into host memory.  Synchronises. */
+fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
+
+/* Advance every case of the array by nsteps; stats (may be NULL) is an
+   array of n entries.  Cases keep their own streams; the call returns when
+   all are done. */
+fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_stats* stats);
+
+fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
+
+/* Profiling hook.  While enabled, every kernel the case launches is
+   bracketed by a pair of CUDA events on the case's stream, and its class,
+   device time and algorithmic bytes are tallied.  Enabling or disabling
+   clears the tallies. */
+fvm_status fvm_profile_enable(fvm_case* c, int enable);
+
+/* Copy up to cap per-class tallies into out (n_out = classes seen), and
+   clear them.  Synchronises the case's stream. */
+fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_out);
+
+/* sizeof of the public structs, for binding checks: out[0..6] = fvm_patch,
+   fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
+   fvm_kernel_stat.  Needs
+   no GPU. */
+void fvm_struct_sizes(size_t out[7]);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fvm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -104,9 +104,14 @@ class Geometry:
                 self.inlet_kw[pid] = (k0, om0)
 
     def levels(self, n):
+        """n grid levels; every active axis must keep at least 2 cells."""
         lv = [self.level0]
         for _ in range(n - 1):
             lv.append(lv[-1].coarsen())
+        for a in range(3):
+            if self.shape[a] > 1:
+                assert lv[-1].shape[a] >= 2 and lv[-1].shape[a] * 2 ** (n - 1) == self.shape[a], \
+                    "active axes must halve evenly down to >= 2 cells"
         return lv
 
     # ---------------------------------------------------------------- ghosts

@@ -1,0 +1,294 @@
+"""ctypes binding of libfvm.so (the C-ABI declared in include/fvm.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  The library must have been built (``build.build()``); if it
+is missing this module raises instead of falling back to anything else.
+
+Field arrays cross the boundary as float64 host buffers in the library's
+layout (x fastest); this module returns and accepts numpy arrays shaped
+(nx, ny, nz), the transposed view of that buffer.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import cases
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfvm.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_BUDGET, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
+STAGE_DT, STAGE_DESTRUCTION, STAGE_EXPLICIT, STAGE_RHS, STAGE_SOLVE, STAGE_PROJECT = range(6)
+
+
+class FvmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fvm status {status}: {msg}")
+        self.status = status
+
+
+class Patch(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("thermal", ct.c_int32), ("T_value", ct.c_double),
+                ("u_normal", ct.c_double), ("intensity", ct.c_double), ("length_scale", ct.c_double),
+                ("T_in", ct.c_double), ("k_value", ct.c_double), ("omega_value", ct.c_double)]
+
+
+class Vent(ct.Structure):
+    _fields_ = [("face", ct.c_int32), ("a0", ct.c_int32), ("a1", ct.c_int32), ("b0", ct.c_int32),
+                ("b1", ct.c_int32), ("reserved", ct.c_int32), ("bc", Patch)]
+
+
+class Box(ct.Structure):
+    _fields_ = [("i0", ct.c_int32), ("i1", ct.c_int32), ("j0", ct.c_int32), ("j1", ct.c_int32),
+                ("k0", ct.c_int32), ("k1", ct.c_int32), ("thermal", ct.c_int32), ("reserved", ct.c_int32),
+                ("T_value", ct.c_double)]
+
+
+class CaseDesc(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("precision", ct.c_int32),
+                ("Lx", ct.c_double), ("Ly", ct.c_double), ("Lz", ct.c_double),
+                ("nu", ct.c_double), ("Pr", ct.c_double), ("Prt", ct.c_double),
+                ("sigma_k", ct.c_double), ("sigma_w", ct.c_double), ("rho", ct.c_double), ("cp", ct.c_double),
+                ("gravity", ct.c_double * 3), ("beta_T", ct.c_double), ("T_ref", ct.c_double),
+                ("buoyancy", ct.c_int32), ("dt_adapt", ct.c_int32), ("dt", ct.c_double), ("cfl", ct.c_double),
+                ("faces", Patch * 6),
+                ("vents", ct.POINTER(Vent)), ("n_vents", ct.c_int32), ("reserved0", ct.c_int32),
+                ("boxes", ct.POINTER(Box)), ("n_boxes", ct.c_int32), ("reserved1", ct.c_int32),
+                ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
+                ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("reserved2", ct.c_int32),
+                ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
+                ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
+                ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
+
+
+class StepStats(ct.Structure):
+    _fields_ = [("steps", ct.c_int32), ("vcycles_total", ct.c_int32), ("vcycles_last", ct.c_int32),
+                ("reserved", ct.c_int32), ("rel_residual", ct.c_double), ("dt_last", ct.c_double),
+                ("sim_time", ct.c_double)]
+
+
+class CaseInfo(ct.Structure):
+    _fields_ = [("cells", ct.c_int64), ("levels", ct.c_int32), ("precision", ct.c_int32),
+                ("dt0", ct.c_double), ("dt", ct.c_double), ("sim_time", ct.c_double),
+                ("device_bytes", ct.c_int64), ("steps", ct.c_int64), ("kernel_launches", ct.c_int64)]
+
+
+class KernelStat(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("ms", ct.c_double), ("bytes", ct.c_double)]
+
+
+EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
+           "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
+           "fvm_step_batch", "fvm_case_get_info", "fvm_profile_enable", "fvm_profile_read", "fvm_struct_sizes",
+           "fvm_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load libfvm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2603_21869_gb300.build.build()")
+    L = ct.CDLL(LIB_PATH)
+    CP = ct.c_void_p
+    L.fvm_case_bytes.argtypes = [ct.POINTER(CaseDesc)]
+    L.fvm_case_bytes.restype = ct.c_size_t
+    L.fvm_create_case.argtypes = [ct.POINTER(CaseDesc), ct.POINTER(CP)]
+    L.fvm_destroy_case.argtypes = [CP]
+    L.fvm_destroy_case.restype = None
+    L.fvm_step.argtypes = [CP, ct.c_int, ct.POINTER(StepStats)]
+    L.fvm_run_stage.argtypes = [CP, ct.c_int]
+    L.fvm_vcycle.argtypes = [CP, ct.c_int, ct.POINTER(ct.c_double)]
+    L.fvm_read_fields.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_write_fields.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_set_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_read_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_step_batch.argtypes = [ct.POINTER(CP), ct.c_int, ct.c_int, ct.POINTER(StepStats)]
+    L.fvm_case_get_info.argtypes = [CP, ct.POINTER(CaseInfo)]
+    L.fvm_profile_enable.argtypes = [CP, ct.c_int]
+    L.fvm_profile_read.argtypes = [CP, ct.POINTER(KernelStat), ct.c_int, ct.POINTER(ct.c_int)]
+    L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
+    L.fvm_struct_sizes.restype = None
+    L.fvm_last_error.restype = ct.c_char_p
+    for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
+                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
+                 "fvm_case_get_info", "fvm_profile_enable", "fvm_profile_read"]:
+        getattr(L, name).restype = ct.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().fvm_last_error().decode()
+
+
+def _check(status, allow=()):
+    if status != OK and status not in allow:
+        raise FvmError(status, last_error())
+    return status
+
+
+def _patch(p: cases.Patch) -> Patch:
+    return Patch(p.kind, p.thermal, p.T_value, p.u_normal, p.intensity, p.length_scale, p.T_in,
+                 p.k_value, p.omega_value)
+
+
+class _Desc:
+    """A CaseDesc plus the vent and box arrays it points to (kept alive together)."""
+
+    def __init__(self, spec: cases.CaseSpec, stream=None):
+        self.vents = (Vent * max(1, len(spec.vents)))()
+        for n, v in enumerate(spec.vents):
+            self.vents[n] = Vent(v.face, v.a0, v.a1, v.b0, v.b1, 0, _patch(v.bc))
+        self.boxes = (Box * max(1, len(spec.boxes)))()
+        for n, b in enumerate(spec.boxes):
+            self.boxes[n] = Box(b.i0, b.i1, b.j0, b.j1, b.k0, b.k1, b.thermal, 0, b.T_value)
+        d = CaseDesc()
+        d.nx, d.ny, d.nz, d.precision = spec.nx, spec.ny, spec.nz, spec.precision
+        d.Lx, d.Ly, d.Lz = spec.Lx, spec.Ly, spec.Lz
+        d.nu, d.Pr, d.Prt, d.sigma_k, d.sigma_w = spec.nu, spec.Pr, spec.Prt, spec.sigma_k, spec.sigma_w
+        d.rho, d.cp = spec.rho, spec.cp
+        d.gravity[:] = list(spec.gravity)
+        d.beta_T, d.T_ref, d.buoyancy, d.dt_adapt = spec.beta_T, spec.T_ref, spec.buoyancy, spec.dt_adapt
+        d.dt, d.cfl = spec.dt, spec.cfl
+        for f in range(6):
+            d.faces[f] = _patch(spec.faces[f])
+        d.vents = ct.cast(self.vents, ct.POINTER(Vent))
+        d.n_vents = len(spec.vents)
+        d.boxes = ct.cast(self.boxes, ct.POINTER(Box))
+        d.n_boxes = len(spec.boxes)
+        d.mg_levels, d.pre_sweeps, d.post_sweeps = spec.mg_levels, spec.pre_sweeps, spec.post_sweeps
+        d.max_vcycles, d.fixed_vcycles = spec.max_vcycles, spec.fixed_vcycles
+        d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
+        d.seed = spec.seed & ((1 << 64) - 1)
+        d.init_perturb = spec.init_perturb
+        d.init_vel[:] = list(spec.init_vel)
+        d.init_T, d.init_k, d.init_omega = spec.init_T, spec.init_k, spec.init_omega
+        d.stream = stream
+        self.desc = d
+
+
+def case_bytes(spec: cases.CaseSpec) -> int:
+    """Device bytes fvm_create_case would allocate for spec (0 if invalid)."""
+    d = _Desc(spec)
+    return int(lib().fvm_case_bytes(ct.byref(d.desc)))
+
+
+def struct_sizes():
+    out = (ct.c_size_t * 7)()
+    lib().fvm_struct_sizes(out)
+    return list(out)
+
+
+def _mask(fields):
+    m = 0
+    for f in fields:
+        m |= 1 << cases.FIELD_INDEX[f]
+    return m
+
+
+class Case:
+    """One case held by the library (device memory owned by libfvm)."""
+
+    def __init__(self, spec: cases.CaseSpec, stream=None):
+        self.spec = spec
+        self.shape = (spec.nx, spec.ny, spec.nz)
+        self.N = spec.nx * spec.ny * spec.nz
+        d = _Desc(spec, stream)
+        h = ct.c_void_p()
+        _check(lib().fvm_create_case(ct.byref(d.desc), ct.byref(h)))
+        self._h = h
+        self._desc = d
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().fvm_destroy_case(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n=1, allow_not_converged=False):
+        st = StepStats()
+        status = lib().fvm_step(self._h, n, ct.byref(st))
+        _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return {"steps": st.steps, "vcycles_total": st.vcycles_total, "vcycles_last": st.vcycles_last,
+                "rel_residual": st.rel_residual, "dt_last": st.dt_last, "sim_time": st.sim_time,
+                "status": status}
+
+    def run_stage(self, stage):
+        _check(lib().fvm_run_stage(self._h, stage))
+
+    def vcycle(self, n=1):
+        rel = ct.c_double()
+        _check(lib().fvm_vcycle(self._h, n, ct.byref(rel)))
+        return rel.value
+
+    def read(self, fields=cases.FIELDS, out=None):
+        fields = [f for f in cases.FIELDS if f in fields]
+        buf = out if out is not None else np.empty(len(fields) * self.N, dtype=np.float64)
+        _check(lib().fvm_read_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        nx, ny, nz = self.shape
+        return {f: buf[i * self.N:(i + 1) * self.N].reshape(nz, ny, nx).transpose(2, 1, 0)
+                for i, f in enumerate(fields)}
+
+    def write(self, values: dict):
+        fields = [f for f in cases.FIELDS if f in values]
+        buf = np.empty(len(fields) * self.N, dtype=np.float64)
+        for i, f in enumerate(fields):
+            buf[i * self.N:(i + 1) * self.N] = np.asarray(values[f], dtype=np.float64).transpose(2, 1, 0).ravel()
+        _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+
+    def set_rhs(self, b):
+        buf = np.ascontiguousarray(np.asarray(b, dtype=np.float64).transpose(2, 1, 0).ravel())
+        _check(lib().fvm_set_poisson_rhs(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+
+    def read_rhs(self):
+        buf = np.empty(self.N, dtype=np.float64)
+        _check(lib().fvm_read_poisson_rhs(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        nx, ny, nz = self.shape
+        return buf.reshape(nz, ny, nx).transpose(2, 1, 0)
+
+    def profile(self, enable=True):
+        _check(lib().fvm_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        cap = 256
+        arr = (KernelStat * cap)()
+        n = ct.c_int()
+        _check(lib().fvm_profile_read(self._h, arr, cap, ct.byref(n)))
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+                for i in range(min(n.value, cap))}
+
+    def info(self):
+        inf = CaseInfo()
+        _check(lib().fvm_case_get_info(self._h, ct.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in CaseInfo._fields_}
+
+
+def step_batch(cs, nsteps, allow_not_converged=False):
+    arr = (ct.c_void_p * len(cs))(*[c.handle.value for c in cs])
+    stats = (StepStats * len(cs))()
+    status = lib().fvm_step_batch(arr, len(cs), nsteps, stats)
+    _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return [{"vcycles_total": s.vcycles_total, "rel_residual": s.rel_residual, "dt_last": s.dt_last}
+            for s in stats]

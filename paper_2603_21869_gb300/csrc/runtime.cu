@@ -1,0 +1,1002 @@
+// Host runtime of the k-omega finite-volume library: descriptor validation,
+// boundary and obstacle tables, the multigrid level hierarchy, the dense
+// coarsest-level inverse, device memory, and the order of kernels in one
+// time step (Section 2.6: dt/2 destruction, explicit stage, dt/2
+// destruction, pressure solve, projection).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fvm_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+fvm_status fail(fvm_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(FVM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr double kCmu = 0.09;
+constexpr double kBetaI = 0.072;
+
+size_t elem_size(int prec) { return prec == FVM_FP64 ? 8 : (prec == FVM_FP32 ? 4 : 2); }
+
+struct HostLevel {
+    int n[3];
+    int active[3];
+    double h[3];
+    std::vector<uint8_t> solid;
+    std::vector<uint8_t> dir[6];
+    int64_t N() const { return (int64_t)n[0] * n[1] * n[2]; }
+};
+
+int face_cells(const int* n, int face) {
+    const int a = face / 2;
+    int m = 1;
+    for (int b = 0; b < 3; ++b)
+        if (b != a) m *= n[b];
+    return m;
+}
+
+void face_dims(const int* n, int face, int& na, int& nb) {
+    const int a = face / 2;
+    const int t0 = a == 0 ? 1 : 0;
+    const int t1 = a == 2 ? 1 : 2;
+    na = n[t0];
+    nb = n[t1];
+}
+
+void inlet_kw(const fvm_patch& p, double& k0, double& om0) {
+    k0 = 0.0;
+    om0 = 0.0;
+    if (p.intensity > 0.0 && p.length_scale > 0.0) {
+        // Section 3.2.4: k0 = 1.5 (I0 u0)^2, eps0 = k0^1.5 / l0, omega0 = eps0 / (C_mu k0)
+        k0 = 1.5 * (p.intensity * p.u_normal) * (p.intensity * p.u_normal);
+        const double eps0 = std::pow(k0, 1.5) / p.length_scale;
+        om0 = k0 > 0.0 ? eps0 / (kCmu * k0) : 0.0;
+    }
+    if (p.k_value > 0.0) k0 = p.k_value;
+    if (p.omega_value > 0.0) om0 = p.omega_value;
+}
+
+HostLevel coarsen(const HostLevel& f) {
+    HostLevel c;
+    int fac[3];
+    for (int a = 0; a < 3; ++a) {
+        fac[a] = f.active[a] ? 2 : 1;
+        c.n[a] = f.n[a] / fac[a];
+        c.h[a] = f.h[a] * fac[a];
+        c.active[a] = f.active[a];
+    }
+    c.solid.assign(c.N(), 1);
+    for (int K = 0; K < c.n[2]; ++K)
+        for (int J = 0; J < c.n[1]; ++J)
+            for (int I = 0; I < c.n[0]; ++I) {
+                uint8_t all = 1;
+                for (int dz = 0; dz < fac[2]; ++dz)
+                    for (int dy = 0; dy < fac[1]; ++dy)
+                        for (int dx = 0; dx < fac[0]; ++dx)
+                            all &= f.solid[cell_index(I * fac[0] + dx, J * fac[1] + dy, K * fac[2] + dz, f.n[0],
+                                                      f.n[1])] ? 1 : 0;
+                c.solid[cell_index(I, J, K, c.n[0], c.n[1])] = all;
+            }
+    for (int face = 0; face < 6; ++face) {
+        const int a = face / 2;
+        const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
+        int cna, cnb, fna, fnb;
+        face_dims(c.n, face, cna, cnb);
+        face_dims(f.n, face, fna, fnb);
+        c.dir[face].assign((size_t)cna * cnb, 0);
+        for (int B = 0; B < cnb; ++B)
+            for (int A = 0; A < cna; ++A) {
+                uint8_t any = 0;
+                for (int db = 0; db < fac[t1]; ++db)
+                    for (int da = 0; da < fac[t0]; ++da)
+                        any |= f.dir[face][(size_t)(A * fac[t0] + da) + (size_t)fna * (B * fac[t1] + db)];
+                c.dir[face][(size_t)A + (size_t)cna * B] = any;
+            }
+    }
+    return c;
+}
+
+// Dense A of the coarsest level (rows/cols of solid cells are the identity),
+// inverted by Gauss-Jordan elimination with partial pivoting.
+bool coarse_inverse(const HostLevel& L, std::vector<double>& inv) {
+    const int64_t n = L.N();
+    std::vector<double> M((size_t)(n * n), 0.0);
+    for (int k = 0; k < L.n[2]; ++k)
+        for (int j = 0; j < L.n[1]; ++j)
+            for (int i = 0; i < L.n[0]; ++i) {
+                const int64_t P = cell_index(i, j, k, L.n[0], L.n[1]);
+                if (L.solid[P]) {
+                    M[P * n + P] = 1.0;
+                    continue;
+                }
+                const int f[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a) {
+                    if (!L.active[a]) continue;
+                    const double ih2 = 1.0 / (L.h[a] * L.h[a]);
+                    for (int side = -1; side <= 1; side += 2) {
+                        int q[3] = {f[0], f[1], f[2]};
+                        q[a] += side;
+                        if (q[a] < 0 || q[a] >= L.n[a]) {
+                            const int face = 2 * a + (side > 0 ? 1 : 0);
+                            if (L.dir[face][face_index(a, i, j, k, L.n)]) M[P * n + P] += 2.0 * ih2;
+                            continue;
+                        }
+                        const int64_t Q = cell_index(q[0], q[1], q[2], L.n[0], L.n[1]);
+                        if (L.solid[Q]) continue;
+                        M[P * n + P] += ih2;
+                        M[P * n + Q] -= ih2;
+                    }
+                }
+            }
+    inv.assign((size_t)(n * n), 0.0);
+    for (int64_t r = 0; r < n; ++r) inv[r * n + r] = 1.0;
+    double scale = 0.0;
+    for (double x : M) scale = std::max(scale, std::fabs(x));
+    for (int64_t col = 0; col < n; ++col) {
+        int64_t piv = col;
+        for (int64_t r = col + 1; r < n; ++r)
+            if (std::fabs(M[r * n + col]) > std::fabs(M[piv * n + col])) piv = r;
+        if (std::fabs(M[piv * n + col]) <= 1e-12 * scale) return false;
+        if (piv != col)
+            for (int64_t x = 0; x < n; ++x) {
+                std::swap(M[piv * n + x], M[col * n + x]);
+                std::swap(inv[piv * n + x], inv[col * n + x]);
+            }
+        const double d = 1.0 / M[col * n + col];
+        for (int64_t x = 0; x < n; ++x) {
+            M[col * n + x] *= d;
+            inv[col * n + x] *= d;
+        }
+        for (int64_t r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double fct = M[r * n + col];
+            if (fct == 0.0) continue;
+            for (int64_t x = 0; x < n; ++x) {
+                M[r * n + x] -= fct * M[col * n + x];
+                inv[r * n + x] -= fct * inv[col * n + x];
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+struct DevLevel {
+    LevelDev dev;
+    void* e[2] = {nullptr, nullptr};
+    void* r = nullptr;
+};
+
+struct fvm_case {
+    fvm_case_desc desc;
+    std::vector<fvm_vent> vents;
+    std::vector<fvm_box> boxes;
+    int prec = FVM_FP64;    // storage of u, v, w, T, k, omega and b
+    int inner = FVM_FP64;   // r, e on every multigrid level
+    CaseDev cd;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* cur[6] = {};
+    void* nxt[6] = {};
+    double* p = nullptr;
+    void* b = nullptr;
+    double* dt_state = nullptr;
+    double* partials = nullptr;
+    double* norms = nullptr;
+    double* h_norms = nullptr;
+    double* h_dt = nullptr;
+    double* staging = nullptr;
+    double* Ainv = nullptr;
+    std::vector<DevLevel> levels;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int64_t steps = 0;
+    double dt0 = 0.0;
+    int nblocks0 = 0;
+    // launch accounting and the profiling hook
+    int64_t launches = 0;
+    bool prof = false;
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> cls_names;
+};
+
+namespace {
+
+struct Plan {
+    fvm_case_desc d;
+    int prec, inner;
+    double dt0;
+    double base[6];
+    std::vector<HostLevel> levels;
+    std::vector<uint8_t> tag;
+    std::vector<uint8_t> face_patch[6];
+    std::vector<fvm_patch> patches;
+    int64_t bytes;
+};
+
+fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
+    if (!d) return fail(FVM_ERR_INVALID, "null descriptor");
+    pl.d = *d;
+    const int n[3] = {d->nx, d->ny, d->nz};
+    const double Ls[3] = {d->Lx, d->Ly, d->Lz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1) return fail(FVM_ERR_INVALID, "grid dimensions must be >= 1");
+        if (!(Ls[a] > 0.0)) return fail(FVM_ERR_INVALID, "domain lengths must be > 0");
+        const bool e0 = d->faces[2 * a].kind == FVM_EMPTY, e1 = d->faces[2 * a + 1].kind == FVM_EMPTY;
+        if ((n[a] == 1) != e0 || (n[a] == 1) != e1)
+            return fail(FVM_ERR_INVALID, "an axis with one cell needs FVM_EMPTY on both faces, and only it");
+    }
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    if (N > (int64_t)1 << 31) return fail(FVM_ERR_INVALID, "more than 2^31 cells");
+    if (d->precision < FVM_FP64 || d->precision > FVM_BF16_MIXED) return fail(FVM_ERR_INVALID, "bad precision");
+    if (!(d->nu > 0.0) || !(d->Pr > 0.0) || !(d->Prt > 0.0) || !(d->sigma_k > 0.0) || !(d->sigma_w > 0.0))
+        return fail(FVM_ERR_INVALID, "nu, Pr, Prt, sigma_k, sigma_w must be > 0");
+    if (d->mg_levels < 2 || d->mg_levels > FVM_MAX_LEVELS) return fail(FVM_ERR_INVALID, "mg_levels must be 2..12");
+    if (d->pre_sweeps < 1 || d->post_sweeps < 1 || d->pre_sweeps > 64 || d->post_sweeps > 64)
+        return fail(FVM_ERR_INVALID, "pre_sweeps and post_sweeps must be 1..64");
+    if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
+        return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
+    if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
+    if (d->n_vents < 0 || d->n_vents > FVM_MAX_PATCHES - 6) return fail(FVM_ERR_INVALID, "at most 10 vents");
+    if (d->n_boxes < 0 || d->n_boxes > FVM_MAX_BOXES) return fail(FVM_ERR_INVALID, "at most 32 boxes");
+    if ((d->n_vents > 0 && !d->vents) || (d->n_boxes > 0 && !d->boxes))
+        return fail(FVM_ERR_INVALID, "null vent or box array");
+    const int div = 1 << (d->mg_levels - 1);
+    int64_t Nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] == 1) continue;
+        if (n[a] % div || n[a] / div < 2)
+            return fail(FVM_ERR_INVALID,
+                        "active grid dimensions must be divisible by 2^(mg_levels-1) with at least 2 coarsest cells");
+        Nc *= n[a] / div;
+    }
+    if (Nc > FVM_MAX_COARSE) return fail(FVM_ERR_INVALID, "coarsest level above 1024 cells: add multigrid levels");
+
+    pl.patches.assign(d->faces, d->faces + 6);
+    for (int v = 0; v < d->n_vents; ++v) {
+        const fvm_vent& ve = d->vents[v];
+        if (ve.face < 0 || ve.face > 5) return fail(FVM_ERR_INVALID, "vent face must be 0..5");
+        int na, nb;
+        face_dims(n, ve.face, na, nb);
+        if (ve.a0 < 0 || ve.a1 > na || ve.a0 >= ve.a1 || ve.b0 < 0 || ve.b1 > nb || ve.b0 >= ve.b1)
+            return fail(FVM_ERR_INVALID, "vent rectangle outside its face");
+        if (ve.bc.kind == FVM_EMPTY || d->faces[ve.face].kind == FVM_EMPTY)
+            return fail(FVM_ERR_INVALID, "vents cannot be or sit on FVM_EMPTY faces");
+        pl.patches.push_back(ve.bc);
+    }
+    for (const fvm_patch& p : pl.patches) {
+        if (p.kind < FVM_WALL || p.kind > FVM_EMPTY) return fail(FVM_ERR_INVALID, "bad patch kind");
+        if (p.kind == FVM_WALL && p.thermal == FVM_HEAT_FLUX && !(d->rho > 0.0 && d->cp > 0.0))
+            return fail(FVM_ERR_INVALID, "heat-flux walls need rho, cp > 0");
+    }
+    for (int bi = 0; bi < d->n_boxes; ++bi) {
+        const fvm_box& bx = d->boxes[bi];
+        if (bx.i0 < 0 || bx.i1 > n[0] || bx.i0 >= bx.i1 || bx.j0 < 0 || bx.j1 > n[1] || bx.j0 >= bx.j1 ||
+            bx.k0 < 0 || bx.k1 > n[2] || bx.k0 >= bx.k1)
+            return fail(FVM_ERR_INVALID, "box outside the grid");
+        if (bx.thermal == FVM_HEAT_FLUX && !(d->rho > 0.0 && d->cp > 0.0))
+            return fail(FVM_ERR_INVALID, "heat-flux boxes need rho, cp > 0");
+    }
+    // tables
+    pl.tag.assign(N, 0);
+    for (int bi = 0; bi < d->n_boxes; ++bi) {
+        const fvm_box& bx = d->boxes[bi];
+        for (int k = bx.k0; k < bx.k1; ++k)
+            for (int j = bx.j0; j < bx.j1; ++j)
+                for (int i = bx.i0; i < bx.i1; ++i) pl.tag[cell_index(i, j, k, n[0], n[1])] = (uint8_t)(bi + 1);
+    }
+    for (int f = 0; f < 6; ++f) pl.face_patch[f].assign(face_cells(n, f), (uint8_t)f);
+    for (int v = 0; v < d->n_vents; ++v) {
+        const fvm_vent& ve = d->vents[v];
+        int na, nb;
+        face_dims(n, ve.face, na, nb);
+        for (int bb = ve.b0; bb < ve.b1; ++bb)
+            for (int aa = ve.a0; aa < ve.a1; ++aa) pl.face_patch[ve.face][(size_t)aa + (size_t)na * bb] = (uint8_t)(6 + v);
+    }
+    // level 0 and coarser levels
+    HostLevel L0;
+    bool any_dir = false;
+    for (int a = 0; a < 3; ++a) {
+        L0.n[a] = n[a];
+        L0.active[a] = n[a] > 1;
+        L0.h[a] = Ls[a] / n[a];
+    }
+    L0.solid.resize(N);
+    for (int64_t c = 0; c < N; ++c) L0.solid[c] = pl.tag[c] ? 1 : 0;
+    for (int f = 0; f < 6; ++f) {
+        L0.dir[f].resize(pl.face_patch[f].size());
+        for (size_t x = 0; x < L0.dir[f].size(); ++x) {
+            L0.dir[f][x] = pl.patches[pl.face_patch[f][x]].kind == FVM_OUTLET ? 1 : 0;
+            any_dir |= L0.dir[f][x] != 0;
+        }
+    }
+    if (!any_dir) return fail(FVM_ERR_INVALID, "no outlet: the pressure problem would be singular");
+    pl.levels.clear();
+    pl.levels.push_back(L0);
+    for (int l = 1; l < d->mg_levels; ++l) pl.levels.push_back(coarsen(pl.levels.back()));
+    // time step
+    double hmin = 1e300;
+    for (int a = 0; a < 3; ++a)
+        if (n[a] > 1) hmin = std::min(hmin, L0.h[a]);
+    if (d->dt > 0.0) pl.dt0 = d->dt;
+    else {
+        if (!(d->cfl > 0.0)) return fail(FVM_ERR_INVALID, "need dt > 0 or cfl > 0");
+        double U = 0.0;
+        bool have = false;
+        for (const fvm_patch& p : pl.patches)
+            if (p.kind == FVM_INLET) {
+                U = have ? std::max(U, p.u_normal) : p.u_normal;
+                have = true;
+            }
+        if (!have)
+            for (int a = 0; a < 3; ++a) U = std::max(U, std::fabs(d->init_vel[a]));
+        if (U <= 0.0) U = 1.0;
+        pl.dt0 = d->cfl * hmin / U;
+    }
+    // initial state base values
+    double k0 = d->init_k, om0 = d->init_omega;
+    if (k0 <= 0.0 || om0 <= 0.0) {
+        bool found = false;
+        for (const fvm_patch& p : pl.patches)
+            if (p.kind == FVM_INLET) {
+                double ik, iw;
+                inlet_kw(p, ik, iw);
+                if (k0 <= 0.0) k0 = ik;
+                if (om0 <= 0.0) om0 = iw;
+                found = true;
+                break;
+            }
+        if (!found) return fail(FVM_ERR_INVALID, "init_k / init_omega <= 0 and no inlet to take them from");
+    }
+    pl.base[0] = d->init_vel[0];
+    pl.base[1] = d->init_vel[1];
+    pl.base[2] = d->init_vel[2];
+    pl.base[3] = d->init_T;
+    pl.base[4] = k0;
+    pl.base[5] = om0;
+    pl.prec = d->precision == FVM_FP64 ? FVM_FP64 : FVM_FP32;
+    pl.inner = d->precision == FVM_FP64 ? FVM_FP64 : (d->precision == FVM_FP32 ? FVM_FP32 : FVM_BF16_MIXED);
+    // bytes
+    const size_t s = elem_size(pl.prec);
+    const size_t si = elem_size(pl.inner);
+    int64_t bytes = 0;
+    bytes += (int64_t)12 * N * s;             // state, two copies of six fields
+    bytes += N * 8 + N * s + N;               // p (FP64), b, tag
+    bytes += N * 8;                           // staging
+    for (int f = 0; f < 6; ++f) bytes += face_cells(n, f);
+    for (size_t l = 0; l < pl.levels.size(); ++l) {
+        const int64_t NL = pl.levels[l].N();
+        bytes += 3 * NL * si + (l ? NL : 0);
+        for (int f = 0; f < 6; ++f) bytes += l ? (int64_t)pl.levels[l].dir[f].size() : 0;
+    }
+    const int64_t nc = pl.levels.back().N();
+    bytes += nc * nc * 8;
+    bytes += (int64_t)(2 * resid0_blocks(N) + 16) * 8;
+    pl.bytes = bytes;
+    return FVM_OK;
+}
+
+void prof_clear(fvm_case* c);
+
+void free_case(fvm_case* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    prof_clear(c);
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_norms) cudaFreeHost(c->h_norms);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+fvm_status dalloc(fvm_case* c, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FVM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    c->bytes += (int64_t)bytes;
+    return FVM_OK;
+}
+
+#define ST_TRY(expr)                     \
+    do {                                 \
+        fvm_status s_ = (expr);          \
+        if (s_ != FVM_OK) return s_;     \
+    } while (0)
+
+StatePtrs ptrs(void* const* f) {
+    StatePtrs s;
+    for (int i = 0; i < 6; ++i) s.f[i] = f[i];
+    return s;
+}
+
+// ------------------------------------------------------------------ profiling
+cudaEvent_t take_event(fvm_case* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+int prof_begin(fvm_case* c, const std::string& name, double bytes) {
+    if (!c->prof) return -1;
+    int cls = -1;
+    for (size_t i = 0; i < c->cls_names.size(); ++i)
+        if (c->cls_names[i] == name) cls = (int)i;
+    if (cls < 0) {
+        cls = (int)c->cls_names.size();
+        c->cls_names.push_back(name);
+    }
+    fvm_case::ProfRec r{cls, take_event(c), take_event(c), bytes};
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, c->stream);
+    c->recs.push_back(r);
+    return (int)c->recs.size() - 1;
+}
+
+void prof_end(fvm_case* c, int idx) {
+    if (idx >= 0) cudaEventRecord(c->recs[idx].b, c->stream);
+}
+
+void prof_clear(fvm_case* c) {
+    for (auto& r : c->recs) {
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    c->cls_names.clear();
+}
+
+// Launch `expr` (which issues nk kernels), counting it and bracketing it with
+// profiling events when the hook is on.  `bytes` = algorithmic bytes.
+#define KLAUNCH(name, bytes, nk, expr)                  \
+    do {                                                \
+        const int pi_ = prof_begin(c, (name), (bytes)); \
+        CUDA_TRY(expr);                                 \
+        prof_end(c, pi_);                               \
+        c->launches += (nk);                            \
+    } while (0)
+
+std::string lvl_name(const char* base, size_t l) { return std::string(base) + "_L" + std::to_string(l); }
+
+// ------------------------------------------------------------------ solve
+// One V-cycle of the correction equation on levels l.. with r on level l;
+// returns the index of the e buffer holding the level's correction.  On
+// level 0 the final post-smoothing sweep adds the correction to p instead.
+fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
+    DevLevel& L = c->levels[l];
+    cudaStream_t s = c->stream;
+    const double N = (double)L.dev.N;
+    const double si = (double)elem_size(c->inner);
+    if (l + 1 == c->levels.size()) {
+        KLAUNCH("coarse_solve", N * N * 8 + 2 * N * si, 1,
+                launch_coarse_solve(c->inner, L.dev, c->Ainv, L.r, L.e[0], s));
+        out_idx = 0;
+        return FVM_OK;
+    }
+    DevLevel& Lc = c->levels[l + 1];
+    const double Nc = (double)Lc.dev.N;
+    int cur = 0;
+    KLAUNCH(lvl_name("smooth_first", l), 2 * N * si + N, 1, launch_smooth_first(c->inner, L.dev, L.r, L.e[0], s));
+    for (int k = 1; k < c->desc.pre_sweeps; ++k) {
+        KLAUNCH(lvl_name("smooth", l), 3 * N * si + N, 1,
+                launch_smooth(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], s));
+        cur ^= 1;
+    }
+    KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + N, 1,
+            launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, s));
+    int ci = 0;
+    ST_TRY(cycle(c, l + 1, ci));
+    KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + N, 1,
+            launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], s));
+    for (int k = 0; k < c->desc.post_sweeps; ++k) {
+        if (l == 0 && k == c->desc.post_sweeps - 1) {
+            KLAUNCH("smooth_to_p_L0", 2 * N * si + 16 * N + N, 1,
+                    launch_smooth_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, s));
+        } else {
+            KLAUNCH(lvl_name("smooth", l), 3 * N * si + N, 1,
+                    launch_smooth(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], s));
+            cur ^= 1;
+        }
+    }
+    out_idx = cur;
+    return FVM_OK;
+}
+
+fvm_status residual0(fvm_case* c, bool want_b2) {
+    int nb = 0;
+    const double N = (double)c->cd.N;
+    KLAUNCH("resid0", N * (8 + elem_size(c->prec) + elem_size(c->inner) + 1), 1,
+            launch_resid0(c->inner, c->prec, c->levels[0].dev, c->p, c->b, c->levels[0].r, c->partials,
+                          want_b2 ? 1 : 0, c->stream, &nb));
+    KLAUNCH("norm_finalize", 16.0 * nb, 1, launch_norm_finalize(c->partials, nb, want_b2 ? 1 : 0, c->norms, c->stream));
+    return FVM_OK;
+}
+
+fvm_status read_norms(fvm_case* c, double& rel) {
+    CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double r2 = c->h_norms[0], b2 = c->h_norms[1];
+    if (!std::isfinite(r2) || !std::isfinite(b2)) {
+        rel = NAN;
+        return FVM_OK;
+    }
+    rel = b2 > 0.0 ? std::sqrt(r2 / b2) : 0.0;
+    return FVM_OK;
+}
+
+fvm_status solve(fvm_case* c, int& cycles, double& rel) {
+    const fvm_case_desc& d = c->desc;
+    cycles = 0;
+    if (d.fixed_vcycles > 0) {
+        for (int it = 0; it < d.fixed_vcycles; ++it) {
+            ST_TRY(residual0(c, it == 0));
+            int idx;
+            ST_TRY(cycle(c, 0, idx));
+        }
+        cycles = d.fixed_vcycles;
+        ST_TRY(residual0(c, false));
+        return read_norms(c, rel);
+    }
+    for (int it = 0;; ++it) {
+        ST_TRY(residual0(c, it == 0));
+        ST_TRY(read_norms(c, rel));
+        if (!std::isfinite(rel)) return FVM_OK;
+        if (rel <= d.mg_rel_tol || it == d.max_vcycles) break;
+        int idx;
+        ST_TRY(cycle(c, 0, idx));
+        ++cycles;
+    }
+    return FVM_OK;
+}
+
+// ------------------------------------------------------------------ stages
+fvm_status stage(fvm_case* c, int st, int* cycles, double* rel) {
+    cudaStream_t s = c->stream;
+    const double N = (double)c->cd.N;
+    const double sz = (double)elem_size(c->prec);
+    switch (st) {
+        case FVM_STAGE_DT:
+            KLAUNCH("dt", N * (5 * sz + 1), 2, launch_dt(c->prec, c->cd, ptrs(c->cur), c->dt_state, s));
+            return FVM_OK;
+        case FVM_STAGE_DESTRUCTION:
+            KLAUNCH("destruction", N * (7 * sz + 1), 1,
+                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, s));
+            std::swap(c->cur[4], c->nxt[4]);
+            std::swap(c->cur[5], c->nxt[5]);
+            return FVM_OK;
+        case FVM_STAGE_EXPLICIT:
+            KLAUNCH("explicit", N * (12 * sz + 1), 1,
+                    launch_explicit(c->prec, c->cd, ptrs(c->cur), ptrs(c->nxt), c->dt_state, s));
+            for (int f = 0; f < 6; ++f) std::swap(c->cur[f], c->nxt[f]);
+            return FVM_OK;
+        case FVM_STAGE_RHS:
+            KLAUNCH("rhs", N * (4 * sz + 1), 1, launch_rhs(c->prec, c->cd, ptrs(c->cur), c->b, c->dt_state, s));
+            return FVM_OK;
+        case FVM_STAGE_SOLVE: {
+            int cy = 0;
+            double r = 0.0;
+            ST_TRY(solve(c, cy, r));
+            if (cycles) *cycles = cy;
+            if (rel) *rel = r;
+            return FVM_OK;
+        }
+        case FVM_STAGE_PROJECT:
+            KLAUNCH("project", N * (6 * sz + 9), 1,
+                    launch_project(c->prec, c->cd, c->levels[0].dev, ptrs(c->cur), ptrs(c->nxt), c->p,
+                                   c->dt_state, s));
+            for (int f = 0; f < 3; ++f) std::swap(c->cur[f], c->nxt[f]);
+            return FVM_OK;
+        default:
+            return fail(FVM_ERR_INVALID, "unknown stage");
+    }
+}
+
+int field_slot(int fid) {
+    // state slots: u v w T k omega; p is separate
+    static const int slot[7] = {0, 1, 2, -1, 3, 4, 5};
+    return slot[fid];
+}
+
+fvm_status build_case(const Plan& pl, fvm_case* c) {
+    const fvm_case_desc& d = pl.d;
+    c->desc = d;
+    c->vents.assign(d.vents, d.vents + d.n_vents);
+    c->boxes.assign(d.boxes, d.boxes + d.n_boxes);
+    c->desc.vents = c->vents.data();
+    c->desc.boxes = c->boxes.data();
+    c->prec = pl.prec;
+    c->inner = pl.inner;
+    c->dt0 = pl.dt0;
+    if (d.stream) c->stream = (cudaStream_t)d.stream;
+    else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const HostLevel& L0 = pl.levels[0];
+    const int64_t N = L0.N();
+    const size_t s = elem_size(pl.prec), si = elem_size(pl.inner);
+    // case description for the kernels
+    CaseDev& cd = c->cd;
+    memset(&cd, 0, sizeof(cd));
+    for (int a = 0; a < 3; ++a) {
+        cd.n[a] = L0.n[a];
+        cd.active[a] = L0.active[a];
+        cd.h[a] = L0.h[a];
+        cd.inv_h[a] = 1.0 / L0.h[a];
+        cd.inv_h2[a] = 1.0 / (L0.h[a] * L0.h[a]);
+        const double dw = 0.5 * L0.h[a];
+        cd.om_wall[a] = 6.0 * d.nu / (kBetaI * dw * dw);
+        cd.gb[a] = d.buoyancy ? -d.gravity[a] * d.beta_T : 0.0;
+    }
+    cd.N = N;
+    cd.nu = d.nu;
+    cd.alpha = d.nu / d.Pr;
+    cd.inv_Prt = 1.0 / d.Prt;
+    cd.inv_sigk = 1.0 / d.sigma_k;
+    cd.inv_sigw = 1.0 / d.sigma_w;
+    cd.T_ref = d.T_ref;
+    cd.cfl = d.cfl;
+    cd.dt0 = pl.dt0;
+    cd.dt_adapt = d.dt_adapt;
+    const double rcp_alpha = (d.rho > 0.0 && d.cp > 0.0) ? 1.0 / (d.rho * d.cp * cd.alpha) : 0.0;
+    cd.n_patches = (int)pl.patches.size();
+    for (size_t pi = 0; pi < pl.patches.size(); ++pi) {
+        const fvm_patch& p = pl.patches[pi];
+        PatchDev& q = cd.patch[pi];
+        q.kind = p.kind;
+        q.thermal = p.thermal;
+        q.T_value = p.T_value;
+        q.q_coef = p.T_value * rcp_alpha;
+        q.vel[0] = q.vel[1] = q.vel[2] = 0.0;
+        q.T_in = p.T_in;
+        inlet_kw(p, q.k_in, q.om_in);
+        // the face this patch sits on decides the inward normal
+        const int face = pi < 6 ? (int)pi : c->vents[pi - 6].face;
+        const double inward = (face % 2 == 0) ? 1.0 : -1.0;
+        if (p.kind == FVM_INLET) q.vel[face / 2] = inward * p.u_normal;
+    }
+    cd.n_boxes = d.n_boxes;
+    for (int bi = 0; bi < d.n_boxes; ++bi) {
+        cd.box[bi].thermal = c->boxes[bi].thermal;
+        cd.box[bi].T_value = c->boxes[bi].T_value;
+        cd.box[bi].q_coef = c->boxes[bi].T_value * rcp_alpha;
+    }
+    // device memory
+    for (int f = 0; f < 6; ++f) {
+        ST_TRY(dalloc(c, &c->cur[f], N * s));
+        ST_TRY(dalloc(c, &c->nxt[f], N * s));
+    }
+    ST_TRY(dalloc(c, (void**)&c->p, N * 8));
+    ST_TRY(dalloc(c, &c->b, N * s));
+    ST_TRY(dalloc(c, (void**)&c->staging, N * 8));
+    uint8_t* tag_d;
+    ST_TRY(dalloc(c, (void**)&tag_d, N));
+    CUDA_TRY(cudaMemcpyAsync(tag_d, pl.tag.data(), N, cudaMemcpyHostToDevice, c->stream));
+    cd.tag = tag_d;
+    for (int f = 0; f < 6; ++f) {
+        uint8_t* fp;
+        ST_TRY(dalloc(c, (void**)&fp, pl.face_patch[f].size()));
+        CUDA_TRY(cudaMemcpyAsync(fp, pl.face_patch[f].data(), pl.face_patch[f].size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+        cd.face_patch[f] = fp;
+    }
+    c->levels.resize(pl.levels.size());
+    for (size_t l = 0; l < pl.levels.size(); ++l) {
+        const HostLevel& H = pl.levels[l];
+        DevLevel& D = c->levels[l];
+        LevelDev& v = D.dev;
+        memset(&v, 0, sizeof(v));
+        double diag = 0.0;
+        int nact = 0;
+        for (int a = 0; a < 3; ++a) {
+            v.n[a] = H.n[a];
+            v.active[a] = H.active[a];
+            v.inv_h2[a] = 1.0 / (H.h[a] * H.h[a]);
+            if (H.active[a]) {
+                diag += 2.0 * v.inv_h2[a];
+                ++nact;
+            }
+        }
+        v.N = H.N();
+        v.inv_D = 1.0 / diag;
+        v.wJ = d.jacobi_weight > 0.0 ? d.jacobi_weight : (nact == 3 ? 6.0 / 7.0 : 4.0 / 5.0);
+        if (l == 0) v.solid = tag_d;
+        else {
+            uint8_t* sd;
+            ST_TRY(dalloc(c, (void**)&sd, v.N));
+            CUDA_TRY(cudaMemcpyAsync(sd, H.solid.data(), v.N, cudaMemcpyHostToDevice, c->stream));
+            v.solid = sd;
+        }
+        for (int f = 0; f < 6; ++f) {
+            uint8_t* dd;
+            ST_TRY(dalloc(c, (void**)&dd, H.dir[f].size()));
+            CUDA_TRY(cudaMemcpyAsync(dd, H.dir[f].data(), H.dir[f].size(), cudaMemcpyHostToDevice, c->stream));
+            v.dir[f] = dd;
+        }
+        ST_TRY(dalloc(c, &D.e[0], v.N * si));
+        ST_TRY(dalloc(c, &D.e[1], v.N * si));
+        ST_TRY(dalloc(c, &D.r, v.N * si));
+    }
+    std::vector<double> inv;
+    if (!coarse_inverse(pl.levels.back(), inv))
+        return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
+    ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 8));
+    CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    c->nblocks0 = resid0_blocks(N);
+    ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
+    ST_TRY(dalloc(c, (void**)&c->norms, 4 * 8));
+    ST_TRY(dalloc(c, (void**)&c->dt_state, 4 * 8));
+    CUDA_TRY(cudaMallocHost((void**)&c->h_norms, 8 * sizeof(double)));
+    c->h_dt = c->h_norms + 4;
+    double dts[4] = {pl.dt0, 0.5 * pl.dt0, 0.0, 0.0};
+    CUDA_TRY(cudaMemcpyAsync(c->dt_state, dts, sizeof(dts), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->p, 0, N * 8, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->b, 0, N * s, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->norms, 0, 4 * 8, c->stream));
+    CUDA_TRY(launch_init_state(c->prec, cd, ptrs(c->cur), pl.base, d.seed, d.init_perturb, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+size_t fvm_case_bytes(const fvm_case_desc* desc) {
+    Plan pl;
+    if (plan_case(desc, pl) != FVM_OK) return 0;
+    return (size_t)pl.bytes;
+}
+
+fvm_status fvm_create_case(const fvm_case_desc* desc, fvm_case** out) {
+    if (!out) return fail(FVM_ERR_INVALID, "null output pointer");
+    Plan pl;
+    ST_TRY(plan_case(desc, pl));
+    fvm_case* c = new fvm_case();
+    fvm_status st = build_case(pl, c);
+    if (st != FVM_OK) {
+        std::string msg = g_err;
+        free_case(c);
+        g_err = msg;
+        return st;
+    }
+    g_err.clear();
+    *out = c;
+    return FVM_OK;
+}
+
+void fvm_destroy_case(fvm_case* c) { free_case(c); }
+
+fvm_status fvm_run_stage(fvm_case* c, int st) {
+    if (!c) return fail(FVM_ERR_INVALID, "null case");
+    ST_TRY(stage(c, st, nullptr, nullptr));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
+    if (!c) return fail(FVM_ERR_INVALID, "null case");
+    if (nsteps < 0) return fail(FVM_ERR_INVALID, "nsteps < 0");
+    fvm_step_stats stats;
+    memset(&stats, 0, sizeof(stats));
+    fvm_status result = FVM_OK;
+    for (int n = 0; n < nsteps; ++n) {
+        int cycles = 0;
+        double rel = 0.0;
+        ST_TRY(stage(c, FVM_STAGE_DT, nullptr, nullptr));
+        ST_TRY(stage(c, FVM_STAGE_DESTRUCTION, nullptr, nullptr));
+        ST_TRY(stage(c, FVM_STAGE_EXPLICIT, nullptr, nullptr));
+        ST_TRY(stage(c, FVM_STAGE_DESTRUCTION, nullptr, nullptr));
+        ST_TRY(stage(c, FVM_STAGE_RHS, nullptr, nullptr));
+        ST_TRY(stage(c, FVM_STAGE_SOLVE, &cycles, &rel));
+        ST_TRY(stage(c, FVM_STAGE_PROJECT, nullptr, nullptr));
+        ++c->steps;
+        stats.steps++;
+        stats.vcycles_total += cycles;
+        stats.vcycles_last = cycles;
+        stats.rel_residual = rel;
+        if (!std::isfinite(rel)) {
+            result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
+            break;
+        }
+        if (c->desc.fixed_vcycles == 0 && rel > c->desc.mg_rel_tol) {
+            result = FVM_ERR_NOT_CONVERGED;
+            g_err = "V-cycle cap reached above the tolerance";
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->h_dt, c->dt_state, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    stats.dt_last = c->h_dt[0];
+    stats.sim_time = c->h_dt[2];
+    if (out) *out = stats;
+    return result;
+}
+
+fvm_status fvm_vcycle(fvm_case* c, int ncycles, double* rel_residual) {
+    if (!c) return fail(FVM_ERR_INVALID, "null case");
+    if (ncycles < 0) return fail(FVM_ERR_INVALID, "ncycles < 0");
+    for (int it = 0; it < ncycles; ++it) {
+        ST_TRY(residual0(c, it == 0));
+        int idx;
+        ST_TRY(cycle(c, 0, idx));
+    }
+    ST_TRY(residual0(c, true));
+    double rel = 0.0;
+    ST_TRY(read_norms(c, rel));
+    if (rel_residual) *rel_residual = rel;
+    return FVM_OK;
+}
+
+fvm_status fvm_read_fields(fvm_case* c, unsigned mask, double* host_out, size_t n) {
+    if (!c || (!host_out && mask)) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (mask >= (1u << 7)) return fail(FVM_ERR_INVALID, "field mask has bits above 6");
+    const int64_t N = c->cd.N;
+    size_t need = 0;
+    for (int f = 0; f < 7; ++f)
+        if (mask & (1u << f)) need += (size_t)N;
+    if (n < need) return fail(FVM_ERR_INVALID, "host buffer too small");
+    size_t off = 0;
+    for (int f = 0; f < 7; ++f) {
+        if (!(mask & (1u << f))) continue;
+        if (f == FVM_P) {
+            CUDA_TRY(cudaMemcpyAsync(host_out + off, c->p, N * 8, cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            CUDA_TRY(launch_pack(c->prec, c->cur[field_slot(f)], c->staging, N, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(host_out + off, c->staging, N * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
+        off += (size_t)N;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+fvm_status fvm_write_fields(fvm_case* c, unsigned mask, const double* host_in, size_t n) {
+    if (!c || (!host_in && mask)) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (mask >= (1u << 7)) return fail(FVM_ERR_INVALID, "field mask has bits above 6");
+    const int64_t N = c->cd.N;
+    size_t need = 0;
+    for (int f = 0; f < 7; ++f)
+        if (mask & (1u << f)) need += (size_t)N;
+    if (n < need) return fail(FVM_ERR_INVALID, "host buffer too small");
+    size_t off = 0;
+    for (int f = 0; f < 7; ++f) {
+        if (!(mask & (1u << f))) continue;
+        if (f == FVM_P) {
+            CUDA_TRY(cudaMemcpyAsync(c->p, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(c->staging, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(launch_unpack(c->prec, c->staging, c->cur[field_slot(f)], N, c->stream));
+        }
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        off += (size_t)N;
+    }
+    return FVM_OK;
+}
+
+fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n) {
+    if (!c || !host_b) return fail(FVM_ERR_INVALID, "null case or buffer");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)N) return fail(FVM_ERR_INVALID, "host buffer too small");
+    CUDA_TRY(cudaMemcpyAsync(c->staging, host_b, N * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(launch_unpack(c->prec, c->staging, c->b, N, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n) {
+    if (!c || !host_b) return fail(FVM_ERR_INVALID, "null case or buffer");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)N) return fail(FVM_ERR_INVALID, "host buffer too small");
+    CUDA_TRY(launch_pack(c->prec, c->b, c->staging, N, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(host_b, c->staging, N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_stats* stats) {
+    if (!cases || n < 0) return fail(FVM_ERR_INVALID, "bad case array");
+    fvm_status worst = FVM_OK;
+    for (int i = 0; i < n; ++i) {
+        fvm_status st = fvm_step(cases[i], nsteps, stats ? stats + i : nullptr);
+        if (st != FVM_OK && (worst == FVM_OK || st < worst)) worst = st;
+    }
+    return worst;
+}
+
+fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out) {
+    if (!c || !out) return fail(FVM_ERR_INVALID, "null case or output");
+    fvm_case_info info;
+    memset(&info, 0, sizeof(info));
+    info.cells = c->cd.N;
+    info.levels = (int32_t)c->levels.size();
+    info.precision = c->desc.precision;
+    info.dt0 = c->dt0;
+    double dts[3] = {0, 0, 0};
+    if (cudaMemcpy(dts, c->dt_state, sizeof(dts), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FVM_ERR_CUDA, "reading dt");
+    info.dt = dts[0];
+    info.sim_time = dts[2];
+    info.device_bytes = c->bytes;
+    info.steps = c->steps;
+    info.kernel_launches = c->launches;
+    *out = info;
+    return FVM_OK;
+}
+
+fvm_status fvm_profile_enable(fvm_case* c, int enable) {
+    if (!c) return fail(FVM_ERR_INVALID, "null case");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    prof_clear(c);
+    c->prof = enable != 0;
+    return FVM_OK;
+}
+
+fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_out) {
+    if (!c || (cap > 0 && !out)) return fail(FVM_ERR_INVALID, "null case or output");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    std::vector<fvm_kernel_stat> acc(c->cls_names.size());
+    for (size_t i = 0; i < acc.size(); ++i) {
+        memset(&acc[i], 0, sizeof(fvm_kernel_stat));
+        snprintf(acc[i].name, sizeof(acc[i].name), "%s", c->cls_names[i].c_str());
+    }
+    for (auto& r : c->recs) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        acc[r.cls].launches += 1;
+        acc[r.cls].ms += ms;
+        acc[r.cls].bytes += r.bytes;
+    }
+    for (int i = 0; i < (int)acc.size() && i < cap; ++i) out[i] = acc[i];
+    if (n_out) *n_out = (int)acc.size();
+    prof_clear(c);
+    return FVM_OK;
+}
+
+void fvm_struct_sizes(size_t out[7]) {
+    out[0] = sizeof(fvm_patch);
+    out[1] = sizeof(fvm_vent);
+    out[2] = sizeof(fvm_box);
+    out[3] = sizeof(fvm_case_desc);
+    out[4] = sizeof(fvm_step_stats);
+    out[5] = sizeof(fvm_case_info);
+    out[6] = sizeof(fvm_kernel_stat);
+}
+
+const char* fvm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

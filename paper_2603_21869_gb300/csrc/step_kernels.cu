@@ -1,0 +1,526 @@
+// Step kernels of the k-omega finite-volume time step: the seeded initial
+// state, the per-step time-step cap, the semi-implicit destruction half
+// step (Section 2.4, Eqs. k_des_step / o_des_step, Algorithm 4), the
+// explicit stage (Sections 2.3, A.2-A.4, Algorithms 2 and 3), the
+// pressure right-hand side (Eq. pc_residual) and the projection.
+//
+// One thread per cell, x fastest.  Neighbour states come from global
+// memory; boundary and obstacle neighbours are replaced by ghost values
+// (Section 2.5) computed in registers, so no ghost layer is stored.
+#include <cstdio>
+
+#include "fvm_internal.cuh"
+
+namespace {
+
+// Closure constants (Section 2.1; R_beta = 8 is the standard value the paper leaves unstated)
+constexpr double kAlphaStarInf = 1.0;
+constexpr double kBetaI = 0.072;
+constexpr double kAlphaStar0 = kBetaI / 3.0;
+constexpr double kRk = 6.0;
+constexpr double kAlphaInf = 0.52;
+constexpr double kAlpha0 = 1.0 / 9.0;
+constexpr double kRw = 2.95;
+constexpr double kBetaStarInf = 0.09;
+constexpr double kBeta = kBetaI;
+constexpr double kRbeta = 8.0;
+constexpr double kEpsOmega = 1e-12;
+constexpr double kKMin = 1e-14;
+constexpr double kOmegaMin = 1e-8;
+
+constexpr int kThreads = 256;
+
+template <class C>
+struct St {
+    C u, v, w, T, k, om;
+};
+
+template <class C>
+__device__ __forceinline__ C vcomp(const St<C>& s, int a) {
+    return a == 0 ? s.u : (a == 1 ? s.v : s.w);
+}
+
+template <class C>
+__device__ __forceinline__ C thermal_ghost(int thermal, double Tval, double qcoef, double h, C TP) {
+    if (thermal == FVM_FIXED_T) return (C)(2.0 * Tval) - TP;
+    if (thermal == FVM_HEAT_FLUX) return TP + (C)(qcoef * h);
+    return TP;
+}
+
+template <class S, class C>
+__device__ __forceinline__ St<C> load_state(const StatePtrs& st, int64_t c) {
+    St<C> s;
+    s.u = to_c<C>(ldg((const S*)st.f[0] + c));
+    s.v = to_c<C>(ldg((const S*)st.f[1] + c));
+    s.w = to_c<C>(ldg((const S*)st.f[2] + c));
+    s.T = to_c<C>(ldg((const S*)st.f[3] + c));
+    s.k = to_c<C>(ldg((const S*)st.f[4] + c));
+    s.om = to_c<C>(ldg((const S*)st.f[5] + c));
+    return s;
+}
+
+// State across the face on `side` (-1 / +1) of cell (i,j,k) along `axis`:
+// the neighbour's values, or the ghost values of Section 2.5 at a domain
+// face or a solid neighbour.  Returns the face kind.
+template <class S, class C>
+__device__ __forceinline__ int neighbour(const CaseDev& cd, const StatePtrs& st, int i, int j, int k,
+                                         int axis, int side, const St<C>& P, St<C>& g) {
+    int q[3] = {i, j, k};
+    q[axis] += side;
+    if (q[axis] < 0 || q[axis] >= cd.n[axis]) {
+        const int face = 2 * axis + (side > 0 ? 1 : 0);
+        const PatchDev& pt = cd.patch[cd.face_patch[face][face_index(axis, i, j, k, cd.n)]];
+        if (pt.kind == FVM_WALL) {
+            g.u = -P.u; g.v = -P.v; g.w = -P.w;
+            g.k = P.k; g.om = P.om;
+            g.T = thermal_ghost<C>(pt.thermal, pt.T_value, pt.q_coef, cd.h[axis], P.T);
+            return FK_WALL;
+        }
+        if (pt.kind == FVM_INLET) {
+            g.u = (C)(2.0 * pt.vel[0]) - P.u;
+            g.v = (C)(2.0 * pt.vel[1]) - P.v;
+            g.w = (C)(2.0 * pt.vel[2]) - P.w;
+            g.T = (C)(2.0 * pt.T_in) - P.T;
+            g.k = (C)(2.0 * pt.k_in) - P.k;
+            g.om = (C)(2.0 * pt.om_in) - P.om;
+            return FK_INLET;
+        }
+        g = P;
+        return pt.kind == FVM_OUTLET ? FK_OUTLET : FK_EMPTY;
+    }
+    const int64_t c = cell_index(q[0], q[1], q[2], cd.n[0], cd.n[1]);
+    const int t = cd.tag[c];
+    if (t) {
+        const BoxDev& b = cd.box[t - 1];
+        g.u = -P.u; g.v = -P.v; g.w = -P.w;
+        g.k = P.k; g.om = P.om;
+        g.T = thermal_ghost<C>(b.thermal, b.T_value, b.q_coef, cd.h[axis], P.T);
+        return FK_WALL;
+    }
+    g = load_state<S, C>(st, c);
+    return FK_INTERIOR;
+}
+
+template <class C>
+__device__ __forceinline__ C omega_safe(C om) { return om > (C)kEpsOmega ? om : (C)kEpsOmega; }
+
+// Re_t (Eq. Re_t) and alpha* (Eq. a_star); nu_t = alpha* k / omega (Eq. ko_turb_diff)
+template <class C>
+__device__ __forceinline__ C re_t(C k, C om, C nu) { return k / (nu * omega_safe(om)); }
+
+template <class C>
+__device__ __forceinline__ C alpha_star_of(C ret) {
+    const C r = ret / (C)kRk;
+    return (C)kAlphaStarInf * ((C)kAlphaStar0 + r) / ((C)1 + r);
+}
+
+template <class C>
+__device__ __forceinline__ C nut_of(C k, C om, C nu) {
+    return alpha_star_of(re_t(k, om, nu)) * k / omega_safe(om);
+}
+
+// ------------------------------------------------------------------ init
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+    // output n (0-based) of SplitMix64 seeded with `seed` (Steele, Lea, Flood 2014)
+    uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class S>
+__global__ void k_init(CaseDev cd, StatePtrs st, double b0, double b1, double b2, double b3, double b4,
+                       double b5, uint64_t seed, double eps) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cd.N) return;
+    const double base[6] = {b0, b1, b2, b3, b4, b5};
+    const int fid[6] = {FVM_U, FVM_V, FVM_W, FVM_T, FVM_K, FVM_OMEGA};
+    const bool solid = cd.tag[c] != 0;
+    for (int f = 0; f < 6; ++f) {
+        double x = base[f];
+        if (eps != 0.0) {
+            const uint64_t bits = splitmix64_at(seed, (uint64_t)fid[f] * (uint64_t)cd.N + (uint64_t)c);
+            const double xi = (double)(bits >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+            x = x * (1.0 + eps * xi);
+        }
+        ((S*)st.f[f])[c] = from_c<S, double>(solid ? 0.0 : x);
+    }
+}
+
+// ------------------------------------------------------------------ dt
+// rate = sum_active (|u_a| / h_a + 2 Gamma / h_a^2), Gamma = max(nu + nu_t, alpha + nu_t / Pr_t);
+// the block maxima go to dt_state[3] (as ordered bits of a non-negative double)
+template <class S>
+__global__ void k_rate_max(CaseDev cd, StatePtrs st, unsigned long long* rate_bits) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double lam = 0.0;
+    if (c < cd.N && cd.tag[c] == 0) {
+        const double u[3] = {(double)to_c<double>(ldg((const S*)st.f[0] + c)),
+                             (double)to_c<double>(ldg((const S*)st.f[1] + c)),
+                             (double)to_c<double>(ldg((const S*)st.f[2] + c))};
+        const double k = to_c<double>(ldg((const S*)st.f[4] + c));
+        const double om = to_c<double>(ldg((const S*)st.f[5] + c));
+        const double nut = nut_of<double>(k, om, cd.nu);
+        const double g1 = cd.nu + nut, g2 = cd.alpha + nut * cd.inv_Prt;
+        const double gam = g1 > g2 ? g1 : g2;
+        for (int a = 0; a < 3; ++a)
+            if (cd.active[a]) lam += fabs(u[a]) * cd.inv_h[a] + 2.0 * gam * cd.inv_h2[a];
+        if (!(lam == lam)) lam = __longlong_as_double(0x7ff0000000000000ll);   // NaN -> +inf
+    }
+    __shared__ double red[kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        atomicMax(rate_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// dt_state: [0] dt, [1] dt/2, [2] simulated time, [3] rate bits (reset here)
+__global__ void k_dt_finalize(double dt0, double cfl, int adapt, double* dt_state) {
+    unsigned long long* bits = (unsigned long long*)(dt_state + 3);
+    const double lam = __longlong_as_double((long long)*bits);
+    double dt = dt0;
+    if (adapt && lam > 0.0) {
+        const double cap = cfl / lam;
+        dt = cap < dt0 ? cap : dt0;
+    }
+    dt_state[0] = dt;
+    dt_state[1] = 0.5 * dt;
+    dt_state[2] += dt;
+    *bits = 0ull;
+}
+
+// ------------------------------------------------------------------ destruction
+template <class S, class C>
+__global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S* __restrict__ om_out,
+                              const double* dt_state) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cd.N) return;
+    const int nx = cd.n[0], ny = cd.n[1];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const St<C> P = load_state<S, C>(in, c);
+    if (cd.tag[c]) {
+        k_out[c] = from_c<S, C>(P.k);
+        om_out[c] = from_c<S, C>(P.om);
+        return;
+    }
+    // cell gradients L_j * D_j * BC_j(phi) of u, v, w, k, omega
+    C gu[3][3], gk[3], gw[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) {
+            gu[0][a] = gu[1][a] = gu[2][a] = (C)0;
+            gk[a] = gw[a] = (C)0;
+            continue;
+        }
+        St<C> L, R;
+        neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
+        neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        const C ih = (C)cd.inv_h[a];
+        gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
+        gu[1][a] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
+        gu[2][a] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
+        gk[a] = (C)0.5 * ((R.k - P.k) * ih + (P.k - L.k) * ih);
+        gw[a] = (C)0.5 * ((R.om - P.om) * ih + (P.om - L.om) * ih);
+    }
+    C Sm[3][3], Om[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Sm[a][b] = (C)0.5 * (gu[a][b] + gu[b][a]);
+            Om[a][b] = (C)0.5 * (gu[a][b] - gu[b][a]);
+        }
+    const C nu = (C)cd.nu;
+    const C oms = omega_safe(P.om);
+    // k: chi_k, f_beta*, beta* (Eqs. k_des, beta_star)
+    const C chik = (gk[0] * gw[0] + gk[1] * gw[1] + gk[2] * gw[2]) / (oms * oms * oms);
+    C fbs = (C)1;
+    if (chik > (C)0) {
+        if (chik > (C)1e8) fbs = (C)(680.0 / 400.0);
+        else {
+            const C c2 = chik * chik;
+            fbs = ((C)1 + (C)680 * c2) / ((C)1 + (C)400 * c2);
+        }
+    }
+    const C x = re_t(P.k, P.om, nu) / (C)kRbeta;
+    C bstar;
+    if (x > (C)1e4) bstar = (C)kBetaStarInf;
+    else {
+        const C x2 = x * x;
+        const C x4 = x2 * x2;
+        bstar = (C)kBetaStarInf * ((C)(4.0 / 15.0) + x4) / ((C)1 + x4);
+    }
+    const C dt = (C)dt_state[1];
+    const C knew = P.k / ((C)1 + dt * bstar * fbs * P.om);
+    // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des)
+    C tr = (C)0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int e = 0; e < 3; ++e) tr += Om[a][b] * Om[b][e] * Sm[e][a];
+    const C bo = (C)kBetaStarInf * oms;
+    const C chiw = fabs(tr / (bo * bo * bo));
+    const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : ((C)1 + (C)70 * chiw) / ((C)1 + (C)80 * chiw);
+    const C omnew = P.om / ((C)1 + dt * (C)kBeta * fb * P.om);
+    k_out[c] = from_c<S, C>(knew);
+    om_out[c] = from_c<S, C>(omnew);
+}
+
+// ------------------------------------------------------------------ explicit stage
+// Flux of (u, v, w, T, k, omega) through one face with states L (lower) and R (upper):
+// -phi_upwind u_face + Gamma (phi_R - phi_L) / h, and -(2/3) k_face on the
+// momentum component along the face normal.
+template <class C>
+__device__ __forceinline__ void face_flux(const CaseDev& cd, int a, const St<C>& L, const St<C>& R, C nut_f,
+                                          C fl[6]) {
+    const C uf = (C)0.5 * (vcomp(L, a) + vcomp(R, a));
+    const bool pos = uf >= (C)0;
+    const C ih = (C)cd.inv_h[a];
+    const C nu = (C)cd.nu;
+    const C gm = nu + nut_f;
+    const C gT = (C)cd.alpha + nut_f * (C)cd.inv_Prt;
+    const C gk = nu + nut_f * (C)cd.inv_sigk;
+    const C gw = nu + nut_f * (C)cd.inv_sigw;
+    fl[0] = -((pos ? L.u : R.u) * uf) + gm * (R.u - L.u) * ih;
+    fl[1] = -((pos ? L.v : R.v) * uf) + gm * (R.v - L.v) * ih;
+    fl[2] = -((pos ? L.w : R.w) * uf) + gm * (R.w - L.w) * ih;
+    fl[3] = -((pos ? L.T : R.T) * uf) + gT * (R.T - L.T) * ih;
+    fl[4] = -((pos ? L.k : R.k) * uf) + gk * (R.k - L.k) * ih;
+    fl[5] = -((pos ? L.om : R.om) * uf) + gw * (R.om - L.om) * ih;
+    fl[a] -= (C)(2.0 / 3.0) * ((C)0.5 * (L.k + R.k));
+}
+
+template <class C>
+__device__ __forceinline__ C face_nut(int kind, C nutP, const St<C>& nb, C nu) {
+    if (kind == FK_WALL) return (C)0;
+    if (kind == FK_INTERIOR) return (C)0.5 * (nutP + nut_of(nb.k, nb.om, nu));
+    return nutP;
+}
+
+template <class S, class C>
+__global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double* dt_state) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cd.N) return;
+    const int nx = cd.n[0], ny = cd.n[1];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const St<C> P = load_state<S, C>(in, c);
+    S* o[6];
+    for (int f = 0; f < 6; ++f) o[f] = (S*)out.f[f];
+    if (cd.tag[c]) {
+        o[0][c] = from_c<S, C>(P.u); o[1][c] = from_c<S, C>(P.v); o[2][c] = from_c<S, C>(P.w);
+        o[3][c] = from_c<S, C>(P.T); o[4][c] = from_c<S, C>(P.k); o[5][c] = from_c<S, C>(P.om);
+        return;
+    }
+    const C nu = (C)cd.nu;
+    const C nutP = nut_of(P.k, P.om, nu);
+    C rhs[6] = {(C)0, (C)0, (C)0, (C)0, (C)0, (C)0};
+    C gu[3][3];
+    C omw = (C)0;
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) {
+            gu[0][a] = gu[1][a] = gu[2][a] = (C)0;
+            continue;
+        }
+        St<C> L, R;
+        const int kl = neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
+        const int kr = neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        C fw[6], fe[6];
+        face_flux(cd, a, L, P, face_nut(kl, nutP, L, nu), fw);
+        face_flux(cd, a, P, R, face_nut(kr, nutP, R, nu), fe);
+        const C ih = (C)cd.inv_h[a];
+        for (int f = 0; f < 6; ++f) rhs[f] += (fe[f] - fw[f]) * ih;
+        gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
+        gu[1][a] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
+        gu[2][a] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
+        if (kl == FK_WALL || kr == FK_WALL) {
+            const C ow = (C)cd.om_wall[a];
+            omw = ow > omw ? ow : omw;
+        }
+    }
+    // production (Eqs. k_gen, o_gen, a) with S^2 = 2 S_ij S_ij
+    C S2 = (C)0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const C s = (C)0.5 * (gu[a][b] + gu[b][a]);
+            S2 += s * s;
+        }
+    S2 = (C)2 * S2;
+    const C Gk = nutP * S2;
+    const C ret = re_t(P.k, P.om, nu);
+    const C rw = ret / (C)kRw;
+    const C alpha = (C)kAlphaInf / alpha_star_of(ret) * ((C)kAlpha0 + rw) / ((C)1 + rw);
+    rhs[4] += Gk;
+    rhs[5] += alpha * P.om / P.k * Gk;
+    // Boussinesq buoyancy -g beta_T (T - T_ref)
+    const C dT = P.T - (C)cd.T_ref;
+    rhs[0] += (C)cd.gb[0] * dT;
+    rhs[1] += (C)cd.gb[1] * dT;
+    rhs[2] += (C)cd.gb[2] * dT;
+    const C dt = (C)dt_state[0];
+    C un = P.u + dt * rhs[0];
+    C vn = P.v + dt * rhs[1];
+    C wn = P.w + dt * rhs[2];
+    C Tn = P.T + dt * rhs[3];
+    C kn = P.k + dt * rhs[4];
+    C on = P.om + dt * rhs[5];
+    kn = kn > (C)kKMin ? kn : (C)kKMin;
+    on = on > (C)kOmegaMin ? on : (C)kOmegaMin;
+    if (omw > (C)0) on = omw;
+    o[0][c] = from_c<S, C>(un); o[1][c] = from_c<S, C>(vn); o[2][c] = from_c<S, C>(wn);
+    o[3][c] = from_c<S, C>(Tn); o[4][c] = from_c<S, C>(kn); o[5][c] = from_c<S, C>(on);
+}
+
+// ------------------------------------------------------------------ pressure RHS
+template <class S, class C>
+__global__ void k_rhs(CaseDev cd, StatePtrs in, S* __restrict__ b, const double* dt_state) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cd.N) return;
+    if (cd.tag[c]) {
+        b[c] = from_c<S, C>((C)0);
+        return;
+    }
+    const int nx = cd.n[0], ny = cd.n[1];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const St<C> P = load_state<S, C>(in, c);
+    C div = (C)0;
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) continue;
+        St<C> L, R;
+        neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
+        neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        const C ue = (C)0.5 * (vcomp(P, a) + vcomp(R, a));
+        const C uw = (C)0.5 * (vcomp(L, a) + vcomp(P, a));
+        div += (ue - uw) * (C)cd.inv_h[a];
+    }
+    b[c] = from_c<S, C>(-div / (C)dt_state[0]);
+}
+
+// ------------------------------------------------------------------ projection
+// pressure across a face: neighbour, Neumann ghost (walls, inlets, solids) or -p (outlets)
+__device__ __forceinline__ double p_across(const LevelDev& L, const double* p, int i, int j, int k, int a,
+                                           int side, double pP) {
+    int q[3] = {i, j, k};
+    q[a] += side;
+    if (q[a] < 0 || q[a] >= L.n[a]) {
+        const int face = 2 * a + (side > 0 ? 1 : 0);
+        return L.dir[face][face_index(a, i, j, k, L.n)] ? -pP : pP;
+    }
+    const int64_t c = cell_index(q[0], q[1], q[2], L.n[0], L.n[1]);
+    return L.solid[c] ? pP : __ldg(p + c);
+}
+
+template <class S, class C>
+__global__ void k_project(CaseDev cd, LevelDev L0, StatePtrs in, StatePtrs out, const double* __restrict__ p,
+                          const double* dt_state) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cd.N) return;
+    S* o[3] = {(S*)out.f[0], (S*)out.f[1], (S*)out.f[2]};
+    const S* q[3] = {(const S*)in.f[0], (const S*)in.f[1], (const S*)in.f[2]};
+    if (cd.tag[c]) {
+        for (int a = 0; a < 3; ++a) o[a][c] = q[a][c];
+        return;
+    }
+    const int nx = cd.n[0], ny = cd.n[1];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const double pP = __ldg(p + c);
+    const C dt = (C)dt_state[0];
+    for (int a = 0; a < 3; ++a) {
+        C g = (C)0;
+        if (cd.active[a]) {
+            // differences of the FP64 pressure are taken in FP64, then rounded
+            const double pl = p_across(L0, p, i, j, k, a, -1, pP);
+            const double pr = p_across(L0, p, i, j, k, a, +1, pP);
+            const double ih = cd.inv_h[a];
+            g = (C)(0.5 * ((pr - pP) * ih + (pP - pl) * ih));
+        }
+        o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
+    }
+}
+
+// ------------------------------------------------------------------ pack / unpack
+template <class S>
+__global__ void k_pack(const S* __restrict__ src, double* __restrict__ dst, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) dst[c] = to_c<double>(src[c]);
+}
+
+template <class S>
+__global__ void k_unpack(const double* __restrict__ src, S* __restrict__ dst, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) dst[c] = from_c<S, double>(src[c]);
+}
+
+inline unsigned nblocks(int64_t N) { return (unsigned)((N + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+#define DISPATCH(prec, ...)                                    \
+    do {                                                       \
+        if ((prec) == FVM_FP64) {                              \
+            using S = double; using C = double; __VA_ARGS__;   \
+        } else {                                               \
+            using S = float; using C = float; __VA_ARGS__;     \
+        }                                                      \
+    } while (0)
+
+cudaError_t launch_init_state(int prec, const CaseDev& cd, StatePtrs st, const double* base, uint64_t seed,
+                              double eps, cudaStream_t s) {
+    DISPATCH(prec, (void)sizeof(C); k_init<S><<<nblocks(cd.N), kThreads, 0, s>>>(
+                       cd, st, base[0], base[1], base[2], base[3], base[4], base[5], seed, eps));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_state, cudaStream_t s) {
+    DISPATCH(prec, (void)sizeof(C);
+             k_rate_max<S><<<nblocks(cd.N), kThreads, 0, s>>>(cd, st, (unsigned long long*)(dt_state + 3)));
+    k_dt_finalize<<<1, 1, 0, s>>>(cd.dt0, cd.cfl, cd.dt_adapt, dt_state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
+                               const double* dt_state, cudaStream_t s) {
+    DISPATCH(prec, k_destruction<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, (S*)k_out, (S*)om_out,
+                                                                           dt_state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out, const double* dt_state,
+                            cudaStream_t s) {
+    DISPATCH(prec, k_explicit<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, out, dt_state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const double* dt_state,
+                       cudaStream_t s) {
+    DISPATCH(prec, k_rhs<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, (S*)b, dt_state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
+                           const double* p, const double* dt_state, cudaStream_t s) {
+    DISPATCH(prec, k_project<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, L0, in, out, p, dt_state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s) {
+    if (prec == FVM_FP64) k_pack<double><<<nblocks(N), kThreads, 0, s>>>((const double*)src, dst, N);
+    else if (prec == FVM_FP32) k_pack<float><<<nblocks(N), kThreads, 0, s>>>((const float*)src, dst, N);
+    else k_pack<__nv_bfloat16><<<nblocks(N), kThreads, 0, s>>>((const __nv_bfloat16*)src, dst, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s) {
+    if (prec == FVM_FP64) k_unpack<double><<<nblocks(N), kThreads, 0, s>>>(src, (double*)dst, N);
+    else if (prec == FVM_FP32) k_unpack<float><<<nblocks(N), kThreads, 0, s>>>(src, (float*)dst, N);
+    else k_unpack<__nv_bfloat16><<<nblocks(N), kThreads, 0, s>>>(src, (__nv_bfloat16*)dst, N);
+    return cudaGetLastError();
+}

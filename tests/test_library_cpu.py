@@ -1,0 +1,65 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every symbol include/fvm.h declares, its structs match the binding, and
+descriptor validation and memory accounting work."""
+import os
+import re
+
+import pytest
+
+from paper_2603_21869_gb300 import binding, cases
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_21869_gb300 import build
+    build.ensure_built()
+    return binding.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "fvm.h")).read()
+    declared = set(re.findall(r"\b(fvm_[a-z_0-9]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(binding.EXPORTS)
+
+
+def test_struct_layout_matches_binding(lib):
+    import ctypes as ct
+    sizes = binding.struct_sizes()
+    ours = [ct.sizeof(t) for t in (binding.Patch, binding.Vent, binding.Box, binding.CaseDesc,
+                                   binding.StepStats, binding.CaseInfo, binding.KernelStat)]
+    assert sizes == ours
+
+
+def test_case_bytes_scale_with_precision(lib):
+    s64 = cases.heated_channel_3d(64, 16, 16, mg_levels=4)
+    s32 = s64.replace(precision=cases.FP32)
+    b64, b32 = binding.case_bytes(s64), binding.case_bytes(s32)
+    N = 64 * 16 * 16
+    assert b64 > 100 * N and b32 < b64
+    # full 3D channel workload (1M cells) in FP32 stays well under 200 MB
+    assert binding.case_bytes(cases.heated_channel_3d(precision=cases.FP32)) < 200e6
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0),
+    dict(mg_levels=9),
+    dict(mg_levels=1),
+    dict(pre_sweeps=0),
+    dict(nu=0.0),
+    dict(boxes=[cases.Box(0, 100, 0, 4, 0, 4)]),
+    dict(vents=[cases.Vent(face=2, a0=0, a1=200, b0=0, b1=2, bc=cases.Patch(cases.OUTLET))]),
+    dict(faces=[cases.Patch(cases.INLET, u_normal=1.0, intensity=0.05, length_scale=0.1)] + [cases.Patch()] * 5),
+    dict(nz=1),
+])
+def test_invalid_descriptors_are_rejected_without_a_gpu(lib, bad):
+    spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3).replace(**bad)
+    assert binding.case_bytes(spec) == 0
+    with pytest.raises(binding.FvmError) as ei:
+        binding.Case(spec)
+    assert ei.value.status == binding.ERR_INVALID
+    assert binding.last_error()
