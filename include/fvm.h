@@ -111,7 +111,8 @@ typedef struct {
     int32_t pre_sweeps, post_sweeps; /* weighted-Jacobi sweeps, each >= 1 */
     int32_t max_vcycles;             /* cap per solve */
     int32_t fixed_vcycles;           /* > 0: exactly this many per solve, no test */
-    int32_t reserved2;
+    int32_t inner_cycles;            /* V-cycles per FP64 outer residual (0: 1 for FP64, 2 otherwise);
+                                        the stopping test runs after each group */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
@@ -207,10 +208,17 @@ fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_st
 
 fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
 
+/* Options (fvm_set_option).  FVM_OPT_GRAPH (default 1): run each time
+   step as one CUDA graph, the V-cycle loop being a device-side while node;
+   0 runs the same kernels launch by launch with one host synchronisation
+   per V-cycle.  Results are identical either way. */
+enum { FVM_OPT_GRAPH = 1 };
+fvm_status fvm_set_option(fvm_case* c, int option, int64_t value);
+
 /* Profiling hook.  While enabled, every kernel the case launches is
    bracketed by a pair of CUDA events on the case's stream, and its class,
-   device time and algorithmic bytes are tallied.  Enabling or disabling
-   clears the tallies. */
+   device time and algorithmic bytes are tallied; steps then run launch by
+   launch (not as graphs).  Enabling or disabling clears the tallies. */
 fvm_status fvm_profile_enable(fvm_case* c, int enable);
 
 /* Copy up to cap per-class tallies into out (n_out = classes seen), and

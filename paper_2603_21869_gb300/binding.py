@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libfvm.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_BUDGET, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
 STAGE_DT, STAGE_DESTRUCTION, STAGE_EXPLICIT, STAGE_RHS, STAGE_SOLVE, STAGE_PROJECT = range(6)
+OPT_GRAPH = 1
 
 
 class FvmError(RuntimeError):
@@ -58,7 +59,7 @@ class CaseDesc(ct.Structure):
                 ("vents", ct.POINTER(Vent)), ("n_vents", ct.c_int32), ("reserved0", ct.c_int32),
                 ("boxes", ct.POINTER(Box)), ("n_boxes", ct.c_int32), ("reserved1", ct.c_int32),
                 ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
-                ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("reserved2", ct.c_int32),
+                ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("inner_cycles", ct.c_int32),
                 ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
                 ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
                 ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
@@ -82,8 +83,8 @@ class KernelStat(ct.Structure):
 
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
-           "fvm_step_batch", "fvm_case_get_info", "fvm_profile_enable", "fvm_profile_read", "fvm_struct_sizes",
-           "fvm_last_error"]
+           "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
+           "fvm_struct_sizes", "fvm_last_error"]
 
 _lib = None
 
@@ -111,6 +112,7 @@ def lib():
     L.fvm_read_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_step_batch.argtypes = [ct.POINTER(CP), ct.c_int, ct.c_int, ct.POINTER(StepStats)]
     L.fvm_case_get_info.argtypes = [CP, ct.POINTER(CaseInfo)]
+    L.fvm_set_option.argtypes = [CP, ct.c_int, ct.c_int64]
     L.fvm_profile_enable.argtypes = [CP, ct.c_int]
     L.fvm_profile_read.argtypes = [CP, ct.POINTER(KernelStat), ct.c_int, ct.POINTER(ct.c_int)]
     L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
@@ -118,7 +120,7 @@ def lib():
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
-                 "fvm_case_get_info", "fvm_profile_enable", "fvm_profile_read"]:
+                 "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read"]:
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -164,7 +166,7 @@ class _Desc:
         d.boxes = ct.cast(self.boxes, ct.POINTER(Box))
         d.n_boxes = len(spec.boxes)
         d.mg_levels, d.pre_sweeps, d.post_sweeps = spec.mg_levels, spec.pre_sweeps, spec.post_sweeps
-        d.max_vcycles, d.fixed_vcycles = spec.max_vcycles, spec.fixed_vcycles
+        d.max_vcycles, d.fixed_vcycles, d.inner_cycles = spec.max_vcycles, spec.fixed_vcycles, spec.inner_cycles
         d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
         d.seed = spec.seed & ((1 << 64) - 1)
         d.init_perturb = spec.init_perturb
@@ -267,6 +269,9 @@ class Case:
         _check(lib().fvm_read_poisson_rhs(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
         nx, ny, nz = self.shape
         return buf.reshape(nz, ny, nx).transpose(2, 1, 0)
+
+    def set_graph(self, enable=True):
+        _check(lib().fvm_set_option(self._h, OPT_GRAPH, 1 if enable else 0))
 
     def profile(self, enable=True):
         _check(lib().fvm_profile_enable(self._h, 1 if enable else 0))

@@ -69,5 +69,17 @@ def ensure_built():
     return LIB
 
 
+def build_alu_peak():
+    """The ALU-throughput probe (a separate executable, not part of the library)."""
+    exe = os.path.join(HERE, "alu_peak")
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", os.path.join(CSRC, "alu_peak.cu"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on alu_peak.cu:\n{r.stdout}\n{r.stderr}")
+    return exe
+
+
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "-v" in sys.argv else []))
+    if "--alu" in sys.argv:
+        print(build_alu_peak())

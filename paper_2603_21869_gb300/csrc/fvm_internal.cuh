@@ -25,6 +25,8 @@ struct PatchDev {
     double q_coef;       // heat flux q / (rho cp alpha); ghost = T_P + q_coef * h_normal
     double vel[3];       // inlet velocity vector (inward normal * u_normal)
     double T_in, k_in, om_in;
+    // FP32 copies of the ghost constants: 2 x the face value, q_coef * h_a
+    float vel2f[3], T_in2f, k_in2f, om_in2f, T_value2f, qhf[3];
 };
 
 struct BoxDev {
@@ -32,6 +34,14 @@ struct BoxDev {
     int32_t pad;
     double T_value;
     double q_coef;
+    float T_value2f, qhf[3];
+};
+
+// FP32 copies of the case constants used by the FP32 kernels
+struct CaseF {
+    float h[3], inv_h[3], inv_h2[3];
+    float nu, alpha, inv_Prt, inv_sigk, inv_sigw;
+    float gb[3], T_ref, om_wall[3];
 };
 
 // Everything the step kernels need about a case; passed by value.
@@ -50,9 +60,15 @@ struct CaseDev {
     int32_t n_patches, n_boxes, pad;
     const uint8_t* tag;      // 0 fluid, b + 1 solid cell of box b
     const uint8_t* face_patch[6];
+    CaseF f;
     PatchDev patch[FVM_MAX_PATCHES];
     BoxDev box[FVM_MAX_BOXES];
 };
+
+// a constant in the compute type: the double for FP64 kernels, its FP32 copy otherwise
+template <class C> __device__ __forceinline__ C prm(double d, float f);
+template <> __device__ __forceinline__ double prm<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float prm<float>(double, float f) { return f; }
 
 // One multigrid level (pressure-like fields).
 struct LevelDev {
@@ -62,8 +78,37 @@ struct LevelDev {
     double inv_h2[3];
     double inv_D;            // 1 / sum_active 2 / h_a^2
     double wJ;               // Jacobi weight
+    double diag;             // sum_active 2 / h_a^2 (A's diagonal away from boundaries)
+    float inv_h2f[3], inv_Df, wJf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
     const uint8_t* solid;    // nonzero = solid
     const uint8_t* dir[6];   // per boundary-face cell: 1 = Dirichlet (p = 0 on the face)
+    const uint16_t* nbf;     // per cell: 2 bits per face (x-,x+,y-,y+,z-,z+): 0 fluid neighbour,
+                             // 1 zero-gradient ghost, 2 zero-value ghost; bit 12: the cell is solid
+};
+
+// Device-side state of one pressure solve: the last residual norms and the
+// stopping rule, applied by the level-0 residual kernel.
+struct SolveState {
+    double r2, b2, rel;
+    double tol;
+    int32_t cycles;          // V-cycles started in this solve
+    int32_t active;          // 1 while another cycle runs
+    uint32_t counter;        // blocks finished (last-block reduction)
+    int32_t nonfinite;       // sticky flag: a non-finite norm was seen
+    int32_t total_cycles;    // summed over the current fvm_step call
+    int32_t max_cycles;
+    int32_t fixed;           // > 0: exactly this many cycles
+    int32_t notconv;         // sticky flag: a solve stopped at max_cycles above tol
+    int32_t inner;           // V-cycles per outer (FP64) residual
+    int32_t pad;
+};
+
+// Levels lc..L-1, cycled by one CTA in shared memory.
+struct CoarseLevels {
+    int32_t nl;              // number of levels handled
+    int32_t pre, post;
+    int32_t pad;
+    LevelDev lv[FVM_MAX_LEVELS];
 };
 
 // ---------------------------------------------------------------- helpers
@@ -88,6 +133,19 @@ template <class S, class C> __device__ __forceinline__ S from_c(C x) { return (S
 template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16, double>(double x) { return __float2bfloat16_rn((float)x); }
 
+// level parameters in the compute type (FP32 kernels read the FP32 copies)
+template <class C> struct LP;
+template <> struct LP<double> {
+    static __device__ __forceinline__ double ih2(const LevelDev& L, int a) { return L.inv_h2[a]; }
+    static __device__ __forceinline__ double iD(const LevelDev& L) { return L.inv_D; }
+    static __device__ __forceinline__ double wJ(const LevelDev& L) { return L.wJ; }
+};
+template <> struct LP<float> {
+    static __device__ __forceinline__ float ih2(const LevelDev& L, int a) { return L.inv_h2f[a]; }
+    static __device__ __forceinline__ float iD(const LevelDev& L) { return L.inv_Df; }
+    static __device__ __forceinline__ float wJ(const LevelDev& L) { return L.wJf; }
+};
+
 // ---------------------------------------------------------------- launchers
 struct StatePtrs {
     void* f[6];   // u, v, w, T, k, omega
@@ -108,22 +166,25 @@ cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, Stat
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 
-// multigrid kernels (mg_kernels.cu); inner = FVM_FP64 / FVM_FP32 (type of r, e on all levels),
-// bprec = storage type of b
-cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b,
-                          void* r, double* partials, int want_b2, cudaStream_t s, int* nblocks_out);
-cudaError_t launch_norm_finalize(const double* partials, int nblocks, int want_b2, double* out,
-                                 cudaStream_t s);
-cudaError_t launch_smooth_first(int inner, const LevelDev& L, const void* r, void* e, cudaStream_t s);
-cudaError_t launch_smooth(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
-                          cudaStream_t s);
-cudaError_t launch_smooth_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
+// multigrid kernels (mg_kernels.cu); inner = FVM_FP64 / FVM_FP32 / FVM_BF16_MIXED (type of r, e on all
+// levels), bprec = storage type of b
+cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s);
+cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
+                          double* partials, SolveState* st, cudaGraphConditionalHandle cond,
+                          cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s);
+cudaError_t launch_sweep_first(int inner, const LevelDev& L, const void* r, void* e, const SolveState* st,
                                cudaStream_t s);
-cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e,
-                                  const void* r, void* rc, cudaStream_t s);
+cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
+                         const SolveState* st, cudaStream_t s);
+cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
+                              const SolveState* st, cudaStream_t s);
+cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
+                                  void* rc, const SolveState* st, cudaStream_t s);
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
-                               cudaStream_t s);
-cudaError_t launch_coarse_solve(int inner, const LevelDev& Lc, const double* Ainv, const void* rc, void* ec,
-                                cudaStream_t s);
+                               const SolveState* st, cudaStream_t s);
+cudaError_t prepare_coarse_cta(int inner, size_t smem);
+cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_in, void* e_out, const double* Ainv,
+                              const SolveState* st, cudaStream_t s);
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
-int resid0_blocks(int64_t N);
+int resid0_blocks(int nx, int ny, int nz);
+size_t coarse_cta_smem(const CoarseLevels& cl, int inner);

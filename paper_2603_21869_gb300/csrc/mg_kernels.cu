@@ -4,233 +4,568 @@
 //
 // The solve runs in correction form: the level-0 residual r = b - A p is
 // formed from the FP64 pressure with an FP64 norm, a V-cycle computes the
-// correction e from A e = r in the inner precision (FP64, or FP32 for the
-// reduced-precision modes), and the last post-smoothing sweep adds e to p.
-// In exact arithmetic this is the V-cycle on p itself; in finite precision it
-// is defect correction with an FP64 outer residual.
+// correction e from A e = r in the inner precision (FP64, FP32 or BF16
+// storage), and the last post-smoothing sweep adds e to p.  In exact
+// arithmetic this is the V-cycle on p itself; in finite precision it is
+// defect correction with an FP64 outer residual.
 //
 //   smoother   e <- e + w_J (r - A e) / D, D = sum_active 2 / h_a^2
 //   RES        coarse r = mean of the children's residuals r - A e
 //   PROL       e += trilinear interpolation of the coarse correction:
 //              3/4 parent + 1/4 neighbour per axis, neighbour index clamped
 //   coarsest   e = A^{-1} r with the dense inverse built on the host
+//
+// Every cell carries a 16-bit neighbour code (two bits per face: 0 = fluid
+// neighbour, 1 = zero-gradient ghost, 2 = zero-value ghost; bit 12 = solid),
+// so the stencil needs one small load instead of mask and face-table lookups.
+// Grid kernels use 3D blocks (no integer division).  All levels that fit in
+// one CTA's shared memory are cycled by a single CTA.  The level-0 residual
+// kernel finishes the norm in its last block and decides on the device
+// whether another cycle runs, so the whole solve can live in a CUDA graph.
 #include "fvm_internal.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
-
-inline unsigned nblocks(int64_t N) { return (unsigned)((N + kThreads - 1) / kThreads); }
-
 template <class T> struct Acc { using type = T; };
 template <> struct Acc<__nv_bfloat16> { using type = float; };
 
-__device__ __forceinline__ void decode(const LevelDev& L, int64_t c, int& i, int& j, int& k) {
-    i = (int)(c % L.n[0]);
-    j = (int)((c / L.n[0]) % L.n[1]);
-    k = (int)(c / ((int64_t)L.n[0] * L.n[1]));
+constexpr int BX = 32, BY = 4, BZ = 2;
+constexpr int kCtaThreads = 1024;
+
+__device__ __forceinline__ bool cell3(const LevelDev& L, int& i, int& j, int& k) {
+    i = blockIdx.x * BX + threadIdx.x;
+    j = blockIdx.y * BY + threadIdx.y;
+    k = blockIdx.z * BZ + threadIdx.z;
+    return i < L.n[0] && j < L.n[1] && k < L.n[2];
 }
 
-// value across the face on `side` of cell (i,j,k) along `a`: neighbour,
-// Neumann ghost (= eP) at walls, inlets and solid cells, -eP on Dirichlet faces
-template <class T, class C>
-__device__ __forceinline__ C across(const LevelDev& L, const T* e, int i, int j, int k, int a, int side, C eP) {
-    int q[3] = {i, j, k};
-    q[a] += side;
-    if (q[a] < 0 || q[a] >= L.n[a]) {
-        const int face = 2 * a + (side > 0 ? 1 : 0);
-        return L.dir[face][face_index(a, i, j, k, L.n)] ? -eP : eP;
-    }
-    const int64_t c = cell_index(q[0], q[1], q[2], L.n[0], L.n[1]);
-    return L.solid[c] ? eP : to_c<C>(ldg(e + c));
+// value across one face: the neighbour (read through `get`, only for code 0),
+// the zero-gradient ghost eP or the zero-value ghost -eP
+template <class C, class G>
+__device__ __forceinline__ C nb_val(uint32_t code, int idx, C eP, G get) {
+    return code == 0 ? get(idx) : (code == 1 ? eP : -eP);
 }
 
-// (A e)(i,j,k) = sum_active (2 eP - eW - eE) / h_a^2
-template <class T, class C>
-__device__ __forceinline__ C apply_A(const LevelDev& L, const T* e, int i, int j, int k, C eP) {
+// (A e)_P = sum_active (2 eP - e_lo - e_hi) / h_a^2; get(q) reads e at cell q
+template <class C, class G>
+__device__ __forceinline__ C apply_A_with(const LevelDev& L, uint32_t f, int c, C eP, G get) {
+    const int sx = 1, sy = L.n[0], sz = L.n[0] * L.n[1];
     C acc = (C)0;
-    for (int a = 0; a < 3; ++a) {
-        if (!L.active[a]) continue;
-        const C w = across<T, C>(L, e, i, j, k, a, -1, eP);
-        const C E = across<T, C>(L, e, i, j, k, a, +1, eP);
-        acc += ((eP - w) + (eP - E)) * (C)L.inv_h2[a];
+    if (L.active[0]) {
+        const C lo = nb_val<C>(f & 3u, c - sx, eP, get), hi = nb_val<C>((f >> 2) & 3u, c + sx, eP, get);
+        acc += ((eP - lo) + (eP - hi)) * LP<C>::ih2(L, 0);
+    }
+    if (L.active[1]) {
+        const C lo = nb_val<C>((f >> 4) & 3u, c - sy, eP, get), hi = nb_val<C>((f >> 6) & 3u, c + sy, eP, get);
+        acc += ((eP - lo) + (eP - hi)) * LP<C>::ih2(L, 1);
+    }
+    if (L.active[2]) {
+        const C lo = nb_val<C>((f >> 8) & 3u, c - sz, eP, get), hi = nb_val<C>((f >> 10) & 3u, c + sz, eP, get);
+        acc += ((eP - lo) + (eP - hi)) * LP<C>::ih2(L, 2);
     }
     return acc;
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    return s;
+// A e for e in global memory (read-only path)
+template <class C, class T>
+__device__ __forceinline__ C apply_A(const LevelDev& L, uint32_t f, const T* e, int c, C eP) {
+    return apply_A_with<C>(L, f, c, eP, [&](int q) { return to_c<C>(ldg(e + q)); });
 }
 
-// level 0: r = b - A p (FP64 arithmetic), per-block sums of r^2 (and b^2)
+__device__ __forceinline__ bool is_solid(uint32_t f) { return (f >> 12) & 1u; }
+
+template <class C>
+__device__ __forceinline__ C sel(uint32_t code, C nb, C eP) {
+    return code == 0 ? nb : (code == 1 ? eP : -eP);
+}
+
+// A e at one cell from its gathered neighbours
+template <class C>
+__device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp, C ym, C yp, C zm, C zp) {
+    C acc = (C)0;
+    if (L.active[0]) acc += ((eP - sel(f & 3u, xm, eP)) + (eP - sel((f >> 2) & 3u, xp, eP))) * LP<C>::ih2(L, 0);
+    if (L.active[1]) acc += ((eP - sel((f >> 4) & 3u, ym, eP)) + (eP - sel((f >> 6) & 3u, yp, eP))) * LP<C>::ih2(L, 1);
+    if (L.active[2]) acc += ((eP - sel((f >> 8) & 3u, zm, eP)) + (eP - sel((f >> 10) & 3u, zp, eP))) * LP<C>::ih2(L, 2);
+    return acc;
+}
+
+// A p in FP64 with few FP64-pipe instructions: cells whose six faces all see fluid
+// neighbours (code bits zero) use diag p - sum_a ih2_a (lo + hi); others the general form
+__device__ __forceinline__ double A7_fp64(const LevelDev& L, uint32_t f, double eP, double xm, double xp,
+                                         double ym, double yp, double zm, double zp) {
+    if ((f & 0xFFFu) == 0u) {
+        double acc = 0.0;
+        if (L.active[0]) acc = (xm + xp) * L.inv_h2[0];
+        if (L.active[1]) acc = fma(ym + yp, L.inv_h2[1], acc);
+        if (L.active[2]) acc = fma(zm + zp, L.inv_h2[2], acc);
+        return fma(L.diag, eP, -acc);
+    }
+    return A7<double>(L, f, eP, xm, xp, ym, yp, zm, zp);
+}
+
+
+// ------------------------------------------------------------------ level 0 residual
+// r = b - A p (FP64), first pre-sweep e = w_J r / D, r^2 and b^2 per block;
+// the last block sums the partials in a fixed order and applies the stopping rule.
 template <class TB, class TI>
-__global__ void k_resid0(LevelDev L, const double* __restrict__ p, const TB* __restrict__ b, TI* __restrict__ r,
-                         double* __restrict__ partials, int want_b2) {
-    __shared__ double red[kThreads / 32];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double r2 = 0.0, b2 = 0.0;
-    if (c < L.N) {
-        double rv = 0.0;
-        if (!L.solid[c]) {
-            int i, j, k;
-            decode(L, c, i, j, k);
-            const double bv = to_c<double>(ldg(b + c));
-            rv = bv - apply_A<double, double>(L, p, i, j, k, __ldg(p + c));
-            b2 = bv * bv;
-        }
-        r[c] = from_c<TI, double>(rv);
-        r2 = rv * rv;
-    }
-    const double s = block_sum(r2, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-    if (want_b2) {
-        const double t = block_sum(b2, red);
-        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = t;
-    }
-}
-
-// fixed-order sum of the per-block partials (deterministic norms)
-__global__ void k_norm_finalize(const double* __restrict__ partials, int nb, int want_b2, double* out) {
-    __shared__ double red[kThreads / 32];
-    double a = 0.0, b = 0.0;
-    for (int x = threadIdx.x; x < nb; x += blockDim.x) {
-        a += partials[x];
-        if (want_b2) b += partials[nb + x];
-    }
-    const double sa = block_sum(a, red);
-    const double sb = block_sum(b, red);
-    if (threadIdx.x == 0) {
-        out[0] = sa;
-        if (want_b2) out[1] = sb;
-    }
-}
-
-// first sweep from e = 0: e = w_J r / D
-template <class TI>
-__global__ void k_smooth_first(LevelDev L, const TI* __restrict__ r, TI* __restrict__ e) {
+__global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const double* __restrict__ p,
+                                                          const TB* __restrict__ b, TI* __restrict__ r,
+                                                          TI* __restrict__ e, double* __restrict__ partials,
+                                                          SolveState* st, cudaGraphConditionalHandle cond,
+                                                          cudaGraphConditionalHandle cond2, int use_cond) {
     using C = typename Acc<TI>::type;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.N) return;
-    C v = (C)0;
-    if (!L.solid[c]) v = (C)L.wJ * to_c<C>(ldg(r + c)) * (C)L.inv_D;
-    e[c] = from_c<TI, C>(v);
-}
-
-template <class TI>
-__global__ void k_smooth(LevelDev L, const TI* __restrict__ ein, const TI* __restrict__ r, TI* __restrict__ eout) {
-    using C = typename Acc<TI>::type;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.N) return;
-    C v = (C)0;
-    if (!L.solid[c]) {
-        int i, j, k;
-        decode(L, c, i, j, k);
-        const C eP = to_c<C>(ldg(ein + c));
-        v = eP + (C)L.wJ * (to_c<C>(ldg(r + c)) - apply_A<TI, C>(L, ein, i, j, k, eP)) * (C)L.inv_D;
-    }
-    eout[c] = from_c<TI, C>(v);
-}
-
-// last level-0 sweep: p += e + w_J (r - A e) / D
-template <class TI>
-__global__ void k_smooth_to_p(LevelDev L, const TI* __restrict__ ein, const TI* __restrict__ r,
-                              double* __restrict__ p) {
-    using C = typename Acc<TI>::type;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.N) return;
-    if (L.solid[c]) return;
+    __shared__ double red[2][BX * BY * BZ / 32];
+    __shared__ bool last;
     int i, j, k;
-    decode(L, c, i, j, k);
-    const C eP = to_c<C>(ldg(ein + c));
-    const C v = eP + (C)L.wJ * (to_c<C>(ldg(r + c)) - apply_A<TI, C>(L, ein, i, j, k, eP)) * (C)L.inv_D;
-    p[c] += (double)v;
+    C r2 = (C)0, b2 = (C)0;     // squares and warp sums in the inner precision, block sums in FP64
+    if (cell3(L, i, j, k)) {
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        const uint32_t f = L.nbf[c];
+        // neighbour loads first (clamped indices), then the FP64 stencil
+        const int sy = L.n[0], sz = L.n[0] * L.n[1];
+        const double pP = __ldg(p + c);
+        const double xm = __ldg(p + c - (i > 0 ? 1 : 0)), xp = __ldg(p + c + (i < L.n[0] - 1 ? 1 : 0));
+        const double ym = __ldg(p + c - (j > 0 ? sy : 0)), yp = __ldg(p + c + (j < L.n[1] - 1 ? sy : 0));
+        const double zm = __ldg(p + c - (k > 0 ? sz : 0)), zp = __ldg(p + c + (k < L.n[2] - 1 ? sz : 0));
+        const TB braw = ldg(b + c);
+        C rc = (C)0, bc = (C)0;
+        if (!is_solid(f)) {
+            const double bv = to_c<double>(braw);
+            const double Ap = A7_fp64(L, f, pP, xm, xp, ym, yp, zm, zp);
+            const TI rs = from_c<TI, double>(bv - Ap);
+            r[c] = rs;
+            rc = to_c<C>(rs);
+            bc = to_c<C>(braw);
+            e[c] = from_c<TI, C>(LP<C>::wJ(L) * rc * LP<C>::iD(L));
+        } else {
+            r[c] = from_c<TI, C>((C)0);
+            e[c] = from_c<TI, C>((C)0);
+        }
+        r2 = rc * rc;
+        b2 = bc * bc;
+    }
+    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    for (int off = 16; off > 0; off >>= 1) {
+        r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, off);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = (double)r2;
+        red[1][tid >> 5] = (double)b2;
+    }
+    __syncthreads();
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < BX * BY * BZ / 32; ++w) {
+            s0 += red[0][w];
+            s1 += red[1][w];
+        }
+        partials[2 * bid] = s0;
+        partials[2 * bid + 1] = s1;
+        __threadfence();
+        const unsigned done = atomicAdd(&st->counter, 1u);
+        last = done == (unsigned)nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // fixed-order reduction over all blocks' partials by the whole last block:
+    // thread t sums blocks t, t + 256, ... in order (L2 loads, independent), then a
+    // fixed shuffle tree and a fixed sum over warps -> deterministic
+    constexpr int NT = BX * BY * BZ;
+    double a0 = 0.0, a1 = 0.0;
+    for (int x = tid; x < nblk; x += NT) {
+        const double2 v = __ldcg((const double2*)partials + x);
+        a0 += v.x;
+        a1 += v.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a0;
+        red[1][tid >> 5] = a1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a0 = 0.0;
+        a1 = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            a0 += red[0][w];
+            a1 += red[1][w];
+        }
+        st->counter = 0u;
+        st->r2 = a0;
+        st->b2 = a1;
+        const bool finite = isfinite(a0) && isfinite(a1);
+        const double rel = a1 > 0.0 ? sqrt(a0 / a1) : 0.0;
+        st->rel = finite ? rel : __longlong_as_double(0x7ff8000000000000ll);
+        if (!finite) st->nonfinite = 1;
+        int go;
+        if (st->fixed > 0) go = st->cycles < st->fixed;
+        else go = finite && rel > st->tol && st->cycles < st->max_cycles;
+        st->active = go;
+        if (!go && st->fixed == 0 && finite && rel > st->tol) st->notconv = 1;
+        if (go) {
+            st->cycles += st->inner;
+            st->total_cycles += st->inner;
+        }
+        if (use_cond) {
+            cudaGraphSetConditional(cond, go ? 1u : 0u);
+            if (use_cond > 1) cudaGraphSetConditional(cond2, go ? 1u : 0u);
+        }
+    }
+}
+
+__global__ void k_solve_begin(SolveState* st) {
+    st->cycles = 0;
+    st->counter = 0u;
+    st->active = 1;
+}
+
+// ------------------------------------------------------------------ grid kernels (one level)
+template <class TI>
+__global__ void __launch_bounds__(BX * BY * BZ) k_sweep_first(LevelDev L, const TI* __restrict__ r,
+                                                               TI* __restrict__ e, const SolveState* st) {
+    using C = typename Acc<TI>::type;
+    if (!st->active) return;
+    int i, j, k;
+    if (!cell3(L, i, j, k)) return;
+    const int c = i + L.n[0] * (j + L.n[1] * k);
+    const uint32_t f = L.nbf[c];
+    e[c] = from_c<TI, C>(is_solid(f) ? (C)0 : LP<C>::wJ(L) * to_c<C>(ldg(r + c)) * LP<C>::iD(L));
 }
 
 // coarse r = mean over the children of (r - A e); one thread per coarse cell
 template <class TI>
-__global__ void k_resid_restrict(LevelDev Lf, LevelDev Lc, const TI* __restrict__ e, const TI* __restrict__ r,
-                                 TI* __restrict__ rc) {
+__global__ void __launch_bounds__(BX * BY * BZ) k_resid_restrict(LevelDev Lf, LevelDev Lc, const TI* __restrict__ e,
+                                                                  const TI* __restrict__ r, TI* __restrict__ rc,
+                                                                  const SolveState* st) {
     using C = typename Acc<TI>::type;
-    const int64_t cc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cc >= Lc.N) return;
+    if (!st->active) return;
     int I, J, K;
-    decode(Lc, cc, I, J, K);
+    if (!cell3(Lc, I, J, K)) return;
     const int fx = Lf.active[0] ? 2 : 1, fy = Lf.active[1] ? 2 : 1, fz = Lf.active[2] ? 2 : 1;
     C sum = (C)0;
     for (int dz = 0; dz < fz; ++dz)
         for (int dy = 0; dy < fy; ++dy)
             for (int dx = 0; dx < fx; ++dx) {
-                const int i = I * fx + dx, j = J * fy + dy, k = K * fz + dz;
-                const int64_t c = cell_index(i, j, k, Lf.n[0], Lf.n[1]);
-                if (Lf.solid[c]) continue;
+                const int c = (I * fx + dx) + Lf.n[0] * ((J * fy + dy) + Lf.n[1] * (K * fz + dz));
+                const uint32_t f = Lf.nbf[c];
+                if (is_solid(f)) continue;
                 const C eP = to_c<C>(ldg(e + c));
-                sum += to_c<C>(ldg(r + c)) - apply_A<TI, C>(Lf, e, i, j, k, eP);
+                sum += to_c<C>(ldg(r + c)) - apply_A<C>(Lf, f, e, c, eP);
             }
-    rc[cc] = from_c<TI, C>(sum / (C)(fx * fy * fz));
+    rc[I + Lc.n[0] * (J + Lc.n[1] * K)] = from_c<TI, C>(sum / (C)(fx * fy * fz));
 }
 
-// e += PROL(ec) on fluid fine cells
-template <class TI>
-__global__ void k_prolong_add(LevelDev Lf, LevelDev Lc, const TI* __restrict__ ec, TI* __restrict__ e) {
-    using C = typename Acc<TI>::type;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Lf.N) return;
-    if (Lf.solid[c]) return;
-    int i, j, k;
-    decode(Lf, c, i, j, k);
+// trilinear prolongation of a coarse field at fine cell (i,j,k)
+template <class C, class G>
+__device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int j, int k, G get) {
     const int f[3] = {i, j, k};
-    int P[3], Nb[3];
+    int P[3], Q[3];
+    C w[3][2];
     for (int a = 0; a < 3; ++a) {
-        if (Lf.active[a]) {
+        if (fa[a]) {
             P[a] = f[a] >> 1;
-            const int s = (f[a] & 1) ? 1 : -1;
-            int q = P[a] + s;
-            q = q < 0 ? 0 : (q >= Lc.n[a] ? Lc.n[a] - 1 : q);
-            Nb[a] = q;
+            int q = P[a] + ((f[a] & 1) ? 1 : -1);
+            Q[a] = q < 0 ? 0 : (q >= cn[a] ? cn[a] - 1 : q);
+            w[a][0] = (C)0.75;
+            w[a][1] = (C)0.25;
         } else {
-            P[a] = f[a];
-            Nb[a] = f[a];
+            P[a] = Q[a] = f[a];
+            w[a][0] = (C)1;
+            w[a][1] = (C)0;
         }
     }
     C acc = (C)0;
-    for (int sz = 0; sz < 2; ++sz) {
-        if (sz && !Lf.active[2]) break;
-        const int kk = sz ? Nb[2] : P[2];
-        const C wz = Lf.active[2] ? (sz ? (C)0.25 : (C)0.75) : (C)1;
-        for (int sy = 0; sy < 2; ++sy) {
-            if (sy && !Lf.active[1]) break;
-            const int jj = sy ? Nb[1] : P[1];
-            const C wy = Lf.active[1] ? (sy ? (C)0.25 : (C)0.75) : (C)1;
-            for (int sx = 0; sx < 2; ++sx) {
-                if (sx && !Lf.active[0]) break;
-                const int ii = sx ? Nb[0] : P[0];
-                const C wx = Lf.active[0] ? (sx ? (C)0.25 : (C)0.75) : (C)1;
-                acc += wx * wy * wz * to_c<C>(ldg(ec + cell_index(ii, jj, kk, Lc.n[0], Lc.n[1])));
+    for (int sz = 0; sz < (fa[2] ? 2 : 1); ++sz)
+        for (int sy = 0; sy < (fa[1] ? 2 : 1); ++sy)
+            for (int sx = 0; sx < (fa[0] ? 2 : 1); ++sx) {
+                const int ii = sx ? Q[0] : P[0], jj = sy ? Q[1] : P[1], kk = sz ? Q[2] : P[2];
+                acc += w[0][sx] * w[1][sy] * w[2][sz] * get(ii + cn[0] * (jj + cn[1] * kk));
             }
-        }
-    }
-    e[c] = from_c<TI, C>(to_c<C>(e[c]) + acc);
+    return acc;
 }
 
-// coarsest level: e = A^{-1} r (row-major dense inverse, FP64), one block
 template <class TI>
-__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const TI* __restrict__ rc,
-                               TI* __restrict__ ec) {
-    __shared__ double rs[FVM_MAX_COARSE];
-    for (int x = threadIdx.x; x < n; x += blockDim.x) rs[x] = to_c<double>(rc[x]);
+__global__ void __launch_bounds__(BX * BY * BZ) k_prolong_add(LevelDev Lf, LevelDev Lc, const TI* __restrict__ ec,
+                                                               TI* __restrict__ e, const SolveState* st) {
+    using C = typename Acc<TI>::type;
+    if (!st->active) return;
+    int i, j, k;
+    if (!cell3(Lf, i, j, k)) return;
+    const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
+    if (is_solid(Lf.nbf[c])) return;
+    const C add = prolong_at<C>(Lf.active, Lc.n, i, j, k, [&](int q) { return to_c<C>(ldg(ec + q)); });
+    e[c] = from_c<TI, C>(to_c<C>(e[c]) + add);
+}
+
+// ------------------------------------------------------------------ marching kernels (levels >= 0)
+// Block TX x TY threads; each thread walks KZ cells along z, keeping the z
+// neighbours in registers.  Neighbour loads use indices clamped into the
+// grid (a face outside the domain reads the cell itself) and are issued
+// before the neighbour code is consulted; the code then selects the
+// neighbour, the zero-gradient ghost or the zero-value ghost.
+constexpr int TX = 32, TY = 8;
+constexpr int kWalkMinCells = 1 << 20;   // below this a thread takes one cell (more blocks)
+
+struct Walk {
+    int i, j, k0, sy, sz, im, ip, jm, jp;
+};
+
+__device__ __forceinline__ bool walk_setup(const LevelDev& L, int kz, Walk& w) {
+    w.i = blockIdx.x * TX + threadIdx.x;
+    w.j = blockIdx.y * TY + threadIdx.y;
+    w.k0 = blockIdx.z * kz;
+    if (w.i >= L.n[0] || w.j >= L.n[1]) return false;
+    w.sy = L.n[0];
+    w.sz = L.n[0] * L.n[1];
+    w.im = w.i > 0 ? -1 : 0;
+    w.ip = w.i < L.n[0] - 1 ? 1 : 0;
+    w.jm = w.j > 0 ? -w.sy : 0;
+    w.jp = w.j < L.n[1] - 1 ? w.sy : 0;
+    return true;
+}
+
+// MODE 0: eout = sweep(ein); MODE 1: p += sweep(ein) (last level-0 sweep).
+// All loads of the thread's KZ cells are issued before any arithmetic.
+template <class TI, int MODE, int KZ>
+__global__ void __launch_bounds__(TX * TY) k_sweep_walk(LevelDev L, const TI* __restrict__ ein,
+                                                        const TI* __restrict__ r, TI* __restrict__ eout,
+                                                        double* __restrict__ p, const SolveState* st) {
+    using C = typename Acc<TI>::type;
+    if (!st->active) return;
+    Walk w;
+    if (!walk_setup(L, KZ, w)) return;
+    const int nz = L.n[2];
+    const int c0 = w.i + w.sy * w.j + w.sz * w.k0;
+    const int kn = nz - w.k0 < KZ ? nz - w.k0 : KZ;   // cells of this thread
+    C col[KZ + 2], xm[KZ], xp[KZ], ym[KZ], yp[KZ], rr[KZ];
+    uint32_t f[KZ];
+    col[0] = to_c<C>(ldg(ein + c0 - (w.k0 > 0 ? w.sz : 0)));
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk) {
+        if (kk < kn) {
+            const int c = c0 + kk * w.sz;
+            col[kk + 1] = to_c<C>(ldg(ein + c));
+            xm[kk] = to_c<C>(ldg(ein + c + w.im));
+            xp[kk] = to_c<C>(ldg(ein + c + w.ip));
+            ym[kk] = to_c<C>(ldg(ein + c + w.jm));
+            yp[kk] = to_c<C>(ldg(ein + c + w.jp));
+            rr[kk] = to_c<C>(ldg(r + c));
+            f[kk] = L.nbf[c];
+            if (kk == kn - 1)   // the plane above the thread's last cell (itself at the top face)
+                col[kk + 2] = w.k0 + kk < nz - 1 ? to_c<C>(ldg(ein + c + w.sz)) : col[kk + 1];
+        }
+    }
+    const C wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk) {
+        if (kk < kn) {
+            const int c = c0 + kk * w.sz;
+            const C eP = col[kk + 1];
+            const bool solid = is_solid(f[kk]);
+            const C v = solid ? (C)0
+                              : eP + wJ * (rr[kk] - A7<C>(L, f[kk], eP, xm[kk], xp[kk], ym[kk], yp[kk], col[kk],
+                                                          col[kk + 2])) * iD;
+            if (MODE == 0) eout[c] = from_c<TI, C>(v);
+            else if (!solid) p[c] += (double)v;
+        }
+    }
+}
+
+// coarse r = mean of the children's (r - A e): one thread per fine cell (the
+// z pair of children in the thread), x / y pairs summed through shared memory.
+// Needs x and y active (2 x 2 children in the plane).
+template <class TI>
+__global__ void __launch_bounds__(TX * TY) k_resid_restrict_walk(LevelDev Lf, LevelDev Lc, const TI* __restrict__ e,
+                                                                 const TI* __restrict__ r, TI* __restrict__ rc,
+                                                                 const SolveState* st) {
+    using C = typename Acc<TI>::type;
+    __shared__ C part[TY][TX + 1];
+    if (!st->active) return;
+    const int fz = Lf.active[2] ? 2 : 1;
+    Walk w;
+    const bool in = walk_setup(Lf, fz, w);
+    C sum = (C)0;
+    if (in) {
+        const int nz = Lf.n[2];
+        int c = w.i + w.sy * w.j + w.sz * w.k0;
+        for (int kk = 0; kk < fz; ++kk) {
+            const int k = w.k0 + kk;
+            const uint32_t f = Lf.nbf[c];
+            const C eP = to_c<C>(ldg(e + c));
+            const C zm = k > 0 ? to_c<C>(ldg(e + c - w.sz)) : eP;
+            const C zp = k < nz - 1 ? to_c<C>(ldg(e + c + w.sz)) : eP;
+            const C xm = to_c<C>(ldg(e + c + w.im)), xp = to_c<C>(ldg(e + c + w.ip));
+            const C ym = to_c<C>(ldg(e + c + w.jm)), yp = to_c<C>(ldg(e + c + w.jp));
+            const C rr = to_c<C>(ldg(r + c));
+            if (!is_solid(f)) sum += rr - A7<C>(Lf, f, eP, xm, xp, ym, yp, zm, zp);
+            c += w.sz;
+        }
+    }
+    part[threadIdx.y][threadIdx.x] = sum;
     __syncthreads();
-    for (int row = threadIdx.x; row < n; row += blockDim.x) {
-        double acc = 0.0;
-        const double* a = Ainv + (int64_t)row * n;
-        for (int col = 0; col < n; ++col) acc += a[col] * rs[col];
-        ec[row] = from_c<TI, double>(acc);
+    if (threadIdx.x < TX / 2 && threadIdx.y < TY / 2) {
+        const int I = blockIdx.x * (TX / 2) + threadIdx.x, J = blockIdx.y * (TY / 2) + threadIdx.y;
+        if (I < Lc.n[0] && J < Lc.n[1]) {
+            const int x = 2 * threadIdx.x, y = 2 * threadIdx.y;
+            const C s4 = (part[y][x] + part[y][x + 1]) + (part[y + 1][x] + part[y + 1][x + 1]);
+            rc[I + Lc.n[0] * (J + Lc.n[1] * blockIdx.z)] = from_c<TI, C>(s4 / (C)(4 * fz));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ coarse levels in one CTA
+// V-cycle over levels lc..L-1 in shared memory: reads r on level lc from
+// global memory, writes the correction e on level lc.
+template <class C>
+__device__ __forceinline__ C cta_apply_A(const LevelDev& L, uint32_t f, const C* e, int c, C eP) {
+    // e lives in shared memory: plain loads (the read-only global path does not apply)
+    return apply_A_with<C>(L, f, c, eP, [&](int q) { return e[q]; });
+}
+
+template <class TI>
+__global__ void __launch_bounds__(kCtaThreads) k_coarse_cta(CoarseLevels cl, const TI* __restrict__ r_in,
+                                                             TI* __restrict__ e_out, const double* __restrict__ Ainv,
+                                                             const SolveState* st) {
+    using C = typename Acc<TI>::type;
+    if (!st->active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // level descriptions and array bases live in shared memory (one copy per CTA)
+    __shared__ LevelDev lvs[FVM_MAX_LEVELS];
+    __shared__ C* E0[FVM_MAX_LEVELS];
+    __shared__ C* E1[FVM_MAX_LEVELS];
+    __shared__ C* R[FVM_MAX_LEVELS];
+    __shared__ uint16_t* F[FVM_MAX_LEVELS];
+    const int T = blockDim.x, tid = threadIdx.x;
+    if (tid == 0) {
+        C* q = (C*)smem_raw;
+        for (int l = 0; l < cl.nl; ++l) {
+            const int N = (int)cl.lv[l].N;
+            E0[l] = q; q += N;
+            E1[l] = q; q += N;
+            R[l] = q; q += N;
+        }
+        uint16_t* u = (uint16_t*)q;
+        for (int l = 0; l < cl.nl; ++l) {
+            F[l] = u;
+            u += cl.lv[l].N;
+            lvs[l] = cl.lv[l];
+            lvs[l].nbf = F[l];
+        }
+    }
+    __syncthreads();
+    for (int l = 0; l < cl.nl; ++l) {
+        const int N = (int)cl.lv[l].N;
+        for (int c = tid; c < N; c += T) F[l][c] = cl.lv[l].nbf[c];
+    }
+    {
+        const int N0 = (int)cl.lv[0].N;
+        for (int c = tid; c < N0; c += T) R[0][c] = to_c<C>(r_in[c]);
+    }
+    __syncthreads();
+    __shared__ int cur[FVM_MAX_LEVELS];
+    // down: pre-smooth, restrict
+    for (int l = 0; l + 1 < cl.nl; ++l) {
+        const LevelDev& L = lvs[l];
+        const int N = (int)L.N;
+        const C w = LP<C>::wJ(L), iD = LP<C>::iD(L);
+        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(L.nbf[c]) ? (C)0 : w * R[l][c] * iD;
+        __syncthreads();
+        int s = 0;
+        for (int it = 1; it < cl.pre; ++it) {
+            C* ein = s ? E1[l] : E0[l];
+            C* eo = s ? E0[l] : E1[l];
+            for (int c = tid; c < N; c += T) {
+                const uint32_t f = L.nbf[c];
+                C v = (C)0;
+                if (!is_solid(f)) {
+                    const C eP = ein[c];
+                    v = eP + w * (R[l][c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
+                }
+                eo[c] = v;
+            }
+            s ^= 1;
+            __syncthreads();
+        }
+        if (tid == 0) cur[l] = s;
+        const LevelDev& Lc = lvs[l + 1];
+        const C* e = s ? E1[l] : E0[l];
+        const int fx = L.active[0] ? 2 : 1, fy = L.active[1] ? 2 : 1, fz = L.active[2] ? 2 : 1;
+        const int Nc = (int)Lc.N;
+        for (int cc = tid; cc < Nc; cc += T) {
+            const int I = cc % Lc.n[0], J = (cc / Lc.n[0]) % Lc.n[1], K = cc / (Lc.n[0] * Lc.n[1]);
+            C sum = (C)0;
+            for (int dz = 0; dz < fz; ++dz)
+                for (int dy = 0; dy < fy; ++dy)
+                    for (int dx = 0; dx < fx; ++dx) {
+                        const int c = (I * fx + dx) + L.n[0] * ((J * fy + dy) + L.n[1] * (K * fz + dz));
+                        const uint32_t f = L.nbf[c];
+                        if (is_solid(f)) continue;
+                        sum += R[l][c] - cta_apply_A<C>(L, f, e, c, e[c]);
+                    }
+            R[l + 1][cc] = sum / (C)(fx * fy * fz);
+        }
+        __syncthreads();
+    }
+    // coarsest: dense solve, one warp per row (coalesced reads of the inverse)
+    {
+        const int l = cl.nl - 1;
+        const int N = (int)lvs[l].N;
+        const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+        for (int row = warp; row < N; row += nw) {
+            double acc = 0.0;
+            const double* a = Ainv + (size_t)row * N;
+            for (int col = lane; col < N; col += 32) acc += __ldg(a + col) * (double)R[l][col];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) E0[l][row] = (C)acc;
+        }
+        if (tid == 0) cur[l] = 0;
+        __syncthreads();
+    }
+    // up: prolong, post-smooth
+    for (int l = cl.nl - 2; l >= 0; --l) {
+        const LevelDev& L = lvs[l];
+        const LevelDev& Lc = lvs[l + 1];
+        const int N = (int)L.N;
+        const C* ec = cur[l + 1] ? E1[l + 1] : E0[l + 1];
+        C* e = cur[l] ? E1[l] : E0[l];
+        for (int c = tid; c < N; c += T) {
+            if (is_solid(L.nbf[c])) continue;
+            const int i = c % L.n[0], j = (c / L.n[0]) % L.n[1], k = c / (L.n[0] * L.n[1]);
+            e[c] += prolong_at<C>(L.active, Lc.n, i, j, k, [&](int q) { return ec[q]; });
+        }
+        __syncthreads();
+        int s = cur[l];
+        const C w = LP<C>::wJ(L), iD = LP<C>::iD(L);
+        for (int it = 0; it < cl.post; ++it) {
+            C* ein = s ? E1[l] : E0[l];
+            C* eo = s ? E0[l] : E1[l];
+            for (int c = tid; c < N; c += T) {
+                const uint32_t f = L.nbf[c];
+                C v = (C)0;
+                if (!is_solid(f)) {
+                    const C eP = ein[c];
+                    v = eP + w * (R[l][c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
+                }
+                eo[c] = v;
+            }
+            s ^= 1;
+            __syncthreads();
+        }
+        if (tid == 0) cur[l] = s;
+        __syncthreads();
+    }
+    {
+        const C* e = cur[0] ? E1[0] : E0[0];
+        const int N0 = (int)lvs[0].N;
+        for (int c = tid; c < N0; c += T) e_out[c] = from_c<TI, C>(e[c]);
     }
 }
 
@@ -240,79 +575,125 @@ __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, int64_
     if (c < N) dst[c] = from_c<B, double>(to_c<double>(src[c]));
 }
 
+dim3 grid3(const LevelDev& L) {
+    return dim3((unsigned)((L.n[0] + BX - 1) / BX), (unsigned)((L.n[1] + BY - 1) / BY),
+                (unsigned)((L.n[2] + BZ - 1) / BZ));
+}
+const dim3 kBlock3(BX, BY, BZ);
+
 }  // namespace
 
-int resid0_blocks(int64_t N) { return (int)nblocks(N); }
+int resid0_blocks(int nx, int ny, int nz) {
+    return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + BZ - 1) / BZ);
+}
 
-#define DISPATCH_I(inner, ...)                                        \
-    do {                                                              \
-        if ((inner) == FVM_FP64) { using TI = double; __VA_ARGS__; }  \
+size_t coarse_cta_smem(const CoarseLevels& cl, int inner) {
+    const size_t cs = inner == FVM_FP64 ? 8 : 4;
+    size_t n = 0, m = 0;
+    for (int l = 0; l < cl.nl; ++l) {
+        n += 3 * (size_t)cl.lv[l].N;
+        m += (size_t)cl.lv[l].N;
+    }
+    return n * cs + m * 2 + 16;
+}
+
+#define DISPATCH_I(inner, ...)                                            \
+    do {                                                                  \
+        if ((inner) == FVM_FP64) { using TI = double; __VA_ARGS__; }      \
         else if ((inner) == FVM_FP32) { using TI = float; __VA_ARGS__; } \
-        else { using TI = __nv_bfloat16; __VA_ARGS__; }               \
+        else { using TI = __nv_bfloat16; __VA_ARGS__; }                   \
     } while (0)
 
-cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r,
-                          double* partials, int want_b2, cudaStream_t s, int* nblocks_out) {
-    const unsigned nb = nblocks(L.N);
-    if (nblocks_out) *nblocks_out = (int)nb;
+cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
+    k_solve_begin<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
+                          double* partials, SolveState* st, cudaGraphConditionalHandle cond,
+                          cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
     DISPATCH_I(inner, {
         if (bprec == FVM_FP64)
-            k_resid0<double, TI><<<nb, kThreads, 0, s>>>(L, p, (const double*)b, (TI*)r, partials, want_b2);
-        else if (bprec == FVM_FP32)
-            k_resid0<float, TI><<<nb, kThreads, 0, s>>>(L, p, (const float*)b, (TI*)r, partials, want_b2);
+            k_resid0<double, TI><<<grid3(L), kBlock3, 0, s>>>(L, p, (const double*)b, (TI*)r, (TI*)e, partials, st,
+                                                              cond, cond2, use_cond);
         else
-            k_resid0<__nv_bfloat16, TI><<<nb, kThreads, 0, s>>>(L, p, (const __nv_bfloat16*)b, (TI*)r, partials,
-                                                                 want_b2);
+            k_resid0<float, TI><<<grid3(L), kBlock3, 0, s>>>(L, p, (const float*)b, (TI*)r, (TI*)e, partials, st,
+                                                             cond, cond2, use_cond);
     });
     return cudaGetLastError();
 }
 
-cudaError_t launch_norm_finalize(const double* partials, int nb, int want_b2, double* out, cudaStream_t s) {
-    k_norm_finalize<<<1, kThreads, 0, s>>>(partials, nb, want_b2, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_smooth_first(int inner, const LevelDev& L, const void* r, void* e, cudaStream_t s) {
-    DISPATCH_I(inner, k_smooth_first<TI><<<nblocks(L.N), kThreads, 0, s>>>(L, (const TI*)r, (TI*)e));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_smooth(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
-                          cudaStream_t s) {
-    DISPATCH_I(inner, k_smooth<TI><<<nblocks(L.N), kThreads, 0, s>>>(L, (const TI*)e_in, (const TI*)r,
-                                                                      (TI*)e_out));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_smooth_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
+cudaError_t launch_sweep_first(int inner, const LevelDev& L, const void* r, void* e, const SolveState* st,
                                cudaStream_t s) {
-    DISPATCH_I(inner, k_smooth_to_p<TI><<<nblocks(L.N), kThreads, 0, s>>>(L, (const TI*)e_in, (const TI*)r, p));
+    DISPATCH_I(inner, k_sweep_first<TI><<<grid3(L), kBlock3, 0, s>>>(L, (const TI*)r, (TI*)e, st));
+    return cudaGetLastError();
+}
+
+static dim3 walk_grid(const LevelDev& L, int kz) {
+    return dim3((unsigned)((L.n[0] + TX - 1) / TX), (unsigned)((L.n[1] + TY - 1) / TY),
+                (unsigned)((L.n[2] + kz - 1) / kz));
+}
+
+template <class TI, int MODE>
+static void sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p, const SolveState* st,
+                       cudaStream_t s) {
+    if (L.N >= kWalkMinCells)
+        k_sweep_walk<TI, MODE, 4><<<walk_grid(L, 4), dim3(TX, TY), 0, s>>>(L, ein, r, eout, p, st);
+    else
+        k_sweep_walk<TI, MODE, 1><<<walk_grid(L, 1), dim3(TX, TY), 0, s>>>(L, ein, r, eout, p, st);
+}
+
+cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
+                         const SolveState* st, cudaStream_t s) {
+    DISPATCH_I(inner, sweep_walk<TI, 0>(L, (const TI*)e_in, (const TI*)r, (TI*)e_out, nullptr, st, s));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
+                              const SolveState* st, cudaStream_t s) {
+    DISPATCH_I(inner, sweep_walk<TI, 1>(L, (const TI*)e_in, (const TI*)r, nullptr, p, st, s));
     return cudaGetLastError();
 }
 
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
-                                  void* rc, cudaStream_t s) {
-    DISPATCH_I(inner, k_resid_restrict<TI><<<nblocks(Lc.N), kThreads, 0, s>>>(Lf, Lc, (const TI*)e,
-                                                                               (const TI*)r, (TI*)rc));
+                                  void* rc, const SolveState* st, cudaStream_t s) {
+    if (Lf.active[0] && Lf.active[1]) {
+        const int fz = Lf.active[2] ? 2 : 1;
+        DISPATCH_I(inner, k_resid_restrict_walk<TI><<<walk_grid(Lf, fz), dim3(TX, TY), 0, s>>>(
+                              Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st));
+    } else {
+        DISPATCH_I(inner, k_resid_restrict<TI><<<grid3(Lc), kBlock3, 0, s>>>(Lf, Lc, (const TI*)e, (const TI*)r,
+                                                                              (TI*)rc, st));
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
-                               cudaStream_t s) {
-    DISPATCH_I(inner, k_prolong_add<TI><<<nblocks(Lf.N), kThreads, 0, s>>>(Lf, Lc, (const TI*)ec, (TI*)e));
+                               const SolveState* st, cudaStream_t s) {
+    DISPATCH_I(inner, k_prolong_add<TI><<<grid3(Lf), kBlock3, 0, s>>>(Lf, Lc, (const TI*)ec, (TI*)e, st));
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(int inner, const LevelDev& Lc, const double* Ainv, const void* rc, void* ec,
-                                cudaStream_t s) {
-    DISPATCH_I(inner, k_coarse_solve<TI><<<1, kThreads, 0, s>>>((int)Lc.N, Ainv, (const TI*)rc, (TI*)ec));
+cudaError_t prepare_coarse_cta(int inner, size_t smem) {
+    DISPATCH_I(inner, {
+        cudaError_t err = cudaFuncSetAttribute(k_coarse_cta<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    });
+    return cudaSuccess;
+}
+
+cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_in, void* e_out, const double* Ainv,
+                              const SolveState* st, cudaStream_t s) {
+    const size_t smem = coarse_cta_smem(cl, inner);
+    DISPATCH_I(inner, k_coarse_cta<TI><<<1, kCtaThreads, smem, s>>>(cl, (const TI*)r_in, (TI*)e_out, Ainv, st));
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert(int sp, int dp, const void* src, void* dst, int64_t N, cudaStream_t s) {
-    const unsigned nb = nblocks(N);
-    if (sp == FVM_FP64 && dp == FVM_FP32) k_convert<double, float><<<nb, kThreads, 0, s>>>((const double*)src, (float*)dst, N);
-    else if (sp == FVM_FP32 && dp == FVM_FP64) k_convert<float, double><<<nb, kThreads, 0, s>>>((const float*)src, (double*)dst, N);
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (sp == FVM_FP64 && dp == FVM_FP32) k_convert<double, float><<<nb, 256, 0, s>>>((const double*)src, (float*)dst, N);
+    else if (sp == FVM_FP32 && dp == FVM_FP64) k_convert<float, double><<<nb, 256, 0, s>>>((const float*)src, (double*)dst, N);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

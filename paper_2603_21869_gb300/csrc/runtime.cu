@@ -39,8 +39,35 @@ struct HostLevel {
     double h[3];
     std::vector<uint8_t> solid;
     std::vector<uint8_t> dir[6];
+    std::vector<uint16_t> nbf;
     int64_t N() const { return (int64_t)n[0] * n[1] * n[2]; }
 };
+
+// Neighbour codes of every cell (see LevelDev::nbf).
+void build_nbf(HostLevel& L) {
+    L.nbf.assign(L.N(), 0);
+    for (int k = 0; k < L.n[2]; ++k)
+        for (int j = 0; j < L.n[1]; ++j)
+            for (int i = 0; i < L.n[0]; ++i) {
+                const int64_t c = cell_index(i, j, k, L.n[0], L.n[1]);
+                if (L.solid[c]) {
+                    L.nbf[c] = (uint16_t)(1u << 12);
+                    continue;
+                }
+                uint32_t code = 0;
+                const int f[3] = {i, j, k};
+                for (int d = 0; d < 6; ++d) {
+                    const int a = d / 2, side = (d & 1) ? 1 : -1;
+                    int q[3] = {f[0], f[1], f[2]};
+                    q[a] += side;
+                    uint32_t v;
+                    if (q[a] < 0 || q[a] >= L.n[a]) v = L.dir[d][face_index(a, i, j, k, L.n)] ? 2u : 1u;
+                    else v = L.solid[cell_index(q[0], q[1], q[2], L.n[0], L.n[1])] ? 1u : 0u;
+                    code |= v << (2 * d);
+                }
+                L.nbf[c] = (uint16_t)code;
+            }
+}
 
 int face_cells(const int* n, int face) {
     const int a = face / 2;
@@ -204,6 +231,23 @@ struct fvm_case {
     double* staging = nullptr;
     double* Ainv = nullptr;
     std::vector<DevLevel> levels;
+    SolveState* sst = nullptr;       // device
+    SolveState* h_sst = nullptr;     // pinned host copy
+    size_t lc = 0;                   // first level cycled by the single-CTA kernel
+    int inner_cycles = 1;            // V-cycles per outer residual (adaptive solves)
+    int rule_inner = 1;              // the same for the rule in force (1 for fixed-count solves)
+    CoarseLevels coarse;
+    // CUDA graphs of whole time steps, keyed by the field pointers they were captured with
+    bool use_graph = true;
+    struct StepGraph {
+        void* before[12];
+        void* after[12];
+        cudaGraph_t g;
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> graphs;
+    cudaStream_t side = nullptr;
+    int64_t kpc = 0;                 // kernels in one V-cycle (after the level-0 residual)
     std::vector<void*> allocs;
     int64_t bytes = 0;
     int64_t steps = 0;
@@ -256,6 +300,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->mg_levels < 2 || d->mg_levels > FVM_MAX_LEVELS) return fail(FVM_ERR_INVALID, "mg_levels must be 2..12");
     if (d->pre_sweeps < 1 || d->post_sweeps < 1 || d->pre_sweeps > 64 || d->post_sweeps > 64)
         return fail(FVM_ERR_INVALID, "pre_sweeps and post_sweeps must be 1..64");
+    if (d->inner_cycles < 0 || d->inner_cycles > 16) return fail(FVM_ERR_INVALID, "inner_cycles must be 0..16");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -336,6 +381,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     pl.levels.clear();
     pl.levels.push_back(L0);
     for (int l = 1; l < d->mg_levels; ++l) pl.levels.push_back(coarsen(pl.levels.back()));
+    for (HostLevel& H : pl.levels) build_nbf(H);
     // time step
     double hmin = 1e300;
     for (int a = 0; a < 3; ++a)
@@ -388,22 +434,25 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     for (int f = 0; f < 6; ++f) bytes += face_cells(n, f);
     for (size_t l = 0; l < pl.levels.size(); ++l) {
         const int64_t NL = pl.levels[l].N();
-        bytes += 3 * NL * si + (l ? NL : 0);
+        bytes += 3 * NL * si + (l ? NL : 0) + 2 * NL;
         for (int f = 0; f < 6; ++f) bytes += l ? (int64_t)pl.levels[l].dir[f].size() : 0;
     }
     const int64_t nc = pl.levels.back().N();
     bytes += nc * nc * 8;
-    bytes += (int64_t)(2 * resid0_blocks(N) + 16) * 8;
+    bytes += (int64_t)(2 * resid0_blocks(n[0], n[1], n[2]) + 16) * 8 + 256;
     pl.bytes = bytes;
     return FVM_OK;
 }
 
 void prof_clear(fvm_case* c);
+void drop_graphs(fvm_case* c);
 
 void free_case(fvm_case* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     prof_clear(c);
+    drop_graphs(c);
+    if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_norms) cudaFreeHost(c->h_norms);
@@ -500,85 +549,98 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     cudaStream_t s = c->stream;
     const double N = (double)L.dev.N;
     const double si = (double)elem_size(c->inner);
-    if (l + 1 == c->levels.size()) {
-        KLAUNCH("coarse_solve", N * N * 8 + 2 * N * si, 1,
-                launch_coarse_solve(c->inner, L.dev, c->Ainv, L.r, L.e[0], s));
+    if (l == c->lc) {
+        double cells = 0.0;
+        for (int q = 0; q < c->coarse.nl; ++q) cells += (double)c->coarse.lv[q].N;
+        const double nco = (double)c->coarse.lv[c->coarse.nl - 1].N;
+        KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
+                launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
         out_idx = 0;
         return FVM_OK;
     }
     DevLevel& Lc = c->levels[l + 1];
     const double Nc = (double)Lc.dev.N;
+    // level 0: the residual kernel already did the first sweep from e = 0, and
+    // runs inner_cycles V-cycles on the same r; the last sweep of the last one adds e to p
+    const int reps = l == 0 ? c->rule_inner : 1;
     int cur = 0;
-    KLAUNCH(lvl_name("smooth_first", l), 2 * N * si + N, 1, launch_smooth_first(c->inner, L.dev, L.r, L.e[0], s));
-    for (int k = 1; k < c->desc.pre_sweeps; ++k) {
-        KLAUNCH(lvl_name("smooth", l), 3 * N * si + N, 1,
-                launch_smooth(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], s));
-        cur ^= 1;
-    }
-    KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + N, 1,
-            launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, s));
-    int ci = 0;
-    ST_TRY(cycle(c, l + 1, ci));
-    KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + N, 1,
-            launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], s));
-    for (int k = 0; k < c->desc.post_sweeps; ++k) {
-        if (l == 0 && k == c->desc.post_sweeps - 1) {
-            KLAUNCH("smooth_to_p_L0", 2 * N * si + 16 * N + N, 1,
-                    launch_smooth_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, s));
-        } else {
-            KLAUNCH(lvl_name("smooth", l), 3 * N * si + N, 1,
-                    launch_smooth(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], s));
+    for (int rep = 0; rep < reps; ++rep) {
+        int pre = c->desc.pre_sweeps;
+        if (rep == 0) {
+            if (l > 0)
+                KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
+                        launch_sweep_first(c->inner, L.dev, L.r, L.e[0], c->sst, s));
+            pre -= 1;
+        }
+        for (int k = 0; k < pre; ++k) {
+            KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
+                    launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
             cur ^= 1;
+        }
+        KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + 2 * N, 1,
+                launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, c->sst, s));
+        int ci = 0;
+        ST_TRY(cycle(c, l + 1, ci));
+        KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + 2 * N, 1,
+                launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], c->sst, s));
+        for (int k = 0; k < c->desc.post_sweeps; ++k) {
+            if (l == 0 && rep == reps - 1 && k == c->desc.post_sweeps - 1) {
+                KLAUNCH("sweep_to_p_L0", 2 * N * si + 16 * N + 2 * N, 1,
+                        launch_sweep_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, c->sst, s));
+            } else {
+                KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
+                        launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
+                cur ^= 1;
+            }
         }
     }
     out_idx = cur;
     return FVM_OK;
 }
 
-fvm_status residual0(fvm_case* c, bool want_b2) {
-    int nb = 0;
+// level-0 residual with the norm, the stopping rule and the first pre-sweep
+fvm_status residual0(fvm_case* c, cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond2,
+                     int use_cond) {
     const double N = (double)c->cd.N;
-    KLAUNCH("resid0", N * (8 + elem_size(c->prec) + elem_size(c->inner) + 1), 1,
-            launch_resid0(c->inner, c->prec, c->levels[0].dev, c->p, c->b, c->levels[0].r, c->partials,
-                          want_b2 ? 1 : 0, c->stream, &nb));
-    KLAUNCH("norm_finalize", 16.0 * nb, 1, launch_norm_finalize(c->partials, nb, want_b2 ? 1 : 0, c->norms, c->stream));
+    KLAUNCH("resid0", N * (8 + elem_size(c->prec) + 2 * elem_size(c->inner) + 2), 1,
+            launch_resid0(c->inner, c->prec, c->levels[0].dev, c->p, c->b, c->levels[0].r, c->levels[0].e[0],
+                          c->partials, c->sst, cond, cond2, use_cond, c->stream));
     return FVM_OK;
 }
 
-fvm_status read_norms(fvm_case* c, double& rel) {
-    CUDA_TRY(cudaMemcpyAsync(c->h_norms, c->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+fvm_status read_state(fvm_case* c) {
+    CUDA_TRY(cudaMemcpyAsync(c->h_sst, c->sst, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    const double r2 = c->h_norms[0], b2 = c->h_norms[1];
-    if (!std::isfinite(r2) || !std::isfinite(b2)) {
-        rel = NAN;
-        return FVM_OK;
-    }
-    rel = b2 > 0.0 ? std::sqrt(r2 / b2) : 0.0;
     return FVM_OK;
 }
 
+// set the stopping rule of the next solves (fixed > 0: exactly that many cycles)
+fvm_status set_rule(fvm_case* c, int fixed) {
+    SolveState h;
+    memset(&h, 0, sizeof(h));
+    h.tol = c->desc.mg_rel_tol;
+    h.max_cycles = c->desc.max_vcycles;
+    h.fixed = fixed;
+    h.inner = fixed > 0 ? 1 : c->inner_cycles;
+    h.active = 1;
+    c->rule_inner = h.inner;
+    CUDA_TRY(cudaMemcpyAsync(c->sst, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+// V-cycles until the device-side rule stops (one host synchronisation per cycle)
 fvm_status solve(fvm_case* c, int& cycles, double& rel) {
-    const fvm_case_desc& d = c->desc;
-    cycles = 0;
-    if (d.fixed_vcycles > 0) {
-        for (int it = 0; it < d.fixed_vcycles; ++it) {
-            ST_TRY(residual0(c, it == 0));
-            int idx;
-            ST_TRY(cycle(c, 0, idx));
-        }
-        cycles = d.fixed_vcycles;
-        ST_TRY(residual0(c, false));
-        return read_norms(c, rel);
-    }
-    for (int it = 0;; ++it) {
-        ST_TRY(residual0(c, it == 0));
-        ST_TRY(read_norms(c, rel));
-        if (!std::isfinite(rel)) return FVM_OK;
-        if (rel <= d.mg_rel_tol || it == d.max_vcycles) break;
+    KLAUNCH("solve_begin", 0.0, 1, launch_solve_begin(c->sst, c->stream));
+    for (;;) {
+        ST_TRY(residual0(c, 0, 0, 0));
+        ST_TRY(read_state(c));
+        if (!c->h_sst->active) break;
         int idx;
         ST_TRY(cycle(c, 0, idx));
-        ++cycles;
     }
+    cycles = c->h_sst->cycles;
+    rel = c->h_sst->rel;
     return FVM_OK;
 }
 
@@ -624,6 +686,140 @@ fvm_status stage(fvm_case* c, int st, int* cycles, double* rel) {
     }
 }
 
+// ------------------------------------------------------------------ graphs
+void save_ptrs(const fvm_case* c, void** out) {
+    for (int f = 0; f < 6; ++f) {
+        out[f] = c->cur[f];
+        out[6 + f] = c->nxt[f];
+    }
+}
+
+void load_ptrs(fvm_case* c, void* const* in) {
+    for (int f = 0; f < 6; ++f) {
+        c->cur[f] = in[f];
+        c->nxt[f] = in[6 + f];
+    }
+}
+
+fvm_status stage(fvm_case* c, int st, int* cycles, double* rel);
+
+// Capture one time step into a graph: the step kernels, then a while node
+// whose body is the level-0 residual followed by an if node holding the
+// V-cycle, both conditions set by the residual kernel.
+fvm_status capture_step(fvm_case* c, fvm_case::StepGraph& G) {
+    save_ptrs(c, G.before);
+    const int64_t launches0 = c->launches;   // captured kernels are counted when they run
+    cudaStream_t s = c->stream;
+    if (!c->side) CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    auto abort_capture = [&](fvm_status st) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        c->stream = s;
+        c->launches = launches0;
+        load_ptrs(c, G.before);
+        cudaGetLastError();
+        return st;
+    };
+    fvm_status st = FVM_OK;
+    for (int k : {FVM_STAGE_DT, FVM_STAGE_DESTRUCTION, FVM_STAGE_EXPLICIT, FVM_STAGE_DESTRUCTION, FVM_STAGE_RHS})
+        if ((st = stage(c, k, nullptr, nullptr)) != FVM_OK) return abort_capture(st);
+    if (launch_solve_begin(c->sst, s) != cudaSuccess) return abort_capture(fail(FVM_ERR_CUDA, "capture solve_begin"));
+    c->launches += 1;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaStreamGetCaptureInfo"));
+    cudaGraphConditionalHandle hw, hi;
+    if (cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaGraphConditionalHandleCreate"));
+    cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &wp) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "adding the while node"));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    // body: residual, then if (go) V-cycle
+    if (cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaGraphConditionalHandleCreate (if)"));
+    c->stream = c->side;
+    if (cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "capturing the while body"));
+    st = residual0(c, hw, hi, 2);
+    cudaStreamCaptureStatus bcs;
+    cudaGraph_t bg = nullptr;
+    const cudaGraphNode_t* bdeps = nullptr;
+    size_t nbdeps = 0;
+    cudaGraphNode_t inode;
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    bool ok = st == FVM_OK &&
+              cudaStreamGetCaptureInfo(c->side, &bcs, nullptr, &bg, &bdeps, nullptr, &nbdeps) == cudaSuccess;
+    if (ok) {
+        ip.conditional.handle = hi;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        ok = cudaGraphAddNode(&inode, bg, bdeps, nullptr, nbdeps, &ip) == cudaSuccess;
+    }
+    cudaGraph_t done_body = nullptr;
+    cudaStreamEndCapture(c->side, &done_body);
+    if (!ok) {
+        c->stream = s;
+        return abort_capture(st != FVM_OK ? st : fail(FVM_ERR_CUDA, "adding the if node"));
+    }
+    cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) {
+        c->stream = s;
+        return abort_capture(fail(FVM_ERR_CUDA, "capturing the V-cycle body"));
+    }
+    int idx = 0;
+    const int64_t before_cycle = c->launches;
+    st = cycle(c, 0, idx);
+    c->kpc = c->launches - before_cycle;
+    cudaGraph_t done_if = nullptr;
+    cudaStreamEndCapture(c->side, &done_if);
+    c->stream = s;
+    if (st != FVM_OK) return abort_capture(st);
+    if (cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaStreamUpdateCaptureDependencies"));
+    if ((st = stage(c, FVM_STAGE_PROJECT, nullptr, nullptr)) != FVM_OK) return abort_capture(st);
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamEndCapture(s, &g));
+    save_ptrs(c, G.after);
+    load_ptrs(c, G.before);
+    c->launches = launches0;
+    G.g = g;
+    cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(FVM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    return FVM_OK;
+}
+
+int find_graph(fvm_case* c) {
+    void* now[12];
+    save_ptrs(c, now);
+    for (size_t g = 0; g < c->graphs.size(); ++g)
+        if (!memcmp(now, c->graphs[g].before, sizeof(now))) return (int)g;
+    return -1;
+}
+
+void drop_graphs(fvm_case* c) {
+    for (auto& G : c->graphs) {
+        cudaGraphExecDestroy(G.exec);
+        cudaGraphDestroy(G.g);
+    }
+    c->graphs.clear();
+}
+
 int field_slot(int fid) {
     // state slots: u v w T k omega; p is separate
     static const int slot[7] = {0, 1, 2, -1, 3, 4, 5};
@@ -639,6 +835,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     c->desc.boxes = c->boxes.data();
     c->prec = pl.prec;
     c->inner = pl.inner;
+    c->inner_cycles = d.inner_cycles > 0 ? d.inner_cycles : (pl.inner == FVM_FP64 ? 1 : 2);
     c->dt0 = pl.dt0;
     if (d.stream) c->stream = (cudaStream_t)d.stream;
     else {
@@ -671,6 +868,19 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     cd.cfl = d.cfl;
     cd.dt0 = pl.dt0;
     cd.dt_adapt = d.dt_adapt;
+    for (int a = 0; a < 3; ++a) {
+        cd.f.h[a] = (float)cd.h[a];
+        cd.f.inv_h[a] = (float)cd.inv_h[a];
+        cd.f.inv_h2[a] = (float)cd.inv_h2[a];
+        cd.f.gb[a] = (float)cd.gb[a];
+        cd.f.om_wall[a] = (float)cd.om_wall[a];
+    }
+    cd.f.nu = (float)cd.nu;
+    cd.f.alpha = (float)cd.alpha;
+    cd.f.inv_Prt = (float)cd.inv_Prt;
+    cd.f.inv_sigk = (float)cd.inv_sigk;
+    cd.f.inv_sigw = (float)cd.inv_sigw;
+    cd.f.T_ref = (float)cd.T_ref;
     const double rcp_alpha = (d.rho > 0.0 && d.cp > 0.0) ? 1.0 / (d.rho * d.cp * cd.alpha) : 0.0;
     cd.n_patches = (int)pl.patches.size();
     for (size_t pi = 0; pi < pl.patches.size(); ++pi) {
@@ -687,12 +897,22 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         const int face = pi < 6 ? (int)pi : c->vents[pi - 6].face;
         const double inward = (face % 2 == 0) ? 1.0 : -1.0;
         if (p.kind == FVM_INLET) q.vel[face / 2] = inward * p.u_normal;
+        for (int a = 0; a < 3; ++a) {
+            q.vel2f[a] = (float)(2.0 * q.vel[a]);
+            q.qhf[a] = (float)(q.q_coef * cd.h[a]);
+        }
+        q.T_in2f = (float)(2.0 * q.T_in);
+        q.k_in2f = (float)(2.0 * q.k_in);
+        q.om_in2f = (float)(2.0 * q.om_in);
+        q.T_value2f = (float)(2.0 * q.T_value);
     }
     cd.n_boxes = d.n_boxes;
     for (int bi = 0; bi < d.n_boxes; ++bi) {
         cd.box[bi].thermal = c->boxes[bi].thermal;
         cd.box[bi].T_value = c->boxes[bi].T_value;
         cd.box[bi].q_coef = c->boxes[bi].T_value * rcp_alpha;
+        cd.box[bi].T_value2f = (float)(2.0 * cd.box[bi].T_value);
+        for (int a = 0; a < 3; ++a) cd.box[bi].qhf[a] = (float)(cd.box[bi].q_coef * cd.h[a]);
     }
     // device memory
     for (int f = 0; f < 6; ++f) {
@@ -732,7 +952,11 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         }
         v.N = H.N();
         v.inv_D = 1.0 / diag;
+        v.diag = diag;
         v.wJ = d.jacobi_weight > 0.0 ? d.jacobi_weight : (nact == 3 ? 6.0 / 7.0 : 4.0 / 5.0);
+        for (int a = 0; a < 3; ++a) v.inv_h2f[a] = (float)v.inv_h2[a];
+        v.inv_Df = (float)v.inv_D;
+        v.wJf = (float)v.wJ;
         if (l == 0) v.solid = tag_d;
         else {
             uint8_t* sd;
@@ -746,27 +970,57 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             CUDA_TRY(cudaMemcpyAsync(dd, H.dir[f].data(), H.dir[f].size(), cudaMemcpyHostToDevice, c->stream));
             v.dir[f] = dd;
         }
+        uint16_t* nb;
+        ST_TRY(dalloc(c, (void**)&nb, v.N * 2));
+        CUDA_TRY(cudaMemcpyAsync(nb, H.nbf.data(), v.N * 2, cudaMemcpyHostToDevice, c->stream));
+        v.nbf = nb;
         ST_TRY(dalloc(c, &D.e[0], v.N * si));
         ST_TRY(dalloc(c, &D.e[1], v.N * si));
         ST_TRY(dalloc(c, &D.r, v.N * si));
+    }
+    // the coarsest levels whose e, e', r fit in one CTA's shared memory (level 0 never does)
+    {
+        // per cell: e, e', r in the compute type plus the 2-byte neighbour code.  FP64 runs
+        // at a small fraction of the FP32 rate on this part, so one SM only takes the
+        // last few hundred cells of an FP64 hierarchy
+        const size_t cs = (pl.inner == FVM_FP64 ? 8 : 4) * 3 + 2;
+        const size_t budget = pl.inner == FVM_FP64 ? 16 * 1024 : 200 * 1024;
+        size_t lc = c->levels.size() - 1;
+        size_t used = (size_t)c->levels[lc].dev.N * cs;
+        while (lc > 1 && used + (size_t)c->levels[lc - 1].dev.N * cs <= budget) {
+            --lc;
+            used += (size_t)c->levels[lc].dev.N * cs;
+        }
+        c->lc = lc;
+        memset(&c->coarse, 0, sizeof(c->coarse));
+        c->coarse.nl = (int)(c->levels.size() - lc);
+        c->coarse.pre = d.pre_sweeps;
+        c->coarse.post = d.post_sweeps;
+        for (int q = 0; q < c->coarse.nl; ++q) c->coarse.lv[q] = c->levels[lc + q].dev;
+        CUDA_TRY(prepare_coarse_cta(pl.inner, coarse_cta_smem(c->coarse, pl.inner)));
     }
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))
         return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
     ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 8));
     CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    c->nblocks0 = resid0_blocks(N);
+    c->nblocks0 = resid0_blocks(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
     ST_TRY(dalloc(c, (void**)&c->norms, 4 * 8));
-    ST_TRY(dalloc(c, (void**)&c->dt_state, 4 * 8));
-    CUDA_TRY(cudaMallocHost((void**)&c->h_norms, 8 * sizeof(double)));
+    ST_TRY(dalloc(c, (void**)&c->dt_state, 6 * 8));
+    ST_TRY(dalloc(c, (void**)&c->sst, sizeof(SolveState)));
+    CUDA_TRY(cudaMallocHost((void**)&c->h_norms, 8 * sizeof(double) + sizeof(SolveState)));
     c->h_dt = c->h_norms + 4;
-    double dts[4] = {pl.dt0, 0.5 * pl.dt0, 0.0, 0.0};
+    c->h_sst = (SolveState*)(c->h_norms + 8);
+    double dts[6] = {pl.dt0, 0.5 * pl.dt0, 0.0, 0.0, 0.0, 0.0};
+    ((float*)(dts + 4))[0] = (float)pl.dt0;
+    ((float*)(dts + 4))[1] = (float)(0.5 * pl.dt0);
     CUDA_TRY(cudaMemcpyAsync(c->dt_state, dts, sizeof(dts), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->p, 0, N * 8, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->b, 0, N * s, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->norms, 0, 4 * 8, c->stream));
     CUDA_TRY(launch_init_state(c->prec, cd, ptrs(c->cur), pl.base, d.seed, d.init_perturb, c->stream));
+    ST_TRY(set_rule(c, d.fixed_vcycles));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return FVM_OK;
 }
@@ -814,7 +1068,28 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     fvm_step_stats stats;
     memset(&stats, 0, sizeof(stats));
     fvm_status result = FVM_OK;
+    // clear the per-call counters of the solve state
+    CUDA_TRY(cudaMemsetAsync(&c->sst->total_cycles, 0, sizeof(int32_t), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->sst->nonfinite, 0, sizeof(int32_t), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->sst->notconv, 0, sizeof(int32_t), c->stream));
+    const bool graph = c->use_graph && !c->prof;
+    int graph_steps = 0;
     for (int n = 0; n < nsteps; ++n) {
+        if (graph) {
+            int g = find_graph(c);
+            if (g < 0) {
+                fvm_case::StepGraph G;
+                ST_TRY(capture_step(c, G));
+                c->graphs.push_back(G);
+                g = (int)c->graphs.size() - 1;
+            }
+            CUDA_TRY(cudaGraphLaunch(c->graphs[g].exec, c->stream));
+            load_ptrs(c, c->graphs[g].after);
+            ++c->steps;
+            ++graph_steps;
+            stats.steps++;
+            continue;
+        }
         int cycles = 0;
         double rel = 0.0;
         ST_TRY(stage(c, FVM_STAGE_DT, nullptr, nullptr));
@@ -826,22 +1101,27 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
         ST_TRY(stage(c, FVM_STAGE_PROJECT, nullptr, nullptr));
         ++c->steps;
         stats.steps++;
-        stats.vcycles_total += cycles;
-        stats.vcycles_last = cycles;
-        stats.rel_residual = rel;
-        if (!std::isfinite(rel)) {
-            result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
-            break;
-        }
-        if (c->desc.fixed_vcycles == 0 && rel > c->desc.mg_rel_tol) {
-            result = FVM_ERR_NOT_CONVERGED;
-            g_err = "V-cycle cap reached above the tolerance";
-        }
+        if (!std::isfinite(rel)) break;
     }
+    ST_TRY(read_state(c));
     CUDA_TRY(cudaMemcpyAsync(c->h_dt, c->dt_state, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    stats.vcycles_total = c->h_sst->total_cycles;
+    // kernels run by the graphs: 8 step kernels per step, one residual per outer iteration plus the
+    // last one of each step, and kpc kernels per outer iteration (inner V-cycles of the if node)
+    if (graph_steps) {
+        const int64_t outer = (int64_t)stats.vcycles_total / std::max(1, c->rule_inner);
+        c->launches += 8 * (int64_t)graph_steps + (int64_t)graph_steps + outer * (1 + c->kpc);
+    }
+    stats.vcycles_last = c->h_sst->cycles;
+    stats.rel_residual = c->h_sst->rel;
     stats.dt_last = c->h_dt[0];
     stats.sim_time = c->h_dt[2];
+    if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
+    else if (c->h_sst->notconv) {
+        result = FVM_ERR_NOT_CONVERGED;
+        g_err = "V-cycle cap reached above the tolerance";
+    }
     if (out) *out = stats;
     return result;
 }
@@ -849,14 +1129,21 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
 fvm_status fvm_vcycle(fvm_case* c, int ncycles, double* rel_residual) {
     if (!c) return fail(FVM_ERR_INVALID, "null case");
     if (ncycles < 0) return fail(FVM_ERR_INVALID, "ncycles < 0");
-    for (int it = 0; it < ncycles; ++it) {
-        ST_TRY(residual0(c, it == 0));
-        int idx;
-        ST_TRY(cycle(c, 0, idx));
-    }
-    ST_TRY(residual0(c, true));
+    int cycles = 0;
     double rel = 0.0;
-    ST_TRY(read_norms(c, rel));
+    fvm_status st = FVM_OK;
+    if (ncycles > 0) {
+        ST_TRY(set_rule(c, ncycles));
+        st = solve(c, cycles, rel);
+    } else {
+        // residual only: whatever the rule decides, no cycle is launched
+        ST_TRY(residual0(c, 0, 0, 0));
+        ST_TRY(read_state(c));
+        rel = c->h_sst->rel;
+    }
+    fvm_status st2 = set_rule(c, c->desc.fixed_vcycles);
+    if (st != FVM_OK) return st;
+    if (st2 != FVM_OK) return st2;
     if (rel_residual) *rel_residual = rel;
     return FVM_OK;
 }
@@ -956,6 +1243,17 @@ fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out) {
     info.kernel_launches = c->launches;
     *out = info;
     return FVM_OK;
+}
+
+fvm_status fvm_set_option(fvm_case* c, int option, int64_t value) {
+    if (!c) return fail(FVM_ERR_INVALID, "null case");
+    if (option == FVM_OPT_GRAPH) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        c->use_graph = value != 0;
+        if (!c->use_graph) drop_graphs(c);
+        return FVM_OK;
+    }
+    return fail(FVM_ERR_INVALID, "unknown option");
 }
 
 fvm_status fvm_profile_enable(fvm_case* c, int enable) {

@@ -29,6 +29,14 @@ constexpr double kKMin = 1e-14;
 constexpr double kOmegaMin = 1e-8;
 
 constexpr int kThreads = 256;
+constexpr int BX = 32, BY = 4, BZ = 2;
+
+__device__ __forceinline__ bool cell3(const CaseDev& cd, int& i, int& j, int& k) {
+    i = blockIdx.x * BX + threadIdx.x;
+    j = blockIdx.y * BY + threadIdx.y;
+    k = blockIdx.z * BZ + threadIdx.z;
+    return i < cd.n[0] && j < cd.n[1] && k < cd.n[2];
+}
 
 template <class C>
 struct St {
@@ -41,10 +49,17 @@ __device__ __forceinline__ C vcomp(const St<C>& s, int a) {
 }
 
 template <class C>
-__device__ __forceinline__ C thermal_ghost(int thermal, double Tval, double qcoef, double h, C TP) {
-    if (thermal == FVM_FIXED_T) return (C)(2.0 * Tval) - TP;
-    if (thermal == FVM_HEAT_FLUX) return TP + (C)(qcoef * h);
+__device__ __forceinline__ C thermal_ghost(int thermal, double Tval, float T2f, double qcoef, double h, float qhf,
+                                          C TP) {
+    if (thermal == FVM_FIXED_T) return prm<C>(2.0 * Tval, T2f) - TP;
+    if (thermal == FVM_HEAT_FLUX) return TP + prm<C>(qcoef * h, qhf);
     return TP;
+}
+
+// dt (slot 0) or dt/2 (slot 1) in the compute type
+template <class C>
+__device__ __forceinline__ C dt_of(const double* dt_state, int slot) {
+    return prm<C>(dt_state[slot], ((const float*)(dt_state + 4))[slot]);
 }
 
 template <class S, class C>
@@ -73,28 +88,28 @@ __device__ __forceinline__ int neighbour(const CaseDev& cd, const StatePtrs& st,
         if (pt.kind == FVM_WALL) {
             g.u = -P.u; g.v = -P.v; g.w = -P.w;
             g.k = P.k; g.om = P.om;
-            g.T = thermal_ghost<C>(pt.thermal, pt.T_value, pt.q_coef, cd.h[axis], P.T);
+            g.T = thermal_ghost<C>(pt.thermal, pt.T_value, pt.T_value2f, pt.q_coef, cd.h[axis], pt.qhf[axis], P.T);
             return FK_WALL;
         }
         if (pt.kind == FVM_INLET) {
-            g.u = (C)(2.0 * pt.vel[0]) - P.u;
-            g.v = (C)(2.0 * pt.vel[1]) - P.v;
-            g.w = (C)(2.0 * pt.vel[2]) - P.w;
-            g.T = (C)(2.0 * pt.T_in) - P.T;
-            g.k = (C)(2.0 * pt.k_in) - P.k;
-            g.om = (C)(2.0 * pt.om_in) - P.om;
+            g.u = prm<C>(2.0 * pt.vel[0], pt.vel2f[0]) - P.u;
+            g.v = prm<C>(2.0 * pt.vel[1], pt.vel2f[1]) - P.v;
+            g.w = prm<C>(2.0 * pt.vel[2], pt.vel2f[2]) - P.w;
+            g.T = prm<C>(2.0 * pt.T_in, pt.T_in2f) - P.T;
+            g.k = prm<C>(2.0 * pt.k_in, pt.k_in2f) - P.k;
+            g.om = prm<C>(2.0 * pt.om_in, pt.om_in2f) - P.om;
             return FK_INLET;
         }
         g = P;
         return pt.kind == FVM_OUTLET ? FK_OUTLET : FK_EMPTY;
     }
-    const int64_t c = cell_index(q[0], q[1], q[2], cd.n[0], cd.n[1]);
+    const int c = q[0] + cd.n[0] * (q[1] + cd.n[1] * q[2]);
     const int t = cd.tag[c];
     if (t) {
         const BoxDev& b = cd.box[t - 1];
         g.u = -P.u; g.v = -P.v; g.w = -P.w;
         g.k = P.k; g.om = P.om;
-        g.T = thermal_ghost<C>(b.thermal, b.T_value, b.q_coef, cd.h[axis], P.T);
+        g.T = thermal_ghost<C>(b.thermal, b.T_value, b.T_value2f, b.q_coef, cd.h[axis], b.qhf[axis], P.T);
         return FK_WALL;
     }
     g = load_state<S, C>(st, c);
@@ -150,21 +165,22 @@ __global__ void k_init(CaseDev cd, StatePtrs st, double b0, double b1, double b2
 // ------------------------------------------------------------------ dt
 // rate = sum_active (|u_a| / h_a + 2 Gamma / h_a^2), Gamma = max(nu + nu_t, alpha + nu_t / Pr_t);
 // the block maxima go to dt_state[3] (as ordered bits of a non-negative double)
-template <class S>
+template <class S, class C>
 __global__ void k_rate_max(CaseDev cd, StatePtrs st, unsigned long long* rate_bits) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double lam = 0.0;
     if (c < cd.N && cd.tag[c] == 0) {
-        const double u[3] = {(double)to_c<double>(ldg((const S*)st.f[0] + c)),
-                             (double)to_c<double>(ldg((const S*)st.f[1] + c)),
-                             (double)to_c<double>(ldg((const S*)st.f[2] + c))};
-        const double k = to_c<double>(ldg((const S*)st.f[4] + c));
-        const double om = to_c<double>(ldg((const S*)st.f[5] + c));
-        const double nut = nut_of<double>(k, om, cd.nu);
-        const double g1 = cd.nu + nut, g2 = cd.alpha + nut * cd.inv_Prt;
-        const double gam = g1 > g2 ? g1 : g2;
+        const C u[3] = {to_c<C>(ldg((const S*)st.f[0] + c)), to_c<C>(ldg((const S*)st.f[1] + c)),
+                        to_c<C>(ldg((const S*)st.f[2] + c))};
+        const C k = to_c<C>(ldg((const S*)st.f[4] + c));
+        const C om = to_c<C>(ldg((const S*)st.f[5] + c));
+        const C nut = nut_of<C>(k, om, prm<C>(cd.nu, cd.f.nu));
+        const C g1 = prm<C>(cd.nu, cd.f.nu) + nut, g2 = prm<C>(cd.alpha, cd.f.alpha) + nut * prm<C>(cd.inv_Prt, cd.f.inv_Prt);
+        const C gam = g1 > g2 ? g1 : g2;
+        C l = (C)0;
         for (int a = 0; a < 3; ++a)
-            if (cd.active[a]) lam += fabs(u[a]) * cd.inv_h[a] + 2.0 * gam * cd.inv_h2[a];
+            if (cd.active[a]) l += fabs(u[a]) * prm<C>(cd.inv_h[a], cd.f.inv_h[a]) + (C)2 * gam * prm<C>(cd.inv_h2[a], cd.f.inv_h2[a]);
+        lam = (double)l;
         if (!(lam == lam)) lam = __longlong_as_double(0x7ff0000000000000ll);   // NaN -> +inf
     }
     __shared__ double red[kThreads / 32];
@@ -190,6 +206,8 @@ __global__ void k_dt_finalize(double dt0, double cfl, int adapt, double* dt_stat
     dt_state[0] = dt;
     dt_state[1] = 0.5 * dt;
     dt_state[2] += dt;
+    ((float*)(dt_state + 4))[0] = (float)dt;
+    ((float*)(dt_state + 4))[1] = (float)(0.5 * dt);
     *bits = 0ull;
 }
 
@@ -197,12 +215,9 @@ __global__ void k_dt_finalize(double dt0, double cfl, int adapt, double* dt_stat
 template <class S, class C>
 __global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S* __restrict__ om_out,
                               const double* dt_state) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cd.N) return;
-    const int nx = cd.n[0], ny = cd.n[1];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
+    int i, j, k;
+    if (!cell3(cd, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     if (cd.tag[c]) {
         k_out[c] = from_c<S, C>(P.k);
@@ -220,7 +235,7 @@ __global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S
         St<C> L, R;
         neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
         neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
-        const C ih = (C)cd.inv_h[a];
+        const C ih = prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
         gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
         gu[1][a] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
         gu[2][a] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
@@ -233,7 +248,7 @@ __global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S
             Sm[a][b] = (C)0.5 * (gu[a][b] + gu[b][a]);
             Om[a][b] = (C)0.5 * (gu[a][b] - gu[b][a]);
         }
-    const C nu = (C)cd.nu;
+    const C nu = prm<C>(cd.nu, cd.f.nu);
     const C oms = omega_safe(P.om);
     // k: chi_k, f_beta*, beta* (Eqs. k_des, beta_star)
     const C chik = (gk[0] * gw[0] + gk[1] * gw[1] + gk[2] * gw[2]) / (oms * oms * oms);
@@ -253,7 +268,7 @@ __global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S
         const C x4 = x2 * x2;
         bstar = (C)kBetaStarInf * ((C)(4.0 / 15.0) + x4) / ((C)1 + x4);
     }
-    const C dt = (C)dt_state[1];
+    const C dt = dt_of<C>(dt_state, 1);
     const C knew = P.k / ((C)1 + dt * bstar * fbs * P.om);
     // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des)
     C tr = (C)0;
@@ -277,12 +292,12 @@ __device__ __forceinline__ void face_flux(const CaseDev& cd, int a, const St<C>&
                                           C fl[6]) {
     const C uf = (C)0.5 * (vcomp(L, a) + vcomp(R, a));
     const bool pos = uf >= (C)0;
-    const C ih = (C)cd.inv_h[a];
-    const C nu = (C)cd.nu;
+    const C ih = prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
+    const C nu = prm<C>(cd.nu, cd.f.nu);
     const C gm = nu + nut_f;
-    const C gT = (C)cd.alpha + nut_f * (C)cd.inv_Prt;
-    const C gk = nu + nut_f * (C)cd.inv_sigk;
-    const C gw = nu + nut_f * (C)cd.inv_sigw;
+    const C gT = prm<C>(cd.alpha, cd.f.alpha) + nut_f * prm<C>(cd.inv_Prt, cd.f.inv_Prt);
+    const C gk = nu + nut_f * prm<C>(cd.inv_sigk, cd.f.inv_sigk);
+    const C gw = nu + nut_f * prm<C>(cd.inv_sigw, cd.f.inv_sigw);
     fl[0] = -((pos ? L.u : R.u) * uf) + gm * (R.u - L.u) * ih;
     fl[1] = -((pos ? L.v : R.v) * uf) + gm * (R.v - L.v) * ih;
     fl[2] = -((pos ? L.w : R.w) * uf) + gm * (R.w - L.w) * ih;
@@ -301,12 +316,9 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, const St<C>& nb, C nu) {
 
 template <class S, class C>
 __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double* dt_state) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cd.N) return;
-    const int nx = cd.n[0], ny = cd.n[1];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
+    int i, j, k;
+    if (!cell3(cd, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     S* o[6];
     for (int f = 0; f < 6; ++f) o[f] = (S*)out.f[f];
@@ -315,7 +327,7 @@ __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double
         o[3][c] = from_c<S, C>(P.T); o[4][c] = from_c<S, C>(P.k); o[5][c] = from_c<S, C>(P.om);
         return;
     }
-    const C nu = (C)cd.nu;
+    const C nu = prm<C>(cd.nu, cd.f.nu);
     const C nutP = nut_of(P.k, P.om, nu);
     C rhs[6] = {(C)0, (C)0, (C)0, (C)0, (C)0, (C)0};
     C gu[3][3];
@@ -331,13 +343,13 @@ __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double
         C fw[6], fe[6];
         face_flux(cd, a, L, P, face_nut(kl, nutP, L, nu), fw);
         face_flux(cd, a, P, R, face_nut(kr, nutP, R, nu), fe);
-        const C ih = (C)cd.inv_h[a];
+        const C ih = prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
         for (int f = 0; f < 6; ++f) rhs[f] += (fe[f] - fw[f]) * ih;
         gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
         gu[1][a] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
         gu[2][a] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
         if (kl == FK_WALL || kr == FK_WALL) {
-            const C ow = (C)cd.om_wall[a];
+            const C ow = prm<C>(cd.om_wall[a], cd.f.om_wall[a]);
             omw = ow > omw ? ow : omw;
         }
     }
@@ -356,11 +368,11 @@ __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double
     rhs[4] += Gk;
     rhs[5] += alpha * P.om / P.k * Gk;
     // Boussinesq buoyancy -g beta_T (T - T_ref)
-    const C dT = P.T - (C)cd.T_ref;
-    rhs[0] += (C)cd.gb[0] * dT;
-    rhs[1] += (C)cd.gb[1] * dT;
-    rhs[2] += (C)cd.gb[2] * dT;
-    const C dt = (C)dt_state[0];
+    const C dT = P.T - prm<C>(cd.T_ref, cd.f.T_ref);
+    rhs[0] += prm<C>(cd.gb[0], cd.f.gb[0]) * dT;
+    rhs[1] += prm<C>(cd.gb[1], cd.f.gb[1]) * dT;
+    rhs[2] += prm<C>(cd.gb[2], cd.f.gb[2]) * dT;
+    const C dt = dt_of<C>(dt_state, 0);
     C un = P.u + dt * rhs[0];
     C vn = P.v + dt * rhs[1];
     C wn = P.w + dt * rhs[2];
@@ -377,16 +389,13 @@ __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double
 // ------------------------------------------------------------------ pressure RHS
 template <class S, class C>
 __global__ void k_rhs(CaseDev cd, StatePtrs in, S* __restrict__ b, const double* dt_state) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cd.N) return;
+    int i, j, k;
+    if (!cell3(cd, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
     if (cd.tag[c]) {
         b[c] = from_c<S, C>((C)0);
         return;
     }
-    const int nx = cd.n[0], ny = cd.n[1];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
     const St<C> P = load_state<S, C>(in, c);
     C div = (C)0;
     for (int a = 0; a < 3; ++a) {
@@ -396,48 +405,43 @@ __global__ void k_rhs(CaseDev cd, StatePtrs in, S* __restrict__ b, const double*
         neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
         const C ue = (C)0.5 * (vcomp(P, a) + vcomp(R, a));
         const C uw = (C)0.5 * (vcomp(L, a) + vcomp(P, a));
-        div += (ue - uw) * (C)cd.inv_h[a];
+        div += (ue - uw) * prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
     }
-    b[c] = from_c<S, C>(-div / (C)dt_state[0]);
+    b[c] = from_c<S, C>(-div / dt_of<C>(dt_state, 0));
 }
 
 // ------------------------------------------------------------------ projection
 // pressure across a face: neighbour, Neumann ghost (walls, inlets, solids) or -p (outlets)
-__device__ __forceinline__ double p_across(const LevelDev& L, const double* p, int i, int j, int k, int a,
+__device__ __forceinline__ double p_across(const LevelDev& L, const double* p, uint32_t f, int c, int a,
                                            int side, double pP) {
-    int q[3] = {i, j, k};
-    q[a] += side;
-    if (q[a] < 0 || q[a] >= L.n[a]) {
-        const int face = 2 * a + (side > 0 ? 1 : 0);
-        return L.dir[face][face_index(a, i, j, k, L.n)] ? -pP : pP;
-    }
-    const int64_t c = cell_index(q[0], q[1], q[2], L.n[0], L.n[1]);
-    return L.solid[c] ? pP : __ldg(p + c);
+    const uint32_t code = (f >> (2 * (2 * a + (side > 0 ? 1 : 0)))) & 3u;
+    if (code == 1u) return pP;
+    if (code == 2u) return -pP;
+    const int stride = a == 0 ? 1 : (a == 1 ? L.n[0] : L.n[0] * L.n[1]);
+    return __ldg(p + c + side * stride);
 }
 
 template <class S, class C>
 __global__ void k_project(CaseDev cd, LevelDev L0, StatePtrs in, StatePtrs out, const double* __restrict__ p,
                           const double* dt_state) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cd.N) return;
+    int i, j, k;
+    if (!cell3(cd, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
     S* o[3] = {(S*)out.f[0], (S*)out.f[1], (S*)out.f[2]};
     const S* q[3] = {(const S*)in.f[0], (const S*)in.f[1], (const S*)in.f[2]};
     if (cd.tag[c]) {
         for (int a = 0; a < 3; ++a) o[a][c] = q[a][c];
         return;
     }
-    const int nx = cd.n[0], ny = cd.n[1];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
     const double pP = __ldg(p + c);
-    const C dt = (C)dt_state[0];
+    const uint32_t f = L0.nbf[c];
+    const C dt = dt_of<C>(dt_state, 0);
     for (int a = 0; a < 3; ++a) {
         C g = (C)0;
         if (cd.active[a]) {
             // differences of the FP64 pressure are taken in FP64, then rounded
-            const double pl = p_across(L0, p, i, j, k, a, -1, pP);
-            const double pr = p_across(L0, p, i, j, k, a, +1, pP);
+            const double pl = p_across(L0, p, f, c, a, -1, pP);
+            const double pr = p_across(L0, p, f, c, a, +1, pP);
             const double ih = cd.inv_h[a];
             g = (C)(0.5 * ((pr - pP) * ih + (pP - pl) * ih));
         }
@@ -459,6 +463,11 @@ __global__ void k_unpack(const double* __restrict__ src, S* __restrict__ dst, in
 }
 
 inline unsigned nblocks(int64_t N) { return (unsigned)((N + kThreads - 1) / kThreads); }
+inline dim3 grid3(const CaseDev& cd) {
+    return dim3((unsigned)((cd.n[0] + BX - 1) / BX), (unsigned)((cd.n[1] + BY - 1) / BY),
+                (unsigned)((cd.n[2] + BZ - 1) / BZ));
+}
+const dim3 kBlock3(BX, BY, BZ);
 
 }  // namespace
 
@@ -480,34 +489,33 @@ cudaError_t launch_init_state(int prec, const CaseDev& cd, StatePtrs st, const d
 }
 
 cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, (void)sizeof(C);
-             k_rate_max<S><<<nblocks(cd.N), kThreads, 0, s>>>(cd, st, (unsigned long long*)(dt_state + 3)));
+    DISPATCH(prec, k_rate_max<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, st, (unsigned long long*)(dt_state + 3)));
     k_dt_finalize<<<1, 1, 0, s>>>(cd.dt0, cd.cfl, cd.dt_adapt, dt_state);
     return cudaGetLastError();
 }
 
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
                                const double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, k_destruction<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, (S*)k_out, (S*)om_out,
+    DISPATCH(prec, k_destruction<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, (S*)k_out, (S*)om_out,
                                                                            dt_state));
     return cudaGetLastError();
 }
 
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out, const double* dt_state,
                             cudaStream_t s) {
-    DISPATCH(prec, k_explicit<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, out, dt_state));
+    DISPATCH(prec, k_explicit<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, out, dt_state));
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const double* dt_state,
                        cudaStream_t s) {
-    DISPATCH(prec, k_rhs<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, in, (S*)b, dt_state));
+    DISPATCH(prec, k_rhs<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, (S*)b, dt_state));
     return cudaGetLastError();
 }
 
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
                            const double* p, const double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, k_project<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, L0, in, out, p, dt_state));
+    DISPATCH(prec, k_project<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, L0, in, out, p, dt_state));
     return cudaGetLastError();
 }
 
