@@ -225,6 +225,30 @@ fvm_status fvm_profile_enable(fvm_case* c, int enable);
    clear them.  Synchronises the case's stream. */
 fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_out);
 
+/* Pressure residual without any device allocation (the paper has no
+   counterpart; this serves callers that cannot call cudaMalloc, e.g. a
+   program whose device memory belongs to a pooling allocator, a control
+   loop that must not take an allocation's latency or implicit
+   synchronisation, or a plug-in that must keep its device footprint fixed).
+   Computes r = b - A p on an nx x ny x nz box without obstacles, A the
+   7-point -Laplacian of the multigrid (Eq. neg_lap_discretize), each domain
+   face zero-gradient for p (dirichlet[face] = 0) or zero-value (1), and
+   norms[0] = ||r||^2, norms[1] = ||b||^2.
+     p, b, r : device pointers to nx*ny*nz doubles, x fastest (caller-owned)
+     norms   : device pointer to 2 doubles (caller-owned)
+     h       : host array, cell sizes along x, y, z; dirichlet: host array of 6
+     stream  : cudaStream_t or NULL; the call only enqueues work
+   The kernel's scratch (per-block partial sums and a counter, about 1 MB) is a
+   static device array that every GPU loading the library keeps until exit;
+   grids above 65,536 blocks of 32 x 4 x 2 cells (16,777,216 cells) are
+   rejected with FVM_ERR_INVALID.  The first call on a device looks up that
+   array's address (with the device current); make that first call before any
+   stream capture.  All calls share the array: calls that overlap on the GPU
+   (other streams, other threads) race and must be serialised by the caller. */
+fvm_status fvm_poisson_residual_static(const double* p, const double* b, int32_t nx, int32_t ny, int32_t nz,
+                                       const double h[3], const int32_t dirichlet[6], double* r,
+                                       double* norms, void* stream);
+
 /* sizeof of the public structs, for binding checks: out[0..6] = fvm_patch,
    fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
    fvm_kernel_stat.  Needs

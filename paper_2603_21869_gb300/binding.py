@@ -84,7 +84,7 @@ class KernelStat(ct.Structure):
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
            "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-           "fvm_struct_sizes", "fvm_last_error"]
+           "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static"]
 
 _lib = None
 
@@ -115,6 +115,10 @@ def lib():
     L.fvm_set_option.argtypes = [CP, ct.c_int, ct.c_int64]
     L.fvm_profile_enable.argtypes = [CP, ct.c_int]
     L.fvm_profile_read.argtypes = [CP, ct.POINTER(KernelStat), ct.c_int, ct.POINTER(ct.c_int)]
+    L.fvm_poisson_residual_static.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32,
+                                              ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32), ct.c_void_p,
+                                              ct.c_void_p, ct.c_void_p]
+    L.fvm_poisson_residual_static.restype = ct.c_int
     L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
     L.fvm_struct_sizes.restype = None
     L.fvm_last_error.restype = ct.c_char_p

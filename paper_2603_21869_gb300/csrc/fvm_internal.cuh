@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/fvm.h"
 
 #define FVM_MAX_PATCHES 16
@@ -188,3 +190,6 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
 int resid0_blocks(int nx, int ny, int nz);
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner);
+
+// message returned by fvm_last_error() on this thread
+void set_last_error(const std::string& msg);

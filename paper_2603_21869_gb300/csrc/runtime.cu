@@ -204,6 +204,8 @@ bool coarse_inverse(const HostLevel& L, std::vector<double>& inv) {
 
 }  // namespace
 
+void set_last_error(const std::string& msg) { g_err = msg; }
+
 struct DevLevel {
     LevelDev dev;
     void* e[2] = {nullptr, nullptr};
