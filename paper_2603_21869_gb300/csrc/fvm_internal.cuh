@@ -113,6 +113,29 @@ struct CoarseLevels {
     LevelDev lv[FVM_MAX_LEVELS];
 };
 
+// Levels lc..L-1, cycled by one thread-block cluster: each level is cut into
+// slabs of planes along axis D (2 = z, or 1 = y in 2D); CTA q owns planes
+// [q ppc, (q + 1) ppc).  Offsets are identical in every CTA's shared memory.
+struct ClusterLevels {
+    int32_t nl, pre, post, cs;
+    int32_t D;
+    int32_t fbyte0;          // byte offset of the neighbour-code region
+    int32_t fcount;          // uint16 entries in that region
+    int32_t lm;              // levels lm.. are held whole by CTA 0 (ppc = nD)
+    int32_t ppc[FVM_MAX_LEVELS];     // planes per CTA
+    int32_t plane[FVM_MAX_LEVELS];   // cells per plane
+    int32_t nD[FVM_MAX_LEVELS];      // planes of the level
+    int32_t off[FVM_MAX_LEVELS];     // first element (compute type) of the level's e, e', r
+    int32_t foff[FVM_MAX_LEVELS];    // first neighbour-code entry of the level
+    // multipliers for exact division by plane size, nx and ppc: q / d = (q * m) >> 40
+    // (m = ceil(2^40 / d); exact while q * d < 2^40)
+    uint64_t mP[FVM_MAX_LEVELS], mX[FVM_MAX_LEVELS], mC[FVM_MAX_LEVELS];
+    LevelDev lv[FVM_MAX_LEVELS];
+};
+
+__host__ __device__ __forceinline__ uint64_t div_magic(uint32_t d) { return ((1ull << 40) + d - 1) / d; }
+__device__ __forceinline__ int fdiv(int q, uint64_t m) { return (int)(((uint64_t)(uint32_t)q * m) >> 40); }
+
 // ---------------------------------------------------------------- helpers
 __host__ __device__ __forceinline__ int64_t cell_index(int i, int j, int k, int nx, int ny) {
     return ((int64_t)k * ny + j) * nx + i;
@@ -190,6 +213,11 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
 int resid0_blocks(int nx, int ny, int nz);
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner);
+// cluster kernel (mg_cluster.cu)
+size_t cluster_smem_bytes(const ClusterLevels& cl, int inner);
+cudaError_t prepare_coarse_cluster(int inner, int cs, size_t smem, int* max_clusters);
+cudaError_t launch_coarse_cluster(int inner, const ClusterLevels& cl, const void* r_in, void* e_out,
+                                  const double* Ainv, const SolveState* st, cudaStream_t s);
 
 // message returned by fvm_last_error() on this thread
 void set_last_error(const std::string& msg);

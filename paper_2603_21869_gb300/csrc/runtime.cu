@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,6 +31,11 @@ fvm_status fail(fvm_status st, const std::string& msg) {
 
 constexpr double kCmu = 0.09;
 constexpr double kBetaI = 0.072;
+
+int getenv_flag(const char* name) {
+    const char* v = getenv(name);
+    return v && *v && *v != '0' ? 1 : 0;
+}
 
 size_t elem_size(int prec) { return prec == FVM_FP64 ? 8 : (prec == FVM_FP32 ? 4 : 2); }
 
@@ -235,7 +241,9 @@ struct fvm_case {
     std::vector<DevLevel> levels;
     SolveState* sst = nullptr;       // device
     SolveState* h_sst = nullptr;     // pinned host copy
-    size_t lc = 0;                   // first level cycled by the single-CTA kernel
+    size_t lc = 0;                   // first level cycled by the coarse kernel (cluster or single CTA)
+    bool use_cluster = false;
+    ClusterLevels cluster;
     int inner_cycles = 1;            // V-cycles per outer residual (adaptive solves)
     int rule_inner = 1;              // the same for the rule in force (1 for fixed-count solves)
     CoarseLevels coarse;
@@ -552,11 +560,15 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     const double N = (double)L.dev.N;
     const double si = (double)elem_size(c->inner);
     if (l == c->lc) {
+        const double nco = (double)c->levels.back().dev.N;
         double cells = 0.0;
-        for (int q = 0; q < c->coarse.nl; ++q) cells += (double)c->coarse.lv[q].N;
-        const double nco = (double)c->coarse.lv[c->coarse.nl - 1].N;
-        KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
-                launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
+        for (size_t q = l; q < c->levels.size(); ++q) cells += (double)c->levels[q].dev.N;
+        if (c->use_cluster)
+            KLAUNCH("coarse_cluster", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
+                    launch_coarse_cluster(c->inner, c->cluster, L.r, L.e[0], c->Ainv, c->sst, s));
+        else
+            KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
+                    launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
         out_idx = 0;
         return FVM_OK;
     }
@@ -1000,6 +1012,86 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         c->coarse.post = d.post_sweeps;
         for (int q = 0; q < c->coarse.nl; ++q) c->coarse.lv[q] = c->levels[lc + q].dev;
         CUDA_TRY(prepare_coarse_cta(pl.inner, coarse_cta_smem(c->coarse, pl.inner)));
+        // a thread-block cluster holds more levels in its distributed shared memory; take
+        // the largest set that fits 200 KB per CTA, with 16 CTAs (or 8) if the GPU can
+        // schedule such a cluster
+        const int D = L0.active[2] ? 2 : (L0.active[1] ? 1 : -1);
+        c->use_cluster = false;
+        // (opt-in: on the 1M-cell channel the cluster kernel is slower than the per-level
+        // kernels plus the single CTA it replaces)
+        if (D > 0 && getenv_flag("FVM_CLUSTER") == 1) {
+            for (int cs : {16, 8}) {
+                ClusterLevels cl;
+                memset(&cl, 0, sizeof(cl));
+                // levels from `lm_abs` on are small enough to be held whole by CTA 0
+                const size_t nlev = c->levels.size();
+                size_t lm_abs = nlev - 1;
+                {
+                    int64_t tail = (int64_t)pl.levels[nlev - 1].N();
+                    while (lm_abs > 1 && tail + (int64_t)pl.levels[lm_abs - 1].N() <= 4096) {
+                        --lm_abs;
+                        tail += (int64_t)pl.levels[lm_abs].N();
+                    }
+                }
+                auto ppc_of = [&](size_t l) {
+                    const int nD = pl.levels[l].n[D];
+                    return l >= lm_abs ? nD : (nD + cs - 1) / cs;
+                };
+                size_t best_lc = 0;
+                size_t elems = 0, codes = 0;
+                for (size_t l0 = nlev - 1; l0 >= 1; --l0) {
+                    size_t e = 0, f = 0;
+                    for (size_t l = l0; l < nlev; ++l) {
+                        const HostLevel& H = pl.levels[l];
+                        const int plane = (int)(H.N() / H.n[D]);
+                        e += (size_t)3 * ppc_of(l) * plane;
+                        f += (size_t)ppc_of(l) * plane;
+                    }
+                    const size_t bytes = e * (pl.inner == FVM_FP64 ? 8 : 4) + f * 2 + 16;
+                    if (bytes > 200 * 1024) break;
+                    best_lc = l0;
+                    elems = e;
+                    codes = f;
+                    if (l0 == 1) break;
+                }
+                if (best_lc == 0 || best_lc > lc) continue;   // no better than the single CTA
+                cl.nl = (int)(c->levels.size() - best_lc);
+                cl.pre = d.pre_sweeps;
+                cl.post = d.post_sweeps;
+                cl.cs = cs;
+                cl.D = D;
+                cl.lm = (int)(lm_abs > best_lc ? lm_abs - best_lc : 0);
+                int eoff = 0, foff = 0;
+                for (int q = 0; q < cl.nl; ++q) {
+                    const HostLevel& H = pl.levels[best_lc + q];
+                    cl.nD[q] = H.n[D];
+                    cl.plane[q] = (int)(H.N() / H.n[D]);
+                    cl.ppc[q] = ppc_of(best_lc + q);
+                    cl.mP[q] = div_magic((uint32_t)cl.plane[q]);
+                    cl.mX[q] = div_magic((uint32_t)H.n[0]);
+                    cl.mC[q] = div_magic((uint32_t)cl.ppc[q]);
+                    cl.off[q] = eoff;
+                    cl.foff[q] = foff;
+                    eoff += 3 * cl.ppc[q] * cl.plane[q];
+                    foff += cl.ppc[q] * cl.plane[q];
+                    cl.lv[q] = c->levels[best_lc + q].dev;
+                }
+                const int cbytes = pl.inner == FVM_FP64 ? 8 : 4;
+                cl.fbyte0 = (eoff * cbytes + 15) / 16 * 16;
+                cl.fcount = foff;
+                (void)elems;
+                (void)codes;
+                int nclusters = 0;
+                if (prepare_coarse_cluster(pl.inner, cs, cluster_smem_bytes(cl, pl.inner), &nclusters) ==
+                        cudaSuccess &&
+                    nclusters >= 1) {
+                    c->cluster = cl;
+                    c->use_cluster = true;
+                    c->lc = best_lc;
+                    break;
+                }
+            }
+        }
     }
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))

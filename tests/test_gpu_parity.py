@@ -235,6 +235,19 @@ def test_graph_and_launch_paths_agree_bitwise(prec):
         assert np.array_equal(f1[f], f2[f]), f
 
 
+def test_cluster_and_single_cta_coarse_paths_agree(monkeypatch):
+    """The coarse levels run either in one thread-block cluster (distributed
+    shared memory) or in one CTA; both match the oracle's V-cycles."""
+    spec = channel_box(fixed_vcycles=3)
+    o = OracleCase(spec).step(2)
+    for cluster in ("1", "0"):
+        monkeypatch.setenv("FVM_CLUSTER", cluster)
+        with binding.Case(spec) as c:
+            c.step(2)
+            got = c.read()
+        assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"FVM_CLUSTER={cluster}")
+
+
 @pytest.mark.slow
 def test_full_size_heated_channel_one_step():
     """The 256 x 64 x 64 channel (the benchmark workload) in FP64, one step
