@@ -102,7 +102,7 @@ struct SolveState {
     int32_t fixed;           // > 0: exactly this many cycles
     int32_t notconv;         // sticky flag: a solve stopped at max_cycles above tol
     int32_t inner;           // V-cycles per outer (FP64) residual
-    int32_t pad;
+    int32_t tma_timeout;     // sticky flag: a bounded wait for a tensor copy gave up
 };
 
 // Levels lc..L-1, cycled by one CTA in shared memory.
@@ -218,6 +218,21 @@ size_t cluster_smem_bytes(const ClusterLevels& cl, int inner);
 cudaError_t prepare_coarse_cluster(int inner, int cs, size_t smem, int* max_clusters);
 cudaError_t launch_coarse_cluster(int inner, const ClusterLevels& cl, const void* r_in, void* e_out,
                                   const double* Ainv, const SolveState* st, cudaStream_t s);
+
+// fused TMA level kernels (mg_tma.cu); FP32 inner precision only
+#include <cuda.h>
+struct TmaMaps {
+    CUtensorMap e[2], r, f;   // fine level: the two e buffers, r, neighbour codes
+    CUtensorMap ec[2];        // coarse level: its two e buffers
+};
+bool tma_level_ok(const LevelDev& L, const LevelDev& Lc);
+cudaError_t tma_prepare();
+bool tma_make_maps(TmaMaps& mp, const LevelDev& L, const LevelDev& Lc, void* const* e, const void* r,
+                   void* const* ec);
+cudaError_t launch_down_tma(int nsweeps, const TmaMaps& mp, int ein, const LevelDev& L, const LevelDev& Lc,
+                            void* e_out, void* rc, SolveState* st, cudaStream_t s);
+cudaError_t launch_up_tma(int nsweeps, bool top, const TmaMaps& mp, int ein, int ecb, const LevelDev& L,
+                          const LevelDev& Lc, void* e_out, double* p, SolveState* st, cudaStream_t s);
 
 // message returned by fvm_last_error() on this thread
 void set_last_error(const std::string& msg);

@@ -216,6 +216,8 @@ struct DevLevel {
     LevelDev dev;
     void* e[2] = {nullptr, nullptr};
     void* r = nullptr;
+    bool tma = false;   // fused TMA down / up kernels on this level
+    TmaMaps maps;
 };
 
 struct fvm_case {
@@ -574,6 +576,32 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     }
     DevLevel& Lc = c->levels[l + 1];
     const double Nc = (double)Lc.dev.N;
+    if (L.tma) {
+        // fused passes: down = sweeps + residual + restriction, up = prolongation + sweeps
+        const int reps = l == 0 ? c->rule_inner : 1;
+        int cur = 0;
+        for (int rep = 0; rep < reps; ++rep) {
+            int n = c->desc.pre_sweeps;
+            if (rep == 0) {
+                if (l > 0)
+                    KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
+                            launch_sweep_first(c->inner, L.dev, L.r, L.e[0], c->sst, s));
+                n -= 1;
+            }
+            KLAUNCH(lvl_name("down_tma", l), N * (3 * si + 2) + Nc * si, 1,
+                    launch_down_tma(n, L.maps, cur, L.dev, Lc.dev, L.e[cur ^ 1], Lc.r, c->sst, s));
+            cur ^= 1;
+            int ci = 0;
+            ST_TRY(cycle(c, l + 1, ci));
+            const bool top = l == 0 && rep == reps - 1;
+            KLAUNCH(lvl_name(top ? "up_tma_to_p" : "up_tma", l), N * (3 * si + 2 + (top ? 16 : 0)) + Nc * si, 1,
+                    launch_up_tma(c->desc.post_sweeps, top, L.maps, cur, ci, L.dev, Lc.dev, L.e[cur ^ 1], c->p,
+                                  c->sst, s));
+            if (!top) cur ^= 1;
+        }
+        out_idx = cur;
+        return FVM_OK;
+    }
     // level 0: the residual kernel already did the first sweep from e = 0, and
     // runs inner_cycles V-cycles on the same r; the last sweep of the last one adds e to p
     const int reps = l == 0 ? c->rule_inner : 1;
@@ -1093,6 +1121,17 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             }
         }
     }
+    // fused TMA kernels on the grid levels that qualify (FP32 inner, tile-divisible 3D); opt-in with
+    // FVM_TMA=1: on GB300 they measure slower than the one-sweep kernels (shared-memory issue bound)
+    if (pl.inner == FVM_FP32 && getenv_flag("FVM_TMA") == 1 && d.pre_sweeps <= 3 && d.post_sweeps <= 4 &&
+        tma_prepare() == cudaSuccess) {
+        for (size_t l = 0; l < c->lc; ++l) {
+            DevLevel& D = c->levels[l];
+            DevLevel& Dc = c->levels[l + 1];
+            if (!tma_level_ok(D.dev, Dc.dev)) continue;
+            D.tma = tma_make_maps(D.maps, D.dev, Dc.dev, D.e, D.r, Dc.e);
+        }
+    }
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))
         return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
@@ -1211,7 +1250,8 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     stats.rel_residual = c->h_sst->rel;
     stats.dt_last = c->h_dt[0];
     stats.sim_time = c->h_dt[2];
-    if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
+    if (c->h_sst->tma_timeout) result = fail(FVM_ERR_CUDA, "a bounded wait for a tensor copy timed out");
+    else if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
     else if (c->h_sst->notconv) {
         result = FVM_ERR_NOT_CONVERGED;
         g_err = "V-cycle cap reached above the tolerance";
