@@ -201,9 +201,51 @@ fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n);
 /* Read b (nx*ny*nz doubles) into host memory.  Synchronises. */
 fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
 
-/* Advance every case of the array by nsteps; stats (may be NULL) is an
-   array of n entries.  Cases keep their own streams; the call returns when
-   all are done. */
+/* ---------------------------------------------------------------- batches
+   Cases stepped together (uneven sizes allowed).  Every launch site of the
+   step (each step kernel, and each multigrid kernel of each level) runs
+   once for all cases: one launch over a table of per-case kernel arguments,
+   each case's blocks laid end to end.  One time step of the whole batch is
+   one CUDA graph; its V-cycle loop runs until no case is active, and each
+   case stops on its own rule (a converged case's blocks return at once).
+   The results are those of stepping each case alone (tested bitwise).
+
+   Requirements: every case has the same precision, runs the default
+   one-sweep level kernels and the single-CTA coarse levels, and has
+   profiling off.  While a case belongs to a live batch, step it only
+   through the batch.  Memory: the batch holds device tables of its launch
+   arguments (kilobytes per case) per pointer parity; the cases keep their
+   own fields. */
+typedef struct fvm_batch fvm_batch;
+
+typedef struct {
+    int32_t n_cases;
+    int32_t graphs;                  /* CUDA graphs captured (one per pointer parity) */
+    int64_t steps;                   /* batch steps taken */
+    int64_t kernel_launches;         /* kernels run by the batch since creation */
+    int64_t cells;                   /* sum of the cases' cells */
+    int64_t launches_per_step;       /* per step outside the V-cycle loop */
+    int64_t launches_per_outer;      /* per outer V-cycle iteration (level-0 residual + V-cycle) */
+} fvm_batch_info;
+
+/* Group n cases (the array is copied; the cases stay owned by the caller,
+   who must destroy the batch before any of its cases).  stream: the
+   cudaStream_t the batch runs on, or NULL for a stream of its own.
+   Errors: FVM_ERR_INVALID (null or repeated case, mixed precisions, a case
+   on the cluster or TMA paths, profiling on), FVM_ERR_OOM, FVM_ERR_CUDA. */
+fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out);
+
+/* Advance every case by nsteps.  stats (may be NULL): n entries, in the
+   order of creation.  Returns the worst status over the cases
+   (FVM_ERR_DIVERGED before FVM_ERR_NOT_CONVERGED); fields stay readable. */
+fvm_status fvm_batch_step(fvm_batch* b, int32_t nsteps, fvm_step_stats* stats);
+
+fvm_status fvm_batch_get_info(const fvm_batch* b, fvm_batch_info* out);
+void fvm_batch_destroy(fvm_batch* b);
+
+/* One-shot form: a temporary batch of the n cases, advanced by nsteps, then
+   released (the graphs are captured on every call; keep a fvm_batch for
+   repeated stepping).  stats (may be NULL): n entries. */
 fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_stats* stats);
 
 fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
@@ -249,11 +291,10 @@ fvm_status fvm_poisson_residual_static(const double* p, const double* b, int32_t
                                        const double h[3], const int32_t dirichlet[6], double* r,
                                        double* norms, void* stream);
 
-/* sizeof of the public structs, for binding checks: out[0..6] = fvm_patch,
+/* sizeof of the public structs, for binding checks: out[0..7] = fvm_patch,
    fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
-   fvm_kernel_stat.  Needs
-   no GPU. */
-void fvm_struct_sizes(size_t out[7]);
+   fvm_kernel_stat, fvm_batch_info.  Needs no GPU. */
+void fvm_struct_sizes(size_t out[8]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* fvm_last_error(void);

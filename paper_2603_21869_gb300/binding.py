@@ -81,10 +81,17 @@ class KernelStat(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("ms", ct.c_double), ("bytes", ct.c_double)]
 
 
+class BatchInfo(ct.Structure):
+    _fields_ = [("n_cases", ct.c_int32), ("graphs", ct.c_int32), ("steps", ct.c_int64),
+                ("kernel_launches", ct.c_int64), ("cells", ct.c_int64), ("launches_per_step", ct.c_int64),
+                ("launches_per_outer", ct.c_int64)]
+
+
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
            "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-           "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static"]
+           "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
+           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy"]
 
 _lib = None
 
@@ -119,12 +126,18 @@ def lib():
                                               ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32), ct.c_void_p,
                                               ct.c_void_p, ct.c_void_p]
     L.fvm_poisson_residual_static.restype = ct.c_int
+    L.fvm_batch_create.argtypes = [ct.POINTER(CP), ct.c_int32, CP, ct.POINTER(CP)]
+    L.fvm_batch_step.argtypes = [CP, ct.c_int32, ct.POINTER(StepStats)]
+    L.fvm_batch_get_info.argtypes = [CP, ct.POINTER(BatchInfo)]
+    L.fvm_batch_destroy.argtypes = [CP]
+    L.fvm_batch_destroy.restype = None
     L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
     L.fvm_struct_sizes.restype = None
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
-                 "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read"]:
+                 "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
+                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info"]:
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -187,7 +200,7 @@ def case_bytes(spec: cases.CaseSpec) -> int:
 
 
 def struct_sizes():
-    out = (ct.c_size_t * 7)()
+    out = (ct.c_size_t * 8)()
     lib().fvm_struct_sizes(out)
     return list(out)
 
@@ -294,10 +307,55 @@ class Case:
         return {k: getattr(inf, k) for k, _ in CaseInfo._fields_}
 
 
+def _stats(s: StepStats, status=OK):
+    return {"steps": s.steps, "vcycles_total": s.vcycles_total, "vcycles_last": s.vcycles_last,
+            "rel_residual": s.rel_residual, "dt_last": s.dt_last, "sim_time": s.sim_time, "status": status}
+
+
 def step_batch(cs, nsteps, allow_not_converged=False):
+    """One-shot batched step of the cases (a temporary fvm_batch)."""
     arr = (ct.c_void_p * len(cs))(*[c.handle.value for c in cs])
     stats = (StepStats * len(cs))()
     status = lib().fvm_step_batch(arr, len(cs), nsteps, stats)
     _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
-    return [{"vcycles_total": s.vcycles_total, "rel_residual": s.rel_residual, "dt_last": s.dt_last}
-            for s in stats]
+    return [_stats(s, status) for s in stats]
+
+
+class Batch:
+    """Cases stepped together by one CUDA graph per step (fvm_batch).  The
+    cases stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, cs, stream=None):
+        self.cases = list(cs)
+        arr = (ct.c_void_p * len(self.cases))(*[c.handle.value for c in self.cases])
+        h = ct.c_void_p()
+        _check(lib().fvm_batch_create(arr, len(self.cases), stream, ct.byref(h)))
+        self._h = h
+
+    def step(self, n=1, allow_not_converged=False):
+        stats = (StepStats * len(self.cases))()
+        status = lib().fvm_batch_step(self._h, n, stats)
+        _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return [_stats(s, status) for s in stats]
+
+    def info(self):
+        inf = BatchInfo()
+        _check(lib().fvm_batch_get_info(self._h, ct.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if self._h:
+            lib().fvm_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

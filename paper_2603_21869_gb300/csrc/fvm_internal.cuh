@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fvm.h"
 
@@ -81,7 +82,7 @@ struct LevelDev {
     double inv_D;            // 1 / sum_active 2 / h_a^2
     double wJ;               // Jacobi weight
     double diag;             // sum_active 2 / h_a^2 (A's diagonal away from boundaries)
-    float inv_h2f[3], inv_Df, wJf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
+    float inv_h2f[3], inv_Df, wJf, diagf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
     const uint8_t* solid;    // nonzero = solid
     const uint8_t* dir[6];   // per boundary-face cell: 1 = Dirichlet (p = 0 on the face)
     const uint16_t* nbf;     // per cell: 2 bits per face (x-,x+,y-,y+,z-,z+): 0 fluid neighbour,
@@ -164,11 +165,13 @@ template <> struct LP<double> {
     static __device__ __forceinline__ double ih2(const LevelDev& L, int a) { return L.inv_h2[a]; }
     static __device__ __forceinline__ double iD(const LevelDev& L) { return L.inv_D; }
     static __device__ __forceinline__ double wJ(const LevelDev& L) { return L.wJ; }
+    static __device__ __forceinline__ double diag(const LevelDev& L) { return L.diag; }
 };
 template <> struct LP<float> {
     static __device__ __forceinline__ float ih2(const LevelDev& L, int a) { return L.inv_h2f[a]; }
     static __device__ __forceinline__ float iD(const LevelDev& L) { return L.inv_Df; }
     static __device__ __forceinline__ float wJ(const LevelDev& L) { return L.wJf; }
+    static __device__ __forceinline__ float diag(const LevelDev& L) { return L.diagf; }
 };
 
 // ---------------------------------------------------------------- launchers
@@ -233,6 +236,160 @@ cudaError_t launch_down_tma(int nsweeps, const TmaMaps& mp, int ein, const Level
                             void* e_out, void* rc, SolveState* st, cudaStream_t s);
 cudaError_t launch_up_tma(int nsweeps, bool top, const TmaMaps& mp, int ein, int ecb, const LevelDev& L,
                           const LevelDev& Lc, void* e_out, double* p, SolveState* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- one case or many per launch
+// Every step and multigrid kernel is a functor K with `static constexpr int
+// kThreads` and `__device__ void run(const BlockAt&) const` (the level-0
+// residual returns an int, see below).  k_one runs it over one case's grid.
+// k_many runs a table of functors, one per case, whose grids are laid end to
+// end along x: case c owns blocks [start[c], start[c + 1]) and sees its own
+// block position and grid shape, so the same body serves both.
+struct BlockAt {
+    uint3 b;   // block position in the case's grid
+    uint3 g;   // the case's grid
+};
+
+struct BatchMap {
+    const int* start;    // n + 1 block offsets (device)
+    const uint3* grid;   // each case's grid (device)
+    int n;
+};
+
+__device__ __forceinline__ int batch_case(const BatchMap& m, int blk) {
+    int lo = 0, hi = m.n - 1;   // last case whose first block is <= blk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(m.start + mid) <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ BlockAt batch_block(const BatchMap& m, int c, unsigned blk) {
+    const uint3 g = m.grid[c];
+    const unsigned l = blk - (unsigned)__ldg(m.start + c);
+    return BlockAt{make_uint3(l % g.x, (l / g.x) % g.y, l / (g.x * g.y)), g};
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads) k_one(const __grid_constant__ K k) {
+    k.run(BlockAt{blockIdx, gridDim});
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads) k_many(const K* __restrict__ ks, BatchMap m) {
+    const int c = batch_case(m, (int)blockIdx.x);
+    ks[c].run(batch_block(m, c, blockIdx.x));
+}
+
+// The level-0 residual decides whether another V-cycle runs.  Over a batch,
+// each case's last block applies that case's stopping rule; the last block of
+// the whole launch then sets the loop condition to "any case still active".
+struct BatchCtl {
+    unsigned* counter;        // blocks finished in this launch (reset by the last one)
+    SolveState* const* st;    // every case's solve state (device array)
+    int n;
+    unsigned total;           // blocks in the launch
+    cudaGraphConditionalHandle cond, cond2;
+    int use_cond;             // 0: none, 1: cond, 2: cond and cond2
+};
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ K k, cudaGraphConditionalHandle cond,
+                                                        cudaGraphConditionalHandle cond2, int use_cond) {
+    const int go = k.run(BlockAt{blockIdx, gridDim});   // >= 0 only in the deciding thread
+    if (go >= 0 && use_cond) {
+        cudaGraphSetConditional(cond, go ? 1u : 0u);
+        if (use_cond > 1) cudaGraphSetConditional(cond2, go ? 1u : 0u);
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
+    const int c = batch_case(m, (int)blockIdx.x);
+    ks[c].run(batch_block(m, c, blockIdx.x));
+    if (threadIdx.x + threadIdx.y + threadIdx.z != 0) return;
+    __threadfence();   // this case's decision (if this block made it) before the count
+    if (atomicAdd(ctl.counter, 1u) != ctl.total - 1u) return;
+    __threadfence();
+    int any = 0;
+    for (int i = 0; i < ctl.n; ++i) any |= ((volatile SolveState*)ctl.st[i])->active;
+    *ctl.counter = 0u;
+    if (ctl.use_cond) {
+        cudaGraphSetConditional(ctl.cond, any ? 1u : 0u);
+        if (ctl.use_cond > 1) cudaGraphSetConditional(ctl.cond2, any ? 1u : 0u);
+    }
+}
+
+// Host side.  While a Recorder is installed on the calling thread, launches
+// are recorded instead of issued: the batch runtime replays one case's
+// sequence of launches per case, then issues one k_many launch per site.
+using ManyFn = cudaError_t (*)(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
+                               const BatchCtl* ctl, cudaStream_t s);
+
+struct RecLaunch {
+    std::string site;                  // launch site (the profiling class name)
+    ManyFn many;                       // issues a table of this functor type
+    std::vector<unsigned char> arg;    // the functor
+    dim3 grid, block;
+    size_t smem;
+};
+
+struct Recorder {
+    std::vector<RecLaunch> out;
+    std::string site;                  // set by the caller before each launch site
+};
+
+extern thread_local Recorder* g_rec;
+
+template <class K>
+cudaError_t many_launch(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
+                        const BatchCtl*, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_many<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (nblk == 0) return cudaSuccess;   // attributes only
+    k_many<K><<<nblk, block, smem, s>>>((const K*)tab, m);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t many_launch_r0(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
+                           const BatchCtl* ctl, cudaStream_t s) {
+    if (nblk == 0) return cudaSuccess;
+    k_many_r0<K><<<nblk, block, smem, s>>>((const K*)tab, m, *ctl);
+    return cudaGetLastError();
+}
+
+template <class K>
+bool record_launch(const K& k, dim3 grid, dim3 block, size_t smem, ManyFn many) {
+    if (!g_rec) return false;
+    RecLaunch r;
+    r.site = g_rec->site;
+    r.many = many;
+    r.arg.assign((const unsigned char*)&k, (const unsigned char*)&k + sizeof(K));
+    r.grid = grid;
+    r.block = block;
+    r.smem = smem;
+    g_rec->out.push_back(std::move(r));
+    return true;
+}
+
+template <class K>
+cudaError_t launch_k(const K& k, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (record_launch(k, grid, block, smem, &many_launch<K>)) return cudaSuccess;
+    k_one<K><<<grid, block, smem, s>>>(k);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_r0(const K& k, dim3 grid, dim3 block, cudaGraphConditionalHandle cond,
+                      cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
+    if (record_launch(k, grid, block, 0, &many_launch_r0<K>)) return cudaSuccess;
+    k_one_r0<K><<<grid, block, 0, s>>>(k, cond, cond2, use_cond);
+    return cudaGetLastError();
+}
 
 // message returned by fvm_last_error() on this thread
 void set_last_error(const std::string& msg);

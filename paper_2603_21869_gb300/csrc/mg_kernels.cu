@@ -32,10 +32,10 @@ template <> struct Acc<__nv_bfloat16> { using type = float; };
 constexpr int BX = 32, BY = 4, BZ = 2;
 constexpr int kCtaThreads = 1024;
 
-__device__ __forceinline__ bool cell3(const LevelDev& L, int& i, int& j, int& k) {
-    i = blockIdx.x * BX + threadIdx.x;
-    j = blockIdx.y * BY + threadIdx.y;
-    k = blockIdx.z * BZ + threadIdx.z;
+__device__ __forceinline__ bool cell3(const LevelDev& L, const BlockAt& at, int& i, int& j, int& k) {
+    i = at.b.x * BX + threadIdx.x;
+    j = at.b.y * BY + threadIdx.y;
+    k = at.b.z * BZ + threadIdx.z;
     return i < L.n[0] && j < L.n[1] && k < L.n[2];
 }
 
@@ -79,9 +79,17 @@ __device__ __forceinline__ C sel(uint32_t code, C nb, C eP) {
     return code == 0 ? nb : (code == 1 ? eP : -eP);
 }
 
-// A e at one cell from its gathered neighbours
+// A e at one cell from its gathered neighbours.  A cell whose six faces all
+// see fluid neighbours (code bits zero; only on 3D levels, where no axis is
+// collapsed) takes diag eP - sum_a ih2_a (lo + hi) without the ghost selects.
 template <class C>
 __device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp, C ym, C yp, C zm, C zp) {
+    if ((f & 0xFFFu) == 0u) {
+        C s = (xm + xp) * LP<C>::ih2(L, 0);
+        s = fma(ym + yp, LP<C>::ih2(L, 1), s);
+        s = fma(zm + zp, LP<C>::ih2(L, 2), s);
+        return fma(LP<C>::diag(L), eP, -s);
+    }
     C acc = (C)0;
     if (L.active[0]) acc += ((eP - sel(f & 3u, xm, eP)) + (eP - sel((f >> 2) & 3u, xp, eP))) * LP<C>::ih2(L, 0);
     if (L.active[1]) acc += ((eP - sel((f >> 4) & 3u, ym, eP)) + (eP - sel((f >> 6) & 3u, yp, eP))) * LP<C>::ih2(L, 1);
@@ -89,36 +97,35 @@ __device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp,
     return acc;
 }
 
-// A p in FP64 with few FP64-pipe instructions: cells whose six faces all see fluid
-// neighbours (code bits zero) use diag p - sum_a ih2_a (lo + hi); others the general form
-__device__ __forceinline__ double A7_fp64(const LevelDev& L, uint32_t f, double eP, double xm, double xp,
-                                         double ym, double yp, double zm, double zp) {
-    if ((f & 0xFFFu) == 0u) {
-        double acc = 0.0;
-        if (L.active[0]) acc = (xm + xp) * L.inv_h2[0];
-        if (L.active[1]) acc = fma(ym + yp, L.inv_h2[1], acc);
-        if (L.active[2]) acc = fma(zm + zp, L.inv_h2[2], acc);
-        return fma(L.diag, eP, -acc);
-    }
-    return A7<double>(L, f, eP, xm, xp, ym, yp, zm, zp);
-}
+
 
 
 // ------------------------------------------------------------------ level 0 residual
 // r = b - A p (FP64), first pre-sweep e = w_J r / D, r^2 and b^2 per block;
 // the last block sums the partials in a fixed order and applies the stopping rule.
+// run() returns the decision (0 / 1) in the thread that made it, else -1.
 template <class TB, class TI>
-__global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const double* __restrict__ p,
-                                                          const TB* __restrict__ b, TI* __restrict__ r,
-                                                          TI* __restrict__ e, double* __restrict__ partials,
-                                                          SolveState* st, cudaGraphConditionalHandle cond,
-                                                          cudaGraphConditionalHandle cond2, int use_cond) {
+struct Resid0K {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev L;
+    const double* p;
+    const TB* b;
+    TI* r;
+    TI* e;
+    double* partials;
+    SolveState* st;
+    __device__ int run(const BlockAt& at) const;
+};
+
+template <class TB, class TI>
+__device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     __shared__ double red[2][BX * BY * BZ / 32];
     __shared__ bool last;
+    if (!st->active) return -1;   // a case that has converged (batched launches)
     int i, j, k;
     C r2 = (C)0, b2 = (C)0;     // squares and warp sums in the inner precision, block sums in FP64
-    if (cell3(L, i, j, k)) {
+    if (cell3(L, at, i, j, k)) {
         const int c = i + L.n[0] * (j + L.n[1] * k);
         const uint32_t f = L.nbf[c];
         // neighbour loads first (clamped indices), then the FP64 stencil
@@ -131,7 +138,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const doubl
         C rc = (C)0, bc = (C)0;
         if (!is_solid(f)) {
             const double bv = to_c<double>(braw);
-            const double Ap = A7_fp64(L, f, pP, xm, xp, ym, yp, zm, zp);
+            const double Ap = A7<double>(L, f, pP, xm, xp, ym, yp, zm, zp);
             const TI rs = from_c<TI, double>(bv - Ap);
             r[c] = rs;
             rc = to_c<C>(rs);
@@ -154,8 +161,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const doubl
         red[1][tid >> 5] = (double)b2;
     }
     __syncthreads();
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblk = at.g.x * at.g.y * at.g.z;
+    const int bid = at.b.x + at.g.x * (at.b.y + at.g.y * at.b.z);
     if (tid == 0) {
         double s0 = 0.0, s1 = 0.0;
         for (int w = 0; w < BX * BY * BZ / 32; ++w) {
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const doubl
         last = done == (unsigned)nblk - 1u;
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) return -1;
     __threadfence();
     // fixed-order reduction over all blocks' partials by the whole last block:
     // thread t sums blocks t, t + 256, ... in order (L2 loads, independent), then a
@@ -214,41 +221,58 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_resid0(LevelDev L, const doubl
             st->cycles += st->inner;
             st->total_cycles += st->inner;
         }
-        if (use_cond) {
-            cudaGraphSetConditional(cond, go ? 1u : 0u);
-            if (use_cond > 1) cudaGraphSetConditional(cond2, go ? 1u : 0u);
-        }
+        return go;
     }
+    return -1;
 }
 
-__global__ void k_solve_begin(SolveState* st) {
-    st->cycles = 0;
-    st->counter = 0u;
-    st->active = 1;
-}
+struct SolveBeginK {
+    static constexpr int kThreads = 1;
+    SolveState* st;
+    __device__ void run(const BlockAt&) const {
+        st->cycles = 0;
+        st->counter = 0u;
+        st->active = 1;
+    }
+};
 
 // ------------------------------------------------------------------ grid kernels (one level)
 template <class TI>
-__global__ void __launch_bounds__(BX * BY * BZ) k_sweep_first(LevelDev L, const TI* __restrict__ r,
-                                                               TI* __restrict__ e, const SolveState* st) {
-    using C = typename Acc<TI>::type;
-    if (!st->active) return;
-    int i, j, k;
-    if (!cell3(L, i, j, k)) return;
-    const int c = i + L.n[0] * (j + L.n[1] * k);
-    const uint32_t f = L.nbf[c];
-    e[c] = from_c<TI, C>(is_solid(f) ? (C)0 : LP<C>::wJ(L) * to_c<C>(ldg(r + c)) * LP<C>::iD(L));
-}
+struct SweepFirstK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev L;
+    const TI* r;
+    TI* e;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const {
+        using C = typename Acc<TI>::type;
+        if (!st->active) return;
+        int i, j, k;
+        if (!cell3(L, at, i, j, k)) return;
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        const uint32_t f = L.nbf[c];
+        e[c] = from_c<TI, C>(is_solid(f) ? (C)0 : LP<C>::wJ(L) * to_c<C>(ldg(r + c)) * LP<C>::iD(L));
+    }
+};
 
 // coarse r = mean over the children of (r - A e); one thread per coarse cell
 template <class TI>
-__global__ void __launch_bounds__(BX * BY * BZ) k_resid_restrict(LevelDev Lf, LevelDev Lc, const TI* __restrict__ e,
-                                                                  const TI* __restrict__ r, TI* __restrict__ rc,
-                                                                  const SolveState* st) {
+struct ResidRestrictK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev Lf, Lc;
+    const TI* e;
+    const TI* r;
+    TI* rc;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void ResidRestrictK<TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     if (!st->active) return;
     int I, J, K;
-    if (!cell3(Lc, I, J, K)) return;
+    if (!cell3(Lc, at, I, J, K)) return;
     const int fx = Lf.active[0] ? 2 : 1, fy = Lf.active[1] ? 2 : 1, fz = Lf.active[2] ? 2 : 1;
     C sum = (C)0;
     for (int dz = 0; dz < fz; ++dz)
@@ -293,17 +317,23 @@ __device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int
 }
 
 template <class TI>
-__global__ void __launch_bounds__(BX * BY * BZ) k_prolong_add(LevelDev Lf, LevelDev Lc, const TI* __restrict__ ec,
-                                                               TI* __restrict__ e, const SolveState* st) {
-    using C = typename Acc<TI>::type;
-    if (!st->active) return;
-    int i, j, k;
-    if (!cell3(Lf, i, j, k)) return;
-    const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
-    if (is_solid(Lf.nbf[c])) return;
-    const C add = prolong_at<C>(Lf.active, Lc.n, i, j, k, [&](int q) { return to_c<C>(ldg(ec + q)); });
-    e[c] = from_c<TI, C>(to_c<C>(e[c]) + add);
-}
+struct ProlongK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev Lf, Lc;
+    const TI* ec;
+    TI* e;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const {
+        using C = typename Acc<TI>::type;
+        if (!st->active) return;
+        int i, j, k;
+        if (!cell3(Lf, at, i, j, k)) return;
+        const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
+        if (is_solid(Lf.nbf[c])) return;
+        const C add = prolong_at<C>(Lf.active, Lc.n, i, j, k, [&](int q) { return to_c<C>(ldg(ec + q)); });
+        e[c] = from_c<TI, C>(to_c<C>(e[c]) + add);
+    }
+};
 
 // ------------------------------------------------------------------ marching kernels (levels >= 0)
 // Block TX x TY threads; each thread walks KZ cells along z, keeping the z
@@ -318,10 +348,10 @@ struct Walk {
     int i, j, k0, sy, sz, im, ip, jm, jp;
 };
 
-__device__ __forceinline__ bool walk_setup(const LevelDev& L, int kz, Walk& w) {
-    w.i = blockIdx.x * TX + threadIdx.x;
-    w.j = blockIdx.y * TY + threadIdx.y;
-    w.k0 = blockIdx.z * kz;
+__device__ __forceinline__ bool walk_setup(const LevelDev& L, const BlockAt& at, int kz, Walk& w) {
+    w.i = at.b.x * TX + threadIdx.x;
+    w.j = at.b.y * TY + threadIdx.y;
+    w.k0 = at.b.z * kz;
     if (w.i >= L.n[0] || w.j >= L.n[1]) return false;
     w.sy = L.n[0];
     w.sz = L.n[0] * L.n[1];
@@ -335,13 +365,23 @@ __device__ __forceinline__ bool walk_setup(const LevelDev& L, int kz, Walk& w) {
 // MODE 0: eout = sweep(ein); MODE 1: p += sweep(ein) (last level-0 sweep).
 // All loads of the thread's KZ cells are issued before any arithmetic.
 template <class TI, int MODE, int KZ>
-__global__ void __launch_bounds__(TX * TY) k_sweep_walk(LevelDev L, const TI* __restrict__ ein,
-                                                        const TI* __restrict__ r, TI* __restrict__ eout,
-                                                        double* __restrict__ p, const SolveState* st) {
+struct SweepK {
+    static constexpr int kThreads = TX * TY;
+    LevelDev L;
+    const TI* ein;
+    const TI* r;
+    TI* eout;
+    double* p;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI, int MODE, int KZ>
+__device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     if (!st->active) return;
     Walk w;
-    if (!walk_setup(L, KZ, w)) return;
+    if (!walk_setup(L, at, KZ, w)) return;
     const int nz = L.n[2];
     const int c0 = w.i + w.sy * w.j + w.sz * w.k0;
     const int kn = nz - w.k0 < KZ ? nz - w.k0 : KZ;   // cells of this thread
@@ -383,15 +423,24 @@ __global__ void __launch_bounds__(TX * TY) k_sweep_walk(LevelDev L, const TI* __
 // z pair of children in the thread), x / y pairs summed through shared memory.
 // Needs x and y active (2 x 2 children in the plane).
 template <class TI>
-__global__ void __launch_bounds__(TX * TY) k_resid_restrict_walk(LevelDev Lf, LevelDev Lc, const TI* __restrict__ e,
-                                                                 const TI* __restrict__ r, TI* __restrict__ rc,
-                                                                 const SolveState* st) {
+struct RRWalkK {
+    static constexpr int kThreads = TX * TY;
+    LevelDev Lf, Lc;
+    const TI* e;
+    const TI* r;
+    TI* rc;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void RRWalkK<TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     __shared__ C part[TY][TX + 1];
     if (!st->active) return;
     const int fz = Lf.active[2] ? 2 : 1;
     Walk w;
-    const bool in = walk_setup(Lf, fz, w);
+    const bool in = walk_setup(Lf, at, fz, w);
     C sum = (C)0;
     if (in) {
         const int nz = Lf.n[2];
@@ -412,11 +461,11 @@ __global__ void __launch_bounds__(TX * TY) k_resid_restrict_walk(LevelDev Lf, Le
     part[threadIdx.y][threadIdx.x] = sum;
     __syncthreads();
     if (threadIdx.x < TX / 2 && threadIdx.y < TY / 2) {
-        const int I = blockIdx.x * (TX / 2) + threadIdx.x, J = blockIdx.y * (TY / 2) + threadIdx.y;
+        const int I = at.b.x * (TX / 2) + threadIdx.x, J = at.b.y * (TY / 2) + threadIdx.y;
         if (I < Lc.n[0] && J < Lc.n[1]) {
             const int x = 2 * threadIdx.x, y = 2 * threadIdx.y;
             const C s4 = (part[y][x] + part[y][x + 1]) + (part[y + 1][x] + part[y + 1][x + 1]);
-            rc[I + Lc.n[0] * (J + Lc.n[1] * blockIdx.z)] = from_c<TI, C>(s4 / (C)(4 * fz));
+            rc[I + Lc.n[0] * (J + Lc.n[1] * (int)at.b.z)] = from_c<TI, C>(s4 / (C)(4 * fz));
         }
     }
 }
@@ -431,9 +480,18 @@ __device__ __forceinline__ C cta_apply_A(const LevelDev& L, uint32_t f, const C*
 }
 
 template <class TI>
-__global__ void __launch_bounds__(kCtaThreads) k_coarse_cta(CoarseLevels cl, const TI* __restrict__ r_in,
-                                                             TI* __restrict__ e_out, const double* __restrict__ Ainv,
-                                                             const SolveState* st) {
+struct CoarseK {
+    static constexpr int kThreads = kCtaThreads;
+    CoarseLevels cl;
+    const TI* r_in;
+    TI* e_out;
+    const double* Ainv;
+    const SolveState* st;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void CoarseK<TI>::run(const BlockAt&) const {
     using C = typename Acc<TI>::type;
     if (!st->active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -605,28 +663,29 @@ size_t coarse_cta_smem(const CoarseLevels& cl, int inner) {
     } while (0)
 
 cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
-    k_solve_begin<<<1, 1, 0, s>>>(st);
-    return cudaGetLastError();
+    return launch_k(SolveBeginK{st}, dim3(1), dim3(1), 0, s);
 }
 
 cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
                           double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                           cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
     DISPATCH_I(inner, {
         if (bprec == FVM_FP64)
-            k_resid0<double, TI><<<grid3(L), kBlock3, 0, s>>>(L, p, (const double*)b, (TI*)r, (TI*)e, partials, st,
-                                                              cond, cond2, use_cond);
+            err = launch_r0(Resid0K<double, TI>{L, p, (const double*)b, (TI*)r, (TI*)e, partials, st}, grid3(L),
+                            kBlock3, cond, cond2, use_cond, s);
         else
-            k_resid0<float, TI><<<grid3(L), kBlock3, 0, s>>>(L, p, (const float*)b, (TI*)r, (TI*)e, partials, st,
-                                                             cond, cond2, use_cond);
+            err = launch_r0(Resid0K<float, TI>{L, p, (const float*)b, (TI*)r, (TI*)e, partials, st}, grid3(L),
+                            kBlock3, cond, cond2, use_cond, s);
     });
-    return cudaGetLastError();
+    return err;
 }
 
 cudaError_t launch_sweep_first(int inner, const LevelDev& L, const void* r, void* e, const SolveState* st,
                                cudaStream_t s) {
-    DISPATCH_I(inner, k_sweep_first<TI><<<grid3(L), kBlock3, 0, s>>>(L, (const TI*)r, (TI*)e, st));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k(SweepFirstK<TI>{L, (const TI*)r, (TI*)e, st}, grid3(L), kBlock3, 0, s));
+    return err;
 }
 
 static dim3 walk_grid(const LevelDev& L, int kz) {
@@ -635,48 +694,51 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
 }
 
 template <class TI, int MODE>
-static void sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p, const SolveState* st,
-                       cudaStream_t s) {
+static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p,
+                              const SolveState* st, cudaStream_t s) {
     if (L.N >= kWalkMinCells)
-        k_sweep_walk<TI, MODE, 4><<<walk_grid(L, 4), dim3(TX, TY), 0, s>>>(L, ein, r, eout, p, st);
-    else
-        k_sweep_walk<TI, MODE, 1><<<walk_grid(L, 1), dim3(TX, TY), 0, s>>>(L, ein, r, eout, p, st);
+        return launch_k(SweepK<TI, MODE, 4>{L, ein, r, eout, p, st}, walk_grid(L, 4), dim3(TX, TY), 0, s);
+    return launch_k(SweepK<TI, MODE, 1>{L, ein, r, eout, p, st}, walk_grid(L, 1), dim3(TX, TY), 0, s);
 }
 
 cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
                          const SolveState* st, cudaStream_t s) {
-    DISPATCH_I(inner, sweep_walk<TI, 0>(L, (const TI*)e_in, (const TI*)r, (TI*)e_out, nullptr, st, s));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = sweep_walk<TI, 0>(L, (const TI*)e_in, (const TI*)r, (TI*)e_out, nullptr, st, s));
+    return err;
 }
 
 cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
                               const SolveState* st, cudaStream_t s) {
-    DISPATCH_I(inner, sweep_walk<TI, 1>(L, (const TI*)e_in, (const TI*)r, nullptr, p, st, s));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = sweep_walk<TI, 1>(L, (const TI*)e_in, (const TI*)r, nullptr, p, st, s));
+    return err;
 }
 
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
                                   void* rc, const SolveState* st, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
     if (Lf.active[0] && Lf.active[1]) {
         const int fz = Lf.active[2] ? 2 : 1;
-        DISPATCH_I(inner, k_resid_restrict_walk<TI><<<walk_grid(Lf, fz), dim3(TX, TY), 0, s>>>(
-                              Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st));
+        DISPATCH_I(inner, err = launch_k(RRWalkK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st},
+                                         walk_grid(Lf, fz), dim3(TX, TY), 0, s));
     } else {
-        DISPATCH_I(inner, k_resid_restrict<TI><<<grid3(Lc), kBlock3, 0, s>>>(Lf, Lc, (const TI*)e, (const TI*)r,
-                                                                              (TI*)rc, st));
+        DISPATCH_I(inner, err = launch_k(ResidRestrictK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st},
+                                         grid3(Lc), kBlock3, 0, s));
     }
-    return cudaGetLastError();
+    return err;
 }
 
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s) {
-    DISPATCH_I(inner, k_prolong_add<TI><<<grid3(Lf), kBlock3, 0, s>>>(Lf, Lc, (const TI*)ec, (TI*)e, st));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k(ProlongK<TI>{Lf, Lc, (const TI*)ec, (TI*)e, st}, grid3(Lf), kBlock3, 0, s));
+    return err;
 }
 
 cudaError_t prepare_coarse_cta(int inner, size_t smem) {
     DISPATCH_I(inner, {
-        cudaError_t err = cudaFuncSetAttribute(k_coarse_cta<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t err = cudaFuncSetAttribute(k_one<CoarseK<TI>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return err;
     });
@@ -686,8 +748,10 @@ cudaError_t prepare_coarse_cta(int inner, size_t smem) {
 cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_in, void* e_out, const double* Ainv,
                               const SolveState* st, cudaStream_t s) {
     const size_t smem = coarse_cta_smem(cl, inner);
-    DISPATCH_I(inner, k_coarse_cta<TI><<<1, kCtaThreads, smem, s>>>(cl, (const TI*)r_in, (TI*)e_out, Ainv, st));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k(CoarseK<TI>{cl, (const TI*)r_in, (TI*)e_out, Ainv, st}, dim3(1),
+                                     dim3(kCtaThreads), smem, s));
+    return err;
 }
 
 cudaError_t launch_convert(int sp, int dp, const void* src, void* dst, int64_t N, cudaStream_t s) {

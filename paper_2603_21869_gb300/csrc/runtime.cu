@@ -212,6 +212,8 @@ bool coarse_inverse(const HostLevel& L, std::vector<double>& inv) {
 
 void set_last_error(const std::string& msg) { g_err = msg; }
 
+thread_local Recorder* g_rec = nullptr;
+
 struct DevLevel {
     LevelDev dev;
     void* e[2] = {nullptr, nullptr};
@@ -544,6 +546,7 @@ void prof_clear(fvm_case* c) {
 // profiling events when the hook is on.  `bytes` = algorithmic bytes.
 #define KLAUNCH(name, bytes, nk, expr)                  \
     do {                                                \
+        if (g_rec) g_rec->site = (name);                \
         const int pi_ = prof_begin(c, (name), (bytes)); \
         CUDA_TRY(expr);                                 \
         prof_end(c, pi_);                               \
@@ -999,6 +1002,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         for (int a = 0; a < 3; ++a) v.inv_h2f[a] = (float)v.inv_h2[a];
         v.inv_Df = (float)v.inv_D;
         v.wJf = (float)v.wJ;
+        v.diagf = (float)v.diag;
         if (l == 0) v.solid = tag_d;
         else {
             uint8_t* sd;
@@ -1158,6 +1162,420 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     return FVM_OK;
 }
 
+
+// ------------------------------------------------------------------ batches
+// Several cases stepped together: each step kernel and multigrid kernel runs
+// once per launch site for all cases (k_many over a table of per-case
+// functors), inside one CUDA graph per pointer parity.  The sequence of
+// launches is obtained by replaying each case's own step with a Recorder
+// installed, so a batched step issues exactly the kernels the cases would
+// issue alone, merged site by site.
+
+struct BatchGather {
+    int32_t cycles, total_cycles, nonfinite, notconv, inner, pad;
+    double rel, dt, sim_time;
+};
+
+// Copy each case's solve state and time step into one array, and add this
+// step's outer V-cycle iterations (the maximum over the cases) to a counter.
+__global__ void k_batch_gather(SolveState* const* sts, double* const* dts, BatchGather* out, int n,
+                               unsigned long long* outer_sum) {
+    int mx = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const SolveState* s = sts[i];
+        BatchGather g;
+        g.cycles = s->cycles;
+        g.total_cycles = s->total_cycles;
+        g.nonfinite = s->nonfinite;
+        g.notconv = s->notconv;
+        g.inner = s->inner;
+        g.pad = 0;
+        g.rel = s->rel;
+        g.dt = dts[i][0];
+        g.sim_time = dts[i][2];
+        out[i] = g;
+        const int outer = s->cycles / (s->inner > 0 ? s->inner : 1);
+        mx = outer > mx ? outer : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    __shared__ int wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, wm[w]);
+        mx = max(mx, wm[0]);
+        *outer_sum += (unsigned long long)mx;
+    }
+}
+
+// One launch of the batched step: a functor type, the cases that take part
+// and their recorded functors.
+struct Merged {
+    ManyFn many;
+    std::string site;
+    dim3 block;
+    size_t smem = 0;
+    std::vector<int> cases;
+    std::vector<const RecLaunch*> recs;
+    // device table (filled when the arena is built)
+    const void* tab = nullptr;
+    BatchMap map{};
+    unsigned nblk = 0;
+    BatchCtl ctl{};
+};
+
+// Merge the cases' launch sequences site by site, keeping each case's order.
+// A launch is identified by (site, functor type, occurrence of that pair in
+// the case's sequence); a key is issued for all cases at once unless a case
+// still has it further ahead, in which case another key goes first.
+std::vector<Merged> merge_sequences(const std::vector<std::vector<RecLaunch>>& seqs) {
+    struct Key {
+        std::string site;
+        ManyFn many;
+        int occ;
+        bool operator==(const Key& o) const { return many == o.many && occ == o.occ && site == o.site; }
+    };
+    const int n = (int)seqs.size();
+    std::vector<std::vector<Key>> keys(n);
+    for (int i = 0; i < n; ++i) {
+        std::vector<std::pair<std::string, ManyFn>> seen;
+        std::vector<int> count;
+        for (const RecLaunch& r : seqs[i]) {
+            int occ = 0;
+            size_t q = 0;
+            for (; q < seen.size(); ++q)
+                if (seen[q].first == r.site && seen[q].second == r.many) break;
+            if (q == seen.size()) {
+                seen.push_back({r.site, r.many});
+                count.push_back(0);
+            }
+            occ = count[q]++;
+            keys[i].push_back(Key{r.site, r.many, occ});
+        }
+    }
+    auto pending_later = [&](int j, size_t from, const Key& k) {
+        for (size_t q = from + 1; q < keys[j].size(); ++q)
+            if (keys[j][q] == k) return true;
+        return false;
+    };
+    std::vector<size_t> cur(n, 0);
+    std::vector<Merged> out;
+    for (;;) {
+        int pick = -1, first = -1;
+        for (int i = 0; i < n && pick < 0; ++i) {
+            if (cur[i] >= keys[i].size()) continue;
+            if (first < 0) first = i;
+            const Key& k = keys[i][cur[i]];
+            bool ok = true;
+            for (int j = 0; j < n && ok; ++j)
+                if (cur[j] < keys[j].size() && !(keys[j][cur[j]] == k) && pending_later(j, cur[j], k)) ok = false;
+            if (ok) pick = i;
+        }
+        if (first < 0) break;
+        if (pick < 0) pick = first;
+        const Key k = keys[pick][cur[pick]];
+        Merged m;
+        m.many = k.many;
+        m.site = k.site;
+        m.block = seqs[pick][cur[pick]].block;
+        for (int j = 0; j < n; ++j) {
+            if (cur[j] >= keys[j].size() || !(keys[j][cur[j]] == k)) continue;
+            const RecLaunch& r = seqs[j][cur[j]];
+            m.cases.push_back(j);
+            m.recs.push_back(&r);
+            m.smem = std::max(m.smem, r.smem);
+            ++cur[j];
+        }
+        out.push_back(std::move(m));
+    }
+    return out;
+}
+
+}  // namespace
+
+struct fvm_batch {
+    std::vector<fvm_case*> cases;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t side = nullptr;
+    struct Graph {
+        std::vector<void*> before, after;   // 12 state pointers per case
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        void* arena = nullptr;              // functor tables, block maps, state lists
+        int64_t per_step = 0;               // launches outside the V-cycle loop
+        int64_t per_outer = 0;              // launches per outer iteration (V-cycle body)
+    };
+    std::vector<Graph> graphs;
+    SolveState** d_sts = nullptr;
+    double** d_dts = nullptr;
+    BatchGather* d_gather = nullptr;
+    BatchGather* h_gather = nullptr;
+    unsigned long long* d_outer = nullptr;
+    unsigned long long* h_outer = nullptr;
+    int64_t launches = 0;
+    int64_t steps = 0;
+};
+
+namespace {
+
+void free_batch(fvm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto& G : b->graphs) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+        if (G.arena) cudaFree(G.arena);
+    }
+    if (b->d_sts) cudaFree(b->d_sts);
+    if (b->d_dts) cudaFree(b->d_dts);
+    if (b->d_gather) cudaFree(b->d_gather);
+    if (b->d_outer) cudaFree(b->d_outer);
+    if (b->h_gather) cudaFreeHost(b->h_gather);
+    if (b->h_outer) cudaFreeHost(b->h_outer);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Lay the merged launches' tables into one device buffer: per launch the
+// functor table, the block offsets, the per-case grids, and (resid0) the
+// block counter and the list of its cases' solve states.
+fvm_status build_arena(std::vector<Merged>* segs, int nseg, const std::vector<fvm_case*>& cases, void** arena_out) {
+    auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+    size_t bytes = 0;
+    for (int s = 0; s < nseg; ++s)
+        for (Merged& m : segs[s]) {
+            const size_t n = m.cases.size();
+            bytes = up(bytes, 256) + n * m.recs[0]->arg.size();
+            bytes = up(bytes, 16) + (n + 1) * sizeof(int);
+            bytes = up(bytes, 16) + n * sizeof(uint3);
+            bytes = up(bytes, 16) + n * sizeof(SolveState*);
+            bytes = up(bytes, 16) + 16;
+        }
+    bytes = up(bytes, 256);
+    std::vector<unsigned char> host(bytes, 0);
+    void* dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FVM_ERR_OOM, std::string("batch tables: ") + cudaGetErrorString(e));
+    }
+    unsigned char* d = (unsigned char*)dev;
+    size_t off = 0;
+    for (int s = 0; s < nseg; ++s)
+        for (Merged& m : segs[s]) {
+            const size_t n = m.cases.size();
+            const size_t ksz = m.recs[0]->arg.size();
+            off = up(off, 256);
+            m.tab = d + off;
+            for (size_t i = 0; i < n; ++i) memcpy(&host[off + i * ksz], m.recs[i]->arg.data(), ksz);
+            off += n * ksz;
+            off = up(off, 16);
+            int* start = (int*)&host[off];
+            m.map.start = (const int*)(d + off);
+            int64_t tot = 0;
+            for (size_t i = 0; i < n; ++i) {
+                start[i] = (int)tot;
+                const dim3 g = m.recs[i]->grid;
+                tot += (int64_t)g.x * g.y * g.z;
+            }
+            start[n] = (int)tot;
+            off += (n + 1) * sizeof(int);
+            off = up(off, 16);
+            uint3* grid = (uint3*)&host[off];
+            m.map.grid = (const uint3*)(d + off);
+            for (size_t i = 0; i < n; ++i)
+                grid[i] = make_uint3(m.recs[i]->grid.x, m.recs[i]->grid.y, m.recs[i]->grid.z);
+            off += n * sizeof(uint3);
+            off = up(off, 16);
+            SolveState** lst = (SolveState**)&host[off];
+            m.ctl.st = (SolveState* const*)(d + off);
+            for (size_t i = 0; i < n; ++i) lst[i] = cases[m.cases[i]]->sst;
+            off += n * sizeof(SolveState*);
+            off = up(off, 16);
+            m.ctl.counter = (unsigned*)(d + off);   // zero
+            off += 16;
+            m.map.n = (int)n;
+            m.ctl.n = (int)n;
+            if (tot >= ((int64_t)1 << 31)) {
+                cudaFree(dev);
+                return fail(FVM_ERR_INVALID, "batch too large for one launch");
+            }
+            m.nblk = (unsigned)tot;
+            m.ctl.total = (unsigned)tot;
+        }
+    e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dev);
+        return fail(FVM_ERR_CUDA, std::string("batch tables upload: ") + cudaGetErrorString(e));
+    }
+    *arena_out = dev;
+    return FVM_OK;
+}
+
+fvm_status issue(std::vector<Merged>& seg, cudaStream_t s) {
+    for (Merged& m : seg) {
+        cudaError_t e = m.many(m.tab, m.map, m.nblk, m.block, m.smem, &m.ctl, s);
+        if (e != cudaSuccess) return fail(FVM_ERR_CUDA, "batched launch " + m.site + ": " + cudaGetErrorString(e));
+    }
+    return FVM_OK;
+}
+
+// Record every case's step (four segments: step kernels up to the solve,
+// the level-0 residual, one V-cycle, the projection), merge, build the
+// tables and capture the graph.
+fvm_status batch_capture(fvm_batch* B, fvm_batch::Graph& G) {
+    const int n = (int)B->cases.size();
+    std::vector<std::vector<RecLaunch>> rec[4];
+    for (int s = 0; s < 4; ++s) rec[s].resize(n);
+    G.before.assign(12 * (size_t)n, nullptr);
+    G.after.assign(12 * (size_t)n, nullptr);
+    fvm_status st = FVM_OK;
+    for (int i = 0; i < n && st == FVM_OK; ++i) {
+        fvm_case* c = B->cases[i];
+        save_ptrs(c, &G.before[12 * (size_t)i]);
+        const int64_t launches0 = c->launches;
+        Recorder R;
+        g_rec = &R;
+        for (int k : {FVM_STAGE_DT, FVM_STAGE_DESTRUCTION, FVM_STAGE_EXPLICIT, FVM_STAGE_DESTRUCTION, FVM_STAGE_RHS})
+            if (st == FVM_OK) st = stage(c, k, nullptr, nullptr);
+        if (st == FVM_OK) {
+            R.site = "solve_begin";
+            if (launch_solve_begin(c->sst, c->stream) != cudaSuccess) st = fail(FVM_ERR_CUDA, "solve_begin");
+        }
+        rec[0][i].swap(R.out);
+        if (st == FVM_OK) st = residual0(c, 0, 0, 0);
+        rec[1][i].swap(R.out);
+        int idx = 0;
+        if (st == FVM_OK) st = cycle(c, 0, idx);
+        rec[2][i].swap(R.out);
+        if (st == FVM_OK) st = stage(c, FVM_STAGE_PROJECT, nullptr, nullptr);
+        rec[3][i].swap(R.out);
+        g_rec = nullptr;
+        save_ptrs(c, &G.after[12 * (size_t)i]);
+        load_ptrs(c, &G.before[12 * (size_t)i]);
+        c->launches = launches0;
+    }
+    g_rec = nullptr;
+    if (st != FVM_OK) return st;
+    std::vector<Merged> seg[4];
+    for (int s = 0; s < 4; ++s) seg[s] = merge_sequences(rec[s]);
+    if (seg[1].size() != 1)
+        return fail(FVM_ERR_INVALID, "batched cases need the same precisions (one level-0 residual launch)");
+    ST_TRY(build_arena(seg, 4, B->cases, &G.arena));
+    // dynamic shared-memory limits of the batched kernels (outside the capture)
+    for (int s = 0; s < 4; ++s)
+        for (Merged& m : seg[s]) CUDA_TRY(m.many(m.tab, m.map, 0, m.block, m.smem, &m.ctl, B->stream));
+    G.per_step = (int64_t)(seg[0].size() + seg[3].size()) + 1 /* gather */ + 1 /* last residual */;
+    G.per_outer = 1 + (int64_t)seg[2].size();
+    cudaStream_t s = B->stream;
+    if (!B->side) CUDA_TRY(cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    auto abort_capture = [&](fvm_status e) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return e;
+    };
+    if ((st = issue(seg[0], s)) != FVM_OK) return abort_capture(st);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaStreamGetCaptureInfo"));
+    cudaGraphConditionalHandle hw, hi;
+    if (cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaGraphConditionalHandleCreate"));
+    cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &wp) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "adding the while node"));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaGraphConditionalHandleCreate (if)"));
+    if (cudaStreamBeginCaptureToGraph(B->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "capturing the while body"));
+    Merged& r0 = seg[1][0];
+    r0.ctl.cond = hw;
+    r0.ctl.cond2 = hi;
+    r0.ctl.use_cond = 2;
+    st = issue(seg[1], B->side);
+    cudaStreamCaptureStatus bcs;
+    cudaGraph_t bg = nullptr;
+    const cudaGraphNode_t* bdeps = nullptr;
+    size_t nbdeps = 0;
+    cudaGraphNode_t inode;
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    bool ok = st == FVM_OK &&
+              cudaStreamGetCaptureInfo(B->side, &bcs, nullptr, &bg, &bdeps, nullptr, &nbdeps) == cudaSuccess;
+    if (ok) {
+        ip.conditional.handle = hi;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        ok = cudaGraphAddNode(&inode, bg, bdeps, nullptr, nbdeps, &ip) == cudaSuccess;
+    }
+    cudaGraph_t done_body = nullptr;
+    cudaStreamEndCapture(B->side, &done_body);
+    if (!ok) return abort_capture(st != FVM_OK ? st : fail(FVM_ERR_CUDA, "adding the if node"));
+    cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(B->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "capturing the V-cycle body"));
+    st = issue(seg[2], B->side);
+    cudaGraph_t done_if = nullptr;
+    cudaStreamEndCapture(B->side, &done_if);
+    if (st != FVM_OK) return abort_capture(st);
+    if (cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return abort_capture(fail(FVM_ERR_CUDA, "cudaStreamUpdateCaptureDependencies"));
+    if ((st = issue(seg[3], s)) != FVM_OK) return abort_capture(st);
+    k_batch_gather<<<1, 256, 0, s>>>(B->d_sts, B->d_dts, B->d_gather, n, B->d_outer);
+    if (cudaGetLastError() != cudaSuccess) return abort_capture(fail(FVM_ERR_CUDA, "gather launch"));
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamEndCapture(s, &g));
+    G.g = g;
+    cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FVM_ERR_CUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(e));
+    }
+    return FVM_OK;
+}
+
+int find_batch_graph(fvm_batch* B) {
+    const size_t n = B->cases.size();
+    std::vector<void*> now(12 * n);
+    for (size_t i = 0; i < n; ++i) save_ptrs(B->cases[i], &now[12 * i]);
+    for (size_t g = 0; g < B->graphs.size(); ++g)
+        if (B->graphs[g].before == now) return (int)g;
+    return -1;
+}
+
+// Can these cases be stepped as one batch?
+fvm_status batch_check(fvm_case* const* cases, int n) {
+    if (!cases || n < 1) return fail(FVM_ERR_INVALID, "need at least one case");
+    for (int i = 0; i < n; ++i) {
+        const fvm_case* c = cases[i];
+        if (!c) return fail(FVM_ERR_INVALID, "null case in the batch");
+        for (int j = 0; j < i; ++j)
+            if (cases[j] == c) return fail(FVM_ERR_INVALID, "a case appears twice in the batch");
+        if (c->prec != cases[0]->prec || c->inner != cases[0]->inner)
+            return fail(FVM_ERR_INVALID, "batched cases need the same precision");
+        if (c->use_cluster) return fail(FVM_ERR_INVALID, "batched cases need the single-CTA coarse levels");
+        for (const DevLevel& L : c->levels)
+            if (L.tma) return fail(FVM_ERR_INVALID, "batched cases need the one-sweep level kernels");
+        if (c->prof) return fail(FVM_ERR_INVALID, "profiling is on for a batched case");
+    }
+    return FVM_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C-ABI
@@ -1270,7 +1688,9 @@ fvm_status fvm_vcycle(fvm_case* c, int ncycles, double* rel_residual) {
         ST_TRY(set_rule(c, ncycles));
         st = solve(c, cycles, rel);
     } else {
-        // residual only: whatever the rule decides, no cycle is launched
+        // residual only: whatever the rule decides, no cycle is launched (the rule is reset
+        // first: the residual kernel skips a solve that is no longer active)
+        ST_TRY(set_rule(c, c->desc.fixed_vcycles));
         ST_TRY(residual0(c, 0, 0, 0));
         ST_TRY(read_state(c));
         rel = c->h_sst->rel;
@@ -1349,14 +1769,143 @@ fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n) {
     return FVM_OK;
 }
 
+fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out) {
+    if (!out) return fail(FVM_ERR_INVALID, "null output");
+    ST_TRY(batch_check(cases, n));
+    fvm_batch* B = new fvm_batch;
+    B->cases.assign(cases, cases + n);
+    auto bail = [&](fvm_status st) {
+        free_batch(B);
+        return st;
+    };
+    if (stream) B->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(FVM_ERR_CUDA, "cudaStreamCreate"));
+        B->own_stream = true;
+    }
+    std::vector<SolveState*> sts(n);
+    std::vector<double*> dts(n);
+    for (int i = 0; i < n; ++i) {
+        sts[i] = cases[i]->sst;
+        dts[i] = cases[i]->dt_state;
+    }
+    if (cudaMalloc((void**)&B->d_sts, n * sizeof(SolveState*)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_dts, n * sizeof(double*)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_gather, n * sizeof(BatchGather)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_outer, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_gather, n * sizeof(BatchGather)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_outer, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(FVM_ERR_OOM, "batch buffers"));
+    }
+    if (cudaMemcpy(B->d_sts, sts.data(), n * sizeof(SolveState*), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B->d_dts, dts.data(), n * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(FVM_ERR_CUDA, "batch pointer tables"));
+    g_err.clear();
+    *out = B;
+    return FVM_OK;
+}
+
+void fvm_batch_destroy(fvm_batch* b) { free_batch(b); }
+
+fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
+    if (!B) return fail(FVM_ERR_INVALID, "null batch");
+    if (nsteps < 0) return fail(FVM_ERR_INVALID, "nsteps < 0");
+    ST_TRY(batch_check(B->cases.data(), (int)B->cases.size()));
+    const int n = (int)B->cases.size();
+    cudaStream_t s = B->stream;
+    // earlier work on the cases' own streams comes first
+    for (fvm_case* c : B->cases) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (fvm_case* c : B->cases) {
+        CUDA_TRY(cudaMemsetAsync(&c->sst->total_cycles, 0, sizeof(int32_t), s));
+        CUDA_TRY(cudaMemsetAsync(&c->sst->nonfinite, 0, sizeof(int32_t), s));
+        CUDA_TRY(cudaMemsetAsync(&c->sst->notconv, 0, sizeof(int32_t), s));
+    }
+    CUDA_TRY(cudaMemsetAsync(B->d_outer, 0, sizeof(unsigned long long), s));
+    int64_t fixed = 0, per_outer = 0;
+    for (int k = 0; k < nsteps; ++k) {
+        int g = find_batch_graph(B);
+        if (g < 0) {
+            fvm_batch::Graph G;
+            fvm_status st = batch_capture(B, G);
+            if (st != FVM_OK) {
+                if (G.exec) cudaGraphExecDestroy(G.exec);
+                if (G.g) cudaGraphDestroy(G.g);
+                if (G.arena) cudaFree(G.arena);
+                return st;
+            }
+            B->graphs.push_back(G);
+            g = (int)B->graphs.size() - 1;
+        }
+        const fvm_batch::Graph& G = B->graphs[g];
+        CUDA_TRY(cudaGraphLaunch(G.exec, s));
+        for (int i = 0; i < n; ++i) {
+            load_ptrs(B->cases[i], &G.after[12 * (size_t)i]);
+            ++B->cases[i]->steps;
+        }
+        fixed += G.per_step;
+        per_outer = G.per_outer;
+        ++B->steps;
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->h_gather, B->d_gather, n * sizeof(BatchGather), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(B->h_outer, B->d_outer, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (nsteps > 0) B->launches += fixed + (int64_t)*B->h_outer * per_outer;
+    fvm_status result = FVM_OK;
+    for (int i = 0; i < n; ++i) {
+        const BatchGather& q = B->h_gather[i];
+        if (stats) {
+            fvm_step_stats& o = stats[i];
+            memset(&o, 0, sizeof(o));
+            o.steps = nsteps;
+            if (nsteps > 0) {
+                o.vcycles_total = q.total_cycles;
+                o.vcycles_last = q.cycles;
+                o.rel_residual = q.rel;
+                o.dt_last = q.dt;
+                o.sim_time = q.sim_time;
+            }
+        }
+        if (nsteps > 0 && q.nonfinite && result != FVM_ERR_DIVERGED)
+            result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual in case " + std::to_string(i));
+        else if (nsteps > 0 && q.notconv && result == FVM_OK) {
+            result = FVM_ERR_NOT_CONVERGED;
+            g_err = "V-cycle cap reached above the tolerance in case " + std::to_string(i);
+        }
+    }
+    return result;
+}
+
+fvm_status fvm_batch_get_info(const fvm_batch* B, fvm_batch_info* out) {
+    if (!B || !out) return fail(FVM_ERR_INVALID, "null batch or output");
+    fvm_batch_info info;
+    memset(&info, 0, sizeof(info));
+    info.n_cases = (int32_t)B->cases.size();
+    info.graphs = (int32_t)B->graphs.size();
+    info.steps = B->steps;
+    info.kernel_launches = B->launches;
+    int64_t cells = 0;
+    for (const fvm_case* c : B->cases) cells += c->cd.N;
+    info.cells = cells;
+    if (!B->graphs.empty()) {
+        info.launches_per_step = B->graphs[0].per_step;
+        info.launches_per_outer = B->graphs[0].per_outer;
+    }
+    *out = info;
+    return FVM_OK;
+}
+
 fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_stats* stats) {
     if (!cases || n < 0) return fail(FVM_ERR_INVALID, "bad case array");
-    fvm_status worst = FVM_OK;
-    for (int i = 0; i < n; ++i) {
-        fvm_status st = fvm_step(cases[i], nsteps, stats ? stats + i : nullptr);
-        if (st != FVM_OK && (worst == FVM_OK || st < worst)) worst = st;
-    }
-    return worst;
+    if (n == 0) return FVM_OK;
+    fvm_batch* B = nullptr;
+    ST_TRY(fvm_batch_create(cases, n, nullptr, &B));
+    fvm_status st = fvm_batch_step(B, nsteps, stats);
+    const std::string msg = g_err;
+    free_batch(B);
+    g_err = msg;
+    return st;
 }
 
 fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out) {
@@ -1419,7 +1968,7 @@ fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_o
     return FVM_OK;
 }
 
-void fvm_struct_sizes(size_t out[7]) {
+void fvm_struct_sizes(size_t out[8]) {
     out[0] = sizeof(fvm_patch);
     out[1] = sizeof(fvm_vent);
     out[2] = sizeof(fvm_box);
@@ -1427,6 +1976,7 @@ void fvm_struct_sizes(size_t out[7]) {
     out[4] = sizeof(fvm_step_stats);
     out[5] = sizeof(fvm_case_info);
     out[6] = sizeof(fvm_kernel_stat);
+    out[7] = sizeof(fvm_batch_info);
 }
 
 const char* fvm_last_error(void) { return g_err.c_str(); }

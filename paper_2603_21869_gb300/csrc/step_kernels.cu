@@ -31,10 +31,10 @@ constexpr double kOmegaMin = 1e-8;
 constexpr int kThreads = 256;
 constexpr int BX = 32, BY = 4, BZ = 2;
 
-__device__ __forceinline__ bool cell3(const CaseDev& cd, int& i, int& j, int& k) {
-    i = blockIdx.x * BX + threadIdx.x;
-    j = blockIdx.y * BY + threadIdx.y;
-    k = blockIdx.z * BZ + threadIdx.z;
+__device__ __forceinline__ bool cell3(const CaseDev& cd, const BlockAt& at, int& i, int& j, int& k) {
+    i = at.b.x * BX + threadIdx.x;
+    j = at.b.y * BY + threadIdx.y;
+    k = at.b.z * BZ + threadIdx.z;
     return i < cd.n[0] && j < cd.n[1] && k < cd.n[2];
 }
 
@@ -166,8 +166,17 @@ __global__ void k_init(CaseDev cd, StatePtrs st, double b0, double b1, double b2
 // rate = sum_active (|u_a| / h_a + 2 Gamma / h_a^2), Gamma = max(nu + nu_t, alpha + nu_t / Pr_t);
 // the block maxima go to dt_state[3] (as ordered bits of a non-negative double)
 template <class S, class C>
-__global__ void k_rate_max(CaseDev cd, StatePtrs st, unsigned long long* rate_bits) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct RateMaxK {
+    static constexpr int kThreads = 256;
+    CaseDev cd;
+    StatePtrs st;
+    unsigned long long* rate_bits;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void RateMaxK<S, C>::run(const BlockAt& at) const {
+    const int64_t c = (int64_t)at.b.x * blockDim.x + threadIdx.x;
     double lam = 0.0;
     if (c < cd.N && cd.tag[c] == 0) {
         const C u[3] = {to_c<C>(ldg((const S*)st.f[0] + c)), to_c<C>(ldg((const S*)st.f[1] + c)),
@@ -195,28 +204,44 @@ __global__ void k_rate_max(CaseDev cd, StatePtrs st, unsigned long long* rate_bi
 }
 
 // dt_state: [0] dt, [1] dt/2, [2] simulated time, [3] rate bits (reset here)
-__global__ void k_dt_finalize(double dt0, double cfl, int adapt, double* dt_state) {
-    unsigned long long* bits = (unsigned long long*)(dt_state + 3);
-    const double lam = __longlong_as_double((long long)*bits);
-    double dt = dt0;
-    if (adapt && lam > 0.0) {
-        const double cap = cfl / lam;
-        dt = cap < dt0 ? cap : dt0;
+struct DtFinalizeK {
+    static constexpr int kThreads = 1;
+    double dt0, cfl;
+    int adapt;
+    double* dt_state;
+    __device__ void run(const BlockAt&) const {
+        unsigned long long* bits = (unsigned long long*)(dt_state + 3);
+        const double lam = __longlong_as_double((long long)*bits);
+        double dt = dt0;
+        if (adapt && lam > 0.0) {
+            const double cap = cfl / lam;
+            dt = cap < dt0 ? cap : dt0;
+        }
+        dt_state[0] = dt;
+        dt_state[1] = 0.5 * dt;
+        dt_state[2] += dt;
+        ((float*)(dt_state + 4))[0] = (float)dt;
+        ((float*)(dt_state + 4))[1] = (float)(0.5 * dt);
+        *bits = 0ull;
     }
-    dt_state[0] = dt;
-    dt_state[1] = 0.5 * dt;
-    dt_state[2] += dt;
-    ((float*)(dt_state + 4))[0] = (float)dt;
-    ((float*)(dt_state + 4))[1] = (float)(0.5 * dt);
-    *bits = 0ull;
-}
+};
 
 // ------------------------------------------------------------------ destruction
 template <class S, class C>
-__global__ void k_destruction(CaseDev cd, StatePtrs in, S* __restrict__ k_out, S* __restrict__ om_out,
-                              const double* dt_state) {
+struct DestructionK {
+    static constexpr int kThreads = BX * BY * BZ;
+    CaseDev cd;
+    StatePtrs in;
+    S* k_out;
+    S* om_out;
+    const double* dt_state;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, i, j, k)) return;
+    if (!cell3(cd, at, i, j, k)) return;
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     if (cd.tag[c]) {
@@ -315,9 +340,18 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, const St<C>& nb, C nu) {
 }
 
 template <class S, class C>
-__global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double* dt_state) {
+struct ExplicitK {
+    static constexpr int kThreads = BX * BY * BZ;
+    CaseDev cd;
+    StatePtrs in, out;
+    const double* dt_state;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, i, j, k)) return;
+    if (!cell3(cd, at, i, j, k)) return;
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     S* o[6];
@@ -388,9 +422,19 @@ __global__ void k_explicit(CaseDev cd, StatePtrs in, StatePtrs out, const double
 
 // ------------------------------------------------------------------ pressure RHS
 template <class S, class C>
-__global__ void k_rhs(CaseDev cd, StatePtrs in, S* __restrict__ b, const double* dt_state) {
+struct RhsK {
+    static constexpr int kThreads = BX * BY * BZ;
+    CaseDev cd;
+    StatePtrs in;
+    S* b;
+    const double* dt_state;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void RhsK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, i, j, k)) return;
+    if (!cell3(cd, at, i, j, k)) return;
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     if (cd.tag[c]) {
         b[c] = from_c<S, C>((C)0);
@@ -422,10 +466,20 @@ __device__ __forceinline__ double p_across(const LevelDev& L, const double* p, u
 }
 
 template <class S, class C>
-__global__ void k_project(CaseDev cd, LevelDev L0, StatePtrs in, StatePtrs out, const double* __restrict__ p,
-                          const double* dt_state) {
+struct ProjectK {
+    static constexpr int kThreads = BX * BY * BZ;
+    CaseDev cd;
+    LevelDev L0;
+    StatePtrs in, out;
+    const double* p;
+    const double* dt_state;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void ProjectK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, i, j, k)) return;
+    if (!cell3(cd, at, i, j, k)) return;
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     S* o[3] = {(S*)out.f[0], (S*)out.f[1], (S*)out.f[2]};
     const S* q[3] = {(const S*)in.f[0], (const S*)in.f[1], (const S*)in.f[2]};
@@ -489,34 +543,40 @@ cudaError_t launch_init_state(int prec, const CaseDev& cd, StatePtrs st, const d
 }
 
 cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, k_rate_max<S, C><<<nblocks(cd.N), kThreads, 0, s>>>(cd, st, (unsigned long long*)(dt_state + 3)));
-    k_dt_finalize<<<1, 1, 0, s>>>(cd.dt0, cd.cfl, cd.dt_adapt, dt_state);
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(RateMaxK<S, C>{cd, st, (unsigned long long*)(dt_state + 3)}, dim3(nblocks(cd.N)),
+                                  dim3(kThreads), 0, s));
+    if (err != cudaSuccess) return err;
+    return launch_k(DtFinalizeK{cd.dt0, cd.cfl, cd.dt_adapt, dt_state}, dim3(1), dim3(1), 0, s);
 }
 
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
                                const double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, k_destruction<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, (S*)k_out, (S*)om_out,
-                                                                           dt_state));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(DestructionK<S, C>{cd, in, (S*)k_out, (S*)om_out, dt_state}, grid3(cd), kBlock3,
+                                  0, s));
+    return err;
 }
 
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out, const double* dt_state,
                             cudaStream_t s) {
-    DISPATCH(prec, k_explicit<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, out, dt_state));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(ExplicitK<S, C>{cd, in, out, dt_state}, grid3(cd), kBlock3, 0, s));
+    return err;
 }
 
 cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const double* dt_state,
                        cudaStream_t s) {
-    DISPATCH(prec, k_rhs<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, in, (S*)b, dt_state));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(RhsK<S, C>{cd, in, (S*)b, dt_state}, grid3(cd), kBlock3, 0, s));
+    return err;
 }
 
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
                            const double* p, const double* dt_state, cudaStream_t s) {
-    DISPATCH(prec, k_project<S, C><<<grid3(cd), kBlock3, 0, s>>>(cd, L0, in, out, p, dt_state));
-    return cudaGetLastError();
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(ProjectK<S, C>{cd, L0, in, out, p, dt_state}, grid3(cd), kBlock3, 0, s));
+    return err;
 }
 
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s) {

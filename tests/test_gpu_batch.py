@@ -1,0 +1,123 @@
+"""Batched stepping (fvm_batch): uneven cases stepped by one graph per step,
+each launch site issued once for all cases.  A batched case must give what
+the same case gives stepped alone."""
+import numpy as np
+import pytest
+
+from paper_2603_21869_gb300 import binding, build, cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.ensure_built()
+    binding.lib()
+
+
+def uneven_channels(precision, n=4, seed=7):
+    """Channels of different sizes, inlet speeds and depths (a box in one)."""
+    rng = np.random.default_rng(seed)
+    sizes = [(32, 16, 16, 3), (64, 16, 16, 4), (48, 32, 16, 3), (64, 32, 32, 4), (96, 32, 32, 4)]
+    out = []
+    for c in range(n):
+        nx, ny, nz, lv = sizes[c % len(sizes)]
+        U = float(rng.uniform(0.5, 3.0))
+        s = cases.heated_channel_3d(nx, ny, nz, mg_levels=lv, precision=precision, seed=100 + c,
+                                    init_perturb=0.02, mg_rel_tol=1e-8, max_vcycles=40)
+        faces = list(s.faces)
+        faces[0] = cases.Patch(cases.INLET, u_normal=U, intensity=float(rng.uniform(0.01, 0.1)),
+                               length_scale=0.07 * s.Ly, T_in=s.faces[0].T_in)
+        s = s.replace(faces=faces, init_vel=(U, 0.0, 0.0))
+        if c == 1:
+            s = s.replace(boxes=[cases.Box(20, 28, 4, 10, 0, 8, thermal=cases.HEAT_FLUX, T_value=120.0)])
+        out.append(s)
+    return out
+
+
+def rel(a, b):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+@pytest.mark.parametrize("prec,tol", [(cases.FP64, 1e-12), (cases.FP32, 1e-5)], ids=["fp64", "fp32"])
+def test_batch_equals_each_case_alone(prec, tol):
+    specs = uneven_channels(prec)
+    nsteps = 4
+    alone, alone_stats = [], []
+    for s in specs:
+        with binding.Case(s) as c:
+            alone_stats.append(c.step(nsteps))
+            alone.append(c.read())
+    cs = [binding.Case(s) for s in specs]
+    try:
+        with binding.Batch(cs) as b:
+            st = b.step(2)
+            st2 = b.step(nsteps - 2)
+            info = b.info()
+        got = [c.read() for c in cs]
+    finally:
+        for c in cs:
+            c.close()
+    assert info["n_cases"] == len(specs) and info["graphs"] == 2 and info["steps"] == nsteps
+    assert info["kernel_launches"] > 0
+    for i, (g, a) in enumerate(zip(got, alone)):
+        assert st2[i]["vcycles_last"] == alone_stats[i]["vcycles_last"], i
+        assert st2[i]["rel_residual"] <= 1e-8
+        for f in cases.FIELDS:
+            assert rel(g[f], a[f]) <= tol, (i, f, rel(g[f], a[f]))
+    assert all(s["steps"] == 2 for s in st)
+
+
+def test_one_shot_batch_and_depth_mix():
+    """fvm_step_batch on cases whose multigrid hierarchies differ in depth
+    (their coarse kernels merge into one launch)."""
+    specs = [cases.heated_channel_3d(32, 16, 16, mg_levels=2, precision=cases.FP64, fixed_vcycles=3),
+             cases.heated_channel_3d(64, 32, 32, mg_levels=4, precision=cases.FP64, fixed_vcycles=3),
+             cases.room_3d(64, 32, 32, seed=3, mg_levels=4, h=0.08, precision=cases.FP64, fixed_vcycles=3)]
+    alone = []
+    for s in specs:
+        with binding.Case(s) as c:
+            c.step(2)
+            alone.append(c.read())
+    cs = [binding.Case(s) for s in specs]
+    try:
+        st = binding.step_batch(cs, 2)
+        got = [c.read() for c in cs]
+    finally:
+        for c in cs:
+            c.close()
+    assert [s["vcycles_last"] for s in st] == [3, 3, 3]
+    for g, a in zip(got, alone):
+        for f in cases.FIELDS:
+            assert rel(g[f], a[f]) <= 1e-12, f
+
+
+def test_batch_reports_a_diverged_case_and_keeps_the_others():
+    specs = uneven_channels(cases.FP64, n=3)
+    cs = [binding.Case(s) for s in specs]
+    try:
+        u = cs[1].read(("u",))["u"].copy()
+        u[3, 3, 3] = np.nan
+        cs[1].write({"u": u})
+        with binding.Batch(cs) as b:
+            with pytest.raises(binding.FvmError) as e:
+                b.step(1)
+            assert e.value.status == binding.ERR_DIVERGED
+        for i in (0, 2):
+            assert np.isfinite(cs[i].read(("u",))["u"]).all()
+    finally:
+        for c in cs:
+            c.close()
+
+
+def test_batch_rejects_mixed_precisions():
+    a = binding.Case(cases.heated_channel_3d(32, 16, 16, mg_levels=3, precision=cases.FP64))
+    b = binding.Case(cases.heated_channel_3d(32, 16, 16, mg_levels=3, precision=cases.FP32))
+    try:
+        with pytest.raises(binding.FvmError) as e:
+            binding.Batch([a, b])
+        assert e.value.status == binding.ERR_INVALID
+    finally:
+        a.close()
+        b.close()

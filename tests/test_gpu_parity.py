@@ -150,19 +150,22 @@ def test_adaptive_solve_tracks_oracle():
     assert_fields(got, o.fields(), 1e-7, cases.FIELDS, "adaptive")
 
 
+@pytest.mark.parametrize("prec", [cases.FP32, cases.BF16_MIXED], ids=["fp32", "bf16"])
 @pytest.mark.parametrize("make", [lambda p: channel_box(precision=p, fixed_vcycles=0, mg_rel_tol=1e-8, max_vcycles=40),
-                                  lambda p: room_small(precision=p, mg_rel_tol=1e-8, max_vcycles=40)])
-def test_fp32_path_within_1e4_of_fp64_oracle(make):
-    """FP32 storage and smoothing with the FP64 defect-correction solve:
-    u, v, w, T, k, omega within 1e-4 (relative to each field's magnitude)."""
-    spec = make(cases.FP32)
+                                  lambda p: room_small(precision=p, mg_rel_tol=1e-8, max_vcycles=40)],
+                         ids=["channel_box", "room"])
+def test_reduced_precision_within_1e4_of_fp64_oracle(make, prec):
+    """FP32 field storage; FP32 or BF16 (FP32 accumulation) multigrid
+    corrections inside the FP64 defect-correction solve: u, v, w, T, k, omega
+    within 1e-4 (relative to each field's magnitude)."""
+    spec = make(prec)
     nsteps = 10
     with binding.Case(spec) as c:
         st = c.step(nsteps)
         got = c.read()
     assert st["rel_residual"] <= 1e-8
     o = OracleCase(spec.replace(precision=cases.FP64)).step(nsteps)
-    assert_fields(got, o.fields(), 1e-4, STATE, "fp32")
+    assert_fields(got, o.fields(), 1e-4, STATE, f"precision {prec}")
 
 
 def test_checkpoint_resume_is_exact():

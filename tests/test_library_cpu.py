@@ -31,8 +31,19 @@ def test_struct_layout_matches_binding(lib):
     import ctypes as ct
     sizes = binding.struct_sizes()
     ours = [ct.sizeof(t) for t in (binding.Patch, binding.Vent, binding.Box, binding.CaseDesc,
-                                   binding.StepStats, binding.CaseInfo, binding.KernelStat)]
+                                   binding.StepStats, binding.CaseInfo, binding.KernelStat, binding.BatchInfo)]
     assert sizes == ours
+
+
+def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
+    import ctypes as ct
+    h = ct.c_void_p()
+    assert lib.fvm_batch_create(None, 0, None, ct.byref(h)) == binding.ERR_INVALID
+    arr = (ct.c_void_p * 2)(None, None)
+    assert lib.fvm_batch_create(arr, 2, None, ct.byref(h)) == binding.ERR_INVALID
+    assert "null case" in binding.last_error()
+    assert not h.value
+    assert lib.fvm_batch_step(None, 1, None) == binding.ERR_INVALID
 
 
 def test_case_bytes_scale_with_precision(lib):
