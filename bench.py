@@ -135,6 +135,182 @@ def run_reference(args, spec, label, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def breakdown(prof, nsteps):
+    """Per-site table, dominant kernel roofline and V-cycle bandwidth from profile tallies."""
+    peak, peak_src = peaks()
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    mg = [k for k in prof if any(k.startswith(p) for p in ("sweep", "resid", "prolong", "coarse"))]
+    mg_bytes = sum(prof[k]["bytes"] for k in mg)
+    mg_ms = sum(prof[k]["ms"] for k in mg)
+    return {
+        "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                     "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+                     "launches": d["launches"]},
+        "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
+                   "frac": (mg_bytes / (mg_ms / 1e3) / 1e9) / peak if mg_ms else None,
+                   "ms_per_step": mg_ms / nsteps},
+        "profiled_pass": {"steps": nsteps, "kernel_ms_per_step": sum(v["ms"] for v in prof.values()) / nsteps,
+                          "mode": "launch by launch, CUDA events around every kernel"},
+        "kernels": {k: {"ms_per_step": v["ms"] / nsteps, "launches_per_step": v["launches"] / nsteps,
+                        "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
+    }
+
+
+def field_errors(got, ref):
+    """Per-field max |a - b| / max |b| (the parity tests' measure)."""
+    import numpy as np
+    out = {}
+    for f in cases.FIELDS:
+        scale = float(np.max(np.abs(ref[f]))) or 1.0
+        out[f] = float(np.max(np.abs(got[f] - ref[f]))) / scale
+    return out
+
+
+def run_batched(args, rank, ws, local, dist):
+    """C4: uneven channel cases stepped as one batch (one CUDA graph per step,
+    one launch per kernel site for all cases), against the same cases stepped
+    one by one (FP32, and the plain FP64 form)."""
+    import numpy as np
+    import torch
+    from paper_2603_21869_gb300 import binding, build
+    build.ensure_built()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prec = PREC[args.precision]
+    specs = cases.batched_channels(args.cases, seed=rank, precision=prec, mg_levels=5)
+    N = sum(sp.cells for sp in specs)
+    cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
+    batch = binding.Batch(cs, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        batch.step(1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    l0 = batch.info()["kernel_launches"]
+    clocks = Clocks(local)
+    clocks.start()
+    times, vc, rels = [], [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = batch.step(1, allow_not_converged=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        vc.append(statistics.mean(x["vcycles_last"] for x in st))
+        rels.append(max(x["rel_residual"] for x in st))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = batch.info()["kernel_launches"] - l0
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * N * args.steps / (total_ms / 1e3)
+    prof_steps = min(args.steps, 5)
+    bd = breakdown(batch.profile(prof_steps), prof_steps)
+
+    # end to end through the C-ABI with host buffers: write every case, one batched step, read back
+    e2e = None
+    if args.e2e_steps > 0:
+        hosts = [torch.empty(7 * sp.cells, dtype=torch.float64, pin_memory=True).numpy() for sp in specs]
+        vals = [{k: v.copy() for k, v in c.read(out=h).items()} for c, h in zip(cs, hosts)]
+        te = 0.0
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            for c, v in zip(cs, vals):
+                c.write(v)
+            batch.step(1, allow_not_converged=True)
+            vals = [{k: x.copy() for k, x in c.read(out=h).items()} for c, h in zip(cs, hosts)]
+            te += time.perf_counter() - t0
+        e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
+               "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = ws * N * args.e2e_steps / float(t.item())
+    batch.close()
+
+    # the same cases stepped one at a time (each its own graph per step), FP32 and plain FP64
+    compare = None
+    if ws == 1 and not args.no_compare:
+        def one_by_one(case_list, rounds):
+            for c in case_list:
+                c.step(1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(rounds):
+                for c in case_list:
+                    c.step(1, allow_not_converged=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            return N * rounds / (ev0.elapsed_time(ev1) / 1e3)
+        per_case = one_by_one(cs, 2)
+        for c in cs:
+            c.close()
+        c64 = [binding.Case(sp.replace(precision=cases.FP64), stream=stream.cuda_stream) for sp in specs]
+        per_case_fp64 = one_by_one(c64, 1)
+        for c in c64:
+            c.close()
+        # accuracy at equal steps on a subset: the batched reduced-precision form vs the plain FP64 form
+        sub = specs[:args.accuracy_cases]
+        steps_acc = 5
+        b_cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in sub]
+        with binding.Batch(b_cs, stream=stream.cuda_stream) as bb:
+            sb = bb.step(steps_acc, allow_not_converged=True)
+        got = [c.read() for c in b_cs]
+        errs, rel64 = [], []
+        for sp, g in zip(sub, got):
+            with binding.Case(sp.replace(precision=cases.FP64), stream=stream.cuda_stream) as c:
+                s64 = c.step(steps_acc, allow_not_converged=True)
+                errs.append(field_errors(g, c.read()))
+                rel64.append(s64["rel_residual"])
+        for c in b_cs:
+            c.close()
+        compare = {"per_case_same_precision": {"value": per_case, "unit": "cell-steps/s"},
+                   "per_case_fp64": {"value": per_case_fp64, "unit": "cell-steps/s"},
+                   "speedup_vs_per_case_fp64": value / per_case_fp64,
+                   "accuracy": {"cases": len(sub), "steps": steps_acc,
+                                "max_rel_error_vs_fp64": {f: max(e[f] for e in errs) for f in cases.FIELDS},
+                                "rel_residual_batched_max": max(x["rel_residual"] for x in sb),
+                                "rel_residual_fp64_max": max(rel64)}}
+    else:
+        for c in cs:
+            c.close()
+    if rank == 0:
+        sizes = sorted({(sp.nx, sp.ny, sp.nz) for sp in specs})
+        line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "data": "synthetic",
+                "config": {"workload": f"batched_channels {len(specs)} cases, 64^3 .. 192x96x96, 5-level V(3,3), "
+                                       "rel tol 1e-8, one batch per GPU",
+                           "cells_per_gpu": N, "cases_per_gpu": len(specs), "sizes": [list(x) for x in sizes],
+                           "precision": args.precision, "parallelism": f"replicas x{ws}",
+                           "l2": "256 MB buffer written between timed steps (the batch's state is larger than L2)"},
+                "vcycles_per_step": statistics.mean(vc), "rel_residual_max": max(rels),
+                **bd, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "compare": compare}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(min(specs, key=lambda sp: sp.cells))
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(spec, budget_s=25.0):
     """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload."""
     from oracle.step import OracleCase
@@ -161,9 +337,24 @@ def main():
     ap.add_argument("--workload", default="channel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cases", type=int, default=64, help="batched workload: cases per GPU")
+    ap.add_argument("--accuracy-cases", type=int, default=8)
+    ap.add_argument("--no-compare", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
+    if args.workload == "batched":
+        rank, ws, local, dist = dist_setup()
+        if args.impl == "reference":
+            args.steps, args.warmup = min(args.steps, 2), 0
+            spec = min(cases.batched_channels(args.cases, seed=rank, mg_levels=5), key=lambda sp: sp.cells)
+            run_reference(args, spec, "batched_channels: the smallest case (oracle, one case at a time)", rank, ws)
+        else:
+            run_batched(args, rank, ws, local, dist)
+            return
+        if dist:
+            dist.destroy_process_group()
+        return
     spec, label = workload(args.workload, PREC[args.precision])
     rank, ws, local, dist = dist_setup()
     if args.impl == "reference":

@@ -241,6 +241,16 @@ fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm
 fvm_status fvm_batch_step(fvm_batch* b, int32_t nsteps, fvm_step_stats* stats);
 
 fvm_status fvm_batch_get_info(const fvm_batch* b, fvm_batch_info* out);
+
+/* Profiling pass of a batch: nsteps steps run launch by launch (the merged
+   launches of the batch's graph, the V-cycle loop driven from the host with
+   one read of the cases' solve states per outer iteration), each launch
+   bracketed by a pair of CUDA events on the batch's stream.  out receives
+   up to cap per-site tallies (name = launch site such as "sweep_L0";
+   launches; summed event time; algorithmic bytes summed over the cases);
+   *n_out (may be NULL) = number of sites.  The steps advance the cases like
+   fvm_batch_step. */
+fvm_status fvm_batch_profile(fvm_batch* b, int32_t nsteps, fvm_kernel_stat* out, int32_t cap, int32_t* n_out);
 void fvm_batch_destroy(fvm_batch* b);
 
 /* One-shot form: a temporary batch of the n cases, advanced by nsteps, then

@@ -91,7 +91,7 @@ EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", 
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
            "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
            "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
-           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy"]
+           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy", "fvm_batch_profile"]
 
 _lib = None
 
@@ -129,6 +129,7 @@ def lib():
     L.fvm_batch_create.argtypes = [ct.POINTER(CP), ct.c_int32, CP, ct.POINTER(CP)]
     L.fvm_batch_step.argtypes = [CP, ct.c_int32, ct.POINTER(StepStats)]
     L.fvm_batch_get_info.argtypes = [CP, ct.POINTER(BatchInfo)]
+    L.fvm_batch_profile.argtypes = [CP, ct.c_int32, ct.POINTER(KernelStat), ct.c_int32, ct.POINTER(ct.c_int32)]
     L.fvm_batch_destroy.argtypes = [CP]
     L.fvm_batch_destroy.restype = None
     L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
@@ -137,7 +138,7 @@ def lib():
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info"]:
+                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_profile"]:
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -337,6 +338,15 @@ class Batch:
         status = lib().fvm_batch_step(self._h, n, stats)
         _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return [_stats(s, status) for s in stats]
+
+    def profile(self, n=1):
+        """n steps launch by launch with CUDA events around every batched launch."""
+        cap = 512
+        arr = (KernelStat * cap)()
+        m = ct.c_int32()
+        _check(lib().fvm_batch_profile(self._h, n, arr, cap, ct.byref(m)))
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+                for i in range(min(m.value, cap))}
 
     def info(self):
         inf = BatchInfo()

@@ -329,6 +329,7 @@ using ManyFn = cudaError_t (*)(const void* tab, const BatchMap& m, unsigned nblk
 
 struct RecLaunch {
     std::string site;                  // launch site (the profiling class name)
+    double bytes;                      // algorithmic bytes of this launch
     ManyFn many;                       // issues a table of this functor type
     std::vector<unsigned char> arg;    // the functor
     dim3 grid, block;
@@ -338,18 +339,26 @@ struct RecLaunch {
 struct Recorder {
     std::vector<RecLaunch> out;
     std::string site;                  // set by the caller before each launch site
+    double bytes = 0.0;                // algorithmic bytes of the site (given to its first launch)
 };
 
 extern thread_local Recorder* g_rec;
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit belongs to the function, which every case shares, so it only grows
+// (a later, smaller case must not lower it below what an earlier one needs).
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+// Has the limit been raised to cover `bytes`?  Launches check this first: a
+// launch the runtime would reject is not issued (inside a stream capture such
+// a launch brought the process down).
+bool smem_limit_covers(const void* fn, size_t bytes);
+
+// nblk == 0: set the kernel's shared-memory limit only (done before any capture)
 template <class K>
 cudaError_t many_launch(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
                         const BatchCtl*, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_many<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    if (nblk == 0) return cudaSuccess;   // attributes only
+    if (nblk == 0) return smem ? raise_smem_limit((const void*)k_many<K>, smem) : cudaSuccess;
+    if (!smem_limit_covers((const void*)k_many<K>, smem)) return cudaErrorInvalidConfiguration;
     k_many<K><<<nblk, block, smem, s>>>((const K*)tab, m);
     return cudaGetLastError();
 }
@@ -367,6 +376,8 @@ bool record_launch(const K& k, dim3 grid, dim3 block, size_t smem, ManyFn many) 
     if (!g_rec) return false;
     RecLaunch r;
     r.site = g_rec->site;
+    r.bytes = g_rec->bytes;
+    g_rec->bytes = 0.0;
     r.many = many;
     r.arg.assign((const unsigned char*)&k, (const unsigned char*)&k + sizeof(K));
     r.grid = grid;
@@ -379,6 +390,7 @@ bool record_launch(const K& k, dim3 grid, dim3 block, size_t smem, ManyFn many) 
 template <class K>
 cudaError_t launch_k(const K& k, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
     if (record_launch(k, grid, block, smem, &many_launch<K>)) return cudaSuccess;
+    if (!smem_limit_covers((const void*)k_one<K>, smem)) return cudaErrorInvalidConfiguration;
     k_one<K><<<grid, block, smem, s>>>(k);
     return cudaGetLastError();
 }

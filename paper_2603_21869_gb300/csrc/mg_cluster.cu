@@ -299,7 +299,7 @@ cudaError_t prepare_coarse_cluster(int inner, int cs, size_t smem, int* max_clus
     DISPATCH_I(inner, {
         auto k = k_coarse_cluster<TI>;
         err = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) err = raise_smem_limit((const void*)k, smem);
         if (err == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(cs);

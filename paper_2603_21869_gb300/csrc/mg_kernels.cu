@@ -738,8 +738,7 @@ cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc
 
 cudaError_t prepare_coarse_cta(int inner, size_t smem) {
     DISPATCH_I(inner, {
-        cudaError_t err = cudaFuncSetAttribute(k_one<CoarseK<TI>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
+        cudaError_t err = raise_smem_limit((const void*)k_one<CoarseK<TI>>, smem);
         if (err != cudaSuccess) return err;
     });
     return cudaSuccess;

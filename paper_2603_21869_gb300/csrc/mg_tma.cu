@@ -553,7 +553,7 @@ cudaError_t tma_prepare() {
     if (done) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     auto set = [&](const void* k, size_t b) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        if (e == cudaSuccess) e = raise_smem_limit(k, b);
     };
     set((const void*)k_down_tma<0>, down_smem<0>());
     set((const void*)k_down_tma<1>, down_smem<1>());

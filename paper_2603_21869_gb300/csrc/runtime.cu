@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -213,6 +215,30 @@ bool coarse_inverse(const HostLevel& L, std::vector<double>& inv) {
 void set_last_error(const std::string& msg) { g_err = msg; }
 
 thread_local Recorder* g_rec = nullptr;
+
+namespace {
+std::mutex g_smem_mu;
+std::map<const void*, size_t> g_smem_limit;   // dynamic shared-memory limit set per kernel
+}  // namespace
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+    // (set even below 48 KB: static shared memory counts against the default limit too)
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    auto& limit = g_smem_limit;
+    size_t& have = limit[fn];
+    if (bytes <= have) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    else cudaGetLastError();
+    return e;
+}
+
+bool smem_limit_covers(const void* fn, size_t bytes) {
+    if (bytes == 0) return true;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    auto it = g_smem_limit.find(fn);
+    return it != g_smem_limit.end() && it->second >= bytes;
+}
 
 struct DevLevel {
     LevelDev dev;
@@ -544,10 +570,13 @@ void prof_clear(fvm_case* c) {
 
 // Launch `expr` (which issues nk kernels), counting it and bracketing it with
 // profiling events when the hook is on.  `bytes` = algorithmic bytes.
-#define KLAUNCH(name, bytes, nk, expr)                  \
+#define KLAUNCH(name, bytes_, nk, expr)                  \
     do {                                                \
-        if (g_rec) g_rec->site = (name);                \
-        const int pi_ = prof_begin(c, (name), (bytes)); \
+        if (g_rec) {                                    \
+            g_rec->site = (name);                       \
+            g_rec->bytes = (bytes_);                     \
+        }                                               \
+        const int pi_ = prof_begin(c, (name), (bytes_)); \
         CUDA_TRY(expr);                                 \
         prof_end(c, pi_);                               \
         c->launches += (nk);                            \
@@ -1172,7 +1201,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
 // issue alone, merged site by site.
 
 struct BatchGather {
-    int32_t cycles, total_cycles, nonfinite, notconv, inner, pad;
+    int32_t cycles, total_cycles, nonfinite, notconv, inner, active;
     double rel, dt, sim_time;
 };
 
@@ -1189,7 +1218,7 @@ __global__ void k_batch_gather(SolveState* const* sts, double* const* dts, Batch
         g.nonfinite = s->nonfinite;
         g.notconv = s->notconv;
         g.inner = s->inner;
-        g.pad = 0;
+        g.active = s->active;
         g.rel = s->rel;
         g.dt = dts[i][0];
         g.sim_time = dts[i][2];
@@ -1216,7 +1245,8 @@ struct Merged {
     dim3 block;
     size_t smem = 0;
     std::vector<int> cases;
-    std::vector<const RecLaunch*> recs;
+    std::vector<const RecLaunch*> recs;   // valid while the tables are built
+    double bytes = 0.0;                   // algorithmic bytes of the launch (all its cases)
     // device table (filled when the arena is built)
     const void* tab = nullptr;
     BatchMap map{};
@@ -1283,6 +1313,7 @@ std::vector<Merged> merge_sequences(const std::vector<std::vector<RecLaunch>>& s
             const RecLaunch& r = seqs[j][cur[j]];
             m.cases.push_back(j);
             m.recs.push_back(&r);
+            m.bytes += r.bytes;
             m.smem = std::max(m.smem, r.smem);
             ++cur[j];
         }
@@ -1305,6 +1336,7 @@ struct fvm_batch {
         void* arena = nullptr;              // functor tables, block maps, state lists
         int64_t per_step = 0;               // launches outside the V-cycle loop
         int64_t per_outer = 0;              // launches per outer iteration (V-cycle body)
+        std::vector<Merged> seg[4];         // step, residual, V-cycle, projection (tables in the arena)
     };
     std::vector<Graph> graphs;
     SolveState** d_sts = nullptr;
@@ -1313,6 +1345,7 @@ struct fvm_batch {
     BatchGather* h_gather = nullptr;
     unsigned long long* d_outer = nullptr;
     unsigned long long* h_outer = nullptr;
+    unsigned long long* d_scratch = nullptr;   // outer-iteration sum of profiled steps (unused)
     int64_t launches = 0;
     int64_t steps = 0;
 };
@@ -1331,6 +1364,7 @@ void free_batch(fvm_batch* b) {
     if (b->d_dts) cudaFree(b->d_dts);
     if (b->d_gather) cudaFree(b->d_gather);
     if (b->d_outer) cudaFree(b->d_outer);
+    if (b->d_scratch) cudaFree(b->d_scratch);
     if (b->h_gather) cudaFreeHost(b->h_gather);
     if (b->h_outer) cudaFreeHost(b->h_outer);
     if (b->side) cudaStreamDestroy(b->side);
@@ -1460,11 +1494,13 @@ fvm_status batch_capture(fvm_batch* B, fvm_batch::Graph& G) {
     }
     g_rec = nullptr;
     if (st != FVM_OK) return st;
-    std::vector<Merged> seg[4];
+    std::vector<Merged>* seg = G.seg;
     for (int s = 0; s < 4; ++s) seg[s] = merge_sequences(rec[s]);
     if (seg[1].size() != 1)
         return fail(FVM_ERR_INVALID, "batched cases need the same precisions (one level-0 residual launch)");
     ST_TRY(build_arena(seg, 4, B->cases, &G.arena));
+    for (int s = 0; s < 4; ++s)
+        for (Merged& m : seg[s]) m.recs.clear();   // the recorded functors now live in the arena
     // dynamic shared-memory limits of the batched kernels (outside the capture)
     for (int s = 0; s < 4; ++s)
         for (Merged& m : seg[s]) CUDA_TRY(m.many(m.tab, m.map, 0, m.block, m.smem, &m.ctl, B->stream));
@@ -1546,6 +1582,25 @@ fvm_status batch_capture(fvm_batch* B, fvm_batch::Graph& G) {
         cudaGetLastError();
         return fail(FVM_ERR_CUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(e));
     }
+    return FVM_OK;
+}
+
+int find_batch_graph(fvm_batch* B);
+
+// the graph (and launch tables) for the cases' current pointers, captured if new
+fvm_status batch_graph(fvm_batch* B, int& g) {
+    g = find_batch_graph(B);
+    if (g >= 0) return FVM_OK;
+    fvm_batch::Graph G;
+    fvm_status st = batch_capture(B, G);
+    if (st != FVM_OK) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+        if (G.arena) cudaFree(G.arena);
+        return st;
+    }
+    B->graphs.push_back(std::move(G));
+    g = (int)B->graphs.size() - 1;
     return FVM_OK;
 }
 
@@ -1794,6 +1849,7 @@ fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm
         cudaMalloc((void**)&B->d_dts, n * sizeof(double*)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_gather, n * sizeof(BatchGather)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_outer, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_scratch, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_gather, n * sizeof(BatchGather)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_outer, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
@@ -1825,19 +1881,8 @@ fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
     CUDA_TRY(cudaMemsetAsync(B->d_outer, 0, sizeof(unsigned long long), s));
     int64_t fixed = 0, per_outer = 0;
     for (int k = 0; k < nsteps; ++k) {
-        int g = find_batch_graph(B);
-        if (g < 0) {
-            fvm_batch::Graph G;
-            fvm_status st = batch_capture(B, G);
-            if (st != FVM_OK) {
-                if (G.exec) cudaGraphExecDestroy(G.exec);
-                if (G.g) cudaGraphDestroy(G.g);
-                if (G.arena) cudaFree(G.arena);
-                return st;
-            }
-            B->graphs.push_back(G);
-            g = (int)B->graphs.size() - 1;
-        }
+        int g = -1;
+        ST_TRY(batch_graph(B, g));
         const fvm_batch::Graph& G = B->graphs[g];
         CUDA_TRY(cudaGraphLaunch(G.exec, s));
         for (int i = 0; i < n; ++i) {
@@ -1893,6 +1938,106 @@ fvm_status fvm_batch_get_info(const fvm_batch* B, fvm_batch_info* out) {
         info.launches_per_outer = B->graphs[0].per_outer;
     }
     *out = info;
+    return FVM_OK;
+}
+
+fvm_status fvm_batch_profile(fvm_batch* B, int32_t nsteps, fvm_kernel_stat* out, int32_t cap, int32_t* n_out) {
+    if (!B || (!out && cap > 0)) return fail(FVM_ERR_INVALID, "null batch or output");
+    if (nsteps < 0) return fail(FVM_ERR_INVALID, "nsteps < 0");
+    ST_TRY(batch_check(B->cases.data(), (int)B->cases.size()));
+    const int n = (int)B->cases.size();
+    cudaStream_t s = B->stream;
+    for (fvm_case* c : B->cases) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    struct Ev {
+        int site;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> evs;
+    std::vector<std::string> names;
+    std::vector<double> bytes;
+    std::vector<int64_t> count;
+    auto release = [&]() {
+        for (Ev& e : evs) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        evs.clear();
+    };
+    auto run = [&](const Merged& m) -> fvm_status {
+        int site = -1;
+        for (size_t q = 0; q < names.size(); ++q)
+            if (names[q] == m.site) site = (int)q;
+        if (site < 0) {
+            site = (int)names.size();
+            names.push_back(m.site);
+            bytes.push_back(0.0);
+            count.push_back(0);
+        }
+        Ev e{site, nullptr, nullptr};
+        if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess)
+            return fail(FVM_ERR_CUDA, "cudaEventCreate");
+        evs.push_back(e);
+        BatchCtl ctl = m.ctl;
+        ctl.use_cond = 0;   // the host drives the loop
+        CUDA_TRY(cudaEventRecord(e.a, s));
+        cudaError_t err = m.many(m.tab, m.map, m.nblk, m.block, m.smem, &ctl, s);
+        if (err != cudaSuccess) return fail(FVM_ERR_CUDA, "batched launch " + m.site + ": " + cudaGetErrorString(err));
+        CUDA_TRY(cudaEventRecord(e.b, s));
+        bytes[site] += m.bytes;
+        count[site] += 1;
+        B->launches += 1;
+        return FVM_OK;
+    };
+    fvm_status st = FVM_OK;
+    for (int k = 0; k < nsteps && st == FVM_OK; ++k) {
+        int g = -1;
+        if ((st = batch_graph(B, g)) != FVM_OK) break;
+        fvm_batch::Graph& G = B->graphs[g];
+        for (const Merged& m : G.seg[0])
+            if (st == FVM_OK) st = run(m);
+        for (int it = 0; st == FVM_OK; ++it) {
+            st = run(G.seg[1][0]);
+            if (st != FVM_OK) break;
+            k_batch_gather<<<1, 256, 0, s>>>(B->d_sts, B->d_dts, B->d_gather, n, B->d_scratch);
+            if (cudaMemcpyAsync(B->h_gather, B->d_gather, n * sizeof(BatchGather), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                st = fail(FVM_ERR_CUDA, "reading the batch's solve states");
+                break;
+            }
+            bool any = false;
+            for (int i = 0; i < n; ++i) any = any || B->h_gather[i].active;
+            if (!any) break;
+            for (const Merged& m : G.seg[2])
+                if (st == FVM_OK) st = run(m);
+        }
+        for (const Merged& m : G.seg[3])
+            if (st == FVM_OK) st = run(m);
+        if (st != FVM_OK) break;
+        for (int i = 0; i < n; ++i) {
+            load_ptrs(B->cases[i], &G.after[12 * (size_t)i]);
+            ++B->cases[i]->steps;
+        }
+        ++B->steps;
+    }
+    if (st == FVM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(FVM_ERR_CUDA, "profiled batch steps");
+    std::vector<double> ms(names.size(), 0.0);
+    if (st == FVM_OK)
+        for (Ev& e : evs) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms[e.site] += t;
+        }
+    release();
+    if (st != FVM_OK) return st;
+    const int m = (int)names.size();
+    for (int i = 0; i < m && i < cap; ++i) {
+        memset(&out[i], 0, sizeof(out[i]));
+        strncpy(out[i].name, names[i].c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = count[i];
+        out[i].ms = ms[i];
+        out[i].bytes = bytes[i];
+    }
+    if (n_out) *n_out = m;
     return FVM_OK;
 }
 

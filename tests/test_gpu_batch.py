@@ -121,3 +121,45 @@ def test_batch_rejects_mixed_precisions():
     finally:
         a.close()
         b.close()
+
+
+def test_batch_profile_pass_equals_graph_steps_and_tallies_sites():
+    """The profiling pass runs the batch's merged launches one by one (host
+    loop); it advances the cases exactly like the graph, and tallies each
+    launch site with its algorithmic bytes."""
+    specs = uneven_channels(cases.FP32, n=3)
+    a = [binding.Case(s) for s in specs]
+    b = [binding.Case(s) for s in specs]
+    try:
+        with binding.Batch(a) as ba:
+            ba.step(2)
+        with binding.Batch(b) as bb:
+            prof = bb.profile(2)
+            info = bb.info()
+        for x, y in zip(a, b):
+            fa, fb = x.read(), y.read()
+            for f in cases.FIELDS:
+                assert np.array_equal(fa[f], fb[f]), f
+    finally:
+        for c in a + b:
+            c.close()
+    assert {"explicit", "resid0", "sweep_L0", "coarse_cta", "project"} <= set(prof)
+    assert prof["explicit"]["launches"] == 2 and prof["explicit"]["bytes"] > 0
+    assert all(v["ms"] > 0 for v in prof.values())
+    assert info["kernel_launches"] == sum(v["launches"] for v in prof.values())
+
+
+def test_coarse_kernel_smem_limit_is_not_lowered_by_a_later_smaller_case():
+    """The coarse single-CTA kernel's shared-memory limit is a property of
+    the function: a small case created after a large one must not lower it
+    below what the large one needs (here about 196 KB)."""
+    big_spec = cases.heated_channel_3d(96, 32, 32, mg_levels=4, precision=cases.FP32, fixed_vcycles=2)
+    small_spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3, precision=cases.FP32, fixed_vcycles=2)
+    with binding.Case(big_spec) as big, binding.Case(small_spec) as small:
+        small.step(1)
+        st = big.step(2)
+        assert st["vcycles_last"] == 2
+        with binding.Batch([big, small]) as b:
+            b.step(1)
+        big.step(1)
+        assert np.isfinite(big.read(("p",))["p"]).all()
