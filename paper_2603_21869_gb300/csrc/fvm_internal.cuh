@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fvm.h"
@@ -83,10 +84,14 @@ struct LevelDev {
     double wJ;               // Jacobi weight
     double diag;             // sum_active 2 / h_a^2 (A's diagonal away from boundaries)
     float inv_h2f[3], inv_Df, wJf, diagf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
+    double ih2a[3];          // inv_h2 on active axes, 0 on a collapsed axis
+    float ih2af[3];
     const uint8_t* solid;    // nonzero = solid
     const uint8_t* dir[6];   // per boundary-face cell: 1 = Dirichlet (p = 0 on the face)
     const uint16_t* nbf;     // per cell: 2 bits per face (x-,x+,y-,y+,z-,z+): 0 fluid neighbour,
-                             // 1 zero-gradient ghost, 2 zero-value ghost; bit 12: the cell is solid
+                             // 1 zero-gradient ghost, 2 zero-value ghost; bit 12: the cell is solid;
+                             // bit 13: a face whose ghost is not the clamped in-grid load (a zero-value
+                             // face, or a zero-gradient face towards a solid neighbour)
 };
 
 // Device-side state of one pressure solve: the last residual norms and the
@@ -166,12 +171,14 @@ template <> struct LP<double> {
     static __device__ __forceinline__ double iD(const LevelDev& L) { return L.inv_D; }
     static __device__ __forceinline__ double wJ(const LevelDev& L) { return L.wJ; }
     static __device__ __forceinline__ double diag(const LevelDev& L) { return L.diag; }
+    static __device__ __forceinline__ double ih2a(const LevelDev& L, int a) { return L.ih2a[a]; }
 };
 template <> struct LP<float> {
     static __device__ __forceinline__ float ih2(const LevelDev& L, int a) { return L.inv_h2f[a]; }
     static __device__ __forceinline__ float iD(const LevelDev& L) { return L.inv_Df; }
     static __device__ __forceinline__ float wJ(const LevelDev& L) { return L.wJf; }
     static __device__ __forceinline__ float diag(const LevelDev& L) { return L.diagf; }
+    static __device__ __forceinline__ float ih2a(const LevelDev& L, int a) { return L.ih2af[a]; }
 };
 
 // ---------------------------------------------------------------- launchers
@@ -242,8 +249,10 @@ cudaError_t launch_up_tma(int nsweeps, bool top, const TmaMaps& mp, int ein, int
 // kThreads` and `__device__ void run(const BlockAt&) const` (the level-0
 // residual returns an int, see below).  k_one runs it over one case's grid.
 // k_many runs a table of functors, one per case, whose grids are laid end to
-// end along x: case c owns blocks [start[c], start[c + 1]) and sees its own
-// block position and grid shape, so the same body serves both.
+// end: case c owns blocks [start[c], start[c + 1]) of the batch and sees its
+// own block position and grid shape, so the same body serves both.  A
+// functor's live() says whether its case still takes part (a converged case
+// skips the rest of the V-cycle loop); k_one runs only live cases.
 struct BlockAt {
     uint3 b;   // block position in the case's grid
     uint3 g;   // the case's grid
@@ -253,6 +262,7 @@ struct BatchMap {
     const int* start;    // n + 1 block offsets (device)
     const uint3* grid;   // each case's grid (device)
     int n;
+    int total;           // start[n]: the cases' blocks together
 };
 
 __device__ __forceinline__ int batch_case(const BatchMap& m, int blk) {
@@ -265,21 +275,77 @@ __device__ __forceinline__ int batch_case(const BatchMap& m, int blk) {
     return lo;
 }
 
-__device__ __forceinline__ BlockAt batch_block(const BatchMap& m, int c, unsigned blk) {
-    const uint3 g = m.grid[c];
-    const unsigned l = blk - (unsigned)__ldg(m.start + c);
-    return BlockAt{make_uint3(l % g.x, (l / g.x) % g.y, l / (g.x * g.y)), g};
-}
+// blocks per SM a functor asks the register allocator to keep resident (K::kMinBlocks, default 1)
+template <class K, class = void>
+struct MinBlocks {
+    static constexpr int value = 1;
+};
+template <class K>
+struct MinBlocks<K, std::void_t<decltype(K::kMinBlocks)>> {
+    static constexpr int value = K::kMinBlocks;
+};
 
 template <class K>
-__global__ void __launch_bounds__(K::kThreads) k_one(const __grid_constant__ K k) {
+__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_one(const __grid_constant__ K k) {
     k.run(BlockAt{blockIdx, gridDim});
 }
 
+// Batched launches are persistent: block i takes the contiguous range
+// [i*per, (i+1)*per) of the cases' blocks, walks it with an incremental block
+// position, and copies a case's functor into shared memory when it enters
+// that case (skipping the case's blocks if it is no longer live).
 template <class K>
-__global__ void __launch_bounds__(K::kThreads) k_many(const K* __restrict__ ks, BatchMap m) {
-    const int c = batch_case(m, (int)blockIdx.x);
-    ks[c].run(batch_block(m, c, blockIdx.x));
+__device__ __forceinline__ void batch_enter(const K* __restrict__ ks, const BatchMap& m, int c, unsigned char* buf,
+                                            int* s_live) {
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    __syncthreads();   // the previous functor is no longer read
+    const uint32_t* src = (const uint32_t*)(ks + c);
+    for (int q = tid; q < (int)(sizeof(K) / 4); q += nt) ((uint32_t*)buf)[q] = __ldg(src + q);
+    __syncthreads();
+    if (tid == 0) *s_live = reinterpret_cast<const K*>(buf)->live() ? 1 : 0;
+    __syncthreads();
+}
+
+template <class K>
+__device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchMap& m) {
+    static_assert(sizeof(K) % 4 == 0, "functor size");
+    __shared__ __align__(16) unsigned char buf[sizeof(K)];
+    __shared__ int s_live;
+    const int per = (m.total + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = (int)blockIdx.x * per, hi = min(m.total, lo + per);
+    if (lo >= hi) return;
+    int c = batch_case(m, lo);
+    uint3 g = m.grid[c];
+    unsigned l = (unsigned)(lo - __ldg(m.start + c));
+    uint3 b = make_uint3(l % g.x, (l / g.x) % g.y, l / (g.x * g.y));
+    int cend = __ldg(m.start + c + 1);
+    batch_enter(ks, m, c, buf, &s_live);
+    for (int v = lo; v < hi; ++v) {
+        if (v == cend) {   // the next case begins at its own first block
+            ++c;
+            g = m.grid[c];
+            b = make_uint3(0, 0, 0);
+            cend = __ldg(m.start + c + 1);
+            batch_enter(ks, m, c, buf, &s_live);
+        }
+        if (s_live) {
+            reinterpret_cast<const K*>(buf)->run(BlockAt{b, g});
+            __syncthreads();   // shared memory of run() is reused by the next block
+        }
+        if (++b.x == g.x) {
+            b.x = 0;
+            if (++b.y == g.y) {
+                b.y = 0;
+                ++b.z;
+            }
+        }
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_many(const K* __restrict__ ks, BatchMap m) {
+    batch_run(ks, m);
 }
 
 // The level-0 residual decides whether another V-cycle runs.  Over a batch,
@@ -289,7 +355,6 @@ struct BatchCtl {
     unsigned* counter;        // blocks finished in this launch (reset by the last one)
     SolveState* const* st;    // every case's solve state (device array)
     int n;
-    unsigned total;           // blocks in the launch
     cudaGraphConditionalHandle cond, cond2;
     int use_cond;             // 0: none, 1: cond, 2: cond and cond2
 };
@@ -306,11 +371,10 @@ __global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ 
 
 template <class K>
 __global__ void __launch_bounds__(K::kThreads) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
-    const int c = batch_case(m, (int)blockIdx.x);
-    ks[c].run(batch_block(m, c, blockIdx.x));
+    batch_run(ks, m);
     if (threadIdx.x + threadIdx.y + threadIdx.z != 0) return;
-    __threadfence();   // this case's decision (if this block made it) before the count
-    if (atomicAdd(ctl.counter, 1u) != ctl.total - 1u) return;
+    __threadfence();   // the decisions this block made, before the count
+    if (atomicAdd(ctl.counter, 1u) != gridDim.x - 1u) return;
     __threadfence();
     int any = 0;
     for (int i = 0; i < ctl.n; ++i) any |= ((volatile SolveState*)ctl.st[i])->active;
@@ -353,21 +417,39 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 // a launch brought the process down).
 bool smem_limit_covers(const void* fn, size_t bytes);
 
-// nblk == 0: set the kernel's shared-memory limit only (done before any capture)
+// Blocks of a persistent batched launch: the SMs times the blocks of this
+// kernel that fit on one SM (queried once per kernel and shared-memory size,
+// outside any capture, when `query` is set).
+int persistent_blocks(const void* fn, int threads, size_t smem, bool query);
+
+// nblk == 0: set the kernel's shared-memory limit and size its persistent
+// grid only (done before any capture)
 template <class K>
 cudaError_t many_launch(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
                         const BatchCtl*, cudaStream_t s) {
-    if (nblk == 0) return smem ? raise_smem_limit((const void*)k_many<K>, smem) : cudaSuccess;
-    if (!smem_limit_covers((const void*)k_many<K>, smem)) return cudaErrorInvalidConfiguration;
-    k_many<K><<<nblk, block, smem, s>>>((const K*)tab, m);
+    const void* fn = (const void*)k_many<K>;
+    const int threads = (int)(block.x * block.y * block.z);
+    if (nblk == 0) {
+        const cudaError_t e = smem ? raise_smem_limit(fn, smem) : cudaSuccess;
+        if (e != cudaSuccess) return e;
+        return persistent_blocks(fn, threads, smem, true) > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    }
+    if (!smem_limit_covers(fn, smem)) return cudaErrorInvalidConfiguration;
+    const int pb = persistent_blocks(fn, threads, smem, false);
+    if (pb <= 0) return cudaErrorInvalidConfiguration;
+    k_many<K><<<nblk < (unsigned)pb ? nblk : (unsigned)pb, block, smem, s>>>((const K*)tab, m);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t many_launch_r0(const void* tab, const BatchMap& m, unsigned nblk, dim3 block, size_t smem,
                            const BatchCtl* ctl, cudaStream_t s) {
-    if (nblk == 0) return cudaSuccess;
-    k_many_r0<K><<<nblk, block, smem, s>>>((const K*)tab, m, *ctl);
+    const void* fn = (const void*)k_many_r0<K>;
+    const int threads = (int)(block.x * block.y * block.z);
+    if (nblk == 0) return persistent_blocks(fn, threads, smem, true) > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    const int pb = persistent_blocks(fn, threads, smem, false);
+    if (pb <= 0) return cudaErrorInvalidConfiguration;
+    k_many_r0<K><<<nblk < (unsigned)pb ? nblk : (unsigned)pb, block, smem, s>>>((const K*)tab, m, *ctl);
     return cudaGetLastError();
 }
 

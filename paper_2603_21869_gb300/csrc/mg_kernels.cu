@@ -79,17 +79,11 @@ __device__ __forceinline__ C sel(uint32_t code, C nb, C eP) {
     return code == 0 ? nb : (code == 1 ? eP : -eP);
 }
 
-// A e at one cell from its gathered neighbours.  A cell whose six faces all
-// see fluid neighbours (code bits zero; only on 3D levels, where no axis is
-// collapsed) takes diag eP - sum_a ih2_a (lo + hi) without the ghost selects.
+// A e at one cell from its gathered neighbours: the general form, with each
+// face's ghost chosen by its code.  Kept out of line so that it cannot be
+// predicated into the common path below.
 template <class C>
-__device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp, C ym, C yp, C zm, C zp) {
-    if ((f & 0xFFFu) == 0u) {
-        C s = (xm + xp) * LP<C>::ih2(L, 0);
-        s = fma(ym + yp, LP<C>::ih2(L, 1), s);
-        s = fma(zm + zp, LP<C>::ih2(L, 2), s);
-        return fma(LP<C>::diag(L), eP, -s);
-    }
+__device__ __noinline__ C A7_general(const LevelDev& L, uint32_t f, C eP, C xm, C xp, C ym, C yp, C zm, C zp) {
     C acc = (C)0;
     if (L.active[0]) acc += ((eP - sel(f & 3u, xm, eP)) + (eP - sel((f >> 2) & 3u, xp, eP))) * LP<C>::ih2(L, 0);
     if (L.active[1]) acc += ((eP - sel((f >> 4) & 3u, ym, eP)) + (eP - sel((f >> 6) & 3u, yp, eP))) * LP<C>::ih2(L, 1);
@@ -97,8 +91,21 @@ __device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp,
     return acc;
 }
 
-
-
+// A e at one cell.  The neighbour values are loaded with indices clamped into
+// the grid, so at a zero-gradient domain face the load already returns eP,
+// the ghost value.  Every cell without a zero-value face or a solid neighbour
+// (code bit 13 clear) therefore takes diag eP - sum_a ih2_a (lo + hi), with
+// ih2_a = 0 on a collapsed axis; the rest take the general form.
+template <class C>
+__device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp, C ym, C yp, C zm, C zp) {
+    if (!((f >> 13) & 1u)) {
+        C s = (xm + xp) * LP<C>::ih2a(L, 0);
+        s = fma(ym + yp, LP<C>::ih2a(L, 1), s);
+        s = fma(zm + zp, LP<C>::ih2a(L, 2), s);
+        return fma(LP<C>::diag(L), eP, -s);
+    }
+    return A7_general<C>(L, f, eP, xm, xp, ym, yp, zm, zp);
+}
 
 // ------------------------------------------------------------------ level 0 residual
 // r = b - A p (FP64), first pre-sweep e = w_J r / D, r^2 and b^2 per block;
@@ -114,6 +121,7 @@ struct Resid0K {
     TI* e;
     double* partials;
     SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ int run(const BlockAt& at) const;
 };
 
@@ -122,7 +130,6 @@ __device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     __shared__ double red[2][BX * BY * BZ / 32];
     __shared__ bool last;
-    if (!st->active) return -1;   // a case that has converged (batched launches)
     int i, j, k;
     C r2 = (C)0, b2 = (C)0;     // squares and warp sums in the inner precision, block sums in FP64
     if (cell3(L, at, i, j, k)) {
@@ -229,6 +236,7 @@ __device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
 struct SolveBeginK {
     static constexpr int kThreads = 1;
     SolveState* st;
+    __device__ bool live() const { return true; }
     __device__ void run(const BlockAt&) const {
         st->cycles = 0;
         st->counter = 0u;
@@ -244,9 +252,9 @@ struct SweepFirstK {
     const TI* r;
     TI* e;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const {
         using C = typename Acc<TI>::type;
-        if (!st->active) return;
         int i, j, k;
         if (!cell3(L, at, i, j, k)) return;
         const int c = i + L.n[0] * (j + L.n[1] * k);
@@ -264,13 +272,13 @@ struct ResidRestrictK {
     const TI* r;
     TI* rc;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
 template <class TI>
 __device__ void ResidRestrictK<TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
-    if (!st->active) return;
     int I, J, K;
     if (!cell3(Lc, at, I, J, K)) return;
     const int fx = Lf.active[0] ? 2 : 1, fy = Lf.active[1] ? 2 : 1, fz = Lf.active[2] ? 2 : 1;
@@ -323,9 +331,9 @@ struct ProlongK {
     const TI* ec;
     TI* e;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const {
         using C = typename Acc<TI>::type;
-        if (!st->active) return;
         int i, j, k;
         if (!cell3(Lf, at, i, j, k)) return;
         const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
@@ -336,13 +344,10 @@ struct ProlongK {
 };
 
 // ------------------------------------------------------------------ marching kernels (levels >= 0)
-// Block TX x TY threads; each thread walks KZ cells along z, keeping the z
-// neighbours in registers.  Neighbour loads use indices clamped into the
-// grid (a face outside the domain reads the cell itself) and are issued
-// before the neighbour code is consulted; the code then selects the
-// neighbour, the zero-gradient ghost or the zero-value ghost.
+// Blocks of TX x TY threads over x-y tiles, marching along z.  Neighbour
+// loads use indices clamped into the grid (a face outside the domain reads
+// the cell itself), so only cells with code bit 13 need the ghost selects.
 constexpr int TX = 32, TY = 8;
-constexpr int kWalkMinCells = 1 << 20;   // below this a thread takes one cell (more blocks)
 
 struct Walk {
     int i, j, k0, sy, sz, im, ip, jm, jp;
@@ -362,8 +367,10 @@ __device__ __forceinline__ bool walk_setup(const LevelDev& L, const BlockAt& at,
     return true;
 }
 
+// Scalar sweep (FP64 levels, and levels whose x extent is not a multiple of
+// 4): each thread walks KZ cells along z, keeping the z neighbours in
+// registers; all loads of its cells are issued before any arithmetic.
 // MODE 0: eout = sweep(ein); MODE 1: p += sweep(ein) (last level-0 sweep).
-// All loads of the thread's KZ cells are issued before any arithmetic.
 template <class TI, int MODE, int KZ>
 struct SweepK {
     static constexpr int kThreads = TX * TY;
@@ -373,13 +380,13 @@ struct SweepK {
     TI* eout;
     double* p;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
 template <class TI, int MODE, int KZ>
 __device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
-    if (!st->active) return;
     Walk w;
     if (!walk_setup(L, at, KZ, w)) return;
     const int nz = L.n[2];
@@ -419,6 +426,135 @@ __device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
     }
 }
 
+// Four consecutive x cells per thread, 128-bit (FP32) or 64-bit (BF16)
+// loads.  A warp covers 128 cells of a row and marches zc planes in z: rows
+// j +- 1 and the plane after next are loaded whole (indices clamped into the
+// grid, so a zero-gradient domain face reads the cell itself), the x
+// neighbours come from the adjacent lanes by shuffles (the warp's two end
+// cells from single loads), and the z neighbours rotate in registers.
+template <class TI> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, int c, float (&o)[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p + c));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ void store(float* p, int c, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, int c, float (&o)[4]) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p + c);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, int c, const float (&v)[4]) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<const uint32_t*>(&a);
+        w.y = *reinterpret_cast<const uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p + c) = w;
+    }
+};
+
+constexpr int V4X = 4 * TX;   // cells of a row per warp
+
+template <class TI, int MODE>
+struct SweepV4K {
+    static constexpr int kThreads = TX * TY;
+    static constexpr int kMinBlocks = 4;   // at most 64 registers: four blocks per SM
+    LevelDev L;
+    const TI* ein;
+    const TI* r;
+    TI* eout;
+    double* p;
+    const SolveState* st;
+    int zc;   // planes per block
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI, int MODE>
+__device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
+    using C = float;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int lane = threadIdx.x;
+    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
+    const bool in = i4 < nx && j < ny;
+    const int sy = nx, sz = nx * ny;
+    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
+    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
+    const bool last = i4 + 4 >= nx;   // the row's last cell is this thread's: its x+ ghost is itself
+    const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
+    const C dg = LP<C>::diag(L), wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
+    // the functor's pointers in registers for the whole march
+    const TI* const ein = this->ein;
+    const TI* const r = this->r;
+    TI* const eout = this->eout;
+    double* const p = this->p;
+    const uint16_t* const nbf = L.nbf;
+    C em[4], ec[4], ep[4];
+    Vec4<TI>::load(ein, max(k0 - 1, 0) * sz + own, em);
+    Vec4<TI>::load(ein, k0 * sz + own, ec);
+    Vec4<TI>::load(ein, min(k0 + 1, nz - 1) * sz + own, ep);
+    for (int k = k0; k < k1; ++k) {
+        const int base = k * sz;
+        C ym[4], yp[4], rr[4], en[4];
+        Vec4<TI>::load(ein, base + om, ym);
+        Vec4<TI>::load(ein, base + op, yp);
+        Vec4<TI>::load(r, base + own, rr);
+        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
+        const C xls = lane == 0 ? to_c<C>(ldg(ein + base + xl)) : (C)0;
+        const C xrs = lane == TX - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
+        Vec4<TI>::load(ein, min(k + 2, nz - 1) * sz + own, en);   // plane after next
+        C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
+        C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        if (lane == 0) left = xls;
+        if (lane == TX - 1) right = xrs;
+        if (last) right = ec[3];
+        const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
+        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+        C v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const C eP = xs[t + 1];
+            C A;
+            if (!((fs[t] >> 13) & 1u)) {
+                C s = (xs[t] + xs[t + 2]) * ihx;
+                s = fma(ym[t] + yp[t], ihy, s);
+                s = fma(em[t] + ep[t], ihz, s);
+                A = fma(dg, eP, -s);
+            } else {
+                A = A7_general<C>(L, fs[t], eP, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t]);
+            }
+            v[t] = is_solid(fs[t]) ? (C)0 : eP + wJ * (rr[t] - A) * iD;
+        }
+        if (in) {
+            if (MODE == 0) {
+                Vec4<TI>::store(eout, base + own, v);
+            } else {
+                double2* pp = reinterpret_cast<double2*>(p + base + own);
+                double2 a = pp[0], b = pp[1];
+                if (!is_solid(fs[0])) a.x += (double)v[0];
+                if (!is_solid(fs[1])) a.y += (double)v[1];
+                if (!is_solid(fs[2])) b.x += (double)v[2];
+                if (!is_solid(fs[3])) b.y += (double)v[3];
+                pp[0] = a;
+                pp[1] = b;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            em[t] = ec[t];
+            ec[t] = ep[t];
+            ep[t] = en[t];
+        }
+    }
+}
+
 // coarse r = mean of the children's (r - A e): one thread per fine cell (the
 // z pair of children in the thread), x / y pairs summed through shared memory.
 // Needs x and y active (2 x 2 children in the plane).
@@ -430,6 +566,7 @@ struct RRWalkK {
     const TI* r;
     TI* rc;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
@@ -437,7 +574,6 @@ template <class TI>
 __device__ void RRWalkK<TI>::run(const BlockAt& at) const {
     using C = typename Acc<TI>::type;
     __shared__ C part[TY][TX + 1];
-    if (!st->active) return;
     const int fz = Lf.active[2] ? 2 : 1;
     Walk w;
     const bool in = walk_setup(Lf, at, fz, w);
@@ -487,13 +623,13 @@ struct CoarseK {
     TI* e_out;
     const double* Ainv;
     const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
 template <class TI>
 __device__ void CoarseK<TI>::run(const BlockAt&) const {
     using C = typename Acc<TI>::type;
-    if (!st->active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // level descriptions and array bases live in shared memory (one copy per CTA)
     __shared__ LevelDev lvs[FVM_MAX_LEVELS];
@@ -693,10 +829,28 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
                 (unsigned)((L.n[2] + kz - 1) / kz));
 }
 
+// planes per block: the most that still give about eight blocks per SM
+static int sweep_planes(int tiles, int nz) {
+    for (int zc : {32, 16, 8, 4})
+        if (tiles * ((nz + zc - 1) / zc) >= 8 * 152) return zc;
+    return nz < 4 ? nz : 4;
+}
+
 template <class TI, int MODE>
 static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p,
                               const SolveState* st, cudaStream_t s) {
-    if (L.N >= kWalkMinCells)
+    if constexpr (sizeof(TI) < 8) {
+        // four cells per thread on large levels and in batches (their blocks add up over the cases)
+        if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
+            const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
+        const int zc = sweep_planes(tiles, L.n[2]);
+        const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
+                        (unsigned)((L.n[2] + zc - 1) / zc));
+        return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc}, grid, dim3(TX, TY), 0, s);
+        }
+    }
+    // four cells per thread on large grids and in batches (one launch for all cases of a level)
+    if (L.N >= (1 << 20) || g_rec)
         return launch_k(SweepK<TI, MODE, 4>{L, ein, r, eout, p, st}, walk_grid(L, 4), dim3(TX, TY), 0, s);
     return launch_k(SweepK<TI, MODE, 1>{L, ein, r, eout, p, st}, walk_grid(L, 1), dim3(TX, TY), 0, s);
 }

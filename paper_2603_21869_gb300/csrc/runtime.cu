@@ -63,16 +63,23 @@ void build_nbf(HostLevel& L) {
                     continue;
                 }
                 uint32_t code = 0;
+                bool irregular = false;   // a ghost that a neighbour load clamped into the grid does not give
                 const int f[3] = {i, j, k};
                 for (int d = 0; d < 6; ++d) {
                     const int a = d / 2, side = (d & 1) ? 1 : -1;
                     int q[3] = {f[0], f[1], f[2]};
                     q[a] += side;
                     uint32_t v;
-                    if (q[a] < 0 || q[a] >= L.n[a]) v = L.dir[d][face_index(a, i, j, k, L.n)] ? 2u : 1u;
-                    else v = L.solid[cell_index(q[0], q[1], q[2], L.n[0], L.n[1])] ? 1u : 0u;
+                    if (q[a] < 0 || q[a] >= L.n[a]) {
+                        v = L.dir[d][face_index(a, i, j, k, L.n)] ? 2u : 1u;
+                        irregular = irregular || v == 2u;
+                    } else {
+                        v = L.solid[cell_index(q[0], q[1], q[2], L.n[0], L.n[1])] ? 1u : 0u;
+                        irregular = irregular || v == 1u;
+                    }
                     code |= v << (2 * d);
                 }
+                if (irregular) code |= 1u << 13;
                 L.nbf[c] = (uint16_t)code;
             }
 }
@@ -231,6 +238,25 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
     if (e == cudaSuccess) have = bytes;
     else cudaGetLastError();
     return e;
+}
+
+int persistent_blocks(const void* fn, int threads, size_t smem, bool query) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({fn, smem});
+    if (it != cache.end()) return it->second;
+    if (!query) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int n = sms * (per_sm > 0 ? per_sm : 1);
+    cache[{fn, smem}] = n;
+    return n;
 }
 
 bool smem_limit_covers(const void* fn, size_t bytes) {
@@ -1028,7 +1054,11 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         v.inv_D = 1.0 / diag;
         v.diag = diag;
         v.wJ = d.jacobi_weight > 0.0 ? d.jacobi_weight : (nact == 3 ? 6.0 / 7.0 : 4.0 / 5.0);
-        for (int a = 0; a < 3; ++a) v.inv_h2f[a] = (float)v.inv_h2[a];
+        for (int a = 0; a < 3; ++a) {
+            v.inv_h2f[a] = (float)v.inv_h2[a];
+            v.ih2a[a] = H.active[a] ? v.inv_h2[a] : 0.0;
+            v.ih2af[a] = (float)v.ih2a[a];
+        }
         v.inv_Df = (float)v.inv_D;
         v.wJf = (float)v.wJ;
         v.diagf = (float)v.diag;
@@ -1437,7 +1467,7 @@ fvm_status build_arena(std::vector<Merged>* segs, int nseg, const std::vector<fv
                 return fail(FVM_ERR_INVALID, "batch too large for one launch");
             }
             m.nblk = (unsigned)tot;
-            m.ctl.total = (unsigned)tot;
+            m.map.total = (int)tot;
         }
     e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -168,6 +168,7 @@ __global__ void k_init(CaseDev cd, StatePtrs st, double b0, double b1, double b2
 template <class S, class C>
 struct RateMaxK {
     static constexpr int kThreads = 256;
+    __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs st;
     unsigned long long* rate_bits;
@@ -206,6 +207,7 @@ __device__ void RateMaxK<S, C>::run(const BlockAt& at) const {
 // dt_state: [0] dt, [1] dt/2, [2] simulated time, [3] rate bits (reset here)
 struct DtFinalizeK {
     static constexpr int kThreads = 1;
+    __device__ bool live() const { return true; }
     double dt0, cfl;
     int adapt;
     double* dt_state;
@@ -230,6 +232,7 @@ struct DtFinalizeK {
 template <class S, class C>
 struct DestructionK {
     static constexpr int kThreads = BX * BY * BZ;
+    __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in;
     S* k_out;
@@ -342,6 +345,7 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, const St<C>& nb, C nu) {
 template <class S, class C>
 struct ExplicitK {
     static constexpr int kThreads = BX * BY * BZ;
+    __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in, out;
     const double* dt_state;
@@ -424,6 +428,7 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
 template <class S, class C>
 struct RhsK {
     static constexpr int kThreads = BX * BY * BZ;
+    __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in;
     S* b;
@@ -468,6 +473,7 @@ __device__ __forceinline__ double p_across(const LevelDev& L, const double* p, u
 template <class S, class C>
 struct ProjectK {
     static constexpr int kThreads = BX * BY * BZ;
+    __device__ bool live() const { return true; }
     CaseDev cd;
     LevelDev L0;
     StatePtrs in, out;
