@@ -311,6 +311,72 @@ def run_batched(args, rank, ws, local, dist):
         dist.destroy_process_group()
 
 
+def run_served(args, rank, ws, local, dist):
+    """C5: a Poisson stream of room and channel requests served with
+    continuous batching under a device-memory budget: p50 / p99 latency
+    (arrival to completion) and the aggregate cell-steps/s."""
+    import torch
+    from paper_2603_21869_gb300 import binding, build
+    build.ensure_built()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    arrivals, specs = cases.served_rooms(args.requests, seed=rank, rate=args.rate)
+    srv = binding.Server(budget_bytes=int(args.budget_gb * (1 << 30)), stream=stream.cuda_stream)
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = srv.now()
+    nxt = 0
+    done = []
+    while len(done) < len(specs):
+        now = srv.now() - t_start
+        while nxt < len(specs) and arrivals[nxt] <= now:
+            srv.submit(specs[nxt], args.served_steps, t_arrive=t_start + float(arrivals[nxt]))
+            nxt += 1
+        inf = srv.info()
+        if inf["running"] == 0 and inf["queued"] == 0 and nxt < len(specs):
+            time.sleep(max(0.0, min(0.05, arrivals[nxt] - (srv.now() - t_start))))
+            continue
+        done += srv.poll(chunk=args.chunk)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_end = srv.now()
+    info = srv.info()
+    srv.close()
+    lat = sorted(d["t_done"] - d["t_arrive"] for d in done)
+    q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
+    makespan = t_end - t_start
+    cell_steps = sum(d["cells"] * d["steps"] for d in done)
+    bad = [d for d in done if d["status"] != 0]
+    if dist:
+        t = torch.tensor([makespan], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(cell_steps)], device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        makespan, cell_steps = float(t.item()), float(c.item())
+    if rank == 0:
+        line = {"metric": "cell-steps/s", "value": cell_steps / makespan, "unit": "cell-steps/s", "n_gpus": ws,
+                "steps": args.served_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16-mixed", "data": "synthetic",
+                "config": {"workload": f"served: Poisson arrivals at {args.rate}/s of {len(specs)} requests per GPU "
+                                       f"(rooms 64^3 .. 256x128x128 with seeded vents, boxes, heat; 20 % channels), "
+                                       f"{args.served_steps} steps each, HBM budget {args.budget_gb} GB, "
+                                       f"rounds of {args.chunk} steps",
+                           "parallelism": f"replicas x{ws}", "l2": "not flushed (a serving loop)"},
+                "latency_s": {"p50": q(0.50), "p99": q(0.99), "max": lat[-1], "mean": statistics.mean(lat)},
+                "makespan_s": makespan, "requests": len(done), "failed": len(bad),
+                "server": info, "clocks": clk,
+                "e2e": {"value": cell_steps / makespan, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0,
+                        "note": "requests enter as case descriptions (fields initialised on the device)"}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(spec, budget_s=25.0):
     """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload."""
     from oracle.step import OracleCase
@@ -340,9 +406,18 @@ def main():
     ap.add_argument("--cases", type=int, default=64, help="batched workload: cases per GPU")
     ap.add_argument("--accuracy-cases", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--requests", type=int, default=64, help="served workload: requests per GPU")
+    ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
+    ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--chunk", type=int, default=10, help="served workload: steps per scheduling round")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
+    if args.workload == "served" and args.impl == "ours":
+        rank, ws, local, dist = dist_setup()
+        run_served(args, rank, ws, local, dist)
+        return
     if args.workload == "batched":
         rank, ws, local, dist = dist_setup()
         if args.impl == "reference":

@@ -260,6 +260,66 @@ fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_st
 
 fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
 
+/* ---------------------------------------------------------------- serving
+   A request loop over resident cases (continuous batching).  A request is a
+   case description plus a number of steps.  fvm_server_poll runs one
+   scheduling round:
+     1. admit, first come first served, the queued requests whose arrival
+        time has passed while their device bytes (fvm_case_bytes) fit the
+        HBM budget and a slot is free: each becomes a resident case;
+     2. step every resident case together: one fvm_batch per precision,
+        min(chunk, fewest remaining steps) steps, so a newly admitted case
+        overlaps with the ones already running;
+     3. retire the finished requests (their memory is freed at once, or kept
+        for fvm_server_read_fields until fvm_server_release when
+        keep_results is set) and report them.
+   Times are seconds on the server's steady clock (fvm_server_now, zero at
+   creation); a request's latency is t_done - t_arrive.  The paper serves
+   no requests: this is an addition for many concurrent cases.  Not
+   thread-safe: drive a server from one thread. */
+typedef struct fvm_server fvm_server;
+
+typedef struct {
+    int64_t id;
+    int32_t status;                  /* FVM_OK, or the status that ended the request */
+    int32_t steps;                   /* steps run */
+    int64_t cells;
+    int64_t device_bytes;
+    int32_t vcycles_total;
+    int32_t reserved;
+    double  rel_residual;            /* after the last solve */
+    double  t_arrive, t_admit, t_done;
+} fvm_request_result;
+
+typedef struct {
+    int64_t queued, running, done;
+    int64_t bytes_in_use;            /* device bytes of the resident cases */
+    int64_t rounds;                  /* scheduling rounds that stepped cases */
+    int64_t batch_rebuilds;          /* batches (re)built after admissions or retirements */
+    int64_t cell_steps;              /* summed over retired and running requests */
+} fvm_server_info;
+
+/* budget_bytes: device bytes the resident cases may hold; max_cases: most
+   resident cases (0: no limit); stream: cudaStream_t or NULL (own stream);
+   keep_results: keep retired cases for reading.  Errors: FVM_ERR_INVALID. */
+fvm_status fvm_server_create(int64_t budget_bytes, int32_t max_cases, void* stream, int32_t keep_results,
+                             fvm_server** out);
+double fvm_server_now(const fvm_server* s);
+/* Queue a request (the descriptor and its vent and box arrays are copied;
+   desc->stream is ignored).  FVM_ERR_BUDGET when the case alone exceeds the
+   budget, FVM_ERR_INVALID for a bad descriptor. */
+fvm_status fvm_server_submit(fvm_server* s, const fvm_case_desc* desc, int32_t nsteps, double t_arrive,
+                             int64_t* id_out);
+/* One scheduling round (see above); done receives up to cap retired
+   requests, *n_done their number (may be NULL).  Returns FVM_OK unless the
+   server itself failed; a request's own failure is in its result. */
+fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* done, int32_t cap, int32_t* n_done);
+fvm_status fvm_server_get_info(const fvm_server* s, fvm_server_info* out);
+/* Fields of a retired request (keep_results), as fvm_read_fields. */
+fvm_status fvm_server_read_fields(fvm_server* s, int64_t id, unsigned field_mask, double* host_out, size_t n);
+fvm_status fvm_server_release(fvm_server* s, int64_t id);
+void fvm_server_destroy(fvm_server* s);
+
 /* Options (fvm_set_option).  FVM_OPT_GRAPH (default 1): run each time
    step as one CUDA graph, the V-cycle loop being a device-side while node;
    0 runs the same kernels launch by launch with one host synchronisation
@@ -301,10 +361,11 @@ fvm_status fvm_poisson_residual_static(const double* p, const double* b, int32_t
                                        const double h[3], const int32_t dirichlet[6], double* r,
                                        double* norms, void* stream);
 
-/* sizeof of the public structs, for binding checks: out[0..7] = fvm_patch,
+/* sizeof of the public structs, for binding checks: out[0..9] = fvm_patch,
    fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
-   fvm_kernel_stat, fvm_batch_info.  Needs no GPU. */
-void fvm_struct_sizes(size_t out[8]);
+   fvm_kernel_stat, fvm_batch_info, fvm_request_result, fvm_server_info.
+   Needs no GPU. */
+void fvm_struct_sizes(size_t out[10]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* fvm_last_error(void);

@@ -81,6 +81,18 @@ class KernelStat(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("ms", ct.c_double), ("bytes", ct.c_double)]
 
 
+class RequestResult(ct.Structure):
+    _fields_ = [("id", ct.c_int64), ("status", ct.c_int32), ("steps", ct.c_int32), ("cells", ct.c_int64),
+                ("device_bytes", ct.c_int64), ("vcycles_total", ct.c_int32), ("reserved", ct.c_int32),
+                ("rel_residual", ct.c_double), ("t_arrive", ct.c_double), ("t_admit", ct.c_double),
+                ("t_done", ct.c_double)]
+
+
+class ServerInfo(ct.Structure):
+    _fields_ = [("queued", ct.c_int64), ("running", ct.c_int64), ("done", ct.c_int64), ("bytes_in_use", ct.c_int64),
+                ("rounds", ct.c_int64), ("batch_rebuilds", ct.c_int64), ("cell_steps", ct.c_int64)]
+
+
 class BatchInfo(ct.Structure):
     _fields_ = [("n_cases", ct.c_int32), ("graphs", ct.c_int32), ("steps", ct.c_int64),
                 ("kernel_launches", ct.c_int64), ("cells", ct.c_int64), ("launches_per_step", ct.c_int64),
@@ -91,7 +103,9 @@ EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", 
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
            "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
            "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
-           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy", "fvm_batch_profile"]
+           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy", "fvm_batch_profile", "fvm_server_create",
+           "fvm_server_now", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields",
+           "fvm_server_release", "fvm_server_destroy"]
 
 _lib = None
 
@@ -130,6 +144,16 @@ def lib():
     L.fvm_batch_step.argtypes = [CP, ct.c_int32, ct.POINTER(StepStats)]
     L.fvm_batch_get_info.argtypes = [CP, ct.POINTER(BatchInfo)]
     L.fvm_batch_profile.argtypes = [CP, ct.c_int32, ct.POINTER(KernelStat), ct.c_int32, ct.POINTER(ct.c_int32)]
+    L.fvm_server_create.argtypes = [ct.c_int64, ct.c_int32, CP, ct.c_int32, ct.POINTER(CP)]
+    L.fvm_server_now.argtypes = [CP]
+    L.fvm_server_now.restype = ct.c_double
+    L.fvm_server_submit.argtypes = [CP, ct.POINTER(CaseDesc), ct.c_int32, ct.c_double, ct.POINTER(ct.c_int64)]
+    L.fvm_server_poll.argtypes = [CP, ct.c_int32, ct.POINTER(RequestResult), ct.c_int32, ct.POINTER(ct.c_int32)]
+    L.fvm_server_get_info.argtypes = [CP, ct.POINTER(ServerInfo)]
+    L.fvm_server_read_fields.argtypes = [CP, ct.c_int64, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_server_release.argtypes = [CP, ct.c_int64]
+    L.fvm_server_destroy.argtypes = [CP]
+    L.fvm_server_destroy.restype = None
     L.fvm_batch_destroy.argtypes = [CP]
     L.fvm_batch_destroy.restype = None
     L.fvm_struct_sizes.argtypes = [ct.POINTER(ct.c_size_t)]
@@ -138,7 +162,9 @@ def lib():
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_profile"]:
+                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_profile",
+                 "fvm_server_create", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info",
+                 "fvm_server_read_fields", "fvm_server_release"]:
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -201,7 +227,7 @@ def case_bytes(spec: cases.CaseSpec) -> int:
 
 
 def struct_sizes():
-    out = (ct.c_size_t * 8)()
+    out = (ct.c_size_t * 10)()
     lib().fvm_struct_sizes(out)
     return list(out)
 
@@ -356,6 +382,70 @@ class Batch:
     def close(self):
         if self._h:
             lib().fvm_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Request loop with continuous batching (fvm_server): requests are
+    admitted by device-memory budget, stepped together, and retired."""
+
+    def __init__(self, budget_bytes, max_cases=0, stream=None, keep_results=False):
+        h = ct.c_void_p()
+        _check(lib().fvm_server_create(int(budget_bytes), int(max_cases), stream, 1 if keep_results else 0,
+                                       ct.byref(h)))
+        self._h = h
+        self._shapes = {}
+        self._descs = []   # keep the submitted descriptors' arrays alive until submit copied them
+
+    def now(self):
+        return lib().fvm_server_now(self._h)
+
+    def submit(self, spec: cases.CaseSpec, nsteps, t_arrive=None):
+        d = _Desc(spec)
+        rid = ct.c_int64()
+        t = self.now() if t_arrive is None else float(t_arrive)
+        _check(lib().fvm_server_submit(self._h, ct.byref(d.desc), int(nsteps), t, ct.byref(rid)))
+        self._shapes[rid.value] = (spec.nx, spec.ny, spec.nz)
+        return rid.value
+
+    def poll(self, chunk=10, cap=1024):
+        arr = (RequestResult * cap)()
+        n = ct.c_int32()
+        _check(lib().fvm_server_poll(self._h, int(chunk), arr, cap, ct.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in RequestResult._fields_} for i in range(min(n.value, cap))]
+
+    def info(self):
+        inf = ServerInfo()
+        _check(lib().fvm_server_get_info(self._h, ct.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in ServerInfo._fields_}
+
+    def read(self, rid, fields=cases.FIELDS):
+        fields = [f for f in cases.FIELDS if f in fields]
+        nx, ny, nz = self._shapes[rid]
+        N = nx * ny * nz
+        buf = np.empty(len(fields) * N, dtype=np.float64)
+        _check(lib().fvm_server_read_fields(self._h, rid, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                            buf.size))
+        return {f: buf[i * N:(i + 1) * N].reshape(nz, ny, nx).transpose(2, 1, 0) for i, f in enumerate(fields)}
+
+    def release(self, rid):
+        _check(lib().fvm_server_release(self._h, rid))
+
+    def close(self):
+        if self._h:
+            lib().fvm_server_destroy(self._h)
             self._h = ct.c_void_p()
 
     def __del__(self):

@@ -247,9 +247,12 @@ def batched_channels(n_cases: int = 64, seed: int = 0, precision: int = FP32,
     return out
 
 
-def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0):
+def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0, channel_share: float = 0.2,
+                 precision: int = BF16_MIXED):
     """Poisson arrivals (rate per second) of room cases sized 64^3 to
-    256 x 128 x 128 (multiples of 32).  Returns (arrival_times, specs)."""
+    256 x 128 x 128 (multiples of 32), with seeded vents, obstacles and heat
+    loads; a share of the requests are heated channels of the same sizes.
+    Returns (arrival_times, specs)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     specs = []
@@ -257,5 +260,9 @@ def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0):
         nx = int(rng.choice([64, 96, 128, 160, 192, 224, 256]))
         ny = int(rng.choice([64, 96, 128]))
         nz = int(rng.choice([64, 96, 128]))
-        specs.append(room_3d(nx, ny, nz, seed=seed * 1000003 + r, mg_levels=5, h=0.04))
+        if rng.uniform() < channel_share:
+            specs.append(heated_channel_3d(nx, ny, nz, mg_levels=5, precision=precision,
+                                           seed=seed * 1000003 + r))
+        else:
+            specs.append(room_3d(nx, ny, nz, seed=seed * 1000003 + r, mg_levels=5, h=0.04, precision=precision))
     return t, specs

@@ -2143,7 +2143,7 @@ fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_o
     return FVM_OK;
 }
 
-void fvm_struct_sizes(size_t out[8]) {
+void fvm_struct_sizes(size_t out[10]) {
     out[0] = sizeof(fvm_patch);
     out[1] = sizeof(fvm_vent);
     out[2] = sizeof(fvm_box);
@@ -2152,6 +2152,8 @@ void fvm_struct_sizes(size_t out[8]) {
     out[5] = sizeof(fvm_case_info);
     out[6] = sizeof(fvm_kernel_stat);
     out[7] = sizeof(fvm_batch_info);
+    out[8] = sizeof(fvm_request_result);
+    out[9] = sizeof(fvm_server_info);
 }
 
 const char* fvm_last_error(void) { return g_err.c_str(); }

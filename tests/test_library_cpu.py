@@ -31,7 +31,8 @@ def test_struct_layout_matches_binding(lib):
     import ctypes as ct
     sizes = binding.struct_sizes()
     ours = [ct.sizeof(t) for t in (binding.Patch, binding.Vent, binding.Box, binding.CaseDesc,
-                                   binding.StepStats, binding.CaseInfo, binding.KernelStat, binding.BatchInfo)]
+                                   binding.StepStats, binding.CaseInfo, binding.KernelStat, binding.BatchInfo,
+                                   binding.RequestResult, binding.ServerInfo)]
     assert sizes == ours
 
 
@@ -44,6 +45,16 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert "null case" in binding.last_error()
     assert not h.value
     assert lib.fvm_batch_step(None, 1, None) == binding.ERR_INVALID
+
+
+def test_server_rejects_bad_arguments_without_a_gpu(lib):
+    import ctypes as ct
+    h = ct.c_void_p()
+    assert lib.fvm_server_create(0, 0, None, 0, ct.byref(h)) == binding.ERR_INVALID
+    assert lib.fvm_server_create(1 << 30, -1, None, 0, ct.byref(h)) == binding.ERR_INVALID
+    assert not h.value
+    assert lib.fvm_server_poll(None, 1, None, 0, None) == binding.ERR_INVALID
+    assert lib.fvm_server_submit(None, None, 1, 0.0, None) == binding.ERR_INVALID
 
 
 def test_case_bytes_scale_with_precision(lib):
