@@ -99,15 +99,12 @@ class Clocks:
 
 
 def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    if ws <= 1:
+    """Ranks of a torchrun launch (one per GPU, nccl); (0, 1, 0, None) alone."""
+    from paper_2603_21869_gb300 import replicas
+    rank, ws, local, on = replicas.setup()
+    if not on:
         return 0, 1, 0, None
-    import torch
     import torch.distributed as dist
-    rank = int(os.environ["RANK"])
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     return rank, ws, local, dist
 
 
@@ -175,7 +172,7 @@ def run_batched(args, rank, ws, local, dist):
     one by one (FP32, and the plain FP64 form)."""
     import numpy as np
     import torch
-    from paper_2603_21869_gb300 import binding, build
+    from paper_2603_21869_gb300 import binding, build, replicas
     build.ensure_built()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -215,9 +212,7 @@ def run_batched(args, rank, ws, local, dist):
     launches = batch.info()["kernel_launches"] - l0
     total_ms = sum(times)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = replicas.max_over_ranks(total_ms)
     value = ws * N * args.steps / (total_ms / 1e3)
     prof_steps = min(args.steps, 5)
     bd = breakdown(batch.profile(prof_steps), prof_steps)
@@ -238,9 +233,7 @@ def run_batched(args, rank, ws, local, dist):
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
                "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
         if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = ws * N * args.e2e_steps / float(t.item())
+            e2e["value"] = ws * N * args.e2e_steps / replicas.max_over_ranks(te)
     batch.close()
 
     # the same cases stepped one at a time (each its own graph per step), FP32 and plain FP64
@@ -316,7 +309,7 @@ def run_served(args, rank, ws, local, dist):
     continuous batching under a device-memory budget: p50 / p99 latency
     (arrival to completion) and the aggregate cell-steps/s."""
     import torch
-    from paper_2603_21869_gb300 import binding, build
+    from paper_2603_21869_gb300 import binding, build, replicas
     build.ensure_built()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -352,11 +345,7 @@ def run_served(args, rank, ws, local, dist):
     cell_steps = sum(d["cells"] * d["steps"] for d in done)
     bad = [d for d in done if d["status"] != 0]
     if dist:
-        t = torch.tensor([makespan], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([float(cell_steps)], device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        makespan, cell_steps = float(t.item()), float(c.item())
+        makespan, cell_steps = replicas.max_over_ranks(makespan), replicas.sum_over_ranks(cell_steps)
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": cell_steps / makespan, "unit": "cell-steps/s", "n_gpus": ws,
                 "steps": args.served_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
@@ -442,7 +431,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_2603_21869_gb300 import binding, build
+    from paper_2603_21869_gb300 import binding, build, replicas
     build.ensure_built()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -483,9 +472,7 @@ def main():
     launches = case.info()["kernel_launches"] - launches0
     total_ms = sum(times)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = replicas.max_over_ranks(total_ms)
     value = ws * N * args.steps / (total_ms / 1e3)
 
     # per-kernel breakdown: the same steps again, launch by launch, each kernel
@@ -524,9 +511,7 @@ def main():
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
                "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
         if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = ws * N * args.e2e_steps / float(t.item())
+            e2e["value"] = ws * N * args.e2e_steps / replicas.max_over_ranks(te)
 
     line = None
     if rank == 0:
