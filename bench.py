@@ -45,6 +45,12 @@ def workload(name, precision):
     raise SystemExit(f"unknown workload {name}")
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel, from one ncu capture each (profiles/sweep_v4_room_channel_batched_fp32.md);
+# to be taken again whenever that kernel changes.
+TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"): 212.38e6}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -523,7 +529,8 @@ def main():
                            "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps"},
                 "vcycles_per_step": statistics.mean(vc), "rel_residual_max": max(rels),
                 "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                             "frac": achieved / peak, "peak_source": peak_src,
+                             "traffic": TRAFFIC.get((args.workload, args.precision, name)),
                              "bytes_per_launch": d["bytes"] / d["launches"],
                              "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"]},
                 "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
