@@ -10,6 +10,7 @@
 
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/fvm.h"
@@ -108,7 +109,22 @@ struct SolveState {
     int32_t fixed;           // > 0: exactly this many cycles
     int32_t notconv;         // sticky flag: a solve stopped at max_cycles above tol
     int32_t inner;           // V-cycles per outer (FP64) residual
-    int32_t tma_timeout;     // sticky flag: a bounded wait for a tensor copy gave up
+    int32_t tma_timeout;     // sticky flag: a bounded device-side wait (tensor copy, grid barrier) gave up
+    uint32_t bar_count;      // grid barrier of the persistent tail kernel: blocks arrived
+    uint32_t bar_gen;        // and its generation
+};
+
+// Levels ls..L-1 of one V-cycle run by one persistent kernel: grid levels
+// ls..lc-1 by all blocks (grid-stride loops between grid barriers), the
+// coarse levels lc.. by block 0 in shared memory.
+struct TailLevels {
+    int32_t ls, lc, nl;      // first level in the kernel, first coarse level, number of levels
+    int32_t pre, post;
+    int32_t pad;
+    LevelDev lv[FVM_MAX_LEVELS];    // by absolute level index
+    void* e[FVM_MAX_LEVELS][2];
+    void* r[FVM_MAX_LEVELS];
+    uint64_t mx[FVM_MAX_LEVELS], my[FVM_MAX_LEVELS];   // exact division by n_x, n_y (div_magic)
 };
 
 // Levels lc..L-1, cycled by one CTA in shared memory.
@@ -218,6 +234,12 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s);
 cudaError_t prepare_coarse_cta(int inner, size_t smem);
+// persistent tail of the V-cycle (levels ls.. of one case); the correction of level ls ends in
+// e[ls][tail_out_index(pre, post)]
+int tail_blocks(int inner, size_t smem);
+cudaError_t launch_tail(int inner, const TailLevels& t, const CoarseLevels& cl, const double* Ainv, SolveState* st,
+                        int nblocks, size_t smem, cudaStream_t s);
+inline int tail_out_index(int pre, int post) { return ((pre - 1) + post) & 1; }
 cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_in, void* e_out, const double* Ainv,
                               const SolveState* st, cudaStream_t s);
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
@@ -285,8 +307,19 @@ struct MinBlocks<K, std::void_t<decltype(K::kMinBlocks)>> {
     static constexpr int value = K::kMinBlocks;
 };
 
+// Programmatic dependent launch: a kernel may be scheduled while the one
+// before it on the stream drains.  Every kernel first waits for the
+// previous grid to complete and flush its memory (griddepcontrol.wait; a
+// no-op when launched without the attribute), then lets its own dependents
+// be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <class K>
 __global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_one(const __grid_constant__ K k) {
+    pdl_enter();
     k.run(BlockAt{blockIdx, gridDim});
 }
 
@@ -345,6 +378,7 @@ __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchM
 
 template <class K>
 __global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_many(const K* __restrict__ ks, BatchMap m) {
+    pdl_enter();
     batch_run(ks, m);
 }
 
@@ -362,6 +396,7 @@ struct BatchCtl {
 template <class K>
 __global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ K k, cudaGraphConditionalHandle cond,
                                                         cudaGraphConditionalHandle cond2, int use_cond) {
+    pdl_enter();
     const int go = k.run(BlockAt{blockIdx, gridDim});   // >= 0 only in the deciding thread
     if (go >= 0 && use_cond) {
         cudaGraphSetConditional(cond, go ? 1u : 0u);
@@ -371,6 +406,7 @@ __global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ 
 
 template <class K>
 __global__ void __launch_bounds__(K::kThreads) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
+    pdl_enter();
     batch_run(ks, m);
     if (threadIdx.x + threadIdx.y + threadIdx.z != 0) return;
     __threadfence();   // the decisions this block made, before the count
@@ -383,6 +419,25 @@ __global__ void __launch_bounds__(K::kThreads) k_many_r0(const K* __restrict__ k
         cudaGraphSetConditional(ctl.cond, any ? 1u : 0u);
         if (ctl.use_cond > 1) cudaGraphSetConditional(ctl.cond2, any ? 1u : 0u);
     }
+}
+
+// Launch with the programmatic-serialization attribute (off when FVM_NO_PDL is set).
+bool pdl_enabled();
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Host side.  While a Recorder is installed on the calling thread, launches
@@ -437,8 +492,7 @@ cudaError_t many_launch(const void* tab, const BatchMap& m, unsigned nblk, dim3 
     if (!smem_limit_covers(fn, smem)) return cudaErrorInvalidConfiguration;
     const int pb = persistent_blocks(fn, threads, smem, false);
     if (pb <= 0) return cudaErrorInvalidConfiguration;
-    k_many<K><<<nblk < (unsigned)pb ? nblk : (unsigned)pb, block, smem, s>>>((const K*)tab, m);
-    return cudaGetLastError();
+    return launch_pdl(k_many<K>, dim3(nblk < (unsigned)pb ? nblk : (unsigned)pb), block, smem, s, (const K*)tab, m);
 }
 
 template <class K>
@@ -449,8 +503,8 @@ cudaError_t many_launch_r0(const void* tab, const BatchMap& m, unsigned nblk, di
     if (nblk == 0) return persistent_blocks(fn, threads, smem, true) > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     const int pb = persistent_blocks(fn, threads, smem, false);
     if (pb <= 0) return cudaErrorInvalidConfiguration;
-    k_many_r0<K><<<nblk < (unsigned)pb ? nblk : (unsigned)pb, block, smem, s>>>((const K*)tab, m, *ctl);
-    return cudaGetLastError();
+    return launch_pdl(k_many_r0<K>, dim3(nblk < (unsigned)pb ? nblk : (unsigned)pb), block, smem, s, (const K*)tab, m,
+                      *ctl);
 }
 
 template <class K>
@@ -473,16 +527,21 @@ template <class K>
 cudaError_t launch_k(const K& k, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
     if (record_launch(k, grid, block, smem, &many_launch<K>)) return cudaSuccess;
     if (!smem_limit_covers((const void*)k_one<K>, smem)) return cudaErrorInvalidConfiguration;
-    k_one<K><<<grid, block, smem, s>>>(k);
-    return cudaGetLastError();
+    return launch_pdl(k_one<K>, grid, block, smem, s, k);
+}
+
+// a launch that is never batched (no recorder, no table form)
+template <class K>
+cudaError_t launch_k_one(const K& k, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (!smem_limit_covers((const void*)k_one<K>, smem)) return cudaErrorInvalidConfiguration;
+    return launch_pdl(k_one<K>, grid, block, smem, s, k);
 }
 
 template <class K>
 cudaError_t launch_r0(const K& k, dim3 grid, dim3 block, cudaGraphConditionalHandle cond,
                       cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
     if (record_launch(k, grid, block, 0, &many_launch_r0<K>)) return cudaSuccess;
-    k_one_r0<K><<<grid, block, 0, s>>>(k, cond, cond2, use_cond);
-    return cudaGetLastError();
+    return launch_pdl(k_one_r0<K>, grid, block, 0, s, k, cond, cond2, use_cond);
 }
 
 // message returned by fvm_last_error() on this thread

@@ -240,6 +240,7 @@ struct SolveBeginK {
     __device__ void run(const BlockAt&) const {
         st->cycles = 0;
         st->counter = 0u;
+        st->bar_count = 0u;
         st->active = 1;
     }
 };
@@ -628,7 +629,17 @@ struct CoarseK {
 };
 
 template <class TI>
+__device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r_in, TI* __restrict__ e_out,
+                                const double* __restrict__ Ainv);
+
+template <class TI>
 __device__ void CoarseK<TI>::run(const BlockAt&) const {
+    coarse_cta_body<TI>(cl, r_in, e_out, Ainv);
+}
+
+template <class TI>
+__device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r_in, TI* __restrict__ e_out,
+                                const double* __restrict__ Ainv) {
     using C = typename Acc<TI>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // level descriptions and array bases live in shared memory (one copy per CTA)
@@ -763,6 +774,162 @@ __device__ void CoarseK<TI>::run(const BlockAt&) const {
     }
 }
 
+// ------------------------------------------------------------------ persistent tail of the V-cycle
+// Levels ls..lc-1 by every block (grid-stride loops over the level's cells,
+// a grid barrier between phases), the coarse levels lc.. by block 0 with the
+// single-CTA solve, then back up.  One launch replaces the sweeps,
+// restrictions, prolongations and the coarse solve of those levels (their
+// grids are small: a kernel boundary costs more than the work).  The grid
+// has one block per SM, all resident; the barrier's wait is bounded and
+// reports a time-out through the solve state.
+constexpr int kTailThreads = 1024;
+
+__device__ bool tail_barrier(SolveState* st, unsigned nblk) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile uint32_t* gen = &st->bar_gen;
+        const uint32_t g = *gen;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == nblk - 1u) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > (1ll << 22)) {   // about a second
+                    st->tma_timeout = 1;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void cell_ijk(const LevelDev& L, uint64_t mx, uint64_t my, int c, int& i, int& j,
+                                         int& k) {
+    const int q = fdiv(c, mx);
+    i = c - q * L.n[0];
+    k = fdiv(q, my);
+    j = q - k * L.n[1];
+}
+
+// one Jacobi sweep of a level (first: from e = 0, i.e. e = w_J r / D)
+template <class TI>
+__device__ void tail_sweep(const LevelDev& L, uint64_t mx, uint64_t my, const TI* ein, const TI* r, TI* eout,
+                           bool first, int g0, int gs) {
+    using C = typename Acc<TI>::type;
+    const C wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
+    const int sy = L.n[0], sz = L.n[0] * L.n[1];
+    for (int c = g0; c < (int)L.N; c += gs) {
+        const uint32_t f = L.nbf[c];
+        const C rr = to_c<C>(ldg(r + c));
+        C v = (C)0;
+        if (!is_solid(f)) {
+            if (first) {
+                v = wJ * rr * iD;
+            } else {
+                int i, j, k;
+                cell_ijk(L, mx, my, c, i, j, k);
+                const C eP = to_c<C>(ldg(ein + c));
+                const C xm = to_c<C>(ldg(ein + c - (i > 0 ? 1 : 0))), xp = to_c<C>(ldg(ein + c + (i < L.n[0] - 1 ? 1 : 0)));
+                const C ym = to_c<C>(ldg(ein + c - (j > 0 ? sy : 0))), yp = to_c<C>(ldg(ein + c + (j < L.n[1] - 1 ? sy : 0)));
+                const C zm = to_c<C>(ldg(ein + c - (k > 0 ? sz : 0))), zp = to_c<C>(ldg(ein + c + (k < L.n[2] - 1 ? sz : 0)));
+                v = eP + wJ * (rr - A7<C>(L, f, eP, xm, xp, ym, yp, zm, zp)) * iD;
+            }
+        }
+        eout[c] = from_c<TI, C>(v);
+    }
+}
+
+template <class TI>
+struct TailK {
+    static constexpr int kThreads = kTailThreads;
+    TailLevels t;
+    CoarseLevels cl;
+    const double* Ainv;
+    SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void TailK<TI>::run(const BlockAt& at) const {
+    using C = typename Acc<TI>::type;
+    const unsigned nblk = at.g.x;
+    const int g0 = at.b.x * kThreads + threadIdx.x, gs = (int)nblk * kThreads;
+    int cur[FVM_MAX_LEVELS];
+    // down
+    for (int l = t.ls; l < t.lc; ++l) {
+        const LevelDev& L = t.lv[l];
+        TI* const* e = (TI* const*)t.e[l];
+        const TI* r = (const TI*)t.r[l];
+        tail_sweep<TI>(L, t.mx[l], t.my[l], nullptr, r, e[0], true, g0, gs);
+        int q = 0;
+        for (int it = 1; it < t.pre; ++it) {
+            if (!tail_barrier(st, nblk)) return;
+            tail_sweep<TI>(L, t.mx[l], t.my[l], e[q], r, e[q ^ 1], false, g0, gs);
+            q ^= 1;
+        }
+        cur[l] = q;
+        if (!tail_barrier(st, nblk)) return;
+        // coarse r = mean of the children's residuals
+        const LevelDev& Lc = t.lv[l + 1];
+        TI* rc = (TI*)t.r[l + 1];
+        const int fx = L.active[0] ? 2 : 1, fy = L.active[1] ? 2 : 1, fz = L.active[2] ? 2 : 1;
+        for (int cc = g0; cc < (int)Lc.N; cc += gs) {
+            int I, J, K;
+            cell_ijk(Lc, t.mx[l + 1], t.my[l + 1], cc, I, J, K);
+            C sum = (C)0;
+            for (int dz = 0; dz < fz; ++dz)
+                for (int dy = 0; dy < fy; ++dy)
+                    for (int dx = 0; dx < fx; ++dx) {
+                        const int c = (I * fx + dx) + L.n[0] * ((J * fy + dy) + L.n[1] * (K * fz + dz));
+                        const uint32_t f = L.nbf[c];
+                        if (is_solid(f)) continue;
+                        const C eP = to_c<C>(ldg(e[q] + c));
+                        sum += to_c<C>(ldg(r + c)) - apply_A<C>(L, f, e[q], c, eP);
+                    }
+            rc[cc] = from_c<TI, C>(sum / (C)(fx * fy * fz));
+        }
+        if (!tail_barrier(st, nblk)) return;
+    }
+    // coarse levels in block 0
+    if (at.b.x == 0) coarse_cta_body<TI>(cl, (const TI*)t.r[t.lc], (TI*)t.e[t.lc][0], Ainv);
+    if (!tail_barrier(st, nblk)) return;
+    // up
+    for (int l = t.lc - 1; l >= t.ls; --l) {
+        const LevelDev& L = t.lv[l];
+        const LevelDev& Lc = t.lv[l + 1];
+        TI* const* e = (TI* const*)t.e[l];
+        const TI* r = (const TI*)t.r[l];
+        const TI* ec = (const TI*)t.e[l + 1][l + 1 == t.lc ? 0 : cur[l + 1]];
+        int q = cur[l];
+        for (int c = g0; c < (int)L.N; c += gs) {
+            if (is_solid(L.nbf[c])) continue;
+            int i, j, k;
+            cell_ijk(L, t.mx[l], t.my[l], c, i, j, k);
+            const C add = prolong_at<C>(L.active, Lc.n, i, j, k, [&](int w) { return to_c<C>(ldg(ec + w)); });
+            e[q][c] = from_c<TI, C>(to_c<C>(e[q][c]) + add);
+        }
+        for (int it = 0; it < t.post; ++it) {
+            if (!tail_barrier(st, nblk)) return;
+            tail_sweep<TI>(L, t.mx[l], t.my[l], e[q], r, e[q ^ 1], false, g0, gs);
+            q ^= 1;
+        }
+        cur[l] = q;
+        if (l > t.ls && !tail_barrier(st, nblk)) return;
+    }
+}
+
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, int64_t N) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -829,11 +996,12 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
                 (unsigned)((L.n[2] + kz - 1) / kz));
 }
 
-// planes per block: the most that still give about eight blocks per SM
+// planes per block: the most that still give about eight blocks per SM (one plane per
+// block on grids too small for that)
 static int sweep_planes(int tiles, int nz) {
-    for (int zc : {32, 16, 8, 4})
+    for (int zc : {32, 16, 8, 4, 2})
         if (tiles * ((nz + zc - 1) / zc) >= 8 * 152) return zc;
-    return nz < 4 ? nz : 4;
+    return 1;
 }
 
 template <class TI, int MODE>
@@ -904,6 +1072,30 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
     cudaError_t err = cudaSuccess;
     DISPATCH_I(inner, err = launch_k(CoarseK<TI>{cl, (const TI*)r_in, (TI*)e_out, Ainv, st}, dim3(1),
                                      dim3(kCtaThreads), smem, s));
+    return err;
+}
+
+int tail_blocks(int inner, size_t smem) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaSuccess;
+    DISPATCH_I(inner, {
+        e = raise_smem_limit((const void*)k_one<TailK<TI>>, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_one<TailK<TI>>, kTailThreads, smem);
+    });
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;   // one block per SM: all resident at once
+}
+
+cudaError_t launch_tail(int inner, const TailLevels& t, const CoarseLevels& cl, const double* Ainv, SolveState* st,
+                        int nblocks, size_t smem, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k_one(TailK<TI>{t, cl, Ainv, st}, dim3(nblocks), dim3(kTailThreads), smem, s));
     return err;
 }
 

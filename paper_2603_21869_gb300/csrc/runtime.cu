@@ -223,6 +223,11 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 
 thread_local Recorder* g_rec = nullptr;
 
+bool pdl_enabled() {
+    static const bool on = getenv("FVM_NO_PDL") == nullptr || getenv("FVM_NO_PDL")[0] == '0';
+    return on;
+}
+
 namespace {
 std::mutex g_smem_mu;
 std::map<const void*, size_t> g_smem_limit;   // dynamic shared-memory limit set per kernel
@@ -303,6 +308,10 @@ struct fvm_case {
     int inner_cycles = 1;            // V-cycles per outer residual (adaptive solves)
     int rule_inner = 1;              // the same for the rule in force (1 for fixed-count solves)
     CoarseLevels coarse;
+    // persistent tail kernel for levels tail_ls.. (0: not used)
+    int tail_ls = 0;
+    int tail_blocks = 0;
+    TailLevels tail;
     // CUDA graphs of whole time steps, keyed by the field pointers they were captured with
     bool use_graph = true;
     struct StepGraph {
@@ -630,6 +639,20 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
             KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
                     launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
         out_idx = 0;
+        return FVM_OK;
+    }
+    if (!g_rec && c->tail_ls > 0 && l == (size_t)c->tail_ls) {
+        // levels l.. of the V-cycle in one persistent kernel (their kernels' bytes, for profiling)
+        double bytes = 0.0;
+        for (size_t q = l; q < c->lc; ++q) {
+            const double n = (double)c->levels[q].dev.N, nc = (double)c->levels[q + 1].dev.N;
+            bytes += (2 * n * si + 2 * n) + (c->desc.pre_sweeps - 1 + c->desc.post_sweeps) * (3 * n * si + 2 * n) +
+                     2 * (2 * n * si + nc * si + 2 * n);
+        }
+        KLAUNCH("vtail", bytes, 1,
+                launch_tail(c->inner, c->tail, c->coarse, c->Ainv, c->sst, c->tail_blocks,
+                            coarse_cta_smem(c->coarse, c->inner), s));
+        out_idx = tail_out_index(c->desc.pre_sweeps, c->desc.post_sweeps);
         return FVM_OK;
     }
     DevLevel& Lc = c->levels[l + 1];
@@ -1195,6 +1218,38 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             D.tma = tma_make_maps(D.maps, D.dev, Dc.dev, D.e, D.r, Dc.e);
         }
     }
+    // the small levels above the coarse ones in one persistent kernel per V-cycle (opt-in with
+    // FVM_TAIL=1: on GB300 a grid barrier costs about as much as the kernel boundary it replaces)
+    if (!c->use_cluster && getenv_flag("FVM_TAIL") == 1) {
+        size_t ls = 0;
+        for (size_t l = 1; l < c->lc; ++l)
+            if (c->levels[l].dev.N <= (1 << 18) && !c->levels[l].tma) {
+                ls = l;
+                break;
+            }
+        // at most one block per SM, and no more blocks than the first tail level has cells / 1024
+        int nb = ls ? tail_blocks(pl.inner, coarse_cta_smem(c->coarse, pl.inner)) : 0;
+        if (ls) nb = std::min<int64_t>(nb, std::max<int64_t>(1, c->levels[ls].dev.N / 1024));
+        if (ls && nb > 0) {
+            c->tail_ls = (int)ls;
+            c->tail_blocks = nb;
+            TailLevels& t = c->tail;
+            memset(&t, 0, sizeof(t));
+            t.ls = (int)ls;
+            t.lc = (int)c->lc;
+            t.nl = (int)c->levels.size();
+            t.pre = d.pre_sweeps;
+            t.post = d.post_sweeps;
+            for (size_t l = 0; l < c->levels.size(); ++l) {
+                t.lv[l] = c->levels[l].dev;
+                t.e[l][0] = c->levels[l].e[0];
+                t.e[l][1] = c->levels[l].e[1];
+                t.r[l] = c->levels[l].r;
+                t.mx[l] = div_magic((uint32_t)c->levels[l].dev.n[0]);
+                t.my[l] = div_magic((uint32_t)c->levels[l].dev.n[1]);
+            }
+        }
+    }
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))
         return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
@@ -1753,7 +1808,7 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     stats.rel_residual = c->h_sst->rel;
     stats.dt_last = c->h_dt[0];
     stats.sim_time = c->h_dt[2];
-    if (c->h_sst->tma_timeout) result = fail(FVM_ERR_CUDA, "a bounded wait for a tensor copy timed out");
+    if (c->h_sst->tma_timeout) result = fail(FVM_ERR_CUDA, "a bounded device-side wait timed out");
     else if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
     else if (c->h_sst->notconv) {
         result = FVM_ERR_NOT_CONVERGED;

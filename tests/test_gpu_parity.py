@@ -286,6 +286,20 @@ def test_fused_tma_vcycle_matches_oracle_vcycle(monkeypatch):
             assert rel_err(c.read(("p",))["p"], p) <= 2e-5
 
 
+@pytest.mark.parametrize("name", ["channel3d_box_vent", "room_buoyant", "channel2d_ragged"])
+def test_persistent_tail_kernel_matches_oracle(monkeypatch, name):
+    """The levels below the finest in one persistent kernel per V-cycle
+    (grid barriers between phases, the coarse levels in block 0): FP64
+    fields within 1e-10 of the oracle."""
+    monkeypatch.setenv("FVM_TAIL", "1")
+    spec = SPECS[name]()
+    with binding.Case(spec) as c:
+        c.step(2)
+        got = c.read()
+    o = OracleCase(spec).step(2)
+    assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name} with the tail kernel")
+
+
 @pytest.mark.slow
 def test_full_size_heated_channel_one_step():
     """The 256 x 64 x 64 channel (the benchmark workload) in FP64, one step
