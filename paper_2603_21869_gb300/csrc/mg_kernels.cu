@@ -556,6 +556,199 @@ __device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
     }
 }
 
+// Trilinear prolongation and correction, four x cells per thread: a lane's
+// four fine cells have the coarse parents I0 = i/2 and I0 + 1 (two
+// consecutive coarse cells, one float2 per coarse row), their x neighbours
+// I0 - 1 and I0 + 2 come from the adjacent lanes; per fine cell the weights
+// are 3/4 for the parent and 1/4 for the neighbour on the cell's side, per
+// axis, neighbour indices clamped (Eq. prolongation).  Needs the x and y axes
+// active and nx % 4 = 0.
+template <class TI> struct Vec2;
+template <> struct Vec2<float> {
+    static __device__ __forceinline__ void load(const float* p, int c, float& a, float& b) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p + c));
+        a = v.x;
+        b = v.y;
+    }
+};
+template <> struct Vec2<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, int c, float& a, float& b) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(p + c);
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+        a = v.x;
+        b = v.y;
+    }
+};
+
+template <class TI>
+struct ProlongV4K {
+    static constexpr int kThreads = TX * TY;
+    static constexpr int kMinBlocks = 4;
+    LevelDev Lf, Lc;
+    const TI* ec;
+    TI* e;
+    const SolveState* st;
+    int zc;   // planes per block
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
+    using C = float;
+    const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
+    const int NX = Lc.n[0], NY = Lc.n[1], NZ = Lc.n[2];
+    const int lane = threadIdx.x;
+    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
+    const bool in = i4 < nx && j < ny;
+    const bool last = i4 + 4 >= nx;
+    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int I0 = ic >> 1;
+    const int Pj = jc >> 1, Qj = min(max(Pj + ((jc & 1) ? 1 : -1), 0), NY - 1);
+    const bool zact = Lf.active[2] != 0;
+    const TI* const ecp = ec;
+    TI* const ep = e;
+    const uint16_t* const nbf = Lf.nbf;
+    for (int k = k0; k < k1; ++k) {
+        const int Pk = zact ? (k >> 1) : k;
+        const int Qk = zact ? min(max(Pk + ((k & 1) ? 1 : -1), 0), NZ - 1) : k;
+        const C wz0 = zact ? (C)0.75 : (C)1, wz1 = zact ? (C)0.25 : (C)0;
+        C add[4] = {(C)0, (C)0, (C)0, (C)0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = (q & 1) ? Qj : Pj, kk = (q & 2) ? Qk : Pk;
+            const C w = ((q & 1) ? (C)0.25 : (C)0.75) * ((q & 2) ? wz1 : wz0);
+            const int row = NX * (jj + NY * kk);
+            C c0, c1;
+            Vec2<TI>::load(ecp, row + I0, c0, c1);
+            const C lft = lane == 0 ? to_c<C>(ldg(ecp + row + max(I0 - 1, 0))) : (C)0;
+            const C rgt = lane == TX - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
+            C left = __shfl_up_sync(0xffffffffu, c1, 1);
+            C right = __shfl_down_sync(0xffffffffu, c0, 1);
+            if (lane == 0) left = lft;
+            if (lane == TX - 1) right = rgt;
+            if (last) right = c1;
+            add[0] += w * ((C)0.75 * c0 + (C)0.25 * left);
+            add[1] += w * ((C)0.75 * c0 + (C)0.25 * c1);
+            add[2] += w * ((C)0.75 * c1 + (C)0.25 * c0);
+            add[3] += w * ((C)0.75 * c1 + (C)0.25 * right);
+        }
+        if (in) {
+            const int c = ic + nx * (jc + ny * k);
+            C v[4];
+            Vec4<TI>::load(ep, c, v);
+            const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + c));
+            const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (!is_solid(fs[t])) v[t] += add[t];
+            Vec4<TI>::store(ep, c, v);
+        }
+    }
+}
+
+// Residual and restriction, four x cells per thread: a thread owns the fine
+// cells i4..i4+3 of rows 2J, 2J+1 and planes 2K, 2K+1 (2D: plane K) and
+// writes the two coarse cells I0 = i4/2, I0 + 1 (mean of their children's
+// r - A e, Eq. restriction).  Rows j +- 1 and planes k +- 1 are loaded whole,
+// x neighbours by shuffles.  Needs x and y active, nx % 4 = 0, ny even.
+template <class TI>
+struct RRV4K {
+    static constexpr int kThreads = TX * TY;
+    static constexpr int kMinBlocks = 3;
+    LevelDev Lf, Lc;
+    const TI* e;
+    const TI* r;
+    TI* rc;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void RRV4K<TI>::run(const BlockAt& at) const {
+    using C = float;
+    const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
+    const int NX = Lc.n[0], NY = Lc.n[1];
+    const int lane = threadIdx.x;
+    const int i4 = at.b.x * V4X + lane * 4, J = at.b.y * TY + threadIdx.y, K = at.b.z;
+    const bool in = i4 < nx && J < NY;
+    const bool last = i4 + 4 >= nx;
+    const int fz = Lf.active[2] ? 2 : 1;
+    const int ic = min(i4, nx - 4), Jc = min(J, NY - 1);
+    const int ja = 2 * Jc, jb = ja + 1, jm = max(ja - 1, 0), jp = min(jb + 1, ny - 1);
+    const int sy = nx, sz = nx * ny;
+    const C ihx = LP<C>::ih2a(Lf, 0), ihy = LP<C>::ih2a(Lf, 1), ihz = LP<C>::ih2a(Lf, 2);
+    const C dg = LP<C>::diag(Lf);
+    const TI* const ep = e;
+    const TI* const rp = r;
+    const uint16_t* const nbf = Lf.nbf;
+    auto at_ = [&](int jj, int kk) { return ic + sy * jj + sz * kk; };
+    C s0 = (C)0, s1 = (C)0;   // sums of the coarse cells I0, I0 + 1
+    for (int dz = 0; dz < fz; ++dz) {
+        const int k = fz * K + dz;
+        const int km = max(k - 1, 0), kp = min(k + 1, nz - 1);
+        C ra[4], rb[4], ym[4], ea[4], eb[4], yp[4], za[4], zb[4], wa[4], wb[4];
+        Vec4<TI>::load(ep, at_(jm, k), ym);
+        Vec4<TI>::load(ep, at_(ja, k), ea);
+        Vec4<TI>::load(ep, at_(jb, k), eb);
+        Vec4<TI>::load(ep, at_(jp, k), yp);
+        Vec4<TI>::load(ep, at_(ja, km), za);   // plane below, rows a and b
+        Vec4<TI>::load(ep, at_(jb, km), zb);
+        Vec4<TI>::load(ep, at_(ja, kp), wa);   // plane above
+        Vec4<TI>::load(ep, at_(jb, kp), wb);
+        Vec4<TI>::load(rp, at_(ja, k), ra);
+        Vec4<TI>::load(rp, at_(jb, k), rb);
+        const uint2 fa = __ldg(reinterpret_cast<const uint2*>(nbf + at_(ja, k)));
+        const uint2 fb = __ldg(reinterpret_cast<const uint2*>(nbf + at_(jb, k)));
+        const C la = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * ja + sz * k)) : (C)0;
+        const C lb = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * jb + sz * k)) : (C)0;
+        const C qa = lane == TX - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * ja + sz * k)) : (C)0;
+        const C qb = lane == TX - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * jb + sz * k)) : (C)0;
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
+            const C* ec = row ? eb : ea;
+            const C* rr = row ? rb : ra;
+            const C* yl = row ? ea : ym;   // row below
+            const C* yh = row ? yp : eb;   // row above
+            const C* zl = row ? zb : za;
+            const C* zh = row ? wb : wa;
+            const uint2 fw = row ? fb : fa;
+            C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
+            C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+            if (lane == 0) left = row ? lb : la;
+            if (lane == TX - 1) right = row ? qb : qa;
+            if (last) right = ec[3];
+            const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
+            const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (is_solid(fs[t])) continue;
+                const C eP = xs[t + 1];
+                C A;
+                if (!((fs[t] >> 13) & 1u)) {
+                    C sa = (xs[t] + xs[t + 2]) * ihx;
+                    sa = fma(yl[t] + yh[t], ihy, sa);
+                    sa = fma(zl[t] + zh[t], ihz, sa);
+                    A = fma(dg, eP, -sa);
+                } else {
+                    A = A7_general<C>(Lf, fs[t], eP, xs[t], xs[t + 2], yl[t], yh[t], zl[t], zh[t]);
+                }
+                if (t < 2) s0 += rr[t] - A;
+                else s1 += rr[t] - A;
+            }
+        }
+    }
+    if (in) {
+        const C inv = (C)1 / (C)(4 * fz);
+        const int I0 = ic >> 1;
+        TI* const out = rc + I0 + NX * (Jc + NY * K);
+        out[0] = from_c<TI, C>(s0 * inv);
+        out[1] = from_c<TI, C>(s1 * inv);
+    }
+}
+
 // coarse r = mean of the children's (r - A e): one thread per fine cell (the
 // z pair of children in the thread), x / y pairs summed through shared memory.
 // Needs x and y active (2 x 2 children in the plane).
@@ -1037,9 +1230,24 @@ cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, co
     return err;
 }
 
+template <class TI>
+static bool v4_transfer_ok(const LevelDev& Lf) {
+    return sizeof(TI) < 8 && Lf.active[0] && Lf.active[1] && Lf.n[0] % 4 == 0 && Lf.n[1] % 2 == 0 &&
+           (Lf.N >= (1 << 20) || g_rec);
+}
+
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
                                   void* rc, const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
+    if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
+        const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lc.n[1] + TY - 1) / TY), (unsigned)Lc.n[2]);
+        if (inner == FVM_FP32)
+            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, st}, grid,
+                            dim3(TX, TY), 0, s);
+        return launch_k(RRV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)e, (const __nv_bfloat16*)r,
+                                             (__nv_bfloat16*)rc, st},
+                        grid, dim3(TX, TY), 0, s);
+    }
     if (Lf.active[0] && Lf.active[1]) {
         const int fz = Lf.active[2] ? 2 : 1;
         DISPATCH_I(inner, err = launch_k(RRWalkK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st},
@@ -1054,6 +1262,16 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
+    if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
+        const int tiles = ((Lf.n[0] + V4X - 1) / V4X) * ((Lf.n[1] + TY - 1) / TY);
+        const int zc = sweep_planes(tiles, Lf.n[2]);
+        const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lf.n[1] + TY - 1) / TY),
+                        (unsigned)((Lf.n[2] + zc - 1) / zc));
+        if (inner == FVM_FP32)
+            return launch_k(ProlongV4K<float>{Lf, Lc, (const float*)ec, (float*)e, st, zc}, grid, dim3(TX, TY), 0, s);
+        return launch_k(ProlongV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc}, grid,
+                        dim3(TX, TY), 0, s);
+    }
     DISPATCH_I(inner, err = launch_k(ProlongK<TI>{Lf, Lc, (const TI*)ec, (TI*)e, st}, grid3(Lf), kBlock3, 0, s));
     return err;
 }
