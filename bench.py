@@ -186,6 +186,13 @@ def run_batched(args, rank, ws, local, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prec = PREC[args.precision]
     specs = cases.batched_channels(args.cases, seed=rank, precision=prec, mg_levels=5)
+    tuning = None
+    if not args.no_autotune:
+        # sweep counts, V-cycles per outer residual and planes per block, measured on the largest case
+        _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
+        specs = [sp.replace(pre_sweeps=tuning["pre_sweeps"], post_sweeps=tuning["post_sweeps"],
+                            inner_cycles=tuning["inner_cycles"], sweep_planes=tuning["sweep_planes"])
+                 for sp in specs]
     N = sum(sp.cells for sp in specs)
     cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
     batch = binding.Batch(cs, stream=stream.cuda_stream)
@@ -261,7 +268,8 @@ def run_batched(args, rank, ws, local, dist):
         per_case = one_by_one(cs, 2)
         for c in cs:
             c.close()
-        c64 = [binding.Case(sp.replace(precision=cases.FP64), stream=stream.cuda_stream) for sp in specs]
+        plain = dict(precision=cases.FP64, pre_sweeps=3, post_sweeps=3, inner_cycles=0, sweep_planes=0)
+        c64 = [binding.Case(sp.replace(**plain), stream=stream.cuda_stream) for sp in specs]
         per_case_fp64 = one_by_one(c64, 1)
         for c in c64:
             c.close()
@@ -274,7 +282,7 @@ def run_batched(args, rank, ws, local, dist):
         got = [c.read() for c in b_cs]
         errs, rel64 = [], []
         for sp, g in zip(sub, got):
-            with binding.Case(sp.replace(precision=cases.FP64), stream=stream.cuda_stream) as c:
+            with binding.Case(sp.replace(**plain), stream=stream.cuda_stream) as c:
                 s64 = c.step(steps_acc, allow_not_converged=True)
                 errs.append(field_errors(g, c.read()))
                 rel64.append(s64["rel_residual"])
@@ -296,8 +304,9 @@ def run_batched(args, rank, ws, local, dist):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
                 "data": "synthetic",
-                "config": {"workload": f"batched_channels {len(specs)} cases, 64^3 .. 192x96x96, 5-level V(3,3), "
+                "config": {"workload": f"batched_channels {len(specs)} cases, 64^3 .. 192x96x96, 5-level V-cycles, "
                                        "rel tol 1e-8, one batch per GPU",
+                           "autotune": tuning,
                            "cells_per_gpu": N, "cases_per_gpu": len(specs), "sizes": [list(x) for x in sizes],
                            "precision": args.precision, "parallelism": f"replicas x{ws}",
                            "l2": "256 MB buffer written between timed steps (the batch's state is larger than L2)"},
@@ -401,6 +410,7 @@ def main():
     ap.add_argument("--cases", type=int, default=64, help="batched workload: cases per GPU")
     ap.add_argument("--accuracy-cases", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
     ap.add_argument("--requests", type=int, default=64, help="served workload: requests per GPU")
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
@@ -427,6 +437,15 @@ def main():
         return
     spec, label = workload(args.workload, PREC[args.precision])
     rank, ws, local, dist = dist_setup()
+    tuning = None
+    if args.impl == "ours" and not args.no_autotune and spec.nz > 1:
+        # smoother sweeps, V-cycles per outer residual and planes per block, measured (fvm_autotune)
+        from paper_2603_21869_gb300 import binding as _b, build as _bd
+        _bd.ensure_built()
+        import torch
+        torch.cuda.set_device(local)
+        spec, tuning = _b.autotune(spec, steps=3)
+        label = label.replace("V(3,3)", f"V({spec.pre_sweeps},{spec.post_sweeps})")
     if args.impl == "reference":
         args.steps = min(args.steps, 2)
         args.warmup = min(args.warmup, 0)
@@ -526,7 +545,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": label, "cells_per_gpu": N, "precision": args.precision,
-                           "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps"},
+                           "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps",
+                           "autotune": tuning},
                 "vcycles_per_step": statistics.mean(vc), "rel_residual_max": max(rels),
                 "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,

@@ -113,6 +113,9 @@ typedef struct {
     int32_t fixed_vcycles;           /* > 0: exactly this many per solve, no test */
     int32_t inner_cycles;            /* V-cycles per FP64 outer residual (0: 1 for FP64, 2 otherwise);
                                         the stopping test runs after each group */
+    int32_t sweep_planes;            /* z planes per block of the four-cell level kernels, 1..64
+                                        (0: the built-in rule, about eight blocks per SM) */
+    int32_t reserved_tune;           /* 0 */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
@@ -260,6 +263,28 @@ fvm_status fvm_step_batch(fvm_case* const* cases, int n, int nsteps, fvm_step_st
 
 fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
 
+/* ---------------------------------------------------------------- autotuning
+   Picks the multigrid parameters for a case by measurement (no counterpart
+   in the paper, whose solver runs a fixed scheme): on temporary copies of
+   the case (own stream; the descriptor is not changed), graph-mode steps
+   after two untimed ones, timed with CUDA events, `steps` steps each.
+   Pass 1: V(nu, nu) for nu = 2, 3, 4 times the V-cycles per FP64 outer
+   residual (1..4 with reduced-precision corrections, 1 in FP64); pass 2: the
+   z planes per block of the four-cell level kernels (the rule, 1 .. 32)
+   with the best pass-1 choice.  Candidates that stop at max_vcycles above
+   the tolerance are not eligible.  Copy the result into the descriptor's
+   pre_sweeps, post_sweeps, inner_cycles and sweep_planes.  Device memory: one
+   temporary case at a time.  Errors: FVM_ERR_INVALID, FVM_ERR_NOT_CONVERGED
+   (no candidate converged), FVM_ERR_CUDA. */
+typedef struct {
+    int32_t pre_sweeps, post_sweeps, inner_cycles, sweep_planes;
+    double  ms_per_step;             /* of the choice, device time per step */
+    int32_t candidates;              /* candidates timed */
+    int32_t reserved;
+} fvm_tuning;
+
+fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm_tuning* out);
+
 /* ---------------------------------------------------------------- serving
    A request loop over resident cases (continuous batching).  A request is a
    case description plus a number of steps.  fvm_server_poll runs one
@@ -361,11 +386,11 @@ fvm_status fvm_poisson_residual_static(const double* p, const double* b, int32_t
                                        const double h[3], const int32_t dirichlet[6], double* r,
                                        double* norms, void* stream);
 
-/* sizeof of the public structs, for binding checks: out[0..9] = fvm_patch,
+/* sizeof of the public structs, for binding checks: out[0..10] = fvm_patch,
    fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
-   fvm_kernel_stat, fvm_batch_info, fvm_request_result, fvm_server_info.
-   Needs no GPU. */
-void fvm_struct_sizes(size_t out[10]);
+   fvm_kernel_stat, fvm_batch_info, fvm_request_result, fvm_server_info,
+   fvm_tuning.  Needs no GPU. */
+void fvm_struct_sizes(size_t out[11]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* fvm_last_error(void);

@@ -60,6 +60,7 @@ class CaseDesc(ct.Structure):
                 ("boxes", ct.POINTER(Box)), ("n_boxes", ct.c_int32), ("reserved1", ct.c_int32),
                 ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
                 ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("inner_cycles", ct.c_int32),
+                ("sweep_planes", ct.c_int32), ("reserved_tune", ct.c_int32),
                 ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
                 ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
                 ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
@@ -93,6 +94,12 @@ class ServerInfo(ct.Structure):
                 ("rounds", ct.c_int64), ("batch_rebuilds", ct.c_int64), ("cell_steps", ct.c_int64)]
 
 
+class Tuning(ct.Structure):
+    _fields_ = [("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32), ("inner_cycles", ct.c_int32),
+                ("sweep_planes", ct.c_int32), ("ms_per_step", ct.c_double), ("candidates", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
 class BatchInfo(ct.Structure):
     _fields_ = [("n_cases", ct.c_int32), ("graphs", ct.c_int32), ("steps", ct.c_int64),
                 ("kernel_launches", ct.c_int64), ("cells", ct.c_int64), ("launches_per_step", ct.c_int64),
@@ -105,7 +112,7 @@ EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", 
            "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
            "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy", "fvm_batch_profile", "fvm_server_create",
            "fvm_server_now", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields",
-           "fvm_server_release", "fvm_server_destroy"]
+           "fvm_server_release", "fvm_server_destroy", "fvm_autotune"]
 
 _lib = None
 
@@ -144,6 +151,7 @@ def lib():
     L.fvm_batch_step.argtypes = [CP, ct.c_int32, ct.POINTER(StepStats)]
     L.fvm_batch_get_info.argtypes = [CP, ct.POINTER(BatchInfo)]
     L.fvm_batch_profile.argtypes = [CP, ct.c_int32, ct.POINTER(KernelStat), ct.c_int32, ct.POINTER(ct.c_int32)]
+    L.fvm_autotune.argtypes = [ct.POINTER(CaseDesc), ct.c_int32, ct.POINTER(Tuning)]
     L.fvm_server_create.argtypes = [ct.c_int64, ct.c_int32, CP, ct.c_int32, ct.POINTER(CP)]
     L.fvm_server_now.argtypes = [CP]
     L.fvm_server_now.restype = ct.c_double
@@ -164,7 +172,7 @@ def lib():
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
                  "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_profile",
                  "fvm_server_create", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info",
-                 "fvm_server_read_fields", "fvm_server_release"]:
+                 "fvm_server_read_fields", "fvm_server_release", "fvm_autotune"]:
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -211,6 +219,7 @@ class _Desc:
         d.n_boxes = len(spec.boxes)
         d.mg_levels, d.pre_sweeps, d.post_sweeps = spec.mg_levels, spec.pre_sweeps, spec.post_sweeps
         d.max_vcycles, d.fixed_vcycles, d.inner_cycles = spec.max_vcycles, spec.fixed_vcycles, spec.inner_cycles
+        d.sweep_planes = spec.sweep_planes
         d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
         d.seed = spec.seed & ((1 << 64) - 1)
         d.init_perturb = spec.init_perturb
@@ -227,7 +236,7 @@ def case_bytes(spec: cases.CaseSpec) -> int:
 
 
 def struct_sizes():
-    out = (ct.c_size_t * 10)()
+    out = (ct.c_size_t * 11)()
     lib().fvm_struct_sizes(out)
     return list(out)
 
@@ -332,6 +341,17 @@ class Case:
         inf = CaseInfo()
         _check(lib().fvm_case_get_info(self._h, ct.byref(inf)))
         return {k: getattr(inf, k) for k, _ in CaseInfo._fields_}
+
+
+def autotune(spec: cases.CaseSpec, steps=5):
+    """Measured choice of V(nu, nu), V-cycles per outer residual and planes per
+    block (fvm_autotune).  Returns (tuned spec, details)."""
+    d = _Desc(spec)
+    t = Tuning()
+    _check(lib().fvm_autotune(ct.byref(d.desc), int(steps), ct.byref(t)))
+    info = {k: getattr(t, k) for k, _ in Tuning._fields_}
+    return spec.replace(pre_sweeps=t.pre_sweeps, post_sweeps=t.post_sweeps, inner_cycles=t.inner_cycles,
+                        sweep_planes=t.sweep_planes), info
 
 
 def _stats(s: StepStats, status=OK):

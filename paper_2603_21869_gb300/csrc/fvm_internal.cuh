@@ -87,6 +87,7 @@ struct LevelDev {
     float inv_h2f[3], inv_Df, wJf, diagf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
     double ih2a[3];          // inv_h2 on active axes, 0 on a collapsed axis
     float ih2af[3];
+    int32_t zc_fixed;        // z planes per block of the four-cell kernels (0: the rule)
     const uint8_t* solid;    // nonzero = solid
     const uint8_t* dir[6];   // per boundary-face cell: 1 = Dirichlet (p = 0 on the face)
     const uint16_t* nbf;     // per cell: 2 bits per face (x-,x+,y-,y+,z-,z+): 0 fluid neighbour,

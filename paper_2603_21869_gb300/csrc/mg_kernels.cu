@@ -1191,7 +1191,8 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
 
 // planes per block: the most that still give about eight blocks per SM (one plane per
 // block on grids too small for that)
-static int sweep_planes(int tiles, int nz) {
+static int sweep_planes(int tiles, int nz, int fixed) {
+    if (fixed > 0) return fixed < nz ? fixed : nz;
     for (int zc : {32, 16, 8, 4, 2})
         if (tiles * ((nz + zc - 1) / zc) >= 8 * 152) return zc;
     return 1;
@@ -1204,7 +1205,7 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
         // four cells per thread on large levels and in batches (their blocks add up over the cases)
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
             const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
-        const int zc = sweep_planes(tiles, L.n[2]);
+        const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
         const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
                         (unsigned)((L.n[2] + zc - 1) / zc));
         return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc}, grid, dim3(TX, TY), 0, s);
@@ -1264,7 +1265,7 @@ cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
         const int tiles = ((Lf.n[0] + V4X - 1) / V4X) * ((Lf.n[1] + TY - 1) / TY);
-        const int zc = sweep_planes(tiles, Lf.n[2]);
+        const int zc = sweep_planes(tiles, Lf.n[2], Lf.zc_fixed);
         const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lf.n[1] + TY - 1) / TY),
                         (unsigned)((Lf.n[2] + zc - 1) / zc));
         if (inner == FVM_FP32)

@@ -376,6 +376,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->pre_sweeps < 1 || d->post_sweeps < 1 || d->pre_sweeps > 64 || d->post_sweeps > 64)
         return fail(FVM_ERR_INVALID, "pre_sweeps and post_sweeps must be 1..64");
     if (d->inner_cycles < 0 || d->inner_cycles > 16) return fail(FVM_ERR_INVALID, "inner_cycles must be 0..16");
+    if (d->sweep_planes < 0 || d->sweep_planes > 64) return fail(FVM_ERR_INVALID, "sweep_planes must be 0..64");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -1085,6 +1086,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         v.inv_Df = (float)v.inv_D;
         v.wJf = (float)v.wJ;
         v.diagf = (float)v.diag;
+        v.zc_fixed = d.sweep_planes;
         if (l == 0) v.solid = tag_d;
         else {
             uint8_t* sd;
@@ -2198,7 +2200,7 @@ fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_o
     return FVM_OK;
 }
 
-void fvm_struct_sizes(size_t out[10]) {
+void fvm_struct_sizes(size_t out[11]) {
     out[0] = sizeof(fvm_patch);
     out[1] = sizeof(fvm_vent);
     out[2] = sizeof(fvm_box);
@@ -2209,6 +2211,7 @@ void fvm_struct_sizes(size_t out[10]) {
     out[7] = sizeof(fvm_batch_info);
     out[8] = sizeof(fvm_request_result);
     out[9] = sizeof(fvm_server_info);
+    out[10] = sizeof(fvm_tuning);
 }
 
 const char* fvm_last_error(void) { return g_err.c_str(); }

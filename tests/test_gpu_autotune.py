@@ -1,0 +1,47 @@
+"""The autotuner (fvm_autotune) and the parameters it sets."""
+import numpy as np
+import pytest
+
+from oracle.step import OracleCase
+from paper_2603_21869_gb300 import binding, build, cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.ensure_built()
+    binding.lib()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
+    spec = cases.heated_channel_3d(128, 32, 32, mg_levels=4, precision=cases.FP32, mg_rel_tol=1e-8,
+                                   max_vcycles=40)
+    tuned, info = binding.autotune(spec, steps=3)
+    assert info["candidates"] == 3 * 4 + 6 and info["ms_per_step"] > 0
+    assert info["pre_sweeps"] == info["post_sweeps"] in (2, 3, 4)
+    assert 1 <= info["inner_cycles"] <= 4 and info["sweep_planes"] in (0, 1, 2, 4, 8, 16, 32)
+    with binding.Case(tuned) as c:
+        st = c.step(4)
+        got = c.read()
+    assert st["rel_residual"] <= 1e-8
+    o = OracleCase(spec.replace(precision=cases.FP64)).step(4)
+    for f in ("u", "v", "w", "T", "k", "omega"):
+        assert rel(got[f], o.fields()[f]) <= 1e-4, f
+
+
+def test_planes_per_block_do_not_change_the_result():
+    """The planes per block only partition the same cell updates among blocks."""
+    base = cases.heated_channel_3d(256, 32, 32, mg_levels=4, precision=cases.FP32, fixed_vcycles=3)
+    res = []
+    for planes in (0, 1, 16):
+        with binding.Case(base.replace(sweep_planes=planes)) as c:
+            c.step(2)
+            res.append(c.read())
+    for other in res[1:]:
+        for f in cases.FIELDS:
+            assert np.array_equal(res[0][f], other[f]), f

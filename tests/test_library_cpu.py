@@ -32,7 +32,7 @@ def test_struct_layout_matches_binding(lib):
     sizes = binding.struct_sizes()
     ours = [ct.sizeof(t) for t in (binding.Patch, binding.Vent, binding.Box, binding.CaseDesc,
                                    binding.StepStats, binding.CaseInfo, binding.KernelStat, binding.BatchInfo,
-                                   binding.RequestResult, binding.ServerInfo)]
+                                   binding.RequestResult, binding.ServerInfo, binding.Tuning)]
     assert sizes == ours
 
 
@@ -45,6 +45,16 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert "null case" in binding.last_error()
     assert not h.value
     assert lib.fvm_batch_step(None, 1, None) == binding.ERR_INVALID
+
+
+def test_autotune_rejects_bad_arguments_without_a_gpu(lib):
+    import ctypes as ct
+    t = binding.Tuning()
+    assert lib.fvm_autotune(None, 3, ct.byref(t)) == binding.ERR_INVALID
+    d = binding._Desc(cases.heated_channel_3d(32, 16, 16, mg_levels=3))
+    assert lib.fvm_autotune(ct.byref(d.desc), 0, ct.byref(t)) == binding.ERR_INVALID
+    bad = binding._Desc(cases.heated_channel_3d(30, 16, 16, mg_levels=3))   # 30 does not halve twice
+    assert lib.fvm_autotune(ct.byref(bad.desc), 3, ct.byref(t)) == binding.ERR_INVALID
 
 
 def test_server_rejects_bad_arguments_without_a_gpu(lib):
