@@ -11,6 +11,9 @@
              (Eq. prolongation)
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
              correct, post-smooth; exact dense solve on the coarsest level
+  Algorithm 1 (mg_variant 1): the fine residual restricted straight down,
+             one unweighted Jacobi per coarse level on the way up, nearest
+             upsampling, a final unweighted Jacobi sweep on p
   projection u = u* - dt G p, G the cell-centred gradient L * D * BC(p)
 
 Solid cells hold zero pressure and are excluded from every norm.
@@ -128,6 +131,16 @@ def prolong(coarse, fine_shape):
     return e
 
 
+def prolong_nearest(coarse, fine_shape):
+    """PROL of the paper's scheme (Algorithm 1, an upsampling layer): every fine
+    cell takes its parent's value."""
+    e = coarse
+    for axis in range(3):
+        if fine_shape[axis] != e.shape[axis]:
+            e = np.repeat(e, 2, axis=axis)
+    return e
+
+
 def dense_operator(lev):
     """The matrix of A on a level, built column by column from unit vectors.
     Rows and columns of solid cells are the identity."""
@@ -175,6 +188,35 @@ class Multigrid:
         p = smooth(lev, p, b, self.spec.post_sweeps, wJ)
         return p
 
+    def paper_cycle(self, p, b):
+        """One iteration of Algorithm 1, in this module's sign convention
+        (r = b - A p, so the correction is added; the paper writes
+        r0 = A p - b and subtracts it).  The fine residual is restricted
+        straight down through every level.  On the way up, each coarse level
+        gets one unweighted Jacobi iteration on the correction, starting from
+        the upsampled coarser correction (zero on the coarsest level), then
+        upsampling (nearest).  The upsampled level-1 correction is added to p,
+        and one unweighted Jacobi sweep on p ends the iteration.  The residual
+        is recomputed each iteration."""
+        levs = self.levels
+        r = [residual(levs[0], p, b)]
+        for l in range(1, len(levs)):
+            r.append(restrict(levs[l - 1], r[l - 1]))
+        w = np.zeros(levs[-1].shape)
+        for l in range(len(levs) - 1, 0, -1):
+            lev = levs[l]
+            w = np.where(lev.fluid, w + residual(lev, w, r[l]) / lev.diag(), 0.0)
+            w = prolong_nearest(w, levs[l - 1].shape)
+        lev0 = levs[0]
+        p = np.where(lev0.fluid, p + w, 0.0)
+        return np.where(lev0.fluid, p + residual(lev0, p, b) / lev0.diag(), 0.0)
+
+    def cycle(self, p, b):
+        """One iteration of the configured scheme (mg_variant 0: V-cycle, 1: Algorithm 1)."""
+        if getattr(self.spec, "mg_variant", 0) == 1:
+            return self.paper_cycle(p, b)
+        return self.vcycle(p, b)
+
     def rel_residual(self, p, b):
         lev = self.levels[0]
         nb = np.linalg.norm(b[lev.fluid])
@@ -189,12 +231,12 @@ class Multigrid:
         s = self.spec
         if s.fixed_vcycles > 0:
             for _ in range(s.fixed_vcycles):
-                p = self.vcycle(p, b)
+                p = self.cycle(p, b)
             return p, s.fixed_vcycles, self.rel_residual(p, b)
         n = 0
         rel = self.rel_residual(p, b)
         while rel > s.mg_rel_tol and n < s.max_vcycles:
-            p = self.vcycle(p, b)
+            p = self.cycle(p, b)
             n += 1
             rel = self.rel_residual(p, b)
         return p, n, rel

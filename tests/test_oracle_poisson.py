@@ -205,3 +205,39 @@ def test_rhs_zero_for_uniform_through_flow():
     c = OracleCase(spec)
     c.rhs()
     assert np.max(np.abs(c.b)) == 0.0
+
+
+# ------------------------------------------------------------------ the paper's scheme (Algorithm 1)
+def test_nearest_upsampling_is_a_kronecker_product_with_ones():
+    from oracle.poisson import prolong_nearest
+    rng = np.random.default_rng(3)
+    c3 = rng.normal(size=(3, 2, 4))
+    assert np.array_equal(prolong_nearest(c3, (6, 4, 8)), np.kron(c3, np.ones((2, 2, 2))))
+    c2 = rng.normal(size=(5, 3, 1))
+    assert np.array_equal(prolong_nearest(c2, (10, 6, 1)), np.kron(c2, np.ones((2, 2, 1))))
+
+
+def test_paper_scheme_keeps_the_exact_solution_and_reduces_the_residual():
+    """The discrete solution of A p = b is a fixed point of an Algorithm-1
+    iteration (every correction it forms is zero there), and from zero the
+    iteration lowers the residual every step on this case, more slowly than
+    a V(3,3) cycle."""
+    from paper_2603_21869_gb300 import cases
+    from oracle.step import OracleCase
+    from oracle.poisson import direct_solve
+    spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3)
+    mg = OracleCase(spec).mg
+    lev = mg.levels[0]
+    rng = np.random.default_rng(1)
+    b = np.where(lev.fluid, rng.normal(size=lev.shape), 0.0)
+    pstar = direct_solve(lev, b)
+    assert np.max(np.abs(mg.paper_cycle(pstar, b) - pstar)) <= 1e-13 * np.max(np.abs(pstar))
+    p = np.zeros(lev.shape)
+    q = np.zeros(lev.shape)
+    rel = [1.0]
+    for _ in range(6):
+        p = mg.paper_cycle(p, b)
+        q = mg.vcycle(q, b)
+        rel.append(mg.rel_residual(p, b))
+    assert all(a > c for a, c in zip(rel, rel[1:]))
+    assert mg.rel_residual(q, b) < rel[-1]
