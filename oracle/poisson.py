@@ -12,12 +12,15 @@
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
              correct, post-smooth; exact dense solve on the coarsest level
   Algorithm 1 (mg_variant 1): the fine residual restricted straight down,
-             one unweighted Jacobi per coarse level on the way up, nearest
-             upsampling, a final unweighted Jacobi sweep on p
+             one unweighted Jacobi per coarse level on the way up (A and D
+             with the fine spacing), nearest upsampling, a final unweighted
+             Jacobi sweep on p
   projection u = u* - dt G p, G the cell-centred gradient L * D * BC(p)
 
 Solid cells hold zero pressure and are excluded from every norm.
 """
+import copy
+
 import numpy as np
 
 from .geometry import U, V, W, FK_SOLID, D_op, L_op, pressure_face_states
@@ -197,14 +200,17 @@ class Multigrid:
         the upsampled coarser correction (zero on the coarsest level), then
         upsampling (nearest).  The upsampled level-1 correction is added to p,
         and one unweighted Jacobi sweep on p ends the iteration.  The residual
-        is recomputed each iteration."""
+        is recomputed each iteration.  A and D keep the fine grid's spacing on
+        every level (the paper applies one convolution kernel and one scalar
+        D = 6/dx^2 at all levels)."""
         levs = self.levels
         r = [residual(levs[0], p, b)]
         for l in range(1, len(levs)):
             r.append(restrict(levs[l - 1], r[l - 1]))
         w = np.zeros(levs[-1].shape)
         for l in range(len(levs) - 1, 0, -1):
-            lev = levs[l]
+            lev = copy.copy(levs[l])
+            lev.h = levs[0].h
             w = np.where(lev.fluid, w + residual(lev, w, r[l]) / lev.diag(), 0.0)
             w = prolong_nearest(w, levs[l - 1].shape)
         lev0 = levs[0]

@@ -241,3 +241,22 @@ def test_paper_scheme_keeps_the_exact_solution_and_reduces_the_residual():
         rel.append(mg.rel_residual(p, b))
     assert all(a > c for a, c in zip(rel, rel[1:]))
     assert mg.rel_residual(q, b) < rel[-1]
+
+
+def test_paper_scheme_converges_at_any_depth():
+    """With the fine grid's A and D on every level (one shared kernel), the
+    scheme's contraction does not degrade with the number of levels (with
+    coarse operators rescaled to each level's spacing it diverges from four
+    levels on: each level's single Jacobi step then overshoots)."""
+    from paper_2603_21869_gb300 import cases
+    from oracle.step import OracleCase
+    rates = []
+    for nx, ny, nz, L in ((32, 16, 16, 3), (128, 32, 32, 5)):
+        mg = OracleCase(cases.heated_channel_3d(nx, ny, nz, mg_levels=L)).mg
+        lev = mg.levels[0]
+        b = np.where(lev.fluid, np.random.default_rng(1).normal(size=lev.shape), 0.0)
+        p = np.zeros(lev.shape)
+        for _ in range(10):
+            p = mg.paper_cycle(p, b)
+        rates.append(mg.rel_residual(p, b))
+    assert rates[1] < 0.1 and rates[1] < 1.5 * rates[0]
