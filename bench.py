@@ -381,6 +381,37 @@ def run_served(args, rank, ws, local, dist):
         dist.destroy_process_group()
 
 
+def compare_variants(args):
+    """The paper's multigrid scheme (Algorithm 1) against V(3,3) cycles on the
+    default channel: device time per iteration (CUDA events) and residual
+    contraction per iteration, in FP32 and FP64, from the same state."""
+    import torch
+    from paper_2603_21869_gb300 import binding, build
+    build.ensure_built()
+    out = {}
+    for pname, prec in (("f32", cases.FP32), ("f64", cases.FP64)):
+        for vname, variant in (("vcycle_V33", 0), ("paper_algorithm1", 1)):
+            spec = cases.heated_channel_3d(256, 64, 64, mg_levels=6, precision=prec, fixed_vcycles=1,
+                                           mg_variant=variant)
+            with binding.Case(spec) as c:
+                c.step(3)
+                rels, ms = [], []
+                for _ in range(20):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    rels.append(c.vcycle(1))
+                    b.record()
+                    b.synchronize()
+                    ms.append(a.elapsed_time(b))
+            out[f"{pname}/{vname}"] = {"ms_per_iteration": statistics.median(ms[2:]),
+                                       "factor_per_iteration": (rels[-1] / rels[9]) ** (1 / 10),
+                                       "rel_after_1_10_20": [rels[0], rels[9], rels[19]]}
+    print(json.dumps({"comparison": "multigrid schemes on heated_channel_3d 256x64x64 (6 levels)",
+                      "note": "one iteration per fvm_vcycle call (with its residual and a host read)",
+                      "results": out}), flush=True)
+
+
 def cpu_baseline(spec, budget_s=25.0):
     """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload."""
     from oracle.step import OracleCase
@@ -416,7 +447,12 @@ def main():
     ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--chunk", type=int, default=10, help="served workload: steps per scheduling round")
+    ap.add_argument("--compare-variants", action="store_true",
+                    help="time the paper's multigrid scheme against V-cycles and exit")
     args = ap.parse_args()
+    if args.compare_variants:
+        compare_variants(args)
+        return
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     if args.workload == "served" and args.impl == "ours":

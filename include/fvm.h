@@ -115,7 +115,9 @@ typedef struct {
                                         the stopping test runs after each group */
     int32_t sweep_planes;            /* z planes per block of the four-cell level kernels, 1..64
                                         (0: the built-in rule, about eight blocks per SM) */
-    int32_t reserved_tune;           /* 0 */
+    int32_t mg_variant;              /* 0: V(pre, post) cycles; 1: the paper's scheme (Algorithm 1:
+                                        residual restricted straight down, one unweighted Jacobi per
+                                        coarse level, nearest upsampling, a final Jacobi on p) */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */

@@ -60,7 +60,7 @@ class CaseDesc(ct.Structure):
                 ("boxes", ct.POINTER(Box)), ("n_boxes", ct.c_int32), ("reserved1", ct.c_int32),
                 ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
                 ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("inner_cycles", ct.c_int32),
-                ("sweep_planes", ct.c_int32), ("reserved_tune", ct.c_int32),
+                ("sweep_planes", ct.c_int32), ("mg_variant", ct.c_int32),
                 ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
                 ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
                 ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
@@ -220,6 +220,7 @@ class _Desc:
         d.mg_levels, d.pre_sweeps, d.post_sweeps = spec.mg_levels, spec.pre_sweeps, spec.post_sweeps
         d.max_vcycles, d.fixed_vcycles, d.inner_cycles = spec.max_vcycles, spec.fixed_vcycles, spec.inner_cycles
         d.sweep_planes = spec.sweep_planes
+        d.mg_variant = spec.mg_variant
         d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
         d.seed = spec.seed & ((1 << 64) - 1)
         d.init_perturb = spec.init_perturb

@@ -235,6 +235,15 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s);
 cudaError_t prepare_coarse_cta(int inner, size_t smem);
+// the paper's scheme (Algorithm 1)
+cudaError_t launch_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* r, void* rc,
+                            const SolveState* st, cudaStream_t s);
+cudaError_t launch_prolong_nearest(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
+                                   const SolveState* st, cudaStream_t s);
+cudaError_t launch_prolong_nearest_to_p(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, double* p,
+                                        const SolveState* st, cudaStream_t s);
+cudaError_t launch_jacobi_p(int bprec, const LevelDev& L, double* p, const void* b, double* q, const SolveState* st,
+                            cudaStream_t s);
 // persistent tail of the V-cycle (levels ls.. of one case); the correction of level ls ends in
 // e[ls][tail_out_index(pre, post)]
 int tail_blocks(int inner, size_t smem);

@@ -967,6 +967,112 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     }
 }
 
+// ------------------------------------------------------------------ the paper's scheme (Algorithm 1)
+// coarse r = mean of the children's r (the residual restricted straight down)
+template <class TI>
+struct RestrictK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev Lf, Lc;
+    const TI* r;
+    TI* rc;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        using C = typename Acc<TI>::type;
+        int I, J, K;
+        if (!cell3(Lc, at, I, J, K)) return;
+        const int fx = Lf.active[0] ? 2 : 1, fy = Lf.active[1] ? 2 : 1, fz = Lf.active[2] ? 2 : 1;
+        C sum = (C)0;
+        for (int dz = 0; dz < fz; ++dz)
+            for (int dy = 0; dy < fy; ++dy)
+                for (int dx = 0; dx < fx; ++dx)
+                    sum += to_c<C>(ldg(r + (I * fx + dx) + Lf.n[0] * ((J * fy + dy) + Lf.n[1] * (K * fz + dz))));
+        rc[I + Lc.n[0] * (J + Lc.n[1] * K)] = from_c<TI, C>(sum / (C)(fx * fy * fz));
+    }
+};
+
+__device__ __forceinline__ int parent_of(const LevelDev& Lf, const LevelDev& Lc, int i, int j, int k) {
+    const int I = Lf.active[0] ? i >> 1 : i, J = Lf.active[1] ? j >> 1 : j, K = Lf.active[2] ? k >> 1 : k;
+    return I + Lc.n[0] * (J + Lc.n[1] * K);
+}
+
+// e = the parent's correction (nearest upsampling), zero in solid cells
+template <class TI>
+struct ProlongNearestK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev Lf, Lc;
+    const TI* ec;
+    TI* e;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        int i, j, k;
+        if (!cell3(Lf, at, i, j, k)) return;
+        const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
+        e[c] = is_solid(Lf.nbf[c]) ? from_c<TI, float>(0.f) : ec[parent_of(Lf, Lc, i, j, k)];
+    }
+};
+
+// p += the parent's level-1 correction (nearest upsampling) in fluid cells
+template <class TI>
+struct ProlongNearestToPK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev Lf, Lc;
+    const TI* ec;
+    double* p;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        int i, j, k;
+        if (!cell3(Lf, at, i, j, k)) return;
+        const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
+        if (!is_solid(Lf.nbf[c])) p[c] += to_c<double>(ldg(ec + parent_of(Lf, Lc, i, j, k)));
+    }
+};
+
+// unweighted Jacobi sweep on the FP64 pressure, out of place: q = p + (b - A p) / D
+template <class TB>
+struct JacobiPK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev L;
+    const double* p;
+    const TB* b;
+    double* q;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        int i, j, k;
+        if (!cell3(L, at, i, j, k)) return;
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        const uint32_t f = L.nbf[c];
+        if (is_solid(f)) {
+            q[c] = 0.0;
+            return;
+        }
+        const int sy = L.n[0], sz = L.n[0] * L.n[1];
+        const double pP = __ldg(p + c);
+        const double xm = __ldg(p + c - (i > 0 ? 1 : 0)), xp = __ldg(p + c + (i < L.n[0] - 1 ? 1 : 0));
+        const double ym = __ldg(p + c - (j > 0 ? sy : 0)), yp = __ldg(p + c + (j < L.n[1] - 1 ? sy : 0));
+        const double zm = __ldg(p + c - (k > 0 ? sz : 0)), zp = __ldg(p + c + (k < L.n[2] - 1 ? sz : 0));
+        q[c] = pP + (to_c<double>(ldg(b + c)) - A7<double>(L, f, pP, xm, xp, ym, yp, zm, zp)) * L.inv_D;
+    }
+};
+
+struct CopyPK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev L;
+    const double* q;
+    double* p;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        int i, j, k;
+        if (!cell3(L, at, i, j, k)) return;
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        p[c] = q[c];
+    }
+};
+
 // ------------------------------------------------------------------ persistent tail of the V-cycle
 // Levels ls..lc-1 by every block (grid-stride loops over the level's cells,
 // a grid barrier between phases), the coarse levels lc.. by block 0 with the
@@ -1292,6 +1398,37 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
     DISPATCH_I(inner, err = launch_k(CoarseK<TI>{cl, (const TI*)r_in, (TI*)e_out, Ainv, st}, dim3(1),
                                      dim3(kCtaThreads), smem, s));
     return err;
+}
+
+cudaError_t launch_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* r, void* rc,
+                            const SolveState* st, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k(RestrictK<TI>{Lf, Lc, (const TI*)r, (TI*)rc, st}, grid3(Lc), kBlock3, 0, s));
+    return err;
+}
+
+cudaError_t launch_prolong_nearest(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
+                                   const SolveState* st, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = launch_k(ProlongNearestK<TI>{Lf, Lc, (const TI*)ec, (TI*)e, st}, grid3(Lf), kBlock3, 0, s));
+    return err;
+}
+
+cudaError_t launch_prolong_nearest_to_p(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, double* p,
+                                        const SolveState* st, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner,
+               err = launch_k(ProlongNearestToPK<TI>{Lf, Lc, (const TI*)ec, p, st}, grid3(Lf), kBlock3, 0, s));
+    return err;
+}
+
+cudaError_t launch_jacobi_p(int bprec, const LevelDev& L, double* p, const void* b, double* q, const SolveState* st,
+                            cudaStream_t s) {
+    cudaError_t err;
+    if (bprec == FVM_FP64) err = launch_k(JacobiPK<double>{L, p, (const double*)b, q, st}, grid3(L), kBlock3, 0, s);
+    else err = launch_k(JacobiPK<float>{L, p, (const float*)b, q, st}, grid3(L), kBlock3, 0, s);
+    if (err != cudaSuccess) return err;
+    return launch_k(CopyPK{L, q, p, st}, grid3(L), kBlock3, 0, s);
 }
 
 int tail_blocks(int inner, size_t smem) {

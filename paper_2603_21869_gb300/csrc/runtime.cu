@@ -299,6 +299,7 @@ struct fvm_case {
     double* h_dt = nullptr;
     double* staging = nullptr;
     double* Ainv = nullptr;
+    double* p_tmp = nullptr;         // the paper's scheme: Jacobi on p out of place
     std::vector<DevLevel> levels;
     SolveState* sst = nullptr;       // device
     SolveState* h_sst = nullptr;     // pinned host copy
@@ -377,6 +378,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
         return fail(FVM_ERR_INVALID, "pre_sweeps and post_sweeps must be 1..64");
     if (d->inner_cycles < 0 || d->inner_cycles > 16) return fail(FVM_ERR_INVALID, "inner_cycles must be 0..16");
     if (d->sweep_planes < 0 || d->sweep_planes > 64) return fail(FVM_ERR_INVALID, "sweep_planes must be 0..64");
+    if (d->mg_variant < 0 || d->mg_variant > 1) return fail(FVM_ERR_INVALID, "mg_variant must be 0 or 1");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -515,6 +517,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     }
     const int64_t nc = pl.levels.back().N();
     bytes += nc * nc * 8;
+    if (d->mg_variant == 1) bytes += N * 8;
     bytes += (int64_t)(2 * resid0_blocks(n[0], n[1], n[2]) + 16) * 8 + 256;
     pl.bytes = bytes;
     return FVM_OK;
@@ -621,10 +624,52 @@ void prof_clear(fvm_case* c) {
 std::string lvl_name(const char* base, size_t l) { return std::string(base) + "_L" + std::to_string(l); }
 
 // ------------------------------------------------------------------ solve
+// One iteration of the paper's scheme (Algorithm 1) after the level-0 residual:
+// restrict r straight down, one unweighted Jacobi step per coarse level on the
+// way up from the nearest-upsampled coarser correction (zero on the coarsest),
+// p += the upsampled level-1 correction, one unweighted Jacobi sweep on p.
+fvm_status paper_cycle(fvm_case* c) {
+    cudaStream_t s = c->stream;
+    const int nl = (int)c->levels.size();
+    const double si = (double)elem_size(c->inner);
+    for (int l = 0; l + 1 < nl; ++l) {
+        DevLevel& L = c->levels[l];
+        DevLevel& Lc = c->levels[l + 1];
+        KLAUNCH(lvl_name("restrict", l), (double)L.dev.N * si + (double)Lc.dev.N * si, 1,
+                launch_restrict(c->inner, L.dev, Lc.dev, L.r, Lc.r, c->sst, s));
+    }
+    DevLevel& Lt = c->levels[nl - 1];
+    KLAUNCH(lvl_name("sweep_first", nl - 1), 2.0 * Lt.dev.N * si + 2.0 * Lt.dev.N, 1,
+            launch_sweep_first(c->inner, Lt.dev, Lt.r, Lt.e[0], c->sst, s));
+    int cur = 0;   // buffer holding the correction of the level below the one being built
+    for (int l = nl - 2; l >= 1; --l) {
+        DevLevel& L = c->levels[l];
+        DevLevel& Lc = c->levels[l + 1];
+        const double N = (double)L.dev.N;
+        KLAUNCH(lvl_name("prolong_nearest", l), N * si + (double)Lc.dev.N * si + 2 * N, 1,
+                launch_prolong_nearest(c->inner, L.dev, Lc.dev, Lc.e[cur], L.e[0], c->sst, s));
+        KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
+                launch_sweep(c->inner, L.dev, L.e[0], L.r, L.e[1], c->sst, s));
+        cur = 1;
+    }
+    DevLevel& L0 = c->levels[0];
+    DevLevel& L1 = c->levels[1];
+    const double N0 = (double)L0.dev.N;
+    KLAUNCH("prolong_nearest_to_p_L0", 16 * N0 + (double)L1.dev.N * si + 2 * N0, 1,
+            launch_prolong_nearest_to_p(c->inner, L0.dev, L1.dev, L1.e[cur], c->p, c->sst, s));
+    KLAUNCH("jacobi_p_L0", N0 * (8 + elem_size(c->prec) + 8 + 2) + 16 * N0, 2,
+            launch_jacobi_p(c->prec, L0.dev, c->p, c->b, c->p_tmp, c->sst, s));
+    return FVM_OK;
+}
+
 // One V-cycle of the correction equation on levels l.. with r on level l;
 // returns the index of the e buffer holding the level's correction.  On
 // level 0 the final post-smoothing sweep adds the correction to p instead.
 fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
+    if (c->desc.mg_variant == 1) {
+        out_idx = 0;
+        return paper_cycle(c);
+    }
     DevLevel& L = c->levels[l];
     cudaStream_t s = c->stream;
     const double N = (double)L.dev.N;
@@ -959,7 +1004,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     c->desc.boxes = c->boxes.data();
     c->prec = pl.prec;
     c->inner = pl.inner;
-    c->inner_cycles = d.inner_cycles > 0 ? d.inner_cycles : (pl.inner == FVM_FP64 ? 1 : 2);
+    c->inner_cycles = d.mg_variant == 1 ? 1 : (d.inner_cycles > 0 ? d.inner_cycles : (pl.inner == FVM_FP64 ? 1 : 2));
     c->dt0 = pl.dt0;
     if (d.stream) c->stream = (cudaStream_t)d.stream;
     else {
@@ -1077,7 +1122,8 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         v.N = H.N();
         v.inv_D = 1.0 / diag;
         v.diag = diag;
-        v.wJ = d.jacobi_weight > 0.0 ? d.jacobi_weight : (nact == 3 ? 6.0 / 7.0 : 4.0 / 5.0);
+        v.wJ = d.mg_variant == 1 ? 1.0   // the paper's scheme: unweighted Jacobi
+                                 : (d.jacobi_weight > 0.0 ? d.jacobi_weight : (nact == 3 ? 6.0 / 7.0 : 4.0 / 5.0));
         for (int a = 0; a < 3; ++a) {
             v.inv_h2f[a] = (float)v.inv_h2[a];
             v.ih2a[a] = H.active[a] ? v.inv_h2[a] : 0.0;
@@ -1252,10 +1298,27 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             }
         }
     }
+    // the paper's scheme applies the fine grid's stencil and diagonal on every level
+    if (d.mg_variant == 1)
+        for (size_t l = 1; l < c->levels.size(); ++l) {
+            LevelDev& v = c->levels[l].dev;
+            const LevelDev& f0 = c->levels[0].dev;
+            for (int a = 0; a < 3; ++a) {
+                v.inv_h2[a] = f0.inv_h2[a];
+                v.inv_h2f[a] = f0.inv_h2f[a];
+                v.ih2a[a] = v.active[a] ? f0.inv_h2[a] : 0.0;
+                v.ih2af[a] = (float)v.ih2a[a];
+            }
+            v.diag = f0.diag;
+            v.diagf = f0.diagf;
+            v.inv_D = f0.inv_D;
+            v.inv_Df = f0.inv_Df;
+        }
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))
         return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
     ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 8));
+    if (d.mg_variant == 1) ST_TRY(dalloc(c, (void**)&c->p_tmp, (size_t)N * 8));
     CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
     c->nblocks0 = resid0_blocks(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));

@@ -300,6 +300,41 @@ def test_persistent_tail_kernel_matches_oracle(monkeypatch, name):
     assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name} with the tail kernel")
 
 
+@pytest.mark.parametrize("name", ["channel3d_box_vent", "room_buoyant", "channel2d_ragged"])
+def test_paper_multigrid_scheme_matches_oracle(name):
+    """mg_variant 1 (Algorithm 1: straight restriction, one unweighted Jacobi
+    per coarse level, nearest upsampling, a final Jacobi on p), a fixed
+    number of iterations per step: FP64 fields within 1e-10 of the oracle."""
+    spec = SPECS[name]().replace(mg_variant=1, fixed_vcycles=5)
+    with binding.Case(spec) as c:
+        c.step(2)
+        got = c.read()
+    o = OracleCase(spec).step(2)
+    assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name}, Algorithm 1")
+
+
+def test_paper_scheme_iterations_track_the_oracle_and_converge_slower():
+    spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3, fixed_vcycles=1)
+    o = OracleCase(spec)
+    lev = o.mg.levels[0]
+    b = np.where(lev.fluid, np.random.default_rng(7).normal(size=lev.shape), 0.0)
+    res = {}
+    for variant in (0, 1):
+        s = spec.replace(mg_variant=variant)
+        mg = OracleCase(s).mg
+        p = np.zeros(lev.shape)
+        with binding.Case(s) as c:
+            c.set_rhs(b)
+            c.write({"p": p})
+            rels = []
+            for _ in range(6):
+                rels.append(c.vcycle(1))
+                p = mg.cycle(p, b)
+            assert rel_err(c.read(("p",))["p"], p) <= 1e-10
+        res[variant] = rels
+    assert res[1][-1] > res[0][-1]   # the paper's scheme converges more slowly per iteration
+
+
 @pytest.mark.slow
 def test_full_size_heated_channel_one_step():
     """The 256 x 64 x 64 channel (the benchmark workload) in FP64, one step
