@@ -190,9 +190,9 @@ def run_batched(args, rank, ws, local, dist):
     if not args.no_autotune:
         # sweep counts, V-cycles per outer residual and planes per block, measured on the largest case
         _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
+        # (the planes per block are left to the batch rule: a batch has blocks to spare)
         specs = [sp.replace(pre_sweeps=tuning["pre_sweeps"], post_sweeps=tuning["post_sweeps"],
-                            inner_cycles=tuning["inner_cycles"], sweep_planes=tuning["sweep_planes"])
-                 for sp in specs]
+                            inner_cycles=tuning["inner_cycles"]) for sp in specs]
     N = sum(sp.cells for sp in specs)
     cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
     batch = binding.Batch(cs, stream=stream.cuda_stream)

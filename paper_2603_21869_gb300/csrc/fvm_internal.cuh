@@ -208,9 +208,9 @@ cudaError_t launch_init_state(int prec, const CaseDev& cd, StatePtrs st, const d
                               uint64_t seed, double eps, cudaStream_t s);
 cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_state, cudaStream_t s);
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
-                               const double* dt_state, cudaStream_t s);
+                               const double* dt_state, void* nut_out, cudaStream_t s);
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out,
-                            const double* dt_state, cudaStream_t s);
+                            const double* dt_state, const void* nut, cudaStream_t s);
 cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const double* dt_state,
                        cudaStream_t s);
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
@@ -350,6 +350,13 @@ __device__ __forceinline__ void batch_enter(const K* __restrict__ ks, const Batc
     __syncthreads();
 }
 
+// the body of one block, kept out of line: inlined into the walk below it would keep the
+// walk's state live across the whole body and raise the register count
+template <class K>
+__device__ __noinline__ void batch_block_body(const K& k, BlockAt at) {
+    k.run(at);
+}
+
 template <class K>
 __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchMap& m) {
     static_assert(sizeof(K) % 4 == 0, "functor size");
@@ -373,7 +380,7 @@ __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchM
             batch_enter(ks, m, c, buf, &s_live);
         }
         if (s_live) {
-            reinterpret_cast<const K*>(buf)->run(BlockAt{b, g});
+            batch_block_body(*reinterpret_cast<const K*>(buf), BlockAt{b, g});
             __syncthreads();   // shared memory of run() is reused by the next block
         }
         if (++b.x == g.x) {

@@ -1299,6 +1299,8 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
 // block on grids too small for that)
 static int sweep_planes(int tiles, int nz, int fixed) {
     if (fixed > 0) return fixed < nz ? fixed : nz;
+    // in a batch the cases' blocks add up: long columns (fewer re-read planes per plane written)
+    if (g_rec) return nz < 16 ? nz : 16;
     for (int zc : {32, 16, 8, 4, 2})
         if (tiles * ((nz + zc - 1) / zc) >= 8 * 152) return zc;
     return 1;

@@ -300,6 +300,8 @@ struct fvm_case {
     double* staging = nullptr;
     double* Ainv = nullptr;
     double* p_tmp = nullptr;         // the paper's scheme: Jacobi on p out of place
+    void* nut = nullptr;             // nu_t of the state after a destruction half step
+    bool nut_valid = false;          // nut matches the current k, omega
     std::vector<DevLevel> levels;
     SolveState* sst = nullptr;       // device
     SolveState* h_sst = nullptr;     // pinned host copy
@@ -509,6 +511,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     bytes += (int64_t)12 * N * s;             // state, two copies of six fields
     bytes += N * 8 + N * s + N;               // p (FP64), b, tag
     bytes += N * 8;                           // staging
+    bytes += N * s;                           // nu_t after a destruction half step
     for (int f = 0; f < 6; ++f) bytes += face_cells(n, f);
     for (size_t l = 0; l < pl.levels.size(); ++l) {
         const int64_t NL = pl.levels[l].N();
@@ -823,15 +826,18 @@ fvm_status stage(fvm_case* c, int st, int* cycles, double* rel) {
             KLAUNCH("dt", N * (5 * sz + 1), 2, launch_dt(c->prec, c->cd, ptrs(c->cur), c->dt_state, s));
             return FVM_OK;
         case FVM_STAGE_DESTRUCTION:
-            KLAUNCH("destruction", N * (7 * sz + 1), 1,
-                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, s));
+            KLAUNCH("destruction", N * (8 * sz + 1), 1,
+                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, c->nut, s));
             std::swap(c->cur[4], c->nxt[4]);
             std::swap(c->cur[5], c->nxt[5]);
+            c->nut_valid = true;
             return FVM_OK;
         case FVM_STAGE_EXPLICIT:
-            KLAUNCH("explicit", N * (12 * sz + 1), 1,
-                    launch_explicit(c->prec, c->cd, ptrs(c->cur), ptrs(c->nxt), c->dt_state, s));
+            KLAUNCH("explicit", N * (13 * sz + 1), 1,
+                    launch_explicit(c->prec, c->cd, ptrs(c->cur), ptrs(c->nxt), c->dt_state,
+                                    c->nut_valid ? c->nut : nullptr, s));
             for (int f = 0; f < 6; ++f) std::swap(c->cur[f], c->nxt[f]);
+            c->nut_valid = false;
             return FVM_OK;
         case FVM_STAGE_RHS:
             KLAUNCH("rhs", N * (4 * sz + 1), 1, launch_rhs(c->prec, c->cd, ptrs(c->cur), c->b, c->dt_state, s));
@@ -1091,6 +1097,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     ST_TRY(dalloc(c, (void**)&c->p, N * 8));
     ST_TRY(dalloc(c, &c->b, N * s));
     ST_TRY(dalloc(c, (void**)&c->staging, N * 8));
+    ST_TRY(dalloc(c, &c->nut, N * s));
     uint8_t* tag_d;
     ST_TRY(dalloc(c, (void**)&tag_d, N));
     CUDA_TRY(cudaMemcpyAsync(tag_d, pl.tag.data(), N, cudaMemcpyHostToDevice, c->stream));
@@ -1947,6 +1954,7 @@ fvm_status fvm_write_fields(fvm_case* c, unsigned mask, const double* host_in, s
         } else {
             CUDA_TRY(cudaMemcpyAsync(c->staging, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
             CUDA_TRY(launch_unpack(c->prec, c->staging, c->cur[field_slot(f)], N, c->stream));
+            c->nut_valid = false;
         }
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         off += (size_t)N;

@@ -232,12 +232,14 @@ struct DtFinalizeK {
 template <class S, class C>
 struct DestructionK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr int kMinBlocks = sizeof(C) == 4 ? 3 : 1;   // FP32: at most 85 registers
     __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in;
     S* k_out;
     S* om_out;
     const double* dt_state;
+    S* nut_out;   // nu_t of the updated k, omega (read by the explicit stage), or null
     __device__ void run(const BlockAt& at) const;
 };
 
@@ -250,6 +252,7 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     if (cd.tag[c]) {
         k_out[c] = from_c<S, C>(P.k);
         om_out[c] = from_c<S, C>(P.om);
+        if (nut_out) nut_out[c] = from_c<S, C>((C)0);
         return;
     }
     // cell gradients L_j * D_j * BC_j(phi) of u, v, w, k, omega
@@ -309,6 +312,7 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     const C omnew = P.om / ((C)1 + dt * (C)kBeta * fb * P.om);
     k_out[c] = from_c<S, C>(knew);
     om_out[c] = from_c<S, C>(omnew);
+    if (nut_out) nut_out[c] = from_c<S, C>(nut_of(knew, omnew, prm<C>(cd.nu, cd.f.nu)));
 }
 
 // ------------------------------------------------------------------ explicit stage
@@ -335,20 +339,23 @@ __device__ __forceinline__ void face_flux(const CaseDev& cd, int a, const St<C>&
     fl[a] -= (C)(2.0 / 3.0) * ((C)0.5 * (L.k + R.k));
 }
 
-template <class C>
-__device__ __forceinline__ C face_nut(int kind, C nutP, const St<C>& nb, C nu) {
+// face nu_t: 0 on walls, the mean of the two cells inside, the cell's own on other faces
+template <class C, class N>
+__device__ __forceinline__ C face_nut(int kind, C nutP, N nut_nb) {
     if (kind == FK_WALL) return (C)0;
-    if (kind == FK_INTERIOR) return (C)0.5 * (nutP + nut_of(nb.k, nb.om, nu));
+    if (kind == FK_INTERIOR) return (C)0.5 * (nutP + nut_nb());
     return nutP;
 }
 
 template <class S, class C>
 struct ExplicitK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr int kMinBlocks = sizeof(C) == 4 ? 3 : 1;   // FP32: at most 85 registers
     __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in, out;
     const double* dt_state;
+    const S* nut;   // nu_t of the input state (written by the destruction half step), or null: computed here
     __device__ void run(const BlockAt& at) const;
 };
 
@@ -366,7 +373,9 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
         return;
     }
     const C nu = prm<C>(cd.nu, cd.f.nu);
-    const C nutP = nut_of(P.k, P.om, nu);
+    const S* const nutf = nut;
+    const C nutP = nutf ? to_c<C>(ldg(nutf + c)) : nut_of(P.k, P.om, nu);
+    const int stride[3] = {1, cd.n[0], cd.n[0] * cd.n[1]};
     C rhs[6] = {(C)0, (C)0, (C)0, (C)0, (C)0, (C)0};
     C gu[3][3];
     C omw = (C)0;
@@ -379,8 +388,11 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
         const int kl = neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
         const int kr = neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
         C fw[6], fe[6];
-        face_flux(cd, a, L, P, face_nut(kl, nutP, L, nu), fw);
-        face_flux(cd, a, P, R, face_nut(kr, nutP, R, nu), fe);
+        auto nb_nut = [&](int side, const St<C>& g) {
+            return [&, side]() { return nutf ? to_c<C>(ldg(nutf + c + side * stride[a])) : nut_of(g.k, g.om, nu); };
+        };
+        face_flux(cd, a, L, P, face_nut<C>(kl, nutP, nb_nut(-1, L)), fw);
+        face_flux(cd, a, P, R, face_nut<C>(kr, nutP, nb_nut(+1, R)), fe);
         const C ih = prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
         for (int f = 0; f < 6; ++f) rhs[f] += (fe[f] - fw[f]) * ih;
         gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
@@ -557,17 +569,17 @@ cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_stat
 }
 
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
-                               const double* dt_state, cudaStream_t s) {
+                               const double* dt_state, void* nut_out, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    DISPATCH(prec, err = launch_k(DestructionK<S, C>{cd, in, (S*)k_out, (S*)om_out, dt_state}, grid3(cd), kBlock3,
-                                  0, s));
+    DISPATCH(prec, err = launch_k(DestructionK<S, C>{cd, in, (S*)k_out, (S*)om_out, dt_state, (S*)nut_out}, grid3(cd),
+                                  kBlock3, 0, s));
     return err;
 }
 
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out, const double* dt_state,
-                            cudaStream_t s) {
+                            const void* nut, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    DISPATCH(prec, err = launch_k(ExplicitK<S, C>{cd, in, out, dt_state}, grid3(cd), kBlock3, 0, s));
+    DISPATCH(prec, err = launch_k(ExplicitK<S, C>{cd, in, out, dt_state, (const S*)nut}, grid3(cd), kBlock3, 0, s));
     return err;
 }
 
