@@ -11,6 +11,8 @@
              (Eq. prolongation)
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
              correct, post-smooth; exact dense solve on the coarsest level
+  krylov 1   GCR with one kept direction around V-cycles (each V-cycle from
+             zero on A z = r preconditions one minimal-residual step)
   Algorithm 1 (mg_variant 1): the fine residual restricted straight down,
              one unweighted Jacobi per coarse level on the way up (A and D
              with the fine spacing), nearest upsampling, a final unweighted
@@ -223,6 +225,39 @@ class Multigrid:
             return self.paper_cycle(p, b)
         return self.vcycle(p, b)
 
+    def gcr_solve(self, p, b, cycles_cap, tol, fixed):
+        """GCR with one kept direction, one V-cycle from zero on A z = r as
+        the preconditioner (the outer acceleration of krylov = 1).  Each
+        iteration: z = V(r), q = A z, both made A-orthogonal to the previous
+        direction (beta = (q, q_prev) / (q_prev, q_prev)), then the step that
+        minimises the new residual, p += alpha z with
+        alpha = (r, q) / (q, q); r = b - A p is recomputed from p.  Inner
+        products over fluid cells."""
+        lev = self.levels[0]
+        fl = lev.fluid
+
+        def dot(a, c):
+            return float(np.sum(a[fl] * c[fl]))
+
+        zp = qp = None
+        n = 0
+        rel = self.rel_residual(p, b)
+        while (n < fixed) if fixed > 0 else (rel > tol and n < cycles_cap):
+            r = residual(lev, p, b)
+            z = self.vcycle(np.zeros(lev.shape), r)
+            q = apply_A(lev, z)
+            if zp is not None:
+                beta = dot(q, qp) / dot(qp, qp)
+                z = z - beta * zp
+                q = q - beta * qp
+            qq = dot(q, q)
+            alpha = dot(r, q) / qq if qq > 0.0 else 0.0
+            p = np.where(fl, p + alpha * z, 0.0)
+            zp, qp = z, q
+            n += 1
+            rel = self.rel_residual(p, b)
+        return p, n, rel
+
     def rel_residual(self, p, b):
         lev = self.levels[0]
         nb = np.linalg.norm(b[lev.fluid])
@@ -235,6 +270,8 @@ class Multigrid:
         else until the relative residual is <= mg_rel_tol or max_vcycles ran.
         Returns (p, cycles, final relative residual)."""
         s = self.spec
+        if getattr(s, "krylov", 0) == 1:
+            return self.gcr_solve(p, b, s.max_vcycles, s.mg_rel_tol, s.fixed_vcycles)
         if s.fixed_vcycles > 0:
             for _ in range(s.fixed_vcycles):
                 p = self.cycle(p, b)
