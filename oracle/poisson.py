@@ -11,8 +11,10 @@
              (Eq. prolongation)
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
              correct, post-smooth; exact dense solve on the coarsest level
-  krylov 1   GCR with one kept direction around V-cycles (each V-cycle from
-             zero on A z = r preconditions one minimal-residual step)
+  krylov 1   flexible CG with one kept direction around V-cycles (each
+             V-cycle from zero on A z = r gives a direction, A-orthogonalised
+             against the previous one, and the step minimising the A-norm of
+             the error along it)
   Algorithm 1 (mg_variant 1): the fine residual restricted straight down,
              one unweighted Jacobi per coarse level on the way up (A and D
              with the fine spacing), nearest upsampling, a final unweighted
@@ -225,35 +227,38 @@ class Multigrid:
             return self.paper_cycle(p, b)
         return self.vcycle(p, b)
 
-    def gcr_solve(self, p, b, cycles_cap, tol, fixed):
-        """GCR with one kept direction, one V-cycle from zero on A z = r as
-        the preconditioner (the outer acceleration of krylov = 1).  Each
-        iteration: z = V(r), q = A z, both made A-orthogonal to the previous
-        direction (beta = (q, q_prev) / (q_prev, q_prev)), then the step that
-        minimises the new residual, p += alpha z with
-        alpha = (r, q) / (q, q); r = b - A p is recomputed from p.  Inner
-        products over fluid cells."""
+    def fcg_solve(self, p, b, cycles_cap, tol, fixed):
+        """Flexible conjugate gradients with one kept direction, one V-cycle
+        from zero on A z = r as the preconditioner (the outer acceleration of
+        krylov = 1).  A is symmetric positive definite on the fluid cells, so
+        a step along any direction d with alpha = (r, d) / (d, A d) cannot
+        raise the A-norm of the error.  Each iteration: z = V(r), made
+        A-orthogonal to the previous direction (beta = (z, A d_prev) /
+        (d_prev, A d_prev), d = z - beta d_prev), then that step,
+        p += alpha d; r = b - A p is recomputed from p.  With a fixed
+        symmetric positive definite preconditioner in place of the V-cycle
+        this is preconditioned CG.  Inner products over fluid cells."""
         lev = self.levels[0]
         fl = lev.fluid
 
         def dot(a, c):
             return float(np.sum(a[fl] * c[fl]))
 
-        zp = qp = None
+        dp = qp = None
         n = 0
         rel = self.rel_residual(p, b)
         while (n < fixed) if fixed > 0 else (rel > tol and n < cycles_cap):
             r = residual(lev, p, b)
-            z = self.vcycle(np.zeros(lev.shape), r)
-            q = apply_A(lev, z)
-            if zp is not None:
-                beta = dot(q, qp) / dot(qp, qp)
-                z = z - beta * zp
+            d = self.vcycle(np.zeros(lev.shape), r)
+            q = apply_A(lev, d)
+            if dp is not None:
+                beta = dot(d, qp) / dot(dp, qp)
+                d = d - beta * dp
                 q = q - beta * qp
-            qq = dot(q, q)
-            alpha = dot(r, q) / qq if qq > 0.0 else 0.0
-            p = np.where(fl, p + alpha * z, 0.0)
-            zp, qp = z, q
+            dq = dot(d, q)
+            alpha = dot(r, d) / dq if dq > 0.0 else 0.0
+            p = np.where(fl, p + alpha * d, 0.0)
+            dp, qp = d, q
             n += 1
             rel = self.rel_residual(p, b)
         return p, n, rel
@@ -271,7 +276,7 @@ class Multigrid:
         Returns (p, cycles, final relative residual)."""
         s = self.spec
         if getattr(s, "krylov", 0) == 1:
-            return self.gcr_solve(p, b, s.max_vcycles, s.mg_rel_tol, s.fixed_vcycles)
+            return self.fcg_solve(p, b, s.max_vcycles, s.mg_rel_tol, s.fixed_vcycles)
         if s.fixed_vcycles > 0:
             for _ in range(s.fixed_vcycles):
                 p = self.cycle(p, b)

@@ -262,7 +262,7 @@ def test_paper_scheme_converges_at_any_depth():
     assert rates[1] < 0.1 and rates[1] < 1.5 * rates[0]
 
 
-# ------------------------------------------------------------------ GCR acceleration (krylov = 1)
+# ------------------------------------------------------------------ flexible CG acceleration (krylov = 1)
 def _room_problem():
     from paper_2603_21869_gb300 import cases
     from oracle.step import OracleCase
@@ -273,9 +273,16 @@ def _room_problem():
     return spec, mg, lev, b
 
 
-def test_gcr_with_an_exact_preconditioner_solves_in_one_step():
-    """With the exact inverse as the preconditioner, z = A^-1 r, q = r and
-    alpha = 1: one GCR step lands on the discrete solution."""
+def _fluid_operator(lev):
+    """A restricted to the fluid cells as a scipy LinearOperator (zero on solid cells)."""
+    from scipy.sparse.linalg import LinearOperator
+    n = int(np.prod(lev.shape))
+    return LinearOperator((n, n), matvec=lambda x: apply_A(lev, x.reshape(lev.shape)).ravel(), dtype=np.float64)
+
+
+def test_fcg_with_an_exact_preconditioner_solves_in_one_step():
+    """With the exact inverse as the preconditioner, d = A^-1 r is the error
+    and alpha = (r, d) / (d, A d) = 1: one step lands on the discrete solution."""
     from paper_2603_21869_gb300 import cases
     from oracle.step import OracleCase
     from oracle.poisson import direct_solve
@@ -283,25 +290,56 @@ def test_gcr_with_an_exact_preconditioner_solves_in_one_step():
     lev = mg.levels[0]
     b = np.where(lev.fluid, np.random.default_rng(11).normal(size=lev.shape), 0.0)
     mg.vcycle = lambda p, r, l=0: direct_solve(lev, r)
-    p, n, rel = mg.gcr_solve(np.zeros(lev.shape), b, 5, 1e-12, 1)
+    p, n, rel = mg.fcg_solve(np.zeros(lev.shape), b, 5, 1e-12, 1)
     assert n == 1 and rel <= 1e-11
     assert np.max(np.abs(p - direct_solve(lev, b))) <= 1e-10 * np.max(np.abs(p))
 
 
-def test_gcr_residuals_never_grow_and_beat_plain_cycles():
-    """Each step minimises the residual along its direction, so the residual
-    is non-increasing; on the room (a small outlet) it also needs fewer
-    cycles than plain V-cycles to the same tolerance."""
+def test_fcg_with_a_fixed_jacobi_preconditioner_is_textbook_pcg():
+    """With a fixed symmetric positive definite preconditioner (r / D on
+    fluid cells) one kept direction already makes every direction
+    A-orthogonal: the iterates are those of preconditioned CG (scipy's cg
+    with the same preconditioner, from zero)."""
+    from scipy.sparse.linalg import LinearOperator, cg
     spec, mg, lev, b = _room_problem()
-    last = mg.rel_residual(np.zeros(lev.shape), b)
-    _, n_gcr, rel_gcr = mg.gcr_solve(np.zeros(lev.shape), b, 60, 1e-8, 0)
+    D = lev.diag()
+    n = int(np.prod(lev.shape))
+    M = LinearOperator((n, n), matvec=lambda x: np.where(lev.fluid, x.reshape(lev.shape) / D, 0.0).ravel(),
+                       dtype=np.float64)
+    ref = []
+    cg(_fluid_operator(lev), b.ravel(), x0=np.zeros(n), M=M, rtol=1e-30, maxiter=12,
+       callback=lambda xk: ref.append(xk.reshape(lev.shape).copy()))
+    mg.vcycle = lambda p, r, l=0: np.where(lev.fluid, r / D, 0.0)
+    for k in (1, 2, 5, 12):
+        p, _, _ = mg.fcg_solve(np.zeros(lev.shape), b, 0, 0.0, k)
+        assert np.max(np.abs(p - ref[k - 1])) <= 1e-9 * np.max(np.abs(ref[k - 1])), k
+
+
+def test_fcg_error_energy_never_grows_and_beats_plain_cycles():
+    """Each step minimises the A-norm of the error along its direction, so
+    that norm is non-increasing (against the solution from scipy's cg to
+    1e-13); on the room (a small outlet) it also needs fewer cycles than
+    plain V-cycles to the same tolerance."""
+    from scipy.sparse.linalg import cg
+    spec, mg, lev, b = _room_problem()
+    ps, info = cg(_fluid_operator(lev), b.ravel(), x0=np.zeros(b.size), rtol=1e-13, maxiter=5000)
+    assert info == 0
+    ps = ps.reshape(lev.shape)
+
+    def energy(p):
+        e = np.where(lev.fluid, p - ps, 0.0)
+        return float(np.sum(e * apply_A(lev, e)))
+
+    last = energy(np.zeros(lev.shape))
+    _, n_fcg, rel_fcg = mg.fcg_solve(np.zeros(lev.shape), b, 60, 1e-8, 0)
     for k in range(1, 8):
-        _, _, rel = mg.gcr_solve(np.zeros(lev.shape), b, 60, 0.0, k)
-        assert rel <= last * (1 + 1e-12)
-        last = rel
+        p, _, _ = mg.fcg_solve(np.zeros(lev.shape), b, 60, 0.0, k)
+        E = energy(p)
+        assert E <= last * (1 + 1e-9), k
+        last = E
     q = np.zeros(lev.shape)
     n_plain = 0
     while mg.rel_residual(q, b) > 1e-8 and n_plain < 60:
         q = mg.vcycle(q, b)
         n_plain += 1
-    assert rel_gcr <= 1e-8 and n_gcr < n_plain
+    assert rel_fcg <= 1e-8 and n_fcg < n_plain
