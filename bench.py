@@ -192,7 +192,7 @@ def run_batched(args, rank, ws, local, dist):
         _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
         # (the planes per block are left to the batch rule: a batch has blocks to spare)
         specs = [sp.replace(pre_sweeps=tuning["pre_sweeps"], post_sweeps=tuning["post_sweeps"],
-                            inner_cycles=tuning["inner_cycles"]) for sp in specs]
+                            inner_cycles=tuning["inner_cycles"], krylov=tuning["krylov"]) for sp in specs]
     N = sum(sp.cells for sp in specs)
     cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
     batch = binding.Batch(cs, stream=stream.cuda_stream)

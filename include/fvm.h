@@ -118,6 +118,12 @@ typedef struct {
     int32_t mg_variant;              /* 0: V(pre, post) cycles; 1: the paper's scheme (Algorithm 1:
                                         residual restricted straight down, one unweighted Jacobi per
                                         coarse level, nearest upsampling, a final Jacobi on p) */
+    int32_t krylov;                  /* 1: flexible CG with one kept direction around the
+                                        V-cycles (each outer iteration steps along the V-cycle
+                                        correction made A-orthogonal to the previous direction,
+                                        by the length that minimises the error's A-norm); 0: none.
+                                        Not with mg_variant 1.  An addition beyond the paper. */
+    int32_t reserved_k;              /* 0 */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
@@ -271,18 +277,19 @@ fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
    the case (own stream; the descriptor is not changed), graph-mode steps
    after two untimed ones, timed with CUDA events, `steps` steps each.
    Pass 1: V(nu, nu) for nu = 2, 3, 4 times the V-cycles per FP64 outer
-   residual (1..4 with reduced-precision corrections, 1 in FP64); pass 2: the
+   residual (1..4 with reduced-precision corrections, 1 in FP64) times the
+   flexible-CG acceleration off / on (off only with mg_variant 1); pass 2: the
    z planes per block of the four-cell level kernels (the rule, 1 .. 32)
    with the best pass-1 choice.  Candidates that stop at max_vcycles above
    the tolerance are not eligible.  Copy the result into the descriptor's
-   pre_sweeps, post_sweeps, inner_cycles and sweep_planes.  Device memory: one
+   pre_sweeps, post_sweeps, inner_cycles, sweep_planes and krylov.  Device memory: one
    temporary case at a time.  Errors: FVM_ERR_INVALID, FVM_ERR_NOT_CONVERGED
    (no candidate converged), FVM_ERR_CUDA. */
 typedef struct {
     int32_t pre_sweeps, post_sweeps, inner_cycles, sweep_planes;
     double  ms_per_step;             /* of the choice, device time per step */
     int32_t candidates;              /* candidates timed */
-    int32_t reserved;
+    int32_t krylov;                  /* 0 / 1: the flexible-CG acceleration */
 } fvm_tuning;
 
 fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm_tuning* out);

@@ -3,9 +3,9 @@
 // untimed steps that capture both pointer parities), timed with CUDA events
 // on the case's stream over `steps` steps to the case's tolerance.
 //
-// Pass 1 tries the smoother sweep counts V(nu, nu), nu = 2, 3, 4, and the
+// Pass 1 tries the smoother sweep counts V(nu, nu), nu = 2, 3, 4, the
 // V-cycles per FP64 outer residual (1..4 with reduced-precision corrections,
-// 1 in FP64); pass 2 tries the z planes per block of the four-cell level
+// 1 in FP64) and the flexible-CG acceleration off / on; pass 2 tries the z planes per block of the four-cell level
 // kernels (the built-in rule, 1 .. 32) with the best pass-1 choice.  A
 // candidate whose solves stop at max_vcycles above the tolerance is not
 // eligible.
@@ -18,7 +18,7 @@
 namespace {
 
 struct Trial {
-    int pre, post, inner, planes;
+    int pre, post, inner, planes, krylov;
     double ms;
 };
 
@@ -29,6 +29,7 @@ double time_candidate(const fvm_case_desc& base, const Trial& t, int steps, cuda
     d.post_sweeps = t.post;
     d.inner_cycles = t.inner;
     d.sweep_planes = t.planes;
+    d.krylov = t.krylov;
     d.stream = s;
     fvm_case* c = nullptr;
     if (fvm_create_case(&d, &c) != FVM_OK) return -1.0;
@@ -70,15 +71,17 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     std::vector<int> inners;
     if (desc->precision == FVM_FP64) inners = {1};
     else inners = {1, 2, 3, 4};
-    Trial best{0, 0, 0, 0, -1.0};
+    Trial best{0, 0, 0, 0, 0, -1.0};
     int tried = 0;
-    for (int nu : {2, 3, 4})
-        for (int inner : inners) {
-            Trial t{nu, nu, inner, 0, 0.0};
-            t.ms = time_candidate(*desc, t, steps, s);
-            ++tried;
-            if (t.ms > 0.0 && (best.ms < 0.0 || t.ms < best.ms)) best = t;
-        }
+    const int kmax = desc->mg_variant == 1 ? 0 : 1;
+    for (int kry = 0; kry <= kmax; ++kry)
+        for (int nu : {2, 3, 4})
+            for (int inner : inners) {
+                Trial t{nu, nu, inner, 0, kry, 0.0};
+                t.ms = time_candidate(*desc, t, steps, s);
+                ++tried;
+                if (t.ms > 0.0 && (best.ms < 0.0 || t.ms < best.ms)) best = t;
+            }
     if (best.ms > 0.0)
         for (int planes : {1, 2, 4, 8, 16, 32}) {
             Trial t = best;
@@ -98,6 +101,7 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     o.post_sweeps = best.post;
     o.inner_cycles = best.inner;
     o.sweep_planes = best.planes;
+    o.krylov = best.krylov;
     o.ms_per_step = best.ms;
     o.candidates = tried;
     *out = o;

@@ -113,6 +113,11 @@ struct SolveState {
     int32_t tma_timeout;     // sticky flag: a bounded device-side wait (tensor copy, grid barrier) gave up
     uint32_t bar_count;      // grid barrier of the persistent tail kernel: blocks arrived
     uint32_t bar_gen;        // and its generation
+    // flexible CG with one kept direction (krylov = 1)
+    uint32_t g_counter;      // blocks finished in the inner-product pass
+    int32_t g_valid;         // a previous direction is kept
+    double g_alpha, g_beta;  // step along the new direction, its component along the previous one
+    double g_dq;             // (d, A d) of the kept direction
 };
 
 // Levels ls..L-1 of one V-cycle run by one persistent kernel: grid levels
@@ -235,6 +240,12 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s);
 cudaError_t prepare_coarse_cta(int inner, size_t smem);
+// flexible CG with one kept direction around the V-cycles: the inner products
+// of z (the V-cycles' correction) with A z, r and the kept direction d_prev
+// (last block: beta, alpha), then d = z - beta d_prev, p += alpha d, d kept.
+// partials: 4 doubles per block, fcg_blocks(n) blocks at most.
+cudaError_t launch_fcg(int inner, const LevelDev& L, const void* z, const void* r, void* dp, double* p,
+                       double* partials, SolveState* st, cudaStream_t s);
 // the paper's scheme (Algorithm 1)
 cudaError_t launch_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* r, void* rc,
                             const SolveState* st, cudaStream_t s);
@@ -254,6 +265,7 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
                               const SolveState* st, cudaStream_t s);
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
 int resid0_blocks(int nx, int ny, int nz);
+int fcg_blocks(int nx, int ny, int nz);   // blocks of a flexible-CG inner-product pass, at most
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner);
 // cluster kernel (mg_cluster.cu)
 size_t cluster_smem_bytes(const ClusterLevels& cl, int inner);

@@ -241,6 +241,8 @@ struct SolveBeginK {
         st->cycles = 0;
         st->counter = 0u;
         st->bar_count = 0u;
+        st->g_counter = 0u;
+        st->g_valid = 0;
         st->active = 1;
     }
 };
@@ -555,6 +557,205 @@ __device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
         }
     }
 }
+
+// The last block of a flexible-CG inner-product pass: sums all blocks'
+// partials in a fixed order (thread t: blocks t, t + NT, ...; then a fixed
+// shuffle tree and a fixed sum over warps) and sets beta, alpha and the kept
+// (d, A d).  Out of line: it runs once per launch and would otherwise hold
+// registers in every block.
+template <int NT>
+__device__ __noinline__ void fcg_finish(const double* partials, int nblk, SolveState* st, bool have,
+                                        double (*red)[NT / 32]) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int x = tid; x < nblk; x += NT) {
+        const double2 u = __ldcg(reinterpret_cast<const double2*>(partials + 4 * x));
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(partials + 4 * x + 2));
+        a[0] += u.x;
+        a[1] += u.y;
+        a[2] += v.x;
+        a[3] += v.y;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        for (int off = 16; off > 0; off >>= 1) a[m] += __shfl_xor_sync(0xffffffffu, a[m], off);
+    __syncthreads();
+    if ((tid & 31) == 0)
+        for (int m = 0; m < 4; ++m) red[m][tid >> 5] = a[m];
+    __syncthreads();
+    if (tid == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int m = 0; m < 4; ++m)
+            for (int w = 0; w < NT / 32; ++w) t[m] += red[m][w];
+        double beta = (have && st->g_dq > 0.0) ? t[1] / st->g_dq : 0.0;
+        double dq = t[0] - beta * t[1];
+        if (!(dq > 0.0)) {   // restart along z alone
+            beta = 0.0;
+            dq = t[0];
+        }
+        st->g_beta = beta;
+        st->g_alpha = dq > 0.0 ? (t[2] - beta * t[3]) / dq : 0.0;
+        st->g_dq = dq;
+        st->g_valid = 1;
+        st->g_counter = 0u;
+    }
+}
+
+// the four sums of one block (each thread's in s) into partials; the last
+// block to finish completes the pass (fcg_finish)
+template <int NT>
+__device__ __forceinline__ void fcg_reduce(double (&s)[4], double* partials, SolveState* st, bool have,
+                                           const BlockAt& at) {
+    __shared__ double red[4][NT / 32];
+    __shared__ bool last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        for (int off = 16; off > 0; off >>= 1) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
+    if ((tid & 31) == 0)
+        for (int m = 0; m < 4; ++m) red[m][tid >> 5] = s[m];
+    __syncthreads();
+    const int nblk = at.g.x * at.g.y * at.g.z;
+    if (tid == 0) {
+        const int bid = at.b.x + at.g.x * (at.b.y + at.g.y * at.b.z);
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < NT / 32; ++w)
+            for (int m = 0; m < 4; ++m) t[m] += red[m][w];
+        reinterpret_cast<double2*>(partials + 4 * bid)[0] = make_double2(t[0], t[1]);
+        reinterpret_cast<double2*>(partials + 4 * bid)[1] = make_double2(t[2], t[3]);
+        __threadfence();
+        last = atomicAdd(&st->g_counter, 1u) == (unsigned)nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    fcg_finish<NT>(partials, nblk, st, have, red);
+}
+
+// The flexible-CG inner products with four x cells per thread and a z march
+// (the sweep's layout and neighbour scheme): products and the thread's sums
+// in FP32, block and grid sums in FP64.  Needs nx % 4 = 0.
+template <class TI>
+struct FcgDotV4K {
+    static constexpr int kThreads = TX * TY;
+    static constexpr int kMinBlocks = 3;   // at most 80 registers
+    LevelDev L;
+    const TI* z;
+    const TI* r;
+    const TI* dp;
+    double* partials;
+    SolveState* st;
+    int zc;   // planes per block
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
+    using C = float;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int lane = threadIdx.x;
+    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
+    const bool in = i4 < nx && j < ny;
+    const int sy = nx, sz = nx * ny;
+    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
+    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
+    const bool lastc = i4 + 4 >= nx;
+    const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
+    const C dg = LP<C>::diag(L);
+    const bool have = st->g_valid != 0;
+    const TI* const zz = this->z;
+    const uint16_t* const nbf = L.nbf;
+    C em[4], ec[4], ep[4];
+    Vec4<TI>::load(zz, max(k0 - 1, 0) * sz + own, em);
+    Vec4<TI>::load(zz, k0 * sz + own, ec);
+    Vec4<TI>::load(zz, min(k0 + 1, nz - 1) * sz + own, ep);
+    C a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int k = k0; k < k1; ++k) {
+        const int base = k * sz;
+        C ym[4], yp[4], rr[4], dd[4] = {0.f, 0.f, 0.f, 0.f}, en[4];
+        Vec4<TI>::load(zz, base + om, ym);
+        Vec4<TI>::load(zz, base + op, yp);
+        Vec4<TI>::load(r, base + own, rr);
+        if (have) Vec4<TI>::load(dp, base + own, dd);
+        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
+        const C xls = lane == 0 ? to_c<C>(ldg(zz + base + xl)) : (C)0;
+        const C xrs = lane == TX - 1 ? to_c<C>(ldg(zz + base + xr)) : (C)0;
+        Vec4<TI>::load(zz, min(k + 2, nz - 1) * sz + own, en);
+        C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
+        C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        if (lane == 0) left = xls;
+        if (lane == TX - 1) right = xrs;
+        if (lastc) right = ec[3];
+        const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
+        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+        if (in) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (is_solid(fs[t])) continue;
+                const C eP = xs[t + 1];
+                C A;
+                if (!((fs[t] >> 13) & 1u)) {
+                    C q = (xs[t] + xs[t + 2]) * ihx;
+                    q = fma(ym[t] + yp[t], ihy, q);
+                    q = fma(em[t] + ep[t], ihz, q);
+                    A = fma(dg, eP, -q);
+                } else {
+                    A = A7_general<C>(L, fs[t], eP, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t]);
+                }
+                a0 = fma(eP, A, a0);
+                a1 = fma(A, dd[t], a1);
+                a2 = fma(rr[t], eP, a2);
+                a3 = fma(rr[t], dd[t], a3);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            em[t] = ec[t];
+            ec[t] = ep[t];
+            ep[t] = en[t];
+        }
+    }
+    double s[4] = {(double)a0, (double)a1, (double)a2, (double)a3};
+    fcg_reduce<kThreads>(s, partials, st, have, at);
+}
+
+// d = z - beta d_prev, p += alpha d (fluid cells), d kept: four consecutive
+// cells per thread, one-dimensional grid.  Needs N % 4 = 0.
+template <class TI>
+struct FcgUpdV4K {
+    static constexpr int kThreads = 256;
+    LevelDev L;
+    const TI* z;
+    TI* dp;
+    double* p;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        const int c = 4 * (at.b.x * kThreads + threadIdx.x);
+        if (c >= L.N) return;
+        const float alpha = (float)st->g_alpha, beta = (float)st->g_beta;
+        float zv[4], dv[4] = {0.f, 0.f, 0.f, 0.f};
+        Vec4<TI>::load(z, c, zv);
+        if (beta != 0.f) Vec4<TI>::load(dp, c, dv);
+        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(L.nbf + c));
+        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+        float d[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) d[t] = fma(-beta, dv[t], zv[t]);
+        Vec4<TI>::store(dp, c, d);
+        double2* pp = reinterpret_cast<double2*>(p + c);
+        double2 u = pp[0], v = pp[1];
+        if (!is_solid(fs[0])) u.x += (double)(alpha * d[0]);
+        if (!is_solid(fs[1])) u.y += (double)(alpha * d[1]);
+        if (!is_solid(fs[2])) v.x += (double)(alpha * d[2]);
+        if (!is_solid(fs[3])) v.y += (double)(alpha * d[3]);
+        pp[0] = u;
+        pp[1] = v;
+    }
+};
 
 // Trilinear prolongation and correction, four x cells per thread: a lane's
 // four fine cells have the coarse parents I0 = i/2 and I0 + 1 (two
@@ -967,6 +1168,80 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     }
 }
 
+// ------------------------------------------------------------------ flexible CG acceleration (krylov = 1)
+// One pass over level 0 with z (the V-cycles' correction for the outer
+// residual r) and the kept direction d_prev: A z at each cell from the
+// stencil (not stored) and the block sums of (z, A z), (A z, d_prev),
+// (r, z), (r, d_prev).  The last block sums them in a fixed order and sets,
+// for d = z - beta d_prev,
+//   beta   = (A z, d_prev) / (d_prev, A d_prev)   [= (z, A d_prev): A is symmetric]
+//   (d, A d) = (z, A z) - beta (A z, d_prev)
+//   alpha  = ((r, z) - beta (r, d_prev)) / (d, A d),
+// keeping (d, A d) for the next iteration.  Should rounding make (d, A d)
+// non-positive (never in exact arithmetic) the direction restarts: beta = 0.
+template <class TI>
+struct FcgDotK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr int kMinBlocks = 4;
+    LevelDev L;
+    const TI* z;
+    const TI* r;
+    const TI* dp;
+    double* partials;
+    SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ void FcgDotK<TI>::run(const BlockAt& at) const {
+    using C = typename Acc<TI>::type;
+    const bool have = st->g_valid != 0;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};   // (z,Az), (Az,dp), (r,z), (r,dp)
+    int i, j, k;
+    if (cell3(L, at, i, j, k)) {
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        const uint32_t f = L.nbf[c];
+        const int sy = L.n[0], sz = L.n[0] * L.n[1];
+        const C eP = to_c<C>(ldg(z + c));
+        const C xm = to_c<C>(ldg(z + c - (i > 0 ? 1 : 0))), xp = to_c<C>(ldg(z + c + (i < L.n[0] - 1 ? 1 : 0)));
+        const C ym = to_c<C>(ldg(z + c - (j > 0 ? sy : 0))), yp = to_c<C>(ldg(z + c + (j < L.n[1] - 1 ? sy : 0)));
+        const C zm = to_c<C>(ldg(z + c - (k > 0 ? sz : 0))), zp = to_c<C>(ldg(z + c + (k < L.n[2] - 1 ? sz : 0)));
+        const double rd = to_c<double>(ldg(r + c));
+        const double dd = have ? to_c<double>(ldg(dp + c)) : 0.0;
+        if (!is_solid(f)) {
+            const double zd = (double)eP;
+            const double qd = (double)A7<C>(L, f, eP, xm, xp, ym, yp, zm, zp);
+            s[0] = zd * qd;
+            s[1] = qd * dd;
+            s[2] = rd * zd;
+            s[3] = rd * dd;
+        }
+    }
+    fcg_reduce<kThreads>(s, partials, st, have, at);
+}
+
+// d = z - beta d_prev; p += alpha d on fluid cells; d kept as d_prev
+template <class TI>
+struct FcgUpdK {
+    static constexpr int kThreads = BX * BY * BZ;
+    LevelDev L;
+    const TI* z;
+    TI* dp;
+    double* p;
+    const SolveState* st;
+    __device__ bool live() const { return st->active != 0; }
+    __device__ void run(const BlockAt& at) const {
+        int i, j, k;
+        if (!cell3(L, at, i, j, k)) return;
+        const int c = i + L.n[0] * (j + L.n[1] * k);
+        const double alpha = st->g_alpha, beta = st->g_beta;
+        const double d = to_c<double>(ldg(z + c)) - (beta != 0.0 ? beta * to_c<double>(dp[c]) : 0.0);
+        if (!is_solid(L.nbf[c])) p[c] += alpha * d;
+        dp[c] = from_c<TI, double>(d);
+    }
+};
+
 // ------------------------------------------------------------------ the paper's scheme (Algorithm 1)
 // coarse r = mean of the children's r (the residual restricted straight down)
 template <class TI>
@@ -1247,6 +1522,12 @@ int resid0_blocks(int nx, int ny, int nz) {
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + BZ - 1) / BZ);
 }
 
+int fcg_blocks(int nx, int ny, int nz) {
+    const int four = ((nx + V4X - 1) / V4X) * ((ny + TY - 1) / TY) * nz;   // the four-cell pass, one plane a block
+    const int r0 = resid0_blocks(nx, ny, nz);
+    return four > r0 ? four : r0;
+}
+
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner) {
     const size_t cs = inner == FVM_FP64 ? 8 : 4;
     size_t n = 0, m = 0;
@@ -1399,6 +1680,34 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
     cudaError_t err = cudaSuccess;
     DISPATCH_I(inner, err = launch_k(CoarseK<TI>{cl, (const TI*)r_in, (TI*)e_out, Ainv, st}, dim3(1),
                                      dim3(kCtaThreads), smem, s));
+    return err;
+}
+
+template <class TI>
+static cudaError_t fcg_launch(const LevelDev& L, const TI* z, const TI* r, TI* dp, double* p, double* partials,
+                              SolveState* st, cudaStream_t s) {
+    if constexpr (sizeof(TI) < 8) {
+        if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
+            const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
+            const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
+            const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
+                            (unsigned)((L.n[2] + zc - 1) / zc));
+            // (at most fcg_blocks(n) blocks: partials has room)
+            cudaError_t err = launch_k(FcgDotV4K<TI>{L, z, r, dp, partials, st, zc}, grid, dim3(TX, TY), 0, s);
+            if (err != cudaSuccess) return err;
+            const unsigned nb = (unsigned)((L.N / 4 + FcgUpdV4K<TI>::kThreads - 1) / FcgUpdV4K<TI>::kThreads);
+            return launch_k(FcgUpdV4K<TI>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdV4K<TI>::kThreads), 0, s);
+        }
+    }
+    cudaError_t err = launch_k(FcgDotK<TI>{L, z, r, dp, partials, st}, grid3(L), kBlock3, 0, s);
+    if (err != cudaSuccess) return err;
+    return launch_k(FcgUpdK<TI>{L, z, dp, p, st}, grid3(L), kBlock3, 0, s);
+}
+
+cudaError_t launch_fcg(int inner, const LevelDev& L, const void* z, const void* r, void* dp, double* p,
+                       double* partials, SolveState* st, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH_I(inner, err = fcg_launch<TI>(L, (const TI*)z, (const TI*)r, (TI*)dp, p, partials, st, s));
     return err;
 }
 

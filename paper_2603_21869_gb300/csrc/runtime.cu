@@ -300,6 +300,8 @@ struct fvm_case {
     double* staging = nullptr;
     double* Ainv = nullptr;
     double* p_tmp = nullptr;         // the paper's scheme: Jacobi on p out of place
+    void* kdir = nullptr;            // flexible CG (krylov = 1): the kept direction (level 0, inner
+    double* kpart = nullptr;         //   precision) and four partial sums per level-0 block
     void* nut = nullptr;             // nu_t of the state after a destruction half step
     bool nut_valid = false;          // nut matches the current k, omega
     std::vector<DevLevel> levels;
@@ -381,6 +383,8 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->inner_cycles < 0 || d->inner_cycles > 16) return fail(FVM_ERR_INVALID, "inner_cycles must be 0..16");
     if (d->sweep_planes < 0 || d->sweep_planes > 64) return fail(FVM_ERR_INVALID, "sweep_planes must be 0..64");
     if (d->mg_variant < 0 || d->mg_variant > 1) return fail(FVM_ERR_INVALID, "mg_variant must be 0 or 1");
+    if (d->krylov < 0 || d->krylov > 1) return fail(FVM_ERR_INVALID, "krylov must be 0 or 1");
+    if (d->krylov == 1 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "krylov 1 needs mg_variant 0");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -521,6 +525,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     const int64_t nc = pl.levels.back().N();
     bytes += nc * nc * 8;
     if (d->mg_variant == 1) bytes += N * 8;
+    if (d->krylov == 1) bytes += N * si + (int64_t)4 * fcg_blocks(n[0], n[1], n[2]) * 8;
     bytes += (int64_t)(2 * resid0_blocks(n[0], n[1], n[2]) + 16) * 8 + 256;
     pl.bytes = bytes;
     return FVM_OK;
@@ -665,6 +670,18 @@ fvm_status paper_cycle(fvm_case* c) {
     return FVM_OK;
 }
 
+// Flexible CG with one kept direction: z = the level-0 correction in e[zi]
+// (the V-cycles' result for the residual r), made A-orthogonal to the kept
+// direction, then the step minimising the error's A-norm along it.
+fvm_status krylov_step(fvm_case* c, int zi) {
+    DevLevel& L = c->levels[0];
+    const double N = (double)L.dev.N;
+    const double si = (double)elem_size(c->inner);
+    KLAUNCH("fcg_L0", N * (6 * si + 20), 2,
+            launch_fcg(c->inner, L.dev, L.e[zi], L.r, c->kdir, c->p, c->kpart, c->sst, c->stream));
+    return FVM_OK;
+}
+
 // One V-cycle of the correction equation on levels l.. with r on level l;
 // returns the index of the e buffer holding the level's correction.  On
 // level 0 the final post-smoothing sweep adds the correction to p instead.
@@ -723,12 +740,13 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
             cur ^= 1;
             int ci = 0;
             ST_TRY(cycle(c, l + 1, ci));
-            const bool top = l == 0 && rep == reps - 1;
+            const bool top = l == 0 && rep == reps - 1 && !c->desc.krylov;
             KLAUNCH(lvl_name(top ? "up_tma_to_p" : "up_tma", l), N * (3 * si + 2 + (top ? 16 : 0)) + Nc * si, 1,
                     launch_up_tma(c->desc.post_sweeps, top, L.maps, cur, ci, L.dev, Lc.dev, L.e[cur ^ 1], c->p,
                                   c->sst, s));
             if (!top) cur ^= 1;
         }
+        if (l == 0 && c->desc.krylov) ST_TRY(krylov_step(c, cur));
         out_idx = cur;
         return FVM_OK;
     }
@@ -756,7 +774,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
         KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + 2 * N, 1,
                 launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], c->sst, s));
         for (int k = 0; k < c->desc.post_sweeps; ++k) {
-            if (l == 0 && rep == reps - 1 && k == c->desc.post_sweeps - 1) {
+            if (l == 0 && rep == reps - 1 && k == c->desc.post_sweeps - 1 && !c->desc.krylov) {
                 KLAUNCH("sweep_to_p_L0", 2 * N * si + 16 * N + 2 * N, 1,
                         launch_sweep_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, c->sst, s));
             } else {
@@ -766,6 +784,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
             }
         }
     }
+    if (l == 0 && c->desc.krylov) ST_TRY(krylov_step(c, cur));
     out_idx = cur;
     return FVM_OK;
 }
@@ -1329,6 +1348,11 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
     c->nblocks0 = resid0_blocks(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
+    if (d.krylov == 1) {
+        const size_t si0 = elem_size(pl.inner);
+        ST_TRY(dalloc(c, &c->kdir, (size_t)N * si0));
+        ST_TRY(dalloc(c, (void**)&c->kpart, (size_t)4 * fcg_blocks(L0.n[0], L0.n[1], L0.n[2]) * 8));
+    }
     ST_TRY(dalloc(c, (void**)&c->norms, 4 * 8));
     ST_TRY(dalloc(c, (void**)&c->dt_state, 6 * 8));
     ST_TRY(dalloc(c, (void**)&c->sst, sizeof(SolveState)));

@@ -22,8 +22,10 @@ def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
     spec = cases.heated_channel_3d(128, 32, 32, mg_levels=4, precision=cases.FP32, mg_rel_tol=1e-8,
                                    max_vcycles=40)
     tuned, info = binding.autotune(spec, steps=3)
-    assert info["candidates"] == 3 * 4 + 6 and info["ms_per_step"] > 0
-    assert info["pre_sweeps"] == info["post_sweeps"] in (2, 3, 4)
+    # pass 1: nu in {2, 3, 4} x inner in {1..4} x krylov in {0, 1}; pass 2: six plane counts
+    assert info["candidates"] == 3 * 4 * 2 + 6 and info["ms_per_step"] > 0
+    assert info["pre_sweeps"] == info["post_sweeps"] in (2, 3, 4) and info["krylov"] in (0, 1)
+    assert tuned.krylov == info["krylov"]
     assert 1 <= info["inner_cycles"] <= 4 and info["sweep_planes"] in (0, 1, 2, 4, 8, 16, 32)
     with binding.Case(tuned) as c:
         st = c.step(4)
@@ -32,6 +34,14 @@ def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
     o = OracleCase(spec.replace(precision=cases.FP64)).step(4)
     for f in ("u", "v", "w", "T", "k", "omega"):
         assert rel(got[f], o.fields()[f]) <= 1e-4, f
+
+
+def test_paper_scheme_is_tuned_without_the_krylov_acceleration():
+    """mg_variant 1 admits no flexible-CG candidates (the descriptor would be rejected)."""
+    spec = cases.heated_channel_3d(64, 16, 16, mg_levels=4, precision=cases.FP32, mg_variant=1,
+                                   mg_rel_tol=2e-2, max_vcycles=100)   # the scheme stalls near 5e-4 here
+    tuned, info = binding.autotune(spec, steps=2)
+    assert info["candidates"] == 3 * 4 + 6 and info["krylov"] == 0 and tuned.mg_variant == 1
 
 
 def test_planes_per_block_do_not_change_the_result():

@@ -1,0 +1,167 @@
+"""Flexible CG with one kept direction around the V-cycles (krylov = 1)
+against the oracle's: FP64 fields within 1e-10, the same residuals and
+iteration counts; alone, in graph and launch modes, batched, and with
+reduced-precision corrections."""
+import numpy as np
+import pytest
+
+from oracle.step import OracleCase
+from paper_2603_21869_gb300 import binding, build, cases
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.ensure_built()
+    binding.lib()
+
+
+def rel_err(a, b):
+    scale = np.max(np.abs(b))
+    if scale == 0.0:
+        return float(np.max(np.abs(a)))
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+def room_small(precision=cases.FP64, **kw):
+    return cases.room_3d(64, 32, 32, seed=3, mg_levels=4, h=0.08, precision=precision, krylov=1, **kw)
+
+
+def channel_box(precision=cases.FP64, **kw):
+    spec = cases.heated_channel_3d(48, 16, 16, mg_levels=3, precision=precision, init_perturb=0.02, krylov=1,
+                                   boxes=[cases.Box(10, 16, 4, 10, 0, 7, thermal=cases.HEAT_FLUX, T_value=150.0)])
+    return spec.replace(**kw)
+
+
+SPECS = {
+    "channel3d_box": lambda: channel_box(fixed_vcycles=4),
+    "room_buoyant": lambda: room_small(fixed_vcycles=4),
+    "channel2d_ragged": lambda: cases.channel_2d(48, 20, 3, fixed_vcycles=4, init_perturb=0.05, krylov=1),
+}
+
+
+@pytest.mark.parametrize("name", list(SPECS))
+def test_fcg_steps_match_oracle(name):
+    spec = SPECS[name]()
+    with binding.Case(spec) as c:
+        st = c.step(2)
+        got = c.read()
+    o = OracleCase(spec).step(2)
+    assert st["vcycles_total"] == 2 * spec.fixed_vcycles
+    assert st["rel_residual"] == pytest.approx(o.last_rel, rel=1e-6)
+    for f in cases.FIELDS:
+        assert rel_err(got[f], o.fields()[f]) <= TOL64, f
+
+
+def test_fcg_iterations_alone_match_oracle():
+    """fvm_vcycle(n) is one flexible-CG solve of n iterations from the given p."""
+    spec = room_small(fixed_vcycles=1)
+    o = OracleCase(spec)
+    lev = o.mg.levels[0]
+    b = np.where(lev.fluid, np.random.default_rng(5).normal(size=lev.shape), 0.0)
+    p0 = np.where(lev.fluid, np.random.default_rng(6).normal(size=lev.shape), 0.0)
+    with binding.Case(spec) as c:
+        c.set_rhs(b)
+        for n in (1, 2, 6):
+            c.write({"p": p0})
+            rel = c.vcycle(n)
+            p, k, orel = o.mg.fcg_solve(p0.copy(), b, 0, 0.0, n)
+            assert k == n
+            assert rel_err(c.read(("p",))["p"], p) <= TOL64, n
+            assert rel == pytest.approx(orel, rel=1e-6), n
+
+
+def test_fcg_adaptive_counts_track_oracle_and_beat_plain_vcycles():
+    spec = room_small(mg_rel_tol=1e-8, max_vcycles=60)
+    counts = {}
+    for kry in (0, 1):
+        s = spec.replace(krylov=kry)
+        with binding.Case(s) as c:
+            cyc = [c.step(1)["vcycles_last"] for _ in range(3)]
+            got = c.read()
+        o = OracleCase(s)
+        ocyc = []
+        for _ in range(3):
+            o.step()
+            ocyc.append(o.last_vcycles)
+        assert all(abs(a - b) <= 1 for a, b in zip(cyc, ocyc)), (kry, cyc, ocyc)
+        for f in cases.FIELDS:
+            assert rel_err(got[f], o.fields()[f]) <= 1e-7, (kry, f)
+        counts[kry] = sum(cyc)
+    assert counts[1] < counts[0], counts
+
+
+@pytest.mark.parametrize("prec", [cases.FP64, cases.FP32])
+def test_fcg_graph_and_launch_paths_agree_bitwise(prec):
+    spec = channel_box(precision=prec, fixed_vcycles=0, mg_rel_tol=1e-8, max_vcycles=40)
+    out = []
+    for graph in (True, False):
+        with binding.Case(spec) as c:
+            c.set_graph(graph)
+            st = c.step(3)
+            out.append((st, c.read()))
+    (s1, f1), (s2, f2) = out
+    assert s1["vcycles_total"] == s2["vcycles_total"] and s1["rel_residual"] == s2["rel_residual"]
+    for f in cases.FIELDS:
+        assert np.array_equal(f1[f], f2[f]), f
+
+
+@pytest.mark.parametrize("prec", [cases.FP32, cases.BF16_MIXED], ids=["fp32", "bf16"])
+def test_fcg_reduced_precision_within_1e4_of_fp64_oracle(prec):
+    spec = room_small(precision=prec, mg_rel_tol=1e-8, max_vcycles=40)
+    with binding.Case(spec) as c:
+        st = c.step(8)
+        got = c.read()
+    assert st["rel_residual"] <= 1e-8
+    o = OracleCase(spec.replace(precision=cases.FP64, krylov=0)).step(8)
+    for f in ("u", "v", "w", "T", "k", "omega"):
+        assert rel_err(got[f], o.fields()[f]) <= 1e-4, f
+
+
+def test_fcg_batched_with_plain_cases_equals_each_alone():
+    """A batch mixing flexible-CG and plain cases: each case as it is stepped alone."""
+    specs = [channel_box(mg_rel_tol=1e-8, max_vcycles=40),
+             cases.heated_channel_3d(64, 16, 16, mg_levels=4, mg_rel_tol=1e-8, max_vcycles=40),
+             room_small(mg_rel_tol=1e-8, max_vcycles=40)]
+    alone, alone_st = [], []
+    for s in specs:
+        with binding.Case(s) as c:
+            alone_st.append(c.step(3))
+            alone.append(c.read())
+    cs = [binding.Case(s) for s in specs]
+    try:
+        with binding.Batch(cs) as b:
+            st = b.step(3)
+        got = [c.read() for c in cs]
+    finally:
+        for c in cs:
+            c.close()
+    for i in range(len(specs)):
+        assert st[i]["vcycles_total"] == alone_st[i]["vcycles_total"], i
+        for f in cases.FIELDS:
+            assert rel_err(got[i][f], alone[i][f]) <= 1e-12, (i, f)
+
+
+@pytest.mark.parametrize("prec", [cases.FP32, cases.BF16_MIXED], ids=["fp32", "bf16"])
+def test_fcg_four_cell_kernels_in_a_batch_within_1e4_of_fp64_oracle(prec):
+    """In a batch the reduced-precision path takes the four-cells-per-thread
+    kernels (FP32 products and thread sums): each case converges and stays
+    within 1e-4 of the FP64 oracle."""
+    specs = [room_small(precision=prec, mg_rel_tol=1e-8, max_vcycles=40),
+             channel_box(precision=prec, mg_rel_tol=1e-8, max_vcycles=40)]
+    cs = [binding.Case(s) for s in specs]
+    try:
+        with binding.Batch(cs) as b:
+            st = b.step(6)
+        got = [c.read() for c in cs]
+    finally:
+        for c in cs:
+            c.close()
+    for i, s in enumerate(specs):
+        assert st[i]["rel_residual"] <= 1e-8, i
+        o = OracleCase(s.replace(precision=cases.FP64, krylov=0)).step(6)
+        for f in ("u", "v", "w", "T", "k", "omega"):
+            assert rel_err(got[i][f], o.fields()[f]) <= 1e-4, (i, f)

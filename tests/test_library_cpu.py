@@ -75,6 +75,8 @@ def test_case_bytes_scale_with_precision(lib):
     assert b64 > 100 * N and b32 < b64
     # full 3D channel workload (1M cells) in FP32 stays well under 200 MB
     assert binding.case_bytes(cases.heated_channel_3d(precision=cases.FP32)) < 200e6
+    # flexible CG keeps one more level-0 vector in the inner precision
+    assert binding.case_bytes(s32.replace(krylov=1)) >= b32 + 4 * N
 
 
 @pytest.mark.parametrize("bad", [
@@ -87,6 +89,9 @@ def test_case_bytes_scale_with_precision(lib):
     dict(vents=[cases.Vent(face=2, a0=0, a1=200, b0=0, b1=2, bc=cases.Patch(cases.OUTLET))]),
     dict(faces=[cases.Patch(cases.INLET, u_normal=1.0, intensity=0.05, length_scale=0.1)] + [cases.Patch()] * 5),
     dict(nz=1),
+    dict(krylov=2),
+    dict(krylov=1, mg_variant=1),
+    dict(mg_variant=2),
 ])
 def test_invalid_descriptors_are_rejected_without_a_gpu(lib, bad):
     spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3).replace(**bad)
