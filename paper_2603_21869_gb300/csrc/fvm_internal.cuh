@@ -75,6 +75,65 @@ template <class C> __device__ __forceinline__ C prm(double d, float f);
 template <> __device__ __forceinline__ double prm<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float prm<float>(double, float f) { return f; }
 
+// Double-float values: FP64 quantities handled without the FP64 pipe (1/64
+// of the FP32 rate on this part).  ff_split takes a double apart exactly by
+// integer operations into hi = its sign, exponent and leading 24 mantissa
+// bits and lo = the next 24 bits (about 2^-47 relative); ff_add / ff_mul are
+// Dekker's error-free sum and the FMA-based product, renormalised.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ FF ff_norm(float h, float l) {
+    const float s = h + l;
+    return {s, l - (s - h)};
+}
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.h, y.h);
+    return ff_norm(s.h, s.l + (x.l + y.l));
+}
+
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.h, -x.l}; }
+
+__device__ __forceinline__ FF ff_mul(FF x, FF c) {
+    const float p = x.h * c.h;
+    float e = fmaf(x.h, c.h, -p);
+    e = fmaf(x.h, c.l, e);
+    e = fmaf(x.l, c.h, e);
+    return ff_norm(p, e);
+}
+
+// exact split of a double (|p| in [2^-126, 2^128); smaller values give 0,
+// larger ones and non-finite values go through the FP64 conversion)
+__device__ __forceinline__ FF ff_split(double p) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(p);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    const unsigned sign = hw & 0x80000000u;
+    if (ex > 1150) return {__double2float_rn(p), 0.0f};
+    if (ex < 897) return {0.0f, 0.0f};
+    const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    float lo = 0.0f;
+    if (ex >= 949) {   // lo = (the low 29 mantissa bits) * 2^(ex - 1075), sign of p
+        const float scale = __uint_as_float((unsigned)(ex - 948) << 23);
+        lo = __uint_as_float(__float_as_uint(__uint2float_rz(lw & 0x1fffffffu) * scale) | sign);
+    }
+    return {hi, lo};
+}
+
+// x - y rounded to FP32
+__device__ __forceinline__ float ff_diff(FF x, FF y) {
+    const FF s = ff_two_sum(x.h, -y.h);
+    return s.h + (s.l + (x.l - y.l));
+}
+
 // One multigrid level (pressure-like fields).
 struct LevelDev {
     int32_t n[3];
@@ -87,6 +146,7 @@ struct LevelDev {
     float inv_h2f[3], inv_Df, wJf, diagf;   // FP32 copies (no FP64-pipe conversions in FP32 kernels)
     double ih2a[3];          // inv_h2 on active axes, 0 on a collapsed axis
     float ih2af[3];
+    float ih2alo[3];         // ih2a - ih2af (float-float coefficients)
     int32_t zc_fixed;        // z planes per block of the four-cell kernels (0: the rule)
     const uint8_t* solid;    // nonzero = solid
     const uint8_t* dir[6];   // per boundary-face cell: 1 = Dirichlet (p = 0 on the face)
@@ -243,7 +303,7 @@ cudaError_t prepare_coarse_cta(int inner, size_t smem);
 // flexible CG with one kept direction around the V-cycles: the inner products
 // of z (the V-cycles' correction) with A z, r and the kept direction d_prev
 // (last block: beta, alpha), then d = z - beta d_prev, p += alpha d, d kept.
-// partials: 4 doubles per block, fcg_blocks(n) blocks at most.
+// partials: 4 doubles per block, level0_blocks_max(n) blocks at most.
 cudaError_t launch_fcg(int inner, const LevelDev& L, const void* z, const void* r, void* dp, double* p,
                        double* partials, SolveState* st, cudaStream_t s);
 // the paper's scheme (Algorithm 1)
@@ -265,7 +325,7 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
                               const SolveState* st, cudaStream_t s);
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
 int resid0_blocks(int nx, int ny, int nz);
-int fcg_blocks(int nx, int ny, int nz);   // blocks of a flexible-CG inner-product pass, at most
+int level0_blocks_max(int nx, int ny, int nz);   // blocks of any level-0 reduction pass, at most
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner);
 // cluster kernel (mg_cluster.cu)
 size_t cluster_smem_bytes(const ClusterLevels& cl, int inner);

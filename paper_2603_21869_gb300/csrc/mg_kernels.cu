@@ -108,6 +108,58 @@ __device__ __forceinline__ C A7(const LevelDev& L, uint32_t f, C eP, C xm, C xp,
 }
 
 // ------------------------------------------------------------------ level 0 residual
+// The last block of a level-0 residual pass: a fixed-order reduction over
+// all blocks' partials (r^2, b^2): thread t sums blocks t, t + NT, ... in
+// order (L2 loads, independent), then a fixed shuffle tree and a fixed sum
+// over warps, so the result is deterministic; then the stopping rule.
+// Returns the decision in thread 0, -1 elsewhere.  Out of line: it runs once
+// per launch and would otherwise hold registers in every block.
+template <int NT>
+__device__ __noinline__ int resid0_finish(const double* partials, int nblk, SolveState* st,
+                                          double (*red)[NT / 32]) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    double a0 = 0.0, a1 = 0.0;
+    for (int x = tid; x < nblk; x += NT) {
+        const double2 v = __ldcg((const double2*)partials + x);
+        a0 += v.x;
+        a1 += v.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a0;
+        red[1][tid >> 5] = a1;
+    }
+    __syncthreads();
+    if (tid != 0) return -1;
+    a0 = 0.0;
+    a1 = 0.0;
+    for (int w = 0; w < NT / 32; ++w) {
+        a0 += red[0][w];
+        a1 += red[1][w];
+    }
+    st->counter = 0u;
+    st->r2 = a0;
+    st->b2 = a1;
+    const bool finite = isfinite(a0) && isfinite(a1);
+    const double rel = a1 > 0.0 ? sqrt(a0 / a1) : 0.0;
+    st->rel = finite ? rel : __longlong_as_double(0x7ff8000000000000ll);
+    if (!finite) st->nonfinite = 1;
+    int go;
+    if (st->fixed > 0) go = st->cycles < st->fixed;
+    else go = finite && rel > st->tol && st->cycles < st->max_cycles;
+    st->active = go;
+    if (!go && st->fixed == 0 && finite && rel > st->tol) st->notconv = 1;
+    if (go) {
+        st->cycles += st->inner;
+        st->total_cycles += st->inner;
+    }
+    return go;
+}
+
 // r = b - A p (FP64), first pre-sweep e = w_J r / D, r^2 and b^2 per block;
 // the last block sums the partials in a fixed order and applies the stopping rule.
 // run() returns the decision (0 / 1) in the thread that made it, else -1.
@@ -185,52 +237,7 @@ __device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
     __syncthreads();
     if (!last) return -1;
     __threadfence();
-    // fixed-order reduction over all blocks' partials by the whole last block:
-    // thread t sums blocks t, t + 256, ... in order (L2 loads, independent), then a
-    // fixed shuffle tree and a fixed sum over warps -> deterministic
-    constexpr int NT = BX * BY * BZ;
-    double a0 = 0.0, a1 = 0.0;
-    for (int x = tid; x < nblk; x += NT) {
-        const double2 v = __ldcg((const double2*)partials + x);
-        a0 += v.x;
-        a1 += v.y;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-    }
-    __syncthreads();
-    if ((tid & 31) == 0) {
-        red[0][tid >> 5] = a0;
-        red[1][tid >> 5] = a1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        a0 = 0.0;
-        a1 = 0.0;
-        for (int w = 0; w < NT / 32; ++w) {
-            a0 += red[0][w];
-            a1 += red[1][w];
-        }
-        st->counter = 0u;
-        st->r2 = a0;
-        st->b2 = a1;
-        const bool finite = isfinite(a0) && isfinite(a1);
-        const double rel = a1 > 0.0 ? sqrt(a0 / a1) : 0.0;
-        st->rel = finite ? rel : __longlong_as_double(0x7ff8000000000000ll);
-        if (!finite) st->nonfinite = 1;
-        int go;
-        if (st->fixed > 0) go = st->cycles < st->fixed;
-        else go = finite && rel > st->tol && st->cycles < st->max_cycles;
-        st->active = go;
-        if (!go && st->fixed == 0 && finite && rel > st->tol) st->notconv = 1;
-        if (go) {
-            st->cycles += st->inner;
-            st->total_cycles += st->inner;
-        }
-        return go;
-    }
-    return -1;
+    return resid0_finish<BX * BY * BZ>(partials, nblk, st, red);
 }
 
 struct SolveBeginK {
@@ -630,6 +637,156 @@ __device__ __forceinline__ void fcg_reduce(double (&s)[4], double* partials, Sol
     if (!last) return;
     __threadfence();
     fcg_finish<NT>(partials, nblk, st, have, red);
+}
+
+// ------------------------------------------------------------------ level 0 residual in float-float
+// p is held in FP64; this path evaluates r = b - A p without the FP64 pipe
+// (1/64 of the FP32 rate here): each p value is split exactly by integer
+// operations into hi = its sign, exponent and leading 24 mantissa bits and
+// lo = the next 24 bits, and the stencil runs in double-float arithmetic
+// (Dekker's error-free sum and FMA-based product), about 2^-48 relative
+// accuracy.  As a difference form, A p = sum_a ih2_a ((P - g_lo) + (P - g_hi))
+// with g the neighbour (code 0), P (zero-gradient: no term) or -P
+// (zero-value: 2P), which equals both branches of A7.
+__device__ __forceinline__ void ff_load4(const double* p, int c, FF (&o)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p + c));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p + c) + 1);
+    o[0] = ff_split(a.x);
+    o[1] = ff_split(a.y);
+    o[2] = ff_split(b.x);
+    o[3] = ff_split(b.y);
+}
+
+// P - ghost across one face: the neighbour (code 0), none (1) or 2P (2)
+__device__ __forceinline__ FF ff_face(uint32_t code, FF P, FF nb) {
+    const FF d = ff_add(P, ff_neg(nb));
+    if (code == 0u) return d;
+    if (code == 1u) return {0.0f, 0.0f};
+    return {2.0f * P.h, 2.0f * P.l};
+}
+
+template <class TI> __device__ __forceinline__ float round_inner(float v) { return v; }
+template <> __device__ __forceinline__ float round_inner<__nv_bfloat16>(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// r = b - A p (float-float), r^2 and b^2, the first pre-sweep e = w_J r / D;
+// four x cells per thread and a z march (the sweep's layout).  FP32 b, nx % 4 = 0.
+template <class TI>
+struct Resid0V4K {
+    static constexpr int kThreads = TX * TY;
+    static constexpr int kMinBlocks = 2;
+    LevelDev L;
+    const double* p;
+    const float* b;
+    TI* r;
+    TI* e;
+    double* partials;
+    SolveState* st;
+    int zc;   // planes per block
+    __device__ bool live() const { return st->active != 0; }
+    __device__ int run(const BlockAt& at) const;
+};
+
+template <class TI>
+__device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int lane = threadIdx.x;
+    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
+    const bool in = i4 < nx && j < ny;
+    const int sy = nx, sz = nx * ny;
+    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
+    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
+    const bool lastc = i4 + 4 >= nx;
+    const FF ihx = {L.ih2af[0], L.ih2alo[0]}, ihy = {L.ih2af[1], L.ih2alo[1]}, ihz = {L.ih2af[2], L.ih2alo[2]};
+    const float wJ = LP<float>::wJ(L), iD = LP<float>::iD(L);
+    const double* const pp = this->p;
+    const uint16_t* const nbf = L.nbf;
+    FF em[4], ec[4], ep[4];
+    ff_load4(pp, max(k0 - 1, 0) * sz + own, em);
+    ff_load4(pp, k0 * sz + own, ec);
+    ff_load4(pp, min(k0 + 1, nz - 1) * sz + own, ep);
+    float r2 = 0.0f, b2 = 0.0f;
+    for (int k = k0; k < k1; ++k) {
+        const int base = k * sz;
+        FF ym[4], yp[4], en[4];
+        ff_load4(pp, base + om, ym);
+        ff_load4(pp, base + op, yp);
+        const float4 bq = __ldg(reinterpret_cast<const float4*>(b + base + own));
+        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
+        const FF xls = lane == 0 ? ff_split(__ldg(pp + base + xl)) : FF{0.0f, 0.0f};
+        const FF xrs = lane == TX - 1 ? ff_split(__ldg(pp + base + xr)) : FF{0.0f, 0.0f};
+        ff_load4(pp, min(k + 2, nz - 1) * sz + own, en);
+        FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1), __shfl_up_sync(0xffffffffu, ec[3].l, 1)};
+        FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1), __shfl_down_sync(0xffffffffu, ec[0].l, 1)};
+        if (lane == 0) left = xls;
+        if (lane == TX - 1) right = xrs;
+        if (lastc) right = ec[3];
+        const FF xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
+        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+        const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
+        float rv[4], ev[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t f = fs[t];
+            const FF P = xs[t + 1];
+            const FF ax = ff_mul(ff_add(ff_face(f & 3u, P, xs[t]), ff_face((f >> 2) & 3u, P, xs[t + 2])), ihx);
+            const FF ay = ff_mul(ff_add(ff_face((f >> 4) & 3u, P, ym[t]), ff_face((f >> 6) & 3u, P, yp[t])), ihy);
+            const FF az = ff_mul(ff_add(ff_face((f >> 8) & 3u, P, em[t]), ff_face((f >> 10) & 3u, P, ep[t])), ihz);
+            const FF A = ff_add(ff_add(ax, ay), az);
+            const FF rr = ff_add(FF{bb[t], 0.0f}, ff_neg(A));
+            const bool fluid = !is_solid(f);
+            const float rc = fluid ? round_inner<TI>(rr.h + rr.l) : 0.0f;
+            rv[t] = rc;
+            ev[t] = wJ * rc * iD;
+            if (in) {
+                r2 = fmaf(rc, rc, r2);
+                if (fluid) b2 = fmaf(bb[t], bb[t], b2);
+            }
+        }
+        if (in) {
+            Vec4<TI>::store(r, base + own, rv);
+            Vec4<TI>::store(e, base + own, ev);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            em[t] = ec[t];
+            ec[t] = ep[t];
+            ep[t] = en[t];
+        }
+    }
+    // block sums in FP64, then the last block's fixed-order reduction and the stopping rule
+    __shared__ double red[2][kThreads / 32];
+    __shared__ bool last;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    double s0 = (double)r2, s1 = (double)b2;
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = s0;
+        red[1][tid >> 5] = s1;
+    }
+    __syncthreads();
+    const int nblk = at.g.x * at.g.y * at.g.z;
+    if (tid == 0) {
+        const int bid = at.b.x + at.g.x * (at.b.y + at.g.y * at.b.z);
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            a0 += red[0][w];
+            a1 += red[1][w];
+        }
+        reinterpret_cast<double2*>(partials)[bid] = make_double2(a0, a1);
+        __threadfence();
+        last = atomicAdd(&st->counter, 1u) == (unsigned)nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return -1;
+    __threadfence();
+    return resid0_finish<kThreads>(partials, nblk, st, red);
 }
 
 // The flexible-CG inner products with four x cells per thread and a z march
@@ -1522,8 +1679,8 @@ int resid0_blocks(int nx, int ny, int nz) {
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + BZ - 1) / BZ);
 }
 
-int fcg_blocks(int nx, int ny, int nz) {
-    const int four = ((nx + V4X - 1) / V4X) * ((ny + TY - 1) / TY) * nz;   // the four-cell pass, one plane a block
+int level0_blocks_max(int nx, int ny, int nz) {
+    const int four = ((nx + V4X - 1) / V4X) * ((ny + TY - 1) / TY) * nz;   // a four-cell pass, one plane a block
     const int r0 = resid0_blocks(nx, ny, nz);
     return four > r0 ? four : r0;
 }
@@ -1549,11 +1706,25 @@ cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
     return launch_k(SolveBeginK{st}, dim3(1), dim3(1), 0, s);
 }
 
+static int sweep_planes(int tiles, int nz, int fixed);
+
 cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
                           double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                           cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     DISPATCH_I(inner, {
+        if constexpr (sizeof(TI) < 8) {
+            // four cells per thread in float-float on large levels and in batches
+            if (bprec == FVM_FP32 && L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
+                const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
+                const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
+                const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
+                                (unsigned)((L.n[2] + zc - 1) / zc));
+                // (at most level0_blocks_max(n) blocks: partials has room)
+                return launch_r0(Resid0V4K<TI>{L, p, (const float*)b, (TI*)r, (TI*)e, partials, st, zc}, grid,
+                                 dim3(TX, TY), cond, cond2, use_cond, s);
+            }
+        }
         if (bprec == FVM_FP64)
             err = launch_r0(Resid0K<double, TI>{L, p, (const double*)b, (TI*)r, (TI*)e, partials, st}, grid3(L),
                             kBlock3, cond, cond2, use_cond, s);
@@ -1692,7 +1863,7 @@ static cudaError_t fcg_launch(const LevelDev& L, const TI* z, const TI* r, TI* d
             const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
             const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
                             (unsigned)((L.n[2] + zc - 1) / zc));
-            // (at most fcg_blocks(n) blocks: partials has room)
+            // (at most level0_blocks_max(n) blocks: partials has room)
             cudaError_t err = launch_k(FcgDotV4K<TI>{L, z, r, dp, partials, st, zc}, grid, dim3(TX, TY), 0, s);
             if (err != cudaSuccess) return err;
             const unsigned nb = (unsigned)((L.N / 4 + FcgUpdV4K<TI>::kThreads - 1) / FcgUpdV4K<TI>::kThreads);

@@ -525,8 +525,8 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     const int64_t nc = pl.levels.back().N();
     bytes += nc * nc * 8;
     if (d->mg_variant == 1) bytes += N * 8;
-    if (d->krylov == 1) bytes += N * si + (int64_t)4 * fcg_blocks(n[0], n[1], n[2]) * 8;
-    bytes += (int64_t)(2 * resid0_blocks(n[0], n[1], n[2]) + 16) * 8 + 256;
+    if (d->krylov == 1) bytes += N * si + (int64_t)4 * level0_blocks_max(n[0], n[1], n[2]) * 8;
+    bytes += (int64_t)(2 * level0_blocks_max(n[0], n[1], n[2]) + 16) * 8 + 256;
     pl.bytes = bytes;
     return FVM_OK;
 }
@@ -1154,6 +1154,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             v.inv_h2f[a] = (float)v.inv_h2[a];
             v.ih2a[a] = H.active[a] ? v.inv_h2[a] : 0.0;
             v.ih2af[a] = (float)v.ih2a[a];
+            v.ih2alo[a] = (float)(v.ih2a[a] - (double)v.ih2af[a]);
         }
         v.inv_Df = (float)v.inv_D;
         v.wJf = (float)v.wJ;
@@ -1334,6 +1335,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
                 v.inv_h2f[a] = f0.inv_h2f[a];
                 v.ih2a[a] = v.active[a] ? f0.inv_h2[a] : 0.0;
                 v.ih2af[a] = (float)v.ih2a[a];
+                v.ih2alo[a] = (float)(v.ih2a[a] - (double)v.ih2af[a]);
             }
             v.diag = f0.diag;
             v.diagf = f0.diagf;
@@ -1346,12 +1348,12 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 8));
     if (d.mg_variant == 1) ST_TRY(dalloc(c, (void**)&c->p_tmp, (size_t)N * 8));
     CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    c->nblocks0 = resid0_blocks(L0.n[0], L0.n[1], L0.n[2]);
+    c->nblocks0 = level0_blocks_max(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
     if (d.krylov == 1) {
         const size_t si0 = elem_size(pl.inner);
         ST_TRY(dalloc(c, &c->kdir, (size_t)N * si0));
-        ST_TRY(dalloc(c, (void**)&c->kpart, (size_t)4 * fcg_blocks(L0.n[0], L0.n[1], L0.n[2]) * 8));
+        ST_TRY(dalloc(c, (void**)&c->kpart, (size_t)4 * level0_blocks_max(L0.n[0], L0.n[1], L0.n[2]) * 8));
     }
     ST_TRY(dalloc(c, (void**)&c->norms, 4 * 8));
     ST_TRY(dalloc(c, (void**)&c->dt_state, 6 * 8));

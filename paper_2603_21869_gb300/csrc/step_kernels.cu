@@ -482,6 +482,16 @@ __device__ __forceinline__ double p_across(const LevelDev& L, const double* p, u
     return __ldg(p + c + side * stride);
 }
 
+// the same in float-float (P: the cell's own value, split)
+__device__ __forceinline__ FF p_across_ff(const LevelDev& L, const double* p, uint32_t f, int c, int a, int side,
+                                          FF P) {
+    const uint32_t code = (f >> (2 * (2 * a + (side > 0 ? 1 : 0)))) & 3u;
+    if (code == 1u) return P;
+    if (code == 2u) return FF{-P.h, -P.l};
+    const int stride = a == 0 ? 1 : (a == 1 ? L.n[0] : L.n[0] * L.n[1]);
+    return ff_split(__ldg(p + c + side * stride));
+}
+
 template <class S, class C>
 struct ProjectK {
     static constexpr int kThreads = BX * BY * BZ;
@@ -508,16 +518,31 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
     const double pP = __ldg(p + c);
     const uint32_t f = L0.nbf[c];
     const C dt = dt_of<C>(dt_state, 0);
-    for (int a = 0; a < 3; ++a) {
-        C g = (C)0;
-        if (cd.active[a]) {
-            // differences of the FP64 pressure are taken in FP64, then rounded
-            const double pl = p_across(L0, p, f, c, a, -1, pP);
-            const double pr = p_across(L0, p, f, c, a, +1, pP);
-            const double ih = cd.inv_h[a];
-            g = (C)(0.5 * ((pr - pP) * ih + (pP - pl) * ih));
+    if constexpr (sizeof(C) == 8) {
+        for (int a = 0; a < 3; ++a) {
+            C g = (C)0;
+            if (cd.active[a]) {
+                // differences of the FP64 pressure are taken in FP64, then rounded
+                const double pl = p_across(L0, p, f, c, a, -1, pP);
+                const double pr = p_across(L0, p, f, c, a, +1, pP);
+                const double ih = cd.inv_h[a];
+                g = (C)(0.5 * ((pr - pP) * ih + (pP - pl) * ih));
+            }
+            o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
         }
-        o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
+    } else {
+        // FP32 fields: the FP64 pressure differences in float-float, rounded once
+        const FF P = ff_split(pP);
+        for (int a = 0; a < 3; ++a) {
+            C g = (C)0;
+            if (cd.active[a]) {
+                const FF pl = p_across_ff(L0, p, f, c, a, -1, P);
+                const FF pr = p_across_ff(L0, p, f, c, a, +1, P);
+                const float ih = cd.f.inv_h[a];
+                g = 0.5f * (ff_diff(pr, P) * ih + ff_diff(P, pl) * ih);
+            }
+            o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
+        }
     }
 }
 
