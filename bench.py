@@ -442,6 +442,8 @@ def main():
     ap.add_argument("--accuracy-cases", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
+    ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
+                    help="flexible-CG acceleration of the pressure solve (auto: the autotuner's choice, else off)")
     ap.add_argument("--requests", type=int, default=64, help="served workload: requests per GPU")
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
@@ -482,6 +484,8 @@ def main():
         torch.cuda.set_device(local)
         spec, tuning = _b.autotune(spec, steps=3)
         label = label.replace("V(3,3)", f"V({spec.pre_sweeps},{spec.post_sweeps})")
+    if args.krylov != "auto":
+        spec = spec.replace(krylov=int(args.krylov))
     if args.impl == "reference":
         args.steps = min(args.steps, 2)
         args.warmup = min(args.warmup, 0)

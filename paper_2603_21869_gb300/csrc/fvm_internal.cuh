@@ -110,8 +110,11 @@ __device__ __forceinline__ FF ff_mul(FF x, FF c) {
     return ff_norm(p, e);
 }
 
-// exact split of a double (|p| in [2^-126, 2^128); smaller values give 0,
-// larger ones and non-finite values go through the FP64 conversion)
+// exact split of a double: hi = sign, exponent and leading 24 mantissa bits,
+// lo = the next 23 bits (the last 6 are dropped: about 2^-46 relative), by
+// integer operations and one FP32 subtraction (2^23 + m as a float's bits,
+// minus 2^23), so no conversion runs on the FP64 pipe.  |p| below 2^-126
+// gives 0; |p| at or above 2^128 and non-finite values take the FP64 path.
 __device__ __forceinline__ FF ff_split(double p) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(p);
     const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
@@ -121,9 +124,10 @@ __device__ __forceinline__ FF ff_split(double p) {
     if (ex < 897) return {0.0f, 0.0f};
     const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
     float lo = 0.0f;
-    if (ex >= 949) {   // lo = (the low 29 mantissa bits) * 2^(ex - 1075), sign of p
-        const float scale = __uint_as_float((unsigned)(ex - 948) << 23);
-        lo = __uint_as_float(__float_as_uint(__uint2float_rz(lw & 0x1fffffffu) * scale) | sign);
+    if (ex >= 943) {   // lo = (mantissa bits 28..6 of the low word) * 2^(ex - 1069), sign of p
+        const float m = __uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)) - 8388608.0f;
+        const float scale = __uint_as_float((unsigned)(ex - 942) << 23);
+        lo = __uint_as_float(__float_as_uint(m * scale) | sign);
     }
     return {hi, lo};
 }

@@ -610,8 +610,8 @@ __device__ __noinline__ void fcg_finish(const double* partials, int nblk, SolveS
 
 // the four sums of one block (each thread's in s) into partials; the last
 // block to finish completes the pass (fcg_finish)
-template <int NT>
-__device__ __forceinline__ void fcg_reduce(double (&s)[4], double* partials, SolveState* st, bool have,
+template <int NT, class T>
+__device__ __forceinline__ void fcg_reduce(T (&s)[4], double* partials, SolveState* st, bool have,
                                            const BlockAt& at) {
     __shared__ double red[4][NT / 32];
     __shared__ bool last;
@@ -620,7 +620,7 @@ __device__ __forceinline__ void fcg_reduce(double (&s)[4], double* partials, Sol
     for (int m = 0; m < 4; ++m)
         for (int off = 16; off > 0; off >>= 1) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
     if ((tid & 31) == 0)
-        for (int m = 0; m < 4; ++m) red[m][tid >> 5] = s[m];
+        for (int m = 0; m < 4; ++m) red[m][tid >> 5] = (double)s[m];
     __syncthreads();
     const int nblk = at.g.x * at.g.y * at.g.z;
     if (tid == 0) {
@@ -663,6 +663,45 @@ __device__ __forceinline__ FF ff_face(uint32_t code, FF P, FF nb) {
     if (code == 0u) return d;
     if (code == 1u) return {0.0f, 0.0f};
     return {2.0f * P.h, 2.0f * P.l};
+}
+
+// one axis of A p at a regular cell: ih (2P - a - b), the neighbours' sum and
+// the difference by error-free sums, the products' low parts by FMA; the
+// result is left unnormalised (its low part is small against the high part's
+// inputs, which is all the sums below need)
+__device__ __forceinline__ FF ff_axis(FF P, FF a, FF b, FF ih) {
+    const FF s = ff_two_sum(a.h, b.h);
+    const float sl = s.l + (a.l + b.l);
+    const FF d = ff_two_sum(2.0f * P.h, -s.h);
+    const float dl = d.l + (2.0f * P.l - sl);
+    const float p = d.h * ih.h;
+    float e = fmaf(d.h, ih.h, -p);
+    e = fmaf(d.h, ih.l, e);
+    e = fmaf(dl, ih.h, e);
+    return {p, e};
+}
+
+// b - A p rounded to FP32 at a regular cell (code bit 13 clear: the clamped
+// loads are the ghosts), ih2 = 0 on a collapsed axis
+__device__ __forceinline__ float ff_resid_regular(float b, FF P, FF xm, FF xp, FF ym, FF yp, FF zm, FF zp, FF ihx,
+                                                  FF ihy, FF ihz) {
+    const FF ax = ff_axis(P, xm, xp, ihx), ay = ff_axis(P, ym, yp, ihy), az = ff_axis(P, zm, zp, ihz);
+    const FF t = ff_two_sum(ax.h, ay.h);
+    const FF t2 = ff_two_sum(t.h, az.h);
+    const float al = (t.l + t2.l) + (ax.l + ay.l + az.l);
+    const FF u = ff_two_sum(b, -t2.h);
+    return u.h + (u.l - al);
+}
+
+// the same for any cell, each face's ghost chosen by its code (out of line: rare)
+__device__ __noinline__ float ff_resid_general(uint32_t f, float b, FF P, FF xm, FF xp, FF ym, FF yp, FF zm, FF zp,
+                                               FF ihx, FF ihy, FF ihz) {
+    const FF ax = ff_mul(ff_add(ff_face(f & 3u, P, xm), ff_face((f >> 2) & 3u, P, xp)), ihx);
+    const FF ay = ff_mul(ff_add(ff_face((f >> 4) & 3u, P, ym), ff_face((f >> 6) & 3u, P, yp)), ihy);
+    const FF az = ff_mul(ff_add(ff_face((f >> 8) & 3u, P, zm), ff_face((f >> 10) & 3u, P, zp)), ihz);
+    const FF A = ff_add(ff_add(ax, ay), az);
+    const FF rr = ff_add(FF{b, 0.0f}, ff_neg(A));
+    return rr.h + rr.l;
 }
 
 template <class TI> __device__ __forceinline__ float round_inner(float v) { return v; }
@@ -732,13 +771,12 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
         for (int t = 0; t < 4; ++t) {
             const uint32_t f = fs[t];
             const FF P = xs[t + 1];
-            const FF ax = ff_mul(ff_add(ff_face(f & 3u, P, xs[t]), ff_face((f >> 2) & 3u, P, xs[t + 2])), ihx);
-            const FF ay = ff_mul(ff_add(ff_face((f >> 4) & 3u, P, ym[t]), ff_face((f >> 6) & 3u, P, yp[t])), ihy);
-            const FF az = ff_mul(ff_add(ff_face((f >> 8) & 3u, P, em[t]), ff_face((f >> 10) & 3u, P, ep[t])), ihz);
-            const FF A = ff_add(ff_add(ax, ay), az);
-            const FF rr = ff_add(FF{bb[t], 0.0f}, ff_neg(A));
+            const float rf = !((f >> 13) & 1u)
+                                 ? ff_resid_regular(bb[t], P, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t], ihx, ihy, ihz)
+                                 : ff_resid_general(f, bb[t], P, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t], ihx,
+                                                    ihy, ihz);
             const bool fluid = !is_solid(f);
-            const float rc = fluid ? round_inner<TI>(rr.h + rr.l) : 0.0f;
+            const float rc = fluid ? round_inner<TI>(rf) : 0.0f;
             rv[t] = rc;
             ev[t] = wJ * rc * iD;
             if (in) {
@@ -790,8 +828,8 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
 }
 
 // The flexible-CG inner products with four x cells per thread and a z march
-// (the sweep's layout and neighbour scheme): products and the thread's sums
-// in FP32, block and grid sums in FP64.  Needs nx % 4 = 0.
+// (the sweep's layout and neighbour scheme): products, the thread's and the
+// warp's sums in FP32, block and grid sums in FP64.  Needs nx % 4 = 0.
 template <class TI>
 struct FcgDotV4K {
     static constexpr int kThreads = TX * TY;
@@ -875,7 +913,7 @@ __device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
             ep[t] = en[t];
         }
     }
-    double s[4] = {(double)a0, (double)a1, (double)a2, (double)a3};
+    float s[4] = {a0, a1, a2, a3};   // FP32 within a warp, FP64 from the warp sums on
     fcg_reduce<kThreads>(s, partials, st, have, at);
 }
 

@@ -178,7 +178,7 @@ struct RateMaxK {
 template <class S, class C>
 __device__ void RateMaxK<S, C>::run(const BlockAt& at) const {
     const int64_t c = (int64_t)at.b.x * blockDim.x + threadIdx.x;
-    double lam = 0.0;
+    C lam = (C)0;   // the warp maximum in the compute type, the block's in FP64
     if (c < cd.N && cd.tag[c] == 0) {
         const C u[3] = {to_c<C>(ldg((const S*)st.f[0] + c)), to_c<C>(ldg((const S*)st.f[1] + c)),
                         to_c<C>(ldg((const S*)st.f[2] + c))};
@@ -190,12 +190,11 @@ __device__ void RateMaxK<S, C>::run(const BlockAt& at) const {
         C l = (C)0;
         for (int a = 0; a < 3; ++a)
             if (cd.active[a]) l += fabs(u[a]) * prm<C>(cd.inv_h[a], cd.f.inv_h[a]) + (C)2 * gam * prm<C>(cd.inv_h2[a], cd.f.inv_h2[a]);
-        lam = (double)l;
-        if (!(lam == lam)) lam = __longlong_as_double(0x7ff0000000000000ll);   // NaN -> +inf
+        lam = l == l ? l : (C)INFINITY;   // NaN -> +inf
     }
     __shared__ double red[kThreads / 32];
     for (int off = 16; off > 0; off >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)lam;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = red[0];
