@@ -255,7 +255,8 @@ def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0, chan
     """Poisson arrivals (rate per second) of room cases sized 64^3 to
     256 x 128 x 128 (multiples of 32), with seeded vents, obstacles and heat
     loads; a share of the requests are heated channels of the same sizes.
-    Returns (arrival_times, specs)."""
+    Rooms run the flexible-CG acceleration (their small outlet makes plain
+    V-cycles slow).  Returns (arrival_times, specs)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     specs = []
@@ -267,5 +268,6 @@ def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0, chan
             specs.append(heated_channel_3d(nx, ny, nz, mg_levels=5, precision=precision,
                                            seed=seed * 1000003 + r))
         else:
-            specs.append(room_3d(nx, ny, nz, seed=seed * 1000003 + r, mg_levels=5, h=0.04, precision=precision))
+            specs.append(room_3d(nx, ny, nz, seed=seed * 1000003 + r, mg_levels=5, h=0.04, precision=precision,
+                                 krylov=1))
     return t, specs

@@ -113,14 +113,17 @@ __device__ __forceinline__ FF ff_mul(FF x, FF c) {
 // exact split of a double: hi = sign, exponent and leading 24 mantissa bits,
 // lo = the next 23 bits (the last 6 are dropped: about 2^-46 relative), by
 // integer operations and one FP32 subtraction (2^23 + m as a float's bits,
-// minus 2^23), so no conversion runs on the FP64 pipe.  |p| below 2^-126
-// gives 0; |p| at or above 2^128 and non-finite values take the FP64 path.
+// minus 2^23), so nothing runs on the FP64 pipe.  |p| below 2^-126 gives 0;
+// |p| at or above 2^128 gives +-infinity, NaN gives NaN.
 __device__ __forceinline__ FF ff_split(double p) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(p);
     const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
     const int ex = (int)((hw >> 20) & 0x7ffu);
     const unsigned sign = hw & 0x80000000u;
-    if (ex > 1150) return {__double2float_rn(p), 0.0f};
+    if (ex > 1150) {
+        const bool nan = ex == 2047 && ((hw & 0xfffffu) | lw) != 0u;
+        return {__uint_as_float(nan ? 0x7fc00000u : (sign | 0x7f800000u)), 0.0f};
+    }
     if (ex < 897) return {0.0f, 0.0f};
     const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
     float lo = 0.0f;
@@ -487,7 +490,7 @@ struct BatchCtl {
 };
 
 template <class K>
-__global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ K k, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_one_r0(const __grid_constant__ K k, cudaGraphConditionalHandle cond,
                                                         cudaGraphConditionalHandle cond2, int use_cond) {
     pdl_enter();
     const int go = k.run(BlockAt{blockIdx, gridDim});   // >= 0 only in the deciding thread
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(K::kThreads) k_one_r0(const __grid_constant__ 
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::kThreads) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
+__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
     pdl_enter();
     batch_run(ks, m);
     if (threadIdx.x + threadIdx.y + threadIdx.z != 0) return;

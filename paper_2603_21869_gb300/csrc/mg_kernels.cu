@@ -166,6 +166,7 @@ __device__ __noinline__ int resid0_finish(const double* partials, int nblk, Solv
 template <class TB, class TI>
 struct Resid0K {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr int kMinBlocks = 4;   // at most 64 registers (the batched form needs them)
     LevelDev L;
     const double* p;
     const TB* b;
@@ -714,7 +715,7 @@ template <> __device__ __forceinline__ float round_inner<__nv_bfloat16>(float v)
 template <class TI>
 struct Resid0V4K {
     static constexpr int kThreads = TX * TY;
-    static constexpr int kMinBlocks = 2;
+    static constexpr int kMinBlocks = 3;   // at most 80 registers
     LevelDev L;
     const double* p;
     const float* b;
