@@ -233,15 +233,18 @@ def run_batched(args, rank, ws, local, dist):
     # end to end through the C-ABI with host buffers: write every case, one batched step, read back
     e2e = None
     if args.e2e_steps > 0:
+        # pinned host buffers in the library's own layout; each step's output is the next input
         hosts = [torch.empty(7 * sp.cells, dtype=torch.float64, pin_memory=True).numpy() for sp in specs]
-        vals = [{k: v.copy() for k, v in c.read(out=h).items()} for c, h in zip(cs, hosts)]
+        for c, h in zip(cs, hosts):
+            c.read_flat(h)
         te = 0.0
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
-            for c, v in zip(cs, vals):
-                c.write(v)
+            for c, h in zip(cs, hosts):
+                c.write_flat(h)
             batch.step(1, allow_not_converged=True)
-            vals = [{k: x.copy() for k, x in c.read(out=h).items()} for c, h in zip(cs, hosts)]
+            for c, h in zip(cs, hosts):
+                c.read_flat(h)
             te += time.perf_counter() - t0
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
                "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
@@ -562,17 +565,16 @@ def main():
     # end to end through the C-ABI with host buffers: write state, one step, read state
     e2e = None
     if args.e2e_steps > 0:
+        # a pinned host buffer in the library's own layout; each step's output is the next input
         host = torch.empty(7 * N, dtype=torch.float64, pin_memory=True).numpy()
-        snap = case.read(out=host)
-        vals = {k: v.copy() for k, v in snap.items()}
+        case.read_flat(host)
         te = 0.0
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
-            case.write(vals)
+            case.write_flat(host)
             case.step(1, allow_not_converged=True)
-            got = case.read(out=host)
+            case.read_flat(host)
             te += time.perf_counter() - t0
-            vals = {k: v.copy() for k, v in got.items()}
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
                "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
         if dist:

@@ -316,6 +316,19 @@ class Case:
             buf[i * self.N:(i + 1) * self.N] = np.asarray(values[f], dtype=np.float64).transpose(2, 1, 0).ravel()
         _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
 
+    def read_flat(self, out, fields=cases.FIELDS):
+        """The fields into a flat float64 buffer in the library's layout (field
+        after field in FIELDS order, x fastest), no host-side reshaping; a
+        pinned buffer gives the full transfer rate."""
+        fields = [f for f in cases.FIELDS if f in fields]
+        _check(lib().fvm_read_fields(self._h, _mask(fields), out.ctypes.data_as(ct.POINTER(ct.c_double)), out.size))
+        return out
+
+    def write_flat(self, buf, fields=cases.FIELDS):
+        """The fields from a flat float64 buffer in the library's layout (see read_flat)."""
+        fields = [f for f in cases.FIELDS if f in fields]
+        _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+
     def set_rhs(self, b):
         buf = np.ascontiguousarray(np.asarray(b, dtype=np.float64).transpose(2, 1, 0).ravel())
         _check(lib().fvm_set_poisson_rhs(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))

@@ -1954,9 +1954,9 @@ fvm_status fvm_read_fields(fvm_case* c, unsigned mask, double* host_out, size_t 
         if (f == FVM_P) {
             CUDA_TRY(cudaMemcpyAsync(host_out + off, c->p, N * 8, cudaMemcpyDeviceToHost, c->stream));
         } else {
+            // (stream order: the next field's pack waits for this copy out of the staging buffer)
             CUDA_TRY(launch_pack(c->prec, c->cur[field_slot(f)], c->staging, N, c->stream));
             CUDA_TRY(cudaMemcpyAsync(host_out + off, c->staging, N * 8, cudaMemcpyDeviceToHost, c->stream));
-            CUDA_TRY(cudaStreamSynchronize(c->stream));
         }
         off += (size_t)N;
     }
@@ -1978,13 +1978,14 @@ fvm_status fvm_write_fields(fvm_case* c, unsigned mask, const double* host_in, s
         if (f == FVM_P) {
             CUDA_TRY(cudaMemcpyAsync(c->p, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
         } else {
+            // (stream order: the next field's copy into the staging buffer waits for this unpack)
             CUDA_TRY(cudaMemcpyAsync(c->staging, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
             CUDA_TRY(launch_unpack(c->prec, c->staging, c->cur[field_slot(f)], N, c->stream));
             c->nut_valid = false;
         }
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
         off += (size_t)N;
     }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
     return FVM_OK;
 }
 

@@ -184,6 +184,27 @@ def test_checkpoint_resume_is_exact():
         assert np.array_equal(got[f], ref[f]), f
 
 
+@pytest.mark.parametrize("prec", [cases.FP64, cases.FP32])
+def test_flat_buffers_match_the_field_dict(prec):
+    """read_flat / write_flat move the same values as read / write, in the
+    library's layout (field after field, x fastest), with no reshaping."""
+    spec = channel_box(precision=prec, fixed_vcycles=2)
+    with binding.Case(spec) as c:
+        c.step(1)
+        ref = c.read()
+        flat = np.empty(7 * c.N)
+        c.read_flat(flat)
+        for i, f in enumerate(cases.FIELDS):
+            assert np.array_equal(flat[i * c.N:(i + 1) * c.N], ref[f].transpose(2, 1, 0).ravel()), f
+        flat2 = flat.copy()
+        flat2[3 * c.N:4 * c.N] *= 2.0   # p
+        c.write_flat(flat2)
+        got = c.read()
+    assert np.array_equal(got["p"], 2.0 * ref["p"])
+    for f in ("u", "v", "w", "T", "k", "omega"):
+        assert np.array_equal(got[f], ref[f]), f
+
+
 def test_zero_rhs_needs_no_cycles():
     """Uniform through-flow is discretely divergence free: b = 0, no V-cycle runs."""
     spec = cases.heated_channel_3d(32, 8, 8, mg_levels=3, init_perturb=0.0)
