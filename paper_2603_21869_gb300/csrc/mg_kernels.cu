@@ -1227,6 +1227,10 @@ __device__ void CoarseK<TI>::run(const BlockAt&) const {
     coarse_cta_body<TI>(cl, r_in, e_out, Ainv);
 }
 
+// c / n for the small levels of the coarse kernel (0 <= c < 2^22, inv_n = 1/n in FP32):
+// (c + 1/2)/n is at least 1/(2n) from an integer, more than the FP32 rounding of the product
+__device__ __forceinline__ int small_div(int c, float inv_n) { return (int)(((float)c + 0.5f) * inv_n); }
+
 template <class TI>
 __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r_in, TI* __restrict__ e_out,
                                 const double* __restrict__ Ainv) {
@@ -1239,6 +1243,12 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     __shared__ C* R[FVM_MAX_LEVELS];
     __shared__ uint16_t* F[FVM_MAX_LEVELS];
     const int T = blockDim.x, tid = threadIdx.x;
+    // the level descriptions, copied word by word by all threads
+    {
+        const int words = cl.nl * (int)(sizeof(LevelDev) / 4);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(cl.lv);
+        for (int w = tid; w < words; w += T) reinterpret_cast<uint32_t*>(lvs)[w] = src[w];
+    }
     if (tid == 0) {
         C* q = (C*)smem_raw;
         for (int l = 0; l < cl.nl; ++l) {
@@ -1251,17 +1261,16 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         for (int l = 0; l < cl.nl; ++l) {
             F[l] = u;
             u += cl.lv[l].N;
-            lvs[l] = cl.lv[l];
-            lvs[l].nbf = F[l];
         }
     }
     __syncthreads();
     for (int l = 0; l < cl.nl; ++l) {
-        const int N = (int)cl.lv[l].N;
-        for (int c = tid; c < N; c += T) F[l][c] = cl.lv[l].nbf[c];
+        const int N = (int)lvs[l].N;
+        const uint16_t* src = lvs[l].nbf;   // the level's codes in global memory
+        for (int c = tid; c < N; c += T) F[l][c] = src[c];
     }
     {
-        const int N0 = (int)cl.lv[0].N;
+        const int N0 = (int)lvs[0].N;
         for (int c = tid; c < N0; c += T) R[0][c] = to_c<C>(r_in[c]);
     }
     __syncthreads();
@@ -1269,20 +1278,22 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     // down: pre-smooth, restrict
     for (int l = 0; l + 1 < cl.nl; ++l) {
         const LevelDev& L = lvs[l];
+        const uint16_t* const fl = F[l];
+        C* const rl = R[l];
         const int N = (int)L.N;
         const C w = LP<C>::wJ(L), iD = LP<C>::iD(L);
-        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(L.nbf[c]) ? (C)0 : w * R[l][c] * iD;
+        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(fl[c]) ? (C)0 : w * rl[c] * iD;
         __syncthreads();
         int s = 0;
         for (int it = 1; it < cl.pre; ++it) {
             C* ein = s ? E1[l] : E0[l];
             C* eo = s ? E0[l] : E1[l];
             for (int c = tid; c < N; c += T) {
-                const uint32_t f = L.nbf[c];
+                const uint32_t f = fl[c];
                 C v = (C)0;
                 if (!is_solid(f)) {
                     const C eP = ein[c];
-                    v = eP + w * (R[l][c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
+                    v = eP + w * (rl[c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
                 }
                 eo[c] = v;
             }
@@ -1293,33 +1304,52 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         const LevelDev& Lc = lvs[l + 1];
         const C* e = s ? E1[l] : E0[l];
         const int fx = L.active[0] ? 2 : 1, fy = L.active[1] ? 2 : 1, fz = L.active[2] ? 2 : 1;
-        const int Nc = (int)Lc.N;
-        for (int cc = tid; cc < Nc; cc += T) {
-            const int I = cc % Lc.n[0], J = (cc / Lc.n[0]) % Lc.n[1], K = cc / (Lc.n[0] * Lc.n[1]);
-            C sum = (C)0;
-            for (int dz = 0; dz < fz; ++dz)
-                for (int dy = 0; dy < fy; ++dy)
-                    for (int dx = 0; dx < fx; ++dx) {
-                        const int c = (I * fx + dx) + L.n[0] * ((J * fy + dy) + L.n[1] * (K * fz + dz));
-                        const uint32_t f = L.nbf[c];
-                        if (is_solid(f)) continue;
-                        sum += R[l][c] - cta_apply_A<C>(L, f, e, c, e[c]);
-                    }
-            R[l + 1][cc] = sum / (C)(fx * fy * fz);
+        const int Nc = (int)Lc.N, cn0 = Lc.n[0], cn1 = Lc.n[1], n0 = L.n[0], n1 = L.n[1];
+        const float icn0 = 1.0f / (float)cn0, icn01 = 1.0f / (float)(cn0 * cn1);
+        C* const rc = R[l + 1];
+        // one child per thread: eight consecutive lanes hold one coarse cell's children
+        // (missing children of a collapsed axis add 0) and sum them by a fixed shuffle tree
+        const int items = 8 * Nc, bound = (items + 31) & ~31;
+        for (int w = tid; w < bound; w += T) {
+            const int cc = w >> 3, ch = w & 7;
+            const int dx = ch & 1, dy = (ch >> 1) & 1, dz = ch >> 2;
+            C v = (C)0;
+            if (w < items && dx < fx && dy < fy && dz < fz) {
+                const int K = small_div(cc, icn01);
+                const int rem = cc - K * cn0 * cn1;
+                const int J = small_div(rem, icn0);
+                const int I = rem - J * cn0;
+                const int c = (I * fx + dx) + n0 * ((J * fy + dy) + n1 * (K * fz + dz));
+                const uint32_t f = fl[c];
+                if (!is_solid(f)) v = rl[c] - cta_apply_A<C>(L, f, e, c, e[c]);
+            }
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            if (ch == 0 && w < items) rc[cc] = v / (C)(fx * fy * fz);
         }
         __syncthreads();
     }
-    // coarsest: dense solve, one warp per row (coalesced reads of the inverse)
+    // coarsest: dense solve, one warp per row (coalesced reads of the inverse); in the
+    // reduced-precision modes from the FP32 copy of the inverse stored after the FP64 one
     {
         const int l = cl.nl - 1;
         const int N = (int)lvs[l].N;
         const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
         for (int row = warp; row < N; row += nw) {
-            double acc = 0.0;
-            const double* a = Ainv + (size_t)row * N;
-            for (int col = lane; col < N; col += 32) acc += __ldg(a + col) * (double)R[l][col];
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == 0) E0[l][row] = (C)acc;
+            if constexpr (sizeof(C) == 8) {
+                double acc = 0.0;
+                const double* a = Ainv + (size_t)row * N;
+                for (int col = lane; col < N; col += 32) acc += __ldg(a + col) * (double)R[l][col];
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (lane == 0) E0[l][row] = (C)acc;
+            } else {
+                float acc = 0.0f;
+                const float* a = reinterpret_cast<const float*>(Ainv + (size_t)N * N) + (size_t)row * N;
+                for (int col = lane; col < N; col += 32) acc = fmaf(__ldg(a + col), R[l][col], acc);
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (lane == 0) E0[l][row] = acc;
+            }
         }
         if (tid == 0) cur[l] = 0;
         __syncthreads();
@@ -1328,12 +1358,17 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     for (int l = cl.nl - 2; l >= 0; --l) {
         const LevelDev& L = lvs[l];
         const LevelDev& Lc = lvs[l + 1];
-        const int N = (int)L.N;
+        const uint16_t* const fl = F[l];
+        const int N = (int)L.N, n0 = L.n[0], n1 = L.n[1];
+        const float in0 = 1.0f / (float)n0, in01 = 1.0f / (float)(n0 * n1);
         const C* ec = cur[l + 1] ? E1[l + 1] : E0[l + 1];
         C* e = cur[l] ? E1[l] : E0[l];
         for (int c = tid; c < N; c += T) {
-            if (is_solid(L.nbf[c])) continue;
-            const int i = c % L.n[0], j = (c / L.n[0]) % L.n[1], k = c / (L.n[0] * L.n[1]);
+            if (is_solid(fl[c])) continue;
+            const int k = small_div(c, in01);
+            const int rem = c - k * n0 * n1;
+            const int j = small_div(rem, in0);
+            const int i = rem - j * n0;
             e[c] += prolong_at<C>(L.active, Lc.n, i, j, k, [&](int q) { return ec[q]; });
         }
         __syncthreads();
@@ -1343,7 +1378,7 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
             C* ein = s ? E1[l] : E0[l];
             C* eo = s ? E0[l] : E1[l];
             for (int c = tid; c < N; c += T) {
-                const uint32_t f = L.nbf[c];
+                const uint32_t f = fl[c];
                 C v = (C)0;
                 if (!is_solid(f)) {
                     const C eP = ein[c];

@@ -523,7 +523,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
         for (int f = 0; f < 6; ++f) bytes += l ? (int64_t)pl.levels[l].dir[f].size() : 0;
     }
     const int64_t nc = pl.levels.back().N();
-    bytes += nc * nc * 8;
+    bytes += nc * nc * 12;   // coarsest inverse, FP64 and FP32
     if (d->mg_variant == 1) bytes += N * 8;
     if (d->krylov == 1) bytes += N * si + (int64_t)4 * level0_blocks_max(n[0], n[1], n[2]) * 8;
     bytes += (int64_t)(2 * level0_blocks_max(n[0], n[1], n[2]) + 16) * 8 + 256;
@@ -1345,9 +1345,14 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     std::vector<double> inv;
     if (!coarse_inverse(pl.levels.back(), inv))
         return fail(FVM_ERR_INVALID, "coarsest-level operator is singular (does an outlet reach every fluid region?)");
-    ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 8));
+    // the coarsest inverse in FP64, followed by its FP32 copy (read by the coarse kernel in
+    // the reduced-precision modes)
+    std::vector<float> invf(inv.begin(), inv.end());
+    ST_TRY(dalloc(c, (void**)&c->Ainv, inv.size() * 12));
     if (d.mg_variant == 1) ST_TRY(dalloc(c, (void**)&c->p_tmp, (size_t)N * 8));
     CUDA_TRY(cudaMemcpyAsync(c->Ainv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->Ainv + inv.size(), invf.data(), inv.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->nblocks0 = level0_blocks_max(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
     if (d.krylov == 1) {
