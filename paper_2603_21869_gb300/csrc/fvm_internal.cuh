@@ -302,8 +302,9 @@ cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const v
                          const SolveState* st, cudaStream_t s);
 cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
                               const SolveState* st, cudaStream_t s);
+// (ec0 not null: also the coarse level's first Jacobi sweep from e = 0)
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
-                                  void* rc, const SolveState* st, cudaStream_t s);
+                                  void* rc, void* ec0, const SolveState* st, cudaStream_t s);
 cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* ec, void* e,
                                const SolveState* st, cudaStream_t s);
 cudaError_t prepare_coarse_cta(int inner, size_t smem);

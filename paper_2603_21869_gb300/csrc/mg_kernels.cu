@@ -274,6 +274,17 @@ struct SweepFirstK {
     }
 };
 
+// store a restricted residual and, where asked (ec0 not null), the coarse
+// level's first Jacobi sweep from e = 0 computed from the stored value, as
+// SweepFirstK would: one launch fewer per level and V-cycle
+template <class TI, class C>
+__device__ __forceinline__ void store_restricted(const LevelDev& Lc, TI* rc, TI* ec0, int idx, C val) {
+    const TI rs = from_c<TI, C>(val);
+    rc[idx] = rs;
+    if (ec0)
+        ec0[idx] = from_c<TI, C>(is_solid(Lc.nbf[idx]) ? (C)0 : LP<C>::wJ(Lc) * to_c<C>(rs) * LP<C>::iD(Lc));
+}
+
 // coarse r = mean over the children of (r - A e); one thread per coarse cell
 template <class TI>
 struct ResidRestrictK {
@@ -282,6 +293,7 @@ struct ResidRestrictK {
     const TI* e;
     const TI* r;
     TI* rc;
+    TI* ec0;   // the coarse level's first sweep, or null
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
@@ -303,7 +315,7 @@ __device__ void ResidRestrictK<TI>::run(const BlockAt& at) const {
                 const C eP = to_c<C>(ldg(e + c));
                 sum += to_c<C>(ldg(r + c)) - apply_A<C>(Lf, f, e, c, eP);
             }
-    rc[I + Lc.n[0] * (J + Lc.n[1] * K)] = from_c<TI, C>(sum / (C)(fx * fy * fz));
+    store_restricted<TI, C>(Lc, rc, ec0, I + Lc.n[0] * (J + Lc.n[1] * K), sum / (C)(fx * fy * fz));
 }
 
 // trilinear prolongation of a coarse field at fine cell (i,j,k)
@@ -1058,6 +1070,7 @@ struct RRV4K {
     const TI* e;
     const TI* r;
     TI* rc;
+    TI* ec0;   // the coarse level's first sweep, or null
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
@@ -1139,10 +1152,9 @@ __device__ void RRV4K<TI>::run(const BlockAt& at) const {
     }
     if (in) {
         const C inv = (C)1 / (C)(4 * fz);
-        const int I0 = ic >> 1;
-        TI* const out = rc + I0 + NX * (Jc + NY * K);
-        out[0] = from_c<TI, C>(s0 * inv);
-        out[1] = from_c<TI, C>(s1 * inv);
+        const int o = (ic >> 1) + NX * (Jc + NY * K);
+        store_restricted<TI, C>(Lc, rc, ec0, o, s0 * inv);
+        store_restricted<TI, C>(Lc, rc, ec0, o + 1, s1 * inv);
     }
 }
 
@@ -1156,6 +1168,7 @@ struct RRWalkK {
     const TI* e;
     const TI* r;
     TI* rc;
+    TI* ec0;   // the coarse level's first sweep, or null
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
@@ -1192,7 +1205,7 @@ __device__ void RRWalkK<TI>::run(const BlockAt& at) const {
         if (I < Lc.n[0] && J < Lc.n[1]) {
             const int x = 2 * threadIdx.x, y = 2 * threadIdx.y;
             const C s4 = (part[y][x] + part[y][x + 1]) + (part[y + 1][x] + part[y + 1][x + 1]);
-            rc[I + Lc.n[0] * (J + Lc.n[1] * (int)at.b.z)] = from_c<TI, C>(s4 / (C)(4 * fz));
+            store_restricted<TI, C>(Lc, rc, ec0, I + Lc.n[0] * (J + Lc.n[1] * (int)at.b.z), s4 / (C)(4 * fz));
         }
     }
 }
@@ -1872,23 +1885,24 @@ static bool v4_transfer_ok(const LevelDev& Lf) {
 }
 
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
-                                  void* rc, const SolveState* st, cudaStream_t s) {
+                                  void* rc, void* ec0, const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
         const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lc.n[1] + TY - 1) / TY), (unsigned)Lc.n[2]);
         if (inner == FVM_FP32)
-            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, st}, grid,
-                            dim3(TX, TY), 0, s);
+            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, (float*)ec0, st},
+                            grid, dim3(TX, TY), 0, s);
         return launch_k(RRV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)e, (const __nv_bfloat16*)r,
-                                             (__nv_bfloat16*)rc, st},
+                                             (__nv_bfloat16*)rc, (__nv_bfloat16*)ec0, st},
                         grid, dim3(TX, TY), 0, s);
     }
     if (Lf.active[0] && Lf.active[1]) {
         const int fz = Lf.active[2] ? 2 : 1;
-        DISPATCH_I(inner, err = launch_k(RRWalkK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st},
+        DISPATCH_I(inner, err = launch_k(RRWalkK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, (TI*)ec0, st},
                                          walk_grid(Lf, fz), dim3(TX, TY), 0, s));
     } else {
-        DISPATCH_I(inner, err = launch_k(ResidRestrictK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, st},
+        DISPATCH_I(inner, err = launch_k(ResidRestrictK<TI>{Lf, Lc, (const TI*)e, (const TI*)r, (TI*)rc, (TI*)ec0,
+                                                            st},
                                          grid3(Lc), kBlock3, 0, s));
     }
     return err;

@@ -682,6 +682,14 @@ fvm_status krylov_step(fvm_case* c, int zi) {
     return FVM_OK;
 }
 
+// Level l (> 0) gets its first Jacobi sweep from the restriction that forms its r:
+// both it and its parent take the plain kernels (not the coarse, tail or TMA forms).
+bool first_sweep_fused(const fvm_case* c, size_t l) {
+    if (l == 0 || l >= c->lc || c->levels[l].tma || c->levels[l - 1].tma) return false;
+    if (!g_rec && c->tail_ls > 0 && l == (size_t)c->tail_ls) return false;
+    return true;
+}
+
 // One V-cycle of the correction equation on levels l.. with r on level l;
 // returns the index of the e buffer holding the level's correction.  On
 // level 0 the final post-smoothing sweep adds the correction to p instead.
@@ -757,7 +765,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     for (int rep = 0; rep < reps; ++rep) {
         int pre = c->desc.pre_sweeps;
         if (rep == 0) {
-            if (l > 0)
+            if (l > 0 && !first_sweep_fused(c, l))
                 KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
                         launch_sweep_first(c->inner, L.dev, L.r, L.e[0], c->sst, s));
             pre -= 1;
@@ -767,8 +775,10 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
                     launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
             cur ^= 1;
         }
-        KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + 2 * N, 1,
-                launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, c->sst, s));
+        const bool fuse = first_sweep_fused(c, l + 1);
+        KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + 2 * N + (fuse ? Nc * (si + 2) : 0.0), 1,
+                launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, fuse ? Lc.e[0] : nullptr,
+                                      c->sst, s));
         int ci = 0;
         ST_TRY(cycle(c, l + 1, ci));
         KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + 2 * N, 1,
