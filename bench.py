@@ -49,6 +49,9 @@ def workload(name, precision):
 # kernel, from one ncu capture each (profiles/sweep_v4_room_channel_batched_fp32.md);
 # to be taken again whenever that kernel changes.
 TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"): 212.38e6}
+# the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell,
+# from a 32-case capture of the same batch (the first 32 of its cases), scaled by the cells
+TRAFFIC_PER_CELL = {("batched", "f32", "sweep_L0"): 441.57e6 / 29294592}
 
 
 def peaks():
@@ -138,8 +141,9 @@ def run_reference(args, spec, label, rank, ws):
     print(json.dumps(line), flush=True)
 
 
-def breakdown(prof, nsteps):
-    """Per-site table, dominant kernel roofline and V-cycle bandwidth from profile tallies."""
+def breakdown(prof, nsteps, traffic=None):
+    """Per-site table, dominant kernel roofline and V-cycle bandwidth from profile tallies
+    (traffic: {site: DRAM bytes per launch} from an ncu capture)."""
     peak, peak_src = peaks()
     name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
@@ -148,7 +152,7 @@ def breakdown(prof, nsteps):
     mg_ms = sum(prof[k]["ms"] for k in mg)
     return {
         "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": (traffic or {}).get(name),
                      "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
                      "launches": d["launches"]},
         "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
@@ -187,7 +191,11 @@ def run_batched(args, rank, ws, local, dist):
     prec = PREC[args.precision]
     specs = cases.batched_channels(args.cases, seed=rank, precision=prec, mg_levels=5)
     tuning = None
-    if not args.no_autotune:
+    if args.params:
+        pre, post, inner, _planes, kry = (int(x) for x in args.params.split(","))
+        specs = [sp.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, krylov=kry) for sp in specs]
+        tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "krylov": kry, "fixed": True}
+    elif not args.no_autotune:
         # sweep counts, V-cycles per outer residual and planes per block, measured on the largest case
         _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
         # (the planes per block are left to the batch rule: a batch has blocks to spare)
@@ -228,7 +236,8 @@ def run_batched(args, rank, ws, local, dist):
         total_ms = replicas.max_over_ranks(total_ms)
     value = ws * N * args.steps / (total_ms / 1e3)
     prof_steps = min(args.steps, 5)
-    bd = breakdown(batch.profile(prof_steps), prof_steps)
+    tpc = TRAFFIC_PER_CELL.get(("batched", args.precision, "sweep_L0"))
+    bd = breakdown(batch.profile(prof_steps), prof_steps, {"sweep_L0": tpc * N} if tpc else None)
 
     # end to end through the C-ABI with host buffers: write every case, one batched step, read back
     e2e = None
@@ -445,6 +454,9 @@ def main():
     ap.add_argument("--accuracy-cases", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
+    ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV",
+                    help="fixed multigrid parameters instead of the autotuner's (e.g. for profiling runs, where "
+                         "the profiler's overhead would distort the autotuner's timings)")
     ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
                     help="flexible-CG acceleration of the pressure solve (auto: the autotuner's choice, else off)")
     ap.add_argument("--requests", type=int, default=64, help="served workload: requests per GPU")
@@ -479,7 +491,13 @@ def main():
     spec, label = workload(args.workload, PREC[args.precision])
     rank, ws, local, dist = dist_setup()
     tuning = None
-    if args.impl == "ours" and not args.no_autotune and spec.nz > 1:
+    if args.params:
+        pre, post, inner, planes, kry = (int(x) for x in args.params.split(","))
+        spec = spec.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, sweep_planes=planes, krylov=kry)
+        label = label.replace("V(3,3)", f"V({pre},{post})")
+        tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "sweep_planes": planes,
+                  "krylov": kry, "fixed": True}
+    elif args.impl == "ours" and not args.no_autotune and spec.nz > 1:
         # smoother sweeps, V-cycles per outer residual and planes per block, measured (fvm_autotune)
         from paper_2603_21869_gb300 import binding as _b, build as _bd
         _bd.ensure_built()

@@ -116,22 +116,28 @@ __device__ __forceinline__ int neighbour(const CaseDev& cd, const StatePtrs& st,
     return FK_INTERIOR;
 }
 
+// a / b: the IEEE quotient in FP64 (the parity path); in FP32 the fast quotient
+// (__fdividef: within 2 ulp for |b| in [2^-126, 2^126], which every use below
+// keeps), its error far inside the FP32 fields' 1e-4 bound
+template <class C> __device__ __forceinline__ C qdiv(C a, C b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 template <class C>
 __device__ __forceinline__ C omega_safe(C om) { return om > (C)kEpsOmega ? om : (C)kEpsOmega; }
 
 // Re_t (Eq. Re_t) and alpha* (Eq. a_star); nu_t = alpha* k / omega (Eq. ko_turb_diff)
 template <class C>
-__device__ __forceinline__ C re_t(C k, C om, C nu) { return k / (nu * omega_safe(om)); }
+__device__ __forceinline__ C re_t(C k, C om, C nu) { return qdiv(k, nu * omega_safe(om)); }
 
 template <class C>
 __device__ __forceinline__ C alpha_star_of(C ret) {
-    const C r = ret / (C)kRk;
-    return (C)kAlphaStarInf * ((C)kAlphaStar0 + r) / ((C)1 + r);
+    const C r = qdiv(ret, (C)kRk);
+    return (C)kAlphaStarInf * qdiv((C)kAlphaStar0 + r, (C)1 + r);
 }
 
 template <class C>
 __device__ __forceinline__ C nut_of(C k, C om, C nu) {
-    return alpha_star_of(re_t(k, om, nu)) * k / omega_safe(om);
+    return qdiv(alpha_star_of(re_t(k, om, nu)) * k, omega_safe(om));
 }
 
 // ------------------------------------------------------------------ init
@@ -287,19 +293,19 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
         if (chik > (C)1e8) fbs = (C)(680.0 / 400.0);
         else {
             const C c2 = chik * chik;
-            fbs = ((C)1 + (C)680 * c2) / ((C)1 + (C)400 * c2);
+            fbs = qdiv((C)1 + (C)680 * c2, (C)1 + (C)400 * c2);
         }
     }
-    const C x = re_t(P.k, P.om, nu) / (C)kRbeta;
+    const C x = qdiv(re_t(P.k, P.om, nu), (C)kRbeta);
     C bstar;
     if (x > (C)1e4) bstar = (C)kBetaStarInf;
     else {
         const C x2 = x * x;
         const C x4 = x2 * x2;
-        bstar = (C)kBetaStarInf * ((C)(4.0 / 15.0) + x4) / ((C)1 + x4);
+        bstar = (C)kBetaStarInf * qdiv((C)(4.0 / 15.0) + x4, (C)1 + x4);
     }
     const C dt = dt_of<C>(dt_state, 1);
-    const C knew = P.k / ((C)1 + dt * bstar * fbs * P.om);
+    const C knew = qdiv(P.k, (C)1 + dt * bstar * fbs * P.om);
     // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des)
     C tr = (C)0;
     for (int a = 0; a < 3; ++a)
@@ -307,8 +313,8 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
             for (int e = 0; e < 3; ++e) tr += Om[a][b] * Om[b][e] * Sm[e][a];
     const C bo = (C)kBetaStarInf * oms;
     const C chiw = fabs(tr / (bo * bo * bo));
-    const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : ((C)1 + (C)70 * chiw) / ((C)1 + (C)80 * chiw);
-    const C omnew = P.om / ((C)1 + dt * (C)kBeta * fb * P.om);
+    const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : qdiv((C)1 + (C)70 * chiw, (C)1 + (C)80 * chiw);
+    const C omnew = qdiv(P.om, (C)1 + dt * (C)kBeta * fb * P.om);
     k_out[c] = from_c<S, C>(knew);
     om_out[c] = from_c<S, C>(omnew);
     if (nut_out) nut_out[c] = from_c<S, C>(nut_of(knew, omnew, prm<C>(cd.nu, cd.f.nu)));
@@ -349,7 +355,7 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, N nut_nb) {
 template <class S, class C>
 struct ExplicitK {
     static constexpr int kThreads = BX * BY * BZ;
-    static constexpr int kMinBlocks = sizeof(C) == 4 ? 3 : 1;   // FP32: at most 85 registers
+    static constexpr int kMinBlocks = sizeof(C) == 4 ? 4 : 1;   // FP32: at most 64 registers
     __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in, out;
@@ -412,10 +418,10 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
     S2 = (C)2 * S2;
     const C Gk = nutP * S2;
     const C ret = re_t(P.k, P.om, nu);
-    const C rw = ret / (C)kRw;
-    const C alpha = (C)kAlphaInf / alpha_star_of(ret) * ((C)kAlpha0 + rw) / ((C)1 + rw);
+    const C rw = qdiv(ret, (C)kRw);
+    const C alpha = qdiv((C)kAlphaInf, alpha_star_of(ret)) * qdiv((C)kAlpha0 + rw, (C)1 + rw);
     rhs[4] += Gk;
-    rhs[5] += alpha * P.om / P.k * Gk;
+    rhs[5] += qdiv(alpha * P.om, P.k) * Gk;
     // Boussinesq buoyancy -g beta_T (T - T_ref)
     const C dT = P.T - prm<C>(cd.T_ref, cd.f.T_ref);
     rhs[0] += prm<C>(cd.gb[0], cd.f.gb[0]) * dT;
