@@ -48,6 +48,7 @@ def workload(name, precision):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture each (profiles/sweep_v4_room_channel_batched_fp32.md);
 # to be taken again whenever that kernel changes.
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's denominator is the measured copy)
 TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"): 212.38e6}
 # the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell,
 # from a 32-case capture of the same batch (the first 32 of its cases), scaled by the cells
@@ -153,6 +154,7 @@ def breakdown(prof, nsteps, traffic=None):
     return {
         "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": (traffic or {}).get(name),
+                     "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                      "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
                      "launches": d["launches"]},
         "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
@@ -326,6 +328,7 @@ def run_batched(args, rank, ws, local, dist):
                 **bd, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "compare": compare}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(min(specs, key=lambda sp: sp.cells))
+            line["cpu_baseline_all_cores"] = cpu_all_cores(min(specs, key=lambda sp: sp.cells))
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -438,6 +441,41 @@ def cpu_baseline(spec, budget_s=25.0):
     return {"value": spec.cells * n / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} step(s) of the full {spec.nx}x{spec.ny}x{spec.nz} workload, numpy float64 on one "
                       f"host thread ({os.cpu_count()} cores present)"}
+
+
+def _oracle_steps(job):
+    """One worker of the all-cores oracle baseline: its own copy of the case, n whole steps."""
+    spec, n = job
+    from oracle.step import OracleCase
+    c = OracleCase(spec)
+    t = time.perf_counter()
+    for _ in range(n):
+        c.step()
+    return time.perf_counter() - t
+
+
+def cpu_all_cores(spec, n=1):
+    """The oracle on every host core: one process per core, each stepping its own copy of the
+    case (cases are independent, as in a batch); aggregate = cores x cells x steps / slowest.
+    Spawned processes (the parent already holds a CUDA context)."""
+    import multiprocessing as mp
+    p = os.cpu_count() or 1
+    # one thread per process (no BLAS thread pools competing for the cores)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with mp.get_context("spawn").Pool(p) as pool:
+            ts = pool.map(_oracle_steps, [(spec.replace(precision=cases.FP64), n)] * p)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": p * spec.cells * n / max(ts), "unit": "cell-steps/s", "cores": p, "kind": "oracle",
+            "sample": f"{p} processes, one copy of the {spec.nx}x{spec.ny}x{spec.nz} case each, {n} step(s); "
+                      "aggregate over the slowest process"}
 
 
 def main():
@@ -610,6 +648,7 @@ def main():
                 "vcycles_per_step": statistics.mean(vc), "rel_residual_max": max(rels),
                 "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,
+                             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                              "traffic": TRAFFIC.get((args.workload, args.precision, name)),
                              "bytes_per_launch": d["bytes"] / d["launches"],
                              "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"]},
@@ -625,6 +664,8 @@ def main():
     case.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec)
+        if spec.cells <= (1 << 21):   # one copy per core must fit in host memory
+            line["cpu_baseline_all_cores"] = cpu_all_cores(spec)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
