@@ -331,6 +331,9 @@ typedef struct {
     int64_t rounds;                  /* scheduling rounds that stepped cases */
     int64_t batch_rebuilds;          /* batches (re)built after admissions or retirements */
     int64_t cell_steps;              /* summed over retired and running requests */
+    double  t_admit_s;               /* host seconds in admission (case creation) */
+    double  t_rebuild_s;             /* host seconds building batches (recording, graph capture) */
+    double  t_step_s;                /* seconds in batched steps (launch to completion) */
 } fvm_server_info;
 
 /* budget_bytes: device bytes the resident cases may hold; max_cases: most

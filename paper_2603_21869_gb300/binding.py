@@ -92,7 +92,8 @@ class RequestResult(ct.Structure):
 
 class ServerInfo(ct.Structure):
     _fields_ = [("queued", ct.c_int64), ("running", ct.c_int64), ("done", ct.c_int64), ("bytes_in_use", ct.c_int64),
-                ("rounds", ct.c_int64), ("batch_rebuilds", ct.c_int64), ("cell_steps", ct.c_int64)]
+                ("rounds", ct.c_int64), ("batch_rebuilds", ct.c_int64), ("cell_steps", ct.c_int64),
+                ("t_admit_s", ct.c_double), ("t_rebuild_s", ct.c_double), ("t_step_s", ct.c_double)]
 
 
 class Tuning(ct.Structure):

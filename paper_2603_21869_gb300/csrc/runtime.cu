@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fvm_internal.cuh"
@@ -185,35 +186,51 @@ bool coarse_inverse(const HostLevel& L, std::vector<double>& inv) {
                     }
                 }
             }
-    inv.assign((size_t)(n * n), 0.0);
-    for (int64_t r = 0; r < n; ++r) inv[r * n + r] = 1.0;
+    // M is symmetric positive definite when every fluid region reaches a zero-value face
+    // (solid rows are identity rows): banded Cholesky M = L L^T, the band being the
+    // stride of the outermost active axis, then A^-1 column by column from L y = e_j,
+    // L^T x = y, the columns shared out among host threads
+    int64_t b = 1;
+    for (int a = 0; a < 3; ++a)
+        if (L.active[a]) b = a == 0 ? 1 : (a == 1 ? L.n[0] : (int64_t)L.n[0] * L.n[1]);
     double scale = 0.0;
     for (double x : M) scale = std::max(scale, std::fabs(x));
-    for (int64_t col = 0; col < n; ++col) {
-        int64_t piv = col;
-        for (int64_t r = col + 1; r < n; ++r)
-            if (std::fabs(M[r * n + col]) > std::fabs(M[piv * n + col])) piv = r;
-        if (std::fabs(M[piv * n + col]) <= 1e-12 * scale) return false;
-        if (piv != col)
-            for (int64_t x = 0; x < n; ++x) {
-                std::swap(M[piv * n + x], M[col * n + x]);
-                std::swap(inv[piv * n + x], inv[col * n + x]);
-            }
-        const double d = 1.0 / M[col * n + col];
-        for (int64_t x = 0; x < n; ++x) {
-            M[col * n + x] *= d;
-            inv[col * n + x] *= d;
-        }
-        for (int64_t r = 0; r < n; ++r) {
-            if (r == col) continue;
-            const double fct = M[r * n + col];
-            if (fct == 0.0) continue;
-            for (int64_t x = 0; x < n; ++x) {
-                M[r * n + x] -= fct * M[col * n + x];
-                inv[r * n + x] -= fct * inv[col * n + x];
-            }
+    std::vector<double> C((size_t)(n * (b + 1)), 0.0);   // C[i*(b+1) + (i-j)] = L[i][j], 0 <= i-j <= b
+    auto Lij = [&](int64_t i, int64_t j) -> double& { return C[(size_t)(i * (b + 1) + (i - j))]; };
+    for (int64_t j = 0; j < n; ++j) {
+        double d = M[j * n + j];
+        for (int64_t k = std::max<int64_t>(0, j - b); k < j; ++k) d -= Lij(j, k) * Lij(j, k);
+        if (!(d > 1e-12 * scale)) return false;   // singular (no zero-value face reached)
+        const double ljj = std::sqrt(d);
+        Lij(j, j) = ljj;
+        for (int64_t i = j + 1; i <= std::min(n - 1, j + b); ++i) {
+            double v = M[i * n + j];
+            for (int64_t k = std::max<int64_t>(0, i - b); k < j; ++k) v -= Lij(i, k) * Lij(j, k);
+            Lij(i, j) = v / ljj;
         }
     }
+    inv.assign((size_t)(n * n), 0.0);
+    auto columns = [&](int64_t c0, int64_t c1) {
+        std::vector<double> y((size_t)n);
+        for (int64_t col = c0; col < c1; ++col) {
+            std::fill(y.begin(), y.end(), 0.0);
+            for (int64_t i = col; i < n; ++i) {   // L y = e_col (y is 0 above col)
+                double v = i == col ? 1.0 : 0.0;
+                for (int64_t k = std::max<int64_t>(col, i - b); k < i; ++k) v -= Lij(i, k) * y[(size_t)k];
+                y[(size_t)i] = v / Lij(i, i);
+            }
+            for (int64_t i = n - 1; i >= 0; --i) {   // L^T x = y, x over y
+                double v = y[(size_t)i];
+                for (int64_t k = i + 1; k <= std::min(n - 1, i + b); ++k) v -= Lij(k, i) * y[(size_t)k];
+                y[(size_t)i] = v / Lij(i, i);
+            }
+            for (int64_t r = 0; r < n; ++r) inv[(size_t)(r * n + col)] = y[(size_t)r];
+        }
+    };
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>((int64_t)std::thread::hardware_concurrency(), n / 64));
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < nt; ++t) pool.emplace_back(columns, n * t / nt, n * (t + 1) / nt);
+    for (auto& th : pool) th.join();
     return true;
 }
 

@@ -63,6 +63,7 @@ struct fvm_server {
     bool dirty = false;
     int64_t used = 0;
     int64_t rounds = 0, rebuilds = 0, cell_steps = 0, done = 0;
+    double t_admit = 0.0, t_rebuild = 0.0, t_step = 0.0;   // host seconds per phase
 };
 
 namespace {
@@ -234,11 +235,15 @@ fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* don
         if (n_done) *n_done = nd;
         return FVM_OK;
     }
+    const double t1 = now_of(s);
+    s->t_admit += t1 - t;
     // 2. one round of batched steps
     if (s->dirty) {
         fvm_status st = rebuild(s);
         if (st != FVM_OK) return st;
     }
+    const double t2 = now_of(s);
+    s->t_rebuild += t2 - t1;
     int32_t steps = chunk;
     for (Request* r : s->running) steps = std::min(steps, r->nsteps - r->done_steps);
     for (auto& kv : s->batches) {
@@ -261,6 +266,7 @@ fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* don
     ++s->rounds;
     // 3. retirement
     const double t_end = now_of(s);
+    s->t_step += t_end - t2;
     for (size_t q = 0; q < s->running.size();) {
         Request* r = s->running[q];
         if (r->state != Q_DONE && r->done_steps >= r->nsteps) retire(s, r, FVM_OK, t_end);
@@ -287,6 +293,9 @@ fvm_status fvm_server_get_info(const fvm_server* s, fvm_server_info* out) {
     o.rounds = s->rounds;
     o.batch_rebuilds = s->rebuilds;
     o.cell_steps = s->cell_steps;
+    o.t_admit_s = s->t_admit;
+    o.t_rebuild_s = s->t_rebuild;
+    o.t_step_s = s->t_step;
     *out = o;
     return FVM_OK;
 }
