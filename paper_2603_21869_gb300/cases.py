@@ -256,7 +256,9 @@ def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0, chan
     256 x 128 x 128 (multiples of 32), with seeded vents, obstacles and heat
     loads; a share of the requests are heated channels of the same sizes.
     Rooms run the flexible-CG acceleration (their small outlet makes plain
-    V-cycles slow).  Returns (arrival_times, specs)."""
+    V-cycles slow) with V(2,2) and two V-cycles per outer residual, channels
+    V(3,3) with three: the autotuner's choices for the full-size room and
+    channel.  Returns (arrival_times, specs)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     specs = []
@@ -266,8 +268,8 @@ def served_rooms(n_requests: int = 2000, seed: int = 0, rate: float = 20.0, chan
         nz = int(rng.choice([64, 96, 128]))
         if rng.uniform() < channel_share:
             specs.append(heated_channel_3d(nx, ny, nz, mg_levels=5, precision=precision,
-                                           seed=seed * 1000003 + r))
+                                           seed=seed * 1000003 + r, inner_cycles=3))
         else:
             specs.append(room_3d(nx, ny, nz, seed=seed * 1000003 + r, mg_levels=5, h=0.04, precision=precision,
-                                 krylov=1))
+                                 krylov=1, pre_sweeps=2, post_sweeps=2, inner_cycles=2))
     return t, specs
