@@ -430,6 +430,17 @@ __device__ __forceinline__ void batch_enter(const K* __restrict__ ks, const Batc
     __syncthreads();
 }
 
+// K::kNoShared: run() uses no shared memory, so a batched block needs no barrier before
+// the next block of the same case starts (the functor swap between cases has its own)
+template <class K, class = void>
+struct NoSharedRun {
+    static constexpr bool value = false;
+};
+template <class K>
+struct NoSharedRun<K, std::void_t<decltype(K::kNoShared)>> {
+    static constexpr bool value = K::kNoShared;
+};
+
 // the body of one block, kept out of line: inlined into the walk below it would keep the
 // walk's state live across the whole body and raise the register count
 template <class K>
@@ -461,7 +472,7 @@ __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchM
         }
         if (s_live) {
             batch_block_body(*reinterpret_cast<const K*>(buf), BlockAt{b, g});
-            __syncthreads();   // shared memory of run() is reused by the next block
+            if constexpr (!NoSharedRun<K>::value) __syncthreads();   // run()'s shared memory is reused next
         }
         if (++b.x == g.x) {
             b.x = 0;

@@ -243,6 +243,7 @@ __device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
 
 struct SolveBeginK {
     static constexpr int kThreads = 1;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     SolveState* st;
     __device__ bool live() const { return true; }
     __device__ void run(const BlockAt&) const {
@@ -259,6 +260,7 @@ struct SolveBeginK {
 template <class TI>
 struct SweepFirstK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const TI* r;
     TI* e;
@@ -289,6 +291,7 @@ __device__ __forceinline__ void store_restricted(const LevelDev& Lc, TI* rc, TI*
 template <class TI>
 struct ResidRestrictK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev Lf, Lc;
     const TI* e;
     const TI* r;
@@ -350,6 +353,7 @@ __device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int
 template <class TI>
 struct ProlongK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev Lf, Lc;
     const TI* ec;
     TI* e;
@@ -397,6 +401,7 @@ __device__ __forceinline__ bool walk_setup(const LevelDev& L, const BlockAt& at,
 template <class TI, int MODE, int KZ>
 struct SweepK {
     static constexpr int kThreads = TX * TY;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const TI* ein;
     const TI* r;
@@ -486,6 +491,7 @@ constexpr int V4X = 4 * TX;   // cells of a row per warp
 template <class TI, int MODE>
 struct SweepV4K {
     static constexpr int kThreads = TX * TY;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = 4;   // at most 64 registers: four blocks per SM
     LevelDev L;
     const TI* ein;
@@ -935,6 +941,7 @@ __device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
 template <class TI>
 struct FcgUpdV4K {
     static constexpr int kThreads = 256;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const TI* z;
     TI* dp;
@@ -992,6 +999,7 @@ template <> struct Vec2<__nv_bfloat16> {
 template <class TI>
 struct ProlongV4K {
     static constexpr int kThreads = TX * TY;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = 4;
     LevelDev Lf, Lc;
     const TI* ec;
@@ -1065,6 +1073,7 @@ __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
 template <class TI>
 struct RRV4K {
     static constexpr int kThreads = TX * TY;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = 3;
     LevelDev Lf, Lc;
     const TI* e;
@@ -1469,6 +1478,7 @@ __device__ void FcgDotK<TI>::run(const BlockAt& at) const {
 template <class TI>
 struct FcgUpdK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const TI* z;
     TI* dp;
@@ -1491,6 +1501,7 @@ struct FcgUpdK {
 template <class TI>
 struct RestrictK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev Lf, Lc;
     const TI* r;
     TI* rc;
@@ -1519,6 +1530,7 @@ __device__ __forceinline__ int parent_of(const LevelDev& Lf, const LevelDev& Lc,
 template <class TI>
 struct ProlongNearestK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev Lf, Lc;
     const TI* ec;
     TI* e;
@@ -1536,6 +1548,7 @@ struct ProlongNearestK {
 template <class TI>
 struct ProlongNearestToPK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev Lf, Lc;
     const TI* ec;
     double* p;
@@ -1553,6 +1566,7 @@ struct ProlongNearestToPK {
 template <class TB>
 struct JacobiPK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const double* p;
     const TB* b;
@@ -1579,6 +1593,7 @@ struct JacobiPK {
 
 struct CopyPK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
     const double* q;
     double* p;

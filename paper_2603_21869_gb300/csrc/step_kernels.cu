@@ -212,6 +212,7 @@ __device__ void RateMaxK<S, C>::run(const BlockAt& at) const {
 // dt_state: [0] dt, [1] dt/2, [2] simulated time, [3] rate bits (reset here)
 struct DtFinalizeK {
     static constexpr int kThreads = 1;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     __device__ bool live() const { return true; }
     double dt0, cfl;
     int adapt;
@@ -237,6 +238,7 @@ struct DtFinalizeK {
 template <class S, class C>
 struct DestructionK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = sizeof(C) == 4 ? 3 : 1;   // FP32: at most 85 registers
     __device__ bool live() const { return true; }
     CaseDev cd;
@@ -355,6 +357,7 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, N nut_nb) {
 template <class S, class C>
 struct ExplicitK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = sizeof(C) == 4 ? 4 : 1;   // FP32: at most 64 registers
     __device__ bool live() const { return true; }
     CaseDev cd;
@@ -445,6 +448,7 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
 template <class S, class C>
 struct RhsK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in;
@@ -500,6 +504,7 @@ __device__ __forceinline__ FF p_across_ff(const LevelDev& L, const double* p, ui
 template <class S, class C>
 struct ProjectK {
     static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
     __device__ bool live() const { return true; }
     CaseDev cd;
     LevelDev L0;
