@@ -484,8 +484,18 @@ __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchM
     }
 }
 
+// blocks per SM for the batched (persistent) form: K::kMinBlocksMany, default as k_one
+template <class K, class = void>
+struct MinBlocksMany {
+    static constexpr int value = MinBlocks<K>::value;
+};
 template <class K>
-__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_many(const K* __restrict__ ks, BatchMap m) {
+struct MinBlocksMany<K, std::void_t<decltype(K::kMinBlocksMany)>> {
+    static constexpr int value = K::kMinBlocksMany;
+};
+
+template <class K>
+__global__ void __launch_bounds__(K::kThreads, MinBlocksMany<K>::value) k_many(const K* __restrict__ ks, BatchMap m) {
     pdl_enter();
     batch_run(ks, m);
 }
@@ -513,7 +523,7 @@ __global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_one_r0(con
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::kThreads, MinBlocks<K>::value) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
+__global__ void __launch_bounds__(K::kThreads, MinBlocksMany<K>::value) k_many_r0(const K* __restrict__ ks, BatchMap m, BatchCtl ctl) {
     pdl_enter();
     batch_run(ks, m);
     if (threadIdx.x + threadIdx.y + threadIdx.z != 0) return;

@@ -492,7 +492,8 @@ template <class TI, int MODE>
 struct SweepV4K {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
-    static constexpr int kMinBlocks = 4;   // at most 64 registers: four blocks per SM
+    static constexpr int kMinBlocks = 4;   // at most 64 registers: four blocks per SM (batched too:
+                                           // the few spilled bytes cost less than a block per SM)
     LevelDev L;
     const TI* ein;
     const TI* r;
@@ -733,7 +734,8 @@ template <> __device__ __forceinline__ float round_inner<__nv_bfloat16>(float v)
 template <class TI>
 struct Resid0V4K {
     static constexpr int kThreads = TX * TY;
-    static constexpr int kMinBlocks = 3;   // at most 80 registers
+    static constexpr int kMinBlocks = 3;       // at most 80 registers
+    static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
     LevelDev L;
     const double* p;
     const float* b;
@@ -852,7 +854,8 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
 template <class TI>
 struct FcgDotV4K {
     static constexpr int kThreads = TX * TY;
-    static constexpr int kMinBlocks = 3;   // at most 80 registers
+    static constexpr int kMinBlocks = 3;       // at most 80 registers
+    static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
     LevelDev L;
     const TI* z;
     const TI* r;
