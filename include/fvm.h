@@ -251,6 +251,15 @@ fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm
    (FVM_ERR_DIVERGED before FVM_ERR_NOT_CONVERGED); fields stay readable. */
 fvm_status fvm_batch_step(fvm_batch* b, int32_t nsteps, fvm_step_stats* stats);
 
+/* fvm_batch_step in two halves, so that the caller can do host work while
+   the steps run: fvm_batch_launch enqueues nsteps steps on the batch's
+   stream and returns; fvm_batch_wait waits for them and fills stats as
+   fvm_batch_step does.  One launch at a time per batch (FVM_ERR_INVALID
+   otherwise, and for a wait with nothing launched); the cases' fields are
+   not to be read or written in between. */
+fvm_status fvm_batch_launch(fvm_batch* b, int32_t nsteps);
+fvm_status fvm_batch_wait(fvm_batch* b, fvm_step_stats* stats);
+
 fvm_status fvm_batch_get_info(const fvm_batch* b, fvm_batch_info* out);
 
 /* Profiling pass of a batch: nsteps steps run launch by launch (the merged
@@ -298,15 +307,15 @@ fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm_tuning* ou
    A request loop over resident cases (continuous batching).  A request is a
    case description plus a number of steps.  fvm_server_poll runs one
    scheduling round:
-     1. admit, first come first served, the queued requests whose arrival
-        time has passed while their device bytes (fvm_case_bytes) fit the
-        HBM budget and a slot is free: each becomes a resident case;
-     2. step every resident case together: one fvm_batch per precision,
-        min(chunk, fewest remaining steps) steps, so a newly admitted case
-        overlaps with the ones already running;
-     3. retire the finished requests (their memory is freed at once, or kept
-        for fvm_server_read_fields until fvm_server_release when
-        keep_results is set) and report them.
+     1. launch the steps of every resident case together: one fvm_batch per
+        precision, min(chunk, fewest remaining steps) steps;
+     2. meanwhile admit, first come first served, the queued requests whose
+        arrival time has passed while their device bytes (fvm_case_bytes)
+        fit the HBM budget and a slot is free: each becomes a resident case
+        that joins the next round, its creation overlapping the steps;
+     3. wait for the steps, retire the finished requests (their memory is
+        freed at once, or kept for fvm_server_read_fields until
+        fvm_server_release when keep_results is set) and report them.
    Times are seconds on the server's steady clock (fvm_server_now, zero at
    creation); a request's latency is t_done - t_arrive.  The paper serves
    no requests: this is an addition for many concurrent cases.  Not

@@ -112,7 +112,8 @@ EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", 
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
            "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
            "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
-           "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_destroy", "fvm_batch_profile", "fvm_server_create",
+           "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info", "fvm_batch_destroy",
+           "fvm_batch_profile", "fvm_server_create",
            "fvm_server_now", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields",
            "fvm_server_release", "fvm_server_destroy", "fvm_autotune"]
 
@@ -151,6 +152,8 @@ def lib():
     L.fvm_poisson_residual_static.restype = ct.c_int
     L.fvm_batch_create.argtypes = [ct.POINTER(CP), ct.c_int32, CP, ct.POINTER(CP)]
     L.fvm_batch_step.argtypes = [CP, ct.c_int32, ct.POINTER(StepStats)]
+    L.fvm_batch_launch.argtypes = [CP, ct.c_int32]
+    L.fvm_batch_wait.argtypes = [CP, ct.POINTER(StepStats)]
     L.fvm_batch_get_info.argtypes = [CP, ct.POINTER(BatchInfo)]
     L.fvm_batch_profile.argtypes = [CP, ct.c_int32, ct.POINTER(KernelStat), ct.c_int32, ct.POINTER(ct.c_int32)]
     L.fvm_autotune.argtypes = [ct.POINTER(CaseDesc), ct.c_int32, ct.POINTER(Tuning)]
@@ -172,7 +175,8 @@ def lib():
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_get_info", "fvm_batch_profile",
+                 "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
+                 "fvm_batch_profile",
                  "fvm_server_create", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info",
                  "fvm_server_read_fields", "fvm_server_release", "fvm_autotune"]:
         getattr(L, name).restype = ct.c_int
@@ -400,6 +404,16 @@ class Batch:
     def step(self, n=1, allow_not_converged=False):
         stats = (StepStats * len(self.cases))()
         status = lib().fvm_batch_step(self._h, n, stats)
+        _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return [_stats(s, status) for s in stats]
+
+    def launch(self, n=1):
+        """Enqueue n steps and return (fvm_batch_launch); wait() collects them."""
+        _check(lib().fvm_batch_launch(self._h, n))
+
+    def wait(self, allow_not_converged=False):
+        stats = (StepStats * len(self.cases))()
+        status = lib().fvm_batch_wait(self._h, stats)
         _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return [_stats(s, status) for s in stats]
 

@@ -1563,6 +1563,10 @@ struct fvm_batch {
     unsigned long long* d_scratch = nullptr;   // outer-iteration sum of profiled steps (unused)
     int64_t launches = 0;
     int64_t steps = 0;
+    // a launch in flight (fvm_batch_launch): its step count and launch tallies
+    bool pending = false;
+    int32_t pend_steps = 0;
+    int64_t pend_fixed = 0, pend_per_outer = 0;
 };
 
 namespace {
@@ -2082,14 +2086,16 @@ fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm
 
 void fvm_batch_destroy(fvm_batch* b) { free_batch(b); }
 
-fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
+fvm_status fvm_batch_launch(fvm_batch* B, int32_t nsteps) {
     if (!B) return fail(FVM_ERR_INVALID, "null batch");
     if (nsteps < 0) return fail(FVM_ERR_INVALID, "nsteps < 0");
+    if (B->pending) return fail(FVM_ERR_INVALID, "the batch already has steps in flight");
     ST_TRY(batch_check(B->cases.data(), (int)B->cases.size()));
     const int n = (int)B->cases.size();
     cudaStream_t s = B->stream;
     // earlier work on the cases' own streams comes first
-    for (fvm_case* c : B->cases) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (fvm_case* c : B->cases)
+        if (c->stream != s) CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (fvm_case* c : B->cases) {
         CUDA_TRY(cudaMemsetAsync(&c->sst->total_cycles, 0, sizeof(int32_t), s));
         CUDA_TRY(cudaMemsetAsync(&c->sst->nonfinite, 0, sizeof(int32_t), s));
@@ -2112,8 +2118,21 @@ fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
     }
     CUDA_TRY(cudaMemcpyAsync(B->h_gather, B->d_gather, n * sizeof(BatchGather), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(B->h_outer, B->d_outer, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (nsteps > 0) B->launches += fixed + (int64_t)*B->h_outer * per_outer;
+    B->pending = true;
+    B->pend_steps = nsteps;
+    B->pend_fixed = fixed;
+    B->pend_per_outer = per_outer;
+    return FVM_OK;
+}
+
+fvm_status fvm_batch_wait(fvm_batch* B, fvm_step_stats* stats) {
+    if (!B) return fail(FVM_ERR_INVALID, "null batch");
+    if (!B->pending) return fail(FVM_ERR_INVALID, "no steps in flight");
+    B->pending = false;
+    const int n = (int)B->cases.size();
+    const int32_t nsteps = B->pend_steps;
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    if (nsteps > 0) B->launches += B->pend_fixed + (int64_t)*B->h_outer * B->pend_per_outer;
     fvm_status result = FVM_OK;
     for (int i = 0; i < n; ++i) {
         const BatchGather& q = B->h_gather[i];
@@ -2139,6 +2158,11 @@ fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
     return result;
 }
 
+fvm_status fvm_batch_step(fvm_batch* B, int32_t nsteps, fvm_step_stats* stats) {
+    ST_TRY(fvm_batch_launch(B, nsteps));
+    return fvm_batch_wait(B, stats);
+}
+
 fvm_status fvm_batch_get_info(const fvm_batch* B, fvm_batch_info* out) {
     if (!B || !out) return fail(FVM_ERR_INVALID, "null batch or output");
     fvm_batch_info info;
@@ -2161,6 +2185,7 @@ fvm_status fvm_batch_get_info(const fvm_batch* B, fvm_batch_info* out) {
 fvm_status fvm_batch_profile(fvm_batch* B, int32_t nsteps, fvm_kernel_stat* out, int32_t cap, int32_t* n_out) {
     if (!B || (!out && cap > 0)) return fail(FVM_ERR_INVALID, "null batch or output");
     if (nsteps < 0) return fail(FVM_ERR_INVALID, "nsteps < 0");
+    if (B->pending) return fail(FVM_ERR_INVALID, "the batch has steps in flight");
     ST_TRY(batch_check(B->cases.data(), (int)B->cases.size()));
     const int n = (int)B->cases.size();
     cudaStream_t s = B->stream;

@@ -2,12 +2,13 @@
 // public C-ABI only: cases are created, batched, stepped and destroyed
 // through fvm_create_case / fvm_batch_* / fvm_destroy_case.
 //
-// One scheduling round admits the queued requests that have arrived, first
-// come first served, while their device bytes fit the budget; steps all
-// resident cases together (one batch per precision, rebuilt when the set of
-// cases changes); and retires the finished ones.  A request admitted while
-// others run joins them at the next round, so their work overlaps on the
-// device.
+// One scheduling round launches the steps of all resident cases together
+// (one batch per precision, rebuilt when the set of cases changes); while
+// they run, admits the queued requests that have arrived, first come first
+// served, while their device bytes fit the budget (case creation on the host
+// overlaps the device work); waits for the steps and retires the finished
+// requests.  An admitted request joins the others at the next round, so their
+// work overlaps on the device.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -174,7 +175,7 @@ fvm_status fvm_server_submit(fvm_server* s, const fvm_case_desc* desc, int32_t n
     r->boxes.assign(desc->boxes, desc->boxes + desc->n_boxes);
     r->desc.vents = r->vents.data();
     r->desc.boxes = r->boxes.data();
-    r->desc.stream = s->stream;
+    r->desc.stream = nullptr;   // a stream of the case's own: its creation runs beside the batch in flight
     r->nsteps = nsteps;
     r->t_arrive = t_arrive;
     r->bytes = bytes;
@@ -195,13 +196,34 @@ fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* don
         if (done && nd < cap) done[nd] = result_of(r);
         ++nd;
     };
-    // 1. admission, first come first served
-    const double t = now_of(s);
+    // 1. this round's steps for the resident cases are launched first, so that admitting
+    //    new requests (host-side case creation) overlaps them on the device
+    const double t0 = now_of(s);
+    int32_t steps = 0;
+    if (!s->running.empty()) {
+        if (s->dirty) {
+            fvm_status st = rebuild(s);
+            if (st != FVM_OK) return st;
+        }
+        steps = chunk;
+        for (Request* r : s->running) steps = std::min(steps, r->nsteps - r->done_steps);
+        for (auto& kv : s->batches) {
+            fvm_status st = fvm_batch_launch(kv.second, steps);
+            if (st != FVM_OK) {
+                for (auto& kw : s->batches) fvm_batch_wait(kw.second, nullptr);   // (refuses those not launched)
+                return st;
+            }
+        }
+    }
+    const double t1 = now_of(s);
+    s->t_rebuild += t1 - t0;
+    // 2. admission, first come first served; admitted cases join the next round
+    std::vector<Request*> joined;
     while (!s->queue.empty()) {
         Request* r = s->queue.front();
-        if (r->t_arrive > t) break;
+        if (r->t_arrive > t1) break;
         if (s->used + r->bytes > s->budget) break;
-        if (s->max_cases > 0 && (int32_t)s->running.size() >= s->max_cases) break;
+        if (s->max_cases > 0 && (int32_t)(s->running.size() + joined.size()) >= s->max_cases) break;
         s->queue.pop_front();
         fvm_status st = fvm_create_case(&r->desc, &r->c);
         if (st == FVM_ERR_OOM) {   // the device holds less than the budget says: retry later
@@ -216,55 +238,37 @@ fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* don
         }
         s->used += r->bytes;
         r->state = Q_RUNNING;
-        s->running.push_back(r);
-        s->dirty = true;
-        if (r->nsteps == 0) retire(s, r, FVM_OK, r->t_admit);
-    }
-    // retire zero-step requests admitted above
-    for (size_t q = 0; q < s->running.size();) {
-        Request* r = s->running[q];
-        if (r->state == Q_DONE) {
+        if (r->nsteps == 0) {
+            retire(s, r, FVM_OK, r->t_admit);
             report(r);
-            s->running.erase(s->running.begin() + q);
-        } else {
-            ++q;
+            continue;
         }
-    }
-    if (s->running.empty()) {
-        drop_batches(s);
-        if (n_done) *n_done = nd;
-        return FVM_OK;
-    }
-    const double t1 = now_of(s);
-    s->t_admit += t1 - t;
-    // 2. one round of batched steps
-    if (s->dirty) {
-        fvm_status st = rebuild(s);
-        if (st != FVM_OK) return st;
+        joined.push_back(r);
     }
     const double t2 = now_of(s);
-    s->t_rebuild += t2 - t1;
-    int32_t steps = chunk;
-    for (Request* r : s->running) steps = std::min(steps, r->nsteps - r->done_steps);
-    for (auto& kv : s->batches) {
-        std::vector<Request*>& mem = s->members[kv.first];
-        std::vector<fvm_step_stats> stats(mem.size());
-        const fvm_status st = fvm_batch_step(kv.second, steps, stats.data());
-        if (st != FVM_OK && st != FVM_ERR_NOT_CONVERGED && st != FVM_ERR_DIVERGED) return st;
-        for (size_t q = 0; q < mem.size(); ++q) {
-            Request* r = mem[q];
-            r->done_steps += stats[q].steps;
-            r->vcycles += stats[q].vcycles_total;
-            r->rel = stats[q].rel_residual;
-            s->cell_steps += r->cells * (int64_t)stats[q].steps;
-            // a case whose own solve diverged ends with that status; a case that hit the
-            // V-cycle cap keeps running (its result carries the residual)
-            if (st == FVM_ERR_DIVERGED && !(stats[q].rel_residual == stats[q].rel_residual))
-                retire(s, r, FVM_ERR_DIVERGED, now_of(s));
+    s->t_admit += t2 - t1;
+    // 3. the round's results
+    if (steps > 0) {
+        for (auto& kv : s->batches) {
+            std::vector<Request*>& mem = s->members[kv.first];
+            std::vector<fvm_step_stats> stats(mem.size());
+            const fvm_status st = fvm_batch_wait(kv.second, stats.data());
+            if (st != FVM_OK && st != FVM_ERR_NOT_CONVERGED && st != FVM_ERR_DIVERGED) return st;
+            for (size_t q = 0; q < mem.size(); ++q) {
+                Request* r = mem[q];
+                r->done_steps += stats[q].steps;
+                r->vcycles += stats[q].vcycles_total;
+                r->rel = stats[q].rel_residual;
+                s->cell_steps += r->cells * (int64_t)stats[q].steps;
+                // a case whose own solve diverged ends with that status; a case that hit the
+                // V-cycle cap keeps running (its result carries the residual)
+                if (st == FVM_ERR_DIVERGED && !(stats[q].rel_residual == stats[q].rel_residual))
+                    retire(s, r, FVM_ERR_DIVERGED, now_of(s));
+            }
         }
+        ++s->rounds;
     }
-    ++s->rounds;
-    // 3. retirement
+    // 4. retirement
     const double t_end = now_of(s);
     s->t_step += t_end - t2;
     for (size_t q = 0; q < s->running.size();) {
@@ -277,6 +281,10 @@ fvm_status fvm_server_poll(fvm_server* s, int32_t chunk, fvm_request_result* don
             ++q;
         }
     }
+    // 5. the admitted cases become resident
+    for (Request* r : joined) s->running.push_back(r);
+    if (!joined.empty()) s->dirty = true;
+    if (s->running.empty()) drop_batches(s);
     if (n_done) *n_done = nd;
     set_last_error("");
     return FVM_OK;

@@ -163,3 +163,34 @@ def test_coarse_kernel_smem_limit_is_not_lowered_by_a_later_smaller_case():
             b.step(1)
         big.step(1)
         assert np.isfinite(big.read(("p",))["p"]).all()
+
+
+def test_launch_and_wait_equal_step_and_guard_their_order():
+    """fvm_batch_launch + fvm_batch_wait give what fvm_batch_step gives; a second
+    launch before the wait, and a wait with nothing launched, are refused."""
+    specs = uneven_channels(cases.FP32, n=3)
+    res = []
+    for split in (False, True):
+        cs = [binding.Case(s) for s in specs]
+        try:
+            with binding.Batch(cs) as b:
+                if split:
+                    b.launch(3)
+                    with pytest.raises(binding.FvmError) as ei:
+                        b.launch(1)
+                    assert ei.value.status == binding.ERR_INVALID
+                    st = b.wait()
+                    with pytest.raises(binding.FvmError):
+                        b.wait()
+                else:
+                    st = b.step(3)
+            res.append((st, [c.read() for c in cs]))
+        finally:
+            for c in cs:
+                c.close()
+    (s0, f0), (s1, f1) = res
+    assert [x["vcycles_total"] for x in s0] == [x["vcycles_total"] for x in s1]
+    for a, b in zip(f0, f1):
+        for f in cases.FIELDS:
+            assert np.array_equal(a[f], b[f]), f
+

@@ -36,11 +36,11 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         with binding.Case(spec) as c:
             c.step(n, allow_not_converged=True)
             alone.append(c.read())
-    with binding.Server(budget_bytes=8 << 30, keep_results=True) as srv:
+    with binding.Server(budget_bytes=8 << 30, keep_results=True) as srv:   # each round: steps, then admissions
         ids = [srv.submit(reqs[0][0], reqs[0][1])]
-        done = srv.poll(chunk=2)            # the first request runs alone for two steps
+        done = srv.poll(chunk=2)            # the first request is admitted
         ids.append(srv.submit(reqs[1][0], reqs[1][1]))
-        done += srv.poll(chunk=2)           # the second joins it
+        done += srv.poll(chunk=2)           # it runs alone for two steps while the second is admitted
         ids.append(srv.submit(reqs[2][0], reqs[2][1]))
         for _ in range(20):
             if len(done) == len(reqs):

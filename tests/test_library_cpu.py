@@ -45,6 +45,8 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert "null case" in binding.last_error()
     assert not h.value
     assert lib.fvm_batch_step(None, 1, None) == binding.ERR_INVALID
+    assert lib.fvm_batch_launch(None, 1) == binding.ERR_INVALID
+    assert lib.fvm_batch_wait(None, None) == binding.ERR_INVALID
 
 
 def test_autotune_rejects_bad_arguments_without_a_gpu(lib):
