@@ -10,7 +10,9 @@
              neighbour per axis, neighbour index clamped to the grid
              (Eq. prolongation)
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
-             correct, post-smooth; exact dense solve on the coarsest level
+             correct, post-smooth; exact dense solve on the coarsest level;
+             coarse_sweeps > 0 sets both sweep counts on the levels below
+             the finest (a tuning choice, not in the paper)
   krylov 1   flexible CG with one kept direction around V-cycles (each
              V-cycle from zero on A z = r gives a direction, A-orthogonalised
              against the previous one, and the step minimising the A-norm of
@@ -183,16 +185,25 @@ class Multigrid:
         rhs = np.where(lev.solid, 0.0, b).ravel()
         return np.linalg.solve(self._coarse_M, rhs).reshape(lev.shape)
 
+    def sweeps(self, l):
+        """(pre, post) smoothing sweeps on level l: the spec's on the finest level;
+        coarse_sweeps, when set, on both sides of every coarser level."""
+        k = getattr(self.spec, "coarse_sweeps", 0)
+        if l > 0 and k > 0:
+            return k, k
+        return self.spec.pre_sweeps, self.spec.post_sweeps
+
     def vcycle(self, p, b, l=0):
         lev = self.levels[l]
         if l == len(self.levels) - 1:
             return self.coarse_solve(b)
         wJ = jacobi_weight(lev, self.spec)
-        p = smooth(lev, p, b, self.spec.pre_sweeps, wJ)
+        pre, post = self.sweeps(l)
+        p = smooth(lev, p, b, pre, wJ)
         bc = restrict(lev, residual(lev, p, b))
         ec = self.vcycle(np.zeros(self.levels[l + 1].shape), bc, l + 1)
         p = np.where(lev.fluid, p + prolong(ec, lev.shape), 0.0)
-        p = smooth(lev, p, b, self.spec.post_sweeps, wJ)
+        p = smooth(lev, p, b, post, wJ)
         return p
 
     def paper_cycle(self, p, b):

@@ -343,3 +343,28 @@ def test_fcg_error_energy_never_grows_and_beats_plain_cycles():
         q = mg.vcycle(q, b)
         n_plain += 1
     assert rel_fcg <= 1e-8 and n_fcg < n_plain
+
+
+# ------------------------------------------------------------------ per-level sweep counts
+def test_coarse_sweeps_change_only_the_coarser_levels_and_keep_the_fixed_point():
+    """coarse_sweeps = the finest level's counts is the plain V-cycle exactly; with one sweep
+    on the coarser levels the V-cycle still contracts to the discrete solution (a dense
+    solve) on a box channel."""
+    from paper_2603_21869_gb300 import cases
+    from oracle.step import OracleCase
+    spec = cases.heated_channel_3d(16, 8, 8, mg_levels=3, boxes=[cases.Box(4, 8, 2, 5, 0, 4)])
+    mg = OracleCase(spec).mg
+    lev = mg.levels[0]
+    b = np.where(lev.fluid, np.random.default_rng(4).normal(size=lev.shape), 0.0)
+    p0 = np.zeros(lev.shape)
+    same = OracleCase(spec.replace(coarse_sweeps=spec.pre_sweeps)).mg
+    assert np.array_equal(mg.vcycle(p0, b), same.vcycle(p0, b))
+    one = OracleCase(spec.replace(coarse_sweeps=1)).mg
+    assert one.sweeps(0) == (spec.pre_sweeps, spec.post_sweeps) and one.sweeps(1) == (1, 1)
+    assert not np.array_equal(mg.vcycle(p0, b), one.vcycle(p0, b))
+    p = p0
+    for _ in range(30):
+        p = one.vcycle(p, b)
+    pd = direct_solve(lev, b)
+    assert np.max(np.abs(p - pd)) <= 1e-9 * np.max(np.abs(pd))
+
