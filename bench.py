@@ -142,6 +142,14 @@ def run_reference(args, spec, label, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def parse_params(text):
+    """PRE,POST,INNER,PLANES,KRYLOV[,COARSE] -> six ints (COARSE defaults to 0)."""
+    v = [int(x) for x in text.split(",")]
+    if len(v) not in (5, 6):
+        raise SystemExit("--params wants PRE,POST,INNER,PLANES,KRYLOV[,COARSE]")
+    return tuple(v + [0] * (6 - len(v)))
+
+
 def breakdown(prof, nsteps, traffic=None):
     """Per-site table, dominant kernel roofline and V-cycle bandwidth from profile tallies
     (traffic: {site: DRAM bytes per launch} from an ncu capture)."""
@@ -194,15 +202,18 @@ def run_batched(args, rank, ws, local, dist):
     specs = cases.batched_channels(args.cases, seed=rank, precision=prec, mg_levels=5)
     tuning = None
     if args.params:
-        pre, post, inner, _planes, kry = (int(x) for x in args.params.split(","))
-        specs = [sp.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, krylov=kry) for sp in specs]
-        tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "krylov": kry, "fixed": True}
+        pre, post, inner, _planes, kry, coarse = parse_params(args.params)
+        specs = [sp.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, krylov=kry, coarse_sweeps=coarse)
+                 for sp in specs]
+        tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "krylov": kry,
+                  "coarse_sweeps": coarse, "fixed": True}
     elif not args.no_autotune:
         # sweep counts, V-cycles per outer residual and planes per block, measured on the largest case
         _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
         # (the planes per block are left to the batch rule: a batch has blocks to spare)
         specs = [sp.replace(pre_sweeps=tuning["pre_sweeps"], post_sweeps=tuning["post_sweeps"],
-                            inner_cycles=tuning["inner_cycles"], krylov=tuning["krylov"]) for sp in specs]
+                            inner_cycles=tuning["inner_cycles"], krylov=tuning["krylov"],
+                            coarse_sweeps=tuning["coarse_sweeps"]) for sp in specs]
     N = sum(sp.cells for sp in specs)
     cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
     batch = binding.Batch(cs, stream=stream.cuda_stream)
@@ -492,7 +503,7 @@ def main():
     ap.add_argument("--accuracy-cases", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
-    ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV",
+    ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV[,COARSE]",
                     help="fixed multigrid parameters instead of the autotuner's (e.g. for profiling runs, where "
                          "the profiler's overhead would distort the autotuner's timings)")
     ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
@@ -530,11 +541,12 @@ def main():
     rank, ws, local, dist = dist_setup()
     tuning = None
     if args.params:
-        pre, post, inner, planes, kry = (int(x) for x in args.params.split(","))
-        spec = spec.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, sweep_planes=planes, krylov=kry)
+        pre, post, inner, planes, kry, coarse = parse_params(args.params)
+        spec = spec.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, sweep_planes=planes, krylov=kry,
+                            coarse_sweeps=coarse)
         label = label.replace("V(3,3)", f"V({pre},{post})")
         tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "sweep_planes": planes,
-                  "krylov": kry, "fixed": True}
+                  "krylov": kry, "coarse_sweeps": coarse, "fixed": True}
     elif args.impl == "ours" and not args.no_autotune and spec.nz > 1:
         # smoother sweeps, V-cycles per outer residual and planes per block, measured (fvm_autotune)
         from paper_2603_21869_gb300 import binding as _b, build as _bd

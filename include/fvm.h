@@ -123,7 +123,8 @@ typedef struct {
                                         correction made A-orthogonal to the previous direction,
                                         by the length that minimises the error's A-norm); 0: none.
                                         Not with mg_variant 1.  An addition beyond the paper. */
-    int32_t reserved_k;              /* 0 */
+    int32_t coarse_sweeps;           /* pre- and post-sweeps on every level below the finest;
+                                        0: the finest level's counts.  Not with mg_variant 1. */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
@@ -289,9 +290,10 @@ fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
    residual (1..4 with reduced-precision corrections, 1 in FP64) times the
    flexible-CG acceleration off / on (off only with mg_variant 1); pass 2: the
    z planes per block of the four-cell level kernels (the rule, 1 .. 32)
-   with the best pass-1 choice.  Candidates that stop at max_vcycles above
+   with the best pass-1 choice; pass 3: 1 and 2 sweeps on the levels below
+   the finest (coarse_sweeps), where fewer than the finest level's.  Candidates that stop at max_vcycles above
    the tolerance are not eligible.  Copy the result into the descriptor's
-   pre_sweeps, post_sweeps, inner_cycles, sweep_planes and krylov.  Device memory: one
+   pre_sweeps, post_sweeps, inner_cycles, sweep_planes, krylov and coarse_sweeps.  Device memory: one
    temporary case at a time.  Errors: FVM_ERR_INVALID, FVM_ERR_NOT_CONVERGED
    (no candidate converged), FVM_ERR_CUDA. */
 typedef struct {
@@ -299,6 +301,8 @@ typedef struct {
     double  ms_per_step;             /* of the choice, device time per step */
     int32_t candidates;              /* candidates timed */
     int32_t krylov;                  /* 0 / 1: the flexible-CG acceleration */
+    int32_t coarse_sweeps;           /* sweeps on the levels below the finest (0: as the finest) */
+    int32_t reserved;
 } fvm_tuning;
 
 fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm_tuning* out);

@@ -5,10 +5,11 @@
 //
 // Pass 1 tries the smoother sweep counts V(nu, nu), nu = 2, 3, 4, the
 // V-cycles per FP64 outer residual (1..4 with reduced-precision corrections,
-// 1 in FP64) and the flexible-CG acceleration off / on; pass 2 tries the z planes per block of the four-cell level
-// kernels (the built-in rule, 1 .. 32) with the best pass-1 choice.  A
-// candidate whose solves stop at max_vcycles above the tolerance is not
-// eligible.
+// 1 in FP64) and the flexible-CG acceleration off / on; pass 2 tries the z
+// planes per block of the four-cell level kernels (the built-in rule,
+// 1 .. 32) with the best pass-1 choice; pass 3 tries 1 and 2 sweeps on the
+// levels below the finest.  A candidate whose solves stop at max_vcycles
+// above the tolerance is not eligible.
 #include <cstring>
 #include <string>
 #include <vector>
@@ -18,7 +19,7 @@
 namespace {
 
 struct Trial {
-    int pre, post, inner, planes, krylov;
+    int pre, post, inner, planes, krylov, coarse;
     double ms;
 };
 
@@ -30,6 +31,7 @@ double time_candidate(const fvm_case_desc& base, const Trial& t, int steps, cuda
     d.inner_cycles = t.inner;
     d.sweep_planes = t.planes;
     d.krylov = t.krylov;
+    d.coarse_sweeps = t.coarse;
     d.stream = s;
     fvm_case* c = nullptr;
     if (fvm_create_case(&d, &c) != FVM_OK) return -1.0;
@@ -71,13 +73,13 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     std::vector<int> inners;
     if (desc->precision == FVM_FP64) inners = {1};
     else inners = {1, 2, 3, 4};
-    Trial best{0, 0, 0, 0, 0, -1.0};
+    Trial best{0, 0, 0, 0, 0, 0, -1.0};
     int tried = 0;
     const int kmax = desc->mg_variant == 1 ? 0 : 1;
     for (int kry = 0; kry <= kmax; ++kry)
         for (int nu : {2, 3, 4})
             for (int inner : inners) {
-                Trial t{nu, nu, inner, 0, kry, 0.0};
+                Trial t{nu, nu, inner, 0, kry, 0, 0.0};
                 t.ms = time_candidate(*desc, t, steps, s);
                 ++tried;
                 if (t.ms > 0.0 && (best.ms < 0.0 || t.ms < best.ms)) best = t;
@@ -86,6 +88,15 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
         for (int planes : {1, 2, 4, 8, 16, 32}) {
             Trial t = best;
             t.planes = planes;
+            t.ms = time_candidate(*desc, t, steps, s);
+            ++tried;
+            if (t.ms > 0.0 && t.ms < best.ms) best = t;
+        }
+    if (best.ms > 0.0 && desc->mg_variant == 0)
+        for (int k : {1, 2}) {
+            if (k >= best.pre) continue;
+            Trial t = best;
+            t.coarse = k;
             t.ms = time_candidate(*desc, t, steps, s);
             ++tried;
             if (t.ms > 0.0 && t.ms < best.ms) best = t;
@@ -102,6 +113,7 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     o.inner_cycles = best.inner;
     o.sweep_planes = best.planes;
     o.krylov = best.krylov;
+    o.coarse_sweeps = best.coarse;
     o.ms_per_step = best.ms;
     o.candidates = tried;
     *out = o;

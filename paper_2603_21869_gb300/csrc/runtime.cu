@@ -402,6 +402,8 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->mg_variant < 0 || d->mg_variant > 1) return fail(FVM_ERR_INVALID, "mg_variant must be 0 or 1");
     if (d->krylov < 0 || d->krylov > 1) return fail(FVM_ERR_INVALID, "krylov must be 0 or 1");
     if (d->krylov == 1 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "krylov 1 needs mg_variant 0");
+    if (d->coarse_sweeps < 0 || d->coarse_sweeps > 64) return fail(FVM_ERR_INVALID, "coarse_sweeps must be 0..64");
+    if (d->coarse_sweeps > 0 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "coarse_sweeps needs mg_variant 0");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -699,6 +701,14 @@ fvm_status krylov_step(fvm_case* c, int zi) {
     return FVM_OK;
 }
 
+// pre- and post-sweeps on level l (coarse_sweeps on the levels below the finest, when set)
+int pre_at(const fvm_case* c, size_t l) {
+    return l > 0 && c->desc.coarse_sweeps > 0 ? c->desc.coarse_sweeps : c->desc.pre_sweeps;
+}
+int post_at(const fvm_case* c, size_t l) {
+    return l > 0 && c->desc.coarse_sweeps > 0 ? c->desc.coarse_sweeps : c->desc.post_sweeps;
+}
+
 // Level l (> 0) gets its first Jacobi sweep from the restriction that forms its r:
 // both it and its parent take the plain kernels (not the coarse, tail or TMA forms).
 bool first_sweep_fused(const fvm_case* c, size_t l) {
@@ -737,13 +747,13 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
         double bytes = 0.0;
         for (size_t q = l; q < c->lc; ++q) {
             const double n = (double)c->levels[q].dev.N, nc = (double)c->levels[q + 1].dev.N;
-            bytes += (2 * n * si + 2 * n) + (c->desc.pre_sweeps - 1 + c->desc.post_sweeps) * (3 * n * si + 2 * n) +
+            bytes += (2 * n * si + 2 * n) + (pre_at(c, q) - 1 + post_at(c, q)) * (3 * n * si + 2 * n) +
                      2 * (2 * n * si + nc * si + 2 * n);
         }
         KLAUNCH("vtail", bytes, 1,
                 launch_tail(c->inner, c->tail, c->coarse, c->Ainv, c->sst, c->tail_blocks,
                             coarse_cta_smem(c->coarse, c->inner), s));
-        out_idx = tail_out_index(c->desc.pre_sweeps, c->desc.post_sweeps);
+        out_idx = tail_out_index(pre_at(c, l), post_at(c, l));
         return FVM_OK;
     }
     DevLevel& Lc = c->levels[l + 1];
@@ -753,7 +763,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
         const int reps = l == 0 ? c->rule_inner : 1;
         int cur = 0;
         for (int rep = 0; rep < reps; ++rep) {
-            int n = c->desc.pre_sweeps;
+            int n = pre_at(c, l);
             if (rep == 0) {
                 if (l > 0)
                     KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
@@ -767,7 +777,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
             ST_TRY(cycle(c, l + 1, ci));
             const bool top = l == 0 && rep == reps - 1 && !c->desc.krylov;
             KLAUNCH(lvl_name(top ? "up_tma_to_p" : "up_tma", l), N * (3 * si + 2 + (top ? 16 : 0)) + Nc * si, 1,
-                    launch_up_tma(c->desc.post_sweeps, top, L.maps, cur, ci, L.dev, Lc.dev, L.e[cur ^ 1], c->p,
+                    launch_up_tma(post_at(c, l), top, L.maps, cur, ci, L.dev, Lc.dev, L.e[cur ^ 1], c->p,
                                   c->sst, s));
             if (!top) cur ^= 1;
         }
@@ -780,7 +790,7 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     const int reps = l == 0 ? c->rule_inner : 1;
     int cur = 0;
     for (int rep = 0; rep < reps; ++rep) {
-        int pre = c->desc.pre_sweeps;
+        int pre = pre_at(c, l);
         if (rep == 0) {
             if (l > 0 && !first_sweep_fused(c, l))
                 KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
@@ -800,8 +810,9 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
         ST_TRY(cycle(c, l + 1, ci));
         KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + 2 * N, 1,
                 launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], c->sst, s));
-        for (int k = 0; k < c->desc.post_sweeps; ++k) {
-            if (l == 0 && rep == reps - 1 && k == c->desc.post_sweeps - 1 && !c->desc.krylov) {
+        const int post = post_at(c, l);
+        for (int k = 0; k < post; ++k) {
+            if (l == 0 && rep == reps - 1 && k == post - 1 && !c->desc.krylov) {
                 KLAUNCH("sweep_to_p_L0", 2 * N * si + 16 * N + 2 * N, 1,
                         launch_sweep_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, c->sst, s));
             } else {
@@ -1224,8 +1235,8 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         c->lc = lc;
         memset(&c->coarse, 0, sizeof(c->coarse));
         c->coarse.nl = (int)(c->levels.size() - lc);
-        c->coarse.pre = d.pre_sweeps;
-        c->coarse.post = d.post_sweeps;
+        c->coarse.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;   // (levels below the finest)
+        c->coarse.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
         for (int q = 0; q < c->coarse.nl; ++q) c->coarse.lv[q] = c->levels[lc + q].dev;
         CUDA_TRY(prepare_coarse_cta(pl.inner, coarse_cta_smem(c->coarse, pl.inner)));
         // a thread-block cluster holds more levels in its distributed shared memory; take
@@ -1272,8 +1283,8 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
                 }
                 if (best_lc == 0 || best_lc > lc) continue;   // no better than the single CTA
                 cl.nl = (int)(c->levels.size() - best_lc);
-                cl.pre = d.pre_sweeps;
-                cl.post = d.post_sweeps;
+                cl.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;
+                cl.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
                 cl.cs = cs;
                 cl.D = D;
                 cl.lm = (int)(lm_abs > best_lc ? lm_abs - best_lc : 0);
@@ -1312,6 +1323,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     // fused TMA kernels on the grid levels that qualify (FP32 inner, tile-divisible 3D); opt-in with
     // FVM_TMA=1: on GB300 they measure slower than the one-sweep kernels (shared-memory issue bound)
     if (pl.inner == FVM_FP32 && getenv_flag("FVM_TMA") == 1 && d.pre_sweeps <= 3 && d.post_sweeps <= 4 &&
+        d.coarse_sweeps == 0 &&
         tma_prepare() == cudaSuccess) {
         for (size_t l = 0; l < c->lc; ++l) {
             DevLevel& D = c->levels[l];
@@ -1340,8 +1352,8 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
             t.ls = (int)ls;
             t.lc = (int)c->lc;
             t.nl = (int)c->levels.size();
-            t.pre = d.pre_sweeps;
-            t.post = d.post_sweeps;
+            t.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;
+            t.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
             for (size_t l = 0; l < c->levels.size(); ++l) {
                 t.lv[l] = c->levels[l].dev;
                 t.e[l][0] = c->levels[l].e[0];

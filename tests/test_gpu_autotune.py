@@ -22,8 +22,11 @@ def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
     spec = cases.heated_channel_3d(128, 32, 32, mg_levels=4, precision=cases.FP32, mg_rel_tol=1e-8,
                                    max_vcycles=40)
     tuned, info = binding.autotune(spec, steps=3)
-    # pass 1: nu in {2, 3, 4} x inner in {1..4} x krylov in {0, 1}; pass 2: six plane counts
-    assert info["candidates"] == 3 * 4 * 2 + 6 and info["ms_per_step"] > 0
+    # pass 1: nu in {2, 3, 4} x inner in {1..4} x krylov in {0, 1}; pass 2: six plane counts;
+    # pass 3: coarse-level sweeps 1 and 2 where fewer than the chosen nu
+    extra = sum(1 for k in (1, 2) if k < info["pre_sweeps"])
+    assert info["candidates"] == 3 * 4 * 2 + 6 + extra and info["ms_per_step"] > 0
+    assert info["coarse_sweeps"] in (0, 1, 2) and tuned.coarse_sweeps == info["coarse_sweeps"]
     assert info["pre_sweeps"] == info["post_sweeps"] in (2, 3, 4) and info["krylov"] in (0, 1)
     assert tuned.krylov == info["krylov"]
     assert 1 <= info["inner_cycles"] <= 4 and info["sweep_planes"] in (0, 1, 2, 4, 8, 16, 32)

@@ -334,6 +334,18 @@ def test_paper_multigrid_scheme_matches_oracle(name):
     assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name}, Algorithm 1")
 
 
+@pytest.mark.parametrize("name", ["channel3d_box_vent", "room_buoyant", "channel2d_ragged"])
+def test_coarse_level_sweep_counts_match_oracle(name):
+    """One sweep on each side of every level below the finest (coarse_sweeps = 1),
+    the finest level keeping its own: FP64 fields within 1e-10 of the oracle."""
+    spec = SPECS[name]().replace(coarse_sweeps=1)
+    with binding.Case(spec) as c:
+        c.step(2)
+        got = c.read()
+    o = OracleCase(spec).step(2)
+    assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name}, coarse_sweeps 1")
+
+
 def test_paper_scheme_iterations_track_the_oracle_and_converge_slower():
     spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3, fixed_vcycles=1)
     o = OracleCase(spec)
