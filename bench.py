@@ -501,6 +501,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cases", type=int, default=64, help="batched workload: cases per GPU")
     ap.add_argument("--accuracy-cases", type=int, default=8)
+    ap.add_argument("--accuracy-steps", type=int, default=5, help="steps of the per-field comparison with FP64")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
     ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV[,COARSE]",
@@ -648,6 +649,20 @@ def main():
         if dist:
             e2e["value"] = ws * N * args.e2e_steps / replicas.max_over_ranks(te)
 
+    # per-field error of this precision against the FP64 path: the same case from its initial
+    # state, a few steps each (not timed)
+    accuracy = None
+    if args.precision != "f64" and not args.no_compare and rank == 0:
+        case.close()
+        runs = {}
+        for prec in (PREC[args.precision], cases.FP64):
+            with binding.Case(spec.replace(precision=prec), stream=stream.cuda_stream) as c2:
+                st2 = c2.step(args.accuracy_steps, allow_not_converged=True)
+                runs[prec] = (c2.read(), st2)
+        (got, s_got), (ref, s_ref) = runs[PREC[args.precision]], runs[cases.FP64]
+        accuracy = {"steps": args.accuracy_steps, "max_rel_error_vs_fp64": field_errors(got, ref),
+                    "rel_residual": s_got["rel_residual"], "rel_residual_fp64": s_ref["rel_residual"]}
+
     line = None
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": ws,
@@ -672,7 +687,7 @@ def main():
                 "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                                 "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
-                "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "accuracy": accuracy}
     case.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec)
