@@ -500,7 +500,9 @@ struct SweepV4K {
     TI* eout;
     double* p;
     const SolveState* st;
-    int zc;   // planes per block
+    int zc;    // planes per block
+    int lrl;   // log2 of the lanes per row segment (5: a warp per 128-cell segment; 4, 3, 2: a warp
+               // covers 2, 4 or 8 rows of 64, 32 or 16 cells, so narrow rows leave no lane idle)
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
@@ -509,8 +511,8 @@ template <class TI, int MODE>
 __device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
     using C = float;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int lane = threadIdx.x;
-    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const int sy = nx, sz = nx * ny;
@@ -538,12 +540,12 @@ __device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
         Vec4<TI>::load(r, base + own, rr);
         const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
         const C xls = lane == 0 ? to_c<C>(ldg(ein + base + xl)) : (C)0;
-        const C xrs = lane == TX - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
+        const C xrs = lane == LR - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
         Vec4<TI>::load(ein, min(k + 2, nz - 1) * sz + own, en);   // plane after next
-        C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
-        C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
+        C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
         if (lane == 0) left = xls;
-        if (lane == TX - 1) right = xrs;
+        if (lane == LR - 1) right = xrs;
         if (last) right = ec[3];
         const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
         const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
@@ -1870,11 +1872,15 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
     if constexpr (sizeof(TI) < 8) {
         // four cells per thread on large levels and in batches (their blocks add up over the cases)
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-            const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
-        const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
-        const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
-                        (unsigned)((L.n[2] + zc - 1) / zc));
-        return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc}, grid, dim3(TX, TY), 0, s);
+            // the widest row segment (128, 64, 32 or 16 cells) that divides nx
+            const int lrl = L.n[0] % 128 == 0 ? 5
+                            : (L.n[0] % 64 == 0 ? 4 : (L.n[0] % 32 == 0 ? 3 : (L.n[0] % 16 == 0 ? 2 : 5)));
+            const int wx = 4 << lrl, wy = TY << (5 - lrl);
+            const int tiles = ((L.n[0] + wx - 1) / wx) * ((L.n[1] + wy - 1) / wy);
+            const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
+            const dim3 grid((unsigned)((L.n[0] + wx - 1) / wx), (unsigned)((L.n[1] + wy - 1) / wy),
+                            (unsigned)((L.n[2] + zc - 1) / zc));
+            return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
         }
     }
     // four cells per thread on large grids and in batches (one launch for all cases of a level)
