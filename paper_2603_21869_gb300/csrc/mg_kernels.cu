@@ -745,7 +745,8 @@ struct Resid0V4K {
     TI* e;
     double* partials;
     SolveState* st;
-    int zc;   // planes per block
+    int zc;    // planes per block
+    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
     __device__ bool live() const { return st->active != 0; }
     __device__ int run(const BlockAt& at) const;
 };
@@ -753,8 +754,8 @@ struct Resid0V4K {
 template <class TI>
 __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int lane = threadIdx.x;
-    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const int sy = nx, sz = nx * ny;
@@ -779,12 +780,12 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
         const float4 bq = __ldg(reinterpret_cast<const float4*>(b + base + own));
         const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
         const FF xls = lane == 0 ? ff_split(__ldg(pp + base + xl)) : FF{0.0f, 0.0f};
-        const FF xrs = lane == TX - 1 ? ff_split(__ldg(pp + base + xr)) : FF{0.0f, 0.0f};
+        const FF xrs = lane == LR - 1 ? ff_split(__ldg(pp + base + xr)) : FF{0.0f, 0.0f};
         ff_load4(pp, min(k + 2, nz - 1) * sz + own, en);
-        FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1), __shfl_up_sync(0xffffffffu, ec[3].l, 1)};
-        FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1), __shfl_down_sync(0xffffffffu, ec[0].l, 1)};
+        FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1, LR), __shfl_up_sync(0xffffffffu, ec[3].l, 1, LR)};
+        FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1, LR), __shfl_down_sync(0xffffffffu, ec[0].l, 1, LR)};
         if (lane == 0) left = xls;
-        if (lane == TX - 1) right = xrs;
+        if (lane == LR - 1) right = xrs;
         if (lastc) right = ec[3];
         const FF xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
         const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
@@ -864,7 +865,8 @@ struct FcgDotV4K {
     const TI* dp;
     double* partials;
     SolveState* st;
-    int zc;   // planes per block
+    int zc;    // planes per block
+    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
     __device__ bool live() const { return st->active != 0; }
     __device__ void run(const BlockAt& at) const;
 };
@@ -873,8 +875,8 @@ template <class TI>
 __device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
     using C = float;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int lane = threadIdx.x;
-    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const int sy = nx, sz = nx * ny;
@@ -901,12 +903,12 @@ __device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
         if (have) Vec4<TI>::load(dp, base + own, dd);
         const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
         const C xls = lane == 0 ? to_c<C>(ldg(zz + base + xl)) : (C)0;
-        const C xrs = lane == TX - 1 ? to_c<C>(ldg(zz + base + xr)) : (C)0;
+        const C xrs = lane == LR - 1 ? to_c<C>(ldg(zz + base + xr)) : (C)0;
         Vec4<TI>::load(zz, min(k + 2, nz - 1) * sz + own, en);
-        C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
-        C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
+        C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
         if (lane == 0) left = xls;
-        if (lane == TX - 1) right = xrs;
+        if (lane == LR - 1) right = xrs;
         if (lastc) right = ec[3];
         const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
         const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
@@ -1786,8 +1788,16 @@ int resid0_blocks(int nx, int ny, int nz) {
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + BZ - 1) / BZ);
 }
 
+// four-cell kernels: log2 of the lanes per row segment, the widest segment of 128, 64, 32 or
+// 16 cells that divides nx (a warp then covers 1, 2, 4 or 8 rows)
+static int v4_lrl(int nx) {
+    return nx % 128 == 0 ? 5 : (nx % 64 == 0 ? 4 : (nx % 32 == 0 ? 3 : (nx % 16 == 0 ? 2 : 5)));
+}
+
 int level0_blocks_max(int nx, int ny, int nz) {
-    const int four = ((nx + V4X - 1) / V4X) * ((ny + TY - 1) / TY) * nz;   // a four-cell pass, one plane a block
+    // a four-cell pass with this nx's row segments, one plane a block
+    const int lrl = v4_lrl(nx), wx = 4 << lrl, wy = TY << (5 - lrl);
+    const int four = ((nx + wx - 1) / wx) * ((ny + wy - 1) / wy) * nz;
     const int r0 = resid0_blocks(nx, ny, nz);
     return four > r0 ? four : r0;
 }
@@ -1815,6 +1825,14 @@ cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
 
 static int sweep_planes(int tiles, int nz, int fixed);
 
+// four-cell kernels: the block's x-y extent for the row segments of v4_lrl
+static dim3 v4_grid(const LevelDev& L, int lrl, int& zc) {
+    const int wx = 4 << lrl, wy = TY << (5 - lrl);
+    const int tiles = ((L.n[0] + wx - 1) / wx) * ((L.n[1] + wy - 1) / wy);
+    zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
+    return dim3((unsigned)((L.n[0] + wx - 1) / wx), (unsigned)((L.n[1] + wy - 1) / wy), (unsigned)((L.n[2] + zc - 1) / zc));
+}
+
 cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
                           double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                           cudaGraphConditionalHandle cond2, int use_cond, cudaStream_t s) {
@@ -1823,12 +1841,11 @@ cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double*
         if constexpr (sizeof(TI) < 8) {
             // four cells per thread in float-float on large levels and in batches
             if (bprec == FVM_FP32 && L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-                const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
-                const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
-                const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
-                                (unsigned)((L.n[2] + zc - 1) / zc));
+                const int lrl = v4_lrl(L.n[0]);
+                int zc = 0;
+                const dim3 grid = v4_grid(L, lrl, zc);
                 // (at most level0_blocks_max(n) blocks: partials has room)
-                return launch_r0(Resid0V4K<TI>{L, p, (const float*)b, (TI*)r, (TI*)e, partials, st, zc}, grid,
+                return launch_r0(Resid0V4K<TI>{L, p, (const float*)b, (TI*)r, (TI*)e, partials, st, zc, lrl}, grid,
                                  dim3(TX, TY), cond, cond2, use_cond, s);
             }
         }
@@ -1872,14 +1889,9 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
     if constexpr (sizeof(TI) < 8) {
         // four cells per thread on large levels and in batches (their blocks add up over the cases)
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-            // the widest row segment (128, 64, 32 or 16 cells) that divides nx
-            const int lrl = L.n[0] % 128 == 0 ? 5
-                            : (L.n[0] % 64 == 0 ? 4 : (L.n[0] % 32 == 0 ? 3 : (L.n[0] % 16 == 0 ? 2 : 5)));
-            const int wx = 4 << lrl, wy = TY << (5 - lrl);
-            const int tiles = ((L.n[0] + wx - 1) / wx) * ((L.n[1] + wy - 1) / wy);
-            const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
-            const dim3 grid((unsigned)((L.n[0] + wx - 1) / wx), (unsigned)((L.n[1] + wy - 1) / wy),
-                            (unsigned)((L.n[2] + zc - 1) / zc));
+            const int lrl = v4_lrl(L.n[0]);
+            int zc = 0;
+            const dim3 grid = v4_grid(L, lrl, zc);
             return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
         }
     }
@@ -1972,12 +1984,11 @@ static cudaError_t fcg_launch(const LevelDev& L, const TI* z, const TI* r, TI* d
                               SolveState* st, cudaStream_t s) {
     if constexpr (sizeof(TI) < 8) {
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-            const int tiles = ((L.n[0] + V4X - 1) / V4X) * ((L.n[1] + TY - 1) / TY);
-            const int zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
-            const dim3 grid((unsigned)((L.n[0] + V4X - 1) / V4X), (unsigned)((L.n[1] + TY - 1) / TY),
-                            (unsigned)((L.n[2] + zc - 1) / zc));
+            const int lrl = v4_lrl(L.n[0]);
+            int zc = 0;
+            const dim3 grid = v4_grid(L, lrl, zc);
             // (at most level0_blocks_max(n) blocks: partials has room)
-            cudaError_t err = launch_k(FcgDotV4K<TI>{L, z, r, dp, partials, st, zc}, grid, dim3(TX, TY), 0, s);
+            cudaError_t err = launch_k(FcgDotV4K<TI>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
             if (err != cudaSuccess) return err;
             const unsigned nb = (unsigned)((L.N / 4 + FcgUpdV4K<TI>::kThreads - 1) / FcgUpdV4K<TI>::kThreads);
             return launch_k(FcgUpdV4K<TI>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdV4K<TI>::kThreads), 0, s);
