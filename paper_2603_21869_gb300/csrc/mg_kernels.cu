@@ -1012,7 +1012,8 @@ struct ProlongV4K {
     const TI* ec;
     TI* e;
     const SolveState* st;
-    int zc;   // planes per block
+    int zc;    // planes per block
+    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
@@ -1022,8 +1023,8 @@ __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
     using C = float;
     const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
     const int NX = Lc.n[0], NY = Lc.n[1], NZ = Lc.n[2];
-    const int lane = threadIdx.x;
-    const int i4 = at.b.x * V4X + lane * 4, j = at.b.y * TY + threadIdx.y;
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const bool last = i4 + 4 >= nx;
@@ -1047,11 +1048,11 @@ __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
             C c0, c1;
             Vec2<TI>::load(ecp, row + I0, c0, c1);
             const C lft = lane == 0 ? to_c<C>(ldg(ecp + row + max(I0 - 1, 0))) : (C)0;
-            const C rgt = lane == TX - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
-            C left = __shfl_up_sync(0xffffffffu, c1, 1);
-            C right = __shfl_down_sync(0xffffffffu, c0, 1);
+            const C rgt = lane == LR - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
+            C left = __shfl_up_sync(0xffffffffu, c1, 1, LR);
+            C right = __shfl_down_sync(0xffffffffu, c0, 1, LR);
             if (lane == 0) left = lft;
-            if (lane == TX - 1) right = rgt;
+            if (lane == LR - 1) right = rgt;
             if (last) right = c1;
             add[0] += w * ((C)0.75 * c0 + (C)0.25 * left);
             add[1] += w * ((C)0.75 * c0 + (C)0.25 * c1);
@@ -1087,6 +1088,7 @@ struct RRV4K {
     const TI* r;
     TI* rc;
     TI* ec0;   // the coarse level's first sweep, or null
+    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
@@ -1097,8 +1099,8 @@ __device__ void RRV4K<TI>::run(const BlockAt& at) const {
     using C = float;
     const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
     const int NX = Lc.n[0], NY = Lc.n[1];
-    const int lane = threadIdx.x;
-    const int i4 = at.b.x * V4X + lane * 4, J = at.b.y * TY + threadIdx.y, K = at.b.z;
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = at.b.x * (4 * LR) + lane * 4, J = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub, K = at.b.z;
     const bool in = i4 < nx && J < NY;
     const bool last = i4 + 4 >= nx;
     const int fz = Lf.active[2] ? 2 : 1;
@@ -1130,8 +1132,8 @@ __device__ void RRV4K<TI>::run(const BlockAt& at) const {
         const uint2 fb = __ldg(reinterpret_cast<const uint2*>(nbf + at_(jb, k)));
         const C la = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * ja + sz * k)) : (C)0;
         const C lb = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * jb + sz * k)) : (C)0;
-        const C qa = lane == TX - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * ja + sz * k)) : (C)0;
-        const C qb = lane == TX - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * jb + sz * k)) : (C)0;
+        const C qa = lane == LR - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * ja + sz * k)) : (C)0;
+        const C qb = lane == LR - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * jb + sz * k)) : (C)0;
 #pragma unroll
         for (int row = 0; row < 2; ++row) {
             const C* ec = row ? eb : ea;
@@ -1141,10 +1143,10 @@ __device__ void RRV4K<TI>::run(const BlockAt& at) const {
             const C* zl = row ? zb : za;
             const C* zh = row ? wb : wa;
             const uint2 fw = row ? fb : fa;
-            C left = __shfl_up_sync(0xffffffffu, ec[3], 1);
-            C right = __shfl_down_sync(0xffffffffu, ec[0], 1);
+            C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
+            C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
             if (lane == 0) left = row ? lb : la;
-            if (lane == TX - 1) right = row ? qb : qa;
+            if (lane == LR - 1) right = row ? qb : qa;
             if (last) right = ec[3];
             const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
             const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
@@ -1925,12 +1927,13 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
                                   void* rc, void* ec0, const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
-        const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lc.n[1] + TY - 1) / TY), (unsigned)Lc.n[2]);
+        const int lrl = v4_lrl(Lf.n[0]), wx = 4 << lrl, wy = TY << (5 - lrl);
+        const dim3 grid((unsigned)((Lf.n[0] + wx - 1) / wx), (unsigned)((Lc.n[1] + wy - 1) / wy), (unsigned)Lc.n[2]);
         if (inner == FVM_FP32)
-            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, (float*)ec0, st},
+            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, (float*)ec0, lrl, st},
                             grid, dim3(TX, TY), 0, s);
         return launch_k(RRV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)e, (const __nv_bfloat16*)r,
-                                             (__nv_bfloat16*)rc, (__nv_bfloat16*)ec0, st},
+                                             (__nv_bfloat16*)rc, (__nv_bfloat16*)ec0, lrl, st},
                         grid, dim3(TX, TY), 0, s);
     }
     if (Lf.active[0] && Lf.active[1]) {
@@ -1949,14 +1952,14 @@ cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc
                                const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
-        const int tiles = ((Lf.n[0] + V4X - 1) / V4X) * ((Lf.n[1] + TY - 1) / TY);
-        const int zc = sweep_planes(tiles, Lf.n[2], Lf.zc_fixed);
-        const dim3 grid((unsigned)((Lf.n[0] + V4X - 1) / V4X), (unsigned)((Lf.n[1] + TY - 1) / TY),
-                        (unsigned)((Lf.n[2] + zc - 1) / zc));
+        const int lrl = v4_lrl(Lf.n[0]);
+        int zc = 0;
+        const dim3 grid = v4_grid(Lf, lrl, zc);
         if (inner == FVM_FP32)
-            return launch_k(ProlongV4K<float>{Lf, Lc, (const float*)ec, (float*)e, st, zc}, grid, dim3(TX, TY), 0, s);
-        return launch_k(ProlongV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc}, grid,
-                        dim3(TX, TY), 0, s);
+            return launch_k(ProlongV4K<float>{Lf, Lc, (const float*)ec, (float*)e, st, zc, lrl}, grid, dim3(TX, TY), 0,
+                            s);
+        return launch_k(ProlongV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc, lrl},
+                        grid, dim3(TX, TY), 0, s);
     }
     DISPATCH_I(inner, err = launch_k(ProlongK<TI>{Lf, Lc, (const TI*)ec, (TI*)e, st}, grid3(Lf), kBlock3, 0, s));
     return err;
