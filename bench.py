@@ -52,7 +52,7 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's denominator is
 TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"): 212.38e6}
 # the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell,
 # from a 32-case capture of the same batch (the first 32 of its cases), scaled by the cells
-TRAFFIC_PER_CELL = {("batched", "f32", "sweep_L0"): 439.06e6 / 29294592}
+TRAFFIC_PER_CELL = {("batched", "f32", "sweep_L0"): 458.10e6 / 29294592}
 
 
 def peaks():
