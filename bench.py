@@ -631,6 +631,21 @@ def main():
     mg_ms = sum(prof[k]["ms"] for k in mg_names)
     kernel_ms = sum(v["ms"] for v in prof.values())
 
+    # the lambda_2 vortex diagnostic (fvm_lambda2) on the current state, outside the step: its
+    # kernel timed by the profiling hook, L2 flushed before each call
+    case.profile(True)
+    lam_out = np.empty(N)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        case.lambda2(out=lam_out)
+    lp = case.profile_read()["lambda2"]
+    case.profile(False)
+    lam_gbs = lp["bytes"] / (lp["ms"] / 1e3) / 1e9
+    diagnostics = {"lambda2": {"ms_per_call": lp["ms"] / lp["launches"], "gbs": lam_gbs,
+                               "frac": lam_gbs / peak, "bytes_per_cell": lp["bytes"] / lp["launches"] / N,
+                               "vortex_cells": int(np.count_nonzero(lam_out < 0))}}
+
     # end to end through the C-ABI with host buffers: write state, one step, read state
     e2e = None
     if args.e2e_steps > 0:
@@ -687,7 +702,8 @@ def main():
                 "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                                 "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
-                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "accuracy": accuracy}
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "accuracy": accuracy,
+                "diagnostics": diagnostics}
     case.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec)

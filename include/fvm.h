@@ -213,6 +213,18 @@ fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n);
 /* Read b (nx*ny*nz doubles) into host memory.  Synchronises. */
 fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
 
+/* lambda_2 vortex criterion of the transient results (Section 3.1.3, after
+   Jeong and Hussain 1995): for every cell, the middle eigenvalue of
+   S^2 + Omega^2, where S and Omega are the symmetric and antisymmetric parts
+   of the cell velocity gradient L_j D_j BC_j(u_i) of Algorithm 4 (boundary
+   and obstacle neighbours by their Section 2.5 ghosts).  Negative values mark
+   vortex cores; solid cells hold 0.  Computed from the case's current u, v, w
+   in its compute precision; written to host_out as nx*ny*nz doubles, x
+   fastest (caller-owned, n = its capacity in doubles).  Runs on the case's
+   stream and synchronises it; the fields are not changed.
+   FVM_ERR_INVALID for a null case or buffer or n < nx*ny*nz. */
+fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n);
+
 /* ---------------------------------------------------------------- batches
    Cases stepped together (uneven sizes allowed).  Every launch site of the
    step (each step kernel, and each multigrid kernel of each level) runs

@@ -110,8 +110,8 @@ class BatchInfo(ct.Structure):
 
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
-           "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
-           "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
+           "fvm_lambda2", "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
+           "fvm_profile_read", "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
            "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info", "fvm_batch_destroy",
            "fvm_batch_profile", "fvm_server_create",
            "fvm_server_now", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields",
@@ -141,6 +141,7 @@ def lib():
     L.fvm_write_fields.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_set_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_read_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_lambda2.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_step_batch.argtypes = [ct.POINTER(CP), ct.c_int, ct.c_int, ct.POINTER(StepStats)]
     L.fvm_case_get_info.argtypes = [CP, ct.POINTER(CaseInfo)]
     L.fvm_set_option.argtypes = [CP, ct.c_int, ct.c_int64]
@@ -173,7 +174,7 @@ def lib():
     L.fvm_struct_sizes.restype = None
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
-                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_step_batch",
+                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2", "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
                  "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
                  "fvm_batch_profile",
@@ -342,6 +343,15 @@ class Case:
     def read_rhs(self):
         buf = np.empty(self.N, dtype=np.float64)
         _check(lib().fvm_read_poisson_rhs(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        nx, ny, nz = self.shape
+        return buf.reshape(nz, ny, nx).transpose(2, 1, 0)
+
+    def lambda2(self, out=None):
+        """lambda_2 vortex criterion of the current velocity (fvm_lambda2),
+        shape (nx, ny, nz); `out` (N float64, optional) receives the flat
+        x-fastest values."""
+        buf = out if out is not None else np.empty(self.N, dtype=np.float64)
+        _check(lib().fvm_lambda2(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
         nx, ny, nz = self.shape
         return buf.reshape(nz, ny, nx).transpose(2, 1, 0)
 

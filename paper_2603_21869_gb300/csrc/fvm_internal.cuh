@@ -287,6 +287,7 @@ cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const
                        cudaStream_t s);
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
                            const double* p, const double* dt_state, cudaStream_t s);
+cudaError_t launch_lambda2(int prec, const CaseDev& cd, StatePtrs in, double* out, cudaStream_t s);
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 

@@ -2057,6 +2057,19 @@ fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n) {
     return FVM_OK;
 }
 
+fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n) {
+    if (!c || !host_out) return fail(FVM_ERR_INVALID, "null case or buffer");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)N) return fail(FVM_ERR_INVALID, "host buffer too small");
+    const double sz = (double)elem_size(c->prec);
+    // algorithmic bytes: u, v, w, the cell tag, the FP64 result
+    KLAUNCH("lambda2", (double)N * (3 * sz + 1 + 8), 1,
+            launch_lambda2(c->prec, c->cd, ptrs(c->cur), c->staging, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(host_out, c->staging, N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
 fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out) {
     if (!out) return fail(FVM_ERR_INVALID, "null output");
     ST_TRY(batch_check(cases, n));

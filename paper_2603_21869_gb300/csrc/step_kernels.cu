@@ -556,6 +556,111 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
     }
 }
 
+// ------------------------------------------------------------------ lambda_2 diagnostic
+// The vortex criterion of the transient results (Section 3.1.3; Jeong and
+// Hussain 1995): lambda_2, the middle eigenvalue of the symmetric matrix
+// M = S^2 + Omega^2 of the cell velocity gradient.  The gradient is the cell
+// gradient L_j * D_j * BC_j(u_i) of Algorithm 4 (the destruction kernel's),
+// so wall, inlet, outlet and obstacle neighbours take their Section 2.5
+// ghosts.  Solid cells get 0.  The result is written as FP64.
+//
+// Middle eigenvalue of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// (Golub and Van Loan, "Matrix Computations", the symmetric Schur
+// decomposition and the cyclic Jacobi method).  The rotation in the (p, q)
+// plane with tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c zeroes a_pq and gives
+// a_pp - t a_pq, a_qq + t a_pq, and (c a_rp - s a_rq, s a_rp + c a_rq) for
+// the third index r.  Sweeps stop once the off-diagonal part is below
+// eps |M|_F (the diagonal is then within that of the eigenvalues, by Weyl's
+// inequality); three to four sweeps suffice, eight bound the loop.  Unlike
+// the trigonometric closed form, whose acos loses half the digits of a
+// nearly repeated eigenvalue, this keeps every eigenvalue to a few eps |M|.
+template <class C> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct Eps<float> { static constexpr float v = 1.1920929e-7f; };
+
+template <class C>
+__device__ __forceinline__ void jacobi_rotate(C& app, C& aqq, C& apq, C& arp, C& arq) {
+    if (apq == (C)0) return;
+    const C tau = (aqq - app) / ((C)2 * apq);
+    const C t = (tau >= (C)0 ? (C)1 : (C)-1) / (fabs(tau) + sqrt((C)1 + tau * tau));
+    const C c = (C)1 / sqrt((C)1 + t * t);
+    const C s = t * c;
+    app -= t * apq;
+    aqq += t * apq;
+    apq = (C)0;
+    const C rp = c * arp - s * arq;
+    arq = s * arp + c * arq;
+    arp = rp;
+}
+
+template <class C>
+__device__ __forceinline__ C sym3_middle_eigenvalue(C a00, C a11, C a22, C a01, C a02, C a12) {
+    const C e = Eps<C>::v;
+    const C fro2 = a00 * a00 + a11 * a11 + a22 * a22 + (C)2 * (a01 * a01 + a02 * a02 + a12 * a12);
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        if (a01 * a01 + a02 * a02 + a12 * a12 <= fro2 * e * e) break;
+        jacobi_rotate(a00, a11, a01, a02, a12);   // (0,1); r = 2
+        jacobi_rotate(a00, a22, a02, a01, a12);   // (0,2); r = 1
+        jacobi_rotate(a11, a22, a12, a01, a02);   // (1,2); r = 0
+    }
+    const C lo = a00 < a11 ? a00 : a11;
+    const C hi = a00 < a11 ? a11 : a00;
+    return a22 < lo ? lo : (a22 > hi ? hi : a22);
+}
+
+template <class S, class C>
+struct Lambda2K {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    StatePtrs in;
+    double* out;
+    __device__ void run(const BlockAt& at) const;
+};
+
+template <class S, class C>
+__device__ void Lambda2K<S, C>::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    if (cd.tag[c]) {
+        out[c] = 0.0;
+        return;
+    }
+    // only u, v, w of the loaded states are used; the other loads are dead code
+    const St<C> P = load_state<S, C>(in, c);
+    C g[3][3];   // g[a][b] = d u_a / d x_b
+    for (int b = 0; b < 3; ++b) {
+        if (!cd.active[b]) {
+            g[0][b] = g[1][b] = g[2][b] = (C)0;
+            continue;
+        }
+        St<C> L, R;
+        neighbour<S, C>(cd, in, i, j, k, b, -1, P, L);
+        neighbour<S, C>(cd, in, i, j, k, b, +1, P, R);
+        const C ih = prm<C>(cd.inv_h[b], cd.f.inv_h[b]);
+        g[0][b] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
+        g[1][b] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
+        g[2][b] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
+    }
+    C Sm[3][3], Om[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Sm[a][b] = (C)0.5 * (g[a][b] + g[b][a]);
+            Om[a][b] = (C)0.5 * (g[a][b] - g[b][a]);
+        }
+    C M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) {
+            C acc = (C)0;
+            for (int e = 0; e < 3; ++e) acc += Sm[a][e] * Sm[e][b] + Om[a][e] * Om[e][b];
+            M[a][b] = acc;
+        }
+    out[c] = (double)sym3_middle_eigenvalue<C>(M[0][0], M[1][1], M[2][2], M[0][1], M[0][2], M[1][2]);
+}
+
 // ------------------------------------------------------------------ pack / unpack
 template <class S>
 __global__ void k_pack(const S* __restrict__ src, double* __restrict__ dst, int64_t N) {
@@ -629,6 +734,12 @@ cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, Stat
                            const double* p, const double* dt_state, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     DISPATCH(prec, err = launch_k(ProjectK<S, C>{cd, L0, in, out, p, dt_state}, grid3(cd), kBlock3, 0, s));
+    return err;
+}
+
+cudaError_t launch_lambda2(int prec, const CaseDev& cd, StatePtrs in, double* out, cudaStream_t s) {
+    cudaError_t err = cudaSuccess;
+    DISPATCH(prec, err = launch_k(Lambda2K<S, C>{cd, in, out}, grid3(cd), kBlock3, 0, s));
     return err;
 }
 

@@ -49,6 +49,13 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(lib):
     assert lib.fvm_batch_wait(None, None) == binding.ERR_INVALID
 
 
+def test_lambda2_rejects_bad_arguments_without_a_gpu(lib):
+    import ctypes as ct
+    buf = (ct.c_double * 4)()
+    assert lib.fvm_lambda2(None, buf, 4) == binding.ERR_INVALID
+    assert "null case" in binding.last_error()
+
+
 def test_autotune_rejects_bad_arguments_without_a_gpu(lib):
     import ctypes as ct
     t = binding.Tuning()
