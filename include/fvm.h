@@ -213,7 +213,7 @@ fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n);
 /* Read b (nx*ny*nz doubles) into host memory.  Synchronises. */
 fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
 
-/* lambda_2 vortex criterion of the transient results (Section 3.1.3, after
+/* lambda_2 vortex criterion of the transient results (Section 3.2.3, after
    Jeong and Hussain 1995): for every cell, the middle eigenvalue of
    S^2 + Omega^2, where S and Omega are the symmetric and antisymmetric parts
    of the cell velocity gradient L_j D_j BC_j(u_i) of Algorithm 4 (boundary

@@ -27,7 +27,7 @@ Modules
   step        one Strang-split time step (Section 2.6) and the seeded
               initial state
   diagnostics the lambda_2 vortex criterion of the transient results
-              (Section 3.1.3)
+              (Section 3.2.3)
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
 against closed forms, invariants, special cases or brute force, except the

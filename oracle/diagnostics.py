@@ -1,4 +1,4 @@
-"""The lambda_2 vortex criterion of the transient results (Section 3.1.3).
+"""The lambda_2 vortex criterion of the transient results (Section 3.2.3).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 

@@ -557,7 +557,7 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
 }
 
 // ------------------------------------------------------------------ lambda_2 diagnostic
-// The vortex criterion of the transient results (Section 3.1.3; Jeong and
+// The vortex criterion of the transient results (Section 3.2.3; Jeong and
 // Hussain 1995): lambda_2, the middle eigenvalue of the symmetric matrix
 // M = S^2 + Omega^2 of the cell velocity gradient.  The gradient is the cell
 // gradient L_j * D_j * BC_j(u_i) of Algorithm 4 (the destruction kernel's),

@@ -1,4 +1,4 @@
-"""The lambda_2 vortex criterion (fvm_lambda2, Section 3.1.3) against the
+"""The lambda_2 vortex criterion (fvm_lambda2, Section 3.2.3) against the
 oracle on the same velocity fields.
 
 The error bound follows from the arithmetic: M = S^2 + Omega^2 =

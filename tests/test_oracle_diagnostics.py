@@ -1,4 +1,4 @@
-"""Pins of the lambda_2 vortex criterion (Section 3.1.3; Jeong and Hussain,
+"""Pins of the lambda_2 vortex criterion (Section 3.2.3; Jeong and Hussain,
 1995): the middle eigenvalue of S^2 + Omega^2 from the cell gradients of
 Algorithm 4.  The central cell gradient is exact on linear velocity fields
 away from the boundary, so interior cells must give the closed forms of
