@@ -6,7 +6,7 @@
  * based Finite Volume Method for Turbulent Flows Using the k-omega Model":
  *
  *   1. dt/2 of the semi-implicit destruction of k and omega
- *      (Section 2.4, Eqs. k_des_step and o_des_step, Algorithm 4);
+ *      (Section 2.5, Eqs. k_des_step and o_des_step, Algorithm 4);
  *   2. one forward-Euler step of convection (first-order upwind, Eq.
  *      upwind_x, Algorithm 2), diffusion (Eq. divergence_theorem) and
  *      production (Eqs. k_gen, o_gen) for u, v, w, T, k, omega
@@ -16,9 +16,9 @@
  *   5. multigrid V-cycles on A p = b, A = -Laplacian (Eq. neg_lap_discretize,
  *      Eq. jacobi_pc, Eqs. restriction / prolongation, Algorithm 1);
  *   6. the projection u = u* - dt grad p (Section 2.4).
- * Boundary conditions use one ghost layer (Section 2.5, Eqs. bc_x - bc) and
+ * Boundary conditions use one ghost layer (Section 2.7, Eqs. bc_x - bc) and
  * masks for solid boxes; walls use omega = 6 nu / (beta_i d^2) in the
- * adjacent cells (Section 2.5); inlet k and omega follow Section 3.2.4.
+ * adjacent cells (Section 2.7); inlet k and omega follow Section 3.2.4.
  *
  * Conventions
  *   - Grid: nx * ny * nz cells, spacing Lx/nx, Ly/ny, Lz/nz; an axis with
@@ -68,7 +68,7 @@ enum { FVM_ADIABATIC = 0, FVM_FIXED_T = 1, FVM_HEAT_FLUX = 2 };
 enum { FVM_FP64 = 0, FVM_FP32 = 1, FVM_BF16_MIXED = 2 };
 enum { FVM_U = 0, FVM_V = 1, FVM_W = 2, FVM_P = 3, FVM_T = 4, FVM_K = 5, FVM_OMEGA = 6 };
 
-/* Boundary condition of a face or vent (Section 2.5). */
+/* Boundary condition of a face or vent (Section 2.7). */
 typedef struct {
     int32_t kind;            /* FVM_WALL / FVM_INLET / FVM_OUTLET / FVM_EMPTY */
     int32_t thermal;         /* walls: FVM_ADIABATIC / FVM_FIXED_T / FVM_HEAT_FLUX */
@@ -217,7 +217,7 @@ fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
    Jeong and Hussain 1995): for every cell, the middle eigenvalue of
    S^2 + Omega^2, where S and Omega are the symmetric and antisymmetric parts
    of the cell velocity gradient L_j D_j BC_j(u_i) of Algorithm 4 (boundary
-   and obstacle neighbours by their Section 2.5 ghosts).  Negative values mark
+   and obstacle neighbours by their Section 2.7 ghosts).  Negative values mark
    vortex cores; solid cells hold 0.  Computed from the case's current u, v, w
    in its compute precision; written to host_out as nx*ny*nz doubles, x
    fastest (caller-owned, n = its capacity in doubles).  Runs on the case's

@@ -8,7 +8,7 @@ it, and this package never imports the product.
 It restates the method of "NeuralFVM: Neural-physics-based Finite Volume
 Method for Turbulent Flows Using the k-omega Model" in plain numpy float64,
 following the paper's tensor notation: fields are arrays of shape
-(nx, ny, nz); BC_x pads one ghost layer along x (Section 2.5, Eqs. bc_x-bc);
+(nx, ny, nz); BC_x pads one ghost layer along x (Section 2.7, Eqs. bc_x-bc);
 L_x and D_x turn n cell values into n+1 face values once padded (Eq. Dx_Lx);
 upwind selection follows Eq. upwind_x / Algorithm 2; fluxes are summed with
 the divergence theorem (Eq. divergence_theorem).  Nothing is fused or
@@ -20,7 +20,7 @@ Modules
   destruction semi-implicit destruction half step (Eqs. k_des_step,
               o_des_step; Algorithm 4)
   transport   explicit stage for u, v, w, T, k, omega (Algorithms 2, 3 and
-              the "rest" terms of Section 2.4)
+              the "rest" terms of Section 2.5)
   poisson     pressure right-hand side (Eq. pc_residual), the operator A,
               Jacobi smoothing (Eq. jacobi_pc), RES / PROL (Eqs. restriction,
               prolongation), the V-cycle, direct solves, projection

@@ -1,4 +1,4 @@
-"""Semi-implicit destruction of k and omega (Section 2.4, Algorithm 4).
+"""Semi-implicit destruction of k and omega (Section 2.5, Algorithm 4).
 
 The destruction terms Y_k = beta* f_beta* k omega and Y_omega = beta f_beta
 omega^2 (Eqs. k_des, o_des) are advanced by the semi-implicit Euler step of

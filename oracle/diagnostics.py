@@ -9,7 +9,7 @@ Hussain, 1995); negative values mark vortex cores.  The paper does not say
 how the gradient is discretised for it.  The reading used here: the same cell
 gradient L_j * D_j * BC_j(u_i) that Algorithm 4 uses for the destruction
 terms, so boundary and obstacle cells take their ghost values from
-Section 2.5.  Solid cells get 0.
+Section 2.7.  Solid cells get 0.
 """
 import numpy as np
 

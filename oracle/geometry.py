@@ -1,10 +1,10 @@
-"""Grid levels, boundary patches and ghost cells (Section 2.5).
+"""Grid levels, boundary patches and ghost cells (Section 2.7).
 
 External boundaries: BC_x pads a field with one ghost layer on each side
 along x (Eq. bc_x); BC_y, BC_z likewise (Eqs. bc_y, bc_z).  Internal
 boundaries (solid boxes): where a face separates a fluid and a solid cell,
 the solid cell's value is replaced by the ghost value built from the
-neighbouring fluid cell, the mask-based treatment of Section 2.5.
+neighbouring fluid cell, the mask-based treatment of Section 2.7.
 
 Ghost values (one rule for external and internal walls):
 

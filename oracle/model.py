@@ -123,5 +123,5 @@ def inlet_turbulence(U, intensity, length_scale):
 
 
 def omega_wall(nu, d):
-    """Near-wall omega = 6 nu / (beta_i d^2), d = centroid-to-wall distance (Section 2.5)."""
+    """Near-wall omega = 6 nu / (beta_i d^2), d = centroid-to-wall distance (Section 2.7)."""
     return 6.0 * nu / (BETA_I * d * d)

@@ -25,7 +25,7 @@ from . import model
 from .destruction import destruction_step
 from .geometry import Geometry, INLET, U, V, W, T, K, OM
 from .poisson import Multigrid, poisson_rhs, project, face_divergence
-from .transport import explicit_stage
+from .transport import explicit_stage_rk
 
 _GAMMA = 0x9E3779B97F4A7C15
 _M1 = 0xBF58476D1CE4E5B9
@@ -126,7 +126,7 @@ class OracleCase:
         self.state = [u, v, w, T_, k, om]
 
     def explicit(self):
-        self.state = explicit_stage(self.geo, self.state, self.dt)
+        self.state = explicit_stage_rk(self.geo, self.state, self.dt, getattr(self.spec, "rk_stages", 1))
 
     def rhs(self):
         u, v, w = self.state[:3]

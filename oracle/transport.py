@@ -22,7 +22,17 @@ empty faces.
 
 After the forward-Euler update k and omega are clamped positive (Section
 A.4) and omega in every cell next to a wall is set to 6 nu / (beta_i d^2)
-with d = half the cell width normal to that wall (Section 2.5).
+with d = half the cell width normal to that wall (Section 2.7).
+
+Section 2.6 leaves the explicit Runge-Kutta scheme for these terms
+unnamed.  Forward Euler is the default; the
+strong-stability-preserving schemes of Shu and Osher (J. Comput. Phys. 77,
+1988) of order 2 and 3 are the alternatives: each stage is the forward-Euler
+update above (clamps and wall omega included) from the previous stage, and
+the stages are convex combinations with the state at the start:
+  RK2: u1 = E(u0);  u = 1/2 u0 + 1/2 E(u1)
+  RK3: u1 = E(u0);  u2 = 3/4 u0 + 1/4 E(u1);  u = 1/3 u0 + 2/3 E(u2)
+with omega set to its wall value again after each combination.
 """
 import numpy as np
 
@@ -113,3 +123,26 @@ def explicit_stage(geo, state, dt):
     ow = wall_omega(geo)
     om = np.where(ow > 0.0, ow, om)
     return [u, v, w, T_, k, om]
+
+
+def _combine(geo, a, x0, b, y):
+    """a x0 + b y in fluid cells (solid cells keep x0), wall omega set again."""
+    out = [np.where(geo.fluid, a * p + b * q, p) for p, q in zip(x0, y)]
+    ow = wall_omega(geo)
+    out[5] = np.where(ow > 0.0, ow, out[5])
+    return out
+
+
+def explicit_stage_rk(geo, state, dt, stages=1):
+    """The explicit terms over dt by forward Euler (stages = 1) or the
+    strong-stability-preserving Runge-Kutta scheme of order 2 or 3 (Shu and
+    Osher) built from forward-Euler stages."""
+    if stages == 1:
+        return explicit_stage(geo, state, dt)
+    u1 = explicit_stage(geo, state, dt)
+    if stages == 2:
+        return _combine(geo, 0.5, state, 0.5, explicit_stage(geo, u1, dt))
+    if stages == 3:
+        u2 = _combine(geo, 0.75, state, 0.25, explicit_stage(geo, u1, dt))
+        return _combine(geo, 1.0 / 3.0, state, 2.0 / 3.0, explicit_stage(geo, u2, dt))
+    raise ValueError("stages must be 1, 2 or 3")

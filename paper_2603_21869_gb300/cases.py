@@ -112,6 +112,7 @@ class CaseSpec:
     mg_variant: int = 0          # 0: V-cycles; 1: the paper's scheme (Algorithm 1)
     krylov: int = 0              # 1: flexible CG with one kept direction around the V-cycles
     coarse_sweeps: int = 0       # pre- and post-sweeps on the levels below the finest (0: as the finest)
+    rk_stages: int = 1           # explicit stage: 1 forward Euler, 2 / 3 strong-stability-preserving RK
     mg_rel_tol: float = 1e-8
     jacobi_weight: float = 0.0   # 0 -> 6/7 in 3D, 4/5 in 2D
     seed: int = 0

@@ -1,6 +1,6 @@
 // Internal declarations of the k-omega finite-volume library: device-side
 // case and level descriptions, the ghost-cell rules of the paper's
-// boundary treatment (Section 2.5) and the launchers shared between
+// boundary treatment (Section 2.7) and the launchers shared between
 // translation units.
 #pragma once
 

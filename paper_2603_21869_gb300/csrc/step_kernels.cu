@@ -1,12 +1,12 @@
 // Step kernels of the k-omega finite-volume time step: the seeded initial
 // state, the per-step time-step cap, the semi-implicit destruction half
-// step (Section 2.4, Eqs. k_des_step / o_des_step, Algorithm 4), the
+// step (Section 2.5, Eqs. k_des_step / o_des_step, Algorithm 4), the
 // explicit stage (Sections 2.3, A.2-A.4, Algorithms 2 and 3), the
 // pressure right-hand side (Eq. pc_residual) and the projection.
 //
 // One thread per cell, x fastest.  Neighbour states come from global
 // memory; boundary and obstacle neighbours are replaced by ghost values
-// (Section 2.5) computed in registers, so no ghost layer is stored.
+// (Section 2.7) computed in registers, so no ghost layer is stored.
 #include <cstdio>
 
 #include "fvm_internal.cuh"
@@ -75,7 +75,7 @@ __device__ __forceinline__ St<C> load_state(const StatePtrs& st, int64_t c) {
 }
 
 // State across the face on `side` (-1 / +1) of cell (i,j,k) along `axis`:
-// the neighbour's values, or the ghost values of Section 2.5 at a domain
+// the neighbour's values, or the ghost values of Section 2.7 at a domain
 // face or a solid neighbour.  Returns the face kind.
 template <class S, class C>
 __device__ __forceinline__ int neighbour(const CaseDev& cd, const StatePtrs& st, int i, int j, int k,
@@ -561,7 +561,7 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
 // Hussain 1995): lambda_2, the middle eigenvalue of the symmetric matrix
 // M = S^2 + Omega^2 of the cell velocity gradient.  The gradient is the cell
 // gradient L_j * D_j * BC_j(u_i) of Algorithm 4 (the destruction kernel's),
-// so wall, inlet, outlet and obstacle neighbours take their Section 2.5
+// so wall, inlet, outlet and obstacle neighbours take their Section 2.7
 // ghosts.  Solid cells get 0.  The result is written as FP64.
 //
 // Middle eigenvalue of a symmetric 3x3 matrix by cyclic Jacobi rotations

@@ -66,7 +66,7 @@ def test_low_reynolds_beta_star():
 
 
 def test_positivity_for_huge_time_step():
-    """The semi-implicit update keeps k, omega positive for any dt (Section 2.4)."""
+    """The semi-implicit update keeps k, omega positive for any dt (Section 2.5)."""
     spec = cases.heated_channel_3d(16, 8, 8, mg_levels=2, init_perturb=0.3)
     c = OracleCase(spec)
     u, v, w, T, k, om = c.state

@@ -231,3 +231,94 @@ def test_mass_balance_after_projection():
     div = c.divergence_after_projection()
     assert np.max(np.abs(div)) < 1e-9 * 2.0 / c.geo.h[0]
     assert c.last_rel <= 1e-11
+
+
+@pytest.mark.parametrize("stages", [1, 2, 3])
+@pytest.mark.parametrize("z", [0.1, 0.45])
+def test_runge_kutta_stability_polynomial_on_a_diffusion_eigenmode(stages, z):
+    """On an eigenmode of the discrete Laplacian the explicit operator is the
+    scalar -alpha lambda_m, so an s-stage scheme of order s multiplies the mode
+    by its stability polynomial R(-z) = sum_{j<=s} (-z)^j / j! per step,
+    z = dt alpha lambda_m (the strong-stability-preserving schemes of order
+    2 and 3 have exactly these polynomials).  m = 8 of 16 keeps the largest
+    eigenvalue of the 2D operator at 4 lambda_m, inside the stability
+    interval for both z (rounding does not seed a growing mode)."""
+    ny, m, nu = 16, 8, 0.01
+    faces = _faces(y=(cases.WALL, cases.WALL))
+    faces[2] = P_(cases.WALL, thermal=cases.ADIABATIC)
+    faces[3] = P_(cases.WALL, thermal=cases.ADIABATIC)
+    spec = cases.CaseSpec(nx=4, ny=ny, nz=1, Lx=0.25, Ly=1.0, Lz=1.0 / 16, nu=nu, Pr=0.7,
+                          faces=faces, dt_adapt=0, mg_levels=2, rk_stages=stages)
+    h = 1.0 / ny
+    alpha = nu / 0.7
+    lam = (2 - 2 * np.cos(m * np.pi / ny)) / h ** 2
+    spec = spec.replace(dt=z / (alpha * lam))
+    j = np.arange(ny) + 0.5
+    T0 = np.broadcast_to(np.cos(m * np.pi * j / ny)[None, :, None], (4, ny, 1))
+    c = OracleCase(spec, state=_state(spec, T=T0))
+    R = sum((-z) ** q / np.prod(range(1, q + 1)) for q in range(stages + 1))
+    c.step(6)
+    assert np.allclose(c.state[3], T0 * R ** 6, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("stages", [2, 3])
+def test_strong_stability_keeps_an_advected_step_within_bounds(stages):
+    """At CFL 1 each forward-Euler upwind stage is a shift, so the convex
+    combinations of the strong-stability-preserving schemes keep a step
+    profile inside [0, 1] (a classical midpoint RK2 would not)."""
+    n = 32
+    faces = _faces()
+    faces[0] = P_(cases.INLET, u_normal=1.0, T_in=1.0, k_value=1e-14, omega_value=1.0)
+    spec = cases.CaseSpec(nx=n, ny=4, nz=1, Lx=1.0, Ly=0.125, Lz=1.0 / 32, nu=1e-30, faces=faces,
+                          dt=1.0 / 32, dt_adapt=0, mg_levels=2, rk_stages=stages)
+    T0 = np.zeros((n, 4, 1))
+    T0[:6] = 1.0
+    c = OracleCase(spec, state=_state(spec, u=1.0, T=T0, om=1.0))
+    for _ in range(12):
+        c.step()
+        T = c.state[3]
+        assert T.min() >= -1e-14 and T.max() <= 1.0 + 1e-14
+    assert 0.0 < T[10, 0, 0] < 1.0          # a smeared front (not the exact shift of forward Euler)
+
+
+def test_runge_kutta_temporal_order_on_smooth_nonlinear_transport():
+    """Nonlinear advection and diffusion of a smooth velocity and temperature
+    field (turbulence negligible: k at its floor) over a fixed time: the error
+    against a fine-step reference falls by 2^s when dt halves, s = the
+    scheme's order (1, 2, 3)."""
+    n, h = (16, 8, 8), 0.01
+    faces = [P_(cases.OUTLET) for _ in range(6)]
+    spec = cases.CaseSpec(nx=n[0], ny=n[1], nz=n[2], Lx=n[0] * h, Ly=n[1] * h, Lz=n[2] * h, nu=1e-4, Pr=0.7,
+                          faces=faces, dt=0.002, dt_adapt=0, mg_levels=2)
+    geo = Geometry(spec)
+    X, Y, Z = np.meshgrid(*[(np.arange(m) + 0.5) * h for m in n], indexing="ij")
+    Lx, Ly, Lz = (m * h for m in n)
+    s0 = [1.0 + 0.3 * np.sin(2 * np.pi * Y / Ly) * np.cos(2 * np.pi * Z / Lz),
+          0.2 * np.sin(2 * np.pi * X / Lx),
+          0.1 * np.cos(2 * np.pi * X / Lx) * np.sin(2 * np.pi * Y / Ly),
+          20.0 + np.cos(2 * np.pi * X / Lx) * np.cos(2 * np.pi * Y / Ly),
+          np.full(X.shape, 1e-14), np.ones(X.shape)]
+    t_end = 0.008
+
+    def run(stages, nsteps):
+        st = [x.copy() for x in s0]
+        for _ in range(nsteps):
+            st = transport.explicit_stage_rk(geo, st, t_end / nsteps, stages)
+        return st[:4]
+
+    ref = run(3, 1024)
+    for stages in (1, 2, 3):
+        errs = [max(float(np.max(np.abs(a - b))) for a, b in zip(run(stages, m), ref)) for m in (4, 8, 16)]
+        for r in (errs[0] / errs[1], errs[1] / errs[2]):
+            assert 0.75 * 2 ** stages < r < 1.25 * 2 ** stages, (stages, errs)
+
+
+def test_one_stage_is_forward_euler_and_bad_stage_count_rejected():
+    spec = cases.heated_channel_3d(16, 8, 8, mg_levels=2, init_perturb=0.2)
+    geo = Geometry(spec)
+    s0 = OracleCase(spec).state
+    a = transport.explicit_stage(geo, s0, 1e-3)
+    b = transport.explicit_stage_rk(geo, s0, 1e-3, 1)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    with pytest.raises(ValueError):
+        transport.explicit_stage_rk(geo, s0, 1e-3, 4)
