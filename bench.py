@@ -509,6 +509,9 @@ def main():
                          "the profiler's overhead would distort the autotuner's timings)")
     ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
                     help="flexible-CG acceleration of the pressure solve (auto: the autotuner's choice, else off)")
+    ap.add_argument("--rk-stages", type=int, default=1, choices=[1, 2, 3],
+                    help="explicit stage: forward Euler (1) or the strong-stability-preserving Runge-Kutta "
+                         "scheme of order 2 or 3")
     ap.add_argument("--requests", type=int, default=64, help="served workload: requests per GPU")
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
@@ -539,6 +542,9 @@ def main():
             dist.destroy_process_group()
         return
     spec, label = workload(args.workload, PREC[args.precision])
+    if args.rk_stages > 1:
+        spec = spec.replace(rk_stages=args.rk_stages)
+        label += f", SSP-RK{args.rk_stages} explicit stage"
     rank, ws, local, dist = dist_setup()
     tuning = None
     if args.params:

@@ -125,6 +125,13 @@ typedef struct {
                                         Not with mg_variant 1.  An addition beyond the paper. */
     int32_t coarse_sweeps;           /* pre- and post-sweeps on every level below the finest;
                                         0: the finest level's counts.  Not with mg_variant 1. */
+    int32_t rk_stages;               /* explicit stage (Section 2.6 leaves the Runge-Kutta scheme
+                                        open): 0 or 1 forward Euler; 2 or 3 the strong-stability-
+                                        preserving schemes of Shu and Osher of that order, each stage
+                                        a forward-Euler update (clamps and wall omega included)
+                                        combined with the stage-0 state.  3 keeps a third copy of
+                                        the six state fields. */
+    int32_t reserved2;               /* 0 */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */

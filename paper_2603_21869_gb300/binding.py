@@ -61,7 +61,7 @@ class CaseDesc(ct.Structure):
                 ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
                 ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("inner_cycles", ct.c_int32),
                 ("sweep_planes", ct.c_int32), ("mg_variant", ct.c_int32), ("krylov", ct.c_int32),
-                ("coarse_sweeps", ct.c_int32),
+                ("coarse_sweeps", ct.c_int32), ("rk_stages", ct.c_int32), ("reserved2", ct.c_int32),
                 ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
                 ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
                 ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
@@ -230,6 +230,7 @@ class _Desc:
         d.mg_variant = spec.mg_variant
         d.krylov = spec.krylov
         d.coarse_sweeps = spec.coarse_sweeps
+        d.rk_stages = spec.rk_stages
         d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
         d.seed = spec.seed & ((1 << 64) - 1)
         d.init_perturb = spec.init_perturb

@@ -282,7 +282,8 @@ cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_stat
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
                                const double* dt_state, void* nut_out, cudaStream_t s);
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out,
-                            const double* dt_state, const void* nut, cudaStream_t s);
+                            const double* dt_state, const void* nut, StatePtrs base, double wb, double ws,
+                            cudaStream_t s);
 cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const double* dt_state,
                        cudaStream_t s);
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,

@@ -307,6 +307,7 @@ struct fvm_case {
     bool own_stream = false;
     void* cur[6] = {};
     void* nxt[6] = {};
+    void* rk3[6] = {};               // rk_stages = 3: the second stage's state
     double* p = nullptr;
     void* b = nullptr;
     double* dt_state = nullptr;
@@ -404,6 +405,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->krylov == 1 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "krylov 1 needs mg_variant 0");
     if (d->coarse_sweeps < 0 || d->coarse_sweeps > 64) return fail(FVM_ERR_INVALID, "coarse_sweeps must be 0..64");
     if (d->coarse_sweeps > 0 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "coarse_sweeps needs mg_variant 0");
+    if (d->rk_stages < 0 || d->rk_stages > 3) return fail(FVM_ERR_INVALID, "rk_stages must be 0..3");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -535,6 +537,7 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     bytes += N * 8 + N * s + N;               // p (FP64), b, tag
     bytes += N * 8;                           // staging
     bytes += N * s;                           // nu_t after a destruction half step
+    if (d->rk_stages == 3) bytes += (int64_t)6 * N * s;   // the third-order scheme's stage state
     for (int f = 0; f < 6; ++f) bytes += face_cells(n, f);
     for (size_t l = 0; l < pl.levels.size(); ++l) {
         const int64_t NL = pl.levels[l].N();
@@ -889,13 +892,34 @@ fvm_status stage(fvm_case* c, int st, int* cycles, double* rel) {
             std::swap(c->cur[5], c->nxt[5]);
             c->nut_valid = true;
             return FVM_OK;
-        case FVM_STAGE_EXPLICIT:
+        case FVM_STAGE_EXPLICIT: {
+            // forward Euler, or the first stage of the Shu-Osher schemes: cur -> nxt
             KLAUNCH("explicit", N * (13 * sz + 1), 1,
                     launch_explicit(c->prec, c->cd, ptrs(c->cur), ptrs(c->nxt), c->dt_state,
-                                    c->nut_valid ? c->nut : nullptr, s));
-            for (int f = 0; f < 6; ++f) std::swap(c->cur[f], c->nxt[f]);
+                                    c->nut_valid ? c->nut : nullptr, StatePtrs{}, 0.0, 0.0, s));
             c->nut_valid = false;
+            const int rk = c->desc.rk_stages;
+            if (rk <= 1) {
+                for (int f = 0; f < 6; ++f) std::swap(c->cur[f], c->nxt[f]);
+                return FVM_OK;
+            }
+            // later stages: a u0 + b E(u_stage), u0 = cur; the last one overwrites cur in place
+            // (each cell reads its own u0 value before writing it; the stencil reads u_stage)
+            const double rk_bytes = N * (19 * sz + 1);
+            if (rk == 2) {
+                KLAUNCH("explicit_rk", rk_bytes, 1,
+                        launch_explicit(c->prec, c->cd, ptrs(c->nxt), ptrs(c->cur), c->dt_state, nullptr,
+                                        ptrs(c->cur), 0.5, 0.5, s));
+            } else {
+                KLAUNCH("explicit_rk", rk_bytes, 1,
+                        launch_explicit(c->prec, c->cd, ptrs(c->nxt), ptrs(c->rk3), c->dt_state, nullptr,
+                                        ptrs(c->cur), 0.75, 0.25, s));
+                KLAUNCH("explicit_rk", rk_bytes, 1,
+                        launch_explicit(c->prec, c->cd, ptrs(c->rk3), ptrs(c->cur), c->dt_state, nullptr,
+                                        ptrs(c->cur), 1.0 / 3.0, 2.0 / 3.0, s));
+            }
             return FVM_OK;
+        }
         case FVM_STAGE_RHS:
             KLAUNCH("rhs", N * (4 * sz + 1), 1, launch_rhs(c->prec, c->cd, ptrs(c->cur), c->b, c->dt_state, s));
             return FVM_OK;
@@ -1150,6 +1174,7 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     for (int f = 0; f < 6; ++f) {
         ST_TRY(dalloc(c, &c->cur[f], N * s));
         ST_TRY(dalloc(c, &c->nxt[f], N * s));
+        if (c->desc.rk_stages == 3) ST_TRY(dalloc(c, &c->rk3[f], N * s));
     }
     ST_TRY(dalloc(c, (void**)&c->p, N * 8));
     ST_TRY(dalloc(c, &c->b, N * s));
@@ -1944,11 +1969,13 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     CUDA_TRY(cudaMemcpyAsync(c->h_dt, c->dt_state, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     stats.vcycles_total = c->h_sst->total_cycles;
-    // kernels run by the graphs: 8 step kernels per step, one residual per outer iteration plus the
-    // last one of each step, and kpc kernels per outer iteration (inner V-cycles of the if node)
+    // kernels run by the graphs: 8 step kernels per step (one more per later Runge-Kutta stage),
+    // one residual per outer iteration plus the last one of each step, and kpc kernels per outer
+    // iteration (inner V-cycles of the if node)
     if (graph_steps) {
         const int64_t outer = (int64_t)stats.vcycles_total / std::max(1, c->rule_inner);
-        c->launches += 8 * (int64_t)graph_steps + (int64_t)graph_steps + outer * (1 + c->kpc);
+        const int64_t step_kernels = 8 + (c->desc.rk_stages > 1 ? c->desc.rk_stages - 1 : 0);
+        c->launches += step_kernels * (int64_t)graph_steps + (int64_t)graph_steps + outer * (1 + c->kpc);
     }
     stats.vcycles_last = c->h_sst->cycles;
     stats.rel_residual = c->h_sst->rel;

@@ -354,7 +354,7 @@ __device__ __forceinline__ C face_nut(int kind, C nutP, N nut_nb) {
     return nutP;
 }
 
-template <class S, class C>
+template <class S, class C, bool kBlend>
 struct ExplicitK {
     static constexpr int kThreads = BX * BY * BZ;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
@@ -364,11 +364,18 @@ struct ExplicitK {
     StatePtrs in, out;
     const double* dt_state;
     const S* nut;   // nu_t of the input state (written by the destruction half step), or null: computed here
+    // kBlend: a later stage of the Shu-Osher Runge-Kutta schemes, out = wb base + ws E(in), where E
+    // is the forward-Euler update (clamps included) and base the stage-0 state (may alias out: each
+    // thread reads its own base cell before writing it); wall omega is set after the combination.
+    // Otherwise plain forward Euler (base and the weights unused).
+    StatePtrs base;
+    double wb, ws;
+    float wbf, wsf;
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class S, class C>
-__device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
+template <class S, class C, bool kBlend>
+__device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
     int i, j, k;
     if (!cell3(cd, at, i, j, k)) return;
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
@@ -439,6 +446,15 @@ __device__ void ExplicitK<S, C>::run(const BlockAt& at) const {
     C on = P.om + dt * rhs[5];
     kn = kn > (C)kKMin ? kn : (C)kKMin;
     on = on > (C)kOmegaMin ? on : (C)kOmegaMin;
+    if constexpr (kBlend) {
+        const C a = prm<C>(wb, wbf), b = prm<C>(ws, wsf);
+        un = a * to_c<C>(((const S*)base.f[0])[c]) + b * un;
+        vn = a * to_c<C>(((const S*)base.f[1])[c]) + b * vn;
+        wn = a * to_c<C>(((const S*)base.f[2])[c]) + b * wn;
+        Tn = a * to_c<C>(((const S*)base.f[3])[c]) + b * Tn;
+        kn = a * to_c<C>(((const S*)base.f[4])[c]) + b * kn;
+        on = a * to_c<C>(((const S*)base.f[5])[c]) + b * on;
+    }
     if (omw > (C)0) on = omw;
     o[0][c] = from_c<S, C>(un); o[1][c] = from_c<S, C>(vn); o[2][c] = from_c<S, C>(wn);
     o[3][c] = from_c<S, C>(Tn); o[4][c] = from_c<S, C>(kn); o[5][c] = from_c<S, C>(on);
@@ -717,9 +733,16 @@ cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* 
 }
 
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out, const double* dt_state,
-                            const void* nut, cudaStream_t s) {
+                            const void* nut, StatePtrs base, double wb, double ws, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    DISPATCH(prec, err = launch_k(ExplicitK<S, C>{cd, in, out, dt_state, (const S*)nut}, grid3(cd), kBlock3, 0, s));
+    if (base.f[0])
+        DISPATCH(prec, err = launch_k(ExplicitK<S, C, true>{cd, in, out, dt_state, (const S*)nut, base, wb, ws,
+                                                            (float)wb, (float)ws},
+                                      grid3(cd), kBlock3, 0, s));
+    else
+        DISPATCH(prec, err = launch_k(ExplicitK<S, C, false>{cd, in, out, dt_state, (const S*)nut, base, wb, ws,
+                                                             (float)wb, (float)ws},
+                                      grid3(cd), kBlock3, 0, s));
     return err;
 }
 

@@ -111,3 +111,13 @@ def test_invalid_descriptors_are_rejected_without_a_gpu(lib, bad):
         binding.Case(spec)
     assert ei.value.status == binding.ERR_INVALID
     assert binding.last_error()
+
+
+def test_rk_stages_validation_and_bytes_without_a_gpu(lib):
+    """rk_stages 3 holds one more copy of the six state fields; 4 is refused."""
+    spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3, precision=cases.FP32)
+    b1 = binding.case_bytes(spec)
+    assert binding.case_bytes(spec.replace(rk_stages=2)) == b1
+    assert binding.case_bytes(spec.replace(rk_stages=3)) - b1 == 6 * spec.cells * 4
+    assert binding.case_bytes(spec.replace(rk_stages=4)) == 0
+    assert "rk_stages" in binding.last_error()
