@@ -7,15 +7,18 @@
  *
  *   1. dt/2 of the semi-implicit destruction of k and omega
  *      (Section 2.5, Eqs. k_des_step and o_des_step, Algorithm 4);
- *   2. one forward-Euler step of convection (first-order upwind, Eq.
- *      upwind_x, Algorithm 2), diffusion (Eq. divergence_theorem) and
- *      production (Eqs. k_gen, o_gen) for u, v, w, T, k, omega
- *      (Eqs. ko_mom - ko_temp, Algorithm 3 and Section A.4);
+ *   2. one forward-Euler step (or a strong-stability-preserving Runge-Kutta
+ *      step of order 2 or 3, desc.rk_stages) of convection (first-order
+ *      upwind, Eq. upwind_x, Algorithm 2), diffusion (Eq.
+ *      divergence_theorem) and production (Eqs. k_gen, o_gen) for u, v, w,
+ *      T, k, omega (Eqs. ko_mom - ko_temp, Algorithm 3 and Section A.4);
  *   3. dt/2 of the destruction again (Strang splitting, Section 2.6);
  *   4. the pressure right-hand side b = -div(u*)/dt (Eq. pc_residual);
  *   5. multigrid V-cycles on A p = b, A = -Laplacian (Eq. neg_lap_discretize,
  *      Eq. jacobi_pc, Eqs. restriction / prolongation, Algorithm 1);
  *   6. the projection u = u* - dt grad p (Section 2.4).
+ * fvm_lambda2 evaluates the lambda_2 vortex criterion of Section 3.2.3 on
+ * the current velocity.
  * Boundary conditions use one ghost layer (Section 2.7, Eqs. bc_x - bc) and
  * masks for solid boxes; walls use omega = 6 nu / (beta_i d^2) in the
  * adjacent cells (Section 2.7); inlet k and omega follow Section 3.2.4.
