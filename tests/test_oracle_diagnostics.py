@@ -122,3 +122,26 @@ def test_solid_cells_zero_and_fluid_finite():
     flipped = lambda2(geo, *[-x for x in u])
     assert np.allclose(flipped[1:], lam[1:], rtol=0, atol=1e-12 * np.max(np.abs(lam)))
     assert not np.allclose(flipped[0], lam[0])
+
+
+def test_taylor_green_vortex_converges_at_second_order():
+    """For a planar divergence-free flow S^2 + Omega^2 = -det(G) on the plane
+    (Cayley-Hamilton for a traceless 2x2 G) and 0 across it, so lambda_2 =
+    u_y v_x - u_x v_y.  The Taylor-Green vortex u = sin x cos y, v = -cos x sin y
+    gives cos^2 x cos^2 y - sin^2 x sin^2 y; the central cell gradient makes the
+    discrete value converge to it at second order."""
+    errs = []
+    for n in (16, 32, 64):
+        faces = [cases.Patch(cases.OUTLET) for _ in range(6)]
+        L = 2 * np.pi
+        spec = cases.CaseSpec(nx=n, ny=n, nz=1, Lx=L, Ly=L, Lz=L / n, nu=1e-5, faces=faces, dt=0.01,
+                              dt_adapt=0, mg_levels=2)
+        geo = Geometry(spec)
+        x = (np.arange(n) + 0.5) * L / n
+        X, Y = np.meshgrid(x, x, indexing="ij")
+        u = (np.sin(X) * np.cos(Y))[:, :, None]
+        v = (-np.cos(X) * np.sin(Y))[:, :, None]
+        lam = lambda2(geo, u, v, np.zeros_like(u))[:, :, 0]
+        exact = np.cos(X) ** 2 * np.cos(Y) ** 2 - np.sin(X) ** 2 * np.sin(Y) ** 2
+        errs.append(float(np.max(np.abs(lam - exact)[1:-1, 1:-1])))
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4, errs
