@@ -235,6 +235,31 @@ fvm_status fvm_read_poisson_rhs(fvm_case* c, double* host_b, size_t n);
    FVM_ERR_INVALID for a null case or buffer or n < nx*ny*nz. */
 fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n);
 
+/* Vector-Jacobian product of the projection, the first piece of a
+   differentiable step (an addition: Section 1 presents the method as
+   differentiable but defines no discrete gradient).  The map is
+   u* -> (u^{n+1}, p) of steps 4-6 above with an exact pressure solve:
+   b = -div(u*)/dt (Eq. pc_residual), A p = b, u^{n+1} = u* - dt G p.  It is
+   affine in u* (the inlets add constants), and this call returns
+   xbar = J^T ybar for its Jacobian J:
+       q = pbar + (d u^{n+1} / d p)^T (ubar, vbar, wbar),
+       A lambda = q (A is symmetric on the fluid cells),
+       xbar = (ubar, vbar, wbar) + (d b / d u*)^T lambda.
+   The solve runs V-cycles of the case's own multigrid from zero until
+   ||q - A lambda|| / ||q|| <= rel_tol or max_vcycles cycles (in chunks of
+   four); the case's p and b are saved and restored, its fields are not
+   touched.  dt: the time step of the projection being differentiated.
+   host_ybar: 4 nx*ny*nz doubles (ubar, vbar, wbar, pbar; field-major, x
+   fastest); host_xbar: 3 nx*ny*nz doubles out; n = the number of doubles
+   host_ybar holds (>= 4 nx*ny*nz); host_xbar must hold 3 nx*ny*nz.
+   *rel_out (may be NULL) gets the final relative residual.  FP64 cases
+   only.  FVM_ERR_NOT_CONVERGED if rel_tol was not reached (xbar is still
+   written); FVM_ERR_INVALID for null pointers, dt <= 0, rel_tol <= 0,
+   max_vcycles < 1, a short buffer or a reduced-precision case.
+   Synchronises. */
+fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
+                              double rel_tol, int32_t max_vcycles, double* rel_out);
+
 /* ---------------------------------------------------------------- batches
    Cases stepped together (uneven sizes allowed).  Every launch site of the
    step (each step kernel, and each multigrid kernel of each level) runs

@@ -109,13 +109,13 @@ class BatchInfo(ct.Structure):
 
 
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
-           "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs",
-           "fvm_lambda2", "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
-           "fvm_profile_read", "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static", "fvm_batch_create",
-           "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info", "fvm_batch_destroy",
-           "fvm_batch_profile", "fvm_server_create",
-           "fvm_server_now", "fvm_server_submit", "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields",
-           "fvm_server_release", "fvm_server_destroy", "fvm_autotune"]
+           "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
+           "fvm_projection_vjp", "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
+           "fvm_profile_read", "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static",
+           "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
+           "fvm_batch_destroy", "fvm_batch_profile", "fvm_server_create", "fvm_server_now", "fvm_server_submit",
+           "fvm_server_poll", "fvm_server_get_info", "fvm_server_read_fields", "fvm_server_release",
+           "fvm_server_destroy", "fvm_autotune"]
 
 _lib = None
 
@@ -142,6 +142,8 @@ def lib():
     L.fvm_set_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_read_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_lambda2.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_projection_vjp.argtypes = [CP, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_size_t,
+                                     ct.c_double, ct.c_int32, ct.POINTER(ct.c_double)]
     L.fvm_step_batch.argtypes = [ct.POINTER(CP), ct.c_int, ct.c_int, ct.POINTER(StepStats)]
     L.fvm_case_get_info.argtypes = [CP, ct.POINTER(CaseInfo)]
     L.fvm_set_option.argtypes = [CP, ct.c_int, ct.c_int64]
@@ -174,7 +176,8 @@ def lib():
     L.fvm_struct_sizes.restype = None
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
-                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2", "fvm_step_batch",
+                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
+                 "fvm_projection_vjp", "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
                  "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
                  "fvm_batch_profile",
@@ -355,6 +358,25 @@ class Case:
         _check(lib().fvm_lambda2(self._h, buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
         nx, ny, nz = self.shape
         return buf.reshape(nz, ny, nx).transpose(2, 1, 0)
+
+    def projection_vjp(self, dt, ubar, vbar, wbar, pbar=None, rel_tol=1e-13, max_vcycles=400,
+                       allow_not_converged=False):
+        """J^T (ubar, vbar, wbar, pbar) for the projection u* -> (u^{n+1}, p)
+        (fvm_projection_vjp); arrays of shape (nx, ny, nz).  Returns
+        ((xbar_u, xbar_v, xbar_w), final relative residual of the solve)."""
+        nx, ny, nz = self.shape
+        z = np.zeros((nx, ny, nz))
+        parts = [ubar, vbar, wbar, z if pbar is None else pbar]
+        buf = np.ascontiguousarray(np.concatenate(
+            [np.asarray(a, dtype=np.float64).transpose(2, 1, 0).ravel() for a in parts]))
+        out = np.empty(3 * self.N, dtype=np.float64)
+        rel = ct.c_double()
+        status = lib().fvm_projection_vjp(self._h, dt, buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                          out.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size, rel_tol,
+                                          max_vcycles, ct.byref(rel))
+        _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        xs = tuple(out[i * self.N:(i + 1) * self.N].reshape(nz, ny, nx).transpose(2, 1, 0) for i in range(3))
+        return xs, rel.value
 
     def set_graph(self, enable=True):
         _check(lib().fvm_set_option(self._h, OPT_GRAPH, 1 if enable else 0))

@@ -289,6 +289,10 @@ cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
                            const double* p, const double* dt_state, cudaStream_t s);
 cudaError_t launch_lambda2(int prec, const CaseDev& cd, StatePtrs in, double* out, cudaStream_t s);
+cudaError_t launch_adj_grad(const CaseDev& cd, const LevelDev& L0, const double* ybar, double* q, double dt,
+                            cudaStream_t s);
+cudaError_t launch_adj_rhs(const CaseDev& cd, const LevelDev& L0, const double* ybar, const double* lambda,
+                           double* xbar, double dt, cudaStream_t s);
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 

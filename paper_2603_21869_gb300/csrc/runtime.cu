@@ -2097,6 +2097,65 @@ fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n) {
     return FVM_OK;
 }
 
+fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
+                              double rel_tol, int32_t max_vcycles, double* rel_out) {
+    if (!c || !host_ybar || !host_xbar) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (c->prec != FVM_FP64 || c->inner != FVM_FP64) return fail(FVM_ERR_INVALID, "FP64 cases only");
+    if (!(dt > 0.0)) return fail(FVM_ERR_INVALID, "dt must be > 0");
+    if (!(rel_tol > 0.0) || max_vcycles < 1) return fail(FVM_ERR_INVALID, "need rel_tol > 0 and max_vcycles >= 1");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)(4 * N)) return fail(FVM_ERR_INVALID, "buffers too small (4 N in, 3 N out)");
+    cudaStream_t s = c->stream;
+    // scratch: ybar (4 N), xbar (3 N), the case's p and b (2 N); freed before returning
+    double* d = nullptr;
+    CUDA_TRY(cudaMalloc((void**)&d, (size_t)9 * N * 8));
+    double* ybar = d;
+    double* xbar = d + 4 * N;
+    double* p_save = d + 7 * N;
+    double* b_save = d + 8 * N;
+    double* b = (double*)c->b;
+    fvm_status st = FVM_OK;
+    double rel = 0.0;
+    bool saved = false;
+    auto run = [&]() -> fvm_status {
+        CUDA_TRY(cudaMemcpyAsync(p_save, c->p, N * 8, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(b_save, b, N * 8, cudaMemcpyDeviceToDevice, s));
+        saved = true;
+        CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)4 * N * 8, cudaMemcpyHostToDevice, s));
+        KLAUNCH("adj_grad", (double)N * (5 * 8 + 2 + 1), 1, launch_adj_grad(c->cd, c->levels[0].dev, ybar, b, dt, s));
+        // A is symmetric on the fluid cells: A^T lambda = q by the case's own solver, from zero
+        CUDA_TRY(cudaMemsetAsync(c->p, 0, N * 8, s));
+        int done = 0;
+        const int chunk = 4;
+        for (;;) {
+            ST_TRY(fvm_vcycle(c, chunk, &rel));
+            done += chunk;
+            if (!std::isfinite(rel)) return fail(FVM_ERR_DIVERGED, "non-finite residual in the adjoint solve");
+            if (rel <= rel_tol || done >= max_vcycles) break;
+        }
+        KLAUNCH("adj_rhs", (double)N * (3 * 8 + 8 + 3 * 8 + 2 + 1), 1,
+                launch_adj_rhs(c->cd, c->levels[0].dev, ybar, c->p, xbar, dt, s));
+        CUDA_TRY(cudaMemcpyAsync(host_xbar, xbar, (size_t)3 * N * 8, cudaMemcpyDeviceToHost, s));
+        return rel <= rel_tol ? FVM_OK : FVM_ERR_NOT_CONVERGED;
+    };
+    st = run();
+    if (saved) {   // the case's p and b back, whatever happened after they were saved
+        const std::string msg = g_err;
+        cudaError_t e1 = cudaMemcpyAsync(c->p, p_save, N * 8, cudaMemcpyDeviceToDevice, s);
+        cudaError_t e2 = cudaMemcpyAsync(b, b_save, N * 8, cudaMemcpyDeviceToDevice, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        g_err = msg;
+        const bool restored = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
+        if (!restored && (st == FVM_OK || st == FVM_ERR_NOT_CONVERGED))
+            st = fail(FVM_ERR_CUDA, "restoring p and b after the adjoint solve");
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (st == FVM_ERR_NOT_CONVERGED) fail(st, "adjoint solve stopped at max_vcycles above rel_tol");
+    if (rel_out) *rel_out = rel;
+    return st;
+}
+
 fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out) {
     if (!out) return fail(FVM_ERR_INVALID, "null output");
     ST_TRY(batch_check(cases, n));

@@ -572,6 +572,102 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
     }
 }
 
+// ------------------------------------------------------------------ projection adjoint
+// Transposes of the two local maps of the projection, for the vector-Jacobian
+// product of u* -> (u^{n+1}, p) (FP64 cases).  With the pressure face codes of
+// level 0 (0 fluid neighbour, 1 zero-gradient ghost, 2 zero-value ghost at an
+// outlet):
+//   projection  out_a(c) = -dt/(2h) (p_{c+} - p_{c-}) on fluid cells, a ghost
+//               p_{c+-} = s p_c with s = +1 (code 1) or -1 (code 2);
+//   rhs         b(c) = -1/(dt h) sum_a (uf_a(c+1/2) - uf_a(c-1/2)), uf the mean of
+//               the two cells across a fluid face, the cell's own value across an
+//               outlet face (mirror ghost), 0 across walls, inlets and obstacles
+//               (odd ghosts; the inlet's constant drops out of the Jacobian).
+// AdjGradK forms q = pbar + (d out / d p)^T ybar; AdjRhsK forms
+// xbar = ybar + (d b / d u*)^T lambda.  Solid cells: q = 0 (their p is fixed at
+// 0), xbar = ybar (the projection copies their velocities).
+__device__ __forceinline__ uint32_t face_code(uint32_t f, int a, int side) {
+    return (f >> (2 * (2 * a + (side > 0 ? 1 : 0)))) & 3u;
+}
+
+struct AdjGradK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    LevelDev L0;
+    const double* ybar;   // ubar, vbar, wbar, pbar (4 N)
+    double* q;
+    double dt;
+    __device__ void run(const BlockAt& at) const;
+};
+
+__device__ void AdjGradK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    if (cd.tag[c]) {
+        q[c] = 0.0;
+        return;
+    }
+    const int64_t N = cd.N;
+    const uint32_t f = L0.nbf[c];
+    double acc = ybar[3 * N + c];
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) continue;
+        const double* ya = ybar + a * N;
+        const int stride = a == 0 ? 1 : (a == 1 ? cd.n[0] : cd.n[0] * cd.n[1]);
+        const double coef = dt * 0.5 * cd.inv_h[a];
+        const uint32_t cm = face_code(f, a, -1), cp = face_code(f, a, +1);
+        const double sm = cm == 1u ? 1.0 : (cm == 2u ? -1.0 : 0.0);
+        const double sp = cp == 1u ? 1.0 : (cp == 2u ? -1.0 : 0.0);
+        acc += coef * (sm - sp) * ya[c];
+        if (cm == 0u) acc -= coef * ya[c - stride];
+        if (cp == 0u) acc += coef * ya[c + stride];
+    }
+    q[c] = acc;
+}
+
+struct AdjRhsK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    LevelDev L0;
+    const double* ybar;     // ubar, vbar, wbar (first 3 N used)
+    const double* lambda;   // A^{-T} q
+    double* xbar;           // 3 N
+    double dt;
+    __device__ void run(const BlockAt& at) const;
+};
+
+__device__ void AdjRhsK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    const int64_t N = cd.N;
+    if (cd.tag[c]) {
+        for (int a = 0; a < 3; ++a) xbar[a * N + c] = ybar[a * N + c];
+        return;
+    }
+    const uint32_t f = L0.nbf[c];
+    const double lc = lambda[c];
+    for (int a = 0; a < 3; ++a) {
+        double x = ybar[a * N + c];
+        if (cd.active[a]) {
+            const int stride = a == 0 ? 1 : (a == 1 ? cd.n[0] : cd.n[0] * cd.n[1]);
+            const uint32_t cm = face_code(f, a, -1), cp = face_code(f, a, +1);
+            double t = 0.0;
+            if (cp == 0u) t += 0.5 * (lc - lambda[c + stride]);
+            if (cp == 2u) t += lc;
+            if (cm == 0u) t -= 0.5 * (lc - lambda[c - stride]);
+            if (cm == 2u) t -= lc;
+            x -= t * cd.inv_h[a] / dt;
+        }
+        xbar[a * N + c] = x;
+    }
+}
+
 // ------------------------------------------------------------------ lambda_2 diagnostic
 // The vortex criterion of the transient results (Section 3.2.3; Jeong and
 // Hussain 1995): lambda_2, the middle eigenvalue of the symmetric matrix
@@ -758,6 +854,16 @@ cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, Stat
     cudaError_t err = cudaSuccess;
     DISPATCH(prec, err = launch_k(ProjectK<S, C>{cd, L0, in, out, p, dt_state}, grid3(cd), kBlock3, 0, s));
     return err;
+}
+
+cudaError_t launch_adj_grad(const CaseDev& cd, const LevelDev& L0, const double* ybar, double* q, double dt,
+                            cudaStream_t s) {
+    return launch_k(AdjGradK{cd, L0, ybar, q, dt}, grid3(cd), kBlock3, 0, s);
+}
+
+cudaError_t launch_adj_rhs(const CaseDev& cd, const LevelDev& L0, const double* ybar, const double* lambda,
+                           double* xbar, double dt, cudaStream_t s) {
+    return launch_k(AdjRhsK{cd, L0, ybar, lambda, xbar, dt}, grid3(cd), kBlock3, 0, s);
 }
 
 cudaError_t launch_lambda2(int prec, const CaseDev& cd, StatePtrs in, double* out, cudaStream_t s) {

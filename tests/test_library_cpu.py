@@ -121,3 +121,10 @@ def test_rk_stages_validation_and_bytes_without_a_gpu(lib):
     assert binding.case_bytes(spec.replace(rk_stages=3)) - b1 == 6 * spec.cells * 4
     assert binding.case_bytes(spec.replace(rk_stages=4)) == 0
     assert "rk_stages" in binding.last_error()
+
+
+def test_projection_vjp_rejects_bad_arguments_without_a_gpu(lib):
+    import ctypes as ct
+    buf = (ct.c_double * 8)()
+    assert lib.fvm_projection_vjp(None, 0.01, buf, buf, 8, 1e-12, 10, None) == binding.ERR_INVALID
+    assert "null case" in binding.last_error()
