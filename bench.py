@@ -55,6 +55,44 @@ TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"):
 TRAFFIC_PER_CELL = {("batched", "f32", "sweep_L0"): 458.10e6 / 29294592}
 
 
+def time_projection_vjp(spec, stream, flush, peak, calls=3):
+    """The projection adjoint (fvm_projection_vjp) on an FP64 copy of the case after one
+    step: wall time per call (its V-cycles included) and, by the profiling hook, the two
+    transposed stencil kernels."""
+    import numpy as np
+    import torch
+    from paper_2603_21869_gb300 import binding
+    sp = spec.replace(precision=cases.FP64)
+    rng = np.random.default_rng(0)
+    ybar = [rng.standard_normal((sp.nx, sp.ny, sp.nz)) for _ in range(4)]
+    with binding.Case(sp, stream=stream.cuda_stream) as c:
+        c.step(1, allow_not_converged=True)
+        dt = c.info()["dt"]
+        c.projection_vjp(dt, *ybar)
+        c.profile(True)
+        wall, rels = 0.0, []
+        for _ in range(calls):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rel = c.projection_vjp(dt, *ybar)
+            wall += time.perf_counter() - t0
+            rels.append(rel)
+        prof = c.profile_read()
+        c.profile(False)
+    out = {"ms_per_call_wall": wall / calls * 1e3, "rel_residual": max(rels),
+           "note": "FP64; wall time includes the 4 N-double copy in, the 3 N-double copy out and the V-cycles"}
+    for k in ("adj_grad", "adj_rhs"):
+        if k in prof:
+            d = prof[k]
+            gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+            out[k] = {"ms": d["ms"] / d["launches"], "gbs": gbs, "frac": gbs / peak}
+    vc = [v for k, v in prof.items() if k not in ("adj_grad", "adj_rhs")]
+    out["solve_kernel_ms_per_call"] = sum(v["ms"] for v in vc) / calls
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -509,6 +547,8 @@ def main():
                          "the profiler's overhead would distort the autotuner's timings)")
     ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
                     help="flexible-CG acceleration of the pressure solve (auto: the autotuner's choice, else off)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="also time the projection adjoint (fvm_projection_vjp) on an FP64 copy of the workload")
     ap.add_argument("--rk-stages", type=int, default=1, choices=[1, 2, 3],
                     help="explicit stage: forward Euler (1) or the strong-stability-preserving Runge-Kutta "
                          "scheme of order 2 or 3")
@@ -651,6 +691,8 @@ def main():
     diagnostics = {"lambda2": {"ms_per_call": lp["ms"] / lp["launches"], "gbs": lam_gbs,
                                "frac": lam_gbs / peak, "bytes_per_cell": lp["bytes"] / lp["launches"] / N,
                                "vortex_cells": int(np.count_nonzero(lam_out < 0))}}
+    if args.adjoint and rank == 0:
+        diagnostics["projection_vjp"] = time_projection_vjp(spec, stream, flush, peak)
 
     # end to end through the C-ABI with host buffers: write state, one step, read state
     e2e = None
