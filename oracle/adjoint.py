@@ -1,5 +1,6 @@
-"""Adjoint of the pressure projection: the vector-Jacobian product of
-u* -> (u^{n+1}, p) for a differentiable step.
+"""Adjoints (vector-Jacobian products) of two stages of the step, for a
+differentiable step: the pressure projection u* -> (u^{n+1}, p) and the
+semi-implicit destruction step.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -115,3 +116,106 @@ class ProjectionAdjoint:
         xbar = self.JPu.T @ ybar + self.JB.T @ self._solve(q, transpose=True)
         N = self.N
         return [xbar[i * N:(i + 1) * N].reshape(self.shape) for i in range(3)]
+
+
+class DestructionAdjoint:
+    """J^T of the semi-implicit destruction step (u, v, w, k, omega) -> (k', omega')
+    over dt (Section 2.5, Algorithm 4), linearised at a given state.
+
+    Per fluid cell the step is a function of k, omega and the cell gradients
+    G = grad(u, v, w), grad k, grad omega; those gradients are affine stencil
+    maps of the fields (their Jacobians come from local_jacobian on
+    geometry.cell_gradient).  The partial derivatives of the pointwise part
+    are written out below from the forward formulas of oracle/model.py:
+      omega_s = max(omega, eps), Re_t = k / (nu omega_s), x = Re_t / R_beta,
+      beta* = beta*_inf (4/15 + x^4) / (1 + x^4),
+      chi_k = (grad k . grad omega) / omega_s^3,
+      f_beta* = 1 (chi_k <= 0) or (1 + 680 chi_k^2) / (1 + 400 chi_k^2),
+      k' = k / (1 + dt beta* f_beta* omega),
+      chi_w = |tr(Omega Omega S)| / (beta*_inf omega_s)^3,
+      f_beta = (1 + 70 chi_w) / (1 + 80 chi_w),
+      omega' = omega / (1 + dt beta f_beta omega).
+    Solid cells keep k and omega (identity)."""
+
+    def __init__(self, geo, dt, state):
+        from .geometry import U, V, W, K, OM, cell_gradient
+        self.geo, self.dt = geo, dt
+        shape = geo.shape
+        self.shape = shape
+        self.N = int(np.prod(shape))
+        fields = (U, V, W, K, OM)
+        self.Jg = [local_jacobian(lambda x, f=f: cell_gradient(geo, x[0], f), 1, shape) for f in fields]
+        u, v, w, k, om = [np.asarray(a, dtype=np.float64) for a in state]
+        grads = [cell_gradient(geo, phi, f) for phi, f in zip((u, v, w, k, om), fields)]
+        self.G = np.stack([np.stack(grads[i], axis=0) for i in range(3)], axis=0)    # (3, 3, ...)
+        self.gk = np.stack(grads[3], axis=0)
+        self.gw = np.stack(grads[4], axis=0)
+        self.k, self.om = k, om
+
+    def _partials(self):
+        from . import model as m
+        nu, dt = self.geo.spec.nu, self.dt
+        k, om, G, gk, gw = self.k, self.om, self.G, self.gk, self.gw
+        oms = np.maximum(om, m.EPS_OMEGA)
+        doms = (om > m.EPS_OMEGA).astype(np.float64)                # d omega_s / d omega
+        # k' = k / Dk
+        re = k / (nu * oms)
+        dre_dk = 1.0 / (nu * oms)
+        dre_dom = -re / oms * doms
+        x = re / m.R_BETA
+        x4 = x ** 4
+        bs = m.BETA_STAR_INF * (4.0 / 15.0 + x4) / (1.0 + x4)
+        dbs_dre = m.BETA_STAR_INF * (11.0 / 15.0) / (1.0 + x4) ** 2 * 4.0 * x ** 3 / m.R_BETA
+        dot = np.sum(gk * gw, axis=0)
+        chik = dot / oms ** 3
+        pos = chik > 0.0
+        fbs = np.where(pos, (1.0 + 680.0 * chik ** 2) / (1.0 + 400.0 * chik ** 2), 1.0)
+        dfbs = np.where(pos, 560.0 * chik / (1.0 + 400.0 * chik ** 2) ** 2, 0.0)
+        Dk = 1.0 + dt * bs * fbs * om
+        c = -k / Dk ** 2 * dt                                       # d k' / d (beta* f_beta* omega)
+        dk_dk = 1.0 / Dk + c * fbs * om * dbs_dre * dre_dk
+        dk_dom = c * (fbs * om * dbs_dre * dre_dom + bs * om * dfbs * (-3.0 * chik / oms * doms) + bs * fbs)
+        dk_dgk = c * bs * om * dfbs * gw / oms ** 3
+        dk_dgw = c * bs * om * dfbs * gk / oms ** 3
+        # omega' = omega / Dw
+        S = 0.5 * (G + np.swapaxes(G, 0, 1))
+        O = 0.5 * (G - np.swapaxes(G, 0, 1))
+        OO = np.einsum("ij...,jk...->ik...", O, O)
+        T = np.einsum("ik...,ki...->...", OO, S)
+        dT_dS = OO                                                  # d tr(O O S) / d S_ab = (O O)_ba = (O O)_ab
+        dT_dO = -(np.einsum("ij...,jk...->ik...", S, O) + np.einsum("ij...,jk...->ik...", O, S))
+        # chain to G: dS_ab/dG = (delta + transpose)/2, dO_ab/dG = (delta - transpose)/2
+        dT_dG = 0.5 * (dT_dS + np.swapaxes(dT_dS, 0, 1)) + 0.5 * (dT_dO - np.swapaxes(dT_dO, 0, 1))
+        den = (m.BETA_STAR_INF * oms) ** 3
+        chiw = np.abs(T) / den
+        dchiw_dG = np.sign(T) / den * dT_dG
+        dchiw_dom = -3.0 * chiw / oms * doms
+        fb = (1.0 + 70.0 * chiw) / (1.0 + 80.0 * chiw)
+        dfb = -10.0 / (1.0 + 80.0 * chiw) ** 2
+        Dw = 1.0 + dt * m.BETA * fb * om
+        cw = -om / Dw ** 2 * dt * m.BETA                            # d omega' / d (f_beta omega)
+        dw_dom = 1.0 / Dw + cw * (fb + om * dfb * dchiw_dom)
+        dw_dG = cw * om * dfb * dchiw_dG
+        return dk_dk, dk_dom, dk_dgk, dk_dgw, dw_dom, dw_dG
+
+    def vjp(self, kbar, ombar):
+        """Cotangents of (u, v, w, k, omega) for cotangents (kbar, ombar) of (k', omega')."""
+        fluid = self.geo.fluid
+        kb = np.where(fluid, kbar, 0.0)
+        wb = np.where(fluid, ombar, 0.0)
+        dk_dk, dk_dom, dk_dgk, dk_dgw, dw_dom, dw_dG = self._partials()
+        out_k = kb * dk_dk + np.where(fluid, 0.0, kbar)
+        out_om = kb * dk_dom + wb * dw_dom + np.where(fluid, 0.0, ombar)
+        Gbar = wb * dw_dG                                           # (3, 3, ...)
+        gkbar = kb * dk_dgk
+        gwbar = kb * dk_dgw
+
+        def back(J, gbar):   # gbar: (3, ...) cotangent of a gradient -> cotangent of its field
+            return (J.T @ np.concatenate([gbar[a].ravel() for a in range(3)])).reshape(self.shape)
+
+        ub = back(self.Jg[0], Gbar[0])
+        vb = back(self.Jg[1], Gbar[1])
+        wbv = back(self.Jg[2], Gbar[2])
+        out_k = out_k + back(self.Jg[3], gkbar)
+        out_om = out_om + back(self.Jg[4], gwbar)
+        return ub, vb, wbv, out_k, out_om
