@@ -1,6 +1,6 @@
-"""Adjoints (vector-Jacobian products) of two stages of the step, for a
-differentiable step: the pressure projection u* -> (u^{n+1}, p) and the
-semi-implicit destruction step.
+"""Adjoints (vector-Jacobian products) of the stages of the step, for a
+differentiable step: the pressure projection u* -> (u^{n+1}, p), the
+semi-implicit destruction step and the explicit stage.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -27,34 +27,36 @@ import scipy.sparse.linalg as spla
 from .poisson import apply_A, poisson_rhs, project
 
 
-def local_jacobian(apply, n_in, shape):
+def local_jacobian(apply, n_in, shape, reach=1):
     """Matrix of the affine map `apply` (a list of n_in arrays of `shape` -> a
-    list of arrays of `shape`) whose outputs depend only on inputs within one
-    index along each axis.  Rows and columns are field-major, each field in
-    numpy C order.  The matrix is checked against the map on a random input."""
+    list of arrays of `shape`) whose outputs depend only on inputs within
+    `reach` indices along each axis (probes with period 2 reach + 1 per axis).
+    Rows and columns are field-major, each field in numpy C order.  The matrix
+    is checked against the map on a random input."""
     N = int(np.prod(shape))
+    P = 2 * reach + 1
     zero = [np.zeros(shape) for _ in range(n_in)]
     y0 = apply(zero)
     n_out = len(y0)
     idx = np.indices(shape)
     rows, cols, vals = [], [], []
     for fi in range(n_in):
-        for colour in np.ndindex(3, 3, 3):
+        for colour in np.ndindex(P, P, P):
             mask = np.ones(shape, dtype=bool)
             for a in range(3):
-                mask &= (idx[a] % 3) == colour[a]
+                mask &= (idx[a] % P) == colour[a]
             if not mask.any():
                 continue
             x = [np.zeros(shape) for _ in range(n_in)]
             x[fi][mask] = 1.0
             y = apply(x)
             # for every output cell, the probed cell within its reach: along each
-            # axis the index among (q - 1, q, q + 1) with the colour's residue
+            # axis the index among q - reach .. q + reach with the colour's residue
             src = []
             ok = np.ones(shape, dtype=bool)
             for a in range(3):
                 q = idx[a]
-                s = q - 1 + ((colour[a] - (q - 1)) % 3)
+                s = q - reach + ((colour[a] - (q - reach)) % P)
                 ok &= (s >= 0) & (s < shape[a])
                 src.append(np.clip(s, 0, shape[a] - 1))
             src_flat = np.ravel_multi_index(src, shape)
@@ -219,3 +221,43 @@ class DestructionAdjoint:
         out_k = out_k + back(self.Jg[3], gkbar)
         out_om = out_om + back(self.Jg[4], gwbar)
         return ub, vb, wbv, out_k, out_om
+
+
+class ExplicitAdjoint:
+    """J^T of the explicit stage (u, v, w, T, k, omega) -> its update over dt
+    (forward Euler, or the Runge-Kutta schemes of rk_stages 2 and 3),
+    linearised at a given state.
+
+    The Jacobian is taken from the forward oracle itself by complex-step
+    differentiation (Squire and Trapp, SIAM Review 40, 1998): for a real
+    direction d, Im F(x + i h d) / h with h = 1e-30 is the directional
+    derivative J d to rounding, with no subtractive cancellation.  The forward
+    functions are complex-safe: branch decisions (the upwind switch, the
+    clamps, max(omega, eps)) compare real parts, as numpy orders complex
+    numbers by their real part first.  A forward-Euler stage reaches one cell
+    along each axis and s stages reach s cells, so colour probes of period
+    2 s + 1 recover every entry of J.  Clamped values and wall omega get zero
+    derivatives, as the forward sets them to constants."""
+
+    H = 1e-30
+
+    def __init__(self, geo, dt, state, stages=1):
+        from .transport import explicit_stage_rk
+        self.shape = geo.shape
+        self.N = int(np.prod(geo.shape))
+        x = [np.asarray(a, dtype=np.float64) for a in state]
+
+        def jvp(d):
+            y = explicit_stage_rk(geo, [a + 1j * self.H * b for a, b in zip(x, d)], dt, stages)
+            return [np.imag(v) / self.H for v in y]
+
+        self.J = local_jacobian(jvp, 6, self.shape, reach=stages)
+
+    def jvp(self, *d):
+        y = self.J @ np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in d])
+        return [y[i * self.N:(i + 1) * self.N].reshape(self.shape) for i in range(6)]
+
+    def vjp(self, *ybar):
+        """Cotangents of (u, v, w, T, k, omega) for cotangents of the updated fields."""
+        x = self.J.T @ np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in ybar])
+        return [x[i * self.N:(i + 1) * self.N].reshape(self.shape) for i in range(6)]

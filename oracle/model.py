@@ -29,7 +29,7 @@ OMEGA_MIN = 1e-8
 
 def omega_safe(om):
     """max(omega, eps) of Algorithm 4."""
-    return np.maximum(om, EPS_OMEGA)
+    return np.where(np.real(om) > EPS_OMEGA, om, EPS_OMEGA)
 
 
 def re_t(k, om, nu):

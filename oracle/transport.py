@@ -63,7 +63,7 @@ def explicit_rhs(geo, state):
     nut = np.where(geo.fluid, model.nu_t(k, om, nu), 0.0)
     gam_mol = {U: nu, V: nu, W: nu, T: geo.alpha, K: nu, OM: nu}
     sigma = {U: 1.0, V: 1.0, W: 1.0, T: s.Prt, K: s.sigma_k, OM: s.sigma_w}
-    rhs = {f: np.zeros(geo.shape) for f in TRANSPORTED}
+    rhs = {f: np.zeros(geo.shape, dtype=np.result_type(*state)) for f in TRANSPORTED}
     vel = (phis[U], phis[V], phis[W])
     for axis in range(3):
         if geo.shape[axis] == 1:
@@ -75,7 +75,7 @@ def explicit_rhs(geo, state):
         kL, kR, _ = geo.face_states(k, K, axis)
         for f in TRANSPORTED:
             pL, pR, _ = geo.face_states(phis[f], f, axis)
-            up = np.where(u_face >= 0.0, pL, pR)             # I[u_face >= 0] selects W+
+            up = np.where(np.real(u_face) >= 0.0, pL, pR)    # I[u_face >= 0] selects W+
             flux = -(up * u_face) + (gam_mol[f] + nut_f / sigma[f]) * (pR - pL) / h
             if f == axis:
                 flux = flux - (2.0 / 3.0) * 0.5 * (kL + kR)
@@ -118,8 +118,10 @@ def explicit_stage(geo, state, dt):
     rhs = explicit_rhs(geo, state)
     new = [np.where(geo.fluid, phi + dt * r, phi) for phi, r in zip(state, rhs)]
     u, v, w, T_, k, om = new
-    k = np.where(geo.fluid, np.maximum(k, model.K_MIN), k)
-    om = np.where(geo.fluid, np.maximum(om, model.OMEGA_MIN), om)
+    # (decisions on the real part: the same values for real fields, and one branch
+    # for the complex-step derivatives of the adjoint)
+    k = np.where(geo.fluid, np.where(np.real(k) > model.K_MIN, k, model.K_MIN), k)
+    om = np.where(geo.fluid, np.where(np.real(om) > model.OMEGA_MIN, om, model.OMEGA_MIN), om)
     ow = wall_omega(geo)
     om = np.where(ow > 0.0, ow, om)
     return [u, v, w, T_, k, om]
