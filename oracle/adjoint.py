@@ -261,3 +261,44 @@ class ExplicitAdjoint:
         """Cotangents of (u, v, w, T, k, omega) for cotangents of the updated fields."""
         x = self.J.T @ np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in ybar])
         return [x[i * self.N:(i + 1) * self.N].reshape(self.shape) for i in range(6)]
+
+
+class StepAdjoint:
+    """J^T of one whole time step (Section 2.6) at a given state, with the
+    pressure solve exact and dt fixed:
+        s1 = D(x0), s2 = E(s1), s3 = D(s2)     (destruction dt/2, explicit dt,
+                                                 destruction dt/2; D changes k and
+                                                 omega only)
+        (u, v, w, p) = Pi(u, v, w of s3)       (right-hand side, solve, projection)
+    with T, k and omega of s3 passing to the output.  The cotangent of the
+    output (u, v, w, p, T, k, omega) runs back through the stage adjoints
+    above in reverse order."""
+
+    def __init__(self, geo, dt, state, stages=1):
+        from .destruction import destruction_step
+        from .transport import explicit_stage_rk
+        self.geo = geo
+        x0 = [np.asarray(a, dtype=np.float64) for a in state]
+        u, v, w, T, k, om = x0
+        self.D1 = DestructionAdjoint(geo, 0.5 * dt, [u, v, w, k, om])
+        k, om = destruction_step(geo, u, v, w, k, om, 0.5 * dt)
+        s1 = [u, v, w, T, k, om]
+        self.E = ExplicitAdjoint(geo, dt, s1, stages)
+        u, v, w, T, k, om = explicit_stage_rk(geo, s1, dt, stages)
+        self.D2 = DestructionAdjoint(geo, 0.5 * dt, [u, v, w, k, om])
+        self.P = ProjectionAdjoint(geo, geo.level0, dt)
+
+    @staticmethod
+    def _through_destruction(D, bar):
+        """bar = cotangents of (u, v, w, T, k, omega) after D -> before D."""
+        u, v, w, T, k, om = bar
+        du, dv, dw, dk, dom = D.vjp(k, om)
+        return [u + du, v + dv, w + dw, T, dk, dom]
+
+    def vjp(self, ubar, vbar, wbar, pbar, Tbar, kbar, ombar):
+        """Cotangents of (u, v, w, T, k, omega) at the start of the step."""
+        bu, bv, bw = self.P.vjp(ubar, vbar, wbar, pbar)
+        bar = [bu, bv, bw, Tbar, kbar, ombar]
+        bar = self._through_destruction(self.D2, bar)
+        bar = self.E.vjp(*bar)
+        return self._through_destruction(self.D1, bar)
