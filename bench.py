@@ -169,7 +169,9 @@ def run_reference(args, spec, label, rank, ws):
         c.step()
     el = time.perf_counter() - t0
     v = spec.cells * args.steps / el
-    line = {"impl": "reference", "metric": "cell-steps/s", "value": v, "unit": "cell-steps/s", "n_gpus": 0,
+    # n_gpus: the launch's N (the driver's key); the oracle itself runs on one host core
+    line = {"impl": "reference", "metric": "cell-steps/s", "value": v, "unit": "cell-steps/s", "n_gpus": ws,
+            "host_only": True,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": label, "cells": spec.cells},
