@@ -567,9 +567,17 @@ def main():
         return
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
-    if args.workload == "served" and args.impl == "ours":
+    if args.workload == "served":
         rank, ws, local, dist = dist_setup()
-        run_served(args, rank, ws, local, dist)
+        if args.impl == "ours":
+            run_served(args, rank, ws, local, dist)
+            return
+        args.steps, args.warmup = min(args.steps, 2), 0
+        _, specs = cases.served_rooms(args.requests, seed=rank, rate=args.rate)
+        run_reference(args, min(specs, key=lambda sp: sp.cells),
+                      "served rooms: the smallest request (oracle, one request at a time)", rank, ws)
+        if dist:
+            dist.destroy_process_group()
         return
     if args.workload == "batched":
         rank, ws, local, dist = dist_setup()
