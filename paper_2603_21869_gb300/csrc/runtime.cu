@@ -457,6 +457,8 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
             for (int j = bx.j0; j < bx.j1; ++j)
                 for (int i = bx.i0; i < bx.i1; ++i) pl.tag[cell_index(i, j, k, n[0], n[1])] = (uint8_t)(bi + 1);
     }
+    if (d->n_boxes > 0 && std::find(pl.tag.begin(), pl.tag.end(), (uint8_t)0) == pl.tag.end())
+        return fail(FVM_ERR_INVALID, "the boxes leave no fluid cell");
     for (int f = 0; f < 6; ++f) pl.face_patch[f].assign(face_cells(n, f), (uint8_t)f);
     for (int v = 0; v < d->n_vents; ++v) {
         const fvm_vent& ve = d->vents[v];

@@ -103,6 +103,8 @@ def test_case_bytes_scale_with_precision(lib):
     dict(mg_variant=2),
     dict(coarse_sweeps=-1),
     dict(coarse_sweeps=1, mg_variant=1),
+    dict(rk_stages=-1),
+    dict(boxes=[cases.Box(0, 32, 0, 16, 0, 8), cases.Box(0, 32, 0, 16, 8, 16)]),
 ])
 def test_invalid_descriptors_are_rejected_without_a_gpu(lib, bad):
     spec = cases.heated_channel_3d(32, 16, 16, mg_levels=3).replace(**bad)
