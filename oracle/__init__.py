@@ -28,8 +28,9 @@ Modules
               initial state
   diagnostics the lambda_2 vortex criterion of the transient results
               (Section 3.2.3)
-  adjoint     the vector-Jacobian product of the projection (b(u*), exact
-              solve, u* - dt G p), the first piece of a differentiable step
+  adjoint     vector-Jacobian products for a differentiable step: the
+              projection (b(u*), exact solve, u* - dt G p), the destruction
+              step, the explicit stage and a whole time step
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
 against closed forms, invariants, special cases or brute force, except the
