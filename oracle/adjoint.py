@@ -29,15 +29,19 @@ from .poisson import apply_A, poisson_rhs, project
 
 def local_jacobian(apply, n_in, shape, reach=1):
     """Matrix of the affine map `apply` (a list of n_in arrays of `shape` -> a
-    list of arrays of `shape`) whose outputs depend only on inputs within
-    `reach` indices along each axis (probes with period 2 reach + 1 per axis).
-    Rows and columns are field-major, each field in numpy C order.  The matrix
-    is checked against the map on a random input."""
+    list of output arrays) whose output entry q depends only on inputs within
+    `reach` indices of q along each axis (probes with period 2 reach + 1 per
+    axis).  An output may have one more entry than `shape` along an axis (face
+    values: face q lies between cells q - 1 and q).  Rows and columns are
+    array-major, each array in numpy C order.  The matrix is checked against the
+    map on a random input."""
     N = int(np.prod(shape))
     P = 2 * reach + 1
     zero = [np.zeros(shape) for _ in range(n_in)]
     y0 = apply(zero)
     n_out = len(y0)
+    out_sizes = [int(np.prod(y.shape)) for y in y0]
+    out_off = np.concatenate([[0], np.cumsum(out_sizes)])
     idx = np.indices(shape)
     rows, cols, vals = [], [], []
     for fi in range(n_in):
@@ -50,26 +54,27 @@ def local_jacobian(apply, n_in, shape, reach=1):
             x = [np.zeros(shape) for _ in range(n_in)]
             x[fi][mask] = 1.0
             y = apply(x)
-            # for every output cell, the probed cell within its reach: along each
-            # axis the index among q - reach .. q + reach with the colour's residue
-            src = []
-            ok = np.ones(shape, dtype=bool)
-            for a in range(3):
-                q = idx[a]
-                s = q - reach + ((colour[a] - (q - reach)) % P)
-                ok &= (s >= 0) & (s < shape[a])
-                src.append(np.clip(s, 0, shape[a] - 1))
-            src_flat = np.ravel_multi_index(src, shape)
             for fo in range(n_out):
+                # for every output entry, the probed cell within its reach: along each
+                # axis the index among q - reach .. q + reach with the colour's residue
+                oidx = np.indices(y0[fo].shape)
+                src = []
+                ok = np.ones(y0[fo].shape, dtype=bool)
+                for a in range(3):
+                    q = oidx[a]
+                    s = q - reach + ((colour[a] - (q - reach)) % P)
+                    ok &= (s >= 0) & (s < shape[a])
+                    src.append(np.clip(s, 0, shape[a] - 1))
+                src_flat = np.ravel_multi_index(src, shape)
                 d = y[fo] - y0[fo]
                 nz = (d != 0.0)
                 assert not (nz & ~ok).any(), "output outside the reach of its probe"
                 r = np.flatnonzero(nz)
-                rows.append(fo * N + r)
+                rows.append(out_off[fo] + r)
                 cols.append(fi * N + src_flat.ravel()[r])
                 vals.append(d.ravel()[r])
     J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(n_out * N, n_in * N))
+                      shape=(int(out_off[-1]), n_in * N))
     rng = np.random.default_rng(12345)
     x = [rng.standard_normal(shape) for _ in range(n_in)]
     want = np.concatenate([(a - b).ravel() for a, b in zip(apply(x), y0)])
@@ -302,3 +307,133 @@ class StepAdjoint:
         bar = self._through_destruction(self.D2, bar)
         bar = self.E.vjp(*bar)
         return self._through_destruction(self.D1, bar)
+
+
+def _face_diff_T(rbar, axis, h):
+    """Transpose of D_op along `axis`: cell cotangents -> face cotangents."""
+    shape = list(rbar.shape)
+    shape[axis] += 1
+    fb = np.zeros(shape)
+    hi = [slice(None)] * 3
+    lo = [slice(None)] * 3
+    hi[axis] = slice(1, None)
+    lo[axis] = slice(0, -1)
+    fb[tuple(hi)] += rbar / h
+    fb[tuple(lo)] -= rbar / h
+    return fb
+
+
+def explicit_vjp_by_hand(geo, state, dt, ybar):
+    """J^T ybar of one forward-Euler explicit stage with every partial derivative
+    written out: an independent derivation of ExplicitAdjoint(stages=1), and the
+    arithmetic a GPU kernel of the adjoint follows.
+
+    Per face along axis a, with u_f = (U_L + U_R)/2, phi_up = phi_L if u_f >= 0 else
+    phi_R and Gamma = gamma + nu_t,f / sigma, the flux -phi_up u_f + Gamma (phi_R -
+    phi_L)/h (- (k_L + k_R)/3 for the momentum component along a) has the partials
+    d/d phi_up = -u_f, d/d u_f = -phi_up, d/d phi_R = -d/d phi_L = Gamma / h,
+    d/d nu_t,f = (phi_R - phi_L) / (sigma h), d/d k_L = d/d k_R = -1/3.  The face
+    states (ghosts of Section 2.7) and the face eddy viscosity are affine maps of the
+    cell values, transposed by colour probing.  Sources: G_k = nu_t S^2 (dS^2/dG_ab =
+    4 S_ab), G_omega = alpha (omega / k) G_k, buoyancy -g_i beta_T (T - T_ref).  The
+    update phi + dt rhs passes nothing from clamped k, omega or the wall omega."""
+    from . import model as m
+    from .geometry import U, V, W, T, K, OM, FK_SOLID, cell_gradient
+    from .transport import TRANSPORTED, _nut_faces, explicit_rhs, wall_omega
+    s = geo.spec
+    nu = s.nu
+    shape = geo.shape
+    x = [np.asarray(a, dtype=np.float64) for a in state]
+    phis = dict(zip(TRANSPORTED, x))
+    pos = {f: i for i, f in enumerate(TRANSPORTED)}              # field id -> state slot
+    k, om = phis[K], phis[OM]
+    fluid = geo.fluid
+    gam_mol = {U: nu, V: nu, W: nu, T: geo.alpha, K: nu, OM: nu}
+    sigma = {U: 1.0, V: 1.0, W: 1.0, T: s.Prt, K: s.sigma_k, OM: s.sigma_w}
+    # the update: which cells pass a derivative
+    rhs = explicit_rhs(geo, x)
+    live_k = fluid & (k + dt * rhs[4] > m.K_MIN)
+    live_o = fluid & (om + dt * rhs[5] > m.OMEGA_MIN) & ~(wall_omega(geo) > 0.0)
+    live = [fluid, fluid, fluid, fluid, live_k, live_o]
+    xbar = [np.where(fluid, 0.0, yb) + np.where(lv, yb, 0.0) for yb, lv in zip(ybar, live)]
+    rbar = [np.where(lv, dt * yb, 0.0) for yb, lv in zip(ybar, live)]
+    nut = np.where(fluid, m.nu_t(k, om, nu), 0.0)
+    nutbar = np.zeros(shape)
+
+    def fs_T(field, axis, Lb, Rb):
+        J = local_jacobian(lambda z: list(geo.face_states(z[0], field, axis)[:2]), 1, shape)
+        return (J.T @ np.concatenate([Lb.ravel(), Rb.ravel()])).reshape(shape)
+
+    for axis in range(3):
+        if shape[axis] == 1:
+            continue
+        h = geo.h[axis]
+        UL, UR, kind = geo.face_states(x[axis], axis, axis)
+        u_face = 0.5 * (UL + UR)
+        nut_f = _nut_faces(nut, axis, kind)
+        solid_f = kind == FK_SOLID
+        ufb = np.zeros(u_face.shape)
+        nfb = np.zeros(u_face.shape)
+        kLb = np.zeros(u_face.shape)
+        kRb = np.zeros(u_face.shape)
+        upL = u_face >= 0.0
+        for f in TRANSPORTED:
+            pL, pR, _ = geo.face_states(phis[f], f, axis)
+            up = np.where(upL, pL, pR)
+            fb = _face_diff_T(rbar[pos[f]], axis, h)
+            fb[solid_f] = 0.0
+            gam = gam_mol[f] + nut_f / sigma[f]
+            pLb = np.where(upL, -u_face * fb, 0.0) - gam / h * fb
+            pRb = np.where(upL, 0.0, -u_face * fb) + gam / h * fb
+            xbar[pos[f]] = xbar[pos[f]] + fs_T(f, axis, pLb, pRb)
+            ufb += -up * fb
+            nfb += (pR - pL) / (h * sigma[f]) * fb
+            if f == axis:
+                kLb += -fb / 3.0
+                kRb += -fb / 3.0
+        xbar[axis] = xbar[axis] + fs_T(axis, axis, 0.5 * ufb, 0.5 * ufb)
+        xbar[pos[K]] = xbar[pos[K]] + fs_T(K, axis, kLb, kRb)
+        JN = local_jacobian(lambda z: [_nut_faces(z[0], axis, kind)], 1, shape)
+        nutbar += (JN.T @ nfb.ravel()).reshape(shape)
+    # sources
+    G = np.stack([np.stack(cell_gradient(geo, x[i], f), axis=0) for i, f in enumerate((U, V, W))], axis=0)
+    S = 0.5 * (G + np.swapaxes(G, 0, 1))
+    S2 = 2.0 * np.sum(S * S, axis=(0, 1))
+    oms = np.where(om > m.EPS_OMEGA, om, m.EPS_OMEGA)
+    doms = (om > m.EPS_OMEGA).astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        re = k / (nu * oms)
+        dre_dk = 1.0 / (nu * oms)
+        dre_dom = -re / oms * doms
+        r = re / m.R_K
+        ast = m.ALPHA_STAR_INF * (m.ALPHA_STAR_0 + r) / (1.0 + r)
+        dast = m.ALPHA_STAR_INF * (1.0 - m.ALPHA_STAR_0) / (m.R_K * (1.0 + r) ** 2)
+        nut_c = ast * k / oms
+        dnut_dk = ast / oms + k / oms * dast * dre_dk
+        dnut_dom = -ast * k / oms ** 2 * doms + k / oms * dast * dre_dom
+        rw = re / m.R_OMEGA
+        A = (m.ALPHA_0 + rw) / (1.0 + rw)
+        dA = (1.0 - m.ALPHA_0) / (m.R_OMEGA * (1.0 + rw) ** 2)
+        ac = m.ALPHA_INF * A / ast
+        dac = m.ALPHA_INF * (dA / ast - A * dast / ast ** 2)
+        Gk = nut_c * S2
+        q = ac * om / k                                             # G_omega = q G_k
+        dq_dk = dac * dre_dk * om / k - ac * om / k ** 2
+        dq_dom = dac * dre_dom * om / k + ac / k
+    rk, ro = rbar[4], rbar[5]
+    Gkb = np.where(fluid, rk + ro * q, 0.0)
+    xbar[4] = xbar[4] + np.where(fluid, ro * Gk * dq_dk, 0.0)
+    xbar[5] = xbar[5] + np.where(fluid, ro * Gk * dq_dom, 0.0)
+    nutbar = nutbar + np.where(fluid, Gkb * S2, 0.0)
+    S2b = np.where(fluid, Gkb * nut_c, 0.0)
+    Gbar = 4.0 * S * S2b
+    xbar[4] = xbar[4] + np.where(fluid, nutbar * dnut_dk, 0.0)
+    xbar[5] = xbar[5] + np.where(fluid, nutbar * dnut_dom, 0.0)
+    for i, f in enumerate((U, V, W)):
+        J = local_jacobian(lambda z, f=f: cell_gradient(geo, z[0], f), 1, shape)
+        xbar[i] = xbar[i] + (J.T @ np.concatenate([Gbar[i, a].ravel() for a in range(3)])).reshape(shape)
+    if s.buoyancy:
+        for i in range(3):
+            if s.gravity[i] != 0.0:
+                xbar[3] = xbar[3] + np.where(fluid, -s.gravity[i] * s.beta_T * rbar[i], 0.0)
+    return xbar

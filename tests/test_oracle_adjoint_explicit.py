@@ -1,14 +1,15 @@
 """Pins of the explicit-stage adjoint (oracle/adjoint.py, ExplicitAdjoint):
 the complex-step directional derivatives agree with central differences of
 the forward stage; the colour-probed Jacobian equals the dense Jacobian built
-one unit vector at a time (brute force on a tiny grid); and the
+one unit vector at a time (brute force on a tiny grid); the
 vector-Jacobian product satisfies <J d, ybar> = <d, J^T ybar> against a
-complex-step derivative taken directly along d."""
+complex-step derivative taken directly along d; and the hand-derived
+forward-Euler adjoint (explicit_vjp_by_hand) equals it to rounding."""
 import numpy as np
 import pytest
 
 from oracle import transport
-from oracle.adjoint import ExplicitAdjoint
+from oracle.adjoint import ExplicitAdjoint, explicit_vjp_by_hand
 from oracle.step import OracleCase
 from paper_2603_21869_gb300 import cases
 
@@ -105,3 +106,13 @@ def test_wall_omega_cells_have_no_derivative():
     ybar = [np.zeros(geo.shape) for _ in range(6)]
     ybar[5] = np.where(ow, rng.standard_normal(geo.shape), 0.0)
     assert all(np.max(np.abs(a)) == 0.0 for a in adj.vjp(*ybar))
+
+
+@pytest.mark.parametrize("name", list(SPECS))
+def test_hand_derived_adjoint_equals_complex_step_adjoint(name):
+    geo, x, dt = _state(SPECS[name](), 8)
+    adj = ExplicitAdjoint(geo, dt, x, 1)
+    rng = np.random.default_rng(9)
+    ybar = [rng.standard_normal(geo.shape) for _ in range(6)]
+    for a, b in zip(adj.vjp(*ybar), explicit_vjp_by_hand(geo, x, dt, ybar)):
+        assert np.max(np.abs(a - b)) <= 1e-13 * max(float(np.max(np.abs(a))), 1e-300)
