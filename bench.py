@@ -1,18 +1,20 @@
 """Benchmark: k-omega RANS finite-volume time steps on one GB300 (or N replicas).
 
-Default workload: the 3D heated channel, 256 x 64 x 64 cells (1 cm cells on
-the paper's 2.56 x 0.64 x 0.64 m verification channel), inlet 2 m/s, 6-level
-V-cycles to a 1e-8 relative residual, seeded +-1 % initial perturbation,
-FP32 storage with the FP64 defect-correction pressure solve.
+Default workload: the mixed-precision indoor room, 512 x 256 x 128 cells
+(16.8 M cells at 2 cm), seeded ceiling vents, floor outlet and heated boxes,
+Boussinesq buoyancy, 7-level multigrid to a 1e-8 relative residual, FP32
+field storage with BF16 multigrid corrections inside the FP64
+defect-correction pressure solve (--precision bf16).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|f32|f64]
+                    [--workload room|channel|channel2d|batched|served]
                     [--impl ours|reference]
 
 Prints one JSON line.  value = cell-steps/s over all ranks (each rank steps
 its own replica; no collective on the data path, weak scaling).  Timing: W
 untimed steps, then K steps each bracketed by CUDA events on the case's
-stream, with a 256 MB buffer written between steps so the step starts with
-a cold L2 (the state is ~30 MB, below the 129 MB L2).
+stream, with a 256 MB buffer written between steps (larger than the 129 MB
+L2; the room's state is larger than L2 as well).
 """
 import argparse
 import json
@@ -45,14 +47,30 @@ def workload(name, precision):
     raise SystemExit(f"unknown workload {name}")
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel, from one ncu capture each (profiles/sweep_v4_room_channel_batched_fp32.md);
-# to be taken again whenever that kernel changes.
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's denominator is the measured copy)
-TRAFFIC = {("channel", "f32", "sweep_L0"): 10.49e6, ("room", "f32", "sweep_L0"): 212.38e6}
-# the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell,
-# from a 32-case capture of the same batch (the first 32 of its cases), scaled by the cells
-TRAFFIC_PER_CELL = {("batched", "f32", "sweep_L0"): 458.10e6 / 29294592}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
+# from one ncu capture, with the SHA-256 prefix of the source file that kernel was built from
+# when the counters were taken: a changed source reports null until it is captured again.
+TRAFFIC = {}
+# the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell
+TRAFFIC_PER_CELL = {}
+
+
+def _src_sha(name):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2603_21869_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(table, key):
+    """Measured DRAM bytes for key, or None if absent or taken from an older source."""
+    t = table.get(key)
+    if not t:
+        return None
+    try:
+        return t["bytes"] if _src_sha(t["src"]) == t["sha"] else None
+    except OSError:
+        return None
 
 
 def time_projection_vjp(spec, stream, flush, peak, calls=3):
@@ -156,19 +174,39 @@ def dist_setup():
     return rank, ws, local, dist
 
 
-def run_reference(args, spec, label, rank, ws):
+# Above this many cells one oracle step takes minutes (about 6 minutes for the 16.8 M-cell
+# room on one host thread): the oracle is then timed on the same workload scaled down.
+ORACLE_FULL_CELLS = 1 << 21
+
+
+def oracle_sample(spec, workload):
+    """(spec, description) of the bounded sample the oracle is timed on: the workload itself when
+    one step is short, else the same generator at a quarter of the cells along each axis and the
+    same cell size (two multigrid levels fewer), whose per-cell-step rate stands in."""
+    if spec.cells <= ORACLE_FULL_CELLS or workload != "room":
+        return spec.replace(precision=cases.FP64), f"the full {spec.nx}x{spec.ny}x{spec.nz} workload"
+    sp = cases.room_3d(spec.nx // 4, spec.ny // 4, spec.nz // 4, seed=spec.seed,
+                       mg_levels=max(2, spec.mg_levels - 2), precision=cases.FP64,
+                       mg_rel_tol=spec.mg_rel_tol, max_vcycles=spec.max_vcycles)
+    return sp, (f"a {sp.nx}x{sp.ny}x{sp.nz} room from the same seeded generator at the same cell size "
+                f"(1/64 of the cells; the oracle's per-cell-step rate falls by about a quarter from "
+                f"0.26 M to 2.1 M cells)")
+
+
+def run_reference(args, spec, label, rank, ws, workload="channel"):
     """The FP64 CPU oracle as it stands, on a bounded sample of the same workload."""
     if rank != 0:
         return
     from oracle.step import OracleCase
-    c = OracleCase(spec.replace(precision=cases.FP64))
+    sp, what = oracle_sample(spec, workload)
+    c = OracleCase(sp)
     for _ in range(args.warmup):
         c.step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         c.step()
     el = time.perf_counter() - t0
-    v = spec.cells * args.steps / el
+    v = sp.cells * args.steps / el
     # n_gpus: the launch's N (the driver's key); the oracle itself runs on one host core
     line = {"impl": "reference", "metric": "cell-steps/s", "value": v, "unit": "cell-steps/s", "n_gpus": ws,
             "host_only": True,
@@ -176,7 +214,7 @@ def run_reference(args, spec, label, rank, ws):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": label, "cells": spec.cells},
             "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.warmup} untimed + {args.steps} timed steps of the full workload "
+                             "sample": f"{args.warmup} untimed + {args.steps} timed steps of {what} "
                                        "(numpy float64, one thread)"},
             "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -289,7 +327,7 @@ def run_batched(args, rank, ws, local, dist):
         total_ms = replicas.max_over_ranks(total_ms)
     value = ws * N * args.steps / (total_ms / 1e3)
     prof_steps = min(args.steps, 5)
-    tpc = TRAFFIC_PER_CELL.get(("batched", args.precision, "sweep_L0"))
+    tpc = traffic_for(TRAFFIC_PER_CELL, ("batched", args.precision, "sweep_L0"))
     bd = breakdown(batch.profile(prof_steps), prof_steps, {"sweep_L0": tpc * N} if tpc else None)
 
     # end to end through the C-ABI with host buffers: write every case, one batched step, read back
@@ -478,20 +516,22 @@ def compare_variants(args):
                       "results": out}), flush=True)
 
 
-def cpu_baseline(spec, budget_s=25.0):
-    """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload."""
+def cpu_baseline(spec, workload="channel", budget_s=25.0):
+    """Time the oracle (rank 0, N = 1) on a bounded sample: whole steps of the workload, or of
+    its scaled-down copy when one full step would take minutes."""
     from oracle.step import OracleCase
+    sp, what = oracle_sample(spec, workload)
     t0 = time.perf_counter()
-    c = OracleCase(spec.replace(precision=cases.FP64))
+    c = OracleCase(sp)
     n = 0
     ts = time.perf_counter()
     while n < 1 or (time.perf_counter() - t0 < budget_s and n < 3):
         c.step()
         n += 1
     el = time.perf_counter() - ts
-    return {"value": spec.cells * n / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} step(s) of the full {spec.nx}x{spec.ny}x{spec.nz} workload, numpy float64 on one "
-                      f"host thread ({os.cpu_count()} cores present)"}
+    return {"value": sp.cells * n / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} step(s) of {what}, numpy float64 on one host thread "
+                      f"({os.cpu_count()} cores present)"}
 
 
 def _oracle_steps(job):
@@ -535,8 +575,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=list(PREC))
-    ap.add_argument("--workload", default="channel")
+    ap.add_argument("--precision", default="bf16", choices=list(PREC))
+    ap.add_argument("--workload", default="room")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cases", type=int, default=64, help="batched workload: cases per GPU")
@@ -615,9 +655,10 @@ def main():
     if args.krylov != "auto":
         spec = spec.replace(krylov=int(args.krylov))
     if args.impl == "reference":
-        args.steps = min(args.steps, 2)
-        args.warmup = min(args.warmup, 0)
-        run_reference(args, spec, label, rank, ws)
+        # a bounded sample: each step of the oracle takes seconds (the scaled room about 5 s)
+        args.steps = min(args.steps, 5)
+        args.warmup = min(args.warmup, 1)
+        run_reference(args, spec, label, rank, ws, args.workload)
         if dist:
             dist.destroy_process_group()
         return
@@ -749,7 +790,7 @@ def main():
                 "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,
                              "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
-                             "traffic": TRAFFIC.get((args.workload, args.precision, name)),
+                             "traffic": traffic_for(TRAFFIC, (args.workload, args.precision, name)),
                              "bytes_per_launch": d["bytes"] / d["launches"],
                              "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"]},
                 "vcycle": {"gbs": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None,
@@ -764,9 +805,10 @@ def main():
                 "diagnostics": diagnostics}
     case.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(spec)
-        if spec.cells <= (1 << 21):   # one copy per core must fit in host memory
-            line["cpu_baseline_all_cores"] = cpu_all_cores(spec)
+        line["cpu_baseline"] = cpu_baseline(spec, args.workload)
+        sp_all, _ = oracle_sample(spec, args.workload)
+        if sp_all.cells <= (1 << 21):   # one copy per core must fit in host memory
+            line["cpu_baseline_all_cores"] = cpu_all_cores(sp_all)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -186,30 +186,59 @@ enum {
    Used for admission against a memory budget. */
 size_t fvm_case_bytes(const fvm_case_desc* desc);
 
-/* Validate desc, allocate the case's device memory, build boundary tables,
-   multigrid levels and the coarsest-level inverse, and set the seeded
-   initial state (p = 0).  *out is set only on FVM_OK. */
+/* Set up one case of the problem statement of Section 2.1 (the k-omega
+   equations, Eqs. ko_mom - ko_temp with the standard constants printed
+   there) on its grid, with the boundary conditions of Section 2.7 (one
+   ghost layer, Eqs. bc_x - bc; solid boxes by masks; wall omega
+   6 nu / (beta_i d^2)) and the inlet turbulence of Section 3.2.4
+   (k0 = 1.5 (u0 I0)^2, omega0 from the length scale l0).
+   Validates desc, allocates the case's device memory, builds boundary
+   tables, the multigrid levels of Section 2.4 (full coarsening, Eq.
+   restriction) and the coarsest-level inverse, and sets the seeded initial
+   state (p = 0).
+     desc : caller-owned, read during the call only (vents, boxes copied)
+     out  : receives the library-owned case; set only on FVM_OK
+   FVM_ERR_INVALID for a bad descriptor (fvm_last_error says which field),
+   FVM_ERR_OOM if device memory runs out (nothing is leaked). */
 fvm_status fvm_create_case(const fvm_case_desc* desc, fvm_case** out);
 
 /* Free everything the case holds (after finishing its queued work). */
 void fvm_destroy_case(fvm_case* c);
 
-/* Advance nsteps time steps.  Synchronises the case's stream; out (may be
-   NULL) receives statistics.  Returns FVM_ERR_NOT_CONVERGED if a solve hit
-   max_vcycles above mg_rel_tol (the step is still taken), FVM_ERR_DIVERGED
-   on a non-finite residual or time step. */
+/* Advance nsteps time steps of the Strang-split scheme of Section 2.6: the
+   destruction half step dt/2 (Section 2.5, Eqs. k_des_step / o_des_step,
+   Algorithm 4), the explicit stage of convection, diffusion and production
+   (Algorithms 2 and 3, Section A.4), the second half step, the pressure
+   right-hand side (Eq. pc_residual), the multigrid solve of Section 2.4 and
+   the projection u = u* - dt grad p.  Each step is one CUDA graph on the
+   case's stream; the call synchronises that stream at the end.
+     c     : the case (not thread safe)
+     out   : caller-owned, may be NULL; statistics of the last step
+   FVM_ERR_NOT_CONVERGED if a solve hit max_vcycles above mg_rel_tol (the
+   step is still taken), FVM_ERR_DIVERGED on a non-finite residual or time
+   step, FVM_ERR_INVALID for nsteps < 0. */
 fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out);
 
 /* Run one stage of the step (FVM_STAGE_*), for verification. */
 fvm_status fvm_run_stage(fvm_case* c, int stage);
 
-/* Run ncycles V-cycles on the case's current b and p (no convergence test);
-   *rel_residual (may be NULL) gets ||b - A p|| / ||b|| afterwards. */
+/* Run ncycles multigrid cycles on A p = b with the case's current b and p
+   (Section 2.4: A the negative Laplacian of Eq. neg_lap_discretize,
+   weighted Jacobi smoothing of Eq. jacobi_pc, Eqs. restriction and
+   prolongation; Algorithm 1's own scheme with desc.mg_variant = 1), with no
+   convergence test; p is updated in place on the device.
+     rel_residual : caller-owned, may be NULL; ||b - A p|| / ||b|| over the
+                    fluid cells after the cycles (FP64)
+   Synchronises the case's stream.  FVM_ERR_INVALID for ncycles < 0. */
 fvm_status fvm_vcycle(fvm_case* c, int ncycles, double* rel_residual);
 
-/* Copy the fields in field_mask, converted to double, into host_out: the
-   selected fields in id order, each nx*ny*nz values.  n = capacity of
-   host_out in doubles.  Synchronises. */
+/* Copy the fields of Section 2.1 selected by field_mask (u, v, w, p, T, k,
+   omega: bit i for field id i) converted to double into host_out: the
+   selected fields in id order, each nx*ny*nz values, x fastest.
+     host_out : caller-owned host buffer of n doubles (pinned or pageable)
+   An empty mask copies nothing.  Synchronises the case's stream.
+   FVM_ERR_INVALID for mask bits above 6, a null buffer with a non-empty
+   mask, or n below the number of values selected. */
 fvm_status fvm_read_fields(fvm_case* c, unsigned field_mask, double* host_out, size_t n);
 
 /* Overwrite the fields in field_mask from host_in (same layout as
@@ -252,7 +281,12 @@ fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n);
    host_ybar: 4 nx*ny*nz doubles (ubar, vbar, wbar, pbar; field-major, x
    fastest); host_xbar: 3 nx*ny*nz doubles out; n = the number of doubles
    host_ybar holds (>= 4 nx*ny*nz); host_xbar must hold 3 nx*ny*nz.
-   *rel_out (may be NULL) gets the final relative residual.  FP64 cases
+   *rel_out (may be NULL) gets the final relative residual.  A is
+   nonsingular on the fluid cells: fvm_create_case rejects cases without a
+   zero-value (outlet) face.  Fluid enclosed by obstacles with no path to an
+   outlet would make A singular there; q then generally lies outside A's range
+   and the solve ends with FVM_ERR_NOT_CONVERGED.  Each chunk of four cycles
+   restarts the flexible-CG direction of krylov = 1 cases.  FP64 cases
    only.  FVM_ERR_NOT_CONVERGED if rel_tol was not reached (xbar is still
    written); FVM_ERR_INVALID for null pointers, dt <= 0, rel_tol <= 0,
    max_vcycles < 1, a short buffer or a reduced-precision case.
@@ -439,18 +473,19 @@ fvm_status fvm_profile_read(fvm_case* c, fvm_kernel_stat* out, int cap, int* n_o
    program whose device memory belongs to a pooling allocator, a control
    loop that must not take an allocation's latency or implicit
    synchronisation, or a plug-in that must keep its device footprint fixed).
-   Computes r = b - A p on an nx x ny x nz box without obstacles, A the
-   7-point -Laplacian of the multigrid (Eq. neg_lap_discretize), each domain
-   face zero-gradient for p (dirichlet[face] = 0) or zero-value (1), and
-   norms[0] = ||r||^2, norms[1] = ||b||^2.
+   Computes r = b - A p on an nx x ny x nz box without obstacles, A the same
+   7-point negative Laplacian the pressure solve uses (one ghost per domain
+   face: zero-gradient for p where dirichlet[face] = 0, zero-value where it
+   is 1; a one-cell axis contributes no term), and norms[0] = ||r||^2,
+   norms[1] = ||b||^2.
      p, b, r : device pointers to nx*ny*nz doubles, x fastest (caller-owned)
      norms   : device pointer to 2 doubles (caller-owned)
      h       : host array, cell sizes along x, y, z; dirichlet: host array of 6
      stream  : cudaStream_t or NULL; the call only enqueues work
    The kernel's scratch (per-block partial sums and a counter, about 1 MB) is a
    static device array that every GPU loading the library keeps until exit;
-   grids above 65,536 blocks of 32 x 4 x 2 cells (16,777,216 cells) are
-   rejected with FVM_ERR_INVALID.  The first call on a device looks up that
+   grids above 65,536 blocks of 32 x 4 x 2 cells (16,777,216 cells), or above
+   65,535 blocks along y or z, are rejected with FVM_ERR_INVALID.  The first call on a device looks up that
    array's address (with the device current); make that first call before any
    stream capture.  All calls share the array: calls that overlap on the GPU
    (other streams, other threads) race and must be serialised by the caller. */

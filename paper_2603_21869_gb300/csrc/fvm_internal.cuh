@@ -469,11 +469,13 @@ __device__ __forceinline__ void batch_run(const K* __restrict__ ks, const BatchM
     int cend = __ldg(m.start + c + 1);
     batch_enter(ks, m, c, buf, &s_live);
     for (int v = lo; v < hi; ++v) {
-        if (v == cend) {   // the next case begins at its own first block
-            ++c;
+        if (v == cend) {   // the next case with blocks begins at its own first block
+            do {           // (the host rejects empty cases; skipping them keeps the walk in bounds anyway)
+                ++c;
+                cend = __ldg(m.start + c + 1);
+            } while (v == cend);
             g = m.grid[c];
             b = make_uint3(0, 0, 0);
-            cend = __ldg(m.start + c + 1);
             batch_enter(ks, m, c, buf, &s_live);
         }
         if (s_live) {

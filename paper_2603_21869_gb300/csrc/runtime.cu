@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -263,21 +264,28 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
 }
 
 int persistent_blocks(const void* fn, int threads, size_t smem, bool query) {
+    // keyed by everything the answer depends on: the kernel, its block size and shared memory, the device
     static std::mutex mu;
-    static std::map<std::pair<const void*, size_t>, int> cache;
+    static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find({fn, smem});
+    const auto key = std::make_tuple(fn, threads, smem, dev);
+    auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     if (!query) return 0;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    const int n = sms * (per_sm > 0 ? per_sm : 1);
-    cache[{fn, smem}] = n;
+    if (per_sm < 1) return 0;   // the kernel cannot run with this block: no launch
+    const int n = sms * per_sm;
+    cache[key] = n;
     return n;
 }
 
@@ -1670,7 +1678,12 @@ fvm_status build_arena(std::vector<Merged>* segs, int nseg, const std::vector<fv
             for (size_t i = 0; i < n; ++i) {
                 start[i] = (int)tot;
                 const dim3 g = m.recs[i]->grid;
-                tot += (int64_t)g.x * g.y * g.z;
+                const int64_t nb = (int64_t)g.x * g.y * g.z;
+                if (nb < 1) {   // every case of a launch owns at least one block (the device walk relies on it)
+                    cudaFree(dev);
+                    return fail(FVM_ERR_INVALID, "batched launch " + m.site + ": a case with an empty grid");
+                }
+                tot += nb;
             }
             start[n] = (int)tot;
             off += (n + 1) * sizeof(int);

@@ -147,12 +147,16 @@ extern "C" fvm_status fvm_poisson_residual_static(const double* p, const double*
         set_last_error("grid dimensions must be >= 1 and spacings > 0");
         return FVM_ERR_INVALID;
     }
-    const dim3 block(SX, SY, SZ);
-    const dim3 grid((unsigned)((nx + SX - 1) / SX), (unsigned)((ny + SY - 1) / SY), (unsigned)((nz + SZ - 1) / SZ));
-    if ((long long)grid.x * grid.y * grid.z > kMaxBlocks) {
-        set_last_error("grid larger than the static scratch holds (65,536 blocks of 32 x 4 x 2 cells)");
+    // block counts in 64-bit arithmetic (nx near INT32_MAX must not wrap), each factor checked
+    // before the product: y and z are also bounded by the launch limit of 65,535 blocks
+    const int64_t gx = ((int64_t)nx + SX - 1) / SX, gy = ((int64_t)ny + SY - 1) / SY, gz = ((int64_t)nz + SZ - 1) / SZ;
+    if (gx > kMaxBlocks || gy > 65535 || gz > 65535 || gx * gy > kMaxBlocks || gx * gy * gz > kMaxBlocks) {
+        set_last_error("grid larger than the static scratch holds (65,536 blocks of 32 x 4 x 2 cells, at most "
+                       "65,535 along y and z)");
         return FVM_ERR_INVALID;
     }
+    const dim3 block(SX, SY, SZ);
+    const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
     double* scratch = nullptr;
     std::string err;
     fvm_status st = scratch_for_current_device(&scratch, err);
