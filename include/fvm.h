@@ -324,8 +324,8 @@ typedef struct {
 /* Group n cases (the array is copied; the cases stay owned by the caller,
    who must destroy the batch before any of its cases).  stream: the
    cudaStream_t the batch runs on, or NULL for a stream of its own.
-   Errors: FVM_ERR_INVALID (null or repeated case, mixed precisions, a case
-   on the cluster or TMA paths, profiling on), FVM_ERR_OOM, FVM_ERR_CUDA. */
+   Errors: FVM_ERR_INVALID (null or repeated case, mixed precisions,
+   profiling on), FVM_ERR_OOM, FVM_ERR_CUDA. */
 fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out);
 
 /* Advance every case by nsteps.  stats (may be NULL): n entries, in the

@@ -7,8 +7,9 @@
              (Eq. jacobi_pc; weighted)
   RES        mean of the 2x2x2 children (Eq. restriction)
   PROL       cell-centred trilinear interpolation, 3/4 parent + 1/4
-             neighbour per axis, neighbour index clamped to the grid
-             (Eq. prolongation)
+             neighbour per axis (Eq. prolongation); beyond a domain face
+             the neighbour is the coarse level's ghost (Section 2.7 rules:
+             the cell itself, negated across a zero-value face)
   V-cycle    pre-smooth, restrict the residual, recurse, prolong and
              correct, post-smooth; exact dense solve on the coarsest level;
              coarse_sweeps > 0 sets both sweep counts on the levels below
@@ -124,18 +125,45 @@ def restrict(lev, r):
     return r.reshape(c[0], f[0], c[1], f[1], c[2], f[2]).mean(axis=(1, 3, 5))
 
 
-def prolong(coarse, fine_shape):
-    """PROL: per active axis, fine cell = 3/4 parent + 1/4 neighbour on the
-    fine cell's side (neighbour index clamped into the coarse grid)."""
-    e = coarse
+def ghost_pad(lev, e):
+    """The coarse field with one ghost layer on each side of every active axis,
+    by the pressure rules of Section 2.7 applied on the level: the cell's own
+    value across a zero-gradient face, its negative across a zero-value
+    (outlet) face.  Axes are padded in turn, so an edge or corner ghost carries
+    the signs of all its faces (the face masks extend into the ghost layers of
+    the axes padded before by their edge values)."""
+    g = e
     for axis in range(3):
-        nc = e.shape[axis]
-        nf = fine_shape[axis]
-        if nf == nc:
+        if not lev.active[axis]:
             continue
+        n = g.shape[axis]
+        lo = np.take(g, [0], axis=axis)
+        hi = np.take(g, [n - 1], axis=axis)
+        masks = []
+        for face in (2 * axis, 2 * axis + 1):
+            m = lev.dirichlet[face]
+            # the mask's two axes are the tangential axes in increasing order
+            tang = [a for a in range(3) if a != axis]
+            pad = [(1, 1) if (lev.active[a] and a < axis) else (0, 0) for a in tang]
+            m = np.pad(m, pad, mode="edge")
+            masks.append(np.expand_dims(m, axis))
+        g = np.concatenate([np.where(masks[0], -lo, lo), g, np.where(masks[1], -hi, hi)], axis=axis)
+    return g
+
+
+def prolong(coarse_lev, coarse, fine_shape):
+    """PROL: cell-centred trilinear interpolation (Eq. prolongation): per
+    active axis, fine cell = 3/4 parent + 1/4 the parent's neighbour on the
+    fine cell's side.  A neighbour beyond a domain face is the coarse level's
+    ghost (ghost_pad)."""
+    e = ghost_pad(coarse_lev, coarse)
+    for axis in range(3):
+        if not coarse_lev.active[axis]:
+            continue
+        nf = fine_shape[axis]
         i_f = np.arange(nf)
-        parent = i_f // 2
-        nb = np.clip(parent + np.where(i_f % 2 == 0, -1, 1), 0, nc - 1)
+        parent = i_f // 2 + 1                                   # +1: the ghost layer
+        nb = parent + np.where(i_f % 2 == 0, -1, 1)
         e = 0.75 * np.take(e, parent, axis=axis) + 0.25 * np.take(e, nb, axis=axis)
     return e
 
@@ -202,7 +230,7 @@ class Multigrid:
         p = smooth(lev, p, b, pre, wJ)
         bc = restrict(lev, residual(lev, p, b))
         ec = self.vcycle(np.zeros(self.levels[l + 1].shape), bc, l + 1)
-        p = np.where(lev.fluid, p + prolong(ec, lev.shape), 0.0)
+        p = np.where(lev.fluid, p + prolong(self.levels[l + 1], ec, lev.shape), 0.0)
         p = smooth(lev, p, b, post, wJ)
         return p
 

@@ -13,8 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfvm.so")
-SOURCES = ["runtime.cu", "step_kernels.cu", "mg_kernels.cu", "mg_cluster.cu", "mg_tma.cu", "static_residual.cu",
-           "server.cu", "autotune.cu"]
+SOURCES = ["runtime.cu", "step_kernels.cu", "mg_kernels.cu", "static_residual.cu", "server.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -177,27 +177,11 @@ struct SolveState {
     int32_t fixed;           // > 0: exactly this many cycles
     int32_t notconv;         // sticky flag: a solve stopped at max_cycles above tol
     int32_t inner;           // V-cycles per outer (FP64) residual
-    int32_t tma_timeout;     // sticky flag: a bounded device-side wait (tensor copy, grid barrier) gave up
-    uint32_t bar_count;      // grid barrier of the persistent tail kernel: blocks arrived
-    uint32_t bar_gen;        // and its generation
     // flexible CG with one kept direction (krylov = 1)
     uint32_t g_counter;      // blocks finished in the inner-product pass
     int32_t g_valid;         // a previous direction is kept
     double g_alpha, g_beta;  // step along the new direction, its component along the previous one
     double g_dq;             // (d, A d) of the kept direction
-};
-
-// Levels ls..L-1 of one V-cycle run by one persistent kernel: grid levels
-// ls..lc-1 by all blocks (grid-stride loops between grid barriers), the
-// coarse levels lc.. by block 0 in shared memory.
-struct TailLevels {
-    int32_t ls, lc, nl;      // first level in the kernel, first coarse level, number of levels
-    int32_t pre, post;
-    int32_t pad;
-    LevelDev lv[FVM_MAX_LEVELS];    // by absolute level index
-    void* e[FVM_MAX_LEVELS][2];
-    void* r[FVM_MAX_LEVELS];
-    uint64_t mx[FVM_MAX_LEVELS], my[FVM_MAX_LEVELS];   // exact division by n_x, n_y (div_magic)
 };
 
 // Levels lc..L-1, cycled by one CTA in shared memory.
@@ -208,28 +192,6 @@ struct CoarseLevels {
     LevelDev lv[FVM_MAX_LEVELS];
 };
 
-// Levels lc..L-1, cycled by one thread-block cluster: each level is cut into
-// slabs of planes along axis D (2 = z, or 1 = y in 2D); CTA q owns planes
-// [q ppc, (q + 1) ppc).  Offsets are identical in every CTA's shared memory.
-struct ClusterLevels {
-    int32_t nl, pre, post, cs;
-    int32_t D;
-    int32_t fbyte0;          // byte offset of the neighbour-code region
-    int32_t fcount;          // uint16 entries in that region
-    int32_t lm;              // levels lm.. are held whole by CTA 0 (ppc = nD)
-    int32_t ppc[FVM_MAX_LEVELS];     // planes per CTA
-    int32_t plane[FVM_MAX_LEVELS];   // cells per plane
-    int32_t nD[FVM_MAX_LEVELS];      // planes of the level
-    int32_t off[FVM_MAX_LEVELS];     // first element (compute type) of the level's e, e', r
-    int32_t foff[FVM_MAX_LEVELS];    // first neighbour-code entry of the level
-    // multipliers for exact division by plane size, nx and ppc: q / d = (q * m) >> 40
-    // (m = ceil(2^40 / d); exact while q * d < 2^40)
-    uint64_t mP[FVM_MAX_LEVELS], mX[FVM_MAX_LEVELS], mC[FVM_MAX_LEVELS];
-    LevelDev lv[FVM_MAX_LEVELS];
-};
-
-__host__ __device__ __forceinline__ uint64_t div_magic(uint32_t d) { return ((1ull << 40) + d - 1) / d; }
-__device__ __forceinline__ int fdiv(int q, uint64_t m) { return (int)(((uint64_t)(uint32_t)q * m) >> 40); }
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ __forceinline__ int64_t cell_index(int i, int j, int k, int nx, int ny) {
@@ -329,39 +291,12 @@ cudaError_t launch_prolong_nearest_to_p(int inner, const LevelDev& Lf, const Lev
                                         const SolveState* st, cudaStream_t s);
 cudaError_t launch_jacobi_p(int bprec, const LevelDev& L, double* p, const void* b, double* q, const SolveState* st,
                             cudaStream_t s);
-// persistent tail of the V-cycle (levels ls.. of one case); the correction of level ls ends in
-// e[ls][tail_out_index(pre, post)]
-int tail_blocks(int inner, size_t smem);
-cudaError_t launch_tail(int inner, const TailLevels& t, const CoarseLevels& cl, const double* Ainv, SolveState* st,
-                        int nblocks, size_t smem, cudaStream_t s);
-inline int tail_out_index(int pre, int post) { return ((pre - 1) + post) & 1; }
 cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_in, void* e_out, const double* Ainv,
                               const SolveState* st, cudaStream_t s);
 cudaError_t launch_convert(int src_prec, int dst_prec, const void* src, void* dst, int64_t N, cudaStream_t s);
 int resid0_blocks(int nx, int ny, int nz);
 int level0_blocks_max(int nx, int ny, int nz);   // blocks of any level-0 reduction pass, at most
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner);
-// cluster kernel (mg_cluster.cu)
-size_t cluster_smem_bytes(const ClusterLevels& cl, int inner);
-cudaError_t prepare_coarse_cluster(int inner, int cs, size_t smem, int* max_clusters);
-cudaError_t launch_coarse_cluster(int inner, const ClusterLevels& cl, const void* r_in, void* e_out,
-                                  const double* Ainv, const SolveState* st, cudaStream_t s);
-
-// fused TMA level kernels (mg_tma.cu); FP32 inner precision only
-#include <cuda.h>
-struct TmaMaps {
-    CUtensorMap e[2], r, f;   // fine level: the two e buffers, r, neighbour codes
-    CUtensorMap ec[2];        // coarse level: its two e buffers
-};
-bool tma_level_ok(const LevelDev& L, const LevelDev& Lc);
-cudaError_t tma_prepare();
-bool tma_make_maps(TmaMaps& mp, const LevelDev& L, const LevelDev& Lc, void* const* e, const void* r,
-                   void* const* ec);
-cudaError_t launch_down_tma(int nsweeps, const TmaMaps& mp, int ein, const LevelDev& L, const LevelDev& Lc,
-                            void* e_out, void* rc, SolveState* st, cudaStream_t s);
-cudaError_t launch_up_tma(int nsweeps, bool top, const TmaMaps& mp, int ein, int ecb, const LevelDev& L,
-                          const LevelDev& Lc, void* e_out, double* p, SolveState* st, cudaStream_t s);
-
 // ---------------------------------------------------------------- one case or many per launch
 // Every step and multigrid kernel is a functor K with `static constexpr int
 // kThreads` and `__device__ void run(const BlockAt&) const` (the level-0

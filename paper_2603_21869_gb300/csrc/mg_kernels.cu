@@ -249,7 +249,6 @@ struct SolveBeginK {
     __device__ void run(const BlockAt&) const {
         st->cycles = 0;
         st->counter = 0u;
-        st->bar_count = 0u;
         st->g_counter = 0u;
         st->g_valid = 0;
         st->active = 1;
@@ -321,17 +320,29 @@ __device__ void ResidRestrictK<TI>::run(const BlockAt& at) const {
     store_restricted<TI, C>(Lc, rc, ec0, I + Lc.n[0] * (J + Lc.n[1] * K), sum / (C)(fx * fy * fz));
 }
 
-// trilinear prolongation of a coarse field at fine cell (i,j,k)
-template <class C, class G>
-__device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int j, int k, G get) {
+// Trilinear prolongation of a coarse field at fine cell (i,j,k) (Eq.
+// prolongation): per active axis 3/4 of the parent and 1/4 of the parent's
+// neighbour on the fine cell's side.  A neighbour beyond a domain face is the
+// coarse level's ghost of the clamped cell (the boundary rules of Section 2.7
+// on every level): the cell's own value across a zero-gradient face, its
+// negative across a zero-value (outlet) face; at an edge or corner the signs
+// of both faces apply.  get(q) reads the coarse value, code(q) the coarse
+// cell's 16-bit neighbour code (two bits per face, 2 = zero-value).
+template <class C, class G, class F>
+__device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int j, int k, G get, F code) {
     const int f[3] = {i, j, k};
-    int P[3], Q[3];
+    int P[3], Q[3], side[3];
+    bool out[3];
     C w[3][2];
     for (int a = 0; a < 3; ++a) {
+        out[a] = false;
+        side[a] = 0;
         if (fa[a]) {
             P[a] = f[a] >> 1;
-            int q = P[a] + ((f[a] & 1) ? 1 : -1);
-            Q[a] = q < 0 ? 0 : (q >= cn[a] ? cn[a] - 1 : q);
+            const int q = P[a] + ((f[a] & 1) ? 1 : -1);
+            out[a] = q < 0 || q >= cn[a];
+            side[a] = q < 0 ? 0 : 1;
+            Q[a] = out[a] ? P[a] : q;
             w[a][0] = (C)0.75;
             w[a][1] = (C)0.25;
         } else {
@@ -345,7 +356,18 @@ __device__ __forceinline__ C prolong_at(const int* fa, const int* cn, int i, int
         for (int sy = 0; sy < (fa[1] ? 2 : 1); ++sy)
             for (int sx = 0; sx < (fa[0] ? 2 : 1); ++sx) {
                 const int ii = sx ? Q[0] : P[0], jj = sy ? Q[1] : P[1], kk = sz ? Q[2] : P[2];
-                acc += w[0][sx] * w[1][sy] * w[2][sz] * get(ii + cn[0] * (jj + cn[1] * kk));
+                const int q = ii + cn[0] * (jj + cn[1] * kk);
+                C v = get(q);
+                const bool gx = sx && out[0], gy = sy && out[1], gz = sz && out[2];
+                if (gx || gy || gz) {
+                    const uint32_t fc = code(q);
+                    bool neg = false;
+                    if (gx) neg ^= ((fc >> (2 * (0 + side[0]))) & 3u) == 2u;
+                    if (gy) neg ^= ((fc >> (2 * (2 + side[1]))) & 3u) == 2u;
+                    if (gz) neg ^= ((fc >> (2 * (4 + side[2]))) & 3u) == 2u;
+                    if (neg) v = -v;
+                }
+                acc += w[0][sx] * w[1][sy] * w[2][sz] * v;
             }
     return acc;
 }
@@ -365,7 +387,8 @@ struct ProlongK {
         if (!cell3(Lf, at, i, j, k)) return;
         const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
         if (is_solid(Lf.nbf[c])) return;
-        const C add = prolong_at<C>(Lf.active, Lc.n, i, j, k, [&](int q) { return to_c<C>(ldg(ec + q)); });
+        const C add = prolong_at<C>(Lf.active, Lc.n, i, j, k, [&](int q) { return to_c<C>(ldg(ec + q)); },
+                                    [&](int q) { return (uint32_t)__ldg(Lc.nbf + q); });
         e[c] = from_c<TI, C>(to_c<C>(e[c]) + add);
     }
 };
@@ -486,7 +509,7 @@ template <> struct Vec4<__nv_bfloat16> {
     }
 };
 
-constexpr int V4X = 4 * TX;   // cells of a row per warp
+
 
 template <class TI, int MODE>
 struct SweepV4K {
@@ -984,7 +1007,8 @@ struct FcgUpdV4K {
 // consecutive coarse cells, one float2 per coarse row), their x neighbours
 // I0 - 1 and I0 + 2 come from the adjacent lanes; per fine cell the weights
 // are 3/4 for the parent and 1/4 for the neighbour on the cell's side, per
-// axis, neighbour indices clamped (Eq. prolongation).  Needs the x and y axes
+// axis (Eq. prolongation); a neighbour beyond a domain face is the coarse
+// cell's ghost, as in prolong_at.  Needs the x and y axes
 // active and nx % 4 = 0.
 template <class TI> struct Vec2;
 template <> struct Vec2<float> {
@@ -1018,6 +1042,13 @@ struct ProlongV4K {
     __device__ void run(const BlockAt& at) const;
 };
 
+// a coarse value across a ghost row or plane: negated for each zero-value face among them
+__device__ __forceinline__ float ghost_signed(uint32_t code, bool gy, int sy, bool gz, int sz, float v) {
+    bool neg = gy && ((code >> (2 * (2 + sy))) & 3u) == 2u;
+    neg ^= gz && ((code >> (2 * (4 + sz))) & 3u) == 2u;
+    return neg ? -v : v;
+}
+
 template <class TI>
 __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
     using C = float;
@@ -1027,33 +1058,51 @@ __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
     const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
-    const bool last = i4 + 4 >= nx;
+    const bool last = i4 + 4 >= nx;   // the row's last coarse cell is this thread's: its x+ neighbour is a ghost
     const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const bool first = ic == 0;       // and its first: the x- neighbour is a ghost
     const int I0 = ic >> 1;
-    const int Pj = jc >> 1, Qj = min(max(Pj + ((jc & 1) ? 1 : -1), 0), NY - 1);
+    // the y neighbour of the parent row; beyond a domain face it is the ghost row (the parent
+    // row's cells, each signed by its own face code)
+    const int Pj = jc >> 1, qj = Pj + ((jc & 1) ? 1 : -1);
+    const bool outJ = qj < 0 || qj >= NY;
+    const int Qj = outJ ? Pj : qj, sJ = qj < 0 ? 0 : 1;
     const bool zact = Lf.active[2] != 0;
     const TI* const ecp = ec;
     TI* const ep = e;
     const uint16_t* const nbf = Lf.nbf;
+    const uint16_t* const cnbf = Lc.nbf;
     for (int k = k0; k < k1; ++k) {
         const int Pk = zact ? (k >> 1) : k;
-        const int Qk = zact ? min(max(Pk + ((k & 1) ? 1 : -1), 0), NZ - 1) : k;
+        const int qk = zact ? Pk + ((k & 1) ? 1 : -1) : k;
+        const bool outK = qk < 0 || qk >= NZ;
+        const int Qk = outK ? Pk : qk, sK = qk < 0 ? 0 : 1;
         const C wz0 = zact ? (C)0.75 : (C)1, wz1 = zact ? (C)0.25 : (C)0;
         C add[4] = {(C)0, (C)0, (C)0, (C)0};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int jj = (q & 1) ? Qj : Pj, kk = (q & 2) ? Qk : Pk;
+            const bool gy = (q & 1) && outJ, gz = (q & 2) && outK;
             const C w = ((q & 1) ? (C)0.25 : (C)0.75) * ((q & 2) ? wz1 : wz0);
             const int row = NX * (jj + NY * kk);
             C c0, c1;
             Vec2<TI>::load(ecp, row + I0, c0, c1);
-            const C lft = lane == 0 ? to_c<C>(ldg(ecp + row + max(I0 - 1, 0))) : (C)0;
-            const C rgt = lane == LR - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
+            C lft = lane == 0 ? to_c<C>(ldg(ecp + row + max(I0 - 1, 0))) : (C)0;
+            C rgt = lane == LR - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
+            uint32_t cw = 0u;   // the codes of coarse cells I0, I0 + 1 (only where a ghost is formed)
+            if (gy || gz || first || last) cw = __ldg(reinterpret_cast<const uint32_t*>(cnbf + row + I0));
+            if (gy || gz) {
+                c0 = ghost_signed(cw & 0xffffu, gy, sJ, gz, sK, c0);
+                c1 = ghost_signed(cw >> 16, gy, sJ, gz, sK, c1);
+                if (lane == 0 && !first) lft = ghost_signed(__ldg(cnbf + row + I0 - 1), gy, sJ, gz, sK, lft);
+                if (lane == LR - 1 && !last) rgt = ghost_signed(__ldg(cnbf + row + I0 + 2), gy, sJ, gz, sK, rgt);
+            }
             C left = __shfl_up_sync(0xffffffffu, c1, 1, LR);
             C right = __shfl_down_sync(0xffffffffu, c0, 1, LR);
             if (lane == 0) left = lft;
             if (lane == LR - 1) right = rgt;
-            if (last) right = c1;
+            if (first) left = (cw & 3u) == 2u ? -c0 : c0;                 // x- ghost of coarse cell I0
+            if (last) right = ((cw >> 18) & 3u) == 2u ? -c1 : c1;         // x+ ghost of coarse cell I0 + 1
             add[0] += w * ((C)0.75 * c0 + (C)0.25 * left);
             add[1] += w * ((C)0.75 * c0 + (C)0.25 * c1);
             add[2] += w * ((C)0.75 * c1 + (C)0.25 * c0);
@@ -1400,7 +1449,9 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
             const int rem = c - k * n0 * n1;
             const int j = small_div(rem, in0);
             const int i = rem - j * n0;
-            e[c] += prolong_at<C>(L.active, Lc.n, i, j, k, [&](int q) { return ec[q]; });
+            const uint16_t* const fc = F[l + 1];
+            e[c] += prolong_at<C>(L.active, Lc.n, i, j, k, [&](int q) { return ec[q]; },
+                                  [&](int q) { return (uint32_t)fc[q]; });
         }
         __syncthreads();
         int s = cur[l];
@@ -1615,162 +1666,6 @@ struct CopyPK {
         p[c] = q[c];
     }
 };
-
-// ------------------------------------------------------------------ persistent tail of the V-cycle
-// Levels ls..lc-1 by every block (grid-stride loops over the level's cells,
-// a grid barrier between phases), the coarse levels lc.. by block 0 with the
-// single-CTA solve, then back up.  One launch replaces the sweeps,
-// restrictions, prolongations and the coarse solve of those levels (their
-// grids are small: a kernel boundary costs more than the work).  The grid
-// has one block per SM, all resident; the barrier's wait is bounded and
-// reports a time-out through the solve state.
-constexpr int kTailThreads = 1024;
-
-__device__ bool tail_barrier(SolveState* st, unsigned nblk) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile uint32_t* gen = &st->bar_gen;
-        const uint32_t g = *gen;
-        __threadfence();
-        if (atomicAdd(&st->bar_count, 1u) == nblk - 1u) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            long long it = 0;
-            while (*gen == g) {
-                if (++it > (1ll << 22)) {   // about a second
-                    st->tma_timeout = 1;
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-__device__ __forceinline__ void cell_ijk(const LevelDev& L, uint64_t mx, uint64_t my, int c, int& i, int& j,
-                                         int& k) {
-    const int q = fdiv(c, mx);
-    i = c - q * L.n[0];
-    k = fdiv(q, my);
-    j = q - k * L.n[1];
-}
-
-// one Jacobi sweep of a level (first: from e = 0, i.e. e = w_J r / D)
-template <class TI>
-__device__ void tail_sweep(const LevelDev& L, uint64_t mx, uint64_t my, const TI* ein, const TI* r, TI* eout,
-                           bool first, int g0, int gs) {
-    using C = typename Acc<TI>::type;
-    const C wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
-    const int sy = L.n[0], sz = L.n[0] * L.n[1];
-    for (int c = g0; c < (int)L.N; c += gs) {
-        const uint32_t f = L.nbf[c];
-        const C rr = to_c<C>(ldg(r + c));
-        C v = (C)0;
-        if (!is_solid(f)) {
-            if (first) {
-                v = wJ * rr * iD;
-            } else {
-                int i, j, k;
-                cell_ijk(L, mx, my, c, i, j, k);
-                const C eP = to_c<C>(ldg(ein + c));
-                const C xm = to_c<C>(ldg(ein + c - (i > 0 ? 1 : 0))), xp = to_c<C>(ldg(ein + c + (i < L.n[0] - 1 ? 1 : 0)));
-                const C ym = to_c<C>(ldg(ein + c - (j > 0 ? sy : 0))), yp = to_c<C>(ldg(ein + c + (j < L.n[1] - 1 ? sy : 0)));
-                const C zm = to_c<C>(ldg(ein + c - (k > 0 ? sz : 0))), zp = to_c<C>(ldg(ein + c + (k < L.n[2] - 1 ? sz : 0)));
-                v = eP + wJ * (rr - A7<C>(L, f, eP, xm, xp, ym, yp, zm, zp)) * iD;
-            }
-        }
-        eout[c] = from_c<TI, C>(v);
-    }
-}
-
-template <class TI>
-struct TailK {
-    static constexpr int kThreads = kTailThreads;
-    TailLevels t;
-    CoarseLevels cl;
-    const double* Ainv;
-    SolveState* st;
-    __device__ bool live() const { return st->active != 0; }
-    __device__ void run(const BlockAt& at) const;
-};
-
-template <class TI>
-__device__ void TailK<TI>::run(const BlockAt& at) const {
-    using C = typename Acc<TI>::type;
-    const unsigned nblk = at.g.x;
-    const int g0 = at.b.x * kThreads + threadIdx.x, gs = (int)nblk * kThreads;
-    int cur[FVM_MAX_LEVELS];
-    // down
-    for (int l = t.ls; l < t.lc; ++l) {
-        const LevelDev& L = t.lv[l];
-        TI* const* e = (TI* const*)t.e[l];
-        const TI* r = (const TI*)t.r[l];
-        tail_sweep<TI>(L, t.mx[l], t.my[l], nullptr, r, e[0], true, g0, gs);
-        int q = 0;
-        for (int it = 1; it < t.pre; ++it) {
-            if (!tail_barrier(st, nblk)) return;
-            tail_sweep<TI>(L, t.mx[l], t.my[l], e[q], r, e[q ^ 1], false, g0, gs);
-            q ^= 1;
-        }
-        cur[l] = q;
-        if (!tail_barrier(st, nblk)) return;
-        // coarse r = mean of the children's residuals
-        const LevelDev& Lc = t.lv[l + 1];
-        TI* rc = (TI*)t.r[l + 1];
-        const int fx = L.active[0] ? 2 : 1, fy = L.active[1] ? 2 : 1, fz = L.active[2] ? 2 : 1;
-        for (int cc = g0; cc < (int)Lc.N; cc += gs) {
-            int I, J, K;
-            cell_ijk(Lc, t.mx[l + 1], t.my[l + 1], cc, I, J, K);
-            C sum = (C)0;
-            for (int dz = 0; dz < fz; ++dz)
-                for (int dy = 0; dy < fy; ++dy)
-                    for (int dx = 0; dx < fx; ++dx) {
-                        const int c = (I * fx + dx) + L.n[0] * ((J * fy + dy) + L.n[1] * (K * fz + dz));
-                        const uint32_t f = L.nbf[c];
-                        if (is_solid(f)) continue;
-                        const C eP = to_c<C>(ldg(e[q] + c));
-                        sum += to_c<C>(ldg(r + c)) - apply_A<C>(L, f, e[q], c, eP);
-                    }
-            rc[cc] = from_c<TI, C>(sum / (C)(fx * fy * fz));
-        }
-        if (!tail_barrier(st, nblk)) return;
-    }
-    // coarse levels in block 0
-    if (at.b.x == 0) coarse_cta_body<TI>(cl, (const TI*)t.r[t.lc], (TI*)t.e[t.lc][0], Ainv);
-    if (!tail_barrier(st, nblk)) return;
-    // up
-    for (int l = t.lc - 1; l >= t.ls; --l) {
-        const LevelDev& L = t.lv[l];
-        const LevelDev& Lc = t.lv[l + 1];
-        TI* const* e = (TI* const*)t.e[l];
-        const TI* r = (const TI*)t.r[l];
-        const TI* ec = (const TI*)t.e[l + 1][l + 1 == t.lc ? 0 : cur[l + 1]];
-        int q = cur[l];
-        for (int c = g0; c < (int)L.N; c += gs) {
-            if (is_solid(L.nbf[c])) continue;
-            int i, j, k;
-            cell_ijk(L, t.mx[l], t.my[l], c, i, j, k);
-            const C add = prolong_at<C>(L.active, Lc.n, i, j, k, [&](int w) { return to_c<C>(ldg(ec + w)); });
-            e[q][c] = from_c<TI, C>(to_c<C>(e[q][c]) + add);
-        }
-        for (int it = 0; it < t.post; ++it) {
-            if (!tail_barrier(st, nblk)) return;
-            tail_sweep<TI>(L, t.mx[l], t.my[l], e[q], r, e[q ^ 1], false, g0, gs);
-            q ^= 1;
-        }
-        cur[l] = q;
-        if (l > t.ls && !tail_barrier(st, nblk)) return;
-    }
-}
 
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, int64_t N) {
@@ -2038,30 +1933,6 @@ cudaError_t launch_jacobi_p(int bprec, const LevelDev& L, double* p, const void*
     else err = launch_k(JacobiPK<float>{L, p, (const float*)b, q, st}, grid3(L), kBlock3, 0, s);
     if (err != cudaSuccess) return err;
     return launch_k(CopyPK{L, q, p, st}, grid3(L), kBlock3, 0, s);
-}
-
-int tail_blocks(int inner, size_t smem) {
-    int per_sm = 0, sms = 0, dev = 0;
-    cudaError_t e = cudaSuccess;
-    DISPATCH_I(inner, {
-        e = raise_smem_limit((const void*)k_one<TailK<TI>>, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_one<TailK<TI>>, kTailThreads, smem);
-    });
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        return 0;
-    }
-    return sms;   // one block per SM: all resident at once
-}
-
-cudaError_t launch_tail(int inner, const TailLevels& t, const CoarseLevels& cl, const double* Ainv, SolveState* st,
-                        int nblocks, size_t smem, cudaStream_t s) {
-    cudaError_t err = cudaSuccess;
-    DISPATCH_I(inner, err = launch_k_one(TailK<TI>{t, cl, Ainv, st}, dim3(nblocks), dim3(kTailThreads), smem, s));
-    return err;
 }
 
 cudaError_t launch_convert(int sp, int dp, const void* src, void* dst, int64_t N, cudaStream_t s) {

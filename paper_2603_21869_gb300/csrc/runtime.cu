@@ -36,11 +36,6 @@ fvm_status fail(fvm_status st, const std::string& msg) {
 constexpr double kCmu = 0.09;
 constexpr double kBetaI = 0.072;
 
-int getenv_flag(const char* name) {
-    const char* v = getenv(name);
-    return v && *v && *v != '0' ? 1 : 0;
-}
-
 size_t elem_size(int prec) { return prec == FVM_FP64 ? 8 : (prec == FVM_FP32 ? 4 : 2); }
 
 struct HostLevel {
@@ -300,8 +295,6 @@ struct DevLevel {
     LevelDev dev;
     void* e[2] = {nullptr, nullptr};
     void* r = nullptr;
-    bool tma = false;   // fused TMA down / up kernels on this level
-    TmaMaps maps;
 };
 
 struct fvm_case {
@@ -333,16 +326,10 @@ struct fvm_case {
     std::vector<DevLevel> levels;
     SolveState* sst = nullptr;       // device
     SolveState* h_sst = nullptr;     // pinned host copy
-    size_t lc = 0;                   // first level cycled by the coarse kernel (cluster or single CTA)
-    bool use_cluster = false;
-    ClusterLevels cluster;
+    size_t lc = 0;                   // first level cycled by the single-CTA coarse kernel
     int inner_cycles = 1;            // V-cycles per outer residual (adaptive solves)
     int rule_inner = 1;              // the same for the rule in force (1 for fixed-count solves)
     CoarseLevels coarse;
-    // persistent tail kernel for levels tail_ls.. (0: not used)
-    int tail_ls = 0;
-    int tail_blocks = 0;
-    TailLevels tail;
     // CUDA graphs of whole time steps, keyed by the field pointers they were captured with
     bool use_graph = true;
     struct StepGraph {
@@ -722,12 +709,10 @@ int post_at(const fvm_case* c, size_t l) {
     return l > 0 && c->desc.coarse_sweeps > 0 ? c->desc.coarse_sweeps : c->desc.post_sweeps;
 }
 
-// Level l (> 0) gets its first Jacobi sweep from the restriction that forms its r:
-// both it and its parent take the plain kernels (not the coarse, tail or TMA forms).
+// Level l (> 0) gets its first Jacobi sweep from the restriction that forms its r
+// (not the levels the single-CTA coarse kernel cycles).
 bool first_sweep_fused(const fvm_case* c, size_t l) {
-    if (l == 0 || l >= c->lc || c->levels[l].tma || c->levels[l - 1].tma) return false;
-    if (!g_rec && c->tail_ls > 0 && l == (size_t)c->tail_ls) return false;
-    return true;
+    return l > 0 && l < c->lc;
 }
 
 // One V-cycle of the correction equation on levels l.. with r on level l;
@@ -746,58 +731,13 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
         const double nco = (double)c->levels.back().dev.N;
         double cells = 0.0;
         for (size_t q = l; q < c->levels.size(); ++q) cells += (double)c->levels[q].dev.N;
-        if (c->use_cluster)
-            KLAUNCH("coarse_cluster", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
-                    launch_coarse_cluster(c->inner, c->cluster, L.r, L.e[0], c->Ainv, c->sst, s));
-        else
-            KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
-                    launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
+        KLAUNCH("coarse_cta", 2 * N * si + nco * nco * 8 + 2 * cells, 1,
+                launch_coarse_cta(c->inner, c->coarse, L.r, L.e[0], c->Ainv, c->sst, s));
         out_idx = 0;
-        return FVM_OK;
-    }
-    if (!g_rec && c->tail_ls > 0 && l == (size_t)c->tail_ls) {
-        // levels l.. of the V-cycle in one persistent kernel (their kernels' bytes, for profiling)
-        double bytes = 0.0;
-        for (size_t q = l; q < c->lc; ++q) {
-            const double n = (double)c->levels[q].dev.N, nc = (double)c->levels[q + 1].dev.N;
-            bytes += (2 * n * si + 2 * n) + (pre_at(c, q) - 1 + post_at(c, q)) * (3 * n * si + 2 * n) +
-                     2 * (2 * n * si + nc * si + 2 * n);
-        }
-        KLAUNCH("vtail", bytes, 1,
-                launch_tail(c->inner, c->tail, c->coarse, c->Ainv, c->sst, c->tail_blocks,
-                            coarse_cta_smem(c->coarse, c->inner), s));
-        out_idx = tail_out_index(pre_at(c, l), post_at(c, l));
         return FVM_OK;
     }
     DevLevel& Lc = c->levels[l + 1];
     const double Nc = (double)Lc.dev.N;
-    if (L.tma) {
-        // fused passes: down = sweeps + residual + restriction, up = prolongation + sweeps
-        const int reps = l == 0 ? c->rule_inner : 1;
-        int cur = 0;
-        for (int rep = 0; rep < reps; ++rep) {
-            int n = pre_at(c, l);
-            if (rep == 0) {
-                if (l > 0)
-                    KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
-                            launch_sweep_first(c->inner, L.dev, L.r, L.e[0], c->sst, s));
-                n -= 1;
-            }
-            KLAUNCH(lvl_name("down_tma", l), N * (3 * si + 2) + Nc * si, 1,
-                    launch_down_tma(n, L.maps, cur, L.dev, Lc.dev, L.e[cur ^ 1], Lc.r, c->sst, s));
-            cur ^= 1;
-            int ci = 0;
-            ST_TRY(cycle(c, l + 1, ci));
-            const bool top = l == 0 && rep == reps - 1 && !c->desc.krylov;
-            KLAUNCH(lvl_name(top ? "up_tma_to_p" : "up_tma", l), N * (3 * si + 2 + (top ? 16 : 0)) + Nc * si, 1,
-                    launch_up_tma(post_at(c, l), top, L.maps, cur, ci, L.dev, Lc.dev, L.e[cur ^ 1], c->p,
-                                  c->sst, s));
-            if (!top) cur ^= 1;
-        }
-        if (l == 0 && c->desc.krylov) ST_TRY(krylov_step(c, cur));
-        out_idx = cur;
-        return FVM_OK;
-    }
     // level 0: the residual kernel already did the first sweep from e = 0, and
     // runs inner_cycles V-cycles on the same r; the last sweep of the last one adds e to p
     const int reps = l == 0 ? c->rule_inner : 1;
@@ -1274,130 +1214,6 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         c->coarse.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
         for (int q = 0; q < c->coarse.nl; ++q) c->coarse.lv[q] = c->levels[lc + q].dev;
         CUDA_TRY(prepare_coarse_cta(pl.inner, coarse_cta_smem(c->coarse, pl.inner)));
-        // a thread-block cluster holds more levels in its distributed shared memory; take
-        // the largest set that fits 200 KB per CTA, with 16 CTAs (or 8) if the GPU can
-        // schedule such a cluster
-        const int D = L0.active[2] ? 2 : (L0.active[1] ? 1 : -1);
-        c->use_cluster = false;
-        // (opt-in: on the 1M-cell channel the cluster kernel is slower than the per-level
-        // kernels plus the single CTA it replaces)
-        if (D > 0 && getenv_flag("FVM_CLUSTER") == 1) {
-            for (int cs : {16, 8}) {
-                ClusterLevels cl;
-                memset(&cl, 0, sizeof(cl));
-                // levels from `lm_abs` on are small enough to be held whole by CTA 0
-                const size_t nlev = c->levels.size();
-                size_t lm_abs = nlev - 1;
-                {
-                    int64_t tail = (int64_t)pl.levels[nlev - 1].N();
-                    while (lm_abs > 1 && tail + (int64_t)pl.levels[lm_abs - 1].N() <= 4096) {
-                        --lm_abs;
-                        tail += (int64_t)pl.levels[lm_abs].N();
-                    }
-                }
-                auto ppc_of = [&](size_t l) {
-                    const int nD = pl.levels[l].n[D];
-                    return l >= lm_abs ? nD : (nD + cs - 1) / cs;
-                };
-                size_t best_lc = 0;
-                size_t elems = 0, codes = 0;
-                for (size_t l0 = nlev - 1; l0 >= 1; --l0) {
-                    size_t e = 0, f = 0;
-                    for (size_t l = l0; l < nlev; ++l) {
-                        const HostLevel& H = pl.levels[l];
-                        const int plane = (int)(H.N() / H.n[D]);
-                        e += (size_t)3 * ppc_of(l) * plane;
-                        f += (size_t)ppc_of(l) * plane;
-                    }
-                    const size_t bytes = e * (pl.inner == FVM_FP64 ? 8 : 4) + f * 2 + 16;
-                    if (bytes > 200 * 1024) break;
-                    best_lc = l0;
-                    elems = e;
-                    codes = f;
-                    if (l0 == 1) break;
-                }
-                if (best_lc == 0 || best_lc > lc) continue;   // no better than the single CTA
-                cl.nl = (int)(c->levels.size() - best_lc);
-                cl.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;
-                cl.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
-                cl.cs = cs;
-                cl.D = D;
-                cl.lm = (int)(lm_abs > best_lc ? lm_abs - best_lc : 0);
-                int eoff = 0, foff = 0;
-                for (int q = 0; q < cl.nl; ++q) {
-                    const HostLevel& H = pl.levels[best_lc + q];
-                    cl.nD[q] = H.n[D];
-                    cl.plane[q] = (int)(H.N() / H.n[D]);
-                    cl.ppc[q] = ppc_of(best_lc + q);
-                    cl.mP[q] = div_magic((uint32_t)cl.plane[q]);
-                    cl.mX[q] = div_magic((uint32_t)H.n[0]);
-                    cl.mC[q] = div_magic((uint32_t)cl.ppc[q]);
-                    cl.off[q] = eoff;
-                    cl.foff[q] = foff;
-                    eoff += 3 * cl.ppc[q] * cl.plane[q];
-                    foff += cl.ppc[q] * cl.plane[q];
-                    cl.lv[q] = c->levels[best_lc + q].dev;
-                }
-                const int cbytes = pl.inner == FVM_FP64 ? 8 : 4;
-                cl.fbyte0 = (eoff * cbytes + 15) / 16 * 16;
-                cl.fcount = foff;
-                (void)elems;
-                (void)codes;
-                int nclusters = 0;
-                if (prepare_coarse_cluster(pl.inner, cs, cluster_smem_bytes(cl, pl.inner), &nclusters) ==
-                        cudaSuccess &&
-                    nclusters >= 1) {
-                    c->cluster = cl;
-                    c->use_cluster = true;
-                    c->lc = best_lc;
-                    break;
-                }
-            }
-        }
-    }
-    // fused TMA kernels on the grid levels that qualify (FP32 inner, tile-divisible 3D); opt-in with
-    // FVM_TMA=1: on GB300 they measure slower than the one-sweep kernels (shared-memory issue bound)
-    if (pl.inner == FVM_FP32 && getenv_flag("FVM_TMA") == 1 && d.pre_sweeps <= 3 && d.post_sweeps <= 4 &&
-        d.coarse_sweeps == 0 &&
-        tma_prepare() == cudaSuccess) {
-        for (size_t l = 0; l < c->lc; ++l) {
-            DevLevel& D = c->levels[l];
-            DevLevel& Dc = c->levels[l + 1];
-            if (!tma_level_ok(D.dev, Dc.dev)) continue;
-            D.tma = tma_make_maps(D.maps, D.dev, Dc.dev, D.e, D.r, Dc.e);
-        }
-    }
-    // the small levels above the coarse ones in one persistent kernel per V-cycle (opt-in with
-    // FVM_TAIL=1: on GB300 a grid barrier costs about as much as the kernel boundary it replaces)
-    if (!c->use_cluster && getenv_flag("FVM_TAIL") == 1) {
-        size_t ls = 0;
-        for (size_t l = 1; l < c->lc; ++l)
-            if (c->levels[l].dev.N <= (1 << 18) && !c->levels[l].tma) {
-                ls = l;
-                break;
-            }
-        // at most one block per SM, and no more blocks than the first tail level has cells / 1024
-        int nb = ls ? tail_blocks(pl.inner, coarse_cta_smem(c->coarse, pl.inner)) : 0;
-        if (ls) nb = std::min<int64_t>(nb, std::max<int64_t>(1, c->levels[ls].dev.N / 1024));
-        if (ls && nb > 0) {
-            c->tail_ls = (int)ls;
-            c->tail_blocks = nb;
-            TailLevels& t = c->tail;
-            memset(&t, 0, sizeof(t));
-            t.ls = (int)ls;
-            t.lc = (int)c->lc;
-            t.nl = (int)c->levels.size();
-            t.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;
-            t.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
-            for (size_t l = 0; l < c->levels.size(); ++l) {
-                t.lv[l] = c->levels[l].dev;
-                t.e[l][0] = c->levels[l].e[0];
-                t.e[l][1] = c->levels[l].e[1];
-                t.r[l] = c->levels[l].r;
-                t.mx[l] = div_magic((uint32_t)c->levels[l].dev.n[0]);
-                t.my[l] = div_magic((uint32_t)c->levels[l].dev.n[1]);
-            }
-        }
     }
     // the paper's scheme applies the fine grid's stencil and diagonal on every level
     if (d.mg_variant == 1)
@@ -1894,9 +1710,6 @@ fvm_status batch_check(fvm_case* const* cases, int n) {
             if (cases[j] == c) return fail(FVM_ERR_INVALID, "a case appears twice in the batch");
         if (c->prec != cases[0]->prec || c->inner != cases[0]->inner)
             return fail(FVM_ERR_INVALID, "batched cases need the same precision");
-        if (c->use_cluster) return fail(FVM_ERR_INVALID, "batched cases need the single-CTA coarse levels");
-        for (const DevLevel& L : c->levels)
-            if (L.tma) return fail(FVM_ERR_INVALID, "batched cases need the one-sweep level kernels");
         if (c->prof) return fail(FVM_ERR_INVALID, "profiling is on for a batched case");
     }
     return FVM_OK;
@@ -1996,8 +1809,7 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     stats.rel_residual = c->h_sst->rel;
     stats.dt_last = c->h_dt[0];
     stats.sim_time = c->h_dt[2];
-    if (c->h_sst->tma_timeout) result = fail(FVM_ERR_CUDA, "a bounded device-side wait timed out");
-    else if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
+    if (c->h_sst->nonfinite) result = fail(FVM_ERR_DIVERGED, "non-finite pressure residual");
     else if (c->h_sst->notconv) {
         result = FVM_ERR_NOT_CONVERGED;
         g_err = "V-cycle cap reached above the tolerance";

@@ -259,68 +259,6 @@ def test_graph_and_launch_paths_agree_bitwise(prec):
         assert np.array_equal(f1[f], f2[f]), f
 
 
-def test_cluster_and_single_cta_coarse_paths_agree(monkeypatch):
-    """The coarse levels run either in one thread-block cluster (distributed
-    shared memory) or in one CTA; both match the oracle's V-cycles."""
-    spec = channel_box(fixed_vcycles=3)
-    o = OracleCase(spec).step(2)
-    for cluster in ("1", "0"):
-        monkeypatch.setenv("FVM_CLUSTER", cluster)
-        with binding.Case(spec) as c:
-            c.step(2)
-            got = c.read()
-        assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"FVM_CLUSTER={cluster}")
-
-
-@pytest.mark.parametrize("tma", ["1", "0"])
-def test_fused_tma_level_kernels_match_plain_kernels(monkeypatch, tma):
-    """The TMA-fed fused down / up passes (FP32) and the one-sweep-per-kernel
-    path give the same solve within FP32 rounding, both within 1e-4 of the
-    FP64 oracle after several steps."""
-    monkeypatch.setenv("FVM_TMA", tma)
-    spec = cases.heated_channel_3d(64, 32, 32, mg_levels=4, precision=cases.FP32,
-                                   boxes=[cases.Box(20, 28, 8, 20, 0, 12, thermal=cases.HEAT_FLUX, T_value=100.0)])
-    with binding.Case(spec) as c:
-        st = c.step(5)
-        got = c.read()
-    assert st["rel_residual"] <= 1e-8
-    o = OracleCase(spec.replace(precision=cases.FP64)).step(5)
-    assert_fields(got, o.fields(), 1e-4, STATE, f"FVM_TMA={tma}")
-
-
-def test_fused_tma_vcycle_matches_oracle_vcycle(monkeypatch):
-    """One V-cycle with the fused passes (FP32 correction, FP64 pressure)
-    against the oracle's V-cycle: p agrees to FP32 accuracy."""
-    monkeypatch.setenv("FVM_TMA", "1")
-    spec = cases.heated_channel_3d(64, 32, 32, mg_levels=4, precision=cases.FP32, fixed_vcycles=1)
-    o = OracleCase(spec.replace(precision=cases.FP64))
-    lev = o.mg.levels[0]
-    b = np.random.default_rng(5).normal(size=lev.shape)
-    p = np.zeros(lev.shape)
-    with binding.Case(spec) as c:
-        c.set_rhs(b)
-        c.write({"p": p})
-        for n in (1, 3):
-            c.vcycle(n)
-            for _ in range(n):
-                p = o.mg.vcycle(p, b)
-            assert rel_err(c.read(("p",))["p"], p) <= 2e-5
-
-
-@pytest.mark.parametrize("name", ["channel3d_box_vent", "room_buoyant", "channel2d_ragged"])
-def test_persistent_tail_kernel_matches_oracle(monkeypatch, name):
-    """The levels below the finest in one persistent kernel per V-cycle
-    (grid barriers between phases, the coarse levels in block 0): FP64
-    fields within 1e-10 of the oracle."""
-    monkeypatch.setenv("FVM_TAIL", "1")
-    spec = SPECS[name]()
-    with binding.Case(spec) as c:
-        c.step(2)
-        got = c.read()
-    o = OracleCase(spec).step(2)
-    assert_fields(got, o.fields(), TOL64, cases.FIELDS, f"{name} with the tail kernel")
-
-
 @pytest.mark.parametrize("name", ["channel3d_box_vent", "room_buoyant", "channel2d_ragged"])
 def test_paper_multigrid_scheme_matches_oracle(name):
     """mg_variant 1 (Algorithm 1: straight restriction, one unweighted Jacobi

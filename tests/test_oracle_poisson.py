@@ -71,26 +71,63 @@ def test_neumann_and_dirichlet_ghosts():
 
 
 def test_restrict_prolong_properties():
-    lev = Geometry(_spec(8, 8, 8)).level0
+    lev = Geometry(_spec(8, 8, 8, outlet_faces=())).level0
+    clev = lev.coarsen()                     # all faces zero-gradient
     c = np.random.default_rng(0).normal(size=(4, 4, 4))
     # RES is the mean of children: constant in, constant out; sums scale by 1/8
     r = np.random.default_rng(1).normal(size=(8, 8, 8))
     assert np.allclose(restrict(lev, np.full((8, 8, 8), 3.5)), 3.5)
     assert restrict(lev, r).sum() == pytest.approx(r.sum() / 8, rel=1e-13)
-    # PROL reproduces constants everywhere and linear functions away from the clamped edge
-    assert np.allclose(prolong(np.full((4, 4, 4), 2.0), (8, 8, 8)), 2.0)
+    # PROL reproduces constants everywhere (zero-gradient ghosts) and linear functions away
+    # from the domain faces
+    assert np.allclose(prolong(clev, np.full((4, 4, 4), 2.0), (8, 8, 8)), 2.0)
     xc = (np.arange(4) + 0.5) * 2.0
     xf = np.arange(8) + 0.5
     lin_c = xc[:, None, None] + 0 * c
-    lin_f = prolong(lin_c, (8, 8, 8))
+    lin_f = prolong(clev, lin_c, (8, 8, 8))
     assert np.allclose(lin_f[1:-1, :, :], xf[1:-1, None, None], atol=1e-13)
     # weights (27, 9, 9, 3, 9, 3, 3, 1)/64 around an interior fine cell
     imp = np.zeros((4, 4, 4))
     imp[1, 1, 1] = 64.0
-    pf = prolong(imp, (8, 8, 8))
+    pf = prolong(clev, imp, (8, 8, 8))
     assert pf[2, 2, 2] == pytest.approx(27) and pf[3, 3, 3] == pytest.approx(27)
     assert pf[1, 2, 2] == pytest.approx(9) and pf[1, 1, 2] == pytest.approx(3)
     assert pf[1, 1, 1] == pytest.approx(1) and pf[4, 4, 4] == pytest.approx(1)
+
+
+def test_prolong_takes_the_coarse_ghost_beyond_a_domain_face():
+    """Across a zero-value (outlet) face the neighbour is the negated cell: a
+    function linear in x that vanishes on that face is interpolated exactly up
+    to the face, and a constant falls to half its value in the fine cells
+    touching the face (the linear profile through 0 on the face).  Across a
+    zero-gradient face the neighbour is the cell itself."""
+    lev = Geometry(_spec(8, 8, 8, outlet_faces=(0,))).level0   # x- face zero-value
+    clev = lev.coarsen()
+    xc = (np.arange(4) + 0.5) * 2.0          # coarse centres (h = 1 on the fine grid), face at x = 0
+    xf = np.arange(8) + 0.5
+    lin_f = prolong(clev, xc[:, None, None] * np.ones((4, 4, 4)), (8, 8, 8))
+    assert np.allclose(lin_f[:-1], np.broadcast_to(xf[:-1, None, None], (7, 8, 8)), rtol=0, atol=1e-13)
+    # the x+ face is zero-gradient: the last fine cell takes 3/4 + 1/4 of the last coarse cell
+    assert np.allclose(lin_f[-1], xc[-1], rtol=0, atol=1e-13)
+    const = prolong(clev, np.full((4, 4, 4), 4.0), (8, 8, 8))
+    assert np.allclose(const[0], 2.0, rtol=0, atol=1e-14) and np.allclose(const[1:], 4.0, rtol=0, atol=1e-14)
+
+
+def test_prolong_corner_ghost_carries_both_face_signs():
+    """A fine cell in the corner of two zero-value faces: of its 8 (2D: 4)
+    interpolation points, the ghost across both faces is the cell with two
+    sign flips (+), the two single-face ghosts are negated."""
+    lev = Geometry(_spec(8, 8, 1, L=(1.0, 1.0, 0.125), outlet_faces=(0, 2))).level0   # x- and y- zero-value
+    clev = lev.coarsen()
+    c = np.zeros((4, 4, 1))
+    c[0, 0, 0] = 16.0
+    pf = prolong(clev, c, (8, 8, 1))
+    # fine (0, 0): 9/16 c + 3/16 (-c) [x ghost] + 3/16 (-c) [y ghost] + 1/16 (+c) [corner] = 4/16 c
+    assert pf[0, 0, 0] == pytest.approx(4.0, rel=1e-14)
+    # fine (1, 0): parent (0,0), x neighbour (1,0) = 0; y ghost row: -c and the ghost of (1, 0), 0
+    assert pf[1, 0, 0] == pytest.approx(16.0 * (9 - 3) / 16, rel=1e-14)
+    # fine (1, 1): no ghost involved
+    assert pf[1, 1, 0] == pytest.approx(9.0, rel=1e-14)
 
 
 @pytest.mark.parametrize("shape,boxes,levels", [
