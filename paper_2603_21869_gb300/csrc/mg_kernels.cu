@@ -477,46 +477,151 @@ __device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
     }
 }
 
-// Four consecutive x cells per thread, 128-bit (FP32) or 64-bit (BF16)
-// loads.  A warp covers 128 cells of a row and marches zc planes in z: rows
-// j +- 1 and the plane after next are loaded whole (indices clamped into the
-// grid, so a zero-gradient domain face reads the cell itself), the x
-// neighbours come from the adjacent lanes by shuffles (the warp's two end
-// cells from single loads), and the z neighbours rotate in registers.
-template <class TI> struct Vec4;
-template <> struct Vec4<float> {
+// W consecutive x cells per thread (the vector kernels): W = 4 with 128-bit
+// loads for FP32 levels, W = 8 with 128-bit loads for BF16 levels (W = 4,
+// 64-bit loads, where nx is not a multiple of 8).  A warp covers W * 32
+// cells of a row (or 2, 4, 8 rows of W * 16, W * 8, W * 4 cells: the widest
+// segment that divides nx) and marches zc planes in z: rows j +- 1 and the
+// plane after next are loaded whole (indices clamped into the grid, so a
+// zero-gradient domain face reads the cell itself), the x neighbours come
+// from the adjacent lanes by shuffles (the segment's two end cells from
+// single loads), and the z neighbours rotate in registers.
+__device__ __forceinline__ void bf2_unpack(uint32_t w, float& a, float& b) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    a = f.x;
+    b = f.y;
+}
+__device__ __forceinline__ uint32_t bf2_pack(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <class TI, int W> struct VecW;
+template <> struct VecW<float, 4> {
     static __device__ __forceinline__ void load(const float* p, int c, float (&o)[4]) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(p + c));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    static __device__ __forceinline__ void load_rw(const float* p, int c, float (&o)[4]) {
+        const float4 v = *reinterpret_cast<const float4*>(p + c);
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
     static __device__ __forceinline__ void store(float* p, int c, const float (&v)[4]) {
         *reinterpret_cast<float4*>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
     }
 };
-template <> struct Vec4<__nv_bfloat16> {
+template <> struct VecW<__nv_bfloat16, 4> {
     static __device__ __forceinline__ void load(const __nv_bfloat16* p, int c, float (&o)[4]) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p + c));
+        bf2_unpack(v.x, o[0], o[1]);
+        bf2_unpack(v.y, o[2], o[3]);
+    }
+    static __device__ __forceinline__ void load_rw(const __nv_bfloat16* p, int c, float (&o)[4]) {
         const uint2 v = *reinterpret_cast<const uint2*>(p + c);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
-        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        bf2_unpack(v.x, o[0], o[1]);
+        bf2_unpack(v.y, o[2], o[3]);
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, int c, const float (&v)[4]) {
-        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
-        uint2 w;
-        w.x = *reinterpret_cast<const uint32_t*>(&a);
-        w.y = *reinterpret_cast<const uint32_t*>(&b);
-        *reinterpret_cast<uint2*>(p + c) = w;
+        *reinterpret_cast<uint2*>(p + c) = make_uint2(bf2_pack(v[0], v[1]), bf2_pack(v[2], v[3]));
+    }
+};
+template <> struct VecW<__nv_bfloat16, 8> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, int c, float (&o)[8]) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + c));
+        bf2_unpack(v.x, o[0], o[1]);
+        bf2_unpack(v.y, o[2], o[3]);
+        bf2_unpack(v.z, o[4], o[5]);
+        bf2_unpack(v.w, o[6], o[7]);
+    }
+    static __device__ __forceinline__ void load_rw(const __nv_bfloat16* p, int c, float (&o)[8]) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p + c);
+        bf2_unpack(v.x, o[0], o[1]);
+        bf2_unpack(v.y, o[2], o[3]);
+        bf2_unpack(v.z, o[4], o[5]);
+        bf2_unpack(v.w, o[6], o[7]);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, int c, const float (&v)[8]) {
+        *reinterpret_cast<uint4*>(p + c) =
+            make_uint4(bf2_pack(v[0], v[1]), bf2_pack(v[2], v[3]), bf2_pack(v[4], v[5]), bf2_pack(v[6], v[7]));
+    }
+};
+// the four-cell loads of the other kernels
+template <class TI> using Vec4 = VecW<TI, 4>;
+
+// the W cells' 16-bit neighbour codes
+template <int W> __device__ __forceinline__ void codes_w(const uint16_t* f, int c, uint32_t (&o)[W]);
+template <> __device__ __forceinline__ void codes_w<4>(const uint16_t* f, int c, uint32_t (&o)[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(f + c));
+    o[0] = v.x & 0xffffu; o[1] = v.x >> 16; o[2] = v.y & 0xffffu; o[3] = v.y >> 16;
+}
+template <> __device__ __forceinline__ void codes_w<8>(const uint16_t* f, int c, uint32_t (&o)[8]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(f + c));
+    o[0] = v.x & 0xffffu; o[1] = v.x >> 16; o[2] = v.y & 0xffffu; o[3] = v.y >> 16;
+    o[4] = v.z & 0xffffu; o[5] = v.z >> 16; o[6] = v.w & 0xffffu; o[7] = v.w >> 16;
+}
+
+template <> __device__ __forceinline__ void codes_w<2>(const uint16_t* f, int c, uint32_t (&o)[2]) {
+    const uint32_t v = __ldg(reinterpret_cast<const unsigned int*>(f + c));
+    o[0] = v & 0xffffu; o[1] = v >> 16;
+}
+
+// cells per thread of the vector kernels on a level of this storage type
+template <class TI> __device__ __host__ constexpr int vec_w() { return sizeof(TI) == 2 ? 8 : 4; }
+
+// The register image of W cells as loaded (16 bytes for W = 4 FP32 and W = 8
+// BF16), converted to FP32 one value at a time where used: keeps the vector
+// kernels' rotating planes at 4 registers each.  A BF16 value is the high half
+// of its FP32 pattern, so the conversion is one shift or mask.
+template <class TI, int W> struct RawW;
+template <> struct RawW<float, 4> {
+    using T = float4;
+    static __device__ __forceinline__ T load(const float* p, int c) { return __ldg(reinterpret_cast<const float4*>(p + c)); }
+    static __device__ __forceinline__ float get(const T& v, int t) {
+        return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
+    }
+};
+template <> struct RawW<float, 2> {
+    using T = float2;
+    static __device__ __forceinline__ T load(const float* p, int c) { return __ldg(reinterpret_cast<const float2*>(p + c)); }
+    static __device__ __forceinline__ float get(const T& v, int t) { return t == 0 ? v.x : v.y; }
+};
+template <> struct RawW<__nv_bfloat16, 2> {
+    using T = uint32_t;
+    static __device__ __forceinline__ T load(const __nv_bfloat16* p, int c) {
+        return __ldg(reinterpret_cast<const unsigned int*>(p + c));
+    }
+    static __device__ __forceinline__ float get(const T& v, int t) {
+        return __uint_as_float((t & 1) ? (v & 0xffff0000u) : (v << 16));
+    }
+};
+template <> struct RawW<__nv_bfloat16, 4> {
+    using T = uint2;
+    static __device__ __forceinline__ T load(const __nv_bfloat16* p, int c) {
+        return __ldg(reinterpret_cast<const uint2*>(p + c));
+    }
+    static __device__ __forceinline__ float get(const T& v, int t) {
+        const uint32_t w = (t >> 1) == 0 ? v.x : v.y;
+        return __uint_as_float((t & 1) ? (w & 0xffff0000u) : (w << 16));
+    }
+};
+template <> struct RawW<__nv_bfloat16, 8> {
+    using T = uint4;
+    static __device__ __forceinline__ T load(const __nv_bfloat16* p, int c) {
+        return __ldg(reinterpret_cast<const uint4*>(p + c));
+    }
+    static __device__ __forceinline__ float get(const T& v, int t) {
+        const uint32_t w = (t >> 1) == 0 ? v.x : ((t >> 1) == 1 ? v.y : ((t >> 1) == 2 ? v.z : v.w));
+        return __uint_as_float((t & 1) ? (w & 0xffff0000u) : (w << 16));
     }
 };
 
-
-
-template <class TI, int MODE>
-struct SweepV4K {
+template <class TI, int MODE, int W>
+struct SweepVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
-    static constexpr int kMinBlocks = 4;   // at most 64 registers: four blocks per SM (batched too:
-                                           // the few spilled bytes cost less than a block per SM)
+    // W = 4: at most 64 registers, four blocks per SM (batched too: the few spilled bytes cost less
+    // than a block per SM); W = 8: at most 80, three blocks
+    static constexpr int kMinBlocks = W == 4 ? 4 : 3;
     LevelDev L;
     const TI* ein;
     const TI* r;
@@ -524,25 +629,25 @@ struct SweepV4K {
     double* p;
     const SolveState* st;
     int zc;    // planes per block
-    int lrl;   // log2 of the lanes per row segment (5: a warp per 128-cell segment; 4, 3, 2: a warp
-               // covers 2, 4 or 8 rows of 64, 32 or 16 cells, so narrow rows leave no lane idle)
+    int lrl;   // log2 of the lanes per row segment (5: a warp per W * 32-cell segment; 4, 3, 2: a warp
+               // covers 2, 4 or 8 rows, so narrow rows leave no lane idle)
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class TI, int MODE>
-__device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
+template <class TI, int MODE, int W>
+__device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
     using C = float;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
-    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
+    const int i4 = at.b.x * (W * LR) + lane * W, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const int sy = nx, sz = nx * ny;
-    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int ic = min(i4, nx - W), jc = min(j, ny - 1);
     const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
-    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
-    const bool last = i4 + 4 >= nx;   // the row's last cell is this thread's: its x+ ghost is itself
+    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + W, nx - 1) + sy * jc;
+    const bool last = i4 + W >= nx;   // the row's last cell is this thread's: its x+ ghost is itself
     const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
     const C dg = LP<C>::diag(L), wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
     // the functor's pointers in registers for the whole march
@@ -551,62 +656,59 @@ __device__ void SweepV4K<TI, MODE>::run(const BlockAt& at) const {
     TI* const eout = this->eout;
     double* const p = this->p;
     const uint16_t* const nbf = L.nbf;
-    C em[4], ec[4], ep[4];
-    Vec4<TI>::load(ein, max(k0 - 1, 0) * sz + own, em);
-    Vec4<TI>::load(ein, k0 * sz + own, ec);
-    Vec4<TI>::load(ein, min(k0 + 1, nz - 1) * sz + own, ep);
+    using R = RawW<TI, W>;
+    typename R::T em = R::load(ein, max(k0 - 1, 0) * sz + own);
+    typename R::T ec = R::load(ein, k0 * sz + own);
+    typename R::T ep = R::load(ein, min(k0 + 1, nz - 1) * sz + own);
     for (int k = k0; k < k1; ++k) {
         const int base = k * sz;
-        C ym[4], yp[4], rr[4], en[4];
-        Vec4<TI>::load(ein, base + om, ym);
-        Vec4<TI>::load(ein, base + op, yp);
-        Vec4<TI>::load(r, base + own, rr);
-        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
+        uint32_t fs[W];
+        const typename R::T ym = R::load(ein, base + om);
+        const typename R::T yp = R::load(ein, base + op);
+        const typename R::T rr = R::load(r, base + own);
+        codes_w<W>(nbf, base + own, fs);
         const C xls = lane == 0 ? to_c<C>(ldg(ein + base + xl)) : (C)0;
         const C xrs = lane == LR - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
-        Vec4<TI>::load(ein, min(k + 2, nz - 1) * sz + own, en);   // plane after next
-        C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
-        C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
+        const typename R::T en = R::load(ein, min(k + 2, nz - 1) * sz + own);   // plane after next
+        C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
+        C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
         if (lane == 0) left = xls;
         if (lane == LR - 1) right = xrs;
-        if (last) right = ec[3];
-        const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
-        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
-        C v[4];
+        if (last) right = R::get(ec, W - 1);
+        C v[W];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const C eP = xs[t + 1];
+        for (int t = 0; t < W; ++t) {
+            const C eP = R::get(ec, t);
+            const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
+            const C zm = R::get(em, t), zp = R::get(ep, t), ya = R::get(ym, t), yb = R::get(yp, t);
             C A;
             if (!((fs[t] >> 13) & 1u)) {
-                C s = (xs[t] + xs[t + 2]) * ihx;
-                s = fma(ym[t] + yp[t], ihy, s);
-                s = fma(em[t] + ep[t], ihz, s);
+                C s = (xm + xp) * ihx;
+                s = fma(ya + yb, ihy, s);
+                s = fma(zm + zp, ihz, s);
                 A = fma(dg, eP, -s);
             } else {
-                A = A7_general<C>(L, fs[t], eP, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t]);
+                A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, zm, zp);
             }
-            v[t] = is_solid(fs[t]) ? (C)0 : eP + wJ * (rr[t] - A) * iD;
+            v[t] = is_solid(fs[t]) ? (C)0 : eP + wJ * (R::get(rr, t) - A) * iD;
         }
         if (in) {
             if (MODE == 0) {
-                Vec4<TI>::store(eout, base + own, v);
+                VecW<TI, W>::store(eout, base + own, v);
             } else {
                 double2* pp = reinterpret_cast<double2*>(p + base + own);
-                double2 a = pp[0], b = pp[1];
-                if (!is_solid(fs[0])) a.x += (double)v[0];
-                if (!is_solid(fs[1])) a.y += (double)v[1];
-                if (!is_solid(fs[2])) b.x += (double)v[2];
-                if (!is_solid(fs[3])) b.y += (double)v[3];
-                pp[0] = a;
-                pp[1] = b;
+#pragma unroll
+                for (int h = 0; h < W / 2; ++h) {
+                    double2 a = pp[h];
+                    if (!is_solid(fs[2 * h])) a.x += (double)v[2 * h];
+                    if (!is_solid(fs[2 * h + 1])) a.y += (double)v[2 * h + 1];
+                    pp[h] = a;
+                }
             }
         }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            em[t] = ec[t];
-            ec[t] = ep[t];
-            ep[t] = en[t];
-        }
+        em = ec;
+        ec = ep;
+        ep = en;
     }
 }
 
@@ -769,7 +871,7 @@ struct Resid0V4K {
     double* partials;
     SolveState* st;
     int zc;    // planes per block
-    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
+    int lrl;   // log2 of the lanes per row segment (as in SweepVK)
     __device__ bool live() const { return st->active != 0; }
     __device__ int run(const BlockAt& at) const;
 };
@@ -874,11 +976,11 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
     return resid0_finish<kThreads>(partials, nblk, st, red);
 }
 
-// The flexible-CG inner products with four x cells per thread and a z march
+// The flexible-CG inner products with W x cells per thread and a z march
 // (the sweep's layout and neighbour scheme): products, the thread's and the
-// warp's sums in FP32, block and grid sums in FP64.  Needs nx % 4 = 0.
-template <class TI>
-struct FcgDotV4K {
+// warp's sums in FP32, block and grid sums in FP64.  Needs nx % W = 0.
+template <class TI, int W>
+struct FcgDotVK {
     static constexpr int kThreads = TX * TY;
     static constexpr int kMinBlocks = 3;       // at most 80 registers
     static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
@@ -889,87 +991,86 @@ struct FcgDotV4K {
     double* partials;
     SolveState* st;
     int zc;    // planes per block
-    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
+    int lrl;   // log2 of the lanes per row segment (as in SweepVK)
     __device__ bool live() const { return st->active != 0; }
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class TI>
-__device__ void FcgDotV4K<TI>::run(const BlockAt& at) const {
+template <class TI, int W>
+__device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
     using C = float;
+    using R = RawW<TI, W>;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
-    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
+    const int i4 = at.b.x * (W * LR) + lane * W, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
     const int sy = nx, sz = nx * ny;
-    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const int ic = min(i4, nx - W), jc = min(j, ny - 1);
     const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
-    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
-    const bool lastc = i4 + 4 >= nx;
+    const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + W, nx - 1) + sy * jc;
+    const bool lastc = i4 + W >= nx;
     const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
     const C dg = LP<C>::diag(L);
     const bool have = st->g_valid != 0;
     const TI* const zz = this->z;
     const uint16_t* const nbf = L.nbf;
-    C em[4], ec[4], ep[4];
-    Vec4<TI>::load(zz, max(k0 - 1, 0) * sz + own, em);
-    Vec4<TI>::load(zz, k0 * sz + own, ec);
-    Vec4<TI>::load(zz, min(k0 + 1, nz - 1) * sz + own, ep);
+    typename R::T em = R::load(zz, max(k0 - 1, 0) * sz + own);
+    typename R::T ec = R::load(zz, k0 * sz + own);
+    typename R::T ep = R::load(zz, min(k0 + 1, nz - 1) * sz + own);
     C a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     for (int k = k0; k < k1; ++k) {
         const int base = k * sz;
-        C ym[4], yp[4], rr[4], dd[4] = {0.f, 0.f, 0.f, 0.f}, en[4];
-        Vec4<TI>::load(zz, base + om, ym);
-        Vec4<TI>::load(zz, base + op, yp);
-        Vec4<TI>::load(r, base + own, rr);
-        if (have) Vec4<TI>::load(dp, base + own, dd);
-        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
+        const typename R::T ym = R::load(zz, base + om);
+        const typename R::T yp = R::load(zz, base + op);
+        const typename R::T rr = R::load(r, base + own);
+        typename R::T dd = {};
+        if (have) dd = R::load(dp, base + own);
+        uint32_t fs[W];
+        codes_w<W>(nbf, base + own, fs);
         const C xls = lane == 0 ? to_c<C>(ldg(zz + base + xl)) : (C)0;
         const C xrs = lane == LR - 1 ? to_c<C>(ldg(zz + base + xr)) : (C)0;
-        Vec4<TI>::load(zz, min(k + 2, nz - 1) * sz + own, en);
-        C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
-        C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
+        const typename R::T en = R::load(zz, min(k + 2, nz - 1) * sz + own);
+        C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
+        C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
         if (lane == 0) left = xls;
         if (lane == LR - 1) right = xrs;
-        if (lastc) right = ec[3];
-        const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
-        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+        if (lastc) right = R::get(ec, W - 1);
         if (in) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < W; ++t) {
                 if (is_solid(fs[t])) continue;
-                const C eP = xs[t + 1];
+                const C eP = R::get(ec, t);
+                const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
+                const C ya = R::get(ym, t), yb = R::get(yp, t), za = R::get(em, t), zb = R::get(ep, t);
                 C A;
                 if (!((fs[t] >> 13) & 1u)) {
-                    C q = (xs[t] + xs[t + 2]) * ihx;
-                    q = fma(ym[t] + yp[t], ihy, q);
-                    q = fma(em[t] + ep[t], ihz, q);
+                    C q = (xm + xp) * ihx;
+                    q = fma(ya + yb, ihy, q);
+                    q = fma(za + zb, ihz, q);
                     A = fma(dg, eP, -q);
                 } else {
-                    A = A7_general<C>(L, fs[t], eP, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t]);
+                    A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, za, zb);
                 }
+                const C d = R::get(dd, t), rv = R::get(rr, t);
                 a0 = fma(eP, A, a0);
-                a1 = fma(A, dd[t], a1);
-                a2 = fma(rr[t], eP, a2);
-                a3 = fma(rr[t], dd[t], a3);
+                a1 = fma(A, d, a1);
+                a2 = fma(rv, eP, a2);
+                a3 = fma(rv, d, a3);
             }
         }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            em[t] = ec[t];
-            ec[t] = ep[t];
-            ep[t] = en[t];
-        }
+        em = ec;
+        ec = ep;
+        ep = en;
     }
     float s[4] = {a0, a1, a2, a3};   // FP32 within a warp, FP64 from the warp sums on
     fcg_reduce<kThreads>(s, partials, st, have, at);
 }
 
-// d = z - beta d_prev, p += alpha d (fluid cells), d kept: four consecutive
-// cells per thread, one-dimensional grid.  Needs N % 4 = 0.
-template <class TI>
-struct FcgUpdV4K {
+// d = z - beta d_prev, p += alpha d (fluid cells), d kept: W consecutive
+// cells per thread, one-dimensional grid.  Needs N % W = 0.
+template <class TI, int W>
+struct FcgUpdVK {
     static constexpr int kThreads = 256;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
@@ -979,26 +1080,28 @@ struct FcgUpdV4K {
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }
     __device__ void run(const BlockAt& at) const {
-        const int c = 4 * (at.b.x * kThreads + threadIdx.x);
+        const int c = W * (at.b.x * kThreads + threadIdx.x);
         if (c >= L.N) return;
         const float alpha = (float)st->g_alpha, beta = (float)st->g_beta;
-        float zv[4], dv[4] = {0.f, 0.f, 0.f, 0.f};
-        Vec4<TI>::load(z, c, zv);
-        if (beta != 0.f) Vec4<TI>::load(dp, c, dv);
-        const uint2 fw = __ldg(reinterpret_cast<const uint2*>(L.nbf + c));
-        const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
-        float d[4];
+        float zv[W], dv[W];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) d[t] = fma(-beta, dv[t], zv[t]);
-        Vec4<TI>::store(dp, c, d);
+        for (int t = 0; t < W; ++t) dv[t] = 0.f;
+        VecW<TI, W>::load(z, c, zv);
+        if (beta != 0.f) VecW<TI, W>::load_rw(dp, c, dv);
+        uint32_t fs[W];
+        codes_w<W>(L.nbf, c, fs);
+        float d[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) d[t] = fma(-beta, dv[t], zv[t]);
+        VecW<TI, W>::store(dp, c, d);
         double2* pp = reinterpret_cast<double2*>(p + c);
-        double2 u = pp[0], v = pp[1];
-        if (!is_solid(fs[0])) u.x += (double)(alpha * d[0]);
-        if (!is_solid(fs[1])) u.y += (double)(alpha * d[1]);
-        if (!is_solid(fs[2])) v.x += (double)(alpha * d[2]);
-        if (!is_solid(fs[3])) v.y += (double)(alpha * d[3]);
-        pp[0] = u;
-        pp[1] = v;
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            double2 u = pp[h];
+            if (!is_solid(fs[2 * h])) u.x += (double)(alpha * d[2 * h]);
+            if (!is_solid(fs[2 * h + 1])) u.y += (double)(alpha * d[2 * h + 1]);
+            pp[h] = u;
+        }
     }
 };
 
@@ -1027,8 +1130,8 @@ template <> struct Vec2<__nv_bfloat16> {
     }
 };
 
-template <class TI>
-struct ProlongV4K {
+template <class TI, int W>
+struct ProlongVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = 4;
@@ -1037,7 +1140,7 @@ struct ProlongV4K {
     TI* e;
     const SolveState* st;
     int zc;    // planes per block
-    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
+    int lrl;   // log2 of the lanes per row segment (as in SweepVK)
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
@@ -1049,17 +1152,19 @@ __device__ __forceinline__ float ghost_signed(uint32_t code, bool gy, int sy, bo
     return neg ? -v : v;
 }
 
-template <class TI>
-__device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
+template <class TI, int W>
+__device__ void ProlongVK<TI, W>::run(const BlockAt& at) const {
     using C = float;
+    constexpr int H = W / 2;   // coarse cells under a thread's W fine cells
+    using RC = RawW<TI, H>;
     const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
     const int NX = Lc.n[0], NY = Lc.n[1], NZ = Lc.n[2];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
-    const int i4 = at.b.x * (4 * LR) + lane * 4, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
+    const int i4 = at.b.x * (W * LR) + lane * W, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
     const int k0 = at.b.z * zc, k1 = min(nz, k0 + zc);
     const bool in = i4 < nx && j < ny;
-    const bool last = i4 + 4 >= nx;   // the row's last coarse cell is this thread's: its x+ neighbour is a ghost
-    const int ic = min(i4, nx - 4), jc = min(j, ny - 1);
+    const bool last = i4 + W >= nx;   // the row's last coarse cell is this thread's: its x+ neighbour is a ghost
+    const int ic = min(i4, nx - W), jc = min(j, ny - 1);
     const bool first = ic == 0;       // and its first: the x- neighbour is a ghost
     const int I0 = ic >> 1;
     // the y neighbour of the parent row; beyond a domain face it is the ghost row (the parent
@@ -1078,57 +1183,65 @@ __device__ void ProlongV4K<TI>::run(const BlockAt& at) const {
         const bool outK = qk < 0 || qk >= NZ;
         const int Qk = outK ? Pk : qk, sK = qk < 0 ? 0 : 1;
         const C wz0 = zact ? (C)0.75 : (C)1, wz1 = zact ? (C)0.25 : (C)0;
-        C add[4] = {(C)0, (C)0, (C)0, (C)0};
+        C add[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) add[t] = (C)0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int jj = (q & 1) ? Qj : Pj, kk = (q & 2) ? Qk : Pk;
             const bool gy = (q & 1) && outJ, gz = (q & 2) && outK;
             const C w = ((q & 1) ? (C)0.25 : (C)0.75) * ((q & 2) ? wz1 : wz0);
             const int row = NX * (jj + NY * kk);
-            C c0, c1;
-            Vec2<TI>::load(ecp, row + I0, c0, c1);
+            const typename RC::T raw = RC::load(ecp, row + I0);
+            C cv[H];
+#pragma unroll
+            for (int h = 0; h < H; ++h) cv[h] = RC::get(raw, h);
             C lft = lane == 0 ? to_c<C>(ldg(ecp + row + max(I0 - 1, 0))) : (C)0;
-            C rgt = lane == LR - 1 ? to_c<C>(ldg(ecp + row + min(I0 + 2, NX - 1))) : (C)0;
-            uint32_t cw = 0u;   // the codes of coarse cells I0, I0 + 1 (only where a ghost is formed)
-            if (gy || gz || first || last) cw = __ldg(reinterpret_cast<const uint32_t*>(cnbf + row + I0));
+            C rgt = lane == LR - 1 ? to_c<C>(ldg(ecp + row + min(I0 + H, NX - 1))) : (C)0;
+            uint32_t cw[H];   // the codes of the coarse cells (only where a ghost is formed)
+#pragma unroll
+            for (int h = 0; h < H; ++h) cw[h] = 0u;
+            if (gy || gz || first || last) codes_w<H>(cnbf, row + I0, cw);
             if (gy || gz) {
-                c0 = ghost_signed(cw & 0xffffu, gy, sJ, gz, sK, c0);
-                c1 = ghost_signed(cw >> 16, gy, sJ, gz, sK, c1);
+#pragma unroll
+                for (int h = 0; h < H; ++h) cv[h] = ghost_signed(cw[h], gy, sJ, gz, sK, cv[h]);
                 if (lane == 0 && !first) lft = ghost_signed(__ldg(cnbf + row + I0 - 1), gy, sJ, gz, sK, lft);
-                if (lane == LR - 1 && !last) rgt = ghost_signed(__ldg(cnbf + row + I0 + 2), gy, sJ, gz, sK, rgt);
+                if (lane == LR - 1 && !last) rgt = ghost_signed(__ldg(cnbf + row + I0 + H), gy, sJ, gz, sK, rgt);
             }
-            C left = __shfl_up_sync(0xffffffffu, c1, 1, LR);
-            C right = __shfl_down_sync(0xffffffffu, c0, 1, LR);
+            C left = __shfl_up_sync(0xffffffffu, cv[H - 1], 1, LR);
+            C right = __shfl_down_sync(0xffffffffu, cv[0], 1, LR);
             if (lane == 0) left = lft;
             if (lane == LR - 1) right = rgt;
-            if (first) left = (cw & 3u) == 2u ? -c0 : c0;                 // x- ghost of coarse cell I0
-            if (last) right = ((cw >> 18) & 3u) == 2u ? -c1 : c1;         // x+ ghost of coarse cell I0 + 1
-            add[0] += w * ((C)0.75 * c0 + (C)0.25 * left);
-            add[1] += w * ((C)0.75 * c0 + (C)0.25 * c1);
-            add[2] += w * ((C)0.75 * c1 + (C)0.25 * c0);
-            add[3] += w * ((C)0.75 * c1 + (C)0.25 * right);
+            if (first) left = (cw[0] & 3u) == 2u ? -cv[0] : cv[0];                         // x- ghost of cell I0
+            if (last) right = ((cw[H - 1] >> 2) & 3u) == 2u ? -cv[H - 1] : cv[H - 1];      // x+ ghost of the last
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                const int h = t >> 1;
+                const C nb = (t & 1) ? (h == H - 1 ? right : cv[h + 1]) : (h == 0 ? left : cv[h - 1]);
+                add[t] += w * ((C)0.75 * cv[h] + (C)0.25 * nb);
+            }
         }
         if (in) {
             const int c = ic + nx * (jc + ny * k);
-            C v[4];
-            Vec4<TI>::load(ep, c, v);
-            const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + c));
-            const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+            C v[W];
+            uint32_t fs[W];
+            VecW<TI, W>::load_rw(ep, c, v);
+            codes_w<W>(nbf, c, fs);
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int t = 0; t < W; ++t)
                 if (!is_solid(fs[t])) v[t] += add[t];
-            Vec4<TI>::store(ep, c, v);
+            VecW<TI, W>::store(ep, c, v);
         }
     }
 }
 
-// Residual and restriction, four x cells per thread: a thread owns the fine
-// cells i4..i4+3 of rows 2J, 2J+1 and planes 2K, 2K+1 (2D: plane K) and
-// writes the two coarse cells I0 = i4/2, I0 + 1 (mean of their children's
-// r - A e, Eq. restriction).  Rows j +- 1 and planes k +- 1 are loaded whole,
-// x neighbours by shuffles.  Needs x and y active, nx % 4 = 0, ny even.
-template <class TI>
-struct RRV4K {
+// Residual and restriction, W x cells per thread: a thread owns the fine
+// cells i4..i4+W-1 of rows 2J, 2J+1 and planes 2K, 2K+1 (2D: plane K) and
+// writes the W/2 coarse cells I0 = i4/2 .. (mean of their children's r - A e,
+// Eq. restriction).  Rows j +- 1 and planes k +- 1 are loaded whole, x
+// neighbours by shuffles.  Needs x and y active, nx % W = 0, ny even.
+template <class TI, int W>
+struct RRVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = 3;
@@ -1137,23 +1250,25 @@ struct RRV4K {
     const TI* r;
     TI* rc;
     TI* ec0;   // the coarse level's first sweep, or null
-    int lrl;   // log2 of the lanes per row segment (as in SweepV4K)
+    int lrl;   // log2 of the lanes per row segment (as in SweepVK)
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class TI>
-__device__ void RRV4K<TI>::run(const BlockAt& at) const {
+template <class TI, int W>
+__device__ void RRVK<TI, W>::run(const BlockAt& at) const {
     using C = float;
+    using R = RawW<TI, W>;
+    constexpr int H = W / 2;
     const int nx = Lf.n[0], ny = Lf.n[1], nz = Lf.n[2];
     const int NX = Lc.n[0], NY = Lc.n[1];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
-    const int i4 = at.b.x * (4 * LR) + lane * 4, J = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub, K = at.b.z;
+    const int i4 = at.b.x * (W * LR) + lane * W, J = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub, K = at.b.z;
     const bool in = i4 < nx && J < NY;
-    const bool last = i4 + 4 >= nx;
+    const bool last = i4 + W >= nx;
     const int fz = Lf.active[2] ? 2 : 1;
-    const int ic = min(i4, nx - 4), Jc = min(J, NY - 1);
+    const int ic = min(i4, nx - W), Jc = min(J, NY - 1);
     const int ja = 2 * Jc, jb = ja + 1, jm = max(ja - 1, 0), jp = min(jb + 1, ny - 1);
     const int sy = nx, sz = nx * ny;
     const C ihx = LP<C>::ih2a(Lf, 0), ihy = LP<C>::ih2a(Lf, 1), ihz = LP<C>::ih2a(Lf, 2);
@@ -1162,66 +1277,54 @@ __device__ void RRV4K<TI>::run(const BlockAt& at) const {
     const TI* const rp = r;
     const uint16_t* const nbf = Lf.nbf;
     auto at_ = [&](int jj, int kk) { return ic + sy * jj + sz * kk; };
-    C s0 = (C)0, s1 = (C)0;   // sums of the coarse cells I0, I0 + 1
+    C s[H];   // sums of the coarse cells I0 .. I0 + H - 1
+#pragma unroll
+    for (int h = 0; h < H; ++h) s[h] = (C)0;
     for (int dz = 0; dz < fz; ++dz) {
         const int k = fz * K + dz;
         const int km = max(k - 1, 0), kp = min(k + 1, nz - 1);
-        C ra[4], rb[4], ym[4], ea[4], eb[4], yp[4], za[4], zb[4], wa[4], wb[4];
-        Vec4<TI>::load(ep, at_(jm, k), ym);
-        Vec4<TI>::load(ep, at_(ja, k), ea);
-        Vec4<TI>::load(ep, at_(jb, k), eb);
-        Vec4<TI>::load(ep, at_(jp, k), yp);
-        Vec4<TI>::load(ep, at_(ja, km), za);   // plane below, rows a and b
-        Vec4<TI>::load(ep, at_(jb, km), zb);
-        Vec4<TI>::load(ep, at_(ja, kp), wa);   // plane above
-        Vec4<TI>::load(ep, at_(jb, kp), wb);
-        Vec4<TI>::load(rp, at_(ja, k), ra);
-        Vec4<TI>::load(rp, at_(jb, k), rb);
-        const uint2 fa = __ldg(reinterpret_cast<const uint2*>(nbf + at_(ja, k)));
-        const uint2 fb = __ldg(reinterpret_cast<const uint2*>(nbf + at_(jb, k)));
-        const C la = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * ja + sz * k)) : (C)0;
-        const C lb = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * jb + sz * k)) : (C)0;
-        const C qa = lane == LR - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * ja + sz * k)) : (C)0;
-        const C qb = lane == LR - 1 ? to_c<C>(ldg(ep + min(ic + 4, nx - 1) + sy * jb + sz * k)) : (C)0;
 #pragma unroll
         for (int row = 0; row < 2; ++row) {
-            const C* ec = row ? eb : ea;
-            const C* rr = row ? rb : ra;
-            const C* yl = row ? ea : ym;   // row below
-            const C* yh = row ? yp : eb;   // row above
-            const C* zl = row ? zb : za;
-            const C* zh = row ? wb : wa;
-            const uint2 fw = row ? fb : fa;
-            C left = __shfl_up_sync(0xffffffffu, ec[3], 1, LR);
-            C right = __shfl_down_sync(0xffffffffu, ec[0], 1, LR);
-            if (lane == 0) left = row ? lb : la;
-            if (lane == LR - 1) right = row ? qb : qa;
-            if (last) right = ec[3];
-            const C xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
-            const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
+            const int jr = row ? jb : ja;
+            const typename R::T ec = R::load(ep, at_(jr, k));
+            const typename R::T yl = R::load(ep, at_(row ? ja : jm, k));   // row below
+            const typename R::T yh = R::load(ep, at_(row ? jp : jb, k));   // row above
+            const typename R::T zl = R::load(ep, at_(jr, km));
+            const typename R::T zh = R::load(ep, at_(jr, kp));
+            const typename R::T rr = R::load(rp, at_(jr, k));
+            uint32_t fs[W];
+            codes_w<W>(nbf, at_(jr, k), fs);
+            const C lx = lane == 0 ? to_c<C>(ldg(ep + max(ic - 1, 0) + sy * jr + sz * k)) : (C)0;
+            const C rx = lane == LR - 1 ? to_c<C>(ldg(ep + min(ic + W, nx - 1) + sy * jr + sz * k)) : (C)0;
+            C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
+            C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
+            if (lane == 0) left = lx;
+            if (lane == LR - 1) right = rx;
+            if (last) right = R::get(ec, W - 1);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < W; ++t) {
                 if (is_solid(fs[t])) continue;
-                const C eP = xs[t + 1];
+                const C eP = R::get(ec, t);
+                const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
+                const C ya = R::get(yl, t), yb = R::get(yh, t), za = R::get(zl, t), zb = R::get(zh, t);
                 C A;
                 if (!((fs[t] >> 13) & 1u)) {
-                    C sa = (xs[t] + xs[t + 2]) * ihx;
-                    sa = fma(yl[t] + yh[t], ihy, sa);
-                    sa = fma(zl[t] + zh[t], ihz, sa);
+                    C sa = (xm + xp) * ihx;
+                    sa = fma(ya + yb, ihy, sa);
+                    sa = fma(za + zb, ihz, sa);
                     A = fma(dg, eP, -sa);
                 } else {
-                    A = A7_general<C>(Lf, fs[t], eP, xs[t], xs[t + 2], yl[t], yh[t], zl[t], zh[t]);
+                    A = A7_general<C>(Lf, fs[t], eP, xm, xp, ya, yb, za, zb);
                 }
-                if (t < 2) s0 += rr[t] - A;
-                else s1 += rr[t] - A;
+                s[t >> 1] += R::get(rr, t) - A;
             }
         }
     }
     if (in) {
         const C inv = (C)1 / (C)(4 * fz);
         const int o = (ic >> 1) + NX * (Jc + NY * K);
-        store_restricted<TI, C>(Lc, rc, ec0, o, s0 * inv);
-        store_restricted<TI, C>(Lc, rc, ec0, o + 1, s1 * inv);
+#pragma unroll
+        for (int h = 0; h < H; ++h) store_restricted<TI, C>(Lc, rc, ec0, o + h, s[h] * inv);
     }
 }
 
@@ -1685,18 +1788,25 @@ int resid0_blocks(int nx, int ny, int nz) {
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + BZ - 1) / BZ);
 }
 
-// four-cell kernels: log2 of the lanes per row segment, the widest segment of 128, 64, 32 or
-// 16 cells that divides nx (a warp then covers 1, 2, 4 or 8 rows)
-static int v4_lrl(int nx) {
-    return nx % 128 == 0 ? 5 : (nx % 64 == 0 ? 4 : (nx % 32 == 0 ? 3 : (nx % 16 == 0 ? 2 : 5)));
+// vector kernels with W cells per thread: log2 of the lanes per row segment, the widest
+// segment of W * 32, W * 16, W * 8 or W * 4 cells that divides nx (a warp then covers 1, 2, 4
+// or 8 rows)
+static int vw_lrl(int nx, int W) {
+    for (int l = 5; l >= 2; --l)
+        if (nx % (W << l) == 0) return l;
+    return 5;
 }
+static int v4_lrl(int nx) { return vw_lrl(nx, 4); }
 
 int level0_blocks_max(int nx, int ny, int nz) {
-    // a four-cell pass with this nx's row segments, one plane a block
-    const int lrl = v4_lrl(nx), wx = 4 << lrl, wy = TY << (5 - lrl);
-    const int four = ((nx + wx - 1) / wx) * ((ny + wy - 1) / wy) * nz;
-    const int r0 = resid0_blocks(nx, ny, nz);
-    return four > r0 ? four : r0;
+    // a vector pass (four or eight cells per thread) with this nx's row segments, one plane a block
+    int most = resid0_blocks(nx, ny, nz);
+    for (int W : {4, 8}) {
+        const int lrl = vw_lrl(nx, W), wx = W << lrl, wy = TY << (5 - lrl);
+        const int n = ((nx + wx - 1) / wx) * ((ny + wy - 1) / wy) * nz;
+        most = n > most ? n : most;
+    }
+    return most;
 }
 
 size_t coarse_cta_smem(const CoarseLevels& cl, int inner) {
@@ -1722,13 +1832,14 @@ cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
 
 static int sweep_planes(int tiles, int nz, int fixed);
 
-// four-cell kernels: the block's x-y extent for the row segments of v4_lrl
-static dim3 v4_grid(const LevelDev& L, int lrl, int& zc) {
-    const int wx = 4 << lrl, wy = TY << (5 - lrl);
+// vector kernels: the block's x-y extent for W cells per thread and the row segments of lrl
+static dim3 vw_grid(const LevelDev& L, int W, int lrl, int& zc) {
+    const int wx = W << lrl, wy = TY << (5 - lrl);
     const int tiles = ((L.n[0] + wx - 1) / wx) * ((L.n[1] + wy - 1) / wy);
     zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
     return dim3((unsigned)((L.n[0] + wx - 1) / wx), (unsigned)((L.n[1] + wy - 1) / wy), (unsigned)((L.n[2] + zc - 1) / zc));
 }
+static dim3 v4_grid(const LevelDev& L, int lrl, int& zc) { return vw_grid(L, 4, lrl, zc); }
 
 cudaError_t launch_resid0(int inner, int bprec, const LevelDev& L, const double* p, const void* b, void* r, void* e,
                           double* partials, SolveState* st, cudaGraphConditionalHandle cond,
@@ -1786,10 +1897,17 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
     if constexpr (sizeof(TI) < 8) {
         // four cells per thread on large levels and in batches (their blocks add up over the cases)
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-            const int lrl = v4_lrl(L.n[0]);
+            constexpr int W = vec_w<TI>();
             int zc = 0;
-            const dim3 grid = v4_grid(L, lrl, zc);
-            return launch_k(SweepV4K<TI, MODE>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+            if (W == 8 && L.n[0] % 8 == 0) {
+                const int lrl = vw_lrl(L.n[0], 8);
+                const dim3 grid = vw_grid(L, 8, lrl, zc);
+                return launch_k(SweepVK<TI, MODE, vec_w<TI>()>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0,
+                                s);
+            }
+            const int lrl = vw_lrl(L.n[0], 4);
+            const dim3 grid = vw_grid(L, 4, lrl, zc);
+            return launch_k(SweepVK<TI, MODE, 4>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
         }
     }
     // four cells per thread on large grids and in batches (one launch for all cases of a level)
@@ -1822,14 +1940,18 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
                                   void* rc, void* ec0, const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
-        const int lrl = v4_lrl(Lf.n[0]), wx = 4 << lrl, wy = TY << (5 - lrl);
+        const int W = inner == FVM_BF16_MIXED && Lf.n[0] % 8 == 0 ? 8 : 4;
+        const int lrl = vw_lrl(Lf.n[0], W), wx = W << lrl, wy = TY << (5 - lrl);
         const dim3 grid((unsigned)((Lf.n[0] + wx - 1) / wx), (unsigned)((Lc.n[1] + wy - 1) / wy), (unsigned)Lc.n[2]);
         if (inner == FVM_FP32)
-            return launch_k(RRV4K<float>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, (float*)ec0, lrl, st},
+            return launch_k(RRVK<float, 4>{Lf, Lc, (const float*)e, (const float*)r, (float*)rc, (float*)ec0, lrl, st},
                             grid, dim3(TX, TY), 0, s);
-        return launch_k(RRV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)e, (const __nv_bfloat16*)r,
-                                             (__nv_bfloat16*)rc, (__nv_bfloat16*)ec0, lrl, st},
-                        grid, dim3(TX, TY), 0, s);
+        using B = __nv_bfloat16;
+        if (W == 8)
+            return launch_k(RRVK<B, 8>{Lf, Lc, (const B*)e, (const B*)r, (B*)rc, (B*)ec0, lrl, st}, grid, dim3(TX, TY),
+                            0, s);
+        return launch_k(RRVK<B, 4>{Lf, Lc, (const B*)e, (const B*)r, (B*)rc, (B*)ec0, lrl, st}, grid, dim3(TX, TY), 0,
+                        s);
     }
     if (Lf.active[0] && Lf.active[1]) {
         const int fz = Lf.active[2] ? 2 : 1;
@@ -1847,13 +1969,23 @@ cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc
                                const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
-        const int lrl = v4_lrl(Lf.n[0]);
         int zc = 0;
-        const dim3 grid = v4_grid(Lf, lrl, zc);
-        if (inner == FVM_FP32)
-            return launch_k(ProlongV4K<float>{Lf, Lc, (const float*)ec, (float*)e, st, zc, lrl}, grid, dim3(TX, TY), 0,
-                            s);
-        return launch_k(ProlongV4K<__nv_bfloat16>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc, lrl},
+        if (inner == FVM_FP32) {
+            const int lrl = vw_lrl(Lf.n[0], 4);
+            const dim3 grid = vw_grid(Lf, 4, lrl, zc);
+            return launch_k(ProlongVK<float, 4>{Lf, Lc, (const float*)ec, (float*)e, st, zc, lrl}, grid, dim3(TX, TY),
+                            0, s);
+        }
+        if (Lf.n[0] % 8 == 0) {
+            const int lrl = vw_lrl(Lf.n[0], 8);
+            const dim3 grid = vw_grid(Lf, 8, lrl, zc);
+            return launch_k(ProlongVK<__nv_bfloat16, 8>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc,
+                                                        lrl},
+                            grid, dim3(TX, TY), 0, s);
+        }
+        const int lrl = vw_lrl(Lf.n[0], 4);
+        const dim3 grid = vw_grid(Lf, 4, lrl, zc);
+        return launch_k(ProlongVK<__nv_bfloat16, 4>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc, lrl},
                         grid, dim3(TX, TY), 0, s);
     }
     DISPATCH_I(inner, err = launch_k(ProlongK<TI>{Lf, Lc, (const TI*)ec, (TI*)e, st}, grid3(Lf), kBlock3, 0, s));
@@ -1882,14 +2014,24 @@ static cudaError_t fcg_launch(const LevelDev& L, const TI* z, const TI* r, TI* d
                               SolveState* st, cudaStream_t s) {
     if constexpr (sizeof(TI) < 8) {
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
-            const int lrl = v4_lrl(L.n[0]);
-            int zc = 0;
-            const dim3 grid = v4_grid(L, lrl, zc);
             // (at most level0_blocks_max(n) blocks: partials has room)
-            cudaError_t err = launch_k(FcgDotV4K<TI>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+            int zc = 0;
+            if (vec_w<TI>() == 8 && L.n[0] % 8 == 0) {
+                constexpr int W = vec_w<TI>();
+                const int lrl = vw_lrl(L.n[0], W);
+                const dim3 grid = vw_grid(L, W, lrl, zc);
+                cudaError_t err =
+                    launch_k(FcgDotVK<TI, W>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+                if (err != cudaSuccess) return err;
+                const unsigned nb = (unsigned)((L.N / W + FcgUpdVK<TI, W>::kThreads - 1) / FcgUpdVK<TI, W>::kThreads);
+                return launch_k(FcgUpdVK<TI, W>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TI, W>::kThreads), 0, s);
+            }
+            const int lrl = vw_lrl(L.n[0], 4);
+            const dim3 grid = vw_grid(L, 4, lrl, zc);
+            cudaError_t err = launch_k(FcgDotVK<TI, 4>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
             if (err != cudaSuccess) return err;
-            const unsigned nb = (unsigned)((L.N / 4 + FcgUpdV4K<TI>::kThreads - 1) / FcgUpdV4K<TI>::kThreads);
-            return launch_k(FcgUpdV4K<TI>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdV4K<TI>::kThreads), 0, s);
+            const unsigned nb = (unsigned)((L.N / 4 + FcgUpdVK<TI, 4>::kThreads - 1) / FcgUpdVK<TI, 4>::kThreads);
+            return launch_k(FcgUpdVK<TI, 4>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TI, 4>::kThreads), 0, s);
         }
     }
     cudaError_t err = launch_k(FcgDotK<TI>{L, z, r, dp, partials, st}, grid3(L), kBlock3, 0, s);
