@@ -65,6 +65,9 @@ struct CaseDev {
     int32_t n_patches, n_boxes, pad;
     const uint8_t* tag;      // 0 fluid, b + 1 solid cell of box b
     const uint8_t* face_patch[6];
+    const uint16_t* nbf0;    // the level-0 neighbour codes (LevelDev::nbf): a fluid cell whose codes on the
+    uint32_t regular_mask;   // active axes (these bits) are all 0 has six fluid in-grid neighbours
+    int32_t pad2;
     CaseF f;
     PatchDev patch[FVM_MAX_PATCHES];
     BoxDev box[FVM_MAX_BOXES];
@@ -241,8 +244,9 @@ struct StatePtrs {
 cudaError_t launch_init_state(int prec, const CaseDev& cd, StatePtrs st, const double* base,
                               uint64_t seed, double eps, cudaStream_t s);
 cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_state, cudaStream_t s);
+// b_out not null: also the pressure right-hand side b = -div(u)/dt of the (unchanged) velocity
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
-                               const double* dt_state, void* nut_out, cudaStream_t s);
+                               const double* dt_state, void* nut_out, void* b_out, cudaStream_t s);
 cudaError_t launch_explicit(int prec, const CaseDev& cd, StatePtrs in, StatePtrs out,
                             const double* dt_state, const void* nut, StatePtrs base, double wb, double ws,
                             cudaStream_t s);

@@ -38,6 +38,12 @@ constexpr double kBetaI = 0.072;
 
 size_t elem_size(int prec) { return prec == FVM_FP64 ? 8 : (prec == FVM_FP32 ? 4 : 2); }
 
+// The stages of a step before the pressure solve (Section 2.6): the time step, the first
+// destruction half step, the explicit stage, and the second half step fused with the pressure
+// right-hand side (an internal stage: fvm_run_stage runs the two separately)
+constexpr int kStageDestructionRhs = 100;
+constexpr int kStepStages[4] = {FVM_STAGE_DT, FVM_STAGE_DESTRUCTION, FVM_STAGE_EXPLICIT, kStageDestructionRhs};
+
 struct HostLevel {
     int n[3];
     int active[3];
@@ -836,15 +842,26 @@ fvm_status stage(fvm_case* c, int st, int* cycles, double* rel) {
             KLAUNCH("dt", N * (5 * sz + 1), 2, launch_dt(c->prec, c->cd, ptrs(c->cur), c->dt_state, s));
             return FVM_OK;
         case FVM_STAGE_DESTRUCTION:
-            KLAUNCH("destruction", N * (8 * sz + 1), 1,
-                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, c->nut, s));
+            KLAUNCH("destruction", N * (8 * sz + 3), 1,
+                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, c->nut,
+                                       nullptr, s));
             std::swap(c->cur[4], c->nxt[4]);
             std::swap(c->cur[5], c->nxt[5]);
             c->nut_valid = true;
             return FVM_OK;
+        case kStageDestructionRhs:
+            // the second half step and the pressure right-hand side in one pass: both read the same
+            // velocity, which the destruction step leaves unchanged (no nu_t: the next stage is the solve)
+            KLAUNCH("destruction_rhs", N * (8 * sz + 3), 1,
+                    launch_destruction(c->prec, c->cd, ptrs(c->cur), c->nxt[4], c->nxt[5], c->dt_state, nullptr,
+                                       c->b, s));
+            std::swap(c->cur[4], c->nxt[4]);
+            std::swap(c->cur[5], c->nxt[5]);
+            c->nut_valid = false;
+            return FVM_OK;
         case FVM_STAGE_EXPLICIT: {
             // forward Euler, or the first stage of the Shu-Osher schemes: cur -> nxt
-            KLAUNCH("explicit", N * (13 * sz + 1), 1,
+            KLAUNCH("explicit", N * (13 * sz + 3), 1,
                     launch_explicit(c->prec, c->cd, ptrs(c->cur), ptrs(c->nxt), c->dt_state,
                                     c->nut_valid ? c->nut : nullptr, StatePtrs{}, 0.0, 0.0, s));
             c->nut_valid = false;
@@ -929,7 +946,7 @@ fvm_status capture_step(fvm_case* c, fvm_case::StepGraph& G) {
         return st;
     };
     fvm_status st = FVM_OK;
-    for (int k : {FVM_STAGE_DT, FVM_STAGE_DESTRUCTION, FVM_STAGE_EXPLICIT, FVM_STAGE_DESTRUCTION, FVM_STAGE_RHS})
+    for (int k : kStepStages)
         if ((st = stage(c, k, nullptr, nullptr)) != FVM_OK) return abort_capture(st);
     if (launch_solve_begin(c->sst, s) != cudaSuccess) return abort_capture(fail(FVM_ERR_CUDA, "capture solve_begin"));
     c->launches += 1;
@@ -1190,6 +1207,11 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         ST_TRY(dalloc(c, (void**)&nb, v.N * 2));
         CUDA_TRY(cudaMemcpyAsync(nb, H.nbf.data(), v.N * 2, cudaMemcpyHostToDevice, c->stream));
         v.nbf = nb;
+        if (l == 0) {
+            cd.nbf0 = nb;
+            cd.regular_mask = (H.active[0] ? 0x00fu : 0u) | (H.active[1] ? 0x0f0u : 0u) | (H.active[2] ? 0xf00u : 0u) |
+                              (1u << 12);
+        }
         ST_TRY(dalloc(c, &D.e[0], v.N * si));
         ST_TRY(dalloc(c, &D.e[1], v.N * si));
         ST_TRY(dalloc(c, &D.r, v.N * si));
@@ -1560,7 +1582,7 @@ fvm_status batch_capture(fvm_batch* B, fvm_batch::Graph& G) {
         const int64_t launches0 = c->launches;
         Recorder R;
         g_rec = &R;
-        for (int k : {FVM_STAGE_DT, FVM_STAGE_DESTRUCTION, FVM_STAGE_EXPLICIT, FVM_STAGE_DESTRUCTION, FVM_STAGE_RHS})
+        for (int k : kStepStages)
             if (st == FVM_OK) st = stage(c, k, nullptr, nullptr);
         if (st == FVM_OK) {
             R.site = "solve_begin";
@@ -1782,11 +1804,7 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
         }
         int cycles = 0;
         double rel = 0.0;
-        ST_TRY(stage(c, FVM_STAGE_DT, nullptr, nullptr));
-        ST_TRY(stage(c, FVM_STAGE_DESTRUCTION, nullptr, nullptr));
-        ST_TRY(stage(c, FVM_STAGE_EXPLICIT, nullptr, nullptr));
-        ST_TRY(stage(c, FVM_STAGE_DESTRUCTION, nullptr, nullptr));
-        ST_TRY(stage(c, FVM_STAGE_RHS, nullptr, nullptr));
+        for (int k : kStepStages) ST_TRY(stage(c, k, nullptr, nullptr));
         ST_TRY(stage(c, FVM_STAGE_SOLVE, &cycles, &rel));
         ST_TRY(stage(c, FVM_STAGE_PROJECT, nullptr, nullptr));
         ++c->steps;
@@ -1797,12 +1815,12 @@ fvm_status fvm_step(fvm_case* c, int nsteps, fvm_step_stats* out) {
     CUDA_TRY(cudaMemcpyAsync(c->h_dt, c->dt_state, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     stats.vcycles_total = c->h_sst->total_cycles;
-    // kernels run by the graphs: 8 step kernels per step (one more per later Runge-Kutta stage),
+    // kernels run by the graphs: 7 step kernels per step (one more per later Runge-Kutta stage),
     // one residual per outer iteration plus the last one of each step, and kpc kernels per outer
     // iteration (inner V-cycles of the if node)
     if (graph_steps) {
         const int64_t outer = (int64_t)stats.vcycles_total / std::max(1, c->rule_inner);
-        const int64_t step_kernels = 8 + (c->desc.rk_stages > 1 ? c->desc.rk_stages - 1 : 0);
+        const int64_t step_kernels = 7 + (c->desc.rk_stages > 1 ? c->desc.rk_stages - 1 : 0);
         c->launches += step_kernels * (int64_t)graph_steps + (int64_t)graph_steps + outer * (1 + c->kpc);
     }
     stats.vcycles_last = c->h_sst->cycles;

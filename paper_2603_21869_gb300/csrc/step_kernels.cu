@@ -116,6 +116,22 @@ __device__ __forceinline__ int neighbour(const CaseDev& cd, const StatePtrs& st,
     return FK_INTERIOR;
 }
 
+// A regular cell: fluid, with a fluid in-grid neighbour across every face of an active axis (all
+// level-0 face codes of those axes 0), so its neighbours need no ghost.  Its neighbours are read
+// by plain loads at coordinates clamped into the grid: for a regular cell the clamp never acts,
+// and whatever a code says, no load leaves the arrays.
+__device__ __forceinline__ bool regular_cell(const CaseDev& cd, int c) {
+    return (__ldg(cd.nbf0 + c) & cd.regular_mask) == 0u;
+}
+
+template <class S, class C>
+__device__ __forceinline__ St<C> regular_neighbour(const CaseDev& cd, const StatePtrs& st, int i, int j, int k, int axis,
+                                                   int side) {
+    int q[3] = {i, j, k};
+    q[axis] = min(max(q[axis] + side, 0), cd.n[axis] - 1);
+    return load_state<S, C>(st, q[0] + cd.n[0] * (q[1] + cd.n[1] * q[2]));
+}
+
 // a / b: the IEEE quotient in FP64 (the parity path); in FP32 the fast quotient
 // (__fdividef: within 2 ulp for |b| in [2^-126, 2^126], which every use below
 // keeps), its error far inside the FP32 fields' 1e-4 bound
@@ -247,6 +263,7 @@ struct DestructionK {
     S* om_out;
     const double* dt_state;
     S* nut_out;   // nu_t of the updated k, omega (read by the explicit stage), or null
+    S* b_out;     // the pressure right-hand side b = -div(u)/dt of the same velocity (Eq. pc_residual), or null
     __device__ void run(const BlockAt& at) const;
 };
 
@@ -260,10 +277,13 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
         k_out[c] = from_c<S, C>(P.k);
         om_out[c] = from_c<S, C>(P.om);
         if (nut_out) nut_out[c] = from_c<S, C>((C)0);
+        if (b_out) b_out[c] = from_c<S, C>((C)0);
         return;
     }
-    // cell gradients L_j * D_j * BC_j(phi) of u, v, w, k, omega
+    const bool reg = regular_cell(cd, c);
+    // cell gradients L_j * D_j * BC_j(phi) of u, v, w, k, omega, and the face-velocity divergence
     C gu[3][3], gk[3], gw[3];
+    C div = (C)0;
     for (int a = 0; a < 3; ++a) {
         if (!cd.active[a]) {
             gu[0][a] = gu[1][a] = gu[2][a] = (C)0;
@@ -271,21 +291,26 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
             continue;
         }
         St<C> L, R;
-        neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
-        neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        if (reg) {
+            L = regular_neighbour<S, C>(cd, in, i, j, k, a, -1);
+            R = regular_neighbour<S, C>(cd, in, i, j, k, a, +1);
+        } else {
+            neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
+            neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        }
         const C ih = prm<C>(cd.inv_h[a], cd.f.inv_h[a]);
         gu[0][a] = (C)0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
         gu[1][a] = (C)0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
         gu[2][a] = (C)0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
         gk[a] = (C)0.5 * ((R.k - P.k) * ih + (P.k - L.k) * ih);
         gw[a] = (C)0.5 * ((R.om - P.om) * ih + (P.om - L.om) * ih);
-    }
-    C Sm[3][3], Om[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            Sm[a][b] = (C)0.5 * (gu[a][b] + gu[b][a]);
-            Om[a][b] = (C)0.5 * (gu[a][b] - gu[b][a]);
+        if (b_out) {
+            const C ue = (C)0.5 * (vcomp(P, a) + vcomp(R, a));
+            const C uw = (C)0.5 * (vcomp(L, a) + vcomp(P, a));
+            div += (ue - uw) * ih;
         }
+    }
+    if (b_out) b_out[c] = from_c<S, C>(-div / dt_of<C>(dt_state, 0));
     const C nu = prm<C>(cd.nu, cd.f.nu);
     const C oms = omega_safe(P.om);
     // k: chi_k, f_beta*, beta* (Eqs. k_des, beta_star)
@@ -308,11 +333,16 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     }
     const C dt = dt_of<C>(dt_state, 1);
     const C knew = qdiv(P.k, (C)1 + dt * bstar * fbs * P.om);
-    // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des)
-    C tr = (C)0;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            for (int e = 0; e < 3; ++e) tr += Om[a][b] * Om[b][e] * Sm[e][a];
+    // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des).  With
+    // the rotation vector w (Omega v = w x v), Omega Omega = w w^T - |w|^2 I, so the trace is
+    // w^T S w - |w|^2 tr(S)
+    const C w1 = (C)0.5 * (gu[2][1] - gu[1][2]), w2 = (C)0.5 * (gu[0][2] - gu[2][0]);
+    const C w3 = (C)0.5 * (gu[1][0] - gu[0][1]);
+    const C s01 = (C)0.5 * (gu[0][1] + gu[1][0]), s02 = (C)0.5 * (gu[0][2] + gu[2][0]);
+    const C s12 = (C)0.5 * (gu[1][2] + gu[2][1]);
+    const C wsw = w1 * w1 * gu[0][0] + w2 * w2 * gu[1][1] + w3 * w3 * gu[2][2] +
+                  (C)2 * (w1 * w2 * s01 + w1 * w3 * s02 + w2 * w3 * s12);
+    const C tr = wsw - (w1 * w1 + w2 * w2 + w3 * w3) * (gu[0][0] + gu[1][1] + gu[2][2]);
     const C bo = (C)kBetaStarInf * oms;
     const C chiw = fabs(tr / (bo * bo * bo));
     const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : qdiv((C)1 + (C)70 * chiw, (C)1 + (C)80 * chiw);
@@ -391,6 +421,7 @@ __device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
     const S* const nutf = nut;
     const C nutP = nutf ? to_c<C>(ldg(nutf + c)) : nut_of(P.k, P.om, nu);
     const int stride[3] = {1, cd.n[0], cd.n[0] * cd.n[1]};
+    const bool reg = regular_cell(cd, c);
     C rhs[6] = {(C)0, (C)0, (C)0, (C)0, (C)0, (C)0};
     C gu[3][3];
     C omw = (C)0;
@@ -400,11 +431,20 @@ __device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
             continue;
         }
         St<C> L, R;
-        const int kl = neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
-        const int kr = neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        int kl = FK_INTERIOR, kr = FK_INTERIOR;
+        if (reg) {
+            L = regular_neighbour<S, C>(cd, in, i, j, k, a, -1);
+            R = regular_neighbour<S, C>(cd, in, i, j, k, a, +1);
+        } else {
+            kl = neighbour<S, C>(cd, in, i, j, k, a, -1, P, L);
+            kr = neighbour<S, C>(cd, in, i, j, k, a, +1, P, R);
+        }
         C fw[6], fe[6];
+        // (an interior face's neighbour index, its coordinate clamped into the grid like every load)
+        const int q = a == 0 ? i : (a == 1 ? j : k);
+        const int cm = c - (q > 0 ? stride[a] : 0), cp = c + (q < cd.n[a] - 1 ? stride[a] : 0);
         auto nb_nut = [&](int side, const St<C>& g) {
-            return [&, side]() { return nutf ? to_c<C>(ldg(nutf + c + side * stride[a])) : nut_of(g.k, g.om, nu); };
+            return [&, side]() { return nutf ? to_c<C>(ldg(nutf + (side < 0 ? cm : cp))) : nut_of(g.k, g.om, nu); };
         };
         face_flux(cd, a, L, P, face_nut<C>(kl, nutP, nb_nut(-1, L)), fw);
         face_flux(cd, a, P, R, face_nut<C>(kr, nutP, nb_nut(+1, R)), fe);
@@ -821,10 +861,10 @@ cudaError_t launch_dt(int prec, const CaseDev& cd, StatePtrs st, double* dt_stat
 }
 
 cudaError_t launch_destruction(int prec, const CaseDev& cd, StatePtrs in, void* k_out, void* om_out,
-                               const double* dt_state, void* nut_out, cudaStream_t s) {
+                               const double* dt_state, void* nut_out, void* b_out, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    DISPATCH(prec, err = launch_k(DestructionK<S, C>{cd, in, (S*)k_out, (S*)om_out, dt_state, (S*)nut_out}, grid3(cd),
-                                  kBlock3, 0, s));
+    DISPATCH(prec, err = launch_k(DestructionK<S, C>{cd, in, (S*)k_out, (S*)om_out, dt_state, (S*)nut_out, (S*)b_out},
+                                  grid3(cd), kBlock3, 0, s));
     return err;
 }
 
