@@ -619,9 +619,10 @@ template <class TI, int MODE, int W>
 struct SweepVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
-    // the software-pipelined march holds two planes' loads: W = 4 at most 80 registers (three
-    // blocks per SM), W = 8 at most 128 (two blocks)
-    static constexpr int kMinBlocks = W == 4 ? 3 : 2;
+    // W = 4: at most 64 registers, four blocks per SM (batched too: the few spilled bytes cost less
+    // than a block per SM); W = 8: at most 80, three blocks.  (Issuing the next plane's loads before
+    // the current plane's arithmetic, at 80 / 128 registers, measured slower on the room.)
+    static constexpr int kMinBlocks = W == 4 ? 4 : 3;
     LevelDev L;
     const TI* ein;
     const TI* r;
@@ -635,30 +636,9 @@ struct SweepVK {
     __device__ void run(const BlockAt& at) const;
 };
 
-// the W cells' 16-bit neighbour codes as loaded (one 8- or 16-byte load)
-template <int W> struct RawCodes;
-template <> struct RawCodes<4> {
-    using T = uint2;
-    static __device__ __forceinline__ T load(const uint16_t* f, int c) { return __ldg(reinterpret_cast<const uint2*>(f + c)); }
-    static __device__ __forceinline__ uint32_t get(const T& v, int t) {
-        const uint32_t w = (t >> 1) == 0 ? v.x : v.y;
-        return (t & 1) ? (w >> 16) : (w & 0xffffu);
-    }
-};
-template <> struct RawCodes<8> {
-    using T = uint4;
-    static __device__ __forceinline__ T load(const uint16_t* f, int c) { return __ldg(reinterpret_cast<const uint4*>(f + c)); }
-    static __device__ __forceinline__ uint32_t get(const T& v, int t) {
-        const uint32_t w = (t >> 1) == 0 ? v.x : ((t >> 1) == 1 ? v.y : ((t >> 1) == 2 ? v.z : v.w));
-        return (t & 1) ? (w >> 16) : (w & 0xffffu);
-    }
-};
-
 template <class TI, int MODE, int W>
 __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
     using C = float;
-    using R = RawW<TI, W>;
-    using F = RawCodes<W>;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
     const int i4 = at.b.x * (W * LR) + lane * W, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
@@ -669,7 +649,6 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
     const int own = ic + sy * jc, om = ic + sy * max(jc - 1, 0), op = ic + sy * min(jc + 1, ny - 1);
     const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + W, nx - 1) + sy * jc;
     const bool last = i4 + W >= nx;   // the row's last cell is this thread's: its x+ ghost is itself
-    const bool lo_lane = lane == 0, hi_lane = lane == LR - 1;
     const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
     const C dg = LP<C>::diag(L), wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
     // the functor's pointers in registers for the whole march
@@ -678,49 +657,41 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
     TI* const eout = this->eout;
     double* const p = this->p;
     const uint16_t* const nbf = L.nbf;
-    // software pipeline: the loads of plane k + 1 (rows j +- 1, r, codes, the x end cells) are
-    // issued before plane k is computed, the plane after next two planes ahead
+    using R = RawW<TI, W>;
     typename R::T em = R::load(ein, max(k0 - 1, 0) * sz + own);
     typename R::T ec = R::load(ein, k0 * sz + own);
     typename R::T ep = R::load(ein, min(k0 + 1, nz - 1) * sz + own);
-    typename R::T ym = R::load(ein, k0 * sz + om);
-    typename R::T yp = R::load(ein, k0 * sz + op);
-    typename R::T rr = R::load(r, k0 * sz + own);
-    typename F::T fw = F::load(nbf, k0 * sz + own);
-    C xls = lo_lane ? to_c<C>(ldg(ein + k0 * sz + xl)) : (C)0;
-    C xrs = hi_lane ? to_c<C>(ldg(ein + k0 * sz + xr)) : (C)0;
     for (int k = k0; k < k1; ++k) {
         const int base = k * sz;
-        const int nb = min(k + 1, nz - 1) * sz;   // next plane (clamped: the last iteration's loads are unused)
-        const typename R::T ym_n = R::load(ein, nb + om);
-        const typename R::T yp_n = R::load(ein, nb + op);
-        const typename R::T rr_n = R::load(r, nb + own);
-        const typename F::T fw_n = F::load(nbf, nb + own);
-        const C xls_n = lo_lane ? to_c<C>(ldg(ein + nb + xl)) : (C)0;
-        const C xrs_n = hi_lane ? to_c<C>(ldg(ein + nb + xr)) : (C)0;
+        uint32_t fs[W];
+        const typename R::T ym = R::load(ein, base + om);
+        const typename R::T yp = R::load(ein, base + op);
+        const typename R::T rr = R::load(r, base + own);
+        codes_w<W>(nbf, base + own, fs);
+        const C xls = lane == 0 ? to_c<C>(ldg(ein + base + xl)) : (C)0;
+        const C xrs = lane == LR - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
         const typename R::T en = R::load(ein, min(k + 2, nz - 1) * sz + own);   // plane after next
         C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
         C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
-        if (lo_lane) left = xls;
-        if (hi_lane) right = xrs;
+        if (lane == 0) left = xls;
+        if (lane == LR - 1) right = xrs;
         if (last) right = R::get(ec, W - 1);
         C v[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) {
-            const uint32_t f = F::get(fw, t);
             const C eP = R::get(ec, t);
             const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
             const C zm = R::get(em, t), zp = R::get(ep, t), ya = R::get(ym, t), yb = R::get(yp, t);
             C A;
-            if (!((f >> 13) & 1u)) {
+            if (!((fs[t] >> 13) & 1u)) {
                 C s = (xm + xp) * ihx;
                 s = fma(ya + yb, ihy, s);
                 s = fma(zm + zp, ihz, s);
                 A = fma(dg, eP, -s);
             } else {
-                A = A7_general<C>(L, f, eP, xm, xp, ya, yb, zm, zp);
+                A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, zm, zp);
             }
-            v[t] = is_solid(f) ? (C)0 : eP + wJ * (R::get(rr, t) - A) * iD;
+            v[t] = is_solid(fs[t]) ? (C)0 : eP + wJ * (R::get(rr, t) - A) * iD;
         }
         if (in) {
             if (MODE == 0) {
@@ -730,8 +701,8 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
 #pragma unroll
                 for (int h = 0; h < W / 2; ++h) {
                     double2 a = pp[h];
-                    if (!is_solid(F::get(fw, 2 * h))) a.x += (double)v[2 * h];
-                    if (!is_solid(F::get(fw, 2 * h + 1))) a.y += (double)v[2 * h + 1];
+                    if (!is_solid(fs[2 * h])) a.x += (double)v[2 * h];
+                    if (!is_solid(fs[2 * h + 1])) a.y += (double)v[2 * h + 1];
                     pp[h] = a;
                 }
             }
@@ -739,12 +710,6 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
         em = ec;
         ec = ep;
         ep = en;
-        ym = ym_n;
-        yp = yp_n;
-        rr = rr_n;
-        fw = fw_n;
-        xls = xls_n;
-        xrs = xrs_n;
     }
 }
 
