@@ -493,6 +493,46 @@ fvm_status fvm_poisson_residual_static(const double* p, const double* b, int32_t
                                        const double h[3], const int32_t dirichlet[6], double* r,
                                        double* norms, void* stream);
 
+/* Vector-Jacobian product of one destruction half step (the k and omega
+   updates of Section 2.5, Eqs. k_des_step and o_des_step, Algorithm 4) over
+   dt, linearised at the case's current u, v, w, k, omega.  The step maps
+   (u, v, w, k, omega) to (u, v, w, k', omega'); host_ybar holds cotangents of
+   its output (u, v, w, k', omega': 5 nx*ny*nz doubles, field-major, x
+   fastest) and host_xbar receives the cotangents of its input (same layout).
+   The partial derivatives of the pointwise formulas (beta*, f_beta*, chi_k,
+   chi_omega, f_beta) are written out and sent back through the transposed
+   cell-gradient stencils with the Section 2.7 ghosts.  FP64 cases only; the
+   case is not changed.  n = capacity of each buffer in doubles (>= 5 N).
+   Synchronises.  FVM_ERR_INVALID for null pointers, dt <= 0, short buffers
+   or a reduced-precision case. */
+fvm_status fvm_destruction_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n);
+
+/* Vector-Jacobian product of the forward-Euler explicit stage (Algorithms 2
+   and 3, Section A.4: upwind convection, central diffusion, the -(2/3) k
+   face term, production G_k, G_omega and buoyancy) over dt, linearised at
+   the case's current u, v, w, T, k, omega.  host_ybar: cotangents of the
+   stage's output (u, v, w, T, k, omega: 6 N doubles); host_xbar: cotangents
+   of its input (6 N).  Clamped k, omega and the wall omega pass no
+   derivative, and at u_face = 0 the upwind side is the lower cell, as in
+   the forward.  FP64, forward-Euler cases only (rk_stages 0 or 1); the case
+   is not changed.  n >= 6 N.  Synchronises.  FVM_ERR_INVALID as above. */
+fvm_status fvm_explicit_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n);
+
+/* Vector-Jacobian product of one whole time step (Section 2.6) with a fixed
+   dt and the pressure solve taken as exact: the first destruction half step,
+   the explicit stage, the second half step, the right-hand side, the solve
+   and the projection, composed in reverse.  host_ybar: cotangents of the
+   step's output u, v, w, p, T, k, omega (7 N doubles, in field id order);
+   host_xbar: cotangents of the step's input u, v, w, T, k, omega (6 N).  The
+   adjoint pressure solve runs the case's V-cycles to rel_tol (as
+   fvm_projection_vjp); *rel_out (may be NULL) gets its final relative
+   residual.  FP64, forward-Euler cases only; the case's fields, p and b are
+   not changed.  n >= 7 N.  Synchronises.  FVM_ERR_NOT_CONVERGED if rel_tol
+   was not reached (xbar is still written); FVM_ERR_INVALID as above or for
+   rel_tol <= 0, max_vcycles < 1. */
+fvm_status fvm_step_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
+                        double rel_tol, int32_t max_vcycles, double* rel_out);
+
 /* sizeof of the public structs, for binding checks: out[0..10] = fvm_patch,
    fvm_vent, fvm_box, fvm_case_desc, fvm_step_stats, fvm_case_info,
    fvm_kernel_stat, fvm_batch_info, fvm_request_result, fvm_server_info,

@@ -110,7 +110,8 @@ class BatchInfo(ct.Structure):
 
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
            "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
-           "fvm_projection_vjp", "fvm_step_batch", "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
+           "fvm_projection_vjp", "fvm_destruction_vjp", "fvm_explicit_vjp", "fvm_step_vjp", "fvm_step_batch",
+           "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
            "fvm_profile_read", "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static",
            "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
            "fvm_batch_destroy", "fvm_batch_profile", "fvm_server_create", "fvm_server_now", "fvm_server_submit",
@@ -144,6 +145,11 @@ def lib():
     L.fvm_lambda2.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_projection_vjp.argtypes = [CP, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_size_t,
                                      ct.c_double, ct.c_int32, ct.POINTER(ct.c_double)]
+    L.fvm_destruction_vjp.argtypes = [CP, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                      ct.c_size_t]
+    L.fvm_explicit_vjp.argtypes = [CP, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_step_vjp.argtypes = [CP, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_size_t,
+                               ct.c_double, ct.c_int32, ct.POINTER(ct.c_double)]
     L.fvm_step_batch.argtypes = [ct.POINTER(CP), ct.c_int, ct.c_int, ct.POINTER(StepStats)]
     L.fvm_case_get_info.argtypes = [CP, ct.POINTER(CaseInfo)]
     L.fvm_set_option.argtypes = [CP, ct.c_int, ct.c_int64]
@@ -177,7 +183,8 @@ def lib():
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
                  "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
-                 "fvm_projection_vjp", "fvm_step_batch",
+                 "fvm_projection_vjp", "fvm_destruction_vjp", "fvm_explicit_vjp", "fvm_step_vjp",
+                 "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
                  "fvm_batch_create", "fvm_batch_step", "fvm_batch_launch", "fvm_batch_wait", "fvm_batch_get_info",
                  "fvm_batch_profile",
@@ -377,6 +384,46 @@ class Case:
         _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         xs = tuple(out[i * self.N:(i + 1) * self.N].reshape(nz, ny, nx).transpose(2, 1, 0) for i in range(3))
         return xs, rel.value
+
+    def _fields_in(self, arrays):
+        return np.ascontiguousarray(np.concatenate(
+            [np.asarray(a, dtype=np.float64).transpose(2, 1, 0).ravel() for a in arrays]))
+
+    def _fields_out(self, buf, n):
+        nx, ny, nz = self.shape
+        return tuple(buf[i * self.N:(i + 1) * self.N].reshape(nz, ny, nx).transpose(2, 1, 0) for i in range(n))
+
+    def destruction_vjp(self, dt, ubar, vbar, wbar, kbar, ombar):
+        """Cotangents of (u, v, w, k, omega) before one destruction step over dt from
+        cotangents of its output (fvm_destruction_vjp), at the current state."""
+        buf = self._fields_in([ubar, vbar, wbar, kbar, ombar])
+        out = np.empty(5 * self.N, dtype=np.float64)
+        _check(lib().fvm_destruction_vjp(self._h, dt, buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                         out.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        return self._fields_out(out, 5)
+
+    def explicit_vjp(self, dt, *ybar):
+        """Cotangents of (u, v, w, T, k, omega) before the forward-Euler explicit stage over dt
+        from cotangents of its output (fvm_explicit_vjp), at the current state."""
+        buf = self._fields_in(ybar)
+        out = np.empty(6 * self.N, dtype=np.float64)
+        _check(lib().fvm_explicit_vjp(self._h, dt, buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                      out.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        return self._fields_out(out, 6)
+
+    def step_vjp(self, dt, ubar, vbar, wbar, pbar, Tbar, kbar, ombar, rel_tol=1e-13, max_vcycles=400,
+                 allow_not_converged=False):
+        """Cotangents of (u, v, w, T, k, omega) at the start of one time step over dt from
+        cotangents of its output (fvm_step_vjp).  Returns (six arrays, relative residual of the
+        adjoint pressure solve)."""
+        buf = self._fields_in([ubar, vbar, wbar, pbar, Tbar, kbar, ombar])
+        out = np.empty(6 * self.N, dtype=np.float64)
+        rel = ct.c_double()
+        status = lib().fvm_step_vjp(self._h, dt, buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                    out.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size, rel_tol, max_vcycles,
+                                    ct.byref(rel))
+        _check(status, allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return self._fields_out(out, 6), rel.value
 
     def set_graph(self, enable=True):
         _check(lib().fvm_set_option(self._h, OPT_GRAPH, 1 if enable else 0))

@@ -259,6 +259,13 @@ cudaError_t launch_adj_grad(const CaseDev& cd, const LevelDev& L0, const double*
                             cudaStream_t s);
 cudaError_t launch_adj_rhs(const CaseDev& cd, const LevelDev& L0, const double* ybar, const double* lambda,
                            double* xbar, double dt, cudaStream_t s);
+// adjoints of the destruction half step (ybar, out: u, v, w, k, omega, 5 N; scratch 17 N) and of the
+// forward-Euler explicit stage (ybar, xbar: u, v, w, T, k, omega, 6 N; y the stage's output at x;
+// scratch 16 N), FP64 cases
+cudaError_t launch_destruction_vjp(const CaseDev& cd, StatePtrs x, double dt, const double* ybar, double* out,
+                                   double* scratch, cudaStream_t s);
+cudaError_t launch_explicit_vjp(const CaseDev& cd, StatePtrs x, StatePtrs y, double dt, const double* ybar,
+                                double* xbar, double* scratch, cudaStream_t s);
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 

@@ -1942,33 +1942,25 @@ fvm_status fvm_lambda2(fvm_case* c, double* host_out, size_t n) {
     return FVM_OK;
 }
 
-fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
-                              double rel_tol, int32_t max_vcycles, double* rel_out) {
-    if (!c || !host_ybar || !host_xbar) return fail(FVM_ERR_INVALID, "null case or buffer");
-    if (c->prec != FVM_FP64 || c->inner != FVM_FP64) return fail(FVM_ERR_INVALID, "FP64 cases only");
-    if (!(dt > 0.0)) return fail(FVM_ERR_INVALID, "dt must be > 0");
-    if (!(rel_tol > 0.0) || max_vcycles < 1) return fail(FVM_ERR_INVALID, "need rel_tol > 0 and max_vcycles >= 1");
+namespace {
+
+// The projection's vector-Jacobian product on device buffers: ybar (u, v, w, p: 4 N) -> xbar
+// (u, v, w: 3 N).  A lambda = q by the case's own V-cycles from zero (A is symmetric on the fluid
+// cells); the case's p and b are saved into save (2 N) and put back, whatever happens.
+fvm_status projection_vjp_dev(fvm_case* c, double dt, const double* ybar, double* xbar, double rel_tol,
+                              int32_t max_vcycles, double* save, double* rel_out) {
     const int64_t N = c->cd.N;
-    if (n < (size_t)(4 * N)) return fail(FVM_ERR_INVALID, "buffers too small (4 N in, 3 N out)");
     cudaStream_t s = c->stream;
-    // scratch: ybar (4 N), xbar (3 N), the case's p and b (2 N); freed before returning
-    double* d = nullptr;
-    CUDA_TRY(cudaMalloc((void**)&d, (size_t)9 * N * 8));
-    double* ybar = d;
-    double* xbar = d + 4 * N;
-    double* p_save = d + 7 * N;
-    double* b_save = d + 8 * N;
+    double* p_save = save;
+    double* b_save = save + N;
     double* b = (double*)c->b;
-    fvm_status st = FVM_OK;
     double rel = 0.0;
     bool saved = false;
     auto run = [&]() -> fvm_status {
         CUDA_TRY(cudaMemcpyAsync(p_save, c->p, N * 8, cudaMemcpyDeviceToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(b_save, b, N * 8, cudaMemcpyDeviceToDevice, s));
         saved = true;
-        CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)4 * N * 8, cudaMemcpyHostToDevice, s));
         KLAUNCH("adj_grad", (double)N * (5 * 8 + 2 + 1), 1, launch_adj_grad(c->cd, c->levels[0].dev, ybar, b, dt, s));
-        // A is symmetric on the fluid cells: A^T lambda = q by the case's own solver, from zero
         CUDA_TRY(cudaMemsetAsync(c->p, 0, N * 8, s));
         int done = 0;
         const int chunk = 4;
@@ -1980,10 +1972,9 @@ fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, d
         }
         KLAUNCH("adj_rhs", (double)N * (3 * 8 + 8 + 3 * 8 + 2 + 1), 1,
                 launch_adj_rhs(c->cd, c->levels[0].dev, ybar, c->p, xbar, dt, s));
-        CUDA_TRY(cudaMemcpyAsync(host_xbar, xbar, (size_t)3 * N * 8, cudaMemcpyDeviceToHost, s));
         return rel <= rel_tol ? FVM_OK : FVM_ERR_NOT_CONVERGED;
     };
-    st = run();
+    fvm_status st = run();
     if (saved) {   // the case's p and b back, whatever happened after they were saved
         const std::string msg = g_err;
         cudaError_t e1 = cudaMemcpyAsync(c->p, p_save, N * 8, cudaMemcpyDeviceToDevice, s);
@@ -1994,11 +1985,170 @@ fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, d
         if (!restored && (st == FVM_OK || st == FVM_ERR_NOT_CONVERGED))
             st = fail(FVM_ERR_CUDA, "restoring p and b after the adjoint solve");
     }
-    cudaStreamSynchronize(s);
-    cudaFree(d);
+    if (rel_out) *rel_out = rel;
+    return st;
+}
+
+// device scratch of the vector-Jacobian products, freed when it goes out of scope
+struct DevScratch {
+    double* d = nullptr;
+    ~DevScratch() {
+        if (d) cudaFree(d);
+    }
+};
+
+fvm_status vjp_checks(fvm_case* c, double dt, const void* a, const void* b) {
+    if (!c || !a || !b) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (c->prec != FVM_FP64 || c->inner != FVM_FP64) return fail(FVM_ERR_INVALID, "FP64 cases only");
+    if (!(dt > 0.0)) return fail(FVM_ERR_INVALID, "dt must be > 0");
+    return FVM_OK;
+}
+
+}  // namespace
+
+fvm_status fvm_projection_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
+                              double rel_tol, int32_t max_vcycles, double* rel_out) {
+    ST_TRY(vjp_checks(c, dt, host_ybar, host_xbar));
+    if (!(rel_tol > 0.0) || max_vcycles < 1) return fail(FVM_ERR_INVALID, "need rel_tol > 0 and max_vcycles >= 1");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)(4 * N)) return fail(FVM_ERR_INVALID, "buffers too small (4 N in, 3 N out)");
+    cudaStream_t s = c->stream;
+    DevScratch sc;   // ybar (4 N), xbar (3 N), the case's p and b (2 N)
+    CUDA_TRY(cudaMalloc((void**)&sc.d, (size_t)9 * N * 8));
+    double* ybar = sc.d;
+    double* xbar = sc.d + 4 * N;
+    CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)4 * N * 8, cudaMemcpyHostToDevice, s));
+    double rel = 0.0;
+    const fvm_status st = projection_vjp_dev(c, dt, ybar, xbar, rel_tol, max_vcycles, sc.d + 7 * N, &rel);
+    if (st == FVM_OK || st == FVM_ERR_NOT_CONVERGED) {
+        CUDA_TRY(cudaMemcpyAsync(host_xbar, xbar, (size_t)3 * N * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
     if (st == FVM_ERR_NOT_CONVERGED) fail(st, "adjoint solve stopped at max_vcycles above rel_tol");
     if (rel_out) *rel_out = rel;
     return st;
+}
+
+fvm_status fvm_destruction_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n) {
+    ST_TRY(vjp_checks(c, dt, host_ybar, host_xbar));
+    const int64_t N = c->cd.N;
+    if (n < (size_t)(5 * N)) return fail(FVM_ERR_INVALID, "buffers too small (5 N in and out)");
+    cudaStream_t s = c->stream;
+    DevScratch sc;   // ybar (5 N), xbar (5 N), kernel scratch (17 N)
+    CUDA_TRY(cudaMalloc((void**)&sc.d, (size_t)27 * N * 8));
+    double* ybar = sc.d;
+    double* xbar = sc.d + 5 * N;
+    CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)5 * N * 8, cudaMemcpyHostToDevice, s));
+    KLAUNCH("adj_destruction", (double)N * (5 * 8 * 2 + 5 * 8 + 17 * 8 * 2), 2,
+            launch_destruction_vjp(c->cd, ptrs(c->cur), dt, ybar, xbar, sc.d + 10 * N, s));
+    CUDA_TRY(cudaMemcpyAsync(host_xbar, xbar, (size_t)5 * N * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return FVM_OK;
+}
+
+namespace {
+
+// The explicit stage of the current state into y (6 fields, forward Euler) with a fixed time step:
+// the destruction-free explicit kernel with a time-step record holding dt.
+fvm_status explicit_forward(fvm_case* c, double dt, StatePtrs x, StatePtrs y, double* dt_dev) {
+    double h[4] = {dt, 0.5 * dt, 0.0, 0.0};
+    float hf[2] = {(float)dt, (float)(0.5 * dt)};
+    CUDA_TRY(cudaMemcpyAsync(dt_dev, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(dt_dev + 4, hf, sizeof(hf), cudaMemcpyHostToDevice, c->stream));
+    KLAUNCH("explicit", (double)c->cd.N * (13 * 8 + 3), 1,
+            launch_explicit(c->prec, c->cd, x, y, dt_dev, nullptr, StatePtrs{}, 0.0, 0.0, c->stream));
+    return FVM_OK;
+}
+
+}  // namespace
+
+fvm_status fvm_explicit_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n) {
+    ST_TRY(vjp_checks(c, dt, host_ybar, host_xbar));
+    if (c->desc.rk_stages > 1) return fail(FVM_ERR_INVALID, "forward-Euler cases only (rk_stages 0 or 1)");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)(6 * N)) return fail(FVM_ERR_INVALID, "buffers too small (6 N in and out)");
+    cudaStream_t s = c->stream;
+    DevScratch sc;   // ybar (6 N), xbar (6 N), the stage's output (6 N), kernel scratch (16 N), time step
+    CUDA_TRY(cudaMalloc((void**)&sc.d, (size_t)34 * N * 8 + 64));
+    double* ybar = sc.d;
+    double* xbar = sc.d + 6 * N;
+    StatePtrs y;
+    for (int f = 0; f < 6; ++f) y.f[f] = sc.d + (12 + f) * N;
+    double* dt_dev = sc.d + 34 * N;
+    CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)6 * N * 8, cudaMemcpyHostToDevice, s));
+    ST_TRY(explicit_forward(c, dt, ptrs(c->cur), y, dt_dev));
+    KLAUNCH("adj_explicit", (double)N * (6 * 8 * 4 + 6 * 8 * 2 + 16 * 8 * 2), 2,
+            launch_explicit_vjp(c->cd, ptrs(c->cur), y, dt, ybar, xbar, sc.d + 18 * N, s));
+    CUDA_TRY(cudaMemcpyAsync(host_xbar, xbar, (size_t)6 * N * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return FVM_OK;
+}
+
+fvm_status fvm_step_vjp(fvm_case* c, double dt, const double* host_ybar, double* host_xbar, size_t n,
+                        double rel_tol, int32_t max_vcycles, double* rel_out) {
+    ST_TRY(vjp_checks(c, dt, host_ybar, host_xbar));
+    if (!(rel_tol > 0.0) || max_vcycles < 1) return fail(FVM_ERR_INVALID, "need rel_tol > 0 and max_vcycles >= 1");
+    if (c->desc.rk_stages > 1) return fail(FVM_ERR_INVALID, "forward-Euler cases only (rk_stages 0 or 1)");
+    const int64_t N = c->cd.N;
+    if (n < (size_t)(7 * N)) return fail(FVM_ERR_INVALID, "buffers too small (7 N in, 6 N out)");
+    cudaStream_t s = c->stream;
+    // scratch (doubles): ybar 7 N | s1 k, omega 2 N | s2 6 N | bar 6 N | tmp 6 N | kernel 17 N |
+    // projection save 2 N | time step
+    DevScratch sc;
+    CUDA_TRY(cudaMalloc((void**)&sc.d, (size_t)46 * N * 8 + 64));
+    double* d = sc.d;
+    double* ybar = d;
+    double* s1k = d + 7 * N;
+    double* s1o = d + 8 * N;
+    StatePtrs s2;
+    for (int f = 0; f < 6; ++f) s2.f[f] = d + (9 + f) * N;
+    double* bar = d + 15 * N;      // u, v, w, T, k, omega
+    double* tmp = d + 21 * N;
+    double* kern = d + 27 * N;
+    double* psave = d + 44 * N;
+    double* dt_dev = d + 46 * N;
+    CUDA_TRY(cudaMemcpyAsync(ybar, host_ybar, (size_t)7 * N * 8, cudaMemcpyHostToDevice, s));
+    // forward: s1 = D(x0) over dt/2 (k, omega only), s2 = E(s1) over dt
+    const StatePtrs x0 = ptrs(c->cur);
+    double h[4] = {dt, 0.5 * dt, 0.0, 0.0};
+    float hf[2] = {(float)dt, (float)(0.5 * dt)};
+    CUDA_TRY(cudaMemcpyAsync(dt_dev, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dt_dev + 4, hf, sizeof(hf), cudaMemcpyHostToDevice, s));
+    KLAUNCH("destruction", (double)N * (8 * 8 + 3), 1,
+            launch_destruction(c->prec, c->cd, x0, s1k, s1o, dt_dev, nullptr, nullptr, s));
+    StatePtrs s1 = x0;
+    s1.f[4] = s1k;
+    s1.f[5] = s1o;
+    ST_TRY(explicit_forward(c, dt, s1, s2, dt_dev));
+    // backward: the projection (u, v, w, p cotangents; ybar holds u, v, w, p in id order)
+    double rel = 0.0;
+    const fvm_status pst = projection_vjp_dev(c, dt, ybar, bar, rel_tol, max_vcycles, psave, &rel);
+    if (pst != FVM_OK && pst != FVM_ERR_NOT_CONVERGED) return pst;
+    // bar: u, v, w (from the projection), T, k, omega (of the output)
+    CUDA_TRY(cudaMemcpyAsync(bar + 3 * N, ybar + 4 * N, (size_t)3 * N * 8, cudaMemcpyDeviceToDevice, s));
+    // through the second half step at s2: (u, v, w, k, omega) cotangents, T passes
+    auto through_destruction = [&](StatePtrs x) -> fvm_status {
+        // tmp: u, v, w, k, omega of bar (contiguous for the kernel)
+        CUDA_TRY(cudaMemcpyAsync(tmp, bar, (size_t)3 * N * 8, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(tmp + 3 * N, bar + 4 * N, (size_t)2 * N * 8, cudaMemcpyDeviceToDevice, s));
+        KLAUNCH("adj_destruction", (double)N * (5 * 8 * 2 + 5 * 8 + 17 * 8 * 2), 2,
+                launch_destruction_vjp(c->cd, x, 0.5 * dt, tmp, tmp, kern, s));
+        CUDA_TRY(cudaMemcpyAsync(bar, tmp, (size_t)3 * N * 8, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(bar + 4 * N, tmp + 3 * N, (size_t)2 * N * 8, cudaMemcpyDeviceToDevice, s));
+        return FVM_OK;
+    };
+    ST_TRY(through_destruction(s2));
+    // through the explicit stage at s1 (its output s2 decides the clamps)
+    KLAUNCH("adj_explicit", (double)N * (6 * 8 * 4 + 6 * 8 * 2 + 16 * 8 * 2), 2,
+            launch_explicit_vjp(c->cd, s1, s2, dt, bar, tmp, kern, s));
+    CUDA_TRY(cudaMemcpyAsync(bar, tmp, (size_t)6 * N * 8, cudaMemcpyDeviceToDevice, s));
+    // through the first half step at x0
+    ST_TRY(through_destruction(x0));
+    CUDA_TRY(cudaMemcpyAsync(host_xbar, bar, (size_t)6 * N * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (rel_out) *rel_out = rel;
+    if (pst == FVM_ERR_NOT_CONVERGED) return fail(pst, "adjoint solve stopped at max_vcycles above rel_tol");
+    return FVM_OK;
 }
 
 fvm_status fvm_batch_create(fvm_case* const* cases, int32_t n, void* stream, fvm_batch** out) {

@@ -708,6 +708,437 @@ __device__ void AdjRhsK::run(const BlockAt& at) const {
     }
 }
 
+// ------------------------------------------------------------------ step adjoints (FP64)
+// Vector-Jacobian products of the destruction half step and of the forward-Euler
+// explicit stage, linearised at a given state (the differentiable step of Section 1,
+// with the partial derivatives of Eqs. k_des_step, o_des_step, ko_turb_diff, a_star,
+// k_gen, o_gen, beta_star and the fluxes of Algorithms 2 and 3 written out).
+// Each runs as two passes: a pointwise pass per cell (partial derivatives, the
+// cotangents of the cell gradients) into a scratch array, then a gather per cell of
+// everything that reaches it through the stencils.  A ghost of Section 2.7 is
+// s * (the cell's own value) + a constant, with s per field and face kind (ghost_sign),
+// so a cotangent on a ghost returns to its cell times s.  Solid cells pass their
+// cotangents through unchanged.
+
+// the face across side `side` (-1 / +1) of cell (i,j,k) along `axis`: its kind, the
+// thermal condition of a wall (domain wall or obstacle) and the neighbour's index
+__device__ __forceinline__ int face_kind_of(const CaseDev& cd, int i, int j, int k, int axis, int side, int& thermal,
+                                            int& nb) {
+    int q[3] = {i, j, k};
+    q[axis] += side;
+    thermal = FVM_ADIABATIC;
+    nb = -1;
+    if (q[axis] < 0 || q[axis] >= cd.n[axis]) {
+        const int face = 2 * axis + (side > 0 ? 1 : 0);
+        const PatchDev& pt = cd.patch[cd.face_patch[face][face_index(axis, i, j, k, cd.n)]];
+        thermal = pt.thermal;
+        if (pt.kind == FVM_WALL) return FK_WALL;
+        if (pt.kind == FVM_INLET) return FK_INLET;
+        return pt.kind == FVM_OUTLET ? FK_OUTLET : FK_EMPTY;
+    }
+    nb = q[0] + cd.n[0] * (q[1] + cd.n[1] * q[2]);
+    const int t = cd.tag[nb];
+    if (t) {
+        thermal = cd.box[t - 1].thermal;
+        return FK_WALL;
+    }
+    return FK_INTERIOR;
+}
+
+// s of the ghost s * phi_P + const of field f (0..5 = u, v, w, T, k, omega) across a face
+__device__ __forceinline__ double ghost_sign(int f, int kind, int thermal) {
+    if (kind == FK_WALL) {
+        if (f < 3) return -1.0;                                  // no slip
+        if (f == 3) return thermal == FVM_FIXED_T ? -1.0 : 1.0;  // fixed T mirrors; adiabatic, heat flux shift
+        return 1.0;                                              // zero gradient of k, omega
+    }
+    return kind == FK_INLET ? -1.0 : 1.0;                        // inlet mirrors; outlet, empty copy
+}
+
+// the cell gradients of (u, v, w, k, omega) at a fluid cell, ghosts included
+__device__ __forceinline__ void cell_gradients(const CaseDev& cd, const StatePtrs& in, int i, int j, int k,
+                                               const St<double>& P, double (&gu)[3][3], double (&gk)[3],
+                                               double (&gw)[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) {
+            gu[0][a] = gu[1][a] = gu[2][a] = gk[a] = gw[a] = 0.0;
+            continue;
+        }
+        St<double> L, R;
+        neighbour<double, double>(cd, in, i, j, k, a, -1, P, L);
+        neighbour<double, double>(cd, in, i, j, k, a, +1, P, R);
+        const double ih = cd.inv_h[a];
+        gu[0][a] = 0.5 * ((R.u - P.u) * ih + (P.u - L.u) * ih);
+        gu[1][a] = 0.5 * ((R.v - P.v) * ih + (P.v - L.v) * ih);
+        gu[2][a] = 0.5 * ((R.w - P.w) * ih + (P.w - L.w) * ih);
+        gk[a] = 0.5 * ((R.k - P.k) * ih + (P.k - L.k) * ih);
+        gw[a] = 0.5 * ((R.om - P.om) * ih + (P.om - L.om) * ih);
+    }
+}
+
+// Transpose of the cell gradient of field f at cell q: gb(m, c) holds the cotangent of
+// d phi / d x_m at cell c (component m of the field's gradient); the gradient at a fluid
+// cell c along m is (R - L) / (2 h) with R, L the neighbours or their ghosts.
+template <class G>
+__device__ __forceinline__ double gradient_transpose(const CaseDev& cd, int f, int i, int j, int k, int q, G gb) {
+    double acc = 0.0;
+    for (int m = 0; m < 3; ++m) {
+        if (!cd.active[m]) continue;
+        const double c2 = 0.5 * cd.inv_h[m];
+        for (int side = -1; side <= 1; side += 2) {
+            int thermal, nb;
+            const int kind = face_kind_of(cd, i, j, k, m, side, thermal, nb);
+            if (kind == FK_INTERIOR) acc += -side * c2 * gb(m, nb);   // q is the neighbour's L (side +) or R (side -)
+            else acc += side * ghost_sign(f, kind, thermal) * c2 * gb(m, q);   // q's own ghost
+        }
+    }
+    return acc;
+}
+
+// pass 1 of the destruction adjoint: per cell the partial derivatives of (k', omega') and
+// the cotangents of the 15 gradient components, gbar = [G (3 x 3, row = velocity
+// component), grad k, grad omega] (15 N doubles, component-major)
+struct DesAdjAK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    StatePtrs x;            // the state the step is linearised at
+    double dt;              // the half step
+    const double* kbar;     // cotangents of k', omega'
+    const double* obar;
+    double* kout;           // d/dk, d/domega parts of the cotangents of k, omega
+    double* oout;
+    double* gbar;           // 15 N
+    __device__ void run(const BlockAt& at) const;
+};
+
+__device__ void DesAdjAK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    const int64_t N = cd.N;
+    const double kb = kbar[c], wb = obar[c];
+    if (cd.tag[c]) {
+        kout[c] = kb;
+        oout[c] = wb;
+        for (int m = 0; m < 15; ++m) gbar[m * N + c] = 0.0;
+        return;
+    }
+    const St<double> P = load_state<double, double>(x, c);
+    double G[3][3], gk[3], gw[3];
+    cell_gradients(cd, x, i, j, k, P, G, gk, gw);
+    const double nu = cd.nu, kk = P.k, om = P.om;
+    const double oms = om > kEpsOmega ? om : kEpsOmega;
+    const double doms = om > kEpsOmega ? 1.0 : 0.0;
+    // k' = k / Dk, Dk = 1 + dt beta* f_beta* omega
+    const double re = kk / (nu * oms), dre_dk = 1.0 / (nu * oms), dre_dom = -re / oms * doms;
+    const double x_ = re / kRbeta, x3 = x_ * x_ * x_, x4 = x3 * x_;
+    double bs, dbs;
+    if (x_ > 1e4) {
+        bs = kBetaStarInf;
+        dbs = 0.0;
+    } else {
+        bs = kBetaStarInf * (4.0 / 15.0 + x4) / (1.0 + x4);
+        dbs = kBetaStarInf * (11.0 / 15.0) * 4.0 * x3 / (kRbeta * (1.0 + x4) * (1.0 + x4));   // d beta* / d Re_t
+    }
+    const double dot = gk[0] * gw[0] + gk[1] * gw[1] + gk[2] * gw[2];
+    const double o3 = oms * oms * oms;
+    const double chik = dot / o3;
+    double fbs = 1.0, dfbs = 0.0;
+    if (chik > 0.0 && chik <= 1e8) {
+        const double c2 = chik * chik, d = 1.0 + 400.0 * c2;
+        fbs = (1.0 + 680.0 * c2) / d;
+        dfbs = 560.0 * chik / (d * d);
+    } else if (chik > 1e8) {
+        fbs = 680.0 / 400.0;
+    }
+    const double Dk = 1.0 + dt * bs * fbs * om;
+    const double ck = -kk / (Dk * Dk) * dt;                    // d k' / d (beta* f_beta* omega)
+    const double dk_dk = 1.0 / Dk + ck * fbs * om * dbs * dre_dk;
+    const double dk_dom = ck * (fbs * om * dbs * dre_dom + bs * om * dfbs * (-3.0 * chik / oms * doms) + bs * fbs);
+    const double dk_dg = ck * bs * om * dfbs / o3;             // times grad omega (for grad k) and grad k
+    // omega' = omega / Dw, Dw = 1 + dt beta f_beta omega, f_beta of chi_w = |T| / (beta*_inf omega_s)^3
+    double S[3][3], O[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            S[a][b] = 0.5 * (G[a][b] + G[b][a]);
+            O[a][b] = 0.5 * (G[a][b] - G[b][a]);
+        }
+    double OO[3][3], SO[3][3], OS[3][3];
+    double T = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int e = 0; e < 3; ++e) {
+                s1 += O[a][e] * O[e][b];
+                s2 += S[a][e] * O[e][b];
+                s3 += O[a][e] * S[e][b];
+            }
+            OO[a][b] = s1;
+            SO[a][b] = s2;
+            OS[a][b] = s3;
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) T += OO[a][b] * S[b][a];
+    const double den = (kBetaStarInf * oms) * (kBetaStarInf * oms) * (kBetaStarInf * oms);
+    const double chiw = fabs(T) / den;
+    double fb, dfb;
+    if (chiw > 1e30) {
+        fb = 70.0 / 80.0;
+        dfb = 0.0;
+    } else {
+        const double d = 1.0 + 80.0 * chiw;
+        fb = (1.0 + 70.0 * chiw) / d;
+        dfb = -10.0 / (d * d);
+    }
+    const double sgn = T > 0.0 ? 1.0 : (T < 0.0 ? -1.0 : 0.0);
+    const double Dw = 1.0 + dt * kBeta * fb * om;
+    const double cw = -om / (Dw * Dw) * dt * kBeta;            // d omega' / d (f_beta omega)
+    const double dw_dom = 1.0 / Dw + cw * (fb + om * dfb * (-3.0 * chiw / oms * doms));
+    const double dwg = cw * om * dfb * sgn / den;              // times d T / d G
+    kout[c] = kb * dk_dk;
+    oout[c] = kb * dk_dom + wb * dw_dom;
+    // d T / d S_ab = (O O)_ba, d T / d O_ab = -(O S + S O)_ab; S, O are the symmetric and
+    // antisymmetric parts of G
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double dS_ab = OO[b][a], dS_ba = OO[a][b];
+            const double dO_ab = -(OS[a][b] + SO[a][b]), dO_ba = -(OS[b][a] + SO[b][a]);
+            const double dT = 0.5 * (dS_ab + dS_ba) + 0.5 * (dO_ab - dO_ba);
+            gbar[(3 * a + b) * N + c] = wb * dwg * dT;
+        }
+    for (int m = 0; m < 3; ++m) {
+        gbar[(9 + m) * N + c] = kb * dk_dg * gw[m];
+        gbar[(12 + m) * N + c] = kb * dk_dg * gk[m];
+    }
+}
+
+// pass 2: the cotangents of (u, v, w, k, omega) before the step: incoming cotangents
+// of u, v, w pass through, k and omega take pass 1's parts, and every field gathers
+// the transposed gradient stencil of its gbar
+struct DesAdjBK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    const double* ubar_in;   // 3 N: cotangents of u, v, w after the step (unchanged by it)
+    const double* kout;
+    const double* oout;
+    const double* gbar;
+    double* out;             // 5 N: u, v, w, k, omega (may alias ubar_in for the first 3 N)
+    __device__ void run(const BlockAt& at) const;
+};
+
+__device__ void DesAdjBK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    const int64_t N = cd.N;
+    const bool fluid = cd.tag[c] == 0;
+    double acc[5] = {ubar_in[c], ubar_in[N + c], ubar_in[2 * N + c], kout[c], oout[c]};
+    if (fluid) {
+        const int field_of[5] = {0, 1, 2, 4, 5};
+        for (int v = 0; v < 5; ++v) {
+            const double* g = gbar + (size_t)(v < 3 ? 3 * v : (v == 3 ? 9 : 12)) * N;
+            acc[v] += gradient_transpose(cd, field_of[v], i, j, k, c,
+                                         [&](int m, int q) { return g[(size_t)m * N + q]; });
+        }
+    }
+    for (int v = 0; v < 5; ++v) out[v * N + c] = acc[v];
+}
+
+// pass 1 of the explicit-stage adjoint (forward Euler): per fluid cell the cotangents of
+// the update's right-hand side, rbar_f = dt ybar_f where the update passes a derivative
+// (not for clamped k, omega or the wall omega), the squared strain S^2 and the
+// cotangent of the velocity gradient from the production term, Gbar_ab = 4 S_ab S2bar
+// (scratch: rbar 6 N, Gbar 9 N, S^2 N)
+struct ExpAdjAK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    StatePtrs x;            // the state the stage is linearised at
+    StatePtrs y;            // the stage's output (its clamps decide which cells pass a derivative)
+    double dt;
+    const double* ybar;     // 6 N: cotangents of the output
+    double* rbar;           // 6 N
+    double* Gbar;           // 9 N
+    double* s2;             // N
+    __device__ void run(const BlockAt& at) const;
+};
+
+// omega of a fluid cell is set to its wall value after the update when a face of an
+// active axis is a wall (domain wall or obstacle)
+__device__ __forceinline__ bool wall_cell(const CaseDev& cd, int i, int j, int k) {
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) continue;
+        for (int side = -1; side <= 1; side += 2) {
+            int thermal, nb;
+            if (face_kind_of(cd, i, j, k, a, side, thermal, nb) == FK_WALL) return true;
+        }
+    }
+    return false;
+}
+
+__device__ void ExpAdjAK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    const int64_t N = cd.N;
+    if (cd.tag[c]) {
+        for (int f = 0; f < 6; ++f) rbar[f * N + c] = 0.0;
+        for (int m = 0; m < 9; ++m) Gbar[m * N + c] = 0.0;
+        s2[c] = 0.0;
+        return;
+    }
+    const double kn = ((const double*)y.f[4])[c], on = ((const double*)y.f[5])[c];
+    const bool live_k = kn > kKMin;
+    const bool live_o = on > kOmegaMin && !wall_cell(cd, i, j, k);
+    for (int f = 0; f < 6; ++f) {
+        const bool lv = f < 4 || (f == 4 ? live_k : live_o);
+        rbar[f * N + c] = lv ? dt * ybar[f * N + c] : 0.0;
+    }
+    const St<double> P = load_state<double, double>(x, c);
+    double G[3][3], gk[3], gw[3];
+    cell_gradients(cd, x, i, j, k, P, G, gk, gw);
+    double S[3][3], S2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            S[a][b] = 0.5 * (G[a][b] + G[b][a]);
+            S2 += S[a][b] * S[a][b];
+        }
+    S2 *= 2.0;
+    s2[c] = S2;
+    const double nu = cd.nu;
+    const double nut = nut_of<double>(P.k, P.om, nu);
+    const double ret = re_t<double>(P.k, P.om, nu), rw = ret / kRw;
+    const double alpha = (kAlphaInf / alpha_star_of<double>(ret)) * ((kAlpha0 + rw) / (1.0 + rw));
+    const double q = alpha * P.om / P.k;                       // G_omega = q G_k
+    const double rk = live_k ? dt * ybar[4 * N + c] : 0.0, ro = live_o ? dt * ybar[5 * N + c] : 0.0;
+    const double S2bar = (rk + ro * q) * nut;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Gbar[(3 * a + b) * N + c] = 4.0 * S[a][b] * S2bar;
+}
+
+// pass 2: per cell, the identity part of the update, the fluxes of its six faces
+// (upwind convection, central diffusion with the face eddy viscosity, the -(2/3) k
+// face term of the normal momentum) transposed onto the cell, the production and
+// buoyancy sources, the eddy viscosity's dependence on k and omega, and the transposed
+// velocity gradient of the production term
+struct ExpAdjBK {
+    static constexpr int kThreads = BX * BY * BZ;
+    static constexpr bool kNoShared = true;
+    __device__ bool live() const { return true; }
+    CaseDev cd;
+    StatePtrs x;
+    const double* ybar;     // 6 N
+    const double* rbar;     // 6 N (pass 1)
+    const double* Gbar;     // 9 N
+    const double* s2;       // N
+    double* xbar;           // 6 N
+    __device__ void run(const BlockAt& at) const;
+};
+
+__device__ void ExpAdjBK::run(const BlockAt& at) const {
+    int i, j, k;
+    if (!cell3(cd, at, i, j, k)) return;
+    const int c = i + cd.n[0] * (j + cd.n[1] * k);
+    const int64_t N = cd.N;
+    if (cd.tag[c]) {
+        for (int f = 0; f < 6; ++f) xbar[f * N + c] = ybar[f * N + c];
+        return;
+    }
+    const double nu = cd.nu;
+    const double gam[6] = {nu, nu, nu, cd.alpha, nu, nu};
+    const double isig[6] = {1.0, 1.0, 1.0, cd.inv_Prt, cd.inv_sigk, cd.inv_sigw};
+    const St<double> P = load_state<double, double>(x, c);
+    double rb[6], acc[6];
+    // the identity part of phi + dt rhs where the update passes a derivative: there rbar =
+    // dt ybar, so rbar = 0 with ybar != 0 marks a clamped k or omega or a wall omega
+    for (int f = 0; f < 6; ++f) {
+        rb[f] = rbar[f * N + c];
+        acc[f] = f < 4 || rb[f] != 0.0 ? ybar[f * N + c] : 0.0;
+    }
+    const double nutP = nut_of<double>(P.k, P.om, nu);
+    double nutbar = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!cd.active[a]) continue;
+        const double ih = cd.inv_h[a];
+        for (int side = -1; side <= 1; side += 2) {
+            int thermal, nb;
+            const int kind = face_kind_of(cd, i, j, k, a, side, thermal, nb);
+            St<double> Q;   // the state across the face (neighbour or ghost)
+            neighbour<double, double>(cd, x, i, j, k, a, side, P, Q);
+            const bool interior = kind == FK_INTERIOR;
+            // face cotangents F_bar_f = (rbar(L cell) - rbar(R cell)) / h
+            double Fb[6];
+            for (int f = 0; f < 6; ++f) {
+                const double rq = interior ? rbar[f * N + nb] : 0.0;
+                Fb[f] = side > 0 ? (rb[f] - rq) * ih : (rq - rb[f]) * ih;
+            }
+            const St<double>& L = side > 0 ? P : Q;
+            const St<double>& R = side > 0 ? Q : P;
+            const double uf = 0.5 * (vcomp(L, a) + vcomp(R, a));
+            const bool upL = uf >= 0.0;
+            const double nutf = kind == FK_WALL ? 0.0
+                                : (interior ? 0.5 * (nutP + nut_of<double>(Q.k, Q.om, nu)) : nutP);
+            const double phL[6] = {L.u, L.v, L.w, L.T, L.k, L.om}, phR[6] = {R.u, R.v, R.w, R.T, R.k, R.om};
+            double ufb = 0.0, nfb = 0.0;
+            for (int f = 0; f < 6; ++f) {
+                const double G_ = gam[f] + nutf * isig[f];
+                const double dL = Fb[f] * ((upL ? -uf : 0.0) - G_ * ih);
+                const double dR = Fb[f] * ((upL ? 0.0 : -uf) + G_ * ih);
+                // this cell's own side, and (across a ghost face) the ghost built from it
+                double d = side > 0 ? dL : dR;
+                if (!interior) d += ghost_sign(f, kind, thermal) * (side > 0 ? dR : dL);
+                acc[f] += d;
+                ufb += -(upL ? phL[f] : phR[f]) * Fb[f];
+                nfb += (phR[f] - phL[f]) * ih * isig[f] * Fb[f];
+            }
+            // face velocity (U_L + U_R) / 2 and the -(k_L + k_R) / 3 of the normal momentum
+            const double sa = interior ? 0.0 : ghost_sign(a, kind, thermal);
+            acc[a] += 0.5 * ufb * (1.0 + sa);
+            const double sk = interior ? 0.0 : ghost_sign(4, kind, thermal);
+            acc[4] += -Fb[a] / 3.0 * (1.0 + sk);
+            // face eddy viscosity: the mean of the two cells inside, this cell's own on
+            // inlet, outlet and empty faces, none on walls
+            if (interior) nutbar += 0.5 * nfb;
+            else if (kind != FK_WALL) nutbar += nfb;
+        }
+    }
+    // sources: G_k = nu_t S^2, G_omega = q G_k, buoyancy -g_i beta_T (T - T_ref)
+    const double S2 = s2[c];
+    const double kk = P.k, om = P.om;
+    const double oms = om > kEpsOmega ? om : kEpsOmega, doms = om > kEpsOmega ? 1.0 : 0.0;
+    const double re = kk / (nu * oms), dre_dk = 1.0 / (nu * oms), dre_dom = -re / oms * doms;
+    const double r = re / kRk;
+    const double ast = kAlphaStarInf * (kAlphaStar0 + r) / (1.0 + r);
+    const double dast = kAlphaStarInf * (1.0 - kAlphaStar0) / (kRk * (1.0 + r) * (1.0 + r));
+    const double nut = ast * kk / oms;
+    const double dnut_dk = ast / oms + kk / oms * dast * dre_dk;
+    const double dnut_dom = -ast * kk / (oms * oms) * doms + kk / oms * dast * dre_dom;
+    const double rw = re / kRw;
+    const double A = (kAlpha0 + rw) / (1.0 + rw), dA = (1.0 - kAlpha0) / (kRw * (1.0 + rw) * (1.0 + rw));
+    const double ac = kAlphaInf * A / ast, dac = kAlphaInf * (dA / ast - A * dast / (ast * ast));
+    const double Gk = nut * S2;
+    const double q = ac * om / kk;
+    const double dq_dk = dac * dre_dk * om / kk - ac * om / (kk * kk);
+    const double dq_dom = dac * dre_dom * om / kk + ac / kk;
+    const double rk = rb[4], ro = rb[5];
+    acc[4] += ro * Gk * dq_dk;
+    acc[5] += ro * Gk * dq_dom;
+    nutbar += (rk + ro * q) * S2;
+    acc[4] += nutbar * dnut_dk;
+    acc[5] += nutbar * dnut_dom;
+    acc[3] += cd.gb[0] * rb[0] + cd.gb[1] * rb[1] + cd.gb[2] * rb[2];
+    // the production's velocity gradient, transposed
+    for (int v = 0; v < 3; ++v)
+        acc[v] += gradient_transpose(cd, v, i, j, k, c,
+                                     [&](int m, int qq) { return Gbar[(size_t)(3 * v + m) * N + qq]; });
+    for (int f = 0; f < 6; ++f) xbar[f * N + c] = acc[f];
+}
+
 // ------------------------------------------------------------------ lambda_2 diagnostic
 // The vortex criterion of the transient results (Section 3.2.3; Jeong and
 // Hussain 1995): lambda_2, the middle eigenvalue of the symmetric matrix
@@ -924,4 +1355,28 @@ cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cud
     else if (prec == FVM_FP32) k_unpack<float><<<nblocks(N), kThreads, 0, s>>>(src, (float*)dst, N);
     else k_unpack<__nv_bfloat16><<<nblocks(N), kThreads, 0, s>>>(src, (__nv_bfloat16*)dst, N);
     return cudaGetLastError();
+}
+
+cudaError_t launch_destruction_vjp(const CaseDev& cd, StatePtrs x, double dt, const double* ybar, double* out,
+                                   double* scratch, cudaStream_t s) {
+    // ybar: u, v, w, k, omega cotangents (5 N); scratch: kout, oout, gbar (17 N)
+    const int64_t N = cd.N;
+    double* kout = scratch;
+    double* oout = scratch + N;
+    double* gbar = scratch + 2 * N;
+    cudaError_t e = launch_k(DesAdjAK{cd, x, dt, ybar + 3 * N, ybar + 4 * N, kout, oout, gbar}, grid3(cd), kBlock3, 0, s);
+    if (e != cudaSuccess) return e;
+    return launch_k(DesAdjBK{cd, ybar, kout, oout, gbar, out}, grid3(cd), kBlock3, 0, s);
+}
+
+cudaError_t launch_explicit_vjp(const CaseDev& cd, StatePtrs x, StatePtrs y, double dt, const double* ybar,
+                                double* xbar, double* scratch, cudaStream_t s) {
+    // scratch: rbar (6 N), Gbar (9 N), S^2 (N)
+    const int64_t N = cd.N;
+    double* rbar = scratch;
+    double* Gbar = scratch + 6 * N;
+    double* s2 = scratch + 15 * N;
+    cudaError_t e = launch_k(ExpAdjAK{cd, x, y, dt, ybar, rbar, Gbar, s2}, grid3(cd), kBlock3, 0, s);
+    if (e != cudaSuccess) return e;
+    return launch_k(ExpAdjBK{cd, x, ybar, rbar, Gbar, s2, xbar}, grid3(cd), kBlock3, 0, s);
 }

@@ -130,3 +130,15 @@ def test_projection_vjp_rejects_bad_arguments_without_a_gpu(lib):
     buf = (ct.c_double * 8)()
     assert lib.fvm_projection_vjp(None, 0.01, buf, buf, 8, 1e-12, 10, None) == binding.ERR_INVALID
     assert "null case" in binding.last_error()
+
+
+def test_step_adjoints_reject_bad_arguments_without_a_gpu(lib):
+    """The new vector-Jacobian products validate their arguments before any device work."""
+    import ctypes as ct
+    dp = ct.POINTER(ct.c_double)
+    for name in ("fvm_destruction_vjp", "fvm_explicit_vjp"):
+        st = getattr(lib, name)(None, 0.01, dp(), dp(), 0)
+        assert st == binding.ERR_INVALID, name
+        assert "null" in binding.last_error()
+    st = lib.fvm_step_vjp(None, 0.01, dp(), dp(), 0, 1e-10, 10, None)
+    assert st == binding.ERR_INVALID and "null" in binding.last_error()
