@@ -463,6 +463,7 @@ def run_served(args, rank, ws, local, dist):
     makespan = t_end - t_start
     cell_steps = sum(d["cells"] * d["steps"] for d in done)
     bad = [d for d in done if d["status"] != 0]
+    compare = served_vs_fp64(args, specs, stream) if (ws == 1 and not args.no_compare and rank == 0) else None
     if dist:
         makespan, cell_steps = replicas.max_over_ranks(makespan), replicas.sum_over_ranks(cell_steps)
     if rank == 0:
@@ -476,13 +477,59 @@ def run_served(args, rank, ws, local, dist):
                            "parallelism": f"replicas x{ws}", "l2": "not flushed (a serving loop)"},
                 "latency_s": {"p50": q(0.50), "p99": q(0.99), "max": lat[-1], "mean": statistics.mean(lat)},
                 "makespan_s": makespan, "requests": len(done), "failed": len(bad),
-                "server": info, "clocks": clk,
+                "server": info, "clocks": clk, "compare": compare,
                 "e2e": {"value": cell_steps / makespan, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0,
                         "note": "requests enter as case descriptions (fields initialised on the device)"}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def served_vs_fp64(args, specs, stream):
+    """The target comparison of the served form: a seeded sample of the same requests, each
+    (a) served (mixed precision, batched, one server) and (b) run alone in the plain FP64
+    per-case form (FP64 fields and corrections, V(3,3), no Krylov acceleration, one graph
+    per step), both for the full number of steps to the same 1e-8 relative residual: the
+    cell-steps/s of each and the per-field error of (a) against (b)."""
+    import numpy as np
+    import torch
+    from paper_2603_21869_gb300 import binding
+    rng = np.random.default_rng(12345)
+    pick = sorted(rng.choice(len(specs), size=min(args.compare_requests, len(specs)), replace=False).tolist())
+    sample = [specs[i] for i in pick]
+    cells = sum(sp.cells for sp in sample) * args.served_steps
+    # (a) served together, all admitted at once
+    with binding.Server(budget_bytes=int(args.budget_gb * (1 << 30)), stream=stream.cuda_stream,
+                        keep_results=True) as srv:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [srv.submit(sp, args.served_steps, t_arrive=srv.now()) for sp in sample]
+        done = []
+        while len(done) < len(ids):
+            done += srv.poll(chunk=args.chunk)
+        t_served = time.perf_counter() - t0
+        served = {i: srv.read(i) for i in ids}
+        rel_served = max(d["rel_residual"] for d in done) if "rel_residual" in done[0] else None
+    # (b) the plain FP64 per-case form, one request at a time
+    plain = dict(precision=cases.FP64, pre_sweeps=3, post_sweeps=3, inner_cycles=0, krylov=0, sweep_planes=0)
+    errs, rels, t_fp64 = [], [], 0.0
+    for i, sp in zip(ids, sample):
+        with binding.Case(sp.replace(**plain), stream=stream.cuda_stream) as c:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = c.step(args.served_steps, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t_fp64 += time.perf_counter() - t0
+            errs.append(field_errors(served[i], c.read()))
+            rels.append(st["rel_residual"])
+    return {"requests": len(sample), "steps": args.served_steps,
+            "served_mixed_batched": {"value": cells / t_served, "unit": "cell-steps/s",
+                                     "rel_residual_max": rel_served},
+            "per_case_fp64": {"value": cells / t_fp64, "unit": "cell-steps/s", "rel_residual_max": max(rels)},
+            "speedup": t_fp64 / t_served,
+            "max_rel_error_vs_fp64": {f: max(e[f] for e in errs) for f in cases.FIELDS},
+            "note": "the same seeded sample of requests, wall time around each form on one GPU"}
 
 
 def compare_variants(args):
@@ -599,6 +646,8 @@ def main():
     ap.add_argument("--served-steps", type=int, default=30, help="served workload: steps per request")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--chunk", type=int, default=10, help="served workload: steps per scheduling round")
+    ap.add_argument("--compare-requests", type=int, default=8,
+                    help="served workload: requests of the sample compared with the plain FP64 per-case form")
     ap.add_argument("--compare-variants", action="store_true",
                     help="time the paper's multigrid scheme against V-cycles and exit")
     args = ap.parse_args()

@@ -281,6 +281,9 @@ cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const v
                          const SolveState* st, cudaStream_t s);
 cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, const void* r, double* p,
                               const SolveState* st, cudaStream_t s);
+// the last level-0 sweep of a BF16 level with its result in FP32 (the flexible-CG direction)
+cudaError_t launch_sweep_to_f32(int inner, const LevelDev& L, const void* e_in, const void* r, float* z,
+                                const SolveState* st, cudaStream_t s);
 // (ec0 not null: also the coarse level's first Jacobi sweep from e = 0)
 cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev& Lc, const void* e, const void* r,
                                   void* rc, void* ec0, const SolveState* st, cudaStream_t s);
@@ -290,6 +293,7 @@ cudaError_t prepare_coarse_cta(int inner, size_t smem);
 // flexible CG with one kept direction around the V-cycles: the inner products
 // of z (the V-cycles' correction) with A z, r and the kept direction d_prev
 // (last block: beta, alpha), then d = z - beta d_prev, p += alpha d, d kept.
+// z and dp are in the inner type, FP32 for BF16 inner (r stays BF16).
 // partials: 4 doubles per block, level0_blocks_max(n) blocks at most.
 cudaError_t launch_fcg(int inner, const LevelDev& L, const void* z, const void* r, void* dp, double* p,
                        double* partials, SolveState* st, cudaStream_t s);

@@ -420,7 +420,8 @@ __device__ __forceinline__ bool walk_setup(const LevelDev& L, const BlockAt& at,
 // Scalar sweep (FP64 levels, and levels whose x extent is not a multiple of
 // 4): each thread walks KZ cells along z, keeping the z neighbours in
 // registers; all loads of its cells are issued before any arithmetic.
-// MODE 0: eout = sweep(ein); MODE 1: p += sweep(ein) (last level-0 sweep).
+// MODE 0: eout = sweep(ein); MODE 1: p += sweep(ein) (last level-0 sweep); MODE 2: the
+// result in FP32 (the last level-0 sweep under the flexible-CG acceleration of BF16 levels).
 template <class TI, int MODE, int KZ>
 struct SweepK {
     static constexpr int kThreads = TX * TY;
@@ -431,6 +432,7 @@ struct SweepK {
     TI* eout;
     double* p;
     const SolveState* st;
+    float* z32;   // MODE 2: the result in FP32
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
     __device__ void run(const BlockAt& at) const;
 };
@@ -472,6 +474,7 @@ __device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
                               : eP + wJ * (rr[kk] - A7<C>(L, f[kk], eP, xm[kk], xp[kk], ym[kk], yp[kk], col[kk],
                                                           col[kk + 2])) * iD;
             if (MODE == 0) eout[c] = from_c<TI, C>(v);
+            else if (MODE == 2) z32[c] = (float)v;
             else if (!solid) p[c] += (double)v;
         }
     }
@@ -508,6 +511,12 @@ template <> struct VecW<float, 4> {
     }
     static __device__ __forceinline__ void store(float* p, int c, const float (&v)[4]) {
         *reinterpret_cast<float4*>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct VecW<float, 8> {
+    static __device__ __forceinline__ void store(float* p, int c, const float (&v)[8]) {
+        *reinterpret_cast<float4*>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(p + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
     }
 };
 template <> struct VecW<__nv_bfloat16, 4> {
@@ -630,6 +639,7 @@ struct SweepVK {
     double* p;
     const SolveState* st;
     int zc;    // planes per block
+    float* z32;   // MODE 2: the sweep's result in FP32 (the flexible-CG direction of BF16 levels)
     int lrl;   // log2 of the lanes per row segment (5: a warp per W * 32-cell segment; 4, 3, 2: a warp
                // covers 2, 4 or 8 rows, so narrow rows leave no lane idle)
     __device__ bool live() const { return st->active != 0; }   // batched: skip a converged case
@@ -696,6 +706,8 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
         if (in) {
             if (MODE == 0) {
                 VecW<TI, W>::store(eout, base + own, v);
+            } else if (MODE == 2) {
+                VecW<float, W>::store(z32, base + own, v);
             } else {
                 double2* pp = reinterpret_cast<double2*>(p + base + own);
 #pragma unroll
@@ -980,15 +992,16 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
 // The flexible-CG inner products with W x cells per thread and a z march
 // (the sweep's layout and neighbour scheme): products, the thread's and the
 // warp's sums in FP32, block and grid sums in FP64.  Needs nx % W = 0.
-template <class TI, int W>
+// (TR: storage of r; TZ: storage of z and the kept direction, FP32 on BF16 levels)
+template <class TR, class TZ, int W>
 struct FcgDotVK {
     static constexpr int kThreads = TX * TY;
     static constexpr int kMinBlocks = 3;       // at most 80 registers
     static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
     LevelDev L;
-    const TI* z;
-    const TI* r;
-    const TI* dp;
+    const TZ* z;
+    const TR* r;
+    const TZ* dp;
     double* partials;
     SolveState* st;
     int zc;    // planes per block
@@ -997,10 +1010,11 @@ struct FcgDotVK {
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class TI, int W>
-__device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
+template <class TR, class TZ, int W>
+__device__ void FcgDotVK<TR, TZ, W>::run(const BlockAt& at) const {
     using C = float;
-    using R = RawW<TI, W>;
+    using R = RawW<TZ, W>;
+    using RR = RawW<TR, W>;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
     const int i4 = at.b.x * (W * LR) + lane * W, j = ((at.b.y * TY + threadIdx.y) << (5 - lrl)) + sub;
@@ -1014,7 +1028,7 @@ __device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
     const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
     const C dg = LP<C>::diag(L);
     const bool have = st->g_valid != 0;
-    const TI* const zz = this->z;
+    const TZ* const zz = this->z;
     const uint16_t* const nbf = L.nbf;
     typename R::T em = R::load(zz, max(k0 - 1, 0) * sz + own);
     typename R::T ec = R::load(zz, k0 * sz + own);
@@ -1024,7 +1038,7 @@ __device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
         const int base = k * sz;
         const typename R::T ym = R::load(zz, base + om);
         const typename R::T yp = R::load(zz, base + op);
-        const typename R::T rr = R::load(r, base + own);
+        const typename RR::T rr = RR::load(r, base + own);
         typename R::T dd = {};
         if (have) dd = R::load(dp, base + own);
         uint32_t fs[W];
@@ -1053,7 +1067,7 @@ __device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
                 } else {
                     A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, za, zb);
                 }
-                const C d = R::get(dd, t), rv = R::get(rr, t);
+                const C d = R::get(dd, t), rv = RR::get(rr, t);
                 a0 = fma(eP, A, a0);
                 a1 = fma(A, d, a1);
                 a2 = fma(rv, eP, a2);
@@ -1070,13 +1084,13 @@ __device__ void FcgDotVK<TI, W>::run(const BlockAt& at) const {
 
 // d = z - beta d_prev, p += alpha d (fluid cells), d kept: W consecutive
 // cells per thread, one-dimensional grid.  Needs N % W = 0.
-template <class TI, int W>
+template <class TZ, int W>
 struct FcgUpdVK {
     static constexpr int kThreads = 256;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
-    const TI* z;
-    TI* dp;
+    const TZ* z;
+    TZ* dp;
     double* p;
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }
@@ -1087,14 +1101,14 @@ struct FcgUpdVK {
         float zv[W], dv[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) dv[t] = 0.f;
-        VecW<TI, W>::load(z, c, zv);
-        if (beta != 0.f) VecW<TI, W>::load_rw(dp, c, dv);
+        VecW<TZ, W>::load(z, c, zv);
+        if (beta != 0.f) VecW<TZ, W>::load_rw(dp, c, dv);
         uint32_t fs[W];
         codes_w<W>(L.nbf, c, fs);
         float d[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) d[t] = fma(-beta, dv[t], zv[t]);
-        VecW<TI, W>::store(dp, c, d);
+        VecW<TZ, W>::store(dp, c, d);
         double2* pp = reinterpret_cast<double2*>(p + c);
 #pragma unroll
         for (int h = 0; h < W / 2; ++h) {
@@ -1596,23 +1610,23 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
 //   alpha  = ((r, z) - beta (r, d_prev)) / (d, A d),
 // keeping (d, A d) for the next iteration.  Should rounding make (d, A d)
 // non-positive (never in exact arithmetic) the direction restarts: beta = 0.
-template <class TI>
+template <class TR, class TZ>
 struct FcgDotK {
     static constexpr int kThreads = BX * BY * BZ;
     static constexpr int kMinBlocks = 4;
     LevelDev L;
-    const TI* z;
-    const TI* r;
-    const TI* dp;
+    const TZ* z;
+    const TR* r;
+    const TZ* dp;
     double* partials;
     SolveState* st;
     __device__ bool live() const { return st->active != 0; }
     __device__ void run(const BlockAt& at) const;
 };
 
-template <class TI>
-__device__ void FcgDotK<TI>::run(const BlockAt& at) const {
-    using C = typename Acc<TI>::type;
+template <class TR, class TZ>
+__device__ void FcgDotK<TR, TZ>::run(const BlockAt& at) const {
+    using C = typename Acc<TZ>::type;
     const bool have = st->g_valid != 0;
     double s[4] = {0.0, 0.0, 0.0, 0.0};   // (z,Az), (Az,dp), (r,z), (r,dp)
     int i, j, k;
@@ -1639,13 +1653,13 @@ __device__ void FcgDotK<TI>::run(const BlockAt& at) const {
 }
 
 // d = z - beta d_prev; p += alpha d on fluid cells; d kept as d_prev
-template <class TI>
+template <class TZ>
 struct FcgUpdK {
     static constexpr int kThreads = BX * BY * BZ;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     LevelDev L;
-    const TI* z;
-    TI* dp;
+    const TZ* z;
+    TZ* dp;
     double* p;
     const SolveState* st;
     __device__ bool live() const { return st->active != 0; }
@@ -1656,7 +1670,7 @@ struct FcgUpdK {
         const double alpha = st->g_alpha, beta = st->g_beta;
         const double d = to_c<double>(ldg(z + c)) - (beta != 0.0 ? beta * to_c<double>(dp[c]) : 0.0);
         if (!is_solid(L.nbf[c])) p[c] += alpha * d;
-        dp[c] = from_c<TI, double>(d);
+        dp[c] = from_c<TZ, double>(d);
     }
 };
 
@@ -1894,7 +1908,7 @@ static int sweep_planes(int tiles, int nz, int fixed) {
 
 template <class TI, int MODE>
 static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p,
-                              const SolveState* st, cudaStream_t s) {
+                              const SolveState* st, cudaStream_t s, float* z32 = nullptr) {
     if constexpr (sizeof(TI) < 8) {
         // four cells per thread on large levels and in batches (their blocks add up over the cases)
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
@@ -1903,18 +1917,18 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
             if (W == 8 && L.n[0] % 8 == 0) {
                 const int lrl = vw_lrl(L.n[0], 8);
                 const dim3 grid = vw_grid(L, 8, lrl, zc);
-                return launch_k(SweepVK<TI, MODE, vec_w<TI>()>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0,
-                                s);
+                return launch_k(SweepVK<TI, MODE, vec_w<TI>()>{L, ein, r, eout, p, st, zc, z32, lrl}, grid,
+                                dim3(TX, TY), 0, s);
             }
             const int lrl = vw_lrl(L.n[0], 4);
             const dim3 grid = vw_grid(L, 4, lrl, zc);
-            return launch_k(SweepVK<TI, MODE, 4>{L, ein, r, eout, p, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+            return launch_k(SweepVK<TI, MODE, 4>{L, ein, r, eout, p, st, zc, z32, lrl}, grid, dim3(TX, TY), 0, s);
         }
     }
     // four cells per thread on large grids and in batches (one launch for all cases of a level)
     if (L.N >= (1 << 20) || g_rec)
-        return launch_k(SweepK<TI, MODE, 4>{L, ein, r, eout, p, st}, walk_grid(L, 4), dim3(TX, TY), 0, s);
-    return launch_k(SweepK<TI, MODE, 1>{L, ein, r, eout, p, st}, walk_grid(L, 1), dim3(TX, TY), 0, s);
+        return launch_k(SweepK<TI, MODE, 4>{L, ein, r, eout, p, st, z32}, walk_grid(L, 4), dim3(TX, TY), 0, s);
+    return launch_k(SweepK<TI, MODE, 1>{L, ein, r, eout, p, st, z32}, walk_grid(L, 1), dim3(TX, TY), 0, s);
 }
 
 cudaError_t launch_sweep(int inner, const LevelDev& L, const void* e_in, const void* r, void* e_out,
@@ -1929,6 +1943,13 @@ cudaError_t launch_sweep_to_p(int inner, const LevelDev& L, const void* e_in, co
     cudaError_t err = cudaSuccess;
     DISPATCH_I(inner, err = sweep_walk<TI, 1>(L, (const TI*)e_in, (const TI*)r, nullptr, p, st, s));
     return err;
+}
+
+cudaError_t launch_sweep_to_f32(int inner, const LevelDev& L, const void* e_in, const void* r, float* z,
+                                const SolveState* st, cudaStream_t s) {
+    if (inner != FVM_BF16_MIXED) return cudaErrorInvalidValue;
+    using TI = __nv_bfloat16;
+    return sweep_walk<TI, 2>(L, (const TI*)e_in, (const TI*)r, nullptr, nullptr, st, s, z);
 }
 
 template <class TI>
@@ -2010,40 +2031,45 @@ cudaError_t launch_coarse_cta(int inner, const CoarseLevels& cl, const void* r_i
     return err;
 }
 
-template <class TI>
-static cudaError_t fcg_launch(const LevelDev& L, const TI* z, const TI* r, TI* dp, double* p, double* partials,
+// z and the kept direction dp in TZ (the inner type, or FP32 on BF16 levels), r in TR
+template <class TR, class TZ>
+static cudaError_t fcg_launch(const LevelDev& L, const TZ* z, const TR* r, TZ* dp, double* p, double* partials,
                               SolveState* st, cudaStream_t s) {
-    if constexpr (sizeof(TI) < 8) {
+    if constexpr (sizeof(TR) < 8) {
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
             // (at most level0_blocks_max(n) blocks: partials has room)
             int zc = 0;
-            if (vec_w<TI>() == 8 && L.n[0] % 8 == 0) {
-                constexpr int W = vec_w<TI>();
+            constexpr int W = std::is_same<TR, TZ>::value ? vec_w<TR>() : 4;
+            if (W == 8 && L.n[0] % 8 == 0) {
                 const int lrl = vw_lrl(L.n[0], W);
                 const dim3 grid = vw_grid(L, W, lrl, zc);
                 cudaError_t err =
-                    launch_k(FcgDotVK<TI, W>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+                    launch_k(FcgDotVK<TR, TZ, W>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
                 if (err != cudaSuccess) return err;
-                const unsigned nb = (unsigned)((L.N / W + FcgUpdVK<TI, W>::kThreads - 1) / FcgUpdVK<TI, W>::kThreads);
-                return launch_k(FcgUpdVK<TI, W>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TI, W>::kThreads), 0, s);
+                const unsigned nb = (unsigned)((L.N / W + FcgUpdVK<TZ, W>::kThreads - 1) / FcgUpdVK<TZ, W>::kThreads);
+                return launch_k(FcgUpdVK<TZ, W>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TZ, W>::kThreads), 0, s);
             }
             const int lrl = vw_lrl(L.n[0], 4);
             const dim3 grid = vw_grid(L, 4, lrl, zc);
-            cudaError_t err = launch_k(FcgDotVK<TI, 4>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
+            cudaError_t err =
+                launch_k(FcgDotVK<TR, TZ, 4>{L, z, r, dp, partials, st, zc, lrl}, grid, dim3(TX, TY), 0, s);
             if (err != cudaSuccess) return err;
-            const unsigned nb = (unsigned)((L.N / 4 + FcgUpdVK<TI, 4>::kThreads - 1) / FcgUpdVK<TI, 4>::kThreads);
-            return launch_k(FcgUpdVK<TI, 4>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TI, 4>::kThreads), 0, s);
+            const unsigned nb = (unsigned)((L.N / 4 + FcgUpdVK<TZ, 4>::kThreads - 1) / FcgUpdVK<TZ, 4>::kThreads);
+            return launch_k(FcgUpdVK<TZ, 4>{L, z, dp, p, st}, dim3(nb), dim3(FcgUpdVK<TZ, 4>::kThreads), 0, s);
         }
     }
-    cudaError_t err = launch_k(FcgDotK<TI>{L, z, r, dp, partials, st}, grid3(L), kBlock3, 0, s);
+    cudaError_t err = launch_k(FcgDotK<TR, TZ>{L, z, r, dp, partials, st}, grid3(L), kBlock3, 0, s);
     if (err != cudaSuccess) return err;
-    return launch_k(FcgUpdK<TI>{L, z, dp, p, st}, grid3(L), kBlock3, 0, s);
+    return launch_k(FcgUpdK<TZ>{L, z, dp, p, st}, grid3(L), kBlock3, 0, s);
 }
 
 cudaError_t launch_fcg(int inner, const LevelDev& L, const void* z, const void* r, void* dp, double* p,
                        double* partials, SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
-    DISPATCH_I(inner, err = fcg_launch<TI>(L, (const TI*)z, (const TI*)r, (TI*)dp, p, partials, st, s));
+    if (inner == FVM_BF16_MIXED)   // z and the kept direction in FP32 (rounding them to BF16 costs V-cycles)
+        return fcg_launch<__nv_bfloat16, float>(L, (const float*)z, (const __nv_bfloat16*)r, (float*)dp, p, partials,
+                                                st, s);
+    DISPATCH_I(inner, err = fcg_launch<TI, TI>(L, (const TI*)z, (const TI*)r, (TI*)dp, p, partials, st, s));
     return err;
 }
 

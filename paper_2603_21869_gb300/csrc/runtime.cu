@@ -326,7 +326,8 @@ struct fvm_case {
     double* Ainv = nullptr;
     double* p_tmp = nullptr;         // the paper's scheme: Jacobi on p out of place
     void* kdir = nullptr;            // flexible CG (krylov = 1): the kept direction (level 0, inner
-    double* kpart = nullptr;         //   precision) and four partial sums per level-0 block
+    double* kpart = nullptr;         //   precision, FP32 for BF16) and four partial sums per level-0 block
+    float* kz = nullptr;             //   BF16 inner: the V-cycles' level-0 correction z in FP32
     void* nut = nullptr;             // nu_t of the state after a destruction half step
     bool nut_valid = false;          // nut matches the current k, omega
     std::vector<DevLevel> levels;
@@ -702,8 +703,12 @@ fvm_status krylov_step(fvm_case* c, int zi) {
     DevLevel& L = c->levels[0];
     const double N = (double)L.dev.N;
     const double si = (double)elem_size(c->inner);
-    KLAUNCH("fcg_L0", N * (6 * si + 20), 2,
-            launch_fcg(c->inner, L.dev, L.e[zi], L.r, c->kdir, c->p, c->kpart, c->sst, c->stream));
+    // BF16 levels: z and the kept direction in FP32 (z from the last sweep), r in BF16
+    const bool f32 = c->inner == FVM_BF16_MIXED;
+    const double sz = f32 ? 4.0 : si;
+    KLAUNCH("fcg_L0", N * (4 * sz + si + sz + 20), 2,
+            launch_fcg(c->inner, L.dev, f32 ? (void*)c->kz : L.e[zi], L.r, c->kdir, c->p, c->kpart, c->sst,
+                       c->stream));
     return FVM_OK;
 }
 
@@ -774,6 +779,10 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
             if (l == 0 && rep == reps - 1 && k == post - 1 && !c->desc.krylov) {
                 KLAUNCH("sweep_to_p_L0", 2 * N * si + 16 * N + 2 * N, 1,
                         launch_sweep_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, c->sst, s));
+            } else if (l == 0 && rep == reps - 1 && k == post - 1 && c->kz) {
+                // BF16 levels under the flexible-CG step: the correction z in FP32
+                KLAUNCH("sweep_L0", 2 * N * si + 4 * N + 2 * N, 1,
+                        launch_sweep_to_f32(c->inner, L.dev, L.e[cur], L.r, c->kz, c->sst, s));
             } else {
                 KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
                         launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
@@ -1268,8 +1277,9 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
     c->nblocks0 = level0_blocks_max(L0.n[0], L0.n[1], L0.n[2]);
     ST_TRY(dalloc(c, (void**)&c->partials, (size_t)(2 * c->nblocks0) * 8));
     if (d.krylov == 1) {
-        const size_t si0 = elem_size(pl.inner);
+        const size_t si0 = elem_size(pl.inner == FVM_BF16_MIXED ? FVM_FP32 : pl.inner);
         ST_TRY(dalloc(c, &c->kdir, (size_t)N * si0));
+        if (pl.inner == FVM_BF16_MIXED) ST_TRY(dalloc(c, (void**)&c->kz, (size_t)N * 4));
         ST_TRY(dalloc(c, (void**)&c->kpart, (size_t)4 * level0_blocks_max(L0.n[0], L0.n[1], L0.n[2]) * 8));
     }
     ST_TRY(dalloc(c, (void**)&c->norms, 4 * 8));
