@@ -512,7 +512,9 @@ def served_vs_fp64(args, specs, stream):
         served = {i: srv.read(i) for i in ids}
         rel_served = max(d["rel_residual"] for d in done) if "rel_residual" in done[0] else None
     # (b) the plain FP64 per-case form, one request at a time
-    plain = dict(precision=cases.FP64, pre_sweeps=3, post_sweeps=3, inner_cycles=0, krylov=0, sweep_planes=0)
+    # (the plain V-cycles need about 55 per step on a room with a small outlet: room to reach 1e-8)
+    plain = dict(precision=cases.FP64, pre_sweeps=3, post_sweeps=3, inner_cycles=0, krylov=0, sweep_planes=0,
+                 max_vcycles=200)
     errs, rels, t_fp64 = [], [], 0.0
     for i, sp in zip(ids, sample):
         with binding.Case(sp.replace(**plain), stream=stream.cuda_stream) as c:

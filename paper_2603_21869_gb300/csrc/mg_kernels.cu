@@ -628,10 +628,11 @@ template <class TI, int MODE, int W>
 struct SweepVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
-    // W = 4: at most 64 registers, four blocks per SM (batched too: the few spilled bytes cost less
-    // than a block per SM); W = 8: at most 80, three blocks.  (Issuing the next plane's loads before
-    // the current plane's arithmetic, at 80 / 128 registers, measured slower on the room.)
-    static constexpr int kMinBlocks = W == 4 ? 4 : 3;
+    // at most 64 registers, four blocks per SM (batched too: the few spilled bytes cost less than a
+    // block per SM); the eight-cell update of p (MODE 1) at most 80, three blocks.  (Issuing the
+    // next plane's loads before the current plane's arithmetic, at 80 / 128 registers, measured
+    // slower on the room.)
+    static constexpr int kMinBlocks = (W == 8 && MODE == 1) ? 3 : 4;
     LevelDev L;
     const TI* ein;
     const TI* r;
