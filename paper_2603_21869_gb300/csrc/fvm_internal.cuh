@@ -78,11 +78,9 @@ template <class C> __device__ __forceinline__ C prm(double d, float f);
 template <> __device__ __forceinline__ double prm<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float prm<float>(double, float f) { return f; }
 
-// Double-float values: FP64 quantities handled without the FP64 pipe (1/64
-// of the FP32 rate on this part).  ff_split takes a double apart exactly by
-// integer operations into hi = its sign, exponent and leading 24 mantissa
-// bits and lo = the next 24 bits (about 2^-47 relative); ff_add / ff_mul are
-// Dekker's error-free sum and the FMA-based product, renormalised.
+// Double-float values: FP64-accurate quantities handled without the FP64 pipe
+// (1/64 of the FP32 rate on this part): ff_add / ff_mul are Dekker's
+// error-free sum and the FMA-based product, renormalised.
 struct FF {
     float h, l;
 };
@@ -113,35 +111,42 @@ __device__ __forceinline__ FF ff_mul(FF x, FF c) {
     return ff_norm(p, e);
 }
 
-// exact split of a double: hi = sign, exponent and leading 24 mantissa bits,
-// lo = the next 23 bits (the last 6 are dropped: about 2^-46 relative), by
-// integer operations and one FP32 subtraction (2^23 + m as a float's bits,
-// minus 2^23), so nothing runs on the FP64 pipe.  |p| below 2^-126 gives 0;
-// |p| at or above 2^128 gives +-infinity, NaN gives NaN.
-__device__ __forceinline__ FF ff_split(double p) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(p);
-    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
-    const int ex = (int)((hw >> 20) & 0x7ffu);
-    const unsigned sign = hw & 0x80000000u;
-    if (ex > 1150) {
-        const bool nan = ex == 2047 && ((hw & 0xfffffu) | lw) != 0u;
-        return {__uint_as_float(nan ? 0x7fc00000u : (sign | 0x7f800000u)), 0.0f};
-    }
-    if (ex < 897) return {0.0f, 0.0f};
-    const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
-    float lo = 0.0f;
-    if (ex >= 943) {   // lo = (mantissa bits 28..6 of the low word) * 2^(ex - 1069), sign of p
-        const float m = __uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)) - 8388608.0f;
-        const float scale = __uint_as_float((unsigned)(ex - 942) << 23);
-        lo = __uint_as_float(__float_as_uint(m * scale) | sign);
-    }
-    return {hi, lo};
-}
-
 // x - y rounded to FP32
 __device__ __forceinline__ float ff_diff(FF x, FF y) {
     const FF s = ff_two_sum(x.h, -y.h);
     return s.h + (s.l + (x.l - y.l));
+}
+
+// The pressure p.  FP64 cases store it in FP64.  The reduced-precision cases
+// store, in the same 8 bytes per cell, a double-float pair: hi and lo, two FP32
+// values (interleaved) with p = hi + lo and |lo| <= ulp(hi) / 2, about 48
+// significant bits, which their kernels read and update with FP32 arithmetic
+// only.  A kernel's compute type says which: FP64 kernels see doubles, FP32 and
+// BF16 kernels see pairs (pp_*).
+__device__ __forceinline__ FF pp_load(const double* p, int64_t c) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p) + c);
+    return {v.x, v.y};
+}
+// hi + lo + v, renormalised (Knuth's two-sum of hi and v, then the low parts folded in)
+__device__ __forceinline__ float2 pp_plus(float2 x, float v) {
+    const float s = x.x + v;
+    const float bb = s - x.x;
+    const float e = (x.x - (s - bb)) + (v - bb) + x.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ void pp_add(double* p, int64_t c, float v) {
+    float2* q = reinterpret_cast<float2*>(p) + c;
+    *q = pp_plus(*q, v);
+}
+// conversions (FP64 arithmetic: only for reads, writes and the small scalar paths)
+__device__ __forceinline__ double pp_get(const double* p, int64_t c) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p) + c);
+    return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ float2 pp_from_double(double x) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
 }
 
 // One multigrid level (pressure-like fields).
@@ -267,6 +272,9 @@ cudaError_t launch_destruction_vjp(const CaseDev& cd, StatePtrs x, double dt, co
 cudaError_t launch_explicit_vjp(const CaseDev& cd, StatePtrs x, StatePtrs y, double dt, const double* ybar,
                                 double* xbar, double* scratch, cudaStream_t s);
 cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaStream_t s);
+// the pressure of a reduced-precision case (double-float pairs) to / from FP64
+cudaError_t launch_p_to_double(const double* pp, double* dst, int64_t N, cudaStream_t s);
+cudaError_t launch_p_from_double(const double* src, double* pp, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 
 // multigrid kernels (mg_kernels.cu); inner = FVM_FP64 / FVM_FP32 / FVM_BF16_MIXED (type of r, e on all

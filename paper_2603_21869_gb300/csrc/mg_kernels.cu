@@ -190,10 +190,12 @@ __device__ int Resid0K<TB, TI>::run(const BlockAt& at) const {
         const uint32_t f = L.nbf[c];
         // neighbour loads first (clamped indices), then the FP64 stencil
         const int sy = L.n[0], sz = L.n[0] * L.n[1];
-        const double pP = __ldg(p + c);
-        const double xm = __ldg(p + c - (i > 0 ? 1 : 0)), xp = __ldg(p + c + (i < L.n[0] - 1 ? 1 : 0));
-        const double ym = __ldg(p + c - (j > 0 ? sy : 0)), yp = __ldg(p + c + (j < L.n[1] - 1 ? sy : 0));
-        const double zm = __ldg(p + c - (k > 0 ? sz : 0)), zp = __ldg(p + c + (k < L.n[2] - 1 ? sz : 0));
+        // (reduced-precision cases: p as double-float pairs, summed in FP64 on this small-grid path)
+        auto P = [&](int q) { return sizeof(TB) == 8 ? __ldg(p + q) : pp_get(p, q); };
+        const double pP = P(c);
+        const double xm = P(c - (i > 0 ? 1 : 0)), xp = P(c + (i < L.n[0] - 1 ? 1 : 0));
+        const double ym = P(c - (j > 0 ? sy : 0)), yp = P(c + (j < L.n[1] - 1 ? sy : 0));
+        const double zm = P(c - (k > 0 ? sz : 0)), zp = P(c + (k < L.n[2] - 1 ? sz : 0));
         const TB braw = ldg(b + c);
         C rc = (C)0, bc = (C)0;
         if (!is_solid(f)) {
@@ -475,7 +477,10 @@ __device__ void SweepK<TI, MODE, KZ>::run(const BlockAt& at) const {
                                                           col[kk + 2])) * iD;
             if (MODE == 0) eout[c] = from_c<TI, C>(v);
             else if (MODE == 2) z32[c] = (float)v;
-            else if (!solid) p[c] += (double)v;
+            else if (!solid) {
+                if constexpr (sizeof(TI) == 8) p[c] += (double)v;
+                else pp_add(p, c, (float)v);
+            }
         }
     }
 }
@@ -709,13 +714,21 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
                 VecW<TI, W>::store(eout, base + own, v);
             } else if (MODE == 2) {
                 VecW<float, W>::store(z32, base + own, v);
-            } else {
-                double2* pp = reinterpret_cast<double2*>(p + base + own);
+            } else {   // p (double-float pairs) += the correction, two cells per 16 bytes
+                float4* pp = reinterpret_cast<float4*>(p + base + own);
 #pragma unroll
                 for (int h = 0; h < W / 2; ++h) {
-                    double2 a = pp[h];
-                    if (!is_solid(fs[2 * h])) a.x += (double)v[2 * h];
-                    if (!is_solid(fs[2 * h + 1])) a.y += (double)v[2 * h + 1];
+                    float4 a = pp[h];
+                    if (!is_solid(fs[2 * h])) {
+                        const float2 x = pp_plus(make_float2(a.x, a.y), v[2 * h]);
+                        a.x = x.x;
+                        a.y = x.y;
+                    }
+                    if (!is_solid(fs[2 * h + 1])) {
+                        const float2 x = pp_plus(make_float2(a.z, a.w), v[2 * h + 1]);
+                        a.z = x.x;
+                        a.w = x.y;
+                    }
                     pp[h] = a;
                 }
             }
@@ -801,21 +814,20 @@ __device__ __forceinline__ void fcg_reduce(T (&s)[4], double* partials, SolveSta
 }
 
 // ------------------------------------------------------------------ level 0 residual in float-float
-// p is held in FP64; this path evaluates r = b - A p without the FP64 pipe
-// (1/64 of the FP32 rate here): each p value is split exactly by integer
-// operations into hi = its sign, exponent and leading 24 mantissa bits and
-// lo = the next 24 bits, and the stencil runs in double-float arithmetic
-// (Dekker's error-free sum and FMA-based product), about 2^-48 relative
-// accuracy.  As a difference form, A p = sum_a ih2_a ((P - g_lo) + (P - g_hi))
-// with g the neighbour (code 0), P (zero-gradient: no term) or -P
-// (zero-value: 2P), which equals both branches of A7.
+// The reduced-precision cases hold p as double-float pairs (pp_load); this
+// path evaluates r = b - A p without the FP64 pipe (1/64 of the FP32 rate
+// here): the stencil runs in double-float arithmetic (Dekker's error-free sum
+// and FMA-based product), about 2^-48 relative accuracy.  As a difference
+// form, A p = sum_a ih2_a ((P - g_lo) + (P - g_hi)) with g the neighbour
+// (code 0), P (zero-gradient: no term) or -P (zero-value: 2P), which equals
+// both branches of A7.
 __device__ __forceinline__ void ff_load4(const double* p, int c, FF (&o)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p + c));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + c) + 1);
-    o[0] = ff_split(a.x);
-    o[1] = ff_split(a.y);
-    o[2] = ff_split(b.x);
-    o[3] = ff_split(b.y);
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p + c));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p + c) + 1);
+    o[0] = {a.x, a.y};
+    o[1] = {a.z, a.w};
+    o[2] = {b.x, b.y};
+    o[3] = {b.z, b.w};
 }
 
 // P - ghost across one face: the neighbour (code 0), none (1) or 2P (2)
@@ -918,8 +930,8 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
         ff_load4(pp, base + op, yp);
         const float4 bq = __ldg(reinterpret_cast<const float4*>(b + base + own));
         const uint2 fw = __ldg(reinterpret_cast<const uint2*>(nbf + base + own));
-        const FF xls = lane == 0 ? ff_split(__ldg(pp + base + xl)) : FF{0.0f, 0.0f};
-        const FF xrs = lane == LR - 1 ? ff_split(__ldg(pp + base + xr)) : FF{0.0f, 0.0f};
+        const FF xls = lane == 0 ? pp_load(pp, base + xl) : FF{0.0f, 0.0f};
+        const FF xrs = lane == LR - 1 ? pp_load(pp, base + xr) : FF{0.0f, 0.0f};
         ff_load4(pp, min(k + 2, nz - 1) * sz + own, en);
         FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1, LR), __shfl_up_sync(0xffffffffu, ec[3].l, 1, LR)};
         FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1, LR), __shfl_down_sync(0xffffffffu, ec[0].l, 1, LR)};
@@ -1110,12 +1122,20 @@ struct FcgUpdVK {
 #pragma unroll
         for (int t = 0; t < W; ++t) d[t] = fma(-beta, dv[t], zv[t]);
         VecW<TZ, W>::store(dp, c, d);
-        double2* pp = reinterpret_cast<double2*>(p + c);
+        float4* pp = reinterpret_cast<float4*>(p + c);   // p as double-float pairs, two cells per 16 bytes
 #pragma unroll
         for (int h = 0; h < W / 2; ++h) {
-            double2 u = pp[h];
-            if (!is_solid(fs[2 * h])) u.x += (double)(alpha * d[2 * h]);
-            if (!is_solid(fs[2 * h + 1])) u.y += (double)(alpha * d[2 * h + 1]);
+            float4 u = pp[h];
+            if (!is_solid(fs[2 * h])) {
+                const float2 x = pp_plus(make_float2(u.x, u.y), alpha * d[2 * h]);
+                u.x = x.x;
+                u.y = x.y;
+            }
+            if (!is_solid(fs[2 * h + 1])) {
+                const float2 x = pp_plus(make_float2(u.z, u.w), alpha * d[2 * h + 1]);
+                u.z = x.x;
+                u.w = x.y;
+            }
             pp[h] = u;
         }
     }
@@ -1670,7 +1690,10 @@ struct FcgUpdK {
         const int c = i + L.n[0] * (j + L.n[1] * k);
         const double alpha = st->g_alpha, beta = st->g_beta;
         const double d = to_c<double>(ldg(z + c)) - (beta != 0.0 ? beta * to_c<double>(dp[c]) : 0.0);
-        if (!is_solid(L.nbf[c])) p[c] += alpha * d;
+        if (!is_solid(L.nbf[c])) {
+            if constexpr (sizeof(TZ) == 8) p[c] += alpha * d;
+            else pp_add(p, c, (float)(alpha * d));
+        }
         dp[c] = from_c<TZ, double>(d);
     }
 };
@@ -1737,11 +1760,14 @@ struct ProlongNearestToPK {
         int i, j, k;
         if (!cell3(Lf, at, i, j, k)) return;
         const int c = i + Lf.n[0] * (j + Lf.n[1] * k);
-        if (!is_solid(Lf.nbf[c])) p[c] += to_c<double>(ldg(ec + parent_of(Lf, Lc, i, j, k)));
+        if (is_solid(Lf.nbf[c])) return;
+        if constexpr (sizeof(TI) == 8) p[c] += to_c<double>(ldg(ec + parent_of(Lf, Lc, i, j, k)));
+        else pp_add(p, c, to_c<float>(ldg(ec + parent_of(Lf, Lc, i, j, k))));
     }
 };
 
-// unweighted Jacobi sweep on the FP64 pressure, out of place: q = p + (b - A p) / D
+// unweighted Jacobi sweep on the pressure, out of place: q = p + (b - A p) / D (copied back by CopyPK,
+// eight bytes per cell in either storage)
 template <class TB>
 struct JacobiPK {
     static constexpr int kThreads = BX * BY * BZ;
@@ -1761,12 +1787,16 @@ struct JacobiPK {
             q[c] = 0.0;
             return;
         }
+        // (reduced-precision cases: p and q as double-float pairs, the sweep in FP64)
+        auto P = [&](int x) { return sizeof(TB) == 8 ? __ldg(p + x) : pp_get(p, x); };
         const int sy = L.n[0], sz = L.n[0] * L.n[1];
-        const double pP = __ldg(p + c);
-        const double xm = __ldg(p + c - (i > 0 ? 1 : 0)), xp = __ldg(p + c + (i < L.n[0] - 1 ? 1 : 0));
-        const double ym = __ldg(p + c - (j > 0 ? sy : 0)), yp = __ldg(p + c + (j < L.n[1] - 1 ? sy : 0));
-        const double zm = __ldg(p + c - (k > 0 ? sz : 0)), zp = __ldg(p + c + (k < L.n[2] - 1 ? sz : 0));
-        q[c] = pP + (to_c<double>(ldg(b + c)) - A7<double>(L, f, pP, xm, xp, ym, yp, zm, zp)) * L.inv_D;
+        const double pP = P(c);
+        const double xm = P(c - (i > 0 ? 1 : 0)), xp = P(c + (i < L.n[0] - 1 ? 1 : 0));
+        const double ym = P(c - (j > 0 ? sy : 0)), yp = P(c + (j < L.n[1] - 1 ? sy : 0));
+        const double zm = P(c - (k > 0 ? sz : 0)), zp = P(c + (k < L.n[2] - 1 ? sz : 0));
+        const double v = pP + (to_c<double>(ldg(b + c)) - A7<double>(L, f, pP, xm, xp, ym, yp, zm, zp)) * L.inv_D;
+        if constexpr (sizeof(TB) == 8) q[c] = v;
+        else reinterpret_cast<float2*>(q)[c] = pp_from_double(v);
     }
 };
 
@@ -1785,6 +1815,16 @@ struct CopyPK {
         p[c] = q[c];
     }
 };
+
+__global__ void k_p_to_double(const double* __restrict__ pp, double* __restrict__ dst, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) dst[c] = pp_get(pp, c);
+}
+
+__global__ void k_p_from_double(const double* __restrict__ src, double* __restrict__ pp, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) reinterpret_cast<float2*>(pp)[c] = pp_from_double(src[c]);
+}
 
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, int64_t N) {
@@ -2110,5 +2150,15 @@ cudaError_t launch_convert(int sp, int dp, const void* src, void* dst, int64_t N
     if (sp == FVM_FP64 && dp == FVM_FP32) k_convert<double, float><<<nb, 256, 0, s>>>((const double*)src, (float*)dst, N);
     else if (sp == FVM_FP32 && dp == FVM_FP64) k_convert<float, double><<<nb, 256, 0, s>>>((const float*)src, (double*)dst, N);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p_to_double(const double* pp, double* dst, int64_t N, cudaStream_t s) {
+    k_p_to_double<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(pp, dst, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p_from_double(const double* src, double* pp, int64_t N, cudaStream_t s) {
+    k_p_from_double<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(src, pp, N);
     return cudaGetLastError();
 }

@@ -1881,8 +1881,11 @@ fvm_status fvm_read_fields(fvm_case* c, unsigned mask, double* host_out, size_t 
     size_t off = 0;
     for (int f = 0; f < 7; ++f) {
         if (!(mask & (1u << f))) continue;
-        if (f == FVM_P) {
+        if (f == FVM_P && c->prec == FVM_FP64) {
             CUDA_TRY(cudaMemcpyAsync(host_out + off, c->p, N * 8, cudaMemcpyDeviceToHost, c->stream));
+        } else if (f == FVM_P) {   // double-float pairs to FP64
+            CUDA_TRY(launch_p_to_double(c->p, c->staging, N, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(host_out + off, c->staging, N * 8, cudaMemcpyDeviceToHost, c->stream));
         } else {
             // (stream order: the next field's pack waits for this copy out of the staging buffer)
             CUDA_TRY(launch_pack(c->prec, c->cur[field_slot(f)], c->staging, N, c->stream));
@@ -1905,8 +1908,11 @@ fvm_status fvm_write_fields(fvm_case* c, unsigned mask, const double* host_in, s
     size_t off = 0;
     for (int f = 0; f < 7; ++f) {
         if (!(mask & (1u << f))) continue;
-        if (f == FVM_P) {
+        if (f == FVM_P && c->prec == FVM_FP64) {
             CUDA_TRY(cudaMemcpyAsync(c->p, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
+        } else if (f == FVM_P) {   // FP64 to double-float pairs
+            CUDA_TRY(cudaMemcpyAsync(c->staging, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(launch_p_from_double(c->staging, c->p, N, c->stream));
         } else {
             // (stream order: the next field's copy into the staging buffer waits for this unpack)
             CUDA_TRY(cudaMemcpyAsync(c->staging, host_in + off, N * 8, cudaMemcpyHostToDevice, c->stream));

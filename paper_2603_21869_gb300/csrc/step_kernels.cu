@@ -547,14 +547,14 @@ __device__ __forceinline__ double p_across(const LevelDev& L, const double* p, u
     return __ldg(p + c + side * stride);
 }
 
-// the same in float-float (P: the cell's own value, split)
+// the same in float-float, p held as double-float pairs (P: the cell's own value)
 __device__ __forceinline__ FF p_across_ff(const LevelDev& L, const double* p, uint32_t f, int c, int a, int side,
                                           FF P) {
     const uint32_t code = (f >> (2 * (2 * a + (side > 0 ? 1 : 0)))) & 3u;
     if (code == 1u) return P;
     if (code == 2u) return FF{-P.h, -P.l};
     const int stride = a == 0 ? 1 : (a == 1 ? L.n[0] : L.n[0] * L.n[1]);
-    return ff_split(__ldg(p + c + side * stride));
+    return pp_load(p, c + side * stride);
 }
 
 template <class S, class C>
@@ -581,10 +581,10 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
         for (int a = 0; a < 3; ++a) o[a][c] = q[a][c];
         return;
     }
-    const double pP = __ldg(p + c);
     const uint32_t f = L0.nbf[c];
     const C dt = dt_of<C>(dt_state, 0);
     if constexpr (sizeof(C) == 8) {
+        const double pP = __ldg(p + c);
         for (int a = 0; a < 3; ++a) {
             C g = (C)0;
             if (cd.active[a]) {
@@ -597,8 +597,8 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
             o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
         }
     } else {
-        // FP32 fields: the FP64 pressure differences in float-float, rounded once
-        const FF P = ff_split(pP);
+        // FP32 fields: the pressure differences in float-float (p as double-float pairs), rounded once
+        const FF P = pp_load(p, c);
         for (int a = 0; a < 3; ++a) {
             C g = (C)0;
             if (cd.active[a]) {
