@@ -629,6 +629,11 @@ template <> struct RawW<__nv_bfloat16, 8> {
     }
 };
 
+// Ask L2 for the line holding p (no register is tied up while it lands): the z-march kernels
+// name their rows of the plane three ahead, so that those loads later hit L2 instead of
+// waiting out a DRAM round trip.
+__device__ __forceinline__ void l2_prefetch(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <class TI, int MODE, int W>
 struct SweepVK {
     static constexpr int kThreads = TX * TY;
@@ -687,6 +692,12 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
         const C xls = lane == 0 ? to_c<C>(ldg(ein + base + xl)) : (C)0;
         const C xrs = lane == LR - 1 ? to_c<C>(ldg(ein + base + xr)) : (C)0;
         const typename R::T en = R::load(ein, min(k + 2, nz - 1) * sz + own);   // plane after next
+        if (k + 3 < k1 + 2 && k + 3 < nz) {   // this row of the plane three ahead
+            const int fb = (k + 3) * sz + own;
+            l2_prefetch(ein + fb);
+            l2_prefetch(r + fb);
+            l2_prefetch(nbf + fb);
+        }
         C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
         C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
         if (lane == 0) left = xls;
@@ -933,6 +944,13 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
         const FF xls = lane == 0 ? pp_load(pp, base + xl) : FF{0.0f, 0.0f};
         const FF xrs = lane == LR - 1 ? pp_load(pp, base + xr) : FF{0.0f, 0.0f};
         ff_load4(pp, min(k + 2, nz - 1) * sz + own, en);
+        if (k + 3 < k1 + 2 && k + 3 < nz) {   // this row of the plane three ahead
+            const int fb = (k + 3) * sz + own;
+            l2_prefetch(pp + fb);
+            l2_prefetch(pp + fb + 2);
+            l2_prefetch(b + fb);
+            l2_prefetch(nbf + fb);
+        }
         FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1, LR), __shfl_up_sync(0xffffffffu, ec[3].l, 1, LR)};
         FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1, LR), __shfl_down_sync(0xffffffffu, ec[0].l, 1, LR)};
         if (lane == 0) left = xls;
@@ -1059,6 +1077,13 @@ __device__ void FcgDotVK<TR, TZ, W>::run(const BlockAt& at) const {
         const C xls = lane == 0 ? to_c<C>(ldg(zz + base + xl)) : (C)0;
         const C xrs = lane == LR - 1 ? to_c<C>(ldg(zz + base + xr)) : (C)0;
         const typename R::T en = R::load(zz, min(k + 2, nz - 1) * sz + own);
+        if (k + 3 < k1 + 2 && k + 3 < nz) {   // this row of the plane three ahead
+            const int fb = (k + 3) * sz + own;
+            l2_prefetch(zz + fb);
+            l2_prefetch(r + fb);
+            l2_prefetch(nbf + fb);
+            if (have) l2_prefetch(dp + fb);
+        }
         C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
         C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
         if (lane == 0) left = xls;
