@@ -671,7 +671,7 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
     const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + W, nx - 1) + sy * jc;
     const bool last = i4 + W >= nx;   // the row's last cell is this thread's: its x+ ghost is itself
     const C ihx = LP<C>::ih2a(L, 0), ihy = LP<C>::ih2a(L, 1), ihz = LP<C>::ih2a(L, 2);
-    const C dg = LP<C>::diag(L), wJ = LP<C>::wJ(L), iD = LP<C>::iD(L);
+    const C dg = LP<C>::diag(L), wiD = LP<C>::wJ(L) * LP<C>::iD(L);
     // the functor's pointers in registers for the whole march
     const TI* const ein = this->ein;
     const TI* const r = this->r;
@@ -704,21 +704,37 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
         if (lane == LR - 1) right = xrs;
         if (last) right = R::get(ec, W - 1);
         C v[W];
+        uint32_t any = 0u;   // solid (bit 12) or irregular (bit 13) anywhere among the W cells
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-            const C eP = R::get(ec, t);
-            const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
-            const C zm = R::get(em, t), zp = R::get(ep, t), ya = R::get(ym, t), yb = R::get(yp, t);
-            C A;
-            if (!((fs[t] >> 13) & 1u)) {
+        for (int t = 0; t < W; ++t) any |= fs[t];
+        if (!(any & 0x3000u)) {
+            // every cell fluid, each ghost the clamped in-grid load: the plain stencil
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                const C eP = R::get(ec, t);
+                const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
                 C s = (xm + xp) * ihx;
-                s = fma(ya + yb, ihy, s);
-                s = fma(zm + zp, ihz, s);
-                A = fma(dg, eP, -s);
-            } else {
-                A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, zm, zp);
+                s = fma(R::get(ym, t) + R::get(yp, t), ihy, s);
+                s = fma(R::get(em, t) + R::get(ep, t), ihz, s);
+                v[t] = fma(wiD, R::get(rr, t) - fma(dg, eP, -s), eP);
             }
-            v[t] = is_solid(fs[t]) ? (C)0 : eP + wJ * (R::get(rr, t) - A) * iD;
+        } else {
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                const C eP = R::get(ec, t);
+                const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
+                const C zm = R::get(em, t), zp = R::get(ep, t), ya = R::get(ym, t), yb = R::get(yp, t);
+                C A;
+                if (!((fs[t] >> 13) & 1u)) {
+                    C s = (xm + xp) * ihx;
+                    s = fma(ya + yb, ihy, s);
+                    s = fma(zm + zp, ihz, s);
+                    A = fma(dg, eP, -s);
+                } else {
+                    A = A7_general<C>(L, fs[t], eP, xm, xp, ya, yb, zm, zp);
+                }
+                v[t] = is_solid(fs[t]) ? (C)0 : fma(wiD, R::get(rr, t) - A, eP);
+            }
         }
         if (in) {
             if (MODE == 0) {
@@ -1027,7 +1043,7 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
 template <class TR, class TZ, int W>
 struct FcgDotVK {
     static constexpr int kThreads = TX * TY;
-    static constexpr int kMinBlocks = 3;       // at most 80 registers
+    static constexpr int kMinBlocks = 4;       // at most 64 registers
     static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
     LevelDev L;
     const TZ* z;
@@ -1089,15 +1105,19 @@ __device__ void FcgDotVK<TR, TZ, W>::run(const BlockAt& at) const {
         if (lane == 0) left = xls;
         if (lane == LR - 1) right = xrs;
         if (lastc) right = R::get(ec, W - 1);
+        uint32_t any = 0u;   // solid (bit 12) or irregular (bit 13) anywhere among the W cells
+#pragma unroll
+        for (int t = 0; t < W; ++t) any |= fs[t];
         if (in) {
 #pragma unroll
             for (int t = 0; t < W; ++t) {
-                if (is_solid(fs[t])) continue;
+                const bool plain = !(any & 0x3000u);   // every cell fluid with in-grid ghosts
+                if (!plain && is_solid(fs[t])) continue;
                 const C eP = R::get(ec, t);
                 const C xm = t == 0 ? left : R::get(ec, t - 1), xp = t == W - 1 ? right : R::get(ec, t + 1);
                 const C ya = R::get(ym, t), yb = R::get(yp, t), za = R::get(em, t), zb = R::get(ep, t);
                 C A;
-                if (!((fs[t] >> 13) & 1u)) {
+                if (plain || !((fs[t] >> 13) & 1u)) {
                     C q = (xm + xp) * ihx;
                     q = fma(ya + yb, ihy, q);
                     q = fma(za + zb, ihz, q);
@@ -1305,7 +1325,7 @@ template <class TI, int W>
 struct RRVK {
     static constexpr int kThreads = TX * TY;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
-    static constexpr int kMinBlocks = 3;
+    static constexpr int kMinBlocks = 4;
     LevelDev Lf, Lc;
     const TI* e;
     const TI* r;
