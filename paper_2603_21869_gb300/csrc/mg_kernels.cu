@@ -893,6 +893,45 @@ __device__ __forceinline__ float ff_resid_regular(float b, FF P, FF xm, FF xp, F
     return u.h + (u.l - al);
 }
 
+// Two cells' double-float values side by side (cells 2q and 2q + 1 of a thread's four) and
+// the arithmetic of ff_axis / ff_resid_regular on both at once with the packed FP32
+// instructions (add / mul / fma .f32x2: one instruction for the pair, each lane rounded as the
+// scalar instruction rounds it).  A difference a - b is fma(b, -1, a), rounded once like the
+// scalar subtraction; a negation is a product by -1 (exact).
+struct FF2 {
+    float2 h, l;
+};
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p2neg(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
+__device__ __forceinline__ FF2 ff2_two_sum(float2 a, float2 b) {
+    const float2 s = p2add(a, b);
+    const float2 bb = p2sub(s, a);
+    return {s, p2add(p2sub(a, p2sub(s, bb)), p2sub(b, bb))};
+}
+__device__ __forceinline__ FF2 ff2_axis(FF2 P, FF2 a, FF2 b, float2 ihh, float2 ihl) {
+    const FF2 s = ff2_two_sum(a.h, b.h);
+    const float2 sl = p2add(s.l, p2add(a.l, b.l));
+    const FF2 d = ff2_two_sum(p2add(P.h, P.h), p2neg(s.h));
+    const float2 dl = p2add(d.l, p2sub(p2add(P.l, P.l), sl));
+    const float2 p = __fmul2_rn(d.h, ihh);
+    float2 e = __ffma2_rn(d.h, ihh, p2neg(p));
+    e = __ffma2_rn(d.h, ihl, e);
+    e = __ffma2_rn(dl, ihh, e);
+    return {p, e};
+}
+__device__ __forceinline__ float2 ff2_resid_regular(float2 b, FF2 P, FF2 xm, FF2 xp, FF2 ym, FF2 yp, FF2 zm, FF2 zp,
+                                                    const float2 ih[6]) {
+    const FF2 ax = ff2_axis(P, xm, xp, ih[0], ih[1]), ay = ff2_axis(P, ym, yp, ih[2], ih[3]);
+    const FF2 az = ff2_axis(P, zm, zp, ih[4], ih[5]);
+    const FF2 t = ff2_two_sum(ax.h, ay.h);
+    const FF2 t2 = ff2_two_sum(t.h, az.h);
+    const float2 al = p2add(p2add(t.l, t2.l), p2add(p2add(ax.l, ay.l), az.l));
+    const FF2 u = ff2_two_sum(b, p2neg(t2.h));
+    return p2add(u.h, p2sub(u.l, al));
+}
+__device__ __forceinline__ FF2 ff2_of(const FF& a, const FF& b) { return {make_float2(a.h, b.h), make_float2(a.l, b.l)}; }
+
 // the same for any cell, each face's ghost chosen by its code (out of line: rare)
 __device__ __noinline__ float ff_resid_general(uint32_t f, float b, FF P, FF xm, FF xp, FF ym, FF yp, FF zm, FF zp,
                                                FF ihx, FF ihy, FF ihz) {
@@ -942,6 +981,8 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
     const int xl = max(ic - 1, 0) + sy * jc, xr = min(ic + 4, nx - 1) + sy * jc;
     const bool lastc = i4 + 4 >= nx;
     const FF ihx = {L.ih2af[0], L.ih2alo[0]}, ihy = {L.ih2af[1], L.ih2alo[1]}, ihz = {L.ih2af[2], L.ih2alo[2]};
+    const float2 ih2[6] = {make_float2(ihx.h, ihx.h), make_float2(ihx.l, ihx.l), make_float2(ihy.h, ihy.h),
+                           make_float2(ihy.l, ihy.l), make_float2(ihz.h, ihz.h), make_float2(ihz.l, ihz.l)};
     const float wJ = LP<float>::wJ(L), iD = LP<float>::iD(L);
     const double* const pp = this->p;
     const uint16_t* const nbf = L.nbf;
@@ -975,15 +1016,33 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
         const FF xs[6] = {left, ec[0], ec[1], ec[2], ec[3], right};
         const uint32_t fs[4] = {fw.x & 0xffffu, fw.x >> 16, fw.y & 0xffffu, fw.y >> 16};
         const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
+        // b - A p: a pair of regular cells (code bit 13 clear) in the packed form, any other cell alone
+        float rfs[4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int t0 = 2 * q, t1 = t0 + 1;
+            if (!(((fs[t0] | fs[t1]) >> 13) & 1u)) {
+                const float2 rr = ff2_resid_regular(
+                    make_float2(bb[t0], bb[t1]), ff2_of(xs[t0 + 1], xs[t1 + 1]), ff2_of(xs[t0], xs[t1]),
+                    ff2_of(xs[t0 + 2], xs[t1 + 2]), ff2_of(ym[t0], ym[t1]), ff2_of(yp[t0], yp[t1]),
+                    ff2_of(em[t0], em[t1]), ff2_of(ep[t0], ep[t1]), ih2);
+                rfs[t0] = rr.x;
+                rfs[t1] = rr.y;
+            } else {
+#pragma unroll
+                for (int t = t0; t <= t1; ++t)
+                    rfs[t] = !((fs[t] >> 13) & 1u)
+                                 ? ff_resid_regular(bb[t], xs[t + 1], xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t], ihx,
+                                                    ihy, ihz)
+                                 : ff_resid_general(fs[t], bb[t], xs[t + 1], xs[t], xs[t + 2], ym[t], yp[t], em[t],
+                                                    ep[t], ihx, ihy, ihz);
+            }
+        }
         float rv[4], ev[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const uint32_t f = fs[t];
-            const FF P = xs[t + 1];
-            const float rf = !((f >> 13) & 1u)
-                                 ? ff_resid_regular(bb[t], P, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t], ihx, ihy, ihz)
-                                 : ff_resid_general(f, bb[t], P, xs[t], xs[t + 2], ym[t], yp[t], em[t], ep[t], ihx,
-                                                    ihy, ihz);
+            const float rf = rfs[t];
             const bool fluid = !is_solid(f);
             const float rc = fluid ? round_inner<TI>(rf) : 0.0f;
             rv[t] = rc;

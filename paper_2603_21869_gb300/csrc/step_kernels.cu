@@ -265,12 +265,57 @@ struct DestructionK {
     S* nut_out;   // nu_t of the updated k, omega (read by the explicit stage), or null
     S* b_out;     // the pressure right-hand side b = -div(u)/dt of the same velocity (Eq. pc_residual), or null
     __device__ void run(const BlockAt& at) const;
+    __device__ void cell(int i, int j, int k) const;
 };
+
+// k and omega after the semi-implicit destruction half step dt (Eqs. k_des_step, o_des_step) of
+// one cell, from its velocity gradient gu[i][a] = d u_i / d x_a and gkw = grad k . grad omega
+template <class C>
+__device__ __forceinline__ void des_update(const C gu[3][3], C gkw, C k, C om, C nu, C dt, C& knew, C& omnew) {
+    const C oms = omega_safe(om);
+    // k: chi_k, f_beta*, beta* (Eqs. k_des, beta_star)
+    const C chik = gkw / (oms * oms * oms);
+    C fbs = (C)1;
+    if (chik > (C)0) {
+        if (chik > (C)1e8) fbs = (C)(680.0 / 400.0);
+        else {
+            const C c2 = chik * chik;
+            fbs = qdiv((C)1 + (C)680 * c2, (C)1 + (C)400 * c2);
+        }
+    }
+    const C x = qdiv(re_t(k, om, nu), (C)kRbeta);
+    C bstar;
+    if (x > (C)1e4) bstar = (C)kBetaStarInf;
+    else {
+        const C x2 = x * x;
+        const C x4 = x2 * x2;
+        bstar = (C)kBetaStarInf * qdiv((C)(4.0 / 15.0) + x4, (C)1 + x4);
+    }
+    knew = qdiv(k, (C)1 + dt * bstar * fbs * om);
+    // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des).  With
+    // the rotation vector w (Omega v = w x v), Omega Omega = w w^T - |w|^2 I, so the trace is
+    // w^T S w - |w|^2 tr(S)
+    const C w1 = (C)0.5 * (gu[2][1] - gu[1][2]), w2 = (C)0.5 * (gu[0][2] - gu[2][0]);
+    const C w3 = (C)0.5 * (gu[1][0] - gu[0][1]);
+    const C s01 = (C)0.5 * (gu[0][1] + gu[1][0]), s02 = (C)0.5 * (gu[0][2] + gu[2][0]);
+    const C s12 = (C)0.5 * (gu[1][2] + gu[2][1]);
+    const C wsw = w1 * w1 * gu[0][0] + w2 * w2 * gu[1][1] + w3 * w3 * gu[2][2] +
+                  (C)2 * (w1 * w2 * s01 + w1 * w3 * s02 + w2 * w3 * s12);
+    const C tr = wsw - (w1 * w1 + w2 * w2 + w3 * w3) * (gu[0][0] + gu[1][1] + gu[2][2]);
+    const C bo = (C)kBetaStarInf * oms;
+    const C chiw = fabs(tr / (bo * bo * bo));
+    const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : qdiv((C)1 + (C)70 * chiw, (C)1 + (C)80 * chiw);
+    omnew = qdiv(om, (C)1 + dt * (C)kBeta * fb * om);
+}
 
 template <class S, class C>
 __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, at, i, j, k)) return;
+    if (cell3(cd, at, i, j, k)) cell(i, j, k);
+}
+
+template <class S, class C>
+__device__ void DestructionK<S, C>::cell(int i, int j, int k) const {
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     if (cd.tag[c]) {
@@ -312,44 +357,82 @@ __device__ void DestructionK<S, C>::run(const BlockAt& at) const {
     }
     if (b_out) b_out[c] = from_c<S, C>(-div / dt_of<C>(dt_state, 0));
     const C nu = prm<C>(cd.nu, cd.f.nu);
-    const C oms = omega_safe(P.om);
-    // k: chi_k, f_beta*, beta* (Eqs. k_des, beta_star)
-    const C chik = (gk[0] * gw[0] + gk[1] * gw[1] + gk[2] * gw[2]) / (oms * oms * oms);
-    C fbs = (C)1;
-    if (chik > (C)0) {
-        if (chik > (C)1e8) fbs = (C)(680.0 / 400.0);
-        else {
-            const C c2 = chik * chik;
-            fbs = qdiv((C)1 + (C)680 * c2, (C)1 + (C)400 * c2);
-        }
-    }
-    const C x = qdiv(re_t(P.k, P.om, nu), (C)kRbeta);
-    C bstar;
-    if (x > (C)1e4) bstar = (C)kBetaStarInf;
-    else {
-        const C x2 = x * x;
-        const C x4 = x2 * x2;
-        bstar = (C)kBetaStarInf * qdiv((C)(4.0 / 15.0) + x4, (C)1 + x4);
-    }
-    const C dt = dt_of<C>(dt_state, 1);
-    const C knew = qdiv(P.k, (C)1 + dt * bstar * fbs * P.om);
-    // omega: chi_omega = |Omega_ij Omega_jk S_ki| / (beta*_inf omega)^3, f_beta (Eq. o_des).  With
-    // the rotation vector w (Omega v = w x v), Omega Omega = w w^T - |w|^2 I, so the trace is
-    // w^T S w - |w|^2 tr(S)
-    const C w1 = (C)0.5 * (gu[2][1] - gu[1][2]), w2 = (C)0.5 * (gu[0][2] - gu[2][0]);
-    const C w3 = (C)0.5 * (gu[1][0] - gu[0][1]);
-    const C s01 = (C)0.5 * (gu[0][1] + gu[1][0]), s02 = (C)0.5 * (gu[0][2] + gu[2][0]);
-    const C s12 = (C)0.5 * (gu[1][2] + gu[2][1]);
-    const C wsw = w1 * w1 * gu[0][0] + w2 * w2 * gu[1][1] + w3 * w3 * gu[2][2] +
-                  (C)2 * (w1 * w2 * s01 + w1 * w3 * s02 + w2 * w3 * s12);
-    const C tr = wsw - (w1 * w1 + w2 * w2 + w3 * w3) * (gu[0][0] + gu[1][1] + gu[2][2]);
-    const C bo = (C)kBetaStarInf * oms;
-    const C chiw = fabs(tr / (bo * bo * bo));
-    const C fb = chiw > (C)1e30 ? (C)(70.0 / 80.0) : qdiv((C)1 + (C)70 * chiw, (C)1 + (C)80 * chiw);
-    const C omnew = qdiv(P.om, (C)1 + dt * (C)kBeta * fb * P.om);
+    C knew, omnew;
+    des_update<C>(gu, gk[0] * gw[0] + gk[1] * gw[1] + gk[2] * gw[2], P.k, P.om, nu, dt_of<C>(dt_state, 1), knew,
+                  omnew);
     k_out[c] = from_c<S, C>(knew);
     om_out[c] = from_c<S, C>(omnew);
-    if (nut_out) nut_out[c] = from_c<S, C>(nut_of(knew, omnew, prm<C>(cd.nu, cd.f.nu)));
+    if (nut_out) nut_out[c] = from_c<S, C>(nut_of(knew, omnew, nu));
+}
+
+// ------------------------------------------------------------------ four-cell form (FP32 fields)
+// The projection with four consecutive x cells per thread, in the multigrid vector kernels'
+// layout: a block of 32 x 8 threads, each warp covering row segments of 4 * LR cells (LR = 2^lrl
+// lanes, the widest segment of 128, 64, 32 or 16 cells that divides nx), x neighbours passed
+// between the lanes of a segment by shuffles and loaded by its two end lanes, rows j +- 1 and
+// planes k +- 1 read as 128-bit loads.  Every load takes coordinates clamped into the grid.
+// Every thread computes all four cells from the values in registers (so the shuffles see all
+// lanes); a regular cell (fluid, every level-0 face code of an active axis 0) keeps that result,
+// since its neighbours are the in-grid cells the registers hold, and any other cell of the group
+// runs the one-cell code instead.  A collapsed axis (n = 1) clamps both neighbours to the cell
+// itself, so its differences vanish as in the one-cell code.  Needs nx % 4 = 0.  (The same form
+// of the destruction and explicit kernels measured slower than their one-cell forms on the
+// 512 x 256 x 128 room: their cost is the closure arithmetic, which four cells per thread do not
+// reduce, while a warp holding a row's end cell waits for that cell's one-cell code.)
+constexpr int VX = 32, VY = 8;
+
+struct Idx4 {
+    int c, ym, yp, zm, zp, xl, xr;   // the group's first cell, the rows j -+ 1 and planes k -+ 1, the x end cells
+    int LR;
+    bool lo, hi;                     // the segment's first / last lane
+};
+
+struct Grp4 {
+    int i, j, k;   // the group's first cell (coordinates clamped into the grid)
+    bool in;       // the thread's group lies in the grid
+    Idx4 x;
+};
+
+__device__ __forceinline__ Grp4 group4(const int n[3], const BlockAt& at, int lrl) {
+    Grp4 g;
+    const int nx = n[0], ny = n[1], nz = n[2];
+    const int LR = 1 << lrl, lane = threadIdx.x & (LR - 1), sub = threadIdx.x >> lrl;
+    const int i4 = (int)at.b.x * (4 * LR) + lane * 4;
+    const int j = (((int)at.b.y * VY + (int)threadIdx.y) << (5 - lrl)) + sub;
+    const int k = min((int)at.b.z, nz - 1);
+    g.in = i4 < nx && j < ny && (int)at.b.z < nz;
+    g.i = min(i4, nx - 4);
+    g.j = min(j, ny - 1);
+    g.k = k;
+    const int sy = nx, sz = nx * ny;
+    const int row = sy * g.j + sz * k;
+    g.x.c = g.i + row;
+    g.x.ym = g.i + sy * max(g.j - 1, 0) + sz * k;
+    g.x.yp = g.i + sy * min(g.j + 1, ny - 1) + sz * k;
+    g.x.zm = g.i + sy * g.j + sz * max(k - 1, 0);
+    g.x.zp = g.i + sy * g.j + sz * min(k + 1, nz - 1);
+    g.x.xl = max(g.i - 1, 0) + row;
+    g.x.xr = min(g.i + 4, nx - 1) + row;
+    g.x.LR = LR;
+    g.x.lo = lane == 0;
+    g.x.hi = lane == LR - 1;
+    return g;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p, int c) { return __ldg(reinterpret_cast<const float4*>(p + c)); }
+__device__ __forceinline__ void st4(float* p, int c, const float v[4]) {
+    *reinterpret_cast<float4*>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void un4(const float4& v, float o[4]) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+// which of the group's four cells are regular (bit t: cell t); 15 when all are
+__device__ __forceinline__ uint32_t regular4(const CaseDev& cd, int c) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(cd.nbf0 + c));
+    const uint32_t m = cd.regular_mask;
+    return ((w.x & m) == 0u ? 1u : 0u) | (((w.x >> 16) & m) == 0u ? 2u : 0u) | ((w.y & m) == 0u ? 4u : 0u) |
+           (((w.y >> 16) & m) == 0u ? 8u : 0u);
 }
 
 // ------------------------------------------------------------------ explicit stage
@@ -402,12 +485,43 @@ struct ExplicitK {
     double wb, ws;
     float wbf, wsf;
     __device__ void run(const BlockAt& at) const;
+    __device__ void cell(int i, int j, int k) const;
 };
+
+// The cell update of the explicit stage from the summed face fluxes rhs (Algorithm 2): the
+// production of k and omega (Eqs. k_gen, o_gen, a) with S2 = 2 S_ij S_ij, Boussinesq buoyancy
+// -g beta_T (T - T_ref), the forward-Euler step dt and the lower bounds of k and omega
+template <class C>
+__device__ __forceinline__ void exp_update(const CaseDev& cd, const St<C>& P, C nutP, C S2, C rhs[6], C dt, C o[6]) {
+    const C nu = prm<C>(cd.nu, cd.f.nu);
+    const C Gk = nutP * S2;
+    const C ret = re_t(P.k, P.om, nu);
+    const C rw = qdiv(ret, (C)kRw);
+    const C alpha = qdiv((C)kAlphaInf, alpha_star_of(ret)) * qdiv((C)kAlpha0 + rw, (C)1 + rw);
+    rhs[4] += Gk;
+    rhs[5] += qdiv(alpha * P.om, P.k) * Gk;
+    const C dT = P.T - prm<C>(cd.T_ref, cd.f.T_ref);
+    rhs[0] += prm<C>(cd.gb[0], cd.f.gb[0]) * dT;
+    rhs[1] += prm<C>(cd.gb[1], cd.f.gb[1]) * dT;
+    rhs[2] += prm<C>(cd.gb[2], cd.f.gb[2]) * dT;
+    o[0] = P.u + dt * rhs[0];
+    o[1] = P.v + dt * rhs[1];
+    o[2] = P.w + dt * rhs[2];
+    o[3] = P.T + dt * rhs[3];
+    const C kn = P.k + dt * rhs[4];
+    const C on = P.om + dt * rhs[5];
+    o[4] = kn > (C)kKMin ? kn : (C)kKMin;
+    o[5] = on > (C)kOmegaMin ? on : (C)kOmegaMin;
+}
 
 template <class S, class C, bool kBlend>
 __device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, at, i, j, k)) return;
+    if (cell3(cd, at, i, j, k)) cell(i, j, k);
+}
+
+template <class S, class C, bool kBlend>
+__device__ void ExplicitK<S, C, kBlend>::cell(int i, int j, int k) const {
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     const St<C> P = load_state<S, C>(in, c);
     S* o[6];
@@ -458,7 +572,7 @@ __device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
             omw = ow > omw ? ow : omw;
         }
     }
-    // production (Eqs. k_gen, o_gen, a) with S^2 = 2 S_ij S_ij
+    // S^2 = 2 S_ij S_ij
     C S2 = (C)0;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -466,38 +580,14 @@ __device__ void ExplicitK<S, C, kBlend>::run(const BlockAt& at) const {
             S2 += s * s;
         }
     S2 = (C)2 * S2;
-    const C Gk = nutP * S2;
-    const C ret = re_t(P.k, P.om, nu);
-    const C rw = qdiv(ret, (C)kRw);
-    const C alpha = qdiv((C)kAlphaInf, alpha_star_of(ret)) * qdiv((C)kAlpha0 + rw, (C)1 + rw);
-    rhs[4] += Gk;
-    rhs[5] += qdiv(alpha * P.om, P.k) * Gk;
-    // Boussinesq buoyancy -g beta_T (T - T_ref)
-    const C dT = P.T - prm<C>(cd.T_ref, cd.f.T_ref);
-    rhs[0] += prm<C>(cd.gb[0], cd.f.gb[0]) * dT;
-    rhs[1] += prm<C>(cd.gb[1], cd.f.gb[1]) * dT;
-    rhs[2] += prm<C>(cd.gb[2], cd.f.gb[2]) * dT;
-    const C dt = dt_of<C>(dt_state, 0);
-    C un = P.u + dt * rhs[0];
-    C vn = P.v + dt * rhs[1];
-    C wn = P.w + dt * rhs[2];
-    C Tn = P.T + dt * rhs[3];
-    C kn = P.k + dt * rhs[4];
-    C on = P.om + dt * rhs[5];
-    kn = kn > (C)kKMin ? kn : (C)kKMin;
-    on = on > (C)kOmegaMin ? on : (C)kOmegaMin;
+    C nw[6];
+    exp_update<C>(cd, P, nutP, S2, rhs, dt_of<C>(dt_state, 0), nw);
     if constexpr (kBlend) {
         const C a = prm<C>(wb, wbf), b = prm<C>(ws, wsf);
-        un = a * to_c<C>(((const S*)base.f[0])[c]) + b * un;
-        vn = a * to_c<C>(((const S*)base.f[1])[c]) + b * vn;
-        wn = a * to_c<C>(((const S*)base.f[2])[c]) + b * wn;
-        Tn = a * to_c<C>(((const S*)base.f[3])[c]) + b * Tn;
-        kn = a * to_c<C>(((const S*)base.f[4])[c]) + b * kn;
-        on = a * to_c<C>(((const S*)base.f[5])[c]) + b * on;
+        for (int f = 0; f < 6; ++f) nw[f] = a * to_c<C>(((const S*)base.f[f])[c]) + b * nw[f];
     }
-    if (omw > (C)0) on = omw;
-    o[0][c] = from_c<S, C>(un); o[1][c] = from_c<S, C>(vn); o[2][c] = from_c<S, C>(wn);
-    o[3][c] = from_c<S, C>(Tn); o[4][c] = from_c<S, C>(kn); o[5][c] = from_c<S, C>(on);
+    if (omw > (C)0) nw[5] = omw;
+    for (int f = 0; f < 6; ++f) o[f][c] = from_c<S, C>(nw[f]);
 }
 
 // ------------------------------------------------------------------ pressure RHS
@@ -568,12 +658,17 @@ struct ProjectK {
     const double* p;
     const double* dt_state;
     __device__ void run(const BlockAt& at) const;
+    __device__ void cell(int i, int j, int k) const;
 };
 
 template <class S, class C>
 __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
     int i, j, k;
-    if (!cell3(cd, at, i, j, k)) return;
+    if (cell3(cd, at, i, j, k)) cell(i, j, k);
+}
+
+template <class S, class C>
+__device__ void ProjectK<S, C>::cell(int i, int j, int k) const {
     const int c = i + cd.n[0] * (j + cd.n[1] * k);
     S* o[3] = {(S*)out.f[0], (S*)out.f[1], (S*)out.f[2]};
     const S* q[3] = {(const S*)in.f[0], (const S*)in.f[1], (const S*)in.f[2]};
@@ -608,6 +703,85 @@ __device__ void ProjectK<S, C>::run(const BlockAt& at) const {
                 g = 0.5f * (ff_diff(pr, P) * ih + ff_diff(P, pl) * ih);
             }
             o[a][c] = from_c<S, C>(to_c<C>(ldg(q[a] + c)) - dt * g);
+        }
+    }
+}
+
+// The projection, four cells per thread (FP32 fields, p as double-float pairs): the layout of
+// the other four-cell forms, the pairs of the x neighbours passed between lanes
+struct ProjectVK {
+    static constexpr int kThreads = VX * VY;
+    static constexpr bool kNoShared = true;   // run() uses no shared memory
+    static constexpr int kMinBlocks = 4;
+    __device__ bool live() const { return true; }
+    ProjectK<float, float> s;   // the arguments; its one-cell code serves the irregular groups
+    int lrl;
+    __device__ void run(const BlockAt& at) const;
+};
+
+// the pairs of four consecutive cells from c (16-byte aligned: c % 4 = 0)
+__device__ __forceinline__ void pp4(const double* p, int c, FF o[4]) {
+    const float4* q = reinterpret_cast<const float4*>(p + c);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    o[0] = {a.x, a.y};
+    o[1] = {a.z, a.w};
+    o[2] = {b.x, b.y};
+    o[3] = {b.z, b.w};
+}
+
+__device__ void ProjectVK::run(const BlockAt& at) const {
+    const CaseDev& cd = s.cd;
+    const Grp4 g = group4(cd.n, at, lrl);
+    const Idx4& x = g.x;
+    FF P[4];
+    pp4(s.p, x.c, P);
+    float grad[3][4];
+    {
+        FF left, right;
+        left.h = __shfl_up_sync(0xffffffffu, P[3].h, 1, x.LR);
+        left.l = __shfl_up_sync(0xffffffffu, P[3].l, 1, x.LR);
+        right.h = __shfl_down_sync(0xffffffffu, P[0].h, 1, x.LR);
+        right.l = __shfl_down_sync(0xffffffffu, P[0].l, 1, x.LR);
+        if (x.lo) left = pp_load(s.p, x.xl);
+        if (x.hi) right = pp_load(s.p, x.xr);
+        const float ih = cd.f.inv_h[0];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const FF L = t == 0 ? left : P[t - 1], R = t == 3 ? right : P[t + 1];
+            grad[0][t] = 0.5f * (ff_diff(R, P[t]) * ih + ff_diff(P[t], L) * ih);
+        }
+    }
+#pragma unroll
+    for (int a = 1; a < 3; ++a) {
+        FF L[4], R[4];
+        pp4(s.p, a == 1 ? x.ym : x.zm, L);
+        pp4(s.p, a == 1 ? x.yp : x.zp, R);
+        const float ih = cd.f.inv_h[a];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) grad[a][t] = 0.5f * (ff_diff(R[t], P[t]) * ih + ff_diff(P[t], L[t]) * ih);
+    }
+    if (!g.in) return;
+    const uint32_t reg = regular4(cd, x.c);
+    const float dt = dt_of<float>(s.dt_state, 0);
+    float v[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        un4(ld4((const float*)s.in.f[a], x.c), v[a]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[a][t] = v[a][t] - dt * (cd.active[a] ? grad[a][t] : 0.f);
+    }
+    if (reg == 15u) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) st4((float*)s.out.f[a], x.c, v[a]);
+        return;
+    }
+#pragma unroll 1
+    for (int t = 0; t < 4; ++t) {
+        if (reg & (1u << t)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ((float*)s.out.f[a])[x.c + t] = v[a][t];
+        } else {
+            s.cell(g.i + t, g.j, g.k);
         }
     }
 }
@@ -1264,6 +1438,19 @@ inline dim3 grid3(const CaseDev& cd) {
 }
 const dim3 kBlock3(BX, BY, BZ);
 
+// the four-cell forms: FP32 fields and nx % 4 = 0
+inline bool four_cells(int prec, const CaseDev& cd) { return prec != FVM_FP64 && cd.n[0] % 4 == 0; }
+// log2 of the lanes of a row segment: the widest of 128, 64, 32 and 16 cells that divides nx
+inline int seg_lrl(int nx) {
+    for (int l = 5; l >= 2; --l)
+        if (nx % (4 << l) == 0) return l;
+    return 5;
+}
+inline dim3 grid4(const CaseDev& cd, int lrl) {
+    const int wx = 4 << lrl, wy = VY << (5 - lrl);
+    return dim3((unsigned)((cd.n[0] + wx - 1) / wx), (unsigned)((cd.n[1] + wy - 1) / wy), (unsigned)cd.n[2]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1323,6 +1510,11 @@ cudaError_t launch_rhs(int prec, const CaseDev& cd, StatePtrs in, void* b, const
 cudaError_t launch_project(int prec, const CaseDev& cd, const LevelDev& L0, StatePtrs in, StatePtrs out,
                            const double* p, const double* dt_state, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
+    if (four_cells(prec, cd)) {
+        const int lrl = seg_lrl(cd.n[0]);
+        return launch_k(ProjectVK{ProjectK<float, float>{cd, L0, in, out, p, dt_state}, lrl}, grid4(cd, lrl),
+                        dim3(VX, VY), 0, s);
+    }
     DISPATCH(prec, err = launch_k(ProjectK<S, C>{cd, L0, in, out, p, dt_state}, grid3(cd), kBlock3, 0, s));
     return err;
 }
