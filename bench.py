@@ -221,11 +221,11 @@ def run_reference(args, spec, label, rank, ws, workload="channel"):
 
 
 def parse_params(text):
-    """PRE,POST,INNER,PLANES,KRYLOV[,COARSE] -> six ints (COARSE defaults to 0)."""
+    """PRE,POST,INNER,PLANES,KRYLOV[,COARSE[,SMOOTHER]] -> seven ints (COARSE, SMOOTHER default to 0)."""
     v = [int(x) for x in text.split(",")]
-    if len(v) not in (5, 6):
-        raise SystemExit("--params wants PRE,POST,INNER,PLANES,KRYLOV[,COARSE]")
-    return tuple(v + [0] * (6 - len(v)))
+    if len(v) not in (5, 6, 7):
+        raise SystemExit("--params wants PRE,POST,INNER,PLANES,KRYLOV[,COARSE[,SMOOTHER]]")
+    return tuple(v + [0] * (7 - len(v)))
 
 
 def breakdown(prof, nsteps, traffic=None):
@@ -280,18 +280,18 @@ def run_batched(args, rank, ws, local, dist):
     specs = cases.batched_channels(args.cases, seed=rank, precision=prec, mg_levels=5)
     tuning = None
     if args.params:
-        pre, post, inner, _planes, kry, coarse = parse_params(args.params)
-        specs = [sp.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, krylov=kry, coarse_sweeps=coarse)
-                 for sp in specs]
+        pre, post, inner, _planes, kry, coarse, smoother = parse_params(args.params)
+        specs = [sp.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, krylov=kry, coarse_sweeps=coarse,
+                            smoother=smoother) for sp in specs]
         tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "krylov": kry,
-                  "coarse_sweeps": coarse, "fixed": True}
+                  "coarse_sweeps": coarse, "smoother": smoother, "fixed": True}
     elif not args.no_autotune:
         # sweep counts, V-cycles per outer residual and planes per block, measured on the largest case
         _, tuning = binding.autotune(max(specs, key=lambda sp: sp.cells), steps=3)
         # (the planes per block are left to the batch rule: a batch has blocks to spare)
         specs = [sp.replace(pre_sweeps=tuning["pre_sweeps"], post_sweeps=tuning["post_sweeps"],
                             inner_cycles=tuning["inner_cycles"], krylov=tuning["krylov"],
-                            coarse_sweeps=tuning["coarse_sweeps"]) for sp in specs]
+                            coarse_sweeps=tuning["coarse_sweeps"], smoother=tuning["smoother"]) for sp in specs]
     N = sum(sp.cells for sp in specs)
     cs = [binding.Case(sp, stream=stream.cuda_stream) for sp in specs]
     batch = binding.Batch(cs, stream=stream.cuda_stream)
@@ -633,7 +633,7 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=5, help="steps of the per-field comparison with FP64")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep V(3,3), the default grouping and plane rule")
-    ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV[,COARSE]",
+    ap.add_argument("--params", default=None, metavar="PRE,POST,INNER,PLANES,KRYLOV[,COARSE[,SMOOTHER]]",
                     help="fixed multigrid parameters instead of the autotuner's (e.g. for profiling runs, where "
                          "the profiler's overhead would distort the autotuner's timings)")
     ap.add_argument("--krylov", default="auto", choices=["auto", "0", "1"],
@@ -689,12 +689,12 @@ def main():
     rank, ws, local, dist = dist_setup()
     tuning = None
     if args.params:
-        pre, post, inner, planes, kry, coarse = parse_params(args.params)
+        pre, post, inner, planes, kry, coarse, smoother = parse_params(args.params)
         spec = spec.replace(pre_sweeps=pre, post_sweeps=post, inner_cycles=inner, sweep_planes=planes, krylov=kry,
-                            coarse_sweeps=coarse)
+                            coarse_sweeps=coarse, smoother=smoother)
         label = label.replace("V(3,3)", f"V({pre},{post})")
         tuning = {"pre_sweeps": pre, "post_sweeps": post, "inner_cycles": inner, "sweep_planes": planes,
-                  "krylov": kry, "coarse_sweeps": coarse, "fixed": True}
+                  "krylov": kry, "coarse_sweeps": coarse, "smoother": smoother, "fixed": True}
     elif args.impl == "ours" and not args.no_autotune and spec.nz > 1:
         # smoother sweeps, V-cycles per outer residual and planes per block, measured (fvm_autotune)
         from paper_2603_21869_gb300 import binding as _b, build as _bd

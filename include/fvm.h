@@ -134,7 +134,14 @@ typedef struct {
                                         a forward-Euler update (clamps and wall omega included)
                                         combined with the stage-0 state.  3 keeps a third copy of
                                         the six state fields. */
-    int32_t reserved2;               /* 0 */
+    int32_t smoother;                /* 0: every weighted-Jacobi sweep takes jacobi_weight (Eq.
+                                        jacobi_pc); 1: sweep i of the n on one side of a level takes
+                                        1 / x_i, x_i the roots (largest first before the coarse
+                                        correction, smallest first after it) of the degree-n
+                                        Chebyshev polynomial of [1/4, 2], which bounds the spectrum
+                                        of D^-1 A: the n sweeps damp its upper part by
+                                        1 / T_n(9/7).  At most 16 sweeps a side.  Not with
+                                        mg_variant 1.  An addition beyond the paper. */
     double  mg_rel_tol;              /* ||b - A p|| / ||b|| target */
     double  jacobi_weight;           /* <= 0: 6/7 in 3D, 4/5 in 2D */
     uint64_t seed;                   /* SplitMix64 seed of the initial perturbation */
@@ -369,12 +376,13 @@ fvm_status fvm_case_get_info(const fvm_case* c, fvm_case_info* out);
    after two untimed ones, timed with CUDA events, `steps` steps each.
    Pass 1: V(nu, nu) for nu = 2, 3, 4 times the V-cycles per FP64 outer
    residual (1..4 with reduced-precision corrections, 1 in FP64) times the
-   flexible-CG acceleration off / on (off only with mg_variant 1); pass 2: the
+   flexible-CG acceleration off / on times the constant / Chebyshev sweep
+   weights (both off only with mg_variant 1); pass 2: the
    z planes per block of the four-cell level kernels (the rule, 1 .. 32)
    with the best pass-1 choice; pass 3: 1 and 2 sweeps on the levels below
    the finest (coarse_sweeps), where fewer than the finest level's.  Candidates that stop at max_vcycles above
    the tolerance are not eligible.  Copy the result into the descriptor's
-   pre_sweeps, post_sweeps, inner_cycles, sweep_planes, krylov and coarse_sweeps.  Device memory: one
+   pre_sweeps, post_sweeps, inner_cycles, sweep_planes, krylov, coarse_sweeps and smoother.  Device memory: one
    temporary case at a time.  Errors: FVM_ERR_INVALID, FVM_ERR_NOT_CONVERGED
    (no candidate converged), FVM_ERR_CUDA. */
 typedef struct {
@@ -383,7 +391,7 @@ typedef struct {
     int32_t candidates;              /* candidates timed */
     int32_t krylov;                  /* 0 / 1: the flexible-CG acceleration */
     int32_t coarse_sweeps;           /* sweeps on the levels below the finest (0: as the finest) */
-    int32_t reserved;
+    int32_t smoother;                /* 0 / 1: the constant or the Chebyshev sweep weights */
 } fvm_tuning;
 
 fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm_tuning* out);

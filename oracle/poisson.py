@@ -4,7 +4,8 @@
   A p      = -Laplacian_h p with one ghost layer (Eq. neg_lap_discretize
              and the printed 3x3x3 kernel)
   smoother   p <- p + w_J D^{-1} (b - A p), D = sum_d 2 / h_d^2 scalar
-             (Eq. jacobi_pc; weighted)
+             (Eq. jacobi_pc; weighted); smoother 1 (an addition): one weight
+             per sweep, the reciprocals of the Chebyshev roots on [1/4, 2]
   RES        mean of the 2x2x2 children (Eq. restriction)
   PROL       cell-centred trilinear interpolation, 3/4 parent + 1/4
              neighbour per axis (Eq. prolongation); beyond a domain face
@@ -110,11 +111,36 @@ def jacobi_weight(lev, spec):
     return 6.0 / 7.0 if all(lev.active) else 4.0 / 5.0
 
 
+def chebyshev_weights(n, lo=0.25, hi=2.0):
+    """Weights of n Jacobi sweeps whose error polynomial prod_i (1 - w_i x) in x = lambda(D^-1 A)
+    is the degree-n Chebyshev polynomial of the interval [lo, hi], scaled to 1 at x = 0: w_i is
+    the reciprocal of its i-th root, (hi + lo)/2 + (hi - lo)/2 cos((2i - 1) pi / (2n)), largest
+    root first.  hi = 2 bounds the spectrum of D^-1 A (Gershgorin, with the scalar D of Eq.
+    jacobi_pc); lo = 1/4 lies below the high-frequency band of full coarsening (1/3 in 3D, 1/2 in
+    2D), so the sweeps damp that band by 1 / T_n((hi + lo)/(hi - lo)) at least."""
+    i = np.arange(1, n + 1)
+    roots = (hi + lo) / 2 + (hi - lo) / 2 * np.cos((2 * i - 1) * np.pi / (2 * n))
+    return list(1.0 / roots)
+
+
+def sweep_weights(lev, spec, n, post):
+    """The weights of n smoothing sweeps: the constant w_J (smoother 0), or (smoother 1, an
+    addition to the paper's fixed weight) the Chebyshev weights, in reverse order after the
+    coarse correction so that the post-smoother mirrors the pre-smoother."""
+    if getattr(spec, "smoother", 0) == 1:
+        w = chebyshev_weights(n)
+        return w[::-1] if post else w
+    return [jacobi_weight(lev, spec)] * n
+
+
 def smooth(lev, p, b, sweeps, wJ):
-    """Weighted Jacobi: p <- p + w_J (b - A p) / D (Eq. jacobi_pc)."""
+    """Weighted Jacobi: p <- p + w_J (b - A p) / D (Eq. jacobi_pc); wJ is one weight for every
+    sweep or a list of one weight per sweep."""
     D = lev.diag()
-    for _ in range(sweeps):
-        p = np.where(lev.fluid, p + wJ * residual(lev, p, b) / D, 0.0)
+    ws = list(wJ) if np.ndim(wJ) else [wJ] * sweeps
+    assert len(ws) == sweeps
+    for w in ws:
+        p = np.where(lev.fluid, p + w * residual(lev, p, b) / D, 0.0)
     return p
 
 
@@ -225,13 +251,12 @@ class Multigrid:
         lev = self.levels[l]
         if l == len(self.levels) - 1:
             return self.coarse_solve(b)
-        wJ = jacobi_weight(lev, self.spec)
         pre, post = self.sweeps(l)
-        p = smooth(lev, p, b, pre, wJ)
+        p = smooth(lev, p, b, pre, sweep_weights(lev, self.spec, pre, False))
         bc = restrict(lev, residual(lev, p, b))
         ec = self.vcycle(np.zeros(self.levels[l + 1].shape), bc, l + 1)
         p = np.where(lev.fluid, p + prolong(self.levels[l + 1], ec, lev.shape), 0.0)
-        p = smooth(lev, p, b, post, wJ)
+        p = smooth(lev, p, b, post, sweep_weights(lev, self.spec, post, True))
         return p
 
     def paper_cycle(self, p, b):

@@ -61,7 +61,7 @@ class CaseDesc(ct.Structure):
                 ("mg_levels", ct.c_int32), ("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32),
                 ("max_vcycles", ct.c_int32), ("fixed_vcycles", ct.c_int32), ("inner_cycles", ct.c_int32),
                 ("sweep_planes", ct.c_int32), ("mg_variant", ct.c_int32), ("krylov", ct.c_int32),
-                ("coarse_sweeps", ct.c_int32), ("rk_stages", ct.c_int32), ("reserved2", ct.c_int32),
+                ("coarse_sweeps", ct.c_int32), ("rk_stages", ct.c_int32), ("smoother", ct.c_int32),
                 ("mg_rel_tol", ct.c_double), ("jacobi_weight", ct.c_double), ("seed", ct.c_uint64),
                 ("init_perturb", ct.c_double), ("init_vel", ct.c_double * 3), ("init_T", ct.c_double),
                 ("init_k", ct.c_double), ("init_omega", ct.c_double), ("stream", ct.c_void_p)]
@@ -99,7 +99,7 @@ class ServerInfo(ct.Structure):
 class Tuning(ct.Structure):
     _fields_ = [("pre_sweeps", ct.c_int32), ("post_sweeps", ct.c_int32), ("inner_cycles", ct.c_int32),
                 ("sweep_planes", ct.c_int32), ("ms_per_step", ct.c_double), ("candidates", ct.c_int32),
-                ("krylov", ct.c_int32), ("coarse_sweeps", ct.c_int32), ("reserved", ct.c_int32)]
+                ("krylov", ct.c_int32), ("coarse_sweeps", ct.c_int32), ("smoother", ct.c_int32)]
 
 
 class BatchInfo(ct.Structure):
@@ -241,6 +241,7 @@ class _Desc:
         d.krylov = spec.krylov
         d.coarse_sweeps = spec.coarse_sweeps
         d.rk_stages = spec.rk_stages
+        d.smoother = spec.smoother
         d.mg_rel_tol, d.jacobi_weight = spec.mg_rel_tol, spec.jacobi_weight
         d.seed = spec.seed & ((1 << 64) - 1)
         d.init_perturb = spec.init_perturb
@@ -447,14 +448,15 @@ class Case:
 
 def autotune(spec: cases.CaseSpec, steps=5):
     """Measured choice of V(nu, nu), V-cycles per outer residual, the Krylov
-    acceleration and planes per block (fvm_autotune).  Returns (tuned spec,
-    details)."""
+    acceleration, the sweep weights, planes per block and the coarser levels'
+    sweeps (fvm_autotune).  Returns (tuned spec, details)."""
     d = _Desc(spec)
     t = Tuning()
     _check(lib().fvm_autotune(ct.byref(d.desc), int(steps), ct.byref(t)))
     info = {k: getattr(t, k) for k, _ in Tuning._fields_}
     return spec.replace(pre_sweeps=t.pre_sweeps, post_sweeps=t.post_sweeps, inner_cycles=t.inner_cycles,
-                        sweep_planes=t.sweep_planes, krylov=t.krylov, coarse_sweeps=t.coarse_sweeps), info
+                        sweep_planes=t.sweep_planes, krylov=t.krylov, coarse_sweeps=t.coarse_sweeps,
+                        smoother=t.smoother), info
 
 
 def _stats(s: StepStats, status=OK):

@@ -115,6 +115,7 @@ class CaseSpec:
     rk_stages: int = 1           # explicit stage: 1 forward Euler, 2 / 3 strong-stability-preserving RK
     mg_rel_tol: float = 1e-8
     jacobi_weight: float = 0.0   # 0 -> 6/7 in 3D, 4/5 in 2D
+    smoother: int = 0            # 0: that weight on every sweep; 1: Chebyshev weights on [1/4, 2] per sweep
     seed: int = 0
     init_perturb: float = 0.0
     init_vel: Tuple[float, float, float] = (0.0, 0.0, 0.0)

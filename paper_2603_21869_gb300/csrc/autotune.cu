@@ -5,7 +5,8 @@
 //
 // Pass 1 tries the smoother sweep counts V(nu, nu), nu = 2, 3, 4, the
 // V-cycles per FP64 outer residual (1..4 with reduced-precision corrections,
-// 1 in FP64) and the flexible-CG acceleration off / on; pass 2 tries the z
+// 1 in FP64), the flexible-CG acceleration off / on and the constant or the
+// Chebyshev sweep weights (both off with mg_variant 1); pass 2 tries the z
 // planes per block of the four-cell level kernels (the built-in rule,
 // 1 .. 32) with the best pass-1 choice; pass 3 tries 1 and 2 sweeps on the
 // levels below the finest.  A candidate whose solves stop at max_vcycles
@@ -19,7 +20,7 @@
 namespace {
 
 struct Trial {
-    int pre, post, inner, planes, krylov, coarse;
+    int pre, post, inner, planes, krylov, coarse, smoother;
     double ms;
 };
 
@@ -32,6 +33,7 @@ double time_candidate(const fvm_case_desc& base, const Trial& t, int steps, cuda
     d.sweep_planes = t.planes;
     d.krylov = t.krylov;
     d.coarse_sweeps = t.coarse;
+    d.smoother = t.smoother;
     d.stream = s;
     fvm_case* c = nullptr;
     if (fvm_create_case(&d, &c) != FVM_OK) return -1.0;
@@ -73,17 +75,18 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     std::vector<int> inners;
     if (desc->precision == FVM_FP64) inners = {1};
     else inners = {1, 2, 3, 4};
-    Trial best{0, 0, 0, 0, 0, 0, -1.0};
+    Trial best{0, 0, 0, 0, 0, 0, 0, -1.0};
     int tried = 0;
     const int kmax = desc->mg_variant == 1 ? 0 : 1;
-    for (int kry = 0; kry <= kmax; ++kry)
-        for (int nu : {2, 3, 4})
-            for (int inner : inners) {
-                Trial t{nu, nu, inner, 0, kry, 0, 0.0};
-                t.ms = time_candidate(*desc, t, steps, s);
-                ++tried;
-                if (t.ms > 0.0 && (best.ms < 0.0 || t.ms < best.ms)) best = t;
-            }
+    for (int sm = 0; sm <= kmax; ++sm)
+        for (int kry = 0; kry <= kmax; ++kry)
+            for (int nu : {2, 3, 4})
+                for (int inner : inners) {
+                    Trial t{nu, nu, inner, 0, kry, 0, sm, 0.0};
+                    t.ms = time_candidate(*desc, t, steps, s);
+                    ++tried;
+                    if (t.ms > 0.0 && (best.ms < 0.0 || t.ms < best.ms)) best = t;
+                }
     if (best.ms > 0.0)
         for (int planes : {1, 2, 4, 8, 16, 32}) {
             Trial t = best;
@@ -114,6 +117,7 @@ extern "C" fvm_status fvm_autotune(const fvm_case_desc* desc, int32_t steps, fvm
     o.sweep_planes = best.planes;
     o.krylov = best.krylov;
     o.coarse_sweeps = best.coarse;
+    o.smoother = best.smoother;
     o.ms_per_step = best.ms;
     o.candidates = tried;
     *out = o;

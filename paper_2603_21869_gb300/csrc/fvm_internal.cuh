@@ -193,11 +193,16 @@ struct SolveState {
 };
 
 // Levels lc..L-1, cycled by one CTA in shared memory.
+// per-sweep Jacobi weights of the Chebyshev smoother (smoother 1: at most this many sweeps a side)
+constexpr int kMaxChebSweeps = 16;
+
 struct CoarseLevels {
     int32_t nl;              // number of levels handled
     int32_t pre, post;
-    int32_t pad;
+    int32_t cheb;            // 1: sweep i of a side takes w[side][i] (0 pre, 1 post); 0: the level's wJ
     LevelDev lv[FVM_MAX_LEVELS];
+    double w[2][kMaxChebSweeps];
+    float wf[2][kMaxChebSweeps];
 };
 
 

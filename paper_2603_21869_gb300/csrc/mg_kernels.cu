@@ -1529,6 +1529,17 @@ __device__ __forceinline__ C cta_apply_A(const LevelDev& L, uint32_t f, const C*
     return apply_A_with<C>(L, f, c, eP, [&](int q) { return e[q]; });
 }
 
+// the weight of sweep i on one side (0 pre, 1 post) of a coarse-CTA level
+template <class C> __device__ __forceinline__ C coarse_weight(const CoarseLevels& cl, const LevelDev& L, int side, int i);
+template <> __device__ __forceinline__ double coarse_weight<double>(const CoarseLevels& cl, const LevelDev& L, int side,
+                                                                   int i) {
+    return cl.cheb ? cl.w[side][i] : L.wJ;
+}
+template <> __device__ __forceinline__ float coarse_weight<float>(const CoarseLevels& cl, const LevelDev& L, int side,
+                                                                 int i) {
+    return cl.cheb ? cl.wf[side][i] : L.wJf;
+}
+
 template <class TI>
 struct CoarseK {
     static constexpr int kThreads = kCtaThreads;
@@ -1604,11 +1615,13 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         const uint16_t* const fl = F[l];
         C* const rl = R[l];
         const int N = (int)L.N;
-        const C w = LP<C>::wJ(L), iD = LP<C>::iD(L);
-        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(fl[c]) ? (C)0 : w * rl[c] * iD;
+        const C iD = LP<C>::iD(L);
+        const C w0 = coarse_weight<C>(cl, L, 0, 0);
+        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(fl[c]) ? (C)0 : w0 * rl[c] * iD;
         __syncthreads();
         int s = 0;
         for (int it = 1; it < cl.pre; ++it) {
+            const C w = coarse_weight<C>(cl, L, 0, it);
             C* ein = s ? E1[l] : E0[l];
             C* eo = s ? E0[l] : E1[l];
             for (int c = tid; c < N; c += T) {
@@ -1698,8 +1711,9 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         }
         __syncthreads();
         int s = cur[l];
-        const C w = LP<C>::wJ(L), iD = LP<C>::iD(L);
+        const C iD = LP<C>::iD(L);
         for (int it = 0; it < cl.post; ++it) {
+            const C w = coarse_weight<C>(cl, L, 1, it);
             C* ein = s ? E1[l] : E0[l];
             C* eo = s ? E0[l] : E1[l];
             for (int c = tid; c < N; c += T) {

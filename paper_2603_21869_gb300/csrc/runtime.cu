@@ -408,6 +408,11 @@ fvm_status plan_case(const fvm_case_desc* d, Plan& pl) {
     if (d->coarse_sweeps < 0 || d->coarse_sweeps > 64) return fail(FVM_ERR_INVALID, "coarse_sweeps must be 0..64");
     if (d->coarse_sweeps > 0 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "coarse_sweeps needs mg_variant 0");
     if (d->rk_stages < 0 || d->rk_stages > 3) return fail(FVM_ERR_INVALID, "rk_stages must be 0..3");
+    if (d->smoother < 0 || d->smoother > 1) return fail(FVM_ERR_INVALID, "smoother must be 0 or 1");
+    if (d->smoother == 1 && d->mg_variant == 1) return fail(FVM_ERR_INVALID, "smoother 1 needs mg_variant 0");
+    if (d->smoother == 1 && (d->pre_sweeps > kMaxChebSweeps || d->post_sweeps > kMaxChebSweeps ||
+                             d->coarse_sweeps > kMaxChebSweeps))
+        return fail(FVM_ERR_INVALID, "smoother 1 takes at most 16 sweeps a side");
     if (d->fixed_vcycles < 0 || (d->fixed_vcycles == 0 && d->max_vcycles < 1))
         return fail(FVM_ERR_INVALID, "need fixed_vcycles > 0 or max_vcycles >= 1");
     if (d->fixed_vcycles == 0 && !(d->mg_rel_tol > 0.0)) return fail(FVM_ERR_INVALID, "mg_rel_tol must be > 0");
@@ -720,6 +725,23 @@ int post_at(const fvm_case* c, size_t l) {
     return l > 0 && c->desc.coarse_sweeps > 0 ? c->desc.coarse_sweeps : c->desc.post_sweeps;
 }
 
+// The weight of sweep i of the n on one side of a level: the level's constant weight, or
+// (smoother 1) the reciprocal of a root of the degree-n Chebyshev polynomial of [1/4, 2],
+// (2 + 1/4)/2 + (2 - 1/4)/2 cos((2q + 1) pi / (2n)) for q = i before the coarse correction (largest
+// root first) and q = n - 1 - i after it.
+double sweep_weight(const fvm_case* c, const LevelDev& L, int n, int i, bool post) {
+    if (c->desc.smoother != 1) return L.wJ;
+    const int q = post ? n - 1 - i : i;
+    return 1.0 / (1.125 + 0.875 * std::cos((2.0 * q + 1.0) * 3.14159265358979323846 / (2.0 * n)));
+}
+
+// a level's description with the weight of one sweep (the kernels read wJ / wJf)
+LevelDev weighted(LevelDev v, double w) {
+    v.wJ = w;
+    v.wJf = (float)w;
+    return v;
+}
+
 // Level l (> 0) gets its first Jacobi sweep from the restriction that forms its r
 // (not the levels the single-CTA coarse kernel cycles).
 bool first_sweep_fused(const fvm_case* c, size_t l) {
@@ -753,39 +775,45 @@ fvm_status cycle(fvm_case* c, size_t l, int& out_idx) {
     // runs inner_cycles V-cycles on the same r; the last sweep of the last one adds e to p
     const int reps = l == 0 ? c->rule_inner : 1;
     int cur = 0;
+    const int npre = pre_at(c, l), npost = post_at(c, l);
     for (int rep = 0; rep < reps; ++rep) {
-        int pre = pre_at(c, l);
+        int pre = npre, first = 0;   // first: the index of the next pre-sweep's weight
         if (rep == 0) {
             if (l > 0 && !first_sweep_fused(c, l))
                 KLAUNCH(lvl_name("sweep_first", l), 2 * N * si + 2 * N, 1,
-                        launch_sweep_first(c->inner, L.dev, L.r, L.e[0], c->sst, s));
+                        launch_sweep_first(c->inner, weighted(L.dev, sweep_weight(c, L.dev, npre, 0, false)), L.r,
+                                           L.e[0], c->sst, s));
             pre -= 1;
+            first = 1;
         }
         for (int k = 0; k < pre; ++k) {
             KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
-                    launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
+                    launch_sweep(c->inner, weighted(L.dev, sweep_weight(c, L.dev, npre, first + k, false)),
+                                 L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
             cur ^= 1;
         }
         const bool fuse = first_sweep_fused(c, l + 1);
+        const LevelDev Lcw = weighted(Lc.dev, sweep_weight(c, Lc.dev, pre_at(c, l + 1), 0, false));
         KLAUNCH(lvl_name("resid_restrict", l), 2 * N * si + Nc * si + 2 * N + (fuse ? Nc * (si + 2) : 0.0), 1,
-                launch_resid_restrict(c->inner, L.dev, Lc.dev, L.e[cur], L.r, Lc.r, fuse ? Lc.e[0] : nullptr,
+                launch_resid_restrict(c->inner, L.dev, Lcw, L.e[cur], L.r, Lc.r, fuse ? Lc.e[0] : nullptr,
                                       c->sst, s));
         int ci = 0;
         ST_TRY(cycle(c, l + 1, ci));
         KLAUNCH(lvl_name("prolong_add", l), 2 * N * si + Nc * si + 2 * N, 1,
                 launch_prolong_add(c->inner, L.dev, Lc.dev, Lc.e[ci], L.e[cur], c->sst, s));
-        const int post = post_at(c, l);
+        const int post = npost;
         for (int k = 0; k < post; ++k) {
+            const LevelDev Lw = weighted(L.dev, sweep_weight(c, L.dev, npost, k, true));
             if (l == 0 && rep == reps - 1 && k == post - 1 && !c->desc.krylov) {
                 KLAUNCH("sweep_to_p_L0", 2 * N * si + 16 * N + 2 * N, 1,
-                        launch_sweep_to_p(c->inner, L.dev, L.e[cur], L.r, c->p, c->sst, s));
+                        launch_sweep_to_p(c->inner, Lw, L.e[cur], L.r, c->p, c->sst, s));
             } else if (l == 0 && rep == reps - 1 && k == post - 1 && c->kz) {
                 // BF16 levels under the flexible-CG step: the correction z in FP32
                 KLAUNCH("sweep_L0", 2 * N * si + 4 * N + 2 * N, 1,
-                        launch_sweep_to_f32(c->inner, L.dev, L.e[cur], L.r, c->kz, c->sst, s));
+                        launch_sweep_to_f32(c->inner, Lw, L.e[cur], L.r, c->kz, c->sst, s));
             } else {
                 KLAUNCH(lvl_name("sweep", l), 3 * N * si + 2 * N, 1,
-                        launch_sweep(c->inner, L.dev, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
+                        launch_sweep(c->inner, Lw, L.e[cur], L.r, L.e[cur ^ 1], c->sst, s));
                 cur ^= 1;
             }
         }
@@ -800,7 +828,9 @@ fvm_status residual0(fvm_case* c, cudaGraphConditionalHandle cond, cudaGraphCond
                      int use_cond) {
     const double N = (double)c->cd.N;
     KLAUNCH("resid0", N * (8 + elem_size(c->prec) + 2 * elem_size(c->inner) + 2), 1,
-            launch_resid0(c->inner, c->prec, c->levels[0].dev, c->p, c->b, c->levels[0].r, c->levels[0].e[0],
+            launch_resid0(c->inner, c->prec,
+                          weighted(c->levels[0].dev, sweep_weight(c, c->levels[0].dev, pre_at(c, 0), 0, false)), c->p,
+                          c->b, c->levels[0].r, c->levels[0].e[0],
                           c->partials, c->sst, cond, cond2, use_cond, c->stream));
     return FVM_OK;
 }
@@ -1244,6 +1274,15 @@ fvm_status build_case(const Plan& pl, fvm_case* c) {
         c->coarse.pre = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.pre_sweeps;   // (levels below the finest)
         c->coarse.post = d.coarse_sweeps > 0 ? d.coarse_sweeps : d.post_sweeps;
         for (int q = 0; q < c->coarse.nl; ++q) c->coarse.lv[q] = c->levels[lc + q].dev;
+        c->coarse.cheb = d.smoother == 1 ? 1 : 0;
+        if (c->coarse.cheb)
+            for (int side = 0; side < 2; ++side) {
+                const int n = side ? c->coarse.post : c->coarse.pre;
+                for (int i = 0; i < n; ++i) {
+                    c->coarse.w[side][i] = sweep_weight(c, c->coarse.lv[0], n, i, side == 1);
+                    c->coarse.wf[side][i] = (float)c->coarse.w[side][i];
+                }
+            }
         CUDA_TRY(prepare_coarse_cta(pl.inner, coarse_cta_smem(c->coarse, pl.inner)));
     }
     // the paper's scheme applies the fine grid's stencil and diagonal on every level

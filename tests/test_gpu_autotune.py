@@ -22,10 +22,11 @@ def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
     spec = cases.heated_channel_3d(128, 32, 32, mg_levels=4, precision=cases.FP32, mg_rel_tol=1e-8,
                                    max_vcycles=40)
     tuned, info = binding.autotune(spec, steps=3)
-    # pass 1: nu in {2, 3, 4} x inner in {1..4} x krylov in {0, 1}; pass 2: six plane counts;
-    # pass 3: coarse-level sweeps 1 and 2 where fewer than the chosen nu
+    # pass 1: nu in {2, 3, 4} x inner in {1..4} x krylov in {0, 1} x smoother in {0, 1}; pass 2: six
+    # plane counts; pass 3: coarse-level sweeps 1 and 2 where fewer than the chosen nu
     extra = sum(1 for k in (1, 2) if k < info["pre_sweeps"])
-    assert info["candidates"] == 3 * 4 * 2 + 6 + extra and info["ms_per_step"] > 0
+    assert info["candidates"] == 3 * 4 * 2 * 2 + 6 + extra and info["ms_per_step"] > 0
+    assert info["smoother"] in (0, 1) and tuned.smoother == info["smoother"]
     assert info["coarse_sweeps"] in (0, 1, 2) and tuned.coarse_sweeps == info["coarse_sweeps"]
     assert info["pre_sweeps"] == info["post_sweeps"] in (2, 3, 4) and info["krylov"] in (0, 1)
     assert tuned.krylov == info["krylov"]
@@ -40,11 +41,13 @@ def test_autotuned_parameters_are_valid_and_still_match_the_oracle():
 
 
 def test_paper_scheme_is_tuned_without_the_krylov_acceleration():
-    """mg_variant 1 admits no flexible-CG candidates (the descriptor would be rejected)."""
+    """mg_variant 1 admits no flexible-CG and no Chebyshev-weight candidates (the descriptor would
+    be rejected)."""
     spec = cases.heated_channel_3d(64, 16, 16, mg_levels=4, precision=cases.FP32, mg_variant=1,
                                    mg_rel_tol=2e-2, max_vcycles=100)   # the scheme stalls near 5e-4 here
     tuned, info = binding.autotune(spec, steps=2)
-    assert info["candidates"] == 3 * 4 + 6 and info["krylov"] == 0 and tuned.mg_variant == 1
+    assert info["candidates"] == 3 * 4 + 6 and info["krylov"] == 0 and info["smoother"] == 0
+    assert tuned.mg_variant == 1
 
 
 def test_planes_per_block_do_not_change_the_result():

@@ -405,3 +405,87 @@ def test_coarse_sweeps_change_only_the_coarser_levels_and_keep_the_fixed_point()
     pd = direct_solve(lev, b)
     assert np.max(np.abs(p - pd)) <= 1e-9 * np.max(np.abs(pd))
 
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_chebyshev_weights_give_the_scaled_chebyshev_polynomial(n):
+    """prod_i (1 - w_i x) equals T_n((hi + lo - 2x)/(hi - lo)) / T_n((hi + lo)/(hi - lo)) (the
+    Chebyshev polynomial of [lo, hi] = [1/4, 2] scaled to 1 at 0, its own closed form
+    cos(n arccos t) inside the interval) at points spanning the interval; n = 1 is the single
+    weight 1 / 1.125."""
+    lo, hi = 0.25, 2.0
+    w = poisson.chebyshev_weights(n)
+    assert len(w) == n and all(np.diff(w) > 0)          # largest root first
+    x = np.linspace(lo, hi, 41)
+    prod = np.prod([1.0 - wi * x for wi in w], axis=0)
+    t = (hi + lo - 2 * x) / (hi - lo)
+    tn = np.cos(n * np.arccos(t))
+    t0 = (hi + lo) / (hi - lo)
+    tn0 = np.cosh(n * np.arccosh(t0))
+    assert np.allclose(prod, tn / tn0, rtol=0, atol=1e-14)
+    assert np.max(np.abs(prod)) <= 1.0 / tn0 + 1e-14
+    if n == 1:
+        assert w[0] == pytest.approx(1.0 / 1.125, rel=1e-15)
+
+
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_sweeps_scale_a_neumann_eigenmode_by_the_weight_polynomial(smoother):
+    """In a closed box (every face zero-gradient, no solid) the cosine modes are eigenvectors of
+    A with eigenvalue sum_d (2 - 2 cos(pi m_d / n_d)) / h_d^2; n sweeps with b = 0 scale such a mode
+    by prod_i (1 - w_i lambda / D) with the weights the V-cycle uses (pre order, then post order)."""
+    spec = _spec(8, 8, 4, L=(1.0, 1.0, 0.5), outlet_faces=(), smoother=smoother)
+    lev = Geometry(spec).levels(1)[0]
+    h = np.array(lev.h, dtype=float)
+    n = np.array(lev.shape)
+    D = float(np.sum(2.0 / h ** 2))
+    for m in [(1, 0, 0), (3, 2, 1), (7, 7, 3), (4, 1, 2)]:
+        g = np.meshgrid(*[np.cos(np.pi * m[d] * (np.arange(n[d]) + 0.5) / n[d]) for d in range(3)], indexing="ij")
+        e = g[0] * g[1] * g[2]
+        lam = float(np.sum((2.0 - 2.0 * np.cos(np.pi * np.array(m) / n)) / h ** 2))
+        assert np.allclose(apply_A(lev, e), lam * e, atol=1e-9 * lam)
+        for post in (False, True):
+            w = poisson.sweep_weights(lev, spec, 3, post)
+            got = poisson.smooth(lev, e, np.zeros(lev.shape), 3, w)
+            want = e * np.prod([1.0 - wi * lam / D for wi in w])
+            assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
+    w0 = poisson.sweep_weights(lev, spec, 2, False)
+    if smoother == 0:
+        assert w0 == [6.0 / 7.0] * 2
+    else:
+        assert w0 == poisson.chebyshev_weights(2) and poisson.sweep_weights(lev, spec, 2, True) == w0[::-1]
+
+
+def test_chebyshev_sweeps_damp_the_high_band_and_never_amplify():
+    """On a small room level (solids, an outlet) the eigenvalues x of D^-1 A lie in [0, 2]; the
+    Chebyshev sweeps' polynomial is at most 1 in magnitude on all of them and at most
+    1 / T_n(9/7) on those at or above 1/4, the band the weights target."""
+    spec = _spec(8, 8, 4, L=(1.0, 1.0, 0.5), outlet_faces=(1,), boxes=[cases.Box(2, 4, 2, 5, 0, 2)])
+    lev = Geometry(spec).levels(1)[0]
+    M = poisson.dense_operator(lev)
+    fl = lev.fluid.ravel()
+    D = float(np.sum(2.0 / np.array(lev.h, dtype=float) ** 2))
+    x = np.linalg.eigvals(M[np.ix_(fl, fl)] / D).real
+    assert x.min() > 0.0 and x.max() <= 2.0 + 1e-12
+    for n in (2, 3, 4):
+        w = poisson.chebyshev_weights(n)
+        pol = np.prod([1.0 - wi * x for wi in w], axis=0)
+        assert np.max(np.abs(pol)) <= 1.0
+        bound = 1.0 / np.cosh(n * np.arccosh(2.25 / 1.75))
+        assert np.max(np.abs(pol[x >= 0.25])) <= bound + 1e-12
+
+
+def test_chebyshev_smoother_keeps_the_fixed_point_and_needs_fewer_cycles():
+    """The discrete solution is a fixed point of the V-cycle with either smoother, and on a room
+    the flexible-CG solve to 1e-8 needs fewer V(2,2) cycles with the Chebyshev weights."""
+    spec = cases.room_3d(32, 16, 16, seed=2, mg_levels=3, h=0.1, precision=cases.FP64, pre_sweeps=2,
+                         post_sweeps=2, krylov=1)
+    counts = {}
+    for sm in (0, 1):
+        mg = OracleCase(spec.replace(smoother=sm)).mg
+        lev = mg.levels[0]
+        b = np.where(lev.fluid, np.random.default_rng(9).normal(size=lev.shape), 0.0)
+        pd = direct_solve(lev, b)
+        assert np.max(np.abs(mg.vcycle(pd, b) - pd)) <= 1e-10 * np.max(np.abs(pd))
+        _, counts[sm], rel = mg.fcg_solve(np.zeros(lev.shape), b, 60, 1e-8, 0)
+        assert rel <= 1e-8
+    assert counts[1] < counts[0], counts
