@@ -333,8 +333,10 @@ def run_batched(args, rank, ws, local, dist):
     # end to end through the C-ABI with host buffers: write every case, one batched step, read back
     e2e = None
     if args.e2e_steps > 0:
-        # pinned host buffers in the library's own layout; each step's output is the next input
-        hosts = [torch.empty(7 * sp.cells, dtype=torch.float64, pin_memory=True).numpy() for sp in specs]
+        # pinned host buffers in the library's own layout, in the fields' storage precision (FP32
+        # for FP32 fields: fvm_read_fields_f32); each step's output is the next input
+        hdt = torch.float64 if args.precision == "f64" else torch.float32
+        hosts = [torch.empty(7 * sp.cells, dtype=hdt, pin_memory=True).numpy() for sp in specs]
         for c, h in zip(cs, hosts):
             c.read_flat(h)
         te = 0.0
@@ -347,7 +349,7 @@ def run_batched(args, rank, ws, local, dist):
                 c.read_flat(h)
             te += time.perf_counter() - t0
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
-               "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
+               "h2d_bytes_per_step": 7 * N * hosts[0].itemsize, "d2h_bytes_per_step": 7 * N * hosts[0].itemsize}
         if dist:
             e2e["value"] = ws * N * args.e2e_steps / replicas.max_over_ranks(te)
     batch.close()
@@ -799,8 +801,10 @@ def main():
     # end to end through the C-ABI with host buffers: write state, one step, read state
     e2e = None
     if args.e2e_steps > 0:
-        # a pinned host buffer in the library's own layout; each step's output is the next input
-        host = torch.empty(7 * N, dtype=torch.float64, pin_memory=True).numpy()
+        # a pinned host buffer in the library's own layout, in the fields' storage precision
+        # (FP32 for FP32 fields: fvm_read_fields_f32); each step's output is the next input
+        hdt = torch.float64 if args.precision == "f64" else torch.float32
+        host = torch.empty(7 * N, dtype=hdt, pin_memory=True).numpy()
         case.read_flat(host)
         te = 0.0
         for _ in range(args.e2e_steps):
@@ -810,7 +814,7 @@ def main():
             case.read_flat(host)
             te += time.perf_counter() - t0
         e2e = {"value": N * args.e2e_steps / te, "unit": "cell-steps/s",
-               "h2d_bytes_per_step": 7 * N * 8, "d2h_bytes_per_step": 7 * N * 8}
+               "h2d_bytes_per_step": 7 * N * host.itemsize, "d2h_bytes_per_step": 7 * N * host.itemsize}
         if dist:
             e2e["value"] = ws * N * args.e2e_steps / replicas.max_over_ranks(te)
 

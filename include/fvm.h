@@ -253,6 +253,15 @@ fvm_status fvm_read_fields(fvm_case* c, unsigned field_mask, double* host_out, s
    Synchronises. */
 fvm_status fvm_write_fields(fvm_case* c, unsigned field_mask, const double* host_in, size_t n);
 
+/* fvm_read_fields / fvm_write_fields with FP32 host values (n floats, same
+   layout, errors and synchronisation), half the bytes moved.  The state
+   fields of an FP32 or BF16-corrections case are stored in FP32 and copy as
+   they are, without conversion; p (held as a double-float pair) is rounded
+   once to FP32 on reading and written as that FP32 value; an FP64 case's
+   fields are rounded to FP32 on reading and widened exactly on writing. */
+fvm_status fvm_read_fields_f32(fvm_case* c, unsigned field_mask, float* host_out, size_t n);
+fvm_status fvm_write_fields_f32(fvm_case* c, unsigned field_mask, const float* host_in, size_t n);
+
 /* Set the Poisson right-hand side b (nx*ny*nz doubles, host). */
 fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n);
 

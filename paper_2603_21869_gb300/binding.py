@@ -109,7 +109,8 @@ class BatchInfo(ct.Structure):
 
 
 EXPORTS = ["fvm_case_bytes", "fvm_create_case", "fvm_destroy_case", "fvm_step", "fvm_run_stage", "fvm_vcycle",
-           "fvm_read_fields", "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
+           "fvm_read_fields", "fvm_write_fields", "fvm_read_fields_f32", "fvm_write_fields_f32",
+           "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
            "fvm_projection_vjp", "fvm_destruction_vjp", "fvm_explicit_vjp", "fvm_step_vjp", "fvm_step_batch",
            "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable",
            "fvm_profile_read", "fvm_struct_sizes", "fvm_last_error", "fvm_poisson_residual_static",
@@ -140,6 +141,8 @@ def lib():
     L.fvm_vcycle.argtypes = [CP, ct.c_int, ct.POINTER(ct.c_double)]
     L.fvm_read_fields.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_write_fields.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_double), ct.c_size_t]
+    L.fvm_read_fields_f32.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_float), ct.c_size_t]
+    L.fvm_write_fields_f32.argtypes = [CP, ct.c_uint, ct.POINTER(ct.c_float), ct.c_size_t]
     L.fvm_set_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_read_poisson_rhs.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
     L.fvm_lambda2.argtypes = [CP, ct.POINTER(ct.c_double), ct.c_size_t]
@@ -182,7 +185,8 @@ def lib():
     L.fvm_struct_sizes.restype = None
     L.fvm_last_error.restype = ct.c_char_p
     for name in ["fvm_create_case", "fvm_step", "fvm_run_stage", "fvm_vcycle", "fvm_read_fields",
-                 "fvm_write_fields", "fvm_set_poisson_rhs", "fvm_read_poisson_rhs", "fvm_lambda2",
+                 "fvm_write_fields", "fvm_read_fields_f32", "fvm_write_fields_f32", "fvm_set_poisson_rhs",
+                 "fvm_read_poisson_rhs", "fvm_lambda2",
                  "fvm_projection_vjp", "fvm_destruction_vjp", "fvm_explicit_vjp", "fvm_step_vjp",
                  "fvm_step_batch",
                  "fvm_case_get_info", "fvm_set_option", "fvm_profile_enable", "fvm_profile_read",
@@ -336,17 +340,32 @@ class Case:
         _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
 
     def read_flat(self, out, fields=cases.FIELDS):
-        """The fields into a flat float64 buffer in the library's layout (field
-        after field in FIELDS order, x fastest), no host-side reshaping; a
-        pinned buffer gives the full transfer rate."""
+        """The fields into a flat float64 or float32 buffer in the library's layout
+        (field after field in FIELDS order, x fastest), no host-side reshaping; a
+        pinned buffer gives the full transfer rate.  float32 (fvm_read_fields_f32)
+        moves an FP32-field case's state as stored and p rounded to FP32."""
         fields = [f for f in cases.FIELDS if f in fields]
-        _check(lib().fvm_read_fields(self._h, _mask(fields), out.ctypes.data_as(ct.POINTER(ct.c_double)), out.size))
+        if out.dtype == np.float32:
+            _check(lib().fvm_read_fields_f32(self._h, _mask(fields), out.ctypes.data_as(ct.POINTER(ct.c_float)),
+                                             out.size))
+        elif out.dtype == np.float64:
+            _check(lib().fvm_read_fields(self._h, _mask(fields), out.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                         out.size))
+        else:
+            raise TypeError("read_flat wants a float64 or float32 buffer")
         return out
 
     def write_flat(self, buf, fields=cases.FIELDS):
-        """The fields from a flat float64 buffer in the library's layout (see read_flat)."""
+        """The fields from a flat float64 or float32 buffer in the library's layout (see read_flat)."""
         fields = [f for f in cases.FIELDS if f in fields]
-        _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)), buf.size))
+        if buf.dtype == np.float32:
+            _check(lib().fvm_write_fields_f32(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_float)),
+                                              buf.size))
+        elif buf.dtype == np.float64:
+            _check(lib().fvm_write_fields(self._h, _mask(fields), buf.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                          buf.size))
+        else:
+            raise TypeError("write_flat wants a float64 or float32 buffer")
 
     def set_rhs(self, b):
         buf = np.ascontiguousarray(np.asarray(b, dtype=np.float64).transpose(2, 1, 0).ravel())

@@ -280,6 +280,8 @@ cudaError_t launch_pack(int prec, const void* src, double* dst, int64_t N, cudaS
 // the pressure of a reduced-precision case (double-float pairs) to / from FP64
 cudaError_t launch_p_to_double(const double* pp, double* dst, int64_t N, cudaStream_t s);
 cudaError_t launch_p_from_double(const double* src, double* pp, int64_t N, cudaStream_t s);
+cudaError_t launch_p_to_float(const double* pp, float* dst, int64_t N, cudaStream_t s);
+cudaError_t launch_p_from_float(const float* src, double* pp, int64_t N, cudaStream_t s);
 cudaError_t launch_unpack(int prec, const double* src, void* dst, int64_t N, cudaStream_t s);
 
 // multigrid kernels (mg_kernels.cu); inner = FVM_FP64 / FVM_FP32 / FVM_BF16_MIXED (type of r, e on all

@@ -1944,6 +1944,18 @@ __global__ void k_p_from_double(const double* __restrict__ src, double* __restri
     if (c < N) reinterpret_cast<float2*>(pp)[c] = pp_from_double(src[c]);
 }
 
+// p to and from FP32 host values: the pair rounded once to FP32 (hi + lo evaluated in FP64,
+// exact), and an FP32 value as the pair (value, 0)
+__global__ void k_p_to_float(const double* __restrict__ pp, float* __restrict__ dst, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) dst[c] = __double2float_rn(pp_get(pp, c));
+}
+
+__global__ void k_p_from_float(const float* __restrict__ src, double* __restrict__ pp, int64_t N) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) reinterpret_cast<float2*>(pp)[c] = make_float2(src[c], 0.0f);
+}
+
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, int64_t N) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2273,6 +2285,16 @@ cudaError_t launch_convert(int sp, int dp, const void* src, void* dst, int64_t N
 
 cudaError_t launch_p_to_double(const double* pp, double* dst, int64_t N, cudaStream_t s) {
     k_p_to_double<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(pp, dst, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p_to_float(const double* pp, float* dst, int64_t N, cudaStream_t s) {
+    k_p_to_float<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(pp, dst, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p_from_float(const float* src, double* pp, int64_t N, cudaStream_t s) {
+    k_p_from_float<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(src, pp, N);
     return cudaGetLastError();
 }
 

@@ -1964,6 +1964,68 @@ fvm_status fvm_write_fields(fvm_case* c, unsigned mask, const double* host_in, s
     return FVM_OK;
 }
 
+// FP32 host values: a reduced-precision case's state fields move as stored (one copy each, no
+// staging), p through the staging buffer as FP32; an FP64 case's fields through the staging
+// buffer, converted there.
+fvm_status fvm_read_fields_f32(fvm_case* c, unsigned mask, float* host_out, size_t n) {
+    if (!c || (!host_out && mask)) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (mask >= (1u << 7)) return fail(FVM_ERR_INVALID, "field mask has bits above 6");
+    const int64_t N = c->cd.N;
+    size_t need = 0;
+    for (int f = 0; f < 7; ++f)
+        if (mask & (1u << f)) need += (size_t)N;
+    if (n < need) return fail(FVM_ERR_INVALID, "host buffer too small");
+    float* const stage = (float*)c->staging;
+    size_t off = 0;
+    for (int f = 0; f < 7; ++f) {
+        if (!(mask & (1u << f))) continue;
+        const void* src = nullptr;
+        if (f == FVM_P) {
+            if (c->prec == FVM_FP64) CUDA_TRY(launch_convert(FVM_FP64, FVM_FP32, c->p, stage, N, c->stream));
+            else CUDA_TRY(launch_p_to_float(c->p, stage, N, c->stream));
+            src = stage;
+        } else if (c->prec == FVM_FP64) {
+            CUDA_TRY(launch_convert(FVM_FP64, FVM_FP32, c->cur[field_slot(f)], stage, N, c->stream));
+            src = stage;
+        } else {
+            src = c->cur[field_slot(f)];
+        }
+        // (stream order: a later conversion into the staging buffer waits for this copy)
+        CUDA_TRY(cudaMemcpyAsync(host_out + off, src, N * 4, cudaMemcpyDeviceToHost, c->stream));
+        off += (size_t)N;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
+fvm_status fvm_write_fields_f32(fvm_case* c, unsigned mask, const float* host_in, size_t n) {
+    if (!c || (!host_in && mask)) return fail(FVM_ERR_INVALID, "null case or buffer");
+    if (mask >= (1u << 7)) return fail(FVM_ERR_INVALID, "field mask has bits above 6");
+    const int64_t N = c->cd.N;
+    size_t need = 0;
+    for (int f = 0; f < 7; ++f)
+        if (mask & (1u << f)) need += (size_t)N;
+    if (n < need) return fail(FVM_ERR_INVALID, "host buffer too small");
+    float* const stage = (float*)c->staging;
+    size_t off = 0;
+    for (int f = 0; f < 7; ++f) {
+        if (!(mask & (1u << f))) continue;
+        if (f != FVM_P && c->prec != FVM_FP64) {
+            CUDA_TRY(cudaMemcpyAsync(c->cur[field_slot(f)], host_in + off, N * 4, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            // (stream order: the next copy into the staging buffer waits for this conversion)
+            CUDA_TRY(cudaMemcpyAsync(stage, host_in + off, N * 4, cudaMemcpyHostToDevice, c->stream));
+            if (f == FVM_P && c->prec != FVM_FP64) CUDA_TRY(launch_p_from_float(stage, c->p, N, c->stream));
+            else CUDA_TRY(launch_convert(FVM_FP32, FVM_FP64, stage, f == FVM_P ? (void*)c->p : c->cur[field_slot(f)], N,
+                                         c->stream));
+        }
+        if (f != FVM_P) c->nut_valid = false;
+        off += (size_t)N;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return FVM_OK;
+}
+
 fvm_status fvm_set_poisson_rhs(fvm_case* c, const double* host_b, size_t n) {
     if (!c || !host_b) return fail(FVM_ERR_INVALID, "null case or buffer");
     const int64_t N = c->cd.N;

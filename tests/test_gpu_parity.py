@@ -205,6 +205,41 @@ def test_flat_buffers_match_the_field_dict(prec):
         assert np.array_equal(got[f], ref[f]), f
 
 
+@pytest.mark.parametrize("prec", [cases.FP64, cases.FP32, cases.BF16_MIXED], ids=["fp64", "fp32", "bf16"])
+def test_flat_float32_buffers(prec):
+    """read_flat / write_flat with float32 buffers (fvm_read_fields_f32 / fvm_write_fields_f32):
+    every field reads as its FP64 read rounded to FP32 (for an FP32-field case the state is
+    the stored value itself, p the double-float pair rounded once); written FP32 values read
+    back exactly, p included, in either storage."""
+    spec = channel_box(precision=prec, fixed_vcycles=2)
+    with binding.Case(spec) as c:
+        c.step(1)
+        ref = c.read()
+        flat = np.empty(7 * c.N, dtype=np.float32)
+        c.read_flat(flat)
+        for i, f in enumerate(cases.FIELDS):
+            want = ref[f].transpose(2, 1, 0).ravel().astype(np.float32)
+            assert np.array_equal(flat[i * c.N:(i + 1) * c.N], want), f
+        rng = np.random.default_rng(3)
+        new = (flat * (1.0 + 0.01 * rng.standard_normal(flat.size))).astype(np.float32)
+        c.write_flat(new)
+        got = c.read()
+        back = np.empty_like(new)
+        c.read_flat(back)
+        # a subset of fields: the others stay
+        c.write_flat(np.zeros(c.N, dtype=np.float32), fields=("T",))
+        after = c.read()
+    for i, f in enumerate(cases.FIELDS):
+        assert np.array_equal(got[f].transpose(2, 1, 0).ravel(), new[i * c.N:(i + 1) * c.N].astype(np.float64)), f
+    assert np.array_equal(back, new)
+    assert not after["T"].any()
+    for f in ("u", "v", "w", "p", "k", "omega"):
+        assert np.array_equal(after[f], got[f]), f
+    with binding.Case(spec) as c:
+        with pytest.raises(binding.FvmError):
+            c.read_flat(np.empty(7 * c.N - 1, dtype=np.float32))
+
+
 def test_zero_rhs_needs_no_cycles():
     """Uniform through-flow is discretely divergence free: b = 0, no V-cycle runs."""
     spec = cases.heated_channel_3d(32, 8, 8, mg_levels=3, init_perturb=0.0)
