@@ -633,6 +633,7 @@ template <> struct RawW<__nv_bfloat16, 8> {
 // name their rows of the plane three ahead, so that those loads later hit L2 instead of
 // waiting out a DRAM round trip.
 __device__ __forceinline__ void l2_prefetch(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void l1_prefetch(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 template <class TI, int MODE, int W>
 struct SweepVK {
@@ -697,6 +698,13 @@ __device__ void SweepVK<TI, MODE, W>::run(const BlockAt& at) const {
             l2_prefetch(ein + fb);
             l2_prefetch(r + fb);
             l2_prefetch(nbf + fb);
+        }
+        if (k + 1 < k1) {   // the next plane's rows into L1 (their loads open the next iteration)
+            const int nb = (k + 1) * sz;
+            l1_prefetch(ein + nb + om);
+            l1_prefetch(ein + nb + op);
+            l1_prefetch(r + nb + own);
+            l1_prefetch(nbf + nb + own);
         }
         C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
         C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);
@@ -1008,6 +1016,13 @@ __device__ int Resid0V4K<TI>::run(const BlockAt& at) const {
             l2_prefetch(b + fb);
             l2_prefetch(nbf + fb);
         }
+        if (k + 1 < k1) {   // the next plane's rows into L1 (their loads open the next iteration)
+            const int nb = (k + 1) * sz;
+            l1_prefetch(pp + nb + om);
+            l1_prefetch(pp + nb + op);
+            l1_prefetch(b + nb + own);
+            l1_prefetch(nbf + nb + own);
+        }
         FF left = {__shfl_up_sync(0xffffffffu, ec[3].h, 1, LR), __shfl_up_sync(0xffffffffu, ec[3].l, 1, LR)};
         FF right = {__shfl_down_sync(0xffffffffu, ec[0].h, 1, LR), __shfl_down_sync(0xffffffffu, ec[0].l, 1, LR)};
         if (lane == 0) left = xls;
@@ -1158,6 +1173,14 @@ __device__ void FcgDotVK<TR, TZ, W>::run(const BlockAt& at) const {
             l2_prefetch(r + fb);
             l2_prefetch(nbf + fb);
             if (have) l2_prefetch(dp + fb);
+        }
+        if (k + 1 < k1) {   // the next plane's rows into L1 (their loads open the next iteration)
+            const int nb = (k + 1) * sz;
+            l1_prefetch(zz + nb + om);
+            l1_prefetch(zz + nb + op);
+            l1_prefetch(r + nb + own);
+            l1_prefetch(nbf + nb + own);
+            if (have) l1_prefetch(dp + nb + own);
         }
         C left = __shfl_up_sync(0xffffffffu, R::get(ec, W - 1), 1, LR);
         C right = __shfl_down_sync(0xffffffffu, R::get(ec, 0), 1, LR);

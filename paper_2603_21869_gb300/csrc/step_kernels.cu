@@ -851,7 +851,7 @@ struct AdjRhsK {
     const double* ybar;     // ubar, vbar, wbar (first 3 N used)
     const double* lambda;   // A^{-T} q
     double* xbar;           // 3 N
-    double dt;
+    double ihdt[3];         // 1 / (h_a dt), formed on the host (no FP64 division per cell)
     __device__ void run(const BlockAt& at) const;
 };
 
@@ -876,7 +876,7 @@ __device__ void AdjRhsK::run(const BlockAt& at) const {
             if (cp == 2u) t += lc;
             if (cm == 0u) t -= 0.5 * (lc - lambda[c - stride]);
             if (cm == 2u) t -= lc;
-            x -= t * cd.inv_h[a] / dt;
+            x -= t * ihdt[a];
         }
         xbar[a * N + c] = x;
     }
@@ -1526,7 +1526,8 @@ cudaError_t launch_adj_grad(const CaseDev& cd, const LevelDev& L0, const double*
 
 cudaError_t launch_adj_rhs(const CaseDev& cd, const LevelDev& L0, const double* ybar, const double* lambda,
                            double* xbar, double dt, cudaStream_t s) {
-    return launch_k(AdjRhsK{cd, L0, ybar, lambda, xbar, dt}, grid3(cd), kBlock3, 0, s);
+    return launch_k(AdjRhsK{cd, L0, ybar, lambda, xbar, {cd.inv_h[0] / dt, cd.inv_h[1] / dt, cd.inv_h[2] / dt}},
+                    grid3(cd), kBlock3, 0, s);
 }
 
 cudaError_t launch_lambda2(int prec, const CaseDev& cd, StatePtrs in, double* out, cudaStream_t s) {
