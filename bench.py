@@ -445,10 +445,11 @@ def run_served(args, rank, ws, local, dist):
     t_start = srv.now()
     nxt = 0
     done = []
+    rid_of = {}   # request id -> index in the stream
     while len(done) < len(specs):
         now = srv.now() - t_start
         while nxt < len(specs) and arrivals[nxt] <= now:
-            srv.submit(specs[nxt], args.served_steps, t_arrive=t_start + float(arrivals[nxt]))
+            rid_of[srv.submit(specs[nxt], args.served_steps, t_arrive=t_start + float(arrivals[nxt]))] = nxt
             nxt += 1
         inf = srv.info()
         if inf["running"] == 0 and inf["queued"] == 0 and nxt < len(specs):
@@ -465,6 +466,12 @@ def run_served(args, rank, ws, local, dist):
     makespan = t_end - t_start
     cell_steps = sum(d["cells"] * d["steps"] for d in done)
     bad = [d for d in done if d["status"] != 0]
+    failures = []
+    for d in bad[:20]:
+        sp = specs[rid_of[d["id"]]]
+        failures.append({"request": rid_of[d["id"]], "status": d["status"], "steps_done": d["steps"],
+                         "kind": "channel" if not sp.boxes and not sp.vents else "room",
+                         "shape": [sp.nx, sp.ny, sp.nz], "rel_residual": d["rel_residual"]})
     compare = served_vs_fp64(args, specs, stream) if (ws == 1 and not args.no_compare and rank == 0) else None
     if dist:
         makespan, cell_steps = replicas.max_over_ranks(makespan), replicas.sum_over_ranks(cell_steps)
@@ -478,7 +485,7 @@ def run_served(args, rank, ws, local, dist):
                                        f"rounds of {args.chunk} steps",
                            "parallelism": f"replicas x{ws}", "l2": "not flushed (a serving loop)"},
                 "latency_s": {"p50": q(0.50), "p99": q(0.99), "max": lat[-1], "mean": statistics.mean(lat)},
-                "makespan_s": makespan, "requests": len(done), "failed": len(bad),
+                "makespan_s": makespan, "requests": len(done), "failed": len(bad), "failures": failures,
                 "server": info, "clocks": clk, "compare": compare,
                 "e2e": {"value": cell_steps / makespan, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0,

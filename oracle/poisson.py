@@ -301,7 +301,9 @@ class Multigrid:
         (d_prev, A d_prev), d = z - beta d_prev), then that step,
         p += alpha d; r = b - A p is recomputed from p.  With a fixed
         symmetric positive definite preconditioner in place of the V-cycle
-        this is preconditioned CG.  Inner products over fluid cells."""
+        this is preconditioned CG.  Inner products over fluid cells.  Should
+        (d, A d) come out <= 0 (by rounding only) the step restarts along z
+        alone."""
         lev = self.levels[0]
         fl = lev.fluid
 
@@ -315,11 +317,15 @@ class Multigrid:
             r = residual(lev, p, b)
             d = self.vcycle(np.zeros(lev.shape), r)
             q = apply_A(lev, d)
-            if dp is not None:
+            z, qz = d, q
+            if dp is not None and dot(dp, qp) > 0.0:
                 beta = dot(d, qp) / dot(dp, qp)
                 d = d - beta * dp
                 q = q - beta * qp
             dq = dot(d, q)
+            if not dq > 0.0:   # (d, A d) <= 0 only by rounding: restart along z alone
+                d, q = z, qz
+                dq = dot(d, q)
             alpha = dot(r, d) / dq if dq > 0.0 else 0.0
             p = np.where(fl, p + alpha * d, 0.0)
             dp, qp = d, q

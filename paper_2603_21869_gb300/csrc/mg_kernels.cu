@@ -2100,6 +2100,11 @@ static int sweep_planes(int tiles, int nz, int fixed) {
     return 1;
 }
 
+// eight cells per thread on BF16 levels: in batches, and on single-case levels of 2^22 cells or
+// more; a smaller level (the room's level 1, 2 M cells) takes four, for twice the threads (at
+// eight its residual-restriction launch had 256 blocks for 152 SMs)
+static bool wide8(const LevelDev& L) { return L.n[0] % 8 == 0 && (g_rec || L.N >= (1 << 22)); }
+
 template <class TI, int MODE>
 static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI* eout, double* p,
                               const SolveState* st, cudaStream_t s, float* z32 = nullptr) {
@@ -2108,7 +2113,7 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
         if (L.n[0] % 4 == 0 && (L.N >= (1 << 20) || g_rec)) {
             constexpr int W = vec_w<TI>();
             int zc = 0;
-            if (W == 8 && L.n[0] % 8 == 0) {
+            if (W == 8 && wide8(L)) {
                 const int lrl = vw_lrl(L.n[0], 8);
                 const dim3 grid = vw_grid(L, 8, lrl, zc);
                 return launch_k(SweepVK<TI, MODE, vec_w<TI>()>{L, ein, r, eout, p, st, zc, z32, lrl}, grid,
@@ -2156,7 +2161,7 @@ cudaError_t launch_resid_restrict(int inner, const LevelDev& Lf, const LevelDev&
                                   void* rc, void* ec0, const SolveState* st, cudaStream_t s) {
     cudaError_t err = cudaSuccess;
     if (inner != FVM_FP64 && v4_transfer_ok<float>(Lf)) {
-        const int W = inner == FVM_BF16_MIXED && Lf.n[0] % 8 == 0 ? 8 : 4;
+        const int W = inner == FVM_BF16_MIXED && wide8(Lf) ? 8 : 4;
         const int lrl = vw_lrl(Lf.n[0], W), wx = W << lrl, wy = TY << (5 - lrl);
         const dim3 grid((unsigned)((Lf.n[0] + wx - 1) / wx), (unsigned)((Lc.n[1] + wy - 1) / wy), (unsigned)Lc.n[2]);
         if (inner == FVM_FP32)
@@ -2192,7 +2197,7 @@ cudaError_t launch_prolong_add(int inner, const LevelDev& Lf, const LevelDev& Lc
             return launch_k(ProlongVK<float, 4>{Lf, Lc, (const float*)ec, (float*)e, st, zc, lrl}, grid, dim3(TX, TY),
                             0, s);
         }
-        if (Lf.n[0] % 8 == 0) {
+        if (wide8(Lf)) {
             const int lrl = vw_lrl(Lf.n[0], 8);
             const dim3 grid = vw_grid(Lf, 8, lrl, zc);
             return launch_k(ProlongVK<__nv_bfloat16, 8>{Lf, Lc, (const __nv_bfloat16*)ec, (__nv_bfloat16*)e, st, zc,

@@ -165,3 +165,16 @@ def test_fcg_four_cell_kernels_in_a_batch_within_1e4_of_fp64_oracle(prec):
         o = OracleCase(s.replace(precision=cases.FP64, krylov=0)).step(6)
         for f in ("u", "v", "w", "T", "k", "omega"):
             assert rel_err(got[i][f], o.fields()[f]) <= 1e-4, (i, f)
+
+
+def test_served_room_converges_with_two_cycles_per_outer_residual():
+    """A 256x128x128 room (seed 395) on which the one-direction flexible-CG step stalls near a
+    relative residual of 0.29 with one V-cycle per outer residual in FP64 (plain V-cycles converge
+    at about 0.6 per cycle there): the served form's two BF16 V-cycles per outer residual bring
+    every solve of the first steps to the tolerance."""
+    spec = cases.room_3d(256, 128, 128, seed=395, mg_levels=5, h=0.04, precision=cases.BF16_MIXED, krylov=1,
+                         pre_sweeps=2, post_sweeps=2, inner_cycles=2, mg_rel_tol=1e-8)
+    with binding.Case(spec) as c:
+        for _ in range(3):
+            st = c.step(1)
+            assert st["rel_residual"] <= 1e-8

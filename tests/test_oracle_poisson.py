@@ -489,3 +489,31 @@ def test_chebyshev_smoother_keeps_the_fixed_point_and_needs_fewer_cycles():
         _, counts[sm], rel = mg.fcg_solve(np.zeros(lev.shape), b, 60, 1e-8, 0)
         assert rel <= 1e-8
     assert counts[1] < counts[0], counts
+
+
+def test_fcg_restarts_when_the_kept_direction_cancels_the_new_one():
+    """With a preconditioner whose directions carry no descent ((r, B r) = 0 for a skew-symmetric
+    B) the step length is zero, so the next direction equals the kept one: orthogonalising leaves
+    d = 0 and (d, A d) = 0, and the step restarts along z alone (the rule the GPU's flexible-CG
+    pass applies) instead of dividing by zero; p stays where it was."""
+    spec = _spec(8, 8, 4, L=(1.0, 1.0, 0.5), outlet_faces=(1,))
+    mg = Multigrid(Geometry(spec), 2)
+    lev = mg.levels[0]
+    fl = lev.fluid
+    n = int(fl.sum())
+    rng = np.random.default_rng(5)
+    K = rng.standard_normal((n, n))
+    S = 0.01 * (K - K.T)                      # skew-symmetric: (r, S r) = 0
+
+    def skew(p, r):
+        out = np.zeros(lev.shape)
+        out[fl] = S @ r[fl]
+        return out
+
+    mg.vcycle = skew
+    b = np.where(fl, rng.standard_normal(lev.shape), 0.0)
+    p0 = np.zeros(lev.shape)
+    for m in range(1, 5):
+        p, cycles, rel = mg.fcg_solve(p0, b, 0, 0.0, m)
+        assert cycles == m and np.isfinite(rel)
+        assert np.allclose(p, p0, atol=1e-14), m
