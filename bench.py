@@ -51,7 +51,12 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's denominator is
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # from one ncu capture, with the SHA-256 prefix of the source file that kernel was built from
 # when the counters were taken: a changed source reports null until it is captured again.
-TRAFFIC = {}
+TRAFFIC = {
+    # fcg_L0 = FcgDotVK + FcgUpdVK on the room with BF16 corrections, one iteration with a kept
+    # direction: ncu dram__bytes_read.sum + dram__bytes_write.sum of the two launches
+    # (204.5 + 449.2 MB; the algorithmic 42 B per cell is 704.6 MB)
+    ("room", "bf16", "fcg_L0"): {"bytes": 653.7e6, "src": "mg_kernels.cu", "sha": "f2dc99bb34bebd8f"},
+}
 # the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell
 TRAFFIC_PER_CELL = {}
 
