@@ -1552,6 +1552,52 @@ __device__ __forceinline__ C cta_apply_A(const LevelDev& L, uint32_t f, const C*
     return apply_A_with<C>(L, f, c, eP, [&](int q) { return e[q]; });
 }
 
+// A level's stencil constants in registers for the coarse CTA's cell loops (the level
+// descriptions live in shared memory, which the loops also write, so the compiler would reload
+// them for every cell), and A e with them: a cell whose face codes are all 0 on three active
+// axes takes the six neighbours without the per-face code selects, in the same arithmetic order
+// as apply_A_with, so both forms give the same value
+template <class C>
+struct CtaStencil {
+    int sy, sz;
+    C ih[3];
+    bool act[3];
+    bool all3;
+};
+
+template <class C>
+__device__ __forceinline__ CtaStencil<C> cta_stencil(const LevelDev& L) {
+    CtaStencil<C> S;
+    S.sy = L.n[0];
+    S.sz = L.n[0] * L.n[1];
+    for (int a = 0; a < 3; ++a) {
+        S.ih[a] = LP<C>::ih2(L, a);
+        S.act[a] = L.active[a] != 0;
+    }
+    S.all3 = S.act[0] && S.act[1] && S.act[2];
+    return S;
+}
+
+template <class C>
+__device__ __forceinline__ C cta_A(const CtaStencil<C>& S, uint32_t f, const C* e, int c, C eP) {
+    if (S.all3 && (f & 0xfffu) == 0u) {
+        C acc = ((eP - e[c - 1]) + (eP - e[c + 1])) * S.ih[0];
+        acc += ((eP - e[c - S.sy]) + (eP - e[c + S.sy])) * S.ih[1];
+        acc += ((eP - e[c - S.sz]) + (eP - e[c + S.sz])) * S.ih[2];
+        return acc;
+    }
+    const int st[3] = {1, S.sy, S.sz};
+    C acc = (C)0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!S.act[a]) continue;
+        const C lo = nb_val<C>((f >> (4 * a)) & 3u, c - st[a], eP, [&](int q) { return e[q]; });
+        const C hi = nb_val<C>((f >> (4 * a + 2)) & 3u, c + st[a], eP, [&](int q) { return e[q]; });
+        acc += ((eP - lo) + (eP - hi)) * S.ih[a];
+    }
+    return acc;
+}
+
 // the weight of sweep i on one side (0 pre, 1 post) of a coarse-CTA level
 template <class C> __device__ __forceinline__ C coarse_weight(const CoarseLevels& cl, const LevelDev& L, int side, int i);
 template <> __device__ __forceinline__ double coarse_weight<double>(const CoarseLevels& cl, const LevelDev& L, int side,
@@ -1595,10 +1641,19 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // level descriptions and array bases live in shared memory (one copy per CTA)
     __shared__ LevelDev lvs[FVM_MAX_LEVELS];
-    __shared__ C* E0[FVM_MAX_LEVELS];
-    __shared__ C* E1[FVM_MAX_LEVELS];
-    __shared__ C* R[FVM_MAX_LEVELS];
-    __shared__ uint16_t* F[FVM_MAX_LEVELS];
+    // the arrays' offsets into the dynamic shared memory (elements of C, codes in 16-bit units):
+    // pointers formed from smem_raw here let the compiler address them as shared memory (pointers
+    // kept in a shared array would be generic, each access a generic load)
+    __shared__ int E0o[FVM_MAX_LEVELS];
+    __shared__ int E1o[FVM_MAX_LEVELS];
+    __shared__ int Ro[FVM_MAX_LEVELS];
+    __shared__ int Fo[FVM_MAX_LEVELS];
+    C* const Cs = reinterpret_cast<C*>(smem_raw);
+    uint16_t* const Us = reinterpret_cast<uint16_t*>(smem_raw);
+    auto E0 = [&](int l) { return Cs + E0o[l]; };
+    auto E1 = [&](int l) { return Cs + E1o[l]; };
+    auto R = [&](int l) { return Cs + Ro[l]; };
+    auto F = [&](int l) { return Us + Fo[l]; };
     const int T = blockDim.x, tid = threadIdx.x;
     // the level descriptions, copied word by word by all threads
     {
@@ -1607,52 +1662,53 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         for (int w = tid; w < words; w += T) reinterpret_cast<uint32_t*>(lvs)[w] = src[w];
     }
     if (tid == 0) {
-        C* q = (C*)smem_raw;
+        int q = 0;
         for (int l = 0; l < cl.nl; ++l) {
             const int N = (int)cl.lv[l].N;
-            E0[l] = q; q += N;
-            E1[l] = q; q += N;
-            R[l] = q; q += N;
+            E0o[l] = q; q += N;
+            E1o[l] = q; q += N;
+            Ro[l] = q; q += N;
         }
-        uint16_t* u = (uint16_t*)q;
+        int u = q * (int)(sizeof(C) / sizeof(uint16_t));
         for (int l = 0; l < cl.nl; ++l) {
-            F[l] = u;
-            u += cl.lv[l].N;
+            Fo[l] = u;
+            u += (int)cl.lv[l].N;
         }
     }
     __syncthreads();
     for (int l = 0; l < cl.nl; ++l) {
         const int N = (int)lvs[l].N;
         const uint16_t* src = lvs[l].nbf;   // the level's codes in global memory
-        for (int c = tid; c < N; c += T) F[l][c] = src[c];
+        for (int c = tid; c < N; c += T) F(l)[c] = src[c];
     }
     {
         const int N0 = (int)lvs[0].N;
-        for (int c = tid; c < N0; c += T) R[0][c] = to_c<C>(r_in[c]);
+        for (int c = tid; c < N0; c += T) R(0)[c] = to_c<C>(r_in[c]);
     }
     __syncthreads();
     __shared__ int cur[FVM_MAX_LEVELS];
     // down: pre-smooth, restrict
     for (int l = 0; l + 1 < cl.nl; ++l) {
         const LevelDev& L = lvs[l];
-        const uint16_t* const fl = F[l];
-        C* const rl = R[l];
+        const CtaStencil<C> S = cta_stencil<C>(L);
+        const uint16_t* const fl = F(l);
+        C* const rl = R(l);
         const int N = (int)L.N;
         const C iD = LP<C>::iD(L);
         const C w0 = coarse_weight<C>(cl, L, 0, 0);
-        for (int c = tid; c < N; c += T) E0[l][c] = is_solid(fl[c]) ? (C)0 : w0 * rl[c] * iD;
+        for (int c = tid; c < N; c += T) E0(l)[c] = is_solid(fl[c]) ? (C)0 : w0 * rl[c] * iD;
         __syncthreads();
         int s = 0;
         for (int it = 1; it < cl.pre; ++it) {
             const C w = coarse_weight<C>(cl, L, 0, it);
-            C* ein = s ? E1[l] : E0[l];
-            C* eo = s ? E0[l] : E1[l];
+            C* ein = s ? E1(l) : E0(l);
+            C* eo = s ? E0(l) : E1(l);
             for (int c = tid; c < N; c += T) {
                 const uint32_t f = fl[c];
                 C v = (C)0;
                 if (!is_solid(f)) {
                     const C eP = ein[c];
-                    v = eP + w * (rl[c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
+                    v = eP + w * (rl[c] - cta_A<C>(S, f, ein, c, eP)) * iD;
                 }
                 eo[c] = v;
             }
@@ -1661,11 +1717,11 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         }
         if (tid == 0) cur[l] = s;
         const LevelDev& Lc = lvs[l + 1];
-        const C* e = s ? E1[l] : E0[l];
+        const C* e = s ? E1(l) : E0(l);
         const int fx = L.active[0] ? 2 : 1, fy = L.active[1] ? 2 : 1, fz = L.active[2] ? 2 : 1;
         const int Nc = (int)Lc.N, cn0 = Lc.n[0], cn1 = Lc.n[1], n0 = L.n[0], n1 = L.n[1];
         const float icn0 = 1.0f / (float)cn0, icn01 = 1.0f / (float)(cn0 * cn1);
-        C* const rc = R[l + 1];
+        C* const rc = R(l + 1);
         // one child per thread: eight consecutive lanes hold one coarse cell's children
         // (missing children of a collapsed axis add 0) and sum them by a fixed shuffle tree
         const int items = 8 * Nc, bound = (items + 31) & ~31;
@@ -1680,7 +1736,7 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
                 const int I = rem - J * cn0;
                 const int c = (I * fx + dx) + n0 * ((J * fy + dy) + n1 * (K * fz + dz));
                 const uint32_t f = fl[c];
-                if (!is_solid(f)) v = rl[c] - cta_apply_A<C>(L, f, e, c, e[c]);
+                if (!is_solid(f)) v = rl[c] - cta_A<C>(S, f, e, c, e[c]);
             }
             v += __shfl_xor_sync(0xffffffffu, v, 1);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -1699,15 +1755,15 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
             if constexpr (sizeof(C) == 8) {
                 double acc = 0.0;
                 const double* a = Ainv + (size_t)row * N;
-                for (int col = lane; col < N; col += 32) acc += __ldg(a + col) * (double)R[l][col];
+                for (int col = lane; col < N; col += 32) acc += __ldg(a + col) * (double)R(l)[col];
                 for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-                if (lane == 0) E0[l][row] = (C)acc;
+                if (lane == 0) E0(l)[row] = (C)acc;
             } else {
                 float acc = 0.0f;
                 const float* a = reinterpret_cast<const float*>(Ainv + (size_t)N * N) + (size_t)row * N;
-                for (int col = lane; col < N; col += 32) acc = fmaf(__ldg(a + col), R[l][col], acc);
+                for (int col = lane; col < N; col += 32) acc = fmaf(__ldg(a + col), R(l)[col], acc);
                 for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-                if (lane == 0) E0[l][row] = acc;
+                if (lane == 0) E0(l)[row] = acc;
             }
         }
         if (tid == 0) cur[l] = 0;
@@ -1717,19 +1773,24 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
     for (int l = cl.nl - 2; l >= 0; --l) {
         const LevelDev& L = lvs[l];
         const LevelDev& Lc = lvs[l + 1];
-        const uint16_t* const fl = F[l];
+        const CtaStencil<C> S = cta_stencil<C>(L);
+        C* const Rl = R(l);
+        const uint16_t* const fl = F(l);
+        const uint16_t* const fc = F(l + 1);
+        // the prolongation's axes and coarse extents in registers (see CtaStencil)
+        const int fa[3] = {L.active[0], L.active[1], L.active[2]};
+        const int cn[3] = {Lc.n[0], Lc.n[1], Lc.n[2]};
         const int N = (int)L.N, n0 = L.n[0], n1 = L.n[1];
         const float in0 = 1.0f / (float)n0, in01 = 1.0f / (float)(n0 * n1);
-        const C* ec = cur[l + 1] ? E1[l + 1] : E0[l + 1];
-        C* e = cur[l] ? E1[l] : E0[l];
+        const C* ec = cur[l + 1] ? E1(l + 1) : E0(l + 1);
+        C* e = cur[l] ? E1(l) : E0(l);
         for (int c = tid; c < N; c += T) {
             if (is_solid(fl[c])) continue;
             const int k = small_div(c, in01);
             const int rem = c - k * n0 * n1;
             const int j = small_div(rem, in0);
             const int i = rem - j * n0;
-            const uint16_t* const fc = F[l + 1];
-            e[c] += prolong_at<C>(L.active, Lc.n, i, j, k, [&](int q) { return ec[q]; },
+            e[c] += prolong_at<C>(fa, cn, i, j, k, [&](int q) { return ec[q]; },
                                   [&](int q) { return (uint32_t)fc[q]; });
         }
         __syncthreads();
@@ -1737,14 +1798,14 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         const C iD = LP<C>::iD(L);
         for (int it = 0; it < cl.post; ++it) {
             const C w = coarse_weight<C>(cl, L, 1, it);
-            C* ein = s ? E1[l] : E0[l];
-            C* eo = s ? E0[l] : E1[l];
+            C* ein = s ? E1(l) : E0(l);
+            C* eo = s ? E0(l) : E1(l);
             for (int c = tid; c < N; c += T) {
                 const uint32_t f = fl[c];
                 C v = (C)0;
                 if (!is_solid(f)) {
                     const C eP = ein[c];
-                    v = eP + w * (R[l][c] - cta_apply_A<C>(L, f, ein, c, eP)) * iD;
+                    v = eP + w * (Rl[c] - cta_A<C>(S, f, ein, c, eP)) * iD;
                 }
                 eo[c] = v;
             }
@@ -1755,7 +1816,7 @@ __device__ void coarse_cta_body(const CoarseLevels& cl, const TI* __restrict__ r
         __syncthreads();
     }
     {
-        const C* e = cur[0] ? E1[0] : E0[0];
+        const C* e = cur[0] ? E1(0) : E0(0);
         const int N0 = (int)lvs[0].N;
         for (int c = tid; c < N0; c += T) e_out[c] = from_c<TI, C>(e[c]);
     }
