@@ -1346,9 +1346,11 @@ __device__ void ProlongVK<TI, W>::run(const BlockAt& at) const {
         const bool outK = qk < 0 || qk >= NZ;
         const int Qk = outK ? Pk : qk, sK = qk < 0 ? 0 : 1;
         const C wz0 = zact ? (C)0.75 : (C)1, wz1 = zact ? (C)0.25 : (C)0;
-        C add[W];
+        // the four coarse rows (parent and neighbour along y and z, ghosts signed) combined with
+        // their y-z weights into one row first, then the x interpolation and the shuffles once
+        C cvc[H], lc = (C)0, rc = (C)0, lg = (C)0, rg = (C)0;
 #pragma unroll
-        for (int t = 0; t < W; ++t) add[t] = (C)0;
+        for (int h = 0; h < H; ++h) cvc[h] = (C)0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int jj = (q & 1) ? Qj : Pj, kk = (q & 2) ? Qk : Pk;
@@ -1371,18 +1373,25 @@ __device__ void ProlongVK<TI, W>::run(const BlockAt& at) const {
                 if (lane == 0 && !first) lft = ghost_signed(__ldg(cnbf + row + I0 - 1), gy, sJ, gz, sK, lft);
                 if (lane == LR - 1 && !last) rgt = ghost_signed(__ldg(cnbf + row + I0 + H), gy, sJ, gz, sK, rgt);
             }
-            C left = __shfl_up_sync(0xffffffffu, cv[H - 1], 1, LR);
-            C right = __shfl_down_sync(0xffffffffu, cv[0], 1, LR);
-            if (lane == 0) left = lft;
-            if (lane == LR - 1) right = rgt;
-            if (first) left = (cw[0] & 3u) == 2u ? -cv[0] : cv[0];                         // x- ghost of cell I0
-            if (last) right = ((cw[H - 1] >> 2) & 3u) == 2u ? -cv[H - 1] : cv[H - 1];      // x+ ghost of the last
 #pragma unroll
-            for (int t = 0; t < W; ++t) {
-                const int h = t >> 1;
-                const C nb = (t & 1) ? (h == H - 1 ? right : cv[h + 1]) : (h == 0 ? left : cv[h - 1]);
-                add[t] += w * ((C)0.75 * cv[h] + (C)0.25 * nb);
-            }
+            for (int h = 0; h < H; ++h) cvc[h] = fma(w, cv[h], cvc[h]);
+            lc = fma(w, lft, lc);
+            rc = fma(w, rgt, rc);
+            if (first) lg = fma(w, (cw[0] & 3u) == 2u ? -cv[0] : cv[0], lg);                       // x- ghost of I0
+            if (last) rg = fma(w, ((cw[H - 1] >> 2) & 3u) == 2u ? -cv[H - 1] : cv[H - 1], rg);   // x+ of the last
+        }
+        C left = __shfl_up_sync(0xffffffffu, cvc[H - 1], 1, LR);
+        C right = __shfl_down_sync(0xffffffffu, cvc[0], 1, LR);
+        if (lane == 0) left = lc;
+        if (lane == LR - 1) right = rc;
+        if (first) left = lg;
+        if (last) right = rg;
+        C add[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            const int h = t >> 1;
+            const C nb = (t & 1) ? (h == H - 1 ? right : cvc[h + 1]) : (h == 0 ? left : cvc[h - 1]);
+            add[t] = (C)0.75 * cvc[h] + (C)0.25 * nb;
         }
         if (in) {
             const int c = ic + nx * (jc + ny * k);
