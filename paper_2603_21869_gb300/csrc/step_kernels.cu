@@ -256,6 +256,7 @@ struct DestructionK {
     static constexpr int kThreads = BX * BY * BZ;
     static constexpr bool kNoShared = true;   // run() uses no shared memory
     static constexpr int kMinBlocks = sizeof(C) == 4 ? 3 : 1;   // FP32: at most 85 registers
+    static constexpr int kMinBlocksMany = sizeof(C) == 4 ? 4 : 1;   // batched FP32: at most 64
     __device__ bool live() const { return true; }
     CaseDev cd;
     StatePtrs in;
