@@ -962,7 +962,9 @@ template <class TI>
 struct Resid0V4K {
     static constexpr int kThreads = TX * TY;
     static constexpr int kMinBlocks = 3;       // at most 80 registers
-    static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
+    // the batched form needs more (BF16 spills at 80; with FP32 corrections 80 registers, three
+    // blocks per SM, measured slower on 64 channels than 128 and two)
+    static constexpr int kMinBlocksMany = 2;
     LevelDev L;
     const double* p;
     const float* b;
@@ -1118,7 +1120,7 @@ template <class TR, class TZ, int W>
 struct FcgDotVK {
     static constexpr int kThreads = TX * TY;
     static constexpr int kMinBlocks = 4;       // at most 64 registers
-    static constexpr int kMinBlocksMany = 2;   // the batched form needs more (spills at 80)
+    static constexpr int kMinBlocksMany = 3;   // the batched form: at most 80 registers
     LevelDev L;
     const TZ* z;
     const TR* r;
