@@ -225,6 +225,12 @@ def run_reference(args, spec, label, rank, ws, workload="channel"):
     print(json.dumps(line), flush=True)
 
 
+def arith_dtype(precision):
+    """The arithmetic type of a precision mode: FP64, or FP32 (fields and corrections computed
+    in FP32, BF16 only storing the multigrid corrections; config.precision names the storage)."""
+    return "f64" if precision == "f64" else "f32"
+
+
 def parse_params(text):
     """PRE,POST,INNER,PLANES,KRYLOV[,COARSE[,SMOOTHER]] -> seven ints (COARSE, SMOOTHER default to 0)."""
     v = [int(x) for x in text.split(",")]
@@ -416,7 +422,7 @@ def run_batched(args, rank, ws, local, dist):
         sizes = sorted({(sp.nx, sp.ny, sp.nz) for sp in specs})
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": arith_dtype(args.precision),
                 "data": "synthetic",
                 "config": {"workload": f"batched_channels {len(specs)} cases, 64^3 .. 192x96x96, 5-level V-cycles, "
                                        "rel tol 1e-8, one batch per GPU",
@@ -487,7 +493,7 @@ def run_served(args, rank, ws, local, dist):
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": cell_steps / makespan, "unit": "cell-steps/s", "n_gpus": ws,
                 "steps": args.served_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16-mixed", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"served: Poisson arrivals at {args.rate}/s of {len(specs)} requests per GPU "
                                        f"(rooms 64^3 .. 256x128x128 with seeded vents, boxes, heat; 20 % channels), "
                                        f"{args.served_steps} steps each, HBM budget {args.budget_gb} GB, "
@@ -852,7 +858,7 @@ def main():
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": args.precision, "data": "synthetic",
+                "dtype": arith_dtype(args.precision), "data": "synthetic",
                 "config": {"workload": label, "cells_per_gpu": N, "precision": args.precision,
                            "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps",
                            "autotune": tuning},
