@@ -3,7 +3,8 @@
 Every stage of a step except the pressure solve is local: a cell's update reads
 the state within one cell of it (face states, cell gradients and the pointwise
 eddy viscosity of the two cells beside a face), and an explicit stage of s
-Runge-Kutta substeps within s cells.  So the oracle can give the exact result
+Runge-Kutta substeps within s cells; a whole step, given its pressure, within
+three (forward Euler).  So the oracle can give the exact result
 of a stage at sampled cells of a grid too large for it to step whole: cut a
 window of the state with a margin of MARGIN cells, build the window as a case
 of its own (the same cell size, the domain faces and vents it touches, the
@@ -21,7 +22,7 @@ from oracle.geometry import Geometry
 from oracle.poisson import poisson_rhs, project
 from oracle.transport import explicit_stage_rk
 
-MARGIN = 3
+MARGIN = 3   # the reach of a whole step's local part, and of a three-stage explicit stage
 STATE = ("u", "v", "w", "T", "k", "omega")
 
 
@@ -101,3 +102,20 @@ class Window:
         (pp,) = self.take([p])
         out = project(self.geo, self.geo.level0, u, v, w, pp, dt)
         return {f: x[self.inner] for f, x in zip(("u", "v", "w"), out)}
+
+    def step(self, state, p, dt, stages=1):
+        """One whole step from `state` with the step's pressure p (the solve's result, which
+        a window cannot form): the destruction half step, the explicit stage, the second half
+        step, the right-hand side b and the projection (Section 2.6).  The velocity after the
+        explicit stage reaches two cells (one, through the first half step's k and omega, one
+        more); b and the second half step's k and omega three.  Returns (fields, b) at the
+        exact cells."""
+        u, v, w, T_, k, om = self.take(state)
+        k, om = destruction_step(self.geo, u, v, w, k, om, 0.5 * dt)
+        u, v, w, T_, k, om = explicit_stage_rk(self.geo, [u, v, w, T_, k, om], dt, stages)
+        k, om = destruction_step(self.geo, u, v, w, k, om, 0.5 * dt)
+        b = poisson_rhs(self.geo, u, v, w, dt)
+        (pp,) = self.take([p])
+        u, v, w = project(self.geo, self.geo.level0, u, v, w, pp, dt)
+        out = dict(zip(STATE, (u, v, w, T_, k, om)))
+        return {f: x[self.inner] for f, x in out.items()}, b[self.inner]

@@ -3,9 +3,10 @@ the whole grid: on a room whose windows hold box edges and corners, a ceiling
 inlet vent, the floor outlet, domain edges and corners and plain interior, the
 exact cells of every window equal the whole-grid result bit for bit, for the
 destruction half step, the explicit stage (forward Euler and the three-stage
-Runge-Kutta form, whose reach is the margin), the right-hand side and the
-projection.  A margin one cell short of the reach changes a cell of the
-Runge-Kutta stage (so the check can fail)."""
+Runge-Kutta form), the right-hand side, the projection and a whole step given
+its pressure.  A margin one cell short of the reach changes a cell of the
+three-stage Runge-Kutta stage and of a step's right-hand side and k, so the
+check can fail."""
 import numpy as np
 import pytest
 
@@ -70,11 +71,29 @@ def test_windowed_stages_equal_whole_grid_stages(room):
             assert np.array_equal(pr[f], pu[f][win.full]), (c, f)
 
 
+def test_windowed_step_equals_whole_grid_step(room):
+    """A whole oracle step (its dt and pressure taken as given) on the windows."""
+    spec, o = room
+    state = [x.copy() for x in o.state]
+    o2 = OracleCase(spec, state=state, p=o.p).step(1)
+    want = o2.fields()
+    for c in centers(spec):
+        win = ow.Window(spec, c, (12, 10, 8))
+        got, b = win.step(state, o2.p, o2.dt)
+        assert np.array_equal(b, o2.b[win.full]), c
+        for f in ow.STATE:
+            assert np.array_equal(got[f], want[f][win.full]), (c, f)
+
+
 def test_a_margin_short_of_the_reach_is_detected(room, monkeypatch):
     spec, o = room
     state = [x.copy() for x in o.state]
     ex3 = dict(zip(ow.STATE, explicit_stage_rk(o.geo, state, o.dt, 3)))
+    o2 = OracleCase(spec, state=state, p=o.p).step(1)
     monkeypatch.setattr(ow, "MARGIN", 2)
     win = ow.Window(spec, (spec.nx // 2, spec.ny // 2, spec.nz // 2), (12, 10, 8))
     e3 = win.explicit(state, o.dt, 3)
     assert any(not np.array_equal(e3[f], ex3[f][win.full]) for f in ow.STATE)
+    got, b = win.step(state, o2.p, o2.dt)
+    assert not np.array_equal(b, o2.b[win.full])
+    assert not np.array_equal(got["k"], o2.fields()["k"][win.full])
