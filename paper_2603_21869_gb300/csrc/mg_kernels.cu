@@ -2111,13 +2111,14 @@ cudaError_t launch_solve_begin(SolveState* st, cudaStream_t s) {
     return launch_k(SolveBeginK{st}, dim3(1), dim3(1), 0, s);
 }
 
-static int sweep_planes(int tiles, int nz, int fixed);
+static int sweep_planes(int tiles, int nz, int fixed, int per_sm);
 
-// vector kernels: the block's x-y extent for W cells per thread and the row segments of lrl
-static dim3 vw_grid(const LevelDev& L, int W, int lrl, int& zc) {
+// vector kernels: the block's x-y extent for W cells per thread and the row segments of lrl;
+// per_sm: the blocks per SM the plane rule aims for
+static dim3 vw_grid(const LevelDev& L, int W, int lrl, int& zc, int per_sm = 8) {
     const int wx = W << lrl, wy = TY << (5 - lrl);
     const int tiles = ((L.n[0] + wx - 1) / wx) * ((L.n[1] + wy - 1) / wy);
-    zc = sweep_planes(tiles, L.n[2], L.zc_fixed);
+    zc = sweep_planes(tiles, L.n[2], L.zc_fixed, per_sm);
     return dim3((unsigned)((L.n[0] + wx - 1) / wx), (unsigned)((L.n[1] + wy - 1) / wy), (unsigned)((L.n[2] + zc - 1) / zc));
 }
 static dim3 v4_grid(const LevelDev& L, int lrl, int& zc) { return vw_grid(L, 4, lrl, zc); }
@@ -2160,15 +2161,19 @@ static dim3 walk_grid(const LevelDev& L, int kz) {
                 (unsigned)((L.n[2] + kz - 1) / kz));
 }
 
-// planes per block: the most that still give about eight blocks per SM (one plane per
-// block on grids too small for that)
-static int sweep_planes(int tiles, int nz, int fixed) {
+// planes per block: the most that still give about per_sm blocks per SM (one plane per
+// block on grids too small for that).  The sweep aims for 16: it has no block reduction, and
+// shorter columns in more blocks balance better (the room's level-0 sweep: 42.3 us at four
+// planes a block, 37.3 at two, 40.0 at one); the kernels that end in a block reduction (the
+// residual, the inner products) aim for 8 (at two planes a block both measured about a third
+// slower, at eight or more planes a few per cent slower).
+static int sweep_planes(int tiles, int nz, int fixed, int per_sm) {
     if (fixed > 0) return fixed < nz ? fixed : nz;
     // in a batch the cases' blocks add up: eight-plane columns (measured on 64 channels against
     // 4, 16 and 32: fewer re-read planes than 4, better balance than 16 or 32)
     if (g_rec) return nz < 8 ? nz : 8;
     for (int zc : {32, 16, 8, 4, 2})
-        if (tiles * ((nz + zc - 1) / zc) >= 8 * 152) return zc;
+        if (tiles * ((nz + zc - 1) / zc) >= per_sm * 152) return zc;
     return 1;
 }
 
@@ -2187,12 +2192,12 @@ static cudaError_t sweep_walk(const LevelDev& L, const TI* ein, const TI* r, TI*
             int zc = 0;
             if (W == 8 && wide8(L)) {
                 const int lrl = vw_lrl(L.n[0], 8);
-                const dim3 grid = vw_grid(L, 8, lrl, zc);
+                const dim3 grid = vw_grid(L, 8, lrl, zc, 16);
                 return launch_k(SweepVK<TI, MODE, vec_w<TI>()>{L, ein, r, eout, p, st, zc, z32, lrl}, grid,
                                 dim3(TX, TY), 0, s);
             }
             const int lrl = vw_lrl(L.n[0], 4);
-            const dim3 grid = vw_grid(L, 4, lrl, zc);
+            const dim3 grid = vw_grid(L, 4, lrl, zc, 16);
             return launch_k(SweepVK<TI, MODE, 4>{L, ein, r, eout, p, st, zc, z32, lrl}, grid, dim3(TX, TY), 0, s);
         }
     }
