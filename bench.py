@@ -212,7 +212,7 @@ def run_reference(args, spec, label, rank, ws, workload="channel"):
         c.step()
     el = time.perf_counter() - t0
     v = sp.cells * args.steps / el
-    # n_gpus: the launch's N (the driver's key); the oracle itself runs on one host core
+    # n_gpus: the launch's N (the --gpus value); the oracle itself runs on one host core
     line = {"impl": "reference", "metric": "cell-steps/s", "value": v, "unit": "cell-steps/s", "n_gpus": ws,
             "host_only": True,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
