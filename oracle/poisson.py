@@ -36,7 +36,7 @@ from .geometry import U, V, W, FK_SOLID, D_op, L_op, pressure_face_states
 
 # ------------------------------------------------------------------ level 0
 def poisson_rhs(geo, u, v, w, dt):
-    """b = -div(u*) / dt with face velocities L * BC(u*) (Algorithm 1 lines on b)."""
+    """b = -div(u*) / dt with face velocities L * BC(u*) (the right-hand side of Algorithm 1; Eq. pc_residual)."""
     div = np.zeros(geo.shape)
     for axis, (phi, f) in enumerate(((u, U), (v, V), (w, W))):
         if geo.shape[axis] == 1:
