@@ -2,9 +2,10 @@
 512 x 256 x 128 room (16.8 M cells: vents, outlet, heated boxes, buoyancy)
 with the multigrid parameters the autotuner picks for it (V(2,2), one V-cycle
 per outer residual, the flexible-CG step, Chebyshev sweep weights), BF16 and
-FP32 corrections; and the 64 uneven channels (57.5 M cells) stepped as one
+FP32 corrections; the 64 uneven channels (57.5 M cells) stepped as one
 batch with theirs (V(3,3), two V-cycles per outer residual, the flexible-CG
-step, Chebyshev weights), FP32.
+step, Chebyshev weights), FP32; and the served stream's largest room
+(256 x 128 x 128) served in a mix, BF16 corrections.
 
 The oracle cannot step these grids in a test's time, so the local part of the
 path is checked on windows of the GPU's own state (tests/oracle_window.py: the
@@ -22,6 +23,7 @@ import pytest
 
 from oracle.geometry import Geometry
 from oracle.poisson import residual
+from oracle.step import stable_dt, time_step
 from paper_2603_21869_gb300 import binding, build, cases
 
 import oracle_window as ow
@@ -33,6 +35,7 @@ TOL_STEP = 1e-4   # a whole step
 STATE = ow.STATE
 WIN = (16, 16, 16)
 BATCH_CELLS = 57_000_000   # the 64 channels hold 57.5 M cells
+SERVED_BIG = (256, 128, 128)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -198,3 +201,46 @@ def test_batched_channels_full_size_graph_step_on_sampled_windows():
     finally:
         for c in cs:
             c.close()
+
+
+def test_served_largest_room_alone_in_the_mix_and_on_oracle_windows():
+    """The served stream's largest room (256 x 128 x 128) admitted with a mid-size room, a
+    channel and a second copy of itself stepped one step less: every result equal alone and in
+    the mix (the reduced-precision bound), and the room's last step, from the copy's state and
+    given the pressure it solved for, against the oracle on windows."""
+    _, specs = cases.served_rooms(400, seed=0)
+    rooms = [sp for sp in specs if sp.buoyancy]
+    big = max(rooms, key=lambda sp: sp.cells)
+    mid = next(sp for sp in rooms if sp.nx == 160)
+    chan = next(sp for sp in specs if not sp.buoyancy)
+    assert (big.nx, big.ny, big.nz) == SERVED_BIG
+    reqs = [(big, 3), (mid, 3), (big, 2), (chan, 2)]
+    alone = []
+    for spec, n in reqs:
+        with binding.Case(spec) as c:
+            c.step(n)
+            alone.append(c.read())
+    with binding.Server(budget_bytes=40 << 30, keep_results=True) as srv:
+        ids = [srv.submit(*reqs[0])]
+        done = srv.poll(chunk=1)
+        for spec, n in reqs[1:]:   # admitted while the first runs
+            ids.append(srv.submit(spec, n))
+            done += srv.poll(chunk=1)
+        for _ in range(20):
+            if len(done) == len(reqs):
+                break
+            done += srv.poll(chunk=1)
+        got = {i: srv.read(i) for i in ids}
+    res = {d["id"]: d for d in done}
+    assert len(done) == len(reqs)
+    for i, (spec, n), a in zip(ids, reqs, alone):
+        assert res[i]["status"] == binding.OK and res[i]["steps"] == n
+        for f in cases.FIELDS:
+            e = float(np.max(np.abs(got[i][f] - a[f]))) / max(float(np.max(np.abs(a[f]))), 1e-300)
+            assert e <= TOL_STEP, (i, f, e)
+    x0 = [got[ids[2]][f] for f in STATE]
+    x1 = {f: got[ids[0]][f] for f in STATE}
+    dt = stable_dt(Geometry(big), x0, time_step(big)) if big.dt_adapt else time_step(big)
+    wins = [ow.Window(big, c, WIN) for c in centers(big, seed=3)]
+    want = {id(w): w.step(x0, got[ids[0]]["p"], dt) for w in wins}
+    check(wins, lambda w: want[id(w)][0], x1, STATE, "served room step", TOL_STEP)
