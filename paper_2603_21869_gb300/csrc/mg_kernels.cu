@@ -1264,32 +1264,15 @@ struct FcgUpdVK {
         }
     }
 };
-
-// Trilinear prolongation and correction, four x cells per thread: a lane's
-// four fine cells have the coarse parents I0 = i/2 and I0 + 1 (two
-// consecutive coarse cells, one float2 per coarse row), their x neighbours
-// I0 - 1 and I0 + 2 come from the adjacent lanes; per fine cell the weights
-// are 3/4 for the parent and 1/4 for the neighbour on the cell's side, per
-// axis (Eq. prolongation); a neighbour beyond a domain face is the coarse
-// cell's ghost, as in prolong_at.  Needs the x and y axes
-// active and nx % 4 = 0.
-template <class TI> struct Vec2;
-template <> struct Vec2<float> {
-    static __device__ __forceinline__ void load(const float* p, int c, float& a, float& b) {
-        const float2 v = __ldg(reinterpret_cast<const float2*>(p + c));
-        a = v.x;
-        b = v.y;
-    }
-};
-template <> struct Vec2<__nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16* p, int c, float& a, float& b) {
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(p + c);
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
-        a = v.x;
-        b = v.y;
-    }
-};
-
+// Trilinear prolongation and correction, W consecutive x cells per thread (4 or
+// 8): a lane's fine cells have the H = W/2 coarse parents I0 = i/2 .. I0 + H - 1
+// (one load per coarse row).  The four coarse rows around the fine row (parent
+// and neighbour along y and z, ghosts signed) are combined with their y-z
+// weights first, then interpolated along x, the x neighbours I0 - 1 and I0 + H
+// coming from the adjacent lanes.  Per fine cell and axis the weights are 3/4
+// for the parent and 1/4 for the neighbour on the cell's side (Eq.
+// prolongation); a neighbour beyond a domain face is the coarse cell's ghost,
+// as in prolong_at.  Needs the x and y axes active and nx % W = 0.
 template <class TI, int W>
 struct ProlongVK {
     static constexpr int kThreads = TX * TY;
@@ -1552,12 +1535,6 @@ __device__ void RRWalkK<TI>::run(const BlockAt& at) const {
 // ------------------------------------------------------------------ coarse levels in one CTA
 // V-cycle over levels lc..L-1 in shared memory: reads r on level lc from
 // global memory, writes the correction e on level lc.
-template <class C>
-__device__ __forceinline__ C cta_apply_A(const LevelDev& L, uint32_t f, const C* e, int c, C eP) {
-    // e lives in shared memory: plain loads (the read-only global path does not apply)
-    return apply_A_with<C>(L, f, c, eP, [&](int q) { return e[q]; });
-}
-
 // A level's stencil constants in registers for the coarse CTA's cell loops (the level
 // descriptions live in shared memory, which the loops also write, so the compiler would reload
 // them for every cell), and A e with them: a cell whose face codes are all 0 on three active
