@@ -54,8 +54,8 @@ NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's denominator is
 TRAFFIC = {
     # fcg_L0 = FcgDotVK + FcgUpdVK on the room with BF16 corrections, one iteration with a kept
     # direction: ncu dram__bytes_read.sum + dram__bytes_write.sum of the two launches
-    # (204.6 + 449.1 MB; the algorithmic 42 B per cell is 704.6 MB)
-    ("room", "bf16", "fcg_L0"): {"bytes": 653.7e6, "src": "mg_kernels.cu", "sha": "7b2c9c5597e16274"},
+    # (201.6 + 446.3 MB; the algorithmic 42 B per cell is 704.6 MB)
+    ("room", "bf16", "fcg_L0"): {"bytes": 647.9e6, "src": "mg_kernels.cu", "sha": "78e46771d833774f"},
 }
 # the batched sweep launch covers every case's finest level: DRAM bytes per finest-level cell
 TRAFFIC_PER_CELL = {}
